@@ -1,0 +1,150 @@
+"""FP64 CPU oracle for Armadillo-style expression trees -- TEST INFRASTRUCTURE.
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The GPU library never calls it and the
+two share no code: the oracle is plain C (``oracle.c``) built with gcc and
+driven here through ``ctypes`` with host NumPy arrays.
+
+Every function follows the plain definition of the operation it evaluates
+(Bandicoot paper, Sec. 2-4: Armadillo function semantics, expression trees of
+Op/eOp/eGlue nodes evaluated on assignment, column-major storage); see
+``oracle.h`` for the program format and the error-bound model.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "liborc.so")
+_lock = threading.Lock()
+_lib = None
+
+DTYPES = {"f32": 0, "f64": 1, "bf16": 2, "f16": 3, "i32": 4}
+_NP_OF = {"f32": np.float32, "f64": np.float64, "bf16": np.uint16, "f16": np.uint16, "i32": np.int32}
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liborc.so with gcc (no FMA contraction, no fast-math)."""
+    src = os.path.join(_HERE, "oracle.c")
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= max(
+        os.path.getmtime(src), os.path.getmtime(os.path.join(_HERE, "oracle.h"))
+    ):
+        return _LIB_PATH
+    tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
+    cmd = ["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+           "-D_POSIX_C_SOURCE=200809L", "-Wall", "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Mat(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("dtype", ctypes.c_int32),
+                ("n_rows", ctypes.c_int64), ("n_cols", ctypes.c_int64), ("ld", ctypes.c_int64)]
+
+
+class _Res(ctypes.Structure):
+    _fields_ = [("is_int", ctypes.c_int32), ("is_reduction", ctypes.c_int32),
+                ("n_rows", ctypes.c_int64), ("n_cols", ctypes.c_int64),
+                ("v", ctypes.POINTER(ctypes.c_double)), ("b", ctypes.POINTER(ctypes.c_double)),
+                ("iv", ctypes.POINTER(ctypes.c_int64)), ("div_by_zero", ctypes.c_int32),
+                ("err", ctypes.c_char * 256)]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            lib.orc_eval.argtypes = [ctypes.c_char_p, ctypes.POINTER(_Mat), ctypes.c_int32,
+                                     ctypes.c_int32, ctypes.POINTER(_Res)]
+            lib.orc_eval.restype = ctypes.c_int
+            lib.orc_free.argtypes = [ctypes.POINTER(_Res)]
+            lib.orc_sum_neumaier.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.c_int64]
+            lib.orc_sum_neumaier.restype = ctypes.c_double
+            lib.orc_ulp.argtypes = [ctypes.c_double, ctypes.c_int32]
+            lib.orc_ulp.restype = ctypes.c_double
+            _lib = lib
+    return _lib
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+class Result:
+    """Oracle output: ``value`` (float64 or int64 ndarray, column-major shape
+    (n_rows, n_cols)), ``bound`` (float64 forward error bound, or None for
+    integer trees), ``is_reduction`` and ``div_by_zero``."""
+
+    def __init__(self, value, bound, is_reduction, div_by_zero):
+        self.value = value
+        self.bound = bound
+        self.is_reduction = is_reduction
+        self.div_by_zero = div_by_zero
+
+
+def _as_mat(a: np.ndarray, dtype: str):
+    if a.ndim == 1:
+        a = a.reshape(-1, 1, order="F")
+    if a.ndim != 2:
+        raise ValueError("leaves must be 1-D or 2-D")
+    want = np.dtype(_NP_OF[dtype])
+    if a.dtype != want:
+        raise TypeError("leaf dtype %s does not match %s" % (a.dtype, dtype))
+    item = a.itemsize
+    n_rows, n_cols = a.shape
+    # column-major: unit row stride; ld = column stride (any ld >= n_rows)
+    if n_rows > 1 and a.strides[0] != item:
+        a = np.asfortranarray(a)
+    ld = a.strides[1] // item if n_cols > 1 else max(n_rows, 1)
+    if n_cols > 1 and a.strides[1] % item:
+        a = np.asfortranarray(a)
+        ld = n_rows
+    return _Mat(a.ctypes.data, DTYPES[dtype], n_rows, n_cols, max(ld, n_rows)), a
+
+
+def evaluate(program: str, leaves, dtype: str, out_dtype: str | None = None) -> Result:
+    """Evaluate an RPN ``program`` over host ``leaves`` (all of ``dtype``).
+
+    BF16/FP16 leaves are passed as uint16 bit patterns."""
+    lib = _load()
+    mats, keep = [], []
+    for a in leaves:
+        m, held = _as_mat(np.asarray(a), dtype)
+        mats.append(m)
+        keep.append(held)
+    arr = (_Mat * len(mats))(*mats)
+    res = _Res()
+    od = -1 if out_dtype is None else DTYPES[out_dtype]
+    rc = lib.orc_eval(program.encode(), arr, len(mats), od, ctypes.byref(res))
+    if rc != 0:
+        raise OracleError(res.err.decode())
+    try:
+        n = res.n_rows * res.n_cols
+        shape = (res.n_rows, res.n_cols)
+        if res.is_int:
+            value = np.ctypeslib.as_array(res.iv, shape=(max(n, 1),))[:n].copy().reshape(shape, order="F")
+            bound = None
+        else:
+            value = np.ctypeslib.as_array(res.v, shape=(max(n, 1),))[:n].copy().reshape(shape, order="F")
+            bound = np.ctypeslib.as_array(res.b, shape=(max(n, 1),))[:n].copy().reshape(shape, order="F")
+        return Result(value, bound, bool(res.is_reduction), bool(res.div_by_zero))
+    finally:
+        lib.orc_free(ctypes.byref(res))
+
+
+def sum_neumaier(x: np.ndarray) -> float:
+    lib = _load()
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    return lib.orc_sum_neumaier(x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), x.size)
+
+
+def ulp(x: float, dtype: str) -> float:
+    return _load().orc_ulp(float(x), DTYPES[dtype])

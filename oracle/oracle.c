@@ -1,0 +1,755 @@
+/*
+ * oracle.c -- FP64 CPU oracle for Armadillo-style expression trees.
+ *
+ * TEST INFRASTRUCTURE ONLY (tests, smoke check, CPU-baseline leg of the
+ * benchmark).  Plain, slow, one operation at a time; every node materialises
+ * a full matrix.  See oracle.h for the program format and the error-bound
+ * model.
+ *
+ * Definitions followed (Bandicoot paper):
+ *   Sec. 2  -- Armadillo-compatible function semantics: accu, sum/mean along a
+ *             dimension, statistics such as variance, submatrix views.
+ *   Sec. 3  -- Op (trans), eOp (element-wise unary incl. scalar forms),
+ *             eGlue (element-wise binary: + - % /) and delayed evaluation:
+ *             the fused result equals the eager one-op-at-a-time result up to
+ *             rounding, which is what this walker computes.
+ *   Sec. 4  -- column-major storage: element (i,j) at data[i + j*ld].
+ * Readings where the paper is silent (documented with the design):
+ *   - a scalar in a tree is converted to the element type (compute type for
+ *     BF16/FP16 storage), as an Armadillo scalar of type eT is;
+ *   - INT32 + - * wrap modulo 2^32; / truncates toward zero, a zero divisor
+ *     gives 0 and raises the div_by_zero flag; reductions are exact int64
+ *     (modulo 2^64); dot multiplies exactly in int64;
+ *   - var uses N-1 (norm_type 0) or N (norm_type 1), two passes; N==1 gives 0;
+ *   - norm of a vector is the 2-norm; matrices take the Frobenius norm only.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ */
+/* helpers                                                             */
+/* ------------------------------------------------------------------ */
+
+double orc_ulp(double x, int32_t dtype) {
+  int e;
+  int mant_bits, emin;
+  x = fabs(x);
+  switch (dtype) {
+    case ORC_F32: mant_bits = 24; emin = -126; break;
+    case ORC_F64: mant_bits = 53; emin = -1022; break;
+    case ORC_BF16: mant_bits = 8; emin = -126; break;
+    case ORC_F16: mant_bits = 11; emin = -14; break;
+    default: return 0.0;
+  }
+  if (isnan(x) || isinf(x)) return 0.0;
+  (void)frexp(x, &e); /* x = m * 2^e, m in [0.5, 1) -> x in [2^(e-1), 2^e) */
+  if (x == 0.0 || e - 1 < emin) e = emin + 1;
+  return ldexp(1.0, e - mant_bits);
+}
+
+double orc_sum_neumaier(const double* x, int64_t n) {
+  double s = 0.0, c = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    double t = s + x[i];
+    if (fabs(s) >= fabs(x[i]))
+      c += (s - t) + x[i];
+    else
+      c += (x[i] - t) + s;
+    s = t;
+  }
+  return s + c;
+}
+
+static double sum_plain(const double* x, int64_t n) {
+  double s = 0.0;
+  for (int64_t i = 0; i < n; ++i) s += x[i];
+  return s;
+}
+
+static int64_t wrap32(int64_t x) { return (int64_t)(int32_t)(uint32_t)(uint64_t)x; }
+
+static double bf16_to_double(uint16_t h) {
+  uint32_t u = (uint32_t)h << 16;
+  float f;
+  memcpy(&f, &u, sizeof f);
+  return (double)f;
+}
+
+static double f16_to_double(uint16_t h) {
+  int sign = (h >> 15) & 1;
+  int e = (h >> 10) & 31;
+  int m = h & 1023;
+  double v;
+  if (e == 0)
+    v = ldexp((double)m, -24);
+  else if (e == 31)
+    v = (m == 0) ? INFINITY : NAN;
+  else
+    v = ldexp((double)(1024 + m), e - 25);
+  return sign ? -v : v;
+}
+
+/* |d| * b, with 0 when b == 0 (so an exact input never turns inf*0 into NaN) */
+static double mulb(double d, double b) { return b == 0.0 ? 0.0 : fabs(d) * b; }
+
+/* ------------------------------------------------------------------ */
+/* values on the evaluation stack                                      */
+/* ------------------------------------------------------------------ */
+
+enum { V_MAT = 0, V_SCALAR = 1 };
+
+typedef struct {
+  int kind;
+  int64_t r, c;
+  double* v;   /* FP values */
+  double* b;   /* FP bounds */
+  int64_t* iv; /* integer values */
+  double k;    /* scalar (already converted to the element type) */
+} val_t;
+
+typedef struct {
+  int is_int;
+  int ct; /* compute dtype: ORC_F32, ORC_F64 or ORC_I32 */
+  int div0;
+  char* err;
+} ctx_t;
+
+static void val_free(val_t* x) {
+  free(x->v);
+  free(x->b);
+  free(x->iv);
+  x->v = x->b = NULL;
+  x->iv = NULL;
+}
+
+static int val_alloc(ctx_t* cx, val_t* x, int64_t r, int64_t c) {
+  size_t n = (size_t)(r * c);
+  size_t nn = n ? n : 1;
+  x->kind = V_MAT;
+  x->r = r;
+  x->c = c;
+  x->v = x->b = NULL;
+  x->iv = NULL;
+  if (cx->is_int) {
+    x->iv = (int64_t*)calloc(nn, sizeof(int64_t));
+    if (!x->iv) return -1;
+  } else {
+    x->v = (double*)calloc(nn, sizeof(double));
+    x->b = (double*)calloc(nn, sizeof(double));
+    if (!x->v || !x->b) return -1;
+  }
+  return 0;
+}
+
+/* local rounding allowance of a node in the compute type, plus the
+ * oracle's own FP64 rounding of the same node */
+static double local(ctx_t* cx, double v, double c_dev, double c_orc) {
+  if (!isfinite(v)) return 0.0;
+  return c_dev * orc_ulp(v, cx->ct) + c_orc * orc_ulp(v, ORC_F64);
+}
+
+static double finite_or_zero_bound(double v, double b) { return isfinite(v) ? b : 0.0; }
+
+/* Largest magnitude that still rounds to a finite value of the format (the
+ * IEEE overflow threshold: max finite + half an ulp of max finite). */
+static double overflow_threshold(int32_t dtype) {
+  switch (dtype) {
+    case ORC_F32: return ldexp(2.0 - ldexp(1.0, -24), 127);   /* (2 - 2^-24) 2^127 */
+    case ORC_BF16: return ldexp(2.0 - ldexp(1.0, -8), 127);   /* (2 - 2^-8)  2^127 */
+    case ORC_F16: return 65520.0;                              /* (2 - 2^-11) 2^15  */
+    default: return INFINITY;
+  }
+}
+
+/* A node result outside the compute type's range is what an IEEE device
+ * returns for it: +-inf (exact, so its bound is 0). */
+static void clamp_to_range(ctx_t* cx, double* v, double* b) {
+  if (cx->ct == ORC_F32 && isfinite(*v) && fabs(*v) >= overflow_threshold(ORC_F32)) {
+    *v = copysign(INFINITY, *v);
+    *b = 0.0;
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* leaves                                                              */
+/* ------------------------------------------------------------------ */
+
+static int load_leaf(ctx_t* cx, const orc_mat* m, val_t* out) {
+  if (m->n_rows < 0 || m->n_cols < 0 || m->ld < m->n_rows) {
+    snprintf(cx->err, 256, "leaf: bad shape");
+    return -1;
+  }
+  if (val_alloc(cx, out, m->n_rows, m->n_cols)) {
+    snprintf(cx->err, 256, "out of memory");
+    return -1;
+  }
+  for (int64_t j = 0; j < m->n_cols; ++j)
+    for (int64_t i = 0; i < m->n_rows; ++i) {
+      int64_t s = i + j * m->ld, d = i + j * m->n_rows;
+      switch (m->dtype) {
+        case ORC_F32: out->v[d] = (double)((const float*)m->data)[s]; break;
+        case ORC_F64: out->v[d] = ((const double*)m->data)[s]; break;
+        case ORC_BF16: out->v[d] = bf16_to_double(((const uint16_t*)m->data)[s]); break;
+        case ORC_F16: out->v[d] = f16_to_double(((const uint16_t*)m->data)[s]); break;
+        case ORC_I32: out->iv[d] = (int64_t)((const int32_t*)m->data)[s]; break;
+      }
+    }
+  return 0; /* stored values are exact: bounds stay 0 */
+}
+
+/* ------------------------------------------------------------------ */
+/* element-wise operations                                             */
+/* ------------------------------------------------------------------ */
+
+enum { U_NEG, U_EXP, U_LOG, U_ABS, U_SQUARE, U_SQRT, U_TRANS };
+enum { B_PLUS, B_MINUS, B_SCHUR, B_DIV, B_TIMES };
+
+static int unary(ctx_t* cx, int op, val_t* x, val_t* out) {
+  int64_t r = x->r, c = x->c, n = r * c;
+  if (op == U_TRANS) {
+    if (val_alloc(cx, out, c, r)) return -1;
+    for (int64_t j = 0; j < c; ++j)
+      for (int64_t i = 0; i < r; ++i) {
+        /* trans(X)(j,i) = X(i,j) */
+        int64_t s = i + j * r, d = j + i * c;
+        if (cx->is_int)
+          out->iv[d] = x->iv[s];
+        else {
+          out->v[d] = x->v[s];
+          out->b[d] = x->b[s];
+        }
+      }
+    return 0;
+  }
+  if (val_alloc(cx, out, r, c)) return -1;
+  if (cx->is_int) {
+    for (int64_t t = 0; t < n; ++t) {
+      int64_t a = x->iv[t];
+      switch (op) {
+        case U_NEG: out->iv[t] = wrap32(-a); break;
+        case U_ABS: out->iv[t] = wrap32(a < 0 ? -a : a); break;
+        case U_SQUARE: out->iv[t] = wrap32((int64_t)((uint64_t)a * (uint64_t)a)); break;
+        default:
+          snprintf(cx->err, 256, "exp/log/sqrt are not defined for INT32 trees");
+          return -1;
+      }
+    }
+    return 0;
+  }
+  for (int64_t t = 0; t < n; ++t) {
+    double a = x->v[t], ba = x->b[t], v = 0.0, bv = 0.0;
+    switch (op) {
+      case U_NEG: v = -a; bv = ba; break;
+      case U_ABS: v = fabs(a); bv = ba; break;
+      case U_EXP:
+        v = exp(a);
+        bv = (ba == 0.0) ? 0.0 : v * expm1(ba);
+        bv += local(cx, v, 4.0, 2.0);
+        break;
+      case U_LOG:
+        v = log(a);
+        if (ba == 0.0)
+          bv = 0.0;
+        else if (ba < fabs(a))
+          bv = -log1p(-ba / fabs(a));
+        else
+          bv = INFINITY;
+        bv += local(cx, v, 4.0, 2.0);
+        break;
+      case U_SQRT: {
+        v = sqrt(a);
+        if (ba == 0.0 || !(a >= 0.0))
+          bv = 0.0;
+        else {
+          double up = ba / (sqrt(a + ba) + sqrt(a));
+          double lo = (a - ba > 0.0) ? ba / (sqrt(a) + sqrt(a - ba)) : sqrt(a);
+          bv = up > lo ? up : lo;
+        }
+        bv += local(cx, v, 4.0, 1.0);
+        break;
+      }
+      case U_SQUARE:
+        v = a * a;
+        bv = mulb(2.0 * a, ba) + ba * ba + local(cx, v, 2.0, 1.0);
+        break;
+    }
+    bv = finite_or_zero_bound(v, bv);
+    clamp_to_range(cx, &v, &bv);
+    out->v[t] = v;
+    out->b[t] = bv;
+  }
+  return 0;
+}
+
+/* integer binary op with the INT32 tree semantics */
+static int64_t ibin(ctx_t* cx, int op, int64_t a, int64_t b) {
+  switch (op) {
+    case B_PLUS: return wrap32(a + b);
+    case B_MINUS: return wrap32(a - b);
+    case B_SCHUR:
+    case B_TIMES: return wrap32((int64_t)((uint64_t)a * (uint64_t)b));
+    case B_DIV:
+      if (b == 0) {
+        cx->div0 = 1;
+        return 0;
+      }
+      return wrap32(a / b); /* C99 division truncates toward zero */
+  }
+  return 0;
+}
+
+/* FP binary op: value and propagated bound */
+static void fbin(ctx_t* cx, int op, double a, double ba, double b, double bb, double* v, double* bv) {
+  double r = 0.0, e = 0.0;
+  switch (op) {
+    case B_PLUS:
+      r = a + b;
+      e = ba + bb;
+      break;
+    case B_MINUS:
+      r = a - b;
+      e = ba + bb;
+      break;
+    case B_SCHUR:
+    case B_TIMES:
+      r = a * b;
+      e = mulb(a, bb) + mulb(b, ba) + ((ba == 0.0 || bb == 0.0) ? 0.0 : ba * bb);
+      break;
+    case B_DIV:
+      r = a / b;
+      if (ba == 0.0 && bb == 0.0)
+        e = 0.0;
+      else if (bb >= fabs(b))
+        e = INFINITY;
+      else
+        e = (ba + mulb(r, bb)) / (fabs(b) - bb);
+      break;
+  }
+  e += local(cx, r, 2.0, 1.0);
+  e = finite_or_zero_bound(r, e);
+  clamp_to_range(cx, &r, &e);
+  *v = r;
+  *bv = e;
+}
+
+static int binary(ctx_t* cx, int op, val_t* x, val_t* y, val_t* out) {
+  int xs = x->kind == V_SCALAR, ys = y->kind == V_SCALAR;
+  if (xs && ys) {
+    snprintf(cx->err, 256, "operation between two scalars");
+    return -1;
+  }
+  if (op == B_TIMES && !xs && !ys) {
+    snprintf(cx->err, 256, "'*' of two matrices is matrix multiplication, not element-wise");
+    return -1;
+  }
+  if (op == B_SCHUR && (xs || ys)) {
+    snprintf(cx->err, 256, "'%%' needs two matrices");
+    return -1;
+  }
+  if (!xs && !ys && (x->r != y->r || x->c != y->c)) {
+    snprintf(cx->err, 256, "incompatible matrix dimensions: %lldx%lld and %lldx%lld", (long long)x->r,
+             (long long)x->c, (long long)y->r, (long long)y->c);
+    return -1;
+  }
+  val_t* m = xs ? y : x;
+  if (val_alloc(cx, out, m->r, m->c)) return -1;
+  int64_t n = m->r * m->c;
+  for (int64_t t = 0; t < n; ++t) {
+    if (cx->is_int) {
+      int64_t a = xs ? (int64_t)x->k : x->iv[t];
+      int64_t b = ys ? (int64_t)y->k : y->iv[t];
+      out->iv[t] = ibin(cx, op, a, b);
+    } else {
+      double a = xs ? x->k : x->v[t], ba = xs ? 0.0 : x->b[t];
+      double b = ys ? y->k : y->v[t], bb = ys ? 0.0 : y->b[t];
+      fbin(cx, op, a, ba, b, bb, &out->v[t], &out->b[t]);
+    }
+  }
+  return 0;
+}
+
+static int submat(ctx_t* cx, val_t* x, int64_t r0, int64_t c0, int64_t nr, int64_t nc, val_t* out) {
+  if (x->kind != V_MAT || r0 < 0 || c0 < 0 || nr < 0 || nc < 0 || r0 + nr > x->r || c0 + nc > x->c) {
+    snprintf(cx->err, 256, "submat: view out of bounds");
+    return -1;
+  }
+  if (val_alloc(cx, out, nr, nc)) return -1;
+  for (int64_t j = 0; j < nc; ++j)
+    for (int64_t i = 0; i < nr; ++i) {
+      /* submat(i,j) = X(r0+i, c0+j) */
+      int64_t s = (r0 + i) + (c0 + j) * x->r, d = i + j * nr;
+      if (cx->is_int)
+        out->iv[d] = x->iv[s];
+      else {
+        out->v[d] = x->v[s];
+        out->b[d] = x->b[s];
+      }
+    }
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* reductions                                                          */
+/* ------------------------------------------------------------------ */
+
+enum { R_ACCU, R_SUM0, R_SUM1, R_MEAN, R_MEAN0, R_MEAN1, R_DOT, R_NORM, R_NORMFRO, R_VAR0, R_VAR1 };
+
+static int alloc_result(orc_result* res, int is_int, int64_t r, int64_t c) {
+  size_t n = (size_t)(r * c);
+  size_t nn = n ? n : 1;
+  res->n_rows = r;
+  res->n_cols = c;
+  if (is_int) {
+    res->iv = (int64_t*)calloc(nn, sizeof(int64_t));
+    return res->iv ? 0 : -1;
+  }
+  res->v = (double*)calloc(nn, sizeof(double));
+  res->b = (double*)calloc(nn, sizeof(double));
+  return (res->v && res->b) ? 0 : -1;
+}
+
+/* sum of a strided selection: elements x[off + t*stride], t < n */
+static void gather(const double* x, int64_t off, int64_t stride, int64_t n, double* buf) {
+  for (int64_t t = 0; t < n; ++t) buf[t] = x[off + t * stride];
+}
+
+static int reduce(ctx_t* cx, int kind, val_t* x, val_t* y, orc_result* res) {
+  int64_t r = x->r, c = x->c, n = r * c;
+  if (cx->is_int && (kind == R_MEAN || kind == R_MEAN0 || kind == R_MEAN1 || kind == R_NORM ||
+                     kind == R_NORMFRO || kind == R_VAR0 || kind == R_VAR1)) {
+    snprintf(cx->err, 256, "mean/norm/var are not defined for INT32 trees");
+    return -1;
+  }
+  if (kind == R_NORM && r != 1 && c != 1) {
+    snprintf(cx->err, 256, "norm: the 2-norm is defined here for vectors only; use norm:fro");
+    return -1;
+  }
+  res->is_reduction = 1;
+  if (kind == R_SUM0 || kind == R_MEAN0 || kind == R_SUM1 || kind == R_MEAN1) {
+    int by_col = (kind == R_SUM0 || kind == R_MEAN0);
+    int64_t nout = by_col ? c : r, len = by_col ? r : c;
+    if (alloc_result(res, cx->is_int, by_col ? 1 : r, by_col ? c : 1)) return -1;
+    if (cx->is_int) {
+      for (int64_t o = 0; o < nout; ++o) {
+        uint64_t s = 0;
+        for (int64_t t = 0; t < len; ++t) s += (uint64_t)x->iv[by_col ? (t + o * r) : (o + t * r)];
+        res->iv[o] = (int64_t)s;
+      }
+      return 0;
+    }
+    double* buf = (double*)malloc((size_t)(len ? len : 1) * sizeof(double));
+    double* bbuf = (double*)malloc((size_t)(len ? len : 1) * sizeof(double));
+    if (!buf || !bbuf) return -1;
+    for (int64_t o = 0; o < nout; ++o) {
+      gather(x->v, by_col ? o * r : o, by_col ? 1 : r, len, buf);
+      gather(x->b, by_col ? o * r : o, by_col ? 1 : r, len, bbuf);
+      double s = orc_sum_neumaier(buf, len), e = sum_plain(bbuf, len);
+      if (kind == R_MEAN0 || kind == R_MEAN1) {
+        s = s / (double)len;
+        e = e / (double)len;
+      }
+      res->v[o] = s;
+      res->b[o] = finite_or_zero_bound(s, e);
+    }
+    free(buf);
+    free(bbuf);
+    return 0;
+  }
+  if (alloc_result(res, cx->is_int, 1, 1)) return -1;
+  if (cx->is_int) {
+    uint64_t s = 0;
+    if (kind == R_DOT) {
+      for (int64_t t = 0; t < n; ++t) s += (uint64_t)(x->iv[t] * y->iv[t]);
+    } else {
+      for (int64_t t = 0; t < n; ++t) s += (uint64_t)x->iv[t];
+    }
+    res->iv[0] = (int64_t)s;
+    return 0;
+  }
+  double* buf = (double*)malloc((size_t)(n ? n : 1) * sizeof(double));
+  double* bbuf = (double*)malloc((size_t)(n ? n : 1) * sizeof(double));
+  if (!buf || !bbuf) return -1;
+  double s = 0.0, e = 0.0;
+  switch (kind) {
+    case R_ACCU:
+    case R_MEAN:
+      s = orc_sum_neumaier(x->v, n);
+      e = sum_plain(x->b, n);
+      if (kind == R_MEAN) {
+        s /= (double)n; /* empty: 0/0 = NaN */
+        e /= (double)n;
+      }
+      break;
+    case R_DOT:
+      for (int64_t t = 0; t < n; ++t) {
+        buf[t] = x->v[t] * y->v[t];
+        bbuf[t] = mulb(x->v[t], y->b[t]) + mulb(y->v[t], x->b[t]);
+      }
+      s = orc_sum_neumaier(buf, n);
+      e = sum_plain(bbuf, n);
+      break;
+    case R_NORM:
+    case R_NORMFRO: {
+      for (int64_t t = 0; t < n; ++t) {
+        buf[t] = x->v[t] * x->v[t];
+        bbuf[t] = mulb(2.0 * x->v[t], x->b[t]);
+      }
+      double ss = orc_sum_neumaier(buf, n), es = sum_plain(bbuf, n);
+      s = sqrt(ss);
+      e = (es == 0.0) ? 0.0 : (s > 0.0 ? es / (2.0 * s) : sqrt(es));
+      break;
+    }
+    case R_VAR0:
+    case R_VAR1: {
+      if (n == 0) {
+        s = NAN;
+        break;
+      }
+      if (n == 1) {
+        s = 0.0;
+        break;
+      }
+      /* pass 1: mean; pass 2: centred sum of squares */
+      double mu = orc_sum_neumaier(x->v, n) / (double)n;
+      for (int64_t t = 0; t < n; ++t) {
+        double d = x->v[t] - mu;
+        buf[t] = d * d;
+        bbuf[t] = mulb(2.0 * d, x->b[t]);
+      }
+      double den = (kind == R_VAR0) ? (double)(n - 1) : (double)n;
+      s = orc_sum_neumaier(buf, n) / den;
+      e = sum_plain(bbuf, n) / den;
+      break;
+    }
+  }
+  free(buf);
+  free(bbuf);
+  res->v[0] = s;
+  res->b[0] = finite_or_zero_bound(s, e);
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* program walker                                                      */
+/* ------------------------------------------------------------------ */
+
+#define MAX_STACK 64
+
+static double to_elem_type(ctx_t* cx, double k, int* ok) {
+  *ok = 1;
+  if (cx->is_int) {
+    if (!isfinite(k) || k <= -2147483649.0 || k >= 2147483648.0) {
+      *ok = 0;
+      return 0;
+    }
+    return (double)(int32_t)k; /* truncation toward zero */
+  }
+  if (cx->ct == ORC_F32) return (double)(float)k;
+  return k;
+}
+
+int orc_eval(const char* program, const orc_mat* leaves, int32_t n_leaves, int32_t out_dtype,
+             orc_result* res) {
+  memset(res, 0, sizeof *res);
+  if (n_leaves < 1) {
+    snprintf(res->err, sizeof res->err, "no leaves");
+    return -1;
+  }
+  int dt = leaves[0].dtype;
+  for (int i = 1; i < n_leaves; ++i)
+    if (leaves[i].dtype != dt) {
+      snprintf(res->err, sizeof res->err, "all leaves must share one dtype");
+      return -1;
+    }
+  ctx_t cx;
+  cx.is_int = (dt == ORC_I32);
+  cx.ct = cx.is_int ? ORC_I32 : (dt == ORC_F64 ? ORC_F64 : ORC_F32);
+  cx.div0 = 0;
+  cx.err = res->err;
+  if (out_dtype < 0) out_dtype = dt;
+  res->is_int = cx.is_int;
+
+  val_t st[MAX_STACK];
+  int sp = 0, rc = -1, reduced = 0;
+  size_t plen = strlen(program);
+  char* buf = (char*)malloc(plen + 1);
+  memcpy(buf, program, plen + 1);
+  char* save = NULL;
+  for (char* tok = strtok_r(buf, " \t\n", &save); tok; tok = strtok_r(NULL, " \t\n", &save)) {
+    if (reduced) {
+      snprintf(res->err, sizeof res->err, "tokens after the reduction");
+      goto done;
+    }
+    if (sp >= MAX_STACK - 1) {
+      snprintf(res->err, sizeof res->err, "stack overflow");
+      goto done;
+    }
+    if (tok[0] >= 'A' && tok[0] <= 'H' && tok[1] == 0) {
+      int li = tok[0] - 'A';
+      if (li >= n_leaves) {
+        snprintf(res->err, sizeof res->err, "leaf %c not given", tok[0]);
+        goto done;
+      }
+      if (load_leaf(&cx, &leaves[li], &st[sp])) goto done;
+      sp++;
+      continue;
+    }
+    if (tok[0] == '#') {
+      int ok;
+      char* end;
+      double k = strtod(tok + 1, &end);
+      if (*end) {
+        snprintf(res->err, sizeof res->err, "bad scalar '%s'", tok);
+        goto done;
+      }
+      memset(&st[sp], 0, sizeof st[sp]);
+      st[sp].kind = V_SCALAR;
+      st[sp].k = to_elem_type(&cx, k, &ok);
+      if (!ok) {
+        snprintf(res->err, sizeof res->err, "scalar %g does not fit INT32", k);
+        goto done;
+      }
+      sp++;
+      continue;
+    }
+    int bop = -1, uop = -1, rop = -1;
+    if (!strcmp(tok, "+")) bop = B_PLUS;
+    else if (!strcmp(tok, "-")) bop = B_MINUS;
+    else if (!strcmp(tok, "%")) bop = B_SCHUR;
+    else if (!strcmp(tok, "/")) bop = B_DIV;
+    else if (!strcmp(tok, "*")) bop = B_TIMES;
+    else if (!strcmp(tok, "neg")) uop = U_NEG;
+    else if (!strcmp(tok, "exp")) uop = U_EXP;
+    else if (!strcmp(tok, "log")) uop = U_LOG;
+    else if (!strcmp(tok, "abs")) uop = U_ABS;
+    else if (!strcmp(tok, "square")) uop = U_SQUARE;
+    else if (!strcmp(tok, "sqrt")) uop = U_SQRT;
+    else if (!strcmp(tok, "trans")) uop = U_TRANS;
+    else if (!strcmp(tok, "accu")) rop = R_ACCU;
+    else if (!strcmp(tok, "sum:0")) rop = R_SUM0;
+    else if (!strcmp(tok, "sum:1")) rop = R_SUM1;
+    else if (!strcmp(tok, "mean")) rop = R_MEAN;
+    else if (!strcmp(tok, "mean:0")) rop = R_MEAN0;
+    else if (!strcmp(tok, "mean:1")) rop = R_MEAN1;
+    else if (!strcmp(tok, "dot")) rop = R_DOT;
+    else if (!strcmp(tok, "norm")) rop = R_NORM;
+    else if (!strcmp(tok, "norm:fro")) rop = R_NORMFRO;
+    else if (!strcmp(tok, "var") || !strcmp(tok, "var:0")) rop = R_VAR0;
+    else if (!strcmp(tok, "var:1")) rop = R_VAR1;
+
+    if (!strncmp(tok, "submat:", 7)) {
+      long long r0, c0, nr, nc;
+      if (sscanf(tok + 7, "%lld:%lld:%lld:%lld", &r0, &c0, &nr, &nc) != 4) {
+        snprintf(res->err, sizeof res->err, "bad submat token '%s'", tok);
+        goto done;
+      }
+      if (sp < 1) goto underflow;
+      val_t out;
+      if (submat(&cx, &st[sp - 1], r0, c0, nr, nc, &out)) goto done;
+      val_free(&st[sp - 1]);
+      st[sp - 1] = out;
+    } else if (bop >= 0) {
+      if (sp < 2) goto underflow;
+      val_t out;
+      if (binary(&cx, bop, &st[sp - 2], &st[sp - 1], &out)) goto done;
+      val_free(&st[sp - 2]);
+      val_free(&st[sp - 1]);
+      st[sp - 2] = out;
+      sp--;
+    } else if (uop >= 0) {
+      if (sp < 1) goto underflow;
+      if (st[sp - 1].kind != V_MAT) {
+        snprintf(res->err, sizeof res->err, "'%s' needs a matrix", tok);
+        goto done;
+      }
+      val_t out;
+      if (unary(&cx, uop, &st[sp - 1], &out)) goto done;
+      val_free(&st[sp - 1]);
+      st[sp - 1] = out;
+    } else if (rop >= 0) {
+      int need = (rop == R_DOT) ? 2 : 1;
+      if (sp != need) {
+        snprintf(res->err, sizeof res->err, "reduction '%s' needs exactly %d matrix operand(s) on the stack",
+                 tok, need);
+        goto done;
+      }
+      for (int q = 0; q < need; ++q)
+        if (st[q].kind != V_MAT) {
+          snprintf(res->err, sizeof res->err, "reduction of a scalar");
+          goto done;
+        }
+      if (rop == R_DOT && (st[0].r * st[0].c != st[1].r * st[1].c)) {
+        snprintf(res->err, sizeof res->err, "dot: operands differ in number of elements");
+        goto done;
+      }
+      if (rop == R_DOT && (st[0].r != st[1].r || st[0].c != st[1].c)) {
+        snprintf(res->err, sizeof res->err, "dot: incompatible matrix dimensions");
+        goto done;
+      }
+      if (reduce(&cx, rop, &st[0], need == 2 ? &st[1] : NULL, res)) goto done;
+      reduced = 1;
+    } else {
+      snprintf(res->err, sizeof res->err, "unknown token '%s'", tok);
+      goto done;
+    }
+    continue;
+  underflow:
+    snprintf(res->err, sizeof res->err, "stack underflow at '%s'", tok);
+    goto done;
+  }
+  if (!reduced) {
+    if (sp != 1 || st[0].kind != V_MAT) {
+      snprintf(res->err, sizeof res->err, "program must leave exactly one matrix");
+      goto done;
+    }
+    res->is_reduction = 0;
+    res->n_rows = st[0].r;
+    res->n_cols = st[0].c;
+    if (cx.is_int) {
+      res->iv = st[0].iv;
+      st[0].iv = NULL;
+    } else {
+      int64_t n = st[0].r * st[0].c;
+      /* the stored result is rounded once more when it is narrower than
+       * the compute type */
+      if (out_dtype == ORC_BF16 || out_dtype == ORC_F16)
+        for (int64_t t = 0; t < n; ++t)
+          if (isfinite(st[0].v[t])) {
+            if (fabs(st[0].v[t]) >= overflow_threshold(out_dtype)) {
+              st[0].v[t] = copysign(INFINITY, st[0].v[t]); /* storage overflow */
+              st[0].b[t] = 0.0;
+            } else {
+              st[0].b[t] += 0.5 * orc_ulp(fabs(st[0].v[t]) + st[0].b[t], out_dtype);
+            }
+          }
+      res->v = st[0].v;
+      res->b = st[0].b;
+      st[0].v = st[0].b = NULL;
+    }
+  }
+  rc = 0;
+done:
+  for (int i = 0; i < sp; ++i) val_free(&st[i]);
+  free(buf);
+  res->div_by_zero = cx.div0;
+  if (rc) {
+    free(res->v);
+    free(res->b);
+    free(res->iv);
+    res->v = res->b = NULL;
+    res->iv = NULL;
+  }
+  return rc;
+}
+
+void orc_free(orc_result* res) {
+  free(res->v);
+  free(res->b);
+  free(res->iv);
+  res->v = res->b = NULL;
+  res->iv = NULL;
+}
