@@ -1,0 +1,273 @@
+/*
+ * coot.h -- C ABI of cootgb: fused evaluation of Armadillo-style matrix
+ * expression trees on one GB300 (sm_103a).
+ *
+ * The computation (Bandicoot paper, Sec. 3): a linear-algebra expression is
+ * captured as a tree of Op / eOp / Glue / eGlue nodes and evaluated only when
+ * it is assigned ("delayed evaluation"), so that the whole tree can be mapped
+ * onto a minimal set of GPU calls.  Here the element-wise part of a tree, the
+ * transposes and submatrix views of its leaves, and the reduction that
+ * consumes it are evaluated in one pass by a kernel generated for that tree
+ * (two passes for var).  Matrices are column-major device memory (Sec. 2 and
+ * Sec. 4: data lives in GPU memory, Armadillo's Mat<eT> layout).
+ *
+ * Conventions shared by every entry point
+ *   - Pointers inside coot_mat are DEVICE pointers; tree descriptors and the
+ *     arrays of coot_mat are HOST memory read during the call only.  The
+ *     caller owns every matrix and stream; the library never frees them.
+ *   - Element (i,j) of a coot_mat is at data[i + j*ld], ld >= n_rows
+ *     (ld is ignored when n_cols <= 1).
+ *   - Every call returns a coot_status and never throws; on failure
+ *     coot_last_error() holds a message for the calling thread.
+ *   - Launches are asynchronous on the given stream (a cudaStream_t; NULL is
+ *     the legacy default stream).  Results are valid once the stream reaches
+ *     them.
+ *   - Reduction results have the accumulation type of the storage type:
+ *     float for F32/BF16/F16, double for F64, int64_t for I32.
+ */
+#ifndef COOT_H
+#define COOT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define COOT_VERSION_MAJOR 1
+#define COOT_VERSION_MINOR 0
+
+#if defined(__GNUC__)
+#define COOT_API __attribute__((visibility("default")))
+#else
+#define COOT_API
+#endif
+
+/* cudaStream_t without the CUDA headers (same type). */
+typedef struct CUstream_st* coot_stream;
+
+typedef enum {
+  COOT_OK = 0,
+  COOT_ERR_INVALID = 1,      /* malformed descriptor / argument              */
+  COOT_ERR_SHAPE = 2,        /* incompatible matrix dimensions              */
+  COOT_ERR_DTYPE = 3,        /* dtype mismatch or op not defined for dtype  */
+  COOT_ERR_ALIAS = 4,        /* output overlaps an input in a racy way      */
+  COOT_ERR_JIT = 5,          /* NVRTC compile or module load failed         */
+  COOT_ERR_OOM = 6,          /* device allocation failed                    */
+  COOT_ERR_CUDA = 7,         /* a CUDA runtime call failed                  */
+  COOT_ERR_DEVICE_FLAG = 8,  /* a kernel raised a device-side error flag    */
+  COOT_ERR_TIMEOUT = 9,      /* reserved: no kernel here waits on anything  */
+  COOT_ERR_UNSUPPORTED = 10  /* valid request outside what is implemented   */
+} coot_status;
+
+typedef enum { COOT_F32 = 0, COOT_F64 = 1, COOT_BF16 = 2, COOT_F16 = 3, COOT_I32 = 4 } coot_dtype;
+
+/* A column-major matrix (Armadillo Mat<eT>; Col = n_cols 1, Row = n_rows 1). */
+typedef struct {
+  void* data;       /* device pointer to element (0,0)               */
+  int32_t dtype;    /* coot_dtype                                    */
+  int32_t reserved; /* must be 0                                     */
+  int64_t n_rows;
+  int64_t n_cols;
+  int64_t ld;       /* column stride in elements, >= n_rows          */
+} coot_mat;
+
+/* Node kinds (Sec. 3): N_TRANS is Op<T1,op_trans>; the unary and scalar
+ * kinds are eOp<T1,eop_type>; N_PLUS..N_DIV are eGlue<T1,T2,eglue_type>
+ * (N_SCHUR is Armadillo's element-wise product operator%).  N_SUBMAT is a
+ * submatrix view of a leaf (Sec. 2: "diagonal and submatrix views"). */
+typedef enum {
+  COOT_N_LEAF = 0,            /* leaf matrix `leaf`                          */
+  COOT_N_SUBMAT = 1,          /* view of node a (an N_LEAF): rows r0..r0+nr-1,
+                                 cols c0..c0+nc-1 (0-based)                  */
+  COOT_N_TRANS = 2,           /* trans(a)                                    */
+  COOT_N_SCAL_TIMES = 3,      /* k * a                                       */
+  COOT_N_SCAL_PLUS = 4,       /* a + k                                       */
+  COOT_N_SCAL_MINUS_PRE = 5,  /* k - a                                       */
+  COOT_N_SCAL_MINUS_POST = 6, /* a - k                                       */
+  COOT_N_SCAL_DIV_PRE = 7,    /* k / a                                       */
+  COOT_N_SCAL_DIV_POST = 8,   /* a / k                                       */
+  COOT_N_PLUS = 9,            /* a + b                                       */
+  COOT_N_MINUS = 10,          /* a - b                                       */
+  COOT_N_SCHUR = 11,          /* a % b  (element-wise product)               */
+  COOT_N_DIV = 12,            /* a / b  (element-wise)                       */
+  COOT_N_NEG = 13,            /* -a                                          */
+  COOT_N_EXP = 14,
+  COOT_N_LOG = 15,
+  COOT_N_ABS = 16,
+  COOT_N_SQUARE = 17,
+  COOT_N_SQRT = 18,
+  COOT_N_COUNT_ = 19
+} coot_opcode;
+
+/* One node of a postfix tree.  Operand indices a, b refer to earlier nodes
+ * (a, b < own index; unused operands are -1); the root is the last node.
+ * Nodes may be shared (a DAG).  The scalar k is converted to the compute
+ * type (FP32 for F32/BF16/F16 trees, FP64 for F64, int32 truncation for I32,
+ * as an Armadillo scalar of type eT is). */
+typedef struct {
+  int32_t op;              /* coot_opcode                      */
+  int32_t a, b;            /* operand node indices or -1       */
+  int32_t leaf;            /* N_LEAF: index into `leaves`      */
+  double k;                /* scalar of the N_SCAL_* kinds     */
+  int64_t r0, c0, nr, nc;  /* N_SUBMAT view                    */
+} coot_node;
+
+typedef struct {
+  int32_t n_nodes;  /* 1 .. COOT_MAX_NODES */
+  int32_t reserved;
+  const coot_node* nodes;
+} coot_tree;
+
+#define COOT_MAX_NODES 64
+#define COOT_MAX_LEAVES 8
+#define COOT_MAX_SCALARS 16
+
+/* The reduction fused onto the tree (Sec. 2: accu/sum, "statistics such as
+ * mean and variance"; Sec. 5 task 1: summation of all elements). */
+typedef enum {
+  COOT_R_NONE = 0,
+  COOT_R_ACCU = 1,     /* sum of all elements -> scalar                           */
+  COOT_R_SUM = 2,      /* dim -1: all; 0: per column -> 1 x n_cols; 1: per row    */
+  COOT_R_MEAN = 3,     /* as R_SUM divided by the count                           */
+  COOT_R_DOT = 4,      /* root must be N_SCHUR a%b: sum of a*b with the products
+                          kept exactly (integer: exact int64 products)            */
+  COOT_R_NORM2 = 5,    /* vector 2-norm (tree must be a row or column vector)     */
+  COOT_R_NORM_FRO = 6, /* Frobenius norm of a matrix                              */
+  COOT_R_VAR = 7       /* two-pass variance over all elements; norm_type 0 -> N-1,
+                          1 -> N; one element gives 0                             */
+} coot_red_kind;
+
+typedef struct {
+  int32_t kind;      /* coot_red_kind                           */
+  int32_t dim;       /* -1 all elements, 0 per column, 1 per row */
+  int32_t norm_type; /* R_VAR only                              */
+  int32_t reserved;
+} coot_reduce;
+
+typedef struct coot_ctx coot_ctx;
+typedef struct coot_batch coot_batch;
+typedef struct coot_graph coot_graph;
+
+/* ---- context -------------------------------------------------------------
+ * coot_ctx_create: bind a context to CUDA device `device` (Sec. 2, coot_init
+ * picks the device).  The context owns the per-tree kernel cache (in memory
+ * and on disk under $COOT_CACHE_DIR, default ~/.cache/cootgb), the tuning
+ * cache and a device workspace that grows on demand.  Flags: */
+#define COOT_CTX_TUNE 1u          /* autotune launch configs on first use    */
+#define COOT_CTX_NO_DISK_CACHE 2u /* keep compiled kernels in memory only    */
+#define COOT_CTX_LOG 4u           /* print JIT / cache / tuning decisions    */
+COOT_API coot_status coot_ctx_create(int device, unsigned flags, coot_ctx** out);
+COOT_API coot_status coot_ctx_destroy(coot_ctx* ctx);
+
+/* ---- fused evaluation ----------------------------------------------------
+ * Evaluates `tree` over `leaves` in one kernel launch (two for R_VAR):
+ *   out     (nullable) receives the element-wise result Y, in the leaves'
+ *           dtype; it may alias a leaf only when every read of that leaf is
+ *           a full, untransposed read with out's exact layout (B += 3*A form);
+ *           any other overlap is COOT_ERR_ALIAS.
+ *   red     the reduction applied to Y (COOT_R_NONE for none);
+ *   red_out (device) scalar or vector of the accumulation type; required
+ *           when red.kind != R_NONE.
+ * All leaves share one dtype.  The first call for a new tree signature
+ * compiles its kernel (NVRTC, sm_103a) and must not happen during stream
+ * capture; coot_warmup does that ahead of time. */
+COOT_API coot_status coot_eval(coot_ctx* ctx, const coot_tree* tree, const coot_mat* leaves, int32_t n_leaves,
+                      const coot_mat* out, coot_reduce red, void* red_out, coot_stream stream);
+
+/* Same result computed eagerly, one kernel launch per node, each node
+ * materialised in a device temporary of the compute type (the paper's
+ * "sequence of calls from a set of predefined GPU kernels", Sec. 4).  This is
+ * the unfused baseline; element-wise results are bitwise equal to coot_eval. */
+COOT_API coot_status coot_eval_unfused(coot_ctx* ctx, const coot_tree* tree, const coot_mat* leaves,
+                              int32_t n_leaves, const coot_mat* out, coot_reduce red, void* red_out,
+                              coot_stream stream);
+
+/* JIT-compile (and, with COOT_CTX_TUNE, autotune) the kernel for this call
+ * without writing to out or red_out. */
+COOT_API coot_status coot_warmup(coot_ctx* ctx, const coot_tree* tree, const coot_mat* leaves, int32_t n_leaves,
+                        const coot_mat* out, coot_reduce red);
+
+/* ---- adjoint ---------------------------------------------------------------
+ * For a scalar loss L = red(tree) with red.kind R_ACCU, R_SUM (dim -1) or
+ * R_MEAN (dim -1), writes grads[i] = upstream * dL/dleaves[i] for every i
+ * whose grads[i].data is non-NULL (same shape/dtype as the leaf; F32/F64).
+ * The forward values are recomputed per element inside the kernel; nothing
+ * from a forward pass is stored.  Every leaf must be read through one full,
+ * untransposed view (else COOT_ERR_UNSUPPORTED).  upstream is a device
+ * scalar of the accumulation type. */
+COOT_API coot_status coot_eval_adjoint(coot_ctx* ctx, const coot_tree* tree, const coot_mat* leaves,
+                              int32_t n_leaves, coot_reduce red, const void* upstream,
+                              const coot_mat* grads, coot_stream stream);
+
+/* ---- batched evaluation ----------------------------------------------------
+ * Many independent problems of the same tree, each with its own leaf shapes
+ * (n_problems * n_leaves coot_mat in `problems`, problem-major, HOST array),
+ * evaluated by one persistent kernel that pulls tiles from a work queue.
+ * outs (nullable, n_problems entries) receives each problem's Y; red may be
+ * R_NONE or R_ACCU/R_SUM(dim -1)/R_MEAN(dim -1) with one result per problem.
+ * coot_batch_create validates, uploads the problem table and compiles; it
+ * synchronises the device.  coot_batch_run launches once on `stream`;
+ * red_out holds n_problems results.  The plan keeps the device pointers it
+ * was given; they must stay valid while the plan is used. */
+COOT_API coot_status coot_batch_create(coot_ctx* ctx, const coot_tree* tree, int64_t n_problems, int32_t n_leaves,
+                              const coot_mat* problems, const coot_mat* outs, coot_reduce red,
+                              coot_batch** out);
+COOT_API coot_status coot_batch_run(coot_batch* batch, void* red_out, coot_stream stream);
+COOT_API coot_status coot_batch_destroy(coot_batch* batch);
+/* create + run + destroy in one call (the plan's device table is released in
+ * stream order). */
+COOT_API coot_status coot_eval_batched(coot_ctx* ctx, const coot_tree* tree, int64_t n_problems, int32_t n_leaves,
+                              const coot_mat* problems, const coot_mat* outs, coot_reduce red,
+                              void* red_out, coot_stream stream);
+
+/* ---- CUDA graphs ------------------------------------------------------------
+ * coot_graph_begin starts capturing `stream`; the coot_eval calls that follow
+ * on it are recorded (their kernels must already be compiled: coot_warmup);
+ * coot_graph_end ends the capture and instantiates the graph;
+ * coot_graph_launch replays it on a stream. */
+COOT_API coot_status coot_graph_begin(coot_ctx* ctx, coot_stream stream);
+COOT_API coot_status coot_graph_end(coot_ctx* ctx, coot_stream stream, coot_graph** out);
+COOT_API coot_status coot_graph_launch(coot_graph* graph, coot_stream stream);
+COOT_API coot_status coot_graph_destroy(coot_graph* graph);
+
+/* ---- host-side introspection (no GPU needed) ---------------------------------
+ * coot_signature: validate the call and write its canonical signature (the
+ * kernel-cache key: dtype, op structure, leaf layout classes, reduction) to
+ * buf.  coot_codegen: write the generated CUDA source of the tree's kernel.
+ * coot_compile: NVRTC-compile that source for sm_103a (no device needed) and
+ * report the cubin size. */
+COOT_API coot_status coot_signature(const coot_tree* tree, const coot_mat* leaves, int32_t n_leaves,
+                           const coot_mat* out, coot_reduce red, char* buf, size_t len);
+COOT_API coot_status coot_codegen(const coot_tree* tree, const coot_mat* leaves, int32_t n_leaves,
+                         const coot_mat* out, coot_reduce red, char* buf, size_t len);
+COOT_API coot_status coot_compile(const coot_tree* tree, const coot_mat* leaves, int32_t n_leaves,
+                         const coot_mat* out, coot_reduce red, size_t* cubin_bytes);
+
+/* ---- errors and diagnostics --------------------------------------------------
+ * coot_check_device_flag: wait for `stream`, read and clear the context's
+ * device error flags (bit 0: an INT32 division by zero).  Returns
+ * COOT_ERR_DEVICE_FLAG when any flag was set. */
+#define COOT_FLAG_INT_DIV_ZERO 1u
+COOT_API coot_status coot_check_device_flag(coot_ctx* ctx, coot_stream stream, uint32_t* flags);
+
+/* Description of the last launch made by coot_eval on this context (kernel
+ * family and launch shape, for profiling and the roofline). */
+typedef struct {
+  char kernel[64];
+  int32_t grid, block;
+  int32_t vec, unroll;
+  int32_t n_launches;
+  int64_t algorithmic_bytes; /* distinct operand bytes read + bytes written */
+} coot_launch_info;
+COOT_API coot_status coot_last_launch(coot_ctx* ctx, coot_launch_info* info);
+
+COOT_API const char* coot_last_error(void);            /* thread-local, never NULL */
+COOT_API const char* coot_status_string(coot_status s); /* static string            */
+COOT_API void coot_version(int32_t* major, int32_t* minor);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* COOT_H */

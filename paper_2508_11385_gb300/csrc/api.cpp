@@ -1,0 +1,1107 @@
+// api.cpp -- the C ABI of libcootgb (see include/coot.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "coot_internal.h"
+
+coot_status coot_get_module(coot_ctx* ctx, const cg::Program& pg, cg::Module** out);
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+coot_status set_error(coot_status s, const char* fmt, ...) {
+  char buf[2048];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+coot_status cuda_error(cudaError_t e, const char* what) {
+  cudaGetLastError();
+  if (e == cudaErrorMemoryAllocation) return set_error(COOT_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+  return set_error(COOT_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool log_enabled(const coot_ctx* ctx) { return ctx && (ctx->flags & COOT_CTX_LOG); }
+
+extern "C" const char* coot_last_error(void) { return g_err.c_str(); }
+
+extern "C" const char* coot_status_string(coot_status s) {
+  switch (s) {
+    case COOT_OK: return "COOT_OK";
+    case COOT_ERR_INVALID: return "COOT_ERR_INVALID";
+    case COOT_ERR_SHAPE: return "COOT_ERR_SHAPE";
+    case COOT_ERR_DTYPE: return "COOT_ERR_DTYPE";
+    case COOT_ERR_ALIAS: return "COOT_ERR_ALIAS";
+    case COOT_ERR_JIT: return "COOT_ERR_JIT";
+    case COOT_ERR_OOM: return "COOT_ERR_OOM";
+    case COOT_ERR_CUDA: return "COOT_ERR_CUDA";
+    case COOT_ERR_DEVICE_FLAG: return "COOT_ERR_DEVICE_FLAG";
+    case COOT_ERR_TIMEOUT: return "COOT_ERR_TIMEOUT";
+    case COOT_ERR_UNSUPPORTED: return "COOT_ERR_UNSUPPORTED";
+  }
+  return "COOT_ERR_?";
+}
+
+extern "C" void coot_version(int32_t* major, int32_t* minor) {
+  if (major) *major = COOT_VERSION_MAJOR;
+  if (minor) *minor = COOT_VERSION_MINOR;
+}
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  bool changed = false;
+  explicit DeviceGuard(int d) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != d) {
+      changed = (cudaSetDevice(d) == cudaSuccess);
+    }
+    cudaGetLastError();
+  }
+  ~DeviceGuard() {
+    if (changed) cudaSetDevice(prev);
+  }
+};
+
+int64_t mat_ld(const coot_mat& m) { return (m.n_cols > 1) ? m.ld : (m.ld > 0 ? m.ld : m.n_rows); }
+
+int rsize(int ct) { return ct == cg::CT_F32 ? 4 : 8; }
+
+bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return cs != cudaStreamCaptureStatusNone;
+}
+
+const size_t kHeader = 1024;  // err flag at 0, mu at 256
+
+// grow the workspace: tickets (zeroed) and partials
+coot_status ws_ensure(coot_ctx* ctx, size_t tickets, size_t partial_bytes, cudaStream_t stream) {
+  if (ctx->ws && tickets <= ctx->n_tickets && partial_bytes <= ctx->partial_bytes) return COOT_OK;
+  if (capturing(stream))
+    return set_error(COOT_ERR_INVALID,
+                     "the workspace must grow (%zu tickets, %zu partial bytes) during stream capture; run the "
+                     "call once (or coot_warmup) before capturing",
+                     tickets, partial_bytes);
+  size_t nt = std::max(tickets, std::max(ctx->n_tickets, (size_t)4096));
+  size_t pb = std::max(partial_bytes, std::max(ctx->partial_bytes, (size_t)1 << 20));
+  if (ctx->ws) {
+    nt = std::max(nt, ctx->n_tickets + ctx->n_tickets / 2);
+    pb = std::max(pb, ctx->partial_bytes + ctx->partial_bytes / 2);
+  }
+  nt = (nt + 63) & ~(size_t)63;
+  pb = (pb + 255) & ~(size_t)255;
+  unsigned old_flag = 0;
+  cudaError_t e;
+  if (ctx->ws) {
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_error(e, "cudaDeviceSynchronize");
+    cudaMemcpy(&old_flag, ctx->err_flag, sizeof old_flag, cudaMemcpyDeviceToHost);
+    cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+  }
+  size_t tbytes = nt * sizeof(unsigned);
+  size_t total = kHeader + tbytes + pb;
+  if ((e = cudaMalloc(&ctx->ws, total)) != cudaSuccess) {
+    ctx->ws = nullptr;
+    ctx->n_tickets = ctx->partial_bytes = 0;
+    return cuda_error(e, "workspace cudaMalloc");
+  }
+  if ((e = cudaMemset(ctx->ws, 0, kHeader + tbytes)) != cudaSuccess) return cuda_error(e, "workspace cudaMemset");
+  char* b = (char*)ctx->ws;
+  ctx->err_flag = (unsigned*)b;
+  ctx->mean_ptr = (double*)(b + 256);
+  ctx->tickets = (unsigned*)(b + kHeader);
+  ctx->partials = (void*)(b + kHeader + tbytes);
+  ctx->n_tickets = nt;
+  ctx->partial_bytes = pb;
+  if (old_flag) cudaMemcpy(ctx->err_flag, &old_flag, sizeof old_flag, cudaMemcpyHostToDevice);
+  return COOT_OK;
+}
+
+uint64_t scalar_bits(double k, int ct) {
+  uint64_t b = 0;
+  if (ct == cg::CT_F32) {
+    float f = (float)k;
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    b = u;
+  } else if (ct == cg::CT_F64) {
+    memcpy(&b, &k, 8);
+  } else {
+    int32_t i = (int32_t)k;  // truncation toward zero (validated range)
+    b = (uint32_t)i;
+  }
+  return b;
+}
+
+int occupancy(cg::Module* m, const std::string& name, int block) {
+  int n = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, (const void*)m->kernels[name], block, 0);
+  if (e != cudaSuccess || n <= 0) {
+    cudaGetLastError();
+    const cudaFuncAttributes& fa = m->attrs[name];
+    int regs = std::max(fa.numRegs, 16);
+    int per_warp = ((regs * 32 + 255) / 256) * 256;
+    int by_regs = 65536 / std::max(per_warp * (block / 32), 1);
+    int by_thr = 2048 / block;
+    int by_smem = fa.sharedSizeBytes ? (int)((227 * 1024) / (fa.sharedSizeBytes + 1024)) : 32;
+    n = std::max(1, std::min(std::min(by_regs, by_thr), std::min(by_smem, 32)));
+  }
+  return n;
+}
+
+// what one launch of a fused program needs
+struct Launch {
+  std::string kname, kname2;  // kname2: second pass of var
+  int grid = 1, block = 256, vec = 1, unroll = 1;
+  size_t tickets = 1, partial_bytes = 0;
+  cg::Params p{};
+};
+
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// fill the launch shape of a fused program for a given kernel variant/config
+void shape_launch(coot_ctx* ctx, const cg::Analysis& an, const cg::Choice& ch, cg::Module* m,
+                  const cg::KernelSpec& k, int block, int bps, Launch* L) {
+  const int64_t R = ch.it_rows, C = ch.it_cols;
+  L->block = block;
+  L->vec = k.vec;
+  L->unroll = k.unroll;
+  const int64_t resident = (int64_t)ctx->sms * std::max(bps, 1);
+  cg::Params& p = L->p;
+  p.n_rows = R;
+  p.n_cols = C;
+  if (ch.fam == cg::F_STR || ch.fam == cg::F_ADJ) {
+    const int64_t chunk = (int64_t)block * k.vec * k.unroll;
+    p.units_per_col = std::max<int64_t>(1, ceil_div(R, chunk));
+    const int64_t units = p.units_per_col * C;
+    L->grid = (int)std::max<int64_t>(1, std::min(units, resident));
+    L->partial_bytes = (size_t)L->grid * 8;
+    L->tickets = 1;
+  } else if (ch.fam == cg::F_COL) {
+    const int64_t wpb = block / 32;
+    L->grid = (int)std::max<int64_t>(1, std::min(ceil_div(C, wpb), resident));
+    L->partial_bytes = 0;
+    L->tickets = 1;
+  } else if (ch.fam == cg::F_ROW) {
+    const int64_t nrb = std::max<int64_t>(1, ceil_div(R, (int64_t)block * k.vec));
+    int64_t nsp = std::max<int64_t>(1, std::min<int64_t>(C, resident / nrb));
+    const int64_t cps = std::max<int64_t>(1, ceil_div(std::max<int64_t>(C, 1), nsp));
+    nsp = std::max<int64_t>(1, ceil_div(std::max<int64_t>(C, 1), cps));
+    p.n_row_blocks = nrb;
+    p.n_splits = nsp;
+    p.units_per_col = cps;
+    L->grid = (int)(nrb * nsp);
+    L->partial_bytes = (nsp > 1) ? (size_t)(nsp * R * 8) : 0;
+    L->tickets = (size_t)nrb;
+  } else if (ch.fam == cg::F_TILE) {
+    const int64_t ntr = ceil_div(R, 32), ntc = ceil_div(C, 32);
+    const int64_t tiles = ntr * ntc;
+    L->grid = (int)std::max<int64_t>(1, std::min(tiles, resident));
+    if (an.red.dim == 0) {
+      L->partial_bytes = (size_t)(ntr * C * 8);
+      L->tickets = (size_t)std::max<int64_t>(ntc, 1);
+    } else if (an.red.dim == 1) {
+      L->partial_bytes = (size_t)(ntc * R * 8);
+      L->tickets = (size_t)std::max<int64_t>(ntr, 1);
+    } else {
+      L->partial_bytes = (size_t)L->grid * 8;
+      L->tickets = 1;
+    }
+  }
+  (void)m;
+}
+
+int64_t algorithmic_bytes(const cg::Analysis& an, const coot_mat* out) {
+  int64_t b = 0;
+  for (const cg::Slot& s : an.slots) b += s.vr * s.vc * an.esz;
+  if (an.red.kind == COOT_R_VAR) b *= 2;  // the tree is read by both passes
+  if (out) b += an.nr * an.nc * an.esz;
+  int64_t nout = 0;
+  if (an.red.kind != COOT_R_NONE) nout = (an.red.dim == 0) ? an.nc : (an.red.dim == 1 ? an.nr : 1);
+  return b + nout * (an.ct == cg::CT_F32 ? 4 : 8);
+}
+
+// pick the default kernel variant of a program for this call: the vector
+// variant with unroll 2 when every column start is 16-byte aligned, else the
+// scalar variant (second passes of var are paired by name)
+int default_variant(const cg::Program& pg, const cg::Choice& ch) {
+  int best = -1;
+  for (int i = 0; i < (int)pg.kernels.size(); ++i) {
+    const cg::KernelSpec& k = pg.kernels[i];
+    if (k.name.find("_p2") != std::string::npos) continue;
+    if (!ch.vec_ok && k.vec > 1) continue;
+    if (best < 0) best = i;
+    if (ch.vec_ok && k.vec > 1 && k.unroll == 2) return i;
+    if (!ch.vec_ok && k.vec == 1) return i;
+  }
+  return best < 0 ? 0 : best;
+}
+
+std::string pair_name(const std::string& p1) {
+  std::string n = p1;
+  size_t at = n.find("_p1");
+  if (at != std::string::npos) n.replace(at, 3, "_p2");
+  return n;
+}
+
+coot_status launch_kernel(cg::Module* m, const std::string& name, int grid, int block, void* params,
+                          cudaStream_t stream) {
+  void* args[] = {params};
+  cudaError_t e = cudaLaunchKernel((const void*)m->kernels[name], dim3(grid), dim3(block), args, 0, stream);
+  if (e != cudaSuccess) return cuda_error(e, name.c_str());
+  return COOT_OK;
+}
+
+coot_status tune(coot_ctx* ctx, const cg::Analysis& an, const cg::Choice& ch, const cg::Program& pg, cg::Module* m,
+                 Launch base, cudaStream_t stream, cg::LaunchCfg* best);
+
+std::string tune_key(const cg::Program& pg, const cg::Choice& ch) {
+  int64_t n = ch.it_rows * std::max<int64_t>(ch.it_cols, 1);
+  int bucket = 0;
+  while ((int64_t(1) << bucket) < n && bucket < 62) ++bucket;
+  return pg.signature + "|b" + std::to_string(bucket) + "|v" + std::to_string(ch.vec_ok) + "|r" +
+         std::to_string(ch.it_cols > 1 ? 1 : 0);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// run one analysed fused evaluation (warm: compile + tune without launching)
+// ---------------------------------------------------------------------------
+static coot_status run_fused(coot_ctx* ctx, const cg::Analysis& an, const coot_mat* leaves, const coot_mat* out,
+                             void* red_out, cudaStream_t stream, bool warm_only) {
+  const bool var = an.red.kind == COOT_R_VAR;
+  cg::Choice ch = cg::choose(an, leaves, out);
+  const int64_t count = an.nr * an.nc;
+  if (!warm_only && count == 0) {
+    // nothing to read: reductions of no elements
+    if (an.red.kind == COOT_R_NONE) return COOT_OK;
+    int64_t nout = (an.red.dim == 0) ? an.nc : (an.red.dim == 1 ? an.nr : 1);
+    bool nan = (an.red.kind == COOT_R_MEAN || an.red.kind == COOT_R_VAR);
+    if (nout > 0) {
+      cudaError_t e = cudaMemsetAsync(red_out, nan ? 0xff : 0, (size_t)nout * rsize(an.ct), stream);
+      if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync");
+    }
+    return COOT_OK;
+  }
+  cg::Program pg = cg::make_program(an, ch.fam, var);
+  if (!ctx->mods.count(pg.signature) && capturing(stream))
+    return set_error(COOT_ERR_INVALID, "this tree's kernel is not compiled yet; call coot_warmup before capturing");
+  cg::Module* m = nullptr;
+  coot_status s = coot_get_module(ctx, pg, &m);
+  if (s) return s;
+
+  Launch L;
+  cg::Params& p = L.p;
+  for (size_t i = 0; i < an.slots.size(); ++i) {
+    const cg::Slot& sl = an.slots[i];
+    const coot_mat& Lf = leaves[sl.leaf];
+    const int64_t ld = mat_ld(Lf);
+    p.src[i] = (const char*)Lf.data + (sl.r0 + sl.c0 * ld) * an.esz;
+    p.ld[i] = ld;
+  }
+  for (size_t i = 0; i < an.scalars.size(); ++i) p.k[i] = scalar_bits(an.scalars[i], an.ct);
+  p.out = out ? out->data : nullptr;
+  p.out_ld = out ? mat_ld(*out) : 0;
+  p.count = count;
+  p.div = 1.0;
+  if (an.red.kind == COOT_R_MEAN)
+    p.div = (an.red.dim == 0) ? (double)an.nr : (an.red.dim == 1 ? (double)an.nc : (double)count);
+  p.den = (an.red.norm_type == 1) ? (double)count : (double)(count - 1);
+  p.red_out = red_out;
+
+  // launch configuration: tuned, else the default variant at full occupancy
+  std::string key = tune_key(pg, ch);
+  cg::LaunchCfg cfg;
+  auto tu = ctx->tuned.find(key);
+  if (tu != ctx->tuned.end()) {
+    cfg = tu->second;
+  } else {
+    cfg.kidx = default_variant(pg, ch);
+    cfg.block = pg.kernels[cfg.kidx].block;
+    if (ch.fam == cg::F_ROW) cfg.block = 256;
+    cfg.blocks_per_sm = occupancy(m, pg.kernels[cfg.kidx].name, cfg.block);
+    if ((ctx->flags & COOT_CTX_TUNE) && !capturing(stream) && count > 0) {
+      Launch base = L;
+      s = tune(ctx, an, ch, pg, m, base, stream, &cfg);
+      if (s) return s;
+      ctx->tuned[key] = cfg;
+    }
+  }
+  const cg::KernelSpec& ks = pg.kernels[cfg.kidx];
+  shape_launch(ctx, an, ch, m, ks, cfg.block, cfg.blocks_per_sm, &L);
+  L.kname = ks.name;
+  if (var) L.kname2 = pair_name(ks.name);
+  s = ws_ensure(ctx, L.tickets, L.partial_bytes, stream);
+  if (s) return s;
+  p.tickets = ctx->tickets;
+  p.err_flag = ctx->err_flag;
+  p.mu = ctx->mean_ptr;
+  p.partials = ctx->partials;
+  if (warm_only) return COOT_OK;
+
+  s = launch_kernel(m, L.kname, L.grid, L.block, &p, stream);
+  if (s) return s;
+  if (var) {
+    s = launch_kernel(m, L.kname2, L.grid, L.block, &p, stream);
+    if (s) return s;
+  }
+  coot_launch_info& li = ctx->last;
+  memset(&li, 0, sizeof li);
+  snprintf(li.kernel, sizeof li.kernel, "%s", L.kname.c_str());
+  li.grid = L.grid;
+  li.block = L.block;
+  li.vec = L.vec;
+  li.unroll = L.unroll;
+  li.n_launches = var ? 2 : 1;
+  li.algorithmic_bytes = algorithmic_bytes(an, out);
+  return COOT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: kernel variant x block size x resident blocks per SM, timed with
+// CUDA events on scratch outputs (user buffers are never written)
+// ---------------------------------------------------------------------------
+namespace {
+coot_status tune(coot_ctx* ctx, const cg::Analysis& an, const cg::Choice& ch, const cg::Program& pg, cg::Module* m,
+                 Launch base, cudaStream_t stream, cg::LaunchCfg* best) {
+  const bool var = an.red.kind == COOT_R_VAR;
+  void* scratch_out = nullptr;
+  void* scratch_red = nullptr;
+  cudaError_t e;
+  // scratch output with the alignment the vector variants need: contiguous
+  // when the call walks one long column, else columns padded to 16 bytes
+  const int64_t per16 = 16 / an.esz;
+  const int64_t sld = ch.collapsed ? std::max<int64_t>(an.nr, 1) : ((an.nr + per16 - 1) / per16) * per16;
+  const size_t out_bytes = base.p.out ? (size_t)(std::max<int64_t>(sld, 1) * std::max<int64_t>(an.nc, 1) * an.esz) : 0;
+  if (out_bytes && (e = cudaMalloc(&scratch_out, out_bytes)) != cudaSuccess) return cuda_error(e, "tune cudaMalloc");
+  const int64_t nred = std::max<int64_t>(an.nr, an.nc) + 1;
+  if ((e = cudaMalloc(&scratch_red, (size_t)nred * 8)) != cudaSuccess) {
+    cudaFree(scratch_out);
+    return cuda_error(e, "tune cudaMalloc");
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best_ms = 1e30f;
+  coot_status st = COOT_OK;
+  for (int ki = 0; ki < (int)pg.kernels.size() && st == COOT_OK; ++ki) {
+    const cg::KernelSpec& k = pg.kernels[ki];
+    if (k.name.find("_p2") != std::string::npos) continue;
+    if (!ch.vec_ok && k.vec > 1) continue;
+    std::vector<int> blocks;
+    if (ch.fam == cg::F_TILE) blocks = {256};
+    else if (ch.fam == cg::F_ROW) blocks = {128, 256, 512};
+    else blocks = {256, 512};
+    for (int block : blocks) {
+      if (block > k.block) continue;
+      int occ = occupancy(m, k.name, block);
+      std::vector<int> bpss = {occ};
+      for (int b : {1, 2, 4}) if (b < occ) bpss.push_back(b);
+      for (int bps : bpss) {
+        Launch L = base;
+        L.p.out = scratch_out;
+        if (scratch_out) L.p.out_ld = sld;
+        L.p.red_out = scratch_red;
+        shape_launch(ctx, an, ch, m, k, block, bps, &L);
+        st = ws_ensure(ctx, L.tickets, L.partial_bytes, stream);
+        if (st) break;
+        L.p.tickets = ctx->tickets;
+        L.p.err_flag = ctx->err_flag;
+        L.p.mu = ctx->mean_ptr;
+        L.p.partials = ctx->partials;
+        std::string k2 = pair_name(k.name);
+        float times[3];
+        for (int rep = 0; rep < 4 && st == COOT_OK; ++rep) {
+          cudaEventRecord(e0, stream);
+          st = launch_kernel(m, k.name, L.grid, L.block, &L.p, stream);
+          if (!st && var) st = launch_kernel(m, k2, L.grid, L.block, &L.p, stream);
+          cudaEventRecord(e1, stream);
+          cudaEventSynchronize(e1);
+          if (rep > 0) cudaEventElapsedTime(&times[rep - 1], e0, e1);
+        }
+        if (st) break;
+        std::sort(times, times + 3);
+        if (times[1] < best_ms) {
+          best_ms = times[1];
+          best->kidx = ki;
+          best->block = block;
+          best->blocks_per_sm = bps;
+        }
+      }
+      if (st) break;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(stream);
+  cudaFree(scratch_out);
+  cudaFree(scratch_red);
+  if (log_enabled(ctx) && st == COOT_OK)
+    fprintf(stderr, "[cootgb] tuned %s: %s block %d x %d/SM (%.3f ms)\n", pg.signature.substr(0, 60).c_str(),
+            pg.kernels[best->kidx].name.c_str(), best->block, best->blocks_per_sm, best_ms);
+  return st;
+}
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+extern "C" coot_status coot_ctx_create(int device, unsigned flags, coot_ctx** out) {
+  if (!out) return set_error(COOT_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= n) return set_error(COOT_ERR_INVALID, "device %d not in 0..%d", device, n - 1);
+  cudaDeviceProp prop;
+  if ((e = cudaGetDeviceProperties(&prop, device)) != cudaSuccess) return cuda_error(e, "cudaGetDeviceProperties");
+  if (!(prop.major == 10 && prop.minor == 3))
+    return set_error(COOT_ERR_UNSUPPORTED, "libcootgb generates sm_103a kernels; device %d is sm_%d%d", device,
+                     prop.major, prop.minor);
+  coot_ctx* c = new coot_ctx();
+  c->device = device;
+  c->flags = flags;
+  const char* lg = getenv("COOT_LOG");
+  if (lg && *lg && strcmp(lg, "0")) c->flags |= COOT_CTX_LOG;
+  const char* tu = getenv("COOT_TUNE");
+  if (tu && (!strcmp(tu, "on") || !strcmp(tu, "1"))) c->flags |= COOT_CTX_TUNE;
+  if (tu && (!strcmp(tu, "off") || !strcmp(tu, "0"))) c->flags &= ~COOT_CTX_TUNE;
+  c->sms = prop.multiProcessorCount;
+  c->l2_bytes = prop.l2CacheSize;
+  const char* cd = getenv("COOT_CACHE_DIR");
+  if (cd && *cd)
+    c->cache_dir = cd;
+  else if (getenv("HOME"))
+    c->cache_dir = std::string(getenv("HOME")) + "/.cache/cootgb";
+  {
+    DeviceGuard g(device);
+    coot_status s = ws_ensure(c, 4096, 1 << 20, nullptr);
+    if (s) {
+      delete c;
+      return s;
+    }
+  }
+  *out = c;
+  return COOT_OK;
+}
+
+extern "C" coot_status coot_ctx_destroy(coot_ctx* ctx) {
+  if (!ctx) return COOT_OK;
+  {
+    DeviceGuard g(ctx->device);
+    cudaDeviceSynchronize();
+    for (auto& kv : ctx->mods)
+      if (kv.second->lib) cudaLibraryUnload(kv.second->lib);
+    if (ctx->ws) cudaFree(ctx->ws);
+    cudaGetLastError();
+  }
+  delete ctx;
+  return COOT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// fused evaluation
+// ---------------------------------------------------------------------------
+extern "C" coot_status coot_eval(coot_ctx* ctx, const coot_tree* tree, const coot_mat* leaves, int32_t n_leaves,
+                                 const coot_mat* out, coot_reduce red, void* red_out, coot_stream stream) {
+  if (!ctx) return set_error(COOT_ERR_INVALID, "ctx is NULL");
+  cg::Analysis an;
+  coot_status s = cg::analyse(tree, leaves, n_leaves, out, red, &an);
+  if (s) return s;
+  if (red.kind != COOT_R_NONE && !red_out) return set_error(COOT_ERR_INVALID, "red_out is NULL");
+  if (red.kind == COOT_R_NONE && !out) return set_error(COOT_ERR_INVALID, "neither out nor a reduction requested");
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  DeviceGuard g(ctx->device);
+  return run_fused(ctx, an, leaves, out, red_out, (cudaStream_t)stream, false);
+}
+
+extern "C" coot_status coot_warmup(coot_ctx* ctx, const coot_tree* tree, const coot_mat* leaves, int32_t n_leaves,
+                                   const coot_mat* out, coot_reduce red) {
+  if (!ctx) return set_error(COOT_ERR_INVALID, "ctx is NULL");
+  cg::Analysis an;
+  coot_status s = cg::analyse(tree, leaves, n_leaves, out, red, &an);
+  if (s) return s;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  DeviceGuard g(ctx->device);
+  return run_fused(ctx, an, leaves, out, nullptr, nullptr, true);
+}
+
+// ---------------------------------------------------------------------------
+// unfused baseline: one launch per node, each node materialised
+// ---------------------------------------------------------------------------
+extern "C" coot_status coot_eval_unfused(coot_ctx* ctx, const coot_tree* tree, const coot_mat* leaves,
+                                         int32_t n_leaves, const coot_mat* out, coot_reduce red, void* red_out,
+                                         coot_stream stream_) {
+  if (!ctx) return set_error(COOT_ERR_INVALID, "ctx is NULL");
+  cudaStream_t stream = (cudaStream_t)stream_;
+  cg::Analysis an;
+  coot_status s = cg::analyse(tree, leaves, n_leaves, out, red, &an);
+  if (s) return s;
+  if (an.dtype == COOT_BF16 || an.dtype == COOT_F16)
+    return set_error(COOT_ERR_UNSUPPORTED, "the unfused baseline keeps temporaries in the storage type; use F32/F64/I32");
+  if (red.kind != COOT_R_NONE && !red_out) return set_error(COOT_ERR_INVALID, "red_out is NULL");
+  if (red.kind == COOT_R_NONE && !out) return set_error(COOT_ERR_INVALID, "neither out nor a reduction requested");
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  DeviceGuard g(ctx->device);
+  const int nn = tree->n_nodes;
+  const int root = nn - 1;
+  // reachable nodes (the R_DOT root is folded into the final dot kernel)
+  const bool dot = (red.kind == COOT_R_DOT);
+  std::vector<char> need(nn, 0);
+  std::vector<int> stack = {root};
+  while (!stack.empty()) {
+    int n = stack.back();
+    stack.pop_back();
+    if (need[n]) continue;
+    need[n] = 1;
+    const coot_node& d = tree->nodes[n];
+    if (d.op != COOT_N_LEAF) {
+      if (d.a >= 0) stack.push_back(d.a);
+      if (d.b >= 0 && d.op >= COOT_N_PLUS && d.op <= COOT_N_DIV) stack.push_back(d.b);
+    }
+  }
+  // shape of every node (validated by analyse)
+  std::vector<coot_mat> val(nn);
+  std::vector<void*> temps;
+  auto release = [&]() {
+    for (void* t : temps) cudaFreeAsync(t, stream);
+  };
+  for (int n = 0; n < nn; ++n) {
+    if (!need[n]) continue;
+    const coot_node& d = tree->nodes[n];
+    if (d.op == COOT_N_LEAF) {
+      val[n] = leaves[d.leaf];
+      val[n].ld = mat_ld(leaves[d.leaf]);
+      continue;
+    }
+    if (d.op == COOT_N_SUBMAT) {  // a view: no kernel
+      coot_mat v = val[d.a];
+      v.data = (char*)v.data + (d.r0 + d.c0 * v.ld) * an.esz;
+      v.n_rows = d.nr;
+      v.n_cols = d.nc;
+      val[n] = v;
+      continue;
+    }
+    if (n == root && dot) continue;
+    // one kernel: node n over its (materialised or viewed) operands
+    coot_mat ops[2];
+    int nops = 0;
+    ops[nops++] = val[d.a];
+    bool bin = (d.op >= COOT_N_PLUS && d.op <= COOT_N_DIV);
+    if (bin) ops[nops++] = val[d.b];
+    coot_node mini[3];
+    memset(mini, 0, sizeof mini);
+    mini[0].op = COOT_N_LEAF;
+    mini[0].leaf = 0;
+    mini[0].a = mini[0].b = -1;
+    int nmini = 1;
+    if (bin) {
+      mini[1].op = COOT_N_LEAF;
+      mini[1].leaf = 1;
+      mini[1].a = mini[1].b = -1;
+      nmini = 2;
+    }
+    coot_node& opn = mini[nmini];
+    opn.op = d.op;
+    opn.a = 0;
+    opn.b = bin ? 1 : -1;
+    opn.k = d.k;
+    ++nmini;
+    coot_tree mt{nmini, 0, mini};
+    int64_t r = (d.op == COOT_N_TRANS) ? ops[0].n_cols : ops[0].n_rows;
+    int64_t c = (d.op == COOT_N_TRANS) ? ops[0].n_rows : ops[0].n_cols;
+    coot_mat dst{};
+    if (n == root && out && !dot) {
+      dst = *out;
+      dst.ld = mat_ld(*out);
+    } else {
+      void* t = nullptr;
+      size_t bytes = (size_t)std::max<int64_t>(r * c, 1) * an.esz;
+      cudaError_t e = cudaMallocAsync(&t, bytes, stream);
+      if (e != cudaSuccess) {
+        release();
+        return cuda_error(e, "cudaMallocAsync (unfused temporary)");
+      }
+      temps.push_back(t);
+      dst.data = t;
+      dst.dtype = an.dtype;
+      dst.n_rows = r;
+      dst.n_cols = c;
+      dst.ld = std::max<int64_t>(r, 1);
+    }
+    cg::Analysis man;
+    coot_reduce none{COOT_R_NONE, -1, 0, 0};
+    s = cg::analyse(&mt, ops, nops, &dst, none, &man);
+    if (!s) s = run_fused(ctx, man, ops, &dst, nullptr, stream, false);
+    if (s) {
+      release();
+      return s;
+    }
+    val[n] = dst;
+  }
+  // the reduction as its own kernel over the materialised root
+  if (red.kind != COOT_R_NONE) {
+    coot_node mini[3];
+    memset(mini, 0, sizeof mini);
+    coot_mat ops[2];
+    int nops;
+    coot_tree mt;
+    if (dot) {
+      const coot_node& d = tree->nodes[root];
+      ops[0] = val[d.a];
+      ops[1] = val[d.b];
+      nops = 2;
+      mini[0].op = COOT_N_LEAF;
+      mini[0].leaf = 0;
+      mini[0].a = mini[0].b = -1;
+      mini[1].op = COOT_N_LEAF;
+      mini[1].leaf = 1;
+      mini[1].a = mini[1].b = -1;
+      mini[2].op = COOT_N_SCHUR;
+      mini[2].a = 0;
+      mini[2].b = 1;
+      mt = coot_tree{3, 0, mini};
+      if (out) {  // the element-wise result still has to be written
+        s = coot_eval_unfused(ctx, tree, leaves, n_leaves, out, coot_reduce{COOT_R_NONE, -1, 0, 0}, nullptr, stream_);
+        if (s) {
+          release();
+          return s;
+        }
+      }
+    } else {
+      ops[0] = val[root];
+      nops = 1;
+      mini[0].op = COOT_N_LEAF;
+      mini[0].leaf = 0;
+      mini[0].a = mini[0].b = -1;
+      mt = coot_tree{1, 0, mini};
+    }
+    cg::Analysis man;
+    s = cg::analyse(&mt, ops, nops, nullptr, red, &man);
+    if (!s) s = run_fused(ctx, man, ops, nullptr, red_out, stream, false);
+    if (s) {
+      release();
+      return s;
+    }
+  } else if (tree->nodes[root].op == COOT_N_LEAF || tree->nodes[root].op == COOT_N_SUBMAT) {
+    // a bare leaf or view: one copy kernel
+    coot_node mini[1];
+    memset(mini, 0, sizeof mini);
+    mini[0].op = COOT_N_LEAF;
+    mini[0].leaf = 0;
+    mini[0].a = mini[0].b = -1;
+    coot_tree mt{1, 0, mini};
+    coot_mat op0 = val[root];
+    cg::Analysis man;
+    coot_reduce none{COOT_R_NONE, -1, 0, 0};
+    s = cg::analyse(&mt, &op0, 1, out, none, &man);
+    if (!s) s = run_fused(ctx, man, &op0, out, nullptr, stream, false);
+    if (s) {
+      release();
+      return s;
+    }
+  }
+  release();
+  return COOT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// adjoint
+// ---------------------------------------------------------------------------
+extern "C" coot_status coot_eval_adjoint(coot_ctx* ctx, const coot_tree* tree, const coot_mat* leaves,
+                                         int32_t n_leaves, coot_reduce red, const void* upstream,
+                                         const coot_mat* grads, coot_stream stream_) {
+  if (!ctx) return set_error(COOT_ERR_INVALID, "ctx is NULL");
+  cudaStream_t stream = (cudaStream_t)stream_;
+  if (!upstream || !grads) return set_error(COOT_ERR_INVALID, "upstream or grads is NULL");
+  const bool ok_red = red.kind == COOT_R_ACCU || red.kind == COOT_R_DOT ||
+                      ((red.kind == COOT_R_SUM || red.kind == COOT_R_MEAN) && red.dim == -1);
+  if (!ok_red)
+    return set_error(COOT_ERR_UNSUPPORTED, "the adjoint covers accu / sum / mean over all elements (and dot)");
+  cg::Analysis an;
+  coot_status s = cg::analyse(tree, leaves, n_leaves, nullptr, red, &an);
+  if (s) return s;
+  if (an.dtype != COOT_F32 && an.dtype != COOT_F64)
+    return set_error(COOT_ERR_UNSUPPORTED, "the adjoint is implemented for F32 and F64 leaves");
+  std::vector<int> uses(n_leaves, 0);
+  for (const cg::Slot& sl : an.slots) {
+    if (sl.trans || !sl.full)
+      return set_error(COOT_ERR_UNSUPPORTED, "the adjoint needs every leaf read whole and untransposed");
+    if (++uses[sl.leaf] > 1) return set_error(COOT_ERR_UNSUPPORTED, "leaf %d is read through two views", sl.leaf);
+  }
+  for (int i = 0; i < n_leaves; ++i) {
+    if (!grads[i].data) continue;
+    if (grads[i].dtype != an.dtype || grads[i].n_rows != leaves[i].n_rows || grads[i].n_cols != leaves[i].n_cols)
+      return set_error(COOT_ERR_SHAPE, "grads[%d] must match leaf %d in shape and dtype", i, i);
+  }
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  DeviceGuard g(ctx->device);
+  const int64_t count = an.nr * an.nc;
+  if (count == 0) return COOT_OK;
+  // iteration shape: one long column when every read and gradient is contiguous
+  cg::Choice ch;
+  ch.fam = cg::F_ADJ;
+  bool contig = true, vec = true;
+  for (size_t i = 0; i < an.slots.size(); ++i) {
+    const coot_mat& L = leaves[an.slots[i].leaf];
+    if (an.nc > 1 && mat_ld(L) != an.nr) contig = false;
+    if ((uintptr_t)L.data % 16) vec = false;
+    const coot_mat& G = grads[an.slots[i].leaf];
+    if (G.data) {
+      if (an.nc > 1 && mat_ld(G) != an.nr) contig = false;
+      if ((uintptr_t)G.data % 16) vec = false;
+    }
+  }
+  if (!contig) {
+    for (size_t i = 0; i < an.slots.size(); ++i) {
+      const coot_mat& L = leaves[an.slots[i].leaf];
+      const coot_mat& G = grads[an.slots[i].leaf];
+      if ((mat_ld(L) * an.esz) % 16) vec = false;
+      if (G.data && (mat_ld(G) * an.esz) % 16) vec = false;
+    }
+  }
+  ch.collapsed = contig;
+  ch.vec_ok = vec;
+  ch.it_rows = contig ? count : an.nr;
+  ch.it_cols = contig ? 1 : an.nc;
+  cg::Program pg = cg::make_program(an, cg::F_ADJ, false);
+  if (!ctx->mods.count(pg.signature) && capturing(stream))
+    return set_error(COOT_ERR_INVALID, "compile the adjoint before capturing");
+  cg::Module* m = nullptr;
+  if ((s = coot_get_module(ctx, pg, &m))) return s;
+  Launch L;
+  cg::Params& p = L.p;
+  for (size_t i = 0; i < an.slots.size(); ++i) {
+    const coot_mat& Lf = leaves[an.slots[i].leaf];
+    p.src[i] = Lf.data;
+    p.ld[i] = mat_ld(Lf);
+    const coot_mat& G = grads[an.slots[i].leaf];
+    p.grad[i] = G.data;
+    p.grad_ld[i] = G.data ? mat_ld(G) : 0;
+  }
+  for (size_t i = 0; i < an.scalars.size(); ++i) p.k[i] = scalar_bits(an.scalars[i], an.ct);
+  p.upstream = upstream;
+  p.grad_mult = (red.kind == COOT_R_MEAN) ? 1.0 / (double)count : 1.0;
+  int kidx = default_variant(pg, ch);
+  const cg::KernelSpec& ks = pg.kernels[kidx];
+  int bps = occupancy(m, ks.name, 512);
+  shape_launch(ctx, an, ch, m, ks, 512, bps, &L);
+  if ((s = ws_ensure(ctx, 1, 0, stream))) return s;
+  p.err_flag = ctx->err_flag;
+  p.tickets = ctx->tickets;
+  p.partials = ctx->partials;
+  p.mu = ctx->mean_ptr;
+  if ((s = launch_kernel(m, ks.name, L.grid, L.block, &p, stream))) return s;
+  coot_launch_info& li = ctx->last;
+  memset(&li, 0, sizeof li);
+  snprintf(li.kernel, sizeof li.kernel, "%s", ks.name.c_str());
+  li.grid = L.grid;
+  li.block = L.block;
+  li.vec = ks.vec;
+  li.unroll = ks.unroll;
+  li.n_launches = 1;
+  int64_t b = 0;
+  for (const cg::Slot& sl : an.slots) {
+    b += count * an.esz;
+    if (grads[sl.leaf].data) b += count * an.esz;
+  }
+  li.algorithmic_bytes = b;
+  return COOT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batched evaluation
+// ---------------------------------------------------------------------------
+extern "C" coot_status coot_batch_create(coot_ctx* ctx, const coot_tree* tree, int64_t n_problems, int32_t n_leaves,
+                                         const coot_mat* problems, const coot_mat* outs, coot_reduce red,
+                                         coot_batch** out) {
+  if (!ctx || !out || !problems) return set_error(COOT_ERR_INVALID, "ctx, problems or out is NULL");
+  *out = nullptr;
+  if (n_problems < 1) return set_error(COOT_ERR_INVALID, "n_problems must be >= 1");
+  const bool ok_red = red.kind == COOT_R_NONE || red.kind == COOT_R_ACCU ||
+                      ((red.kind == COOT_R_SUM || red.kind == COOT_R_MEAN) && red.dim == -1);
+  if (!ok_red) return set_error(COOT_ERR_UNSUPPORTED, "batched reductions: accu / sum / mean over all elements");
+  if (red.kind == COOT_R_NONE && !outs) return set_error(COOT_ERR_INVALID, "neither outs nor a reduction requested");
+  cg::Analysis an0;
+  coot_status s = cg::analyse(tree, problems, n_leaves, outs ? &outs[0] : nullptr, red, &an0);
+  if (s) return set_error(s, "problem 0: %s", coot_last_error());
+  std::vector<coot::BatchProblem> probs((size_t)n_problems);
+  std::vector<long long> begin((size_t)n_problems + 1);
+  long long tiles = 0;
+  int64_t bytes = 0;
+  for (int64_t q = 0; q < n_problems; ++q) {
+    cg::Analysis an;
+    const coot_mat* lv = &problems[q * n_leaves];
+    s = cg::analyse(tree, lv, n_leaves, outs ? &outs[q] : nullptr, red, &an);
+    if (s) return set_error(s, "problem %lld: %s", (long long)q, coot_last_error());
+    if (an.dtype != an0.dtype || an.slots.size() != an0.slots.size() || an.trmask != an0.trmask)
+      return set_error(COOT_ERR_INVALID, "problem %lld differs in dtype or leaf reads", (long long)q);
+    coot::BatchProblem& bp = probs[q];
+    memset(&bp, 0, sizeof bp);
+    for (size_t i = 0; i < an.slots.size(); ++i) {
+      const cg::Slot& sl = an.slots[i];
+      const coot_mat& L = lv[sl.leaf];
+      const int64_t ld = mat_ld(L);
+      bp.src[i] = (const char*)L.data + (sl.r0 + sl.c0 * ld) * an.esz;
+      bp.ld[i] = ld;
+      bytes += sl.vr * sl.vc * an.esz;
+    }
+    if (outs) {
+      bp.out = outs[q].data;
+      bp.out_ld = mat_ld(outs[q]);
+      bytes += an.nr * an.nc * an.esz;
+    }
+    bp.n_rows = an.nr;
+    bp.n_cols = an.nc;
+    int64_t ntr = std::max<int64_t>(1, ceil_div(an.nr, 32));
+    int64_t ntc = std::max<int64_t>(1, ceil_div(an.nc, 32));
+    bp.n_tile_rows = ntr;
+    bp.tile_begin = tiles;
+    begin[q] = tiles;
+    tiles += ntr * ntc;
+  }
+  begin[n_problems] = tiles;
+  if (red.kind != COOT_R_NONE) bytes += n_problems * rsize(an0.ct);
+
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  DeviceGuard g(ctx->device);
+  cg::Program pg = cg::make_program(an0, cg::F_BATCH, false);
+  cg::Module* m = nullptr;
+  if ((s = coot_get_module(ctx, pg, &m))) return s;
+  if ((s = ws_ensure(ctx, 1, 0, nullptr))) return s;
+
+  auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t o_probs = 0;
+  const size_t o_begin = align(o_probs + probs.size() * sizeof(coot::BatchProblem));
+  const size_t o_done = align(o_begin + begin.size() * sizeof(long long));
+  const size_t o_queue = align(o_done + (size_t)n_problems * sizeof(unsigned));
+  const size_t o_part = align(o_queue + 2 * sizeof(unsigned));
+  const size_t total = align(o_part + (size_t)tiles * 8);
+  coot_batch* b = new coot_batch();
+  cudaError_t e = cudaMalloc(&b->dev_mem, total);
+  if (e != cudaSuccess) {
+    delete b;
+    return cuda_error(e, "batch cudaMalloc");
+  }
+  char* base = (char*)b->dev_mem;
+  if ((e = cudaMemcpy(base + o_probs, probs.data(), probs.size() * sizeof(coot::BatchProblem),
+                      cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(base + o_begin, begin.data(), begin.size() * sizeof(long long), cudaMemcpyHostToDevice)) !=
+          cudaSuccess ||
+      (e = cudaMemset(base + o_done, 0, o_part - o_done)) != cudaSuccess) {
+    cudaFree(b->dev_mem);
+    delete b;
+    return cuda_error(e, "batch upload");
+  }
+  b->ctx = ctx;
+  b->mod = m;
+  b->kname = "coot_batch";
+  b->n_problems = n_problems;
+  b->has_red = red.kind != COOT_R_NONE;
+  b->block = 256;
+  b->grid = ctx->sms * occupancy(m, b->kname, b->block);
+  b->algorithmic_bytes = bytes;
+  coot::BatchParams& bp = b->bp;
+  memset(&bp, 0, sizeof bp);
+  bp.probs = (const coot::BatchProblem*)(base + o_probs);
+  bp.tile_begin = (const long long*)(base + o_begin);
+  bp.n_problems = n_problems;
+  bp.n_tiles = tiles;
+  for (size_t i = 0; i < an0.scalars.size(); ++i) bp.k[i] = scalar_bits(an0.scalars[i], an0.ct);
+  bp.partials = base + o_part;
+  bp.done = (unsigned*)(base + o_done);
+  bp.queue = (unsigned*)(base + o_queue);
+  bp.err_flag = ctx->err_flag;
+  bp.has_out = outs ? 1 : 0;
+  bp.mean = (red.kind == COOT_R_MEAN) ? 1 : 0;
+  *out = b;
+  return COOT_OK;
+}
+
+extern "C" coot_status coot_batch_run(coot_batch* b, void* red_out, coot_stream stream) {
+  if (!b) return set_error(COOT_ERR_INVALID, "batch is NULL");
+  if (b->has_red && !red_out) return set_error(COOT_ERR_INVALID, "red_out is NULL");
+  std::lock_guard<std::recursive_mutex> lk(b->ctx->mu);
+  DeviceGuard g(b->ctx->device);
+  coot::BatchParams bp = b->bp;
+  bp.red_out = red_out;
+  coot_status s = launch_kernel(b->mod, b->kname, b->grid, b->block, &bp, (cudaStream_t)stream);
+  if (s) return s;
+  coot_launch_info& li = b->ctx->last;
+  memset(&li, 0, sizeof li);
+  snprintf(li.kernel, sizeof li.kernel, "%s", b->kname.c_str());
+  li.grid = b->grid;
+  li.block = b->block;
+  li.vec = 1;
+  li.unroll = 1;
+  li.n_launches = 1;
+  li.algorithmic_bytes = b->algorithmic_bytes;
+  return COOT_OK;
+}
+
+extern "C" coot_status coot_batch_destroy(coot_batch* b) {
+  if (!b) return COOT_OK;
+  {
+    DeviceGuard g(b->ctx->device);
+    cudaDeviceSynchronize();
+    cudaFree(b->dev_mem);
+    cudaGetLastError();
+  }
+  delete b;
+  return COOT_OK;
+}
+
+extern "C" coot_status coot_eval_batched(coot_ctx* ctx, const coot_tree* tree, int64_t n_problems, int32_t n_leaves,
+                                         const coot_mat* problems, const coot_mat* outs, coot_reduce red,
+                                         void* red_out, coot_stream stream) {
+  coot_batch* b = nullptr;
+  coot_status s = coot_batch_create(ctx, tree, n_problems, n_leaves, problems, outs, red, &b);
+  if (s) return s;
+  s = coot_batch_run(b, red_out, stream);
+  {
+    DeviceGuard g(ctx->device);
+    // release the plan's table in stream order
+    cudaFreeAsync(b->dev_mem, (cudaStream_t)stream);
+    b->dev_mem = nullptr;
+    cudaGetLastError();
+  }
+  delete b;
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// CUDA graphs
+// ---------------------------------------------------------------------------
+extern "C" coot_status coot_graph_begin(coot_ctx* ctx, coot_stream stream) {
+  if (!ctx) return set_error(COOT_ERR_INVALID, "ctx is NULL");
+  if (!stream) return set_error(COOT_ERR_INVALID, "capture needs a non-default stream");
+  DeviceGuard g(ctx->device);
+  cudaError_t e = cudaStreamBeginCapture((cudaStream_t)stream, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) return cuda_error(e, "cudaStreamBeginCapture");
+  return COOT_OK;
+}
+
+extern "C" coot_status coot_graph_end(coot_ctx* ctx, coot_stream stream, coot_graph** out) {
+  if (!ctx || !out) return set_error(COOT_ERR_INVALID, "ctx or out is NULL");
+  *out = nullptr;
+  DeviceGuard g(ctx->device);
+  coot_graph* gr = new coot_graph();
+  cudaError_t e = cudaStreamEndCapture((cudaStream_t)stream, &gr->graph);
+  if (e != cudaSuccess) {
+    delete gr;
+    return cuda_error(e, "cudaStreamEndCapture");
+  }
+  e = cudaGraphInstantiate(&gr->exec, gr->graph, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(gr->graph);
+    delete gr;
+    return cuda_error(e, "cudaGraphInstantiate");
+  }
+  *out = gr;
+  return COOT_OK;
+}
+
+extern "C" coot_status coot_graph_launch(coot_graph* gr, coot_stream stream) {
+  if (!gr) return set_error(COOT_ERR_INVALID, "graph is NULL");
+  cudaError_t e = cudaGraphLaunch(gr->exec, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGraphLaunch");
+  return COOT_OK;
+}
+
+extern "C" coot_status coot_graph_destroy(coot_graph* gr) {
+  if (!gr) return COOT_OK;
+  if (gr->exec) cudaGraphExecDestroy(gr->exec);
+  if (gr->graph) cudaGraphDestroy(gr->graph);
+  delete gr;
+  return COOT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// host-side introspection
+// ---------------------------------------------------------------------------
+static coot_status analyse_for_host(const coot_tree* tree, const coot_mat* leaves, int32_t n_leaves,
+                                    const coot_mat* out, coot_reduce red, cg::Analysis* an, cg::Program* pg) {
+  coot_status s = cg::analyse(tree, leaves, n_leaves, out, red, an);
+  if (s) return s;
+  cg::Choice ch = cg::choose(*an, leaves, out);
+  *pg = cg::make_program(*an, ch.fam, red.kind == COOT_R_VAR);
+  return COOT_OK;
+}
+
+extern "C" coot_status coot_signature(const coot_tree* tree, const coot_mat* leaves, int32_t n_leaves,
+                                      const coot_mat* out, coot_reduce red, char* buf, size_t len) {
+  cg::Analysis an;
+  cg::Program pg;
+  coot_status s = analyse_for_host(tree, leaves, n_leaves, out, red, &an, &pg);
+  if (s) return s;
+  if (!buf || len == 0) return set_error(COOT_ERR_INVALID, "buf is NULL");
+  if (pg.signature.size() + 1 > len) return set_error(COOT_ERR_INVALID, "buf too small (%zu needed)", pg.signature.size() + 1);
+  memcpy(buf, pg.signature.c_str(), pg.signature.size() + 1);
+  return COOT_OK;
+}
+
+extern "C" coot_status coot_codegen(const coot_tree* tree, const coot_mat* leaves, int32_t n_leaves,
+                                    const coot_mat* out, coot_reduce red, char* buf, size_t len) {
+  cg::Analysis an;
+  cg::Program pg;
+  coot_status s = analyse_for_host(tree, leaves, n_leaves, out, red, &an, &pg);
+  if (s) return s;
+  if (!buf || len == 0) return set_error(COOT_ERR_INVALID, "buf is NULL");
+  if (pg.source.size() + 1 > len) return set_error(COOT_ERR_INVALID, "buf too small (%zu needed)", pg.source.size() + 1);
+  memcpy(buf, pg.source.c_str(), pg.source.size() + 1);
+  return COOT_OK;
+}
+
+extern "C" coot_status coot_compile(const coot_tree* tree, const coot_mat* leaves, int32_t n_leaves,
+                                    const coot_mat* out, coot_reduce red, size_t* cubin_bytes) {
+  cg::Analysis an;
+  cg::Program pg;
+  coot_status s = analyse_for_host(tree, leaves, n_leaves, out, red, &an, &pg);
+  if (s) return s;
+  std::vector<char> cubin;
+  std::string log;
+  s = cg::nvrtc_compile(pg.source, &cubin, &log);
+  if (s) return s;
+  if (cubin_bytes) *cubin_bytes = cubin.size();
+  return COOT_OK;
+}
+
+extern "C" coot_status coot_check_device_flag(coot_ctx* ctx, coot_stream stream, uint32_t* flags) {
+  if (!ctx) return set_error(COOT_ERR_INVALID, "ctx is NULL");
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  DeviceGuard g(ctx->device);
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_error(e, "cudaStreamSynchronize");
+  unsigned f = 0;
+  if ((e = cudaMemcpy(&f, ctx->err_flag, sizeof f, cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_error(e, "read device flag");
+  if (f && (e = cudaMemset(ctx->err_flag, 0, sizeof f)) != cudaSuccess) return cuda_error(e, "clear device flag");
+  if (flags) *flags = f;
+  if (f) return set_error(COOT_ERR_DEVICE_FLAG, "device flag 0x%x (bit 0: INT32 division by zero)", f);
+  return COOT_OK;
+}
+
+extern "C" coot_status coot_last_launch(coot_ctx* ctx, coot_launch_info* info) {
+  if (!ctx || !info) return set_error(COOT_ERR_INVALID, "ctx or info is NULL");
+  *info = ctx->last;
+  return COOT_OK;
+}

@@ -1,0 +1,160 @@
+// coot_internal.h -- host-side internals of libcootgb.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "coot.h"
+#include "dev/coot_params.h"
+
+namespace cg {
+
+using coot::Params;
+
+// device reduction modes (must match coot_dev.cuh)
+enum { RED_NONE = 0, RED_SUM = 1, RED_DOT = 2, RED_SSQ = 3, RED_MEAN1 = 4, RED_CSQ = 5 };
+
+enum Family { F_STR = 0, F_COL = 1, F_ROW = 2, F_TILE = 3, F_ADJ = 4, F_BATCH = 5 };
+const char* family_name(Family f);
+
+// compute types
+enum { CT_F32 = 0, CT_F64 = 1, CT_I32 = 2 };
+
+// A leaf read after trans() has been pushed down to the leaves: tree element
+// (i,j) reads view(i,j) (trans == false) or view(j,i) (trans == true), where
+// view(r,c) = leaf(r0 + r, c0 + c).
+struct Slot {
+  int leaf;
+  int64_t r0, c0;
+  int64_t vr, vc;  // view shape (rows, cols) of the leaf region read
+  bool trans;
+  bool full;  // the view is the whole leaf
+};
+
+// canonical node: op from coot_opcode (N_LEAF means "slot"), no N_TRANS/N_SUBMAT
+struct CNode {
+  int op;
+  int a = -1, b = -1;
+  int slot = -1;
+  int kidx = -1;
+};
+
+struct Analysis {
+  coot_dtype dtype = COOT_F32;
+  int esz = 4;
+  int ct = CT_F32;
+  int64_t nr = 0, nc = 0;  // shape of the tree's result
+  std::vector<Slot> slots;
+  std::vector<CNode> cn;
+  int root = -1;
+  std::vector<double> scalars;
+  std::string type_str;
+  int trmask = 0;
+  bool any_trans = false;
+  coot_reduce red{};
+  int red_mode = RED_NONE;  // device mode of the (last) pass
+  bool has_out = false;
+  int root_op = -1;         // op of the root (R_DOT needs N_SCHUR)
+};
+
+// Validate the call and canonicalise the tree.  `out` and `red_out` checks
+// are part of it.  Returns COOT_OK or an error with set_error().
+coot_status analyse(const coot_tree* tree, const coot_mat* leaves, int32_t n_leaves, const coot_mat* out,
+                    coot_reduce red, Analysis* an);
+
+// Kernel selection for a fused evaluation.
+struct Choice {
+  Family fam = F_STR;
+  bool collapsed = false;  // contiguous tree walked as one long column
+  bool vec_ok = false;     // every read and the output 16-byte aligned along columns
+  int64_t it_rows = 0, it_cols = 0;
+};
+Choice choose(const Analysis& an, const coot_mat* leaves, const coot_mat* out);
+
+struct KernelSpec {
+  std::string name;
+  int vec = 1, unroll = 1;
+  int block = 256;  // threads per block the kernel is built for (max)
+};
+
+struct Program {
+  std::string signature;  // cache key
+  std::string source;     // NVRTC source
+  std::vector<KernelSpec> kernels;
+};
+
+// Build the program (signature + source + kernel list) for a family.
+Program make_program(const Analysis& an, Family fam, bool var_two_pass);
+std::string storage_type_name(coot_dtype d);
+
+// ---- JIT ------------------------------------------------------------------
+struct Module {
+  cudaLibrary_t lib = nullptr;
+  std::map<std::string, cudaKernel_t> kernels;
+  std::map<std::string, cudaFuncAttributes> attrs;
+  size_t cubin_bytes = 0;
+};
+
+// NVRTC-compile `source` for sm_103a; no device needed.
+coot_status nvrtc_compile(const std::string& source, std::vector<char>* cubin, std::string* log);
+uint64_t fnv1a(const void* data, size_t n, uint64_t h = 1469598103934665603ull);
+uint64_t headers_hash();
+
+// ---- tuning ---------------------------------------------------------------
+struct LaunchCfg {
+  int kidx = 0;  // index in Program::kernels
+  int block = 256;
+  int blocks_per_sm = 4;
+};
+
+}  // namespace cg
+
+struct coot_ctx {
+  int device = 0;
+  unsigned flags = 0;
+  int sms = 0;
+  int l2_bytes = 0;
+  std::string cache_dir;
+  std::recursive_mutex mu;
+  std::unordered_map<std::string, std::unique_ptr<cg::Module>> mods;
+  std::map<std::string, cg::LaunchCfg> tuned;  // signature|bucket -> config
+  // workspace: [tickets][err flag][mu][partials]
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  size_t n_tickets = 0;
+  size_t partial_bytes = 0;
+  unsigned* tickets = nullptr;
+  unsigned* err_flag = nullptr;
+  double* mean_ptr = nullptr;
+  void* partials = nullptr;
+  coot_launch_info last{};
+};
+
+struct coot_batch {
+  coot_ctx* ctx = nullptr;
+  cg::Module* mod = nullptr;
+  std::string kname;
+  coot::BatchParams bp{};
+  void* dev_mem = nullptr;  // problems, prefix, done counters, queue, partials
+  int64_t n_problems = 0;
+  int grid = 0, block = 256;
+  int64_t algorithmic_bytes = 0;
+  bool has_red = false;
+};
+
+struct coot_graph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+// error helpers (api.cpp)
+coot_status set_error(coot_status s, const char* fmt, ...);
+coot_status cuda_error(cudaError_t e, const char* what);
+bool log_enabled(const coot_ctx* ctx);

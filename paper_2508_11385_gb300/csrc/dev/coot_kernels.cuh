@@ -1,0 +1,672 @@
+// coot_kernels.cuh -- kernel bodies instantiated per expression tree.
+//
+// Families (one generated __global__ wrapper per instantiation):
+//   str   element-wise map over a column-major 2-D range without transposed
+//         reads (a contiguous tree is walked as one long column), with an
+//         optional full reduction; 128-bit vector loads/stores when every
+//         read and the output are 16-byte aligned along columns.
+//   col   the same map with a per-column reduction (sum/mean along dim 0):
+//         one warp per column.
+//   row   the same map with a per-row reduction (dim 1): a thread owns V
+//         consecutive rows and walks a range of columns; column ranges are
+//         combined by the last block of each row block.
+//   tile  any tree with transposed reads: 32x32 output tiles, transposed
+//         reads staged through a padded shared-memory tile so that both the
+//         read and the write are coalesced; full, dim-0 and dim-1 reductions.
+//   adj   fused adjoint of a scalar loss sum(tree): forward values are
+//         recomputed per element and the reverse sweep writes every leaf's
+//         gradient.
+//   batch persistent kernel over many problems pulling 32x32 tiles from a
+//         queue, with a per-problem reduction.
+// Cross-block combines use a ticket counter: the block that arrives last
+// combines the partials in a fixed order and resets the counter.  Nothing
+// ever waits on another block.
+#pragma once
+#include "coot_params.h"
+#include "coot_dev.cuh"
+
+namespace coot {
+
+// ld.global.cg: read a value another block wrote (at L2, not L1)
+template <class A> __device__ __forceinline__ A load_cg(const A* p) {
+  A r;
+  const unsigned int* src = (const unsigned int*)p;
+  unsigned int* dst = (unsigned int*)&r;
+#pragma unroll
+  for (int i = 0; i < (int)(sizeof(A) / 4); ++i) asm volatile("ld.global.cg.u32 %0, [%1];" : "=r"(dst[i]) : "l"(src + i));
+  return r;
+}
+
+template <class S> __device__ __forceinline__ const S* at(const void* base, long long i, long long j, long long ld) {
+  return (const S*)base + (i + j * ld);
+}
+template <class S> __device__ __forceinline__ S* at_out(void* base, long long i, long long j, long long ld) {
+  return (S*)base + (i + j * ld);
+}
+
+// ---------------------------------------------------------------------------
+// per-element contribution of the root to the reduction
+// ---------------------------------------------------------------------------
+template <class T, int RED, class X, class K, class A, class Q>
+__device__ __forceinline__ typename X::C eval_elem(const X& x, const K& k, u32& err, int l, A& acc, const Q& csq) {
+  typedef typename X::C C;
+  if constexpr (RED == RED_DOT) {
+    C a = T::A::ev(x, k, err, l), b = T::B::ev(x, k, err, l);
+    acc.add_prod(a, b);
+    return op_mul(a, b);
+  } else {
+    C y = T::ev(x, k, err, l);
+    if constexpr (RED == RED_SUM || RED == RED_MEAN1) acc.add(y);
+    if constexpr (RED == RED_SSQ) acc.add_prod(y, y);
+    if constexpr (RED == RED_CSQ) {
+      C d = csq.centred(y);
+      acc.add(op_mul(d, d));
+    }
+    return y;
+  }
+}
+
+// the final value written for one reduction output
+template <class C, int RED, class A>
+__device__ __forceinline__ void write_result(const Params& p, const A& a, long long idx, double div) {
+  typedef typename rtype<C>::type R;
+  if constexpr (is_int_c<C>::value) {
+    // integer trees: exact int64 sums (sum / dot)
+    ((long long*)p.red_out)[idx] = a.ivalue();
+  } else {
+    if constexpr (RED == RED_SUM || RED == RED_DOT) {
+      ((R*)p.red_out)[idx] = (R)(a.value() / div);
+    } else if constexpr (RED == RED_SSQ) {
+      ((R*)p.red_out)[idx] = (R)sqrt(a.value());
+    } else if constexpr (RED == RED_MEAN1) {
+      *p.mu = a.value() / (double)p.count;
+    } else if constexpr (RED == RED_CSQ) {
+      double v;
+      if (p.count == 0)
+        v = __longlong_as_double(0x7ff8000000000000ll);  // NaN: no elements
+      else if (p.count == 1)
+        v = 0.0;
+      else
+        v = a.value() / p.den;
+      ((R*)p.red_out)[idx] = (R)v;
+    }
+  }
+}
+
+// block-level partial -> ticket -> last block combines all partials in order
+template <class C, int RED, class A> __device__ __forceinline__ void finish_full(const Params& p, A acc, A* smem) {
+  __shared__ int am_last;
+  acc = block_reduce(acc, smem);
+  if (threadIdx.x == 0) {
+    ((A*)p.partials)[blockIdx.x] = acc;
+    __threadfence();
+    unsigned int t = atomicAdd(p.tickets, 1u);
+    am_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (am_last) {
+    __threadfence();
+    A a;
+    a.init();
+    for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x) a.merge(load_cg(&((const A*)p.partials)[b]));
+    a = block_reduce(a, smem);
+    if (threadIdx.x == 0) {
+      write_result<C, RED>(p, a, 0, p.div);
+      *p.tickets = 0u;  // ready for the next launch
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// str: map (+ full reduction) over n_rows x n_cols, no transposed reads
+// ---------------------------------------------------------------------------
+template <class T, class S, int NS, int NK, int RED, int V, int U, bool OUT>
+__device__ __forceinline__ void str_kernel(const Params& p) {
+  typedef typename ctype<S>::type C;
+  typedef typename AccOf<C>::type A;
+  __shared__ A smem[32];
+  Scal<C, NK> k;
+#pragma unroll
+  for (int q = 0; q < NK; ++q) k.k[q] = scalar_from_bits<C>(p.k[q]);
+  typename CsqOf<C>::type csq;
+  if constexpr (RED == RED_CSQ) csq.set_mean(*p.mu);
+  u32 err = 0;
+  A acc;
+  acc.init();
+  const long long nr = p.n_rows, nc = p.n_cols, cpc = p.units_per_col;
+  const long long units = cpc * nc;
+  const long long step = (long long)blockDim.x * V;
+  const long long CH = step * U;
+  for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+    const long long j = (nc == 1) ? 0 : u / cpc;
+    const long long i0 = (u - j * cpc) * CH + (long long)threadIdx.x * V;
+    Vals<C, NS, V> x[U];
+    bool full[U];
+#pragma unroll
+    for (int g = 0; g < U; ++g) {
+      const long long i = i0 + g * step;
+      full[g] = (i + V <= nr);
+      if (full[g]) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) IO<S>::template load<V>(at<S>(p.src[s], i, j, p.ld[s]), x[g].v[s]);
+      } else {
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+#pragma unroll
+          for (int l = 0; l < V; ++l) x[g].v[s][l] = (i + l < nr) ? IO<S>::load1(at<S>(p.src[s], i + l, j, p.ld[s])) : C(0);
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < U; ++g) {
+      const long long i = i0 + g * step;
+      if (full[g]) {
+        C y[V];
+        if constexpr (sizeof(C) == 8 && RED != RED_NONE) {
+          // FP64: pre-sum the group pairwise, one addition into the chain
+          A part;
+          part.init();
+#pragma unroll
+          for (int l = 0; l < V; ++l) y[l] = eval_elem<T, RED>(x[g], k, err, l, part, csq);
+          acc.merge(part);
+        } else {
+#pragma unroll
+          for (int l = 0; l < V; ++l) y[l] = eval_elem<T, RED>(x[g], k, err, l, acc, csq);
+        }
+        if constexpr (OUT) IO<S>::template store<V>(at_out<S>(p.out, i, j, p.out_ld), y);
+      } else {
+#pragma unroll
+        for (int l = 0; l < V; ++l)
+          if (i + l < nr) {
+            C y = eval_elem<T, RED>(x[g], k, err, l, acc, csq);
+            if constexpr (OUT) IO<S>::store1(at_out<S>(p.out, i + l, j, p.out_ld), y);
+          }
+      }
+    }
+  }
+  if (err) atomicOr(p.err_flag, err);
+  if constexpr (RED != RED_NONE) finish_full<C, RED>(p, acc, smem);
+}
+
+// ---------------------------------------------------------------------------
+// col: map + per-column reduction (dim 0), one warp per column
+// ---------------------------------------------------------------------------
+template <class T, class S, int NS, int NK, int RED, int V, int U, bool OUT>
+__device__ __forceinline__ void col_kernel(const Params& p) {
+  typedef typename ctype<S>::type C;
+  typedef typename AccOf<C>::type A;
+  Scal<C, NK> k;
+#pragma unroll
+  for (int q = 0; q < NK; ++q) k.k[q] = scalar_from_bits<C>(p.k[q]);
+  typename CsqOf<C>::type csq;
+  u32 err = 0;
+  const int lane = threadIdx.x & 31;
+  const long long wpb = blockDim.x >> 5;
+  const long long nr = p.n_rows, nc = p.n_cols;
+  const long long step = 32LL * V;
+  for (long long j = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); j < nc; j += (long long)gridDim.x * wpb) {
+    A acc;
+    acc.init();
+    for (long long i0 = (long long)lane * V; i0 < nr; i0 += step * U) {
+      Vals<C, NS, V> x[U];
+      bool full[U];
+#pragma unroll
+      for (int g = 0; g < U; ++g) {
+        const long long i = i0 + g * step;
+        full[g] = (i + V <= nr);
+        if (full[g]) {
+#pragma unroll
+          for (int s = 0; s < NS; ++s) IO<S>::template load<V>(at<S>(p.src[s], i, j, p.ld[s]), x[g].v[s]);
+        } else {
+#pragma unroll
+          for (int s = 0; s < NS; ++s)
+#pragma unroll
+            for (int l = 0; l < V; ++l)
+              x[g].v[s][l] = (i + l < nr) ? IO<S>::load1(at<S>(p.src[s], i + l, j, p.ld[s])) : C(0);
+        }
+      }
+#pragma unroll
+      for (int g = 0; g < U; ++g) {
+        const long long i = i0 + g * step;
+        if (full[g]) {
+          C y[V];
+#pragma unroll
+          for (int l = 0; l < V; ++l) y[l] = eval_elem<T, RED>(x[g], k, err, l, acc, csq);
+          if constexpr (OUT) IO<S>::template store<V>(at_out<S>(p.out, i, j, p.out_ld), y);
+        } else {
+#pragma unroll
+          for (int l = 0; l < V; ++l)
+            if (i + l < nr) {
+              C y = eval_elem<T, RED>(x[g], k, err, l, acc, csq);
+              if constexpr (OUT) IO<S>::store1(at_out<S>(p.out, i + l, j, p.out_ld), y);
+            }
+        }
+      }
+    }
+    acc = warp_reduce(acc);
+    if (lane == 0) write_result<C, RED>(p, acc, j, p.div);
+  }
+  if (err) atomicOr(p.err_flag, err);
+}
+
+// ---------------------------------------------------------------------------
+// row: map + per-row reduction (dim 1)
+//   block b -> row block rb = b % n_row_blocks, column split sp = b / n_row_blocks
+// ---------------------------------------------------------------------------
+template <class T, class S, int NS, int NK, int RED, int V, int U, bool OUT>
+__device__ __forceinline__ void row_kernel(const Params& p) {
+  typedef typename ctype<S>::type C;
+  typedef typename AccOf<C>::type A;
+  __shared__ int am_last;
+  Scal<C, NK> k;
+#pragma unroll
+  for (int q = 0; q < NK; ++q) k.k[q] = scalar_from_bits<C>(p.k[q]);
+  typename CsqOf<C>::type csq;
+  u32 err = 0;
+  const long long nr = p.n_rows, nc = p.n_cols;
+  const long long nrb = p.n_row_blocks, nsp = p.n_splits, cps = p.units_per_col;
+  const long long rb = blockIdx.x % nrb, sp = blockIdx.x / nrb;
+  const long long i = (rb * blockDim.x + threadIdx.x) * V;
+  const long long j0 = sp * cps;
+  const long long j1 = (j0 + cps < nc) ? j0 + cps : nc;
+  const bool fullv = (i + V <= nr);
+  A acc[V];
+#pragma unroll
+  for (int l = 0; l < V; ++l) acc[l].init();
+  if (i < nr) {
+    for (long long jb = j0; jb < j1; jb += U) {
+      Vals<C, NS, V> x[U];
+#pragma unroll
+      for (int g = 0; g < U; ++g) {
+        const long long j = jb + g;
+        if (j < j1) {
+          if (fullv) {
+#pragma unroll
+            for (int s = 0; s < NS; ++s) IO<S>::template load<V>(at<S>(p.src[s], i, j, p.ld[s]), x[g].v[s]);
+          } else {
+#pragma unroll
+            for (int s = 0; s < NS; ++s)
+#pragma unroll
+              for (int l = 0; l < V; ++l)
+                x[g].v[s][l] = (i + l < nr) ? IO<S>::load1(at<S>(p.src[s], i + l, j, p.ld[s])) : C(0);
+          }
+        }
+      }
+#pragma unroll
+      for (int g = 0; g < U; ++g) {
+        const long long j = jb + g;
+        if (j < j1) {
+          if (fullv) {
+            C y[V];
+#pragma unroll
+            for (int l = 0; l < V; ++l) y[l] = eval_elem<T, RED>(x[g], k, err, l, acc[l], csq);
+            if constexpr (OUT) IO<S>::template store<V>(at_out<S>(p.out, i, j, p.out_ld), y);
+          } else {
+#pragma unroll
+            for (int l = 0; l < V; ++l)
+              if (i + l < nr) {
+                C y = eval_elem<T, RED>(x[g], k, err, l, acc[l], csq);
+                if constexpr (OUT) IO<S>::store1(at_out<S>(p.out, i + l, j, p.out_ld), y);
+              }
+          }
+        }
+      }
+    }
+  }
+  if (err) atomicOr(p.err_flag, err);
+  if (nsp == 1) {
+#pragma unroll
+    for (int l = 0; l < V; ++l)
+      if (i + l < nr) write_result<C, RED>(p, acc[l], i + l, p.div);
+    return;
+  }
+#pragma unroll
+  for (int l = 0; l < V; ++l)
+    if (i + l < nr) ((A*)p.partials)[sp * nr + i + l] = acc[l];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int t = atomicAdd(&p.tickets[rb], 1u);
+    am_last = (t == (unsigned int)(nsp - 1));
+  }
+  __syncthreads();
+  if (am_last) {
+    __threadfence();
+#pragma unroll
+    for (int l = 0; l < V; ++l)
+      if (i + l < nr) {
+        A a;
+        a.init();
+        for (long long s = 0; s < nsp; ++s) a.merge(load_cg(&((const A*)p.partials)[s * nr + i + l]));
+        write_result<C, RED>(p, a, i + l, p.div);
+      }
+    if (threadIdx.x == 0) p.tickets[rb] = 0u;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// tile: any tree with transposed reads; TRMASK marks the transposed slots.
+//   32x32 output tile, 256 threads as 32 (rows) x 8 (column phases); each
+//   thread evaluates rows i = 32 ti + tx of columns j = 32 tj + ty + 8 q.
+//   A transposed slot reads view(j, i): its 32x32 source block is read with
+//   consecutive threads on consecutive source rows and parked in shared
+//   memory with one column of padding, then read back transposed.
+//   DIM: -1 full reduction, 0 per column, 1 per row.
+// ---------------------------------------------------------------------------
+constexpr int TILE = 32;
+constexpr int TILE_PH = 8;  // blockDim.x == TILE * TILE_PH
+constexpr int TILE_Q = TILE / TILE_PH;
+
+template <int M> struct popc { static constexpr int value = (M & 1) + popc<(M >> 1)>::value; };
+template <> struct popc<0> { static constexpr int value = 0; };
+
+template <class T, class S, int NS, int NK, int RED, int DIM, int TRMASK, bool OUT>
+__device__ __forceinline__ void tile_kernel(const Params& p) {
+  typedef typename ctype<S>::type C;
+  typedef typename AccOf<C>::type A;
+  constexpr int NTR = popc<TRMASK>::value;
+  __shared__ C stage[NTR > 0 ? NTR : 1][TILE][TILE + 1];
+  __shared__ A smem[32];
+  __shared__ A rsum[TILE_PH][TILE];
+  __shared__ int am_last;
+  Scal<C, NK> k;
+#pragma unroll
+  for (int q = 0; q < NK; ++q) k.k[q] = scalar_from_bits<C>(p.k[q]);
+  typename CsqOf<C>::type csq;
+  if constexpr (RED == RED_CSQ) csq.set_mean(*p.mu);
+  u32 err = 0;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const long long nr = p.n_rows, nc = p.n_cols;
+  const long long ntr = (nr + TILE - 1) / TILE, ntc = (nc + TILE - 1) / TILE;
+  const long long tiles = ntr * ntc;
+  A acc;
+  acc.init();
+  for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const long long ti = t % ntr, tj = t / ntr;
+    const long long i = ti * TILE + tx;
+    if constexpr (NTR > 0) {
+      __syncthreads();  // the previous tile's shared reads are done
+      int q = 0;
+#pragma unroll
+      for (int s = 0; s < NS; ++s)
+        if ((TRMASK >> s) & 1) {
+          const long long vr = tj * TILE + tx;  // view row  = output column
+#pragma unroll
+          for (int w = 0; w < TILE_Q; ++w) {
+            const long long vc = ti * TILE + ty + TILE_PH * w;  // view column = output row
+            stage[q][ty + TILE_PH * w][tx] = (vr < nc && vc < nr) ? IO<S>::load1(at<S>(p.src[s], vr, vc, p.ld[s])) : C(0);
+          }
+          ++q;
+        }
+      __syncthreads();
+    }
+    Vals<C, NS, TILE_Q> x;
+#pragma unroll
+    for (int w = 0; w < TILE_Q; ++w) {
+      const long long j = tj * TILE + ty + TILE_PH * w;
+      const bool ok = (i < nr && j < nc);
+      int q = 0;
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        if ((TRMASK >> s) & 1) {
+          x.v[s][w] = stage[q][tx][ty + TILE_PH * w];
+          ++q;
+        } else {
+          x.v[s][w] = ok ? IO<S>::load1(at<S>(p.src[s], i, j, p.ld[s])) : C(0);
+        }
+      }
+    }
+    A racc;  // per-row partial over this tile's columns (DIM 1)
+    racc.init();
+#pragma unroll
+    for (int w = 0; w < TILE_Q; ++w) {
+      const long long j = tj * TILE + ty + TILE_PH * w;
+      const bool ok = (i < nr && j < nc);
+      if constexpr (DIM == 0) {
+        A cacc;
+        cacc.init();
+        if (ok) {
+          C y = eval_elem<T, RED>(x, k, err, w, cacc, csq);
+          if constexpr (OUT) IO<S>::store1(at_out<S>(p.out, i, j, p.out_ld), y);
+        }
+        cacc = warp_reduce(cacc);  // the 32 rows of column j
+        if (tx == 0 && j < nc) ((A*)p.partials)[ti * nc + j] = cacc;
+      } else if constexpr (DIM == 1) {
+        if (ok) {
+          C y = eval_elem<T, RED>(x, k, err, w, racc, csq);
+          if constexpr (OUT) IO<S>::store1(at_out<S>(p.out, i, j, p.out_ld), y);
+        }
+      } else {
+        if (ok) {
+          C y = eval_elem<T, RED>(x, k, err, w, acc, csq);
+          if constexpr (OUT) IO<S>::store1(at_out<S>(p.out, i, j, p.out_ld), y);
+        }
+      }
+    }
+    if constexpr (DIM == 1) {
+      rsum[ty][tx] = racc;
+      __syncthreads();
+      if (ty == 0) {
+        A a = rsum[0][tx];
+        for (int r = 1; r < TILE_PH; ++r) a.merge(rsum[r][tx]);
+        if (i < nr) ((A*)p.partials)[tj * nr + i] = a;
+      }
+    }
+    if constexpr (DIM == 0 || DIM == 1) {
+      // last tile of a column strip (DIM 0) / row strip (DIM 1) combines
+      __threadfence();
+      __syncthreads();
+      const long long strip = (DIM == 0) ? tj : ti;
+      const long long need = (DIM == 0) ? ntr : ntc;
+      if (threadIdx.x == 0) {
+        unsigned int tk = atomicAdd(&p.tickets[strip], 1u);
+        am_last = (tk == (unsigned int)(need - 1));
+      }
+      __syncthreads();
+      if (am_last) {
+        __threadfence();
+        // thread (tx, ty): output o = 32 strip + tx, partials ty, ty+8, ...
+        const long long o = strip * TILE + tx;
+        const long long no = (DIM == 0) ? nc : nr;
+        A a;
+        a.init();
+        if (o < no)
+          for (long long s = ty; s < need; s += TILE_PH) a.merge(load_cg(&((const A*)p.partials)[s * no + o]));
+        rsum[ty][tx] = a;
+        __syncthreads();
+        if (ty == 0 && o < no) {
+          A b = rsum[0][tx];
+          for (int r = 1; r < TILE_PH; ++r) b.merge(rsum[r][tx]);
+          write_result<C, RED>(p, b, o, p.div);
+        }
+        if (threadIdx.x == 0) p.tickets[strip] = 0u;
+      }
+      __syncthreads();
+    }
+  }
+  if (err) atomicOr(p.err_flag, err);
+  if constexpr (DIM == -1 && RED != RED_NONE) finish_full<C, RED>(p, acc, smem);
+}
+
+// ---------------------------------------------------------------------------
+// adj: gradient of L = mult * sum(tree) with respect to every slot
+// ---------------------------------------------------------------------------
+template <class T, class S, int NS, int NK, int V, int U>
+__device__ __forceinline__ void adj_kernel(const Params& p) {
+  typedef typename ctype<S>::type C;
+  Scal<C, NK> k;
+#pragma unroll
+  for (int q = 0; q < NK; ++q) k.k[q] = scalar_from_bits<C>(p.k[q]);
+  u32 err = 0;
+  const C g0 = (C)((double)(*(const C*)p.upstream) * p.grad_mult);
+  const long long nr = p.n_rows, nc = p.n_cols, cpc = p.units_per_col;
+  const long long units = cpc * nc;
+  const long long step = (long long)blockDim.x * V;
+  const long long CH = step * U;
+  for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+    const long long j = (nc == 1) ? 0 : u / cpc;
+    const long long i0 = (u - j * cpc) * CH + (long long)threadIdx.x * V;
+    Vals<C, NS, V> x[U];
+    bool full[U];
+#pragma unroll
+    for (int g = 0; g < U; ++g) {
+      const long long i = i0 + g * step;
+      full[g] = (i + V <= nr);
+      if (full[g]) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) IO<S>::template load<V>(at<S>(p.src[s], i, j, p.ld[s]), x[g].v[s]);
+      } else {
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+#pragma unroll
+          for (int l = 0; l < V; ++l) x[g].v[s][l] = (i + l < nr) ? IO<S>::load1(at<S>(p.src[s], i + l, j, p.ld[s])) : C(0);
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < U; ++g) {
+      const long long i = i0 + g * step;
+      C gs[NS][V];
+#pragma unroll
+      for (int l = 0; l < V; ++l) {
+        C gl[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) gl[s] = C(0);
+        if (full[g] || i + l < nr) T::bw(x[g], k, err, l, g0, gl);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) gs[s][l] = gl[s];
+      }
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        if (p.grad[s] == nullptr) continue;
+        if (full[g]) {
+          IO<S>::template store<V>(at_out<S>(p.grad[s], i, j, p.grad_ld[s]), gs[s]);
+        } else {
+#pragma unroll
+          for (int l = 0; l < V; ++l)
+            if (i + l < nr) IO<S>::store1(at_out<S>(p.grad[s], i + l, j, p.grad_ld[s]), gs[s][l]);
+        }
+      }
+    }
+  }
+  if (err) atomicOr(p.err_flag, err);
+}
+
+// ---------------------------------------------------------------------------
+// batch: persistent kernel over tiles of many problems
+// ---------------------------------------------------------------------------
+template <class T, class S, int NS, int NK, int TRMASK, bool RED>
+__device__ __forceinline__ void batch_kernel(const BatchParams bp) {
+  typedef typename ctype<S>::type C;
+  typedef typename AccOf<C>::type A;
+  constexpr int NTR = popc<TRMASK>::value;
+  __shared__ C stage[NTR > 0 ? NTR : 1][TILE][TILE + 1];
+  __shared__ A smem[32];
+  __shared__ long long s_tile;
+  __shared__ int am_last;
+  Scal<C, NK> k;
+#pragma unroll
+  for (int q = 0; q < NK; ++q) k.k[q] = scalar_from_bits<C>(bp.k[q]);
+  typename CsqOf<C>::type csq;
+  u32 err = 0;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (;;) {
+    __syncthreads();  // everyone is done with the previous tile and s_tile
+    if (threadIdx.x == 0) s_tile = (long long)atomicAdd(&bp.queue[0], 1u);
+    __syncthreads();
+    const long long t = s_tile;
+    if (t >= bp.n_tiles) break;
+    // problem owning tile t: largest pb with tile_begin[pb] <= t
+    long long lo = 0, hi = bp.n_problems - 1;
+    while (lo < hi) {
+      long long mid = (lo + hi + 1) >> 1;
+      if (bp.tile_begin[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const BatchProblem& pr = bp.probs[lo];
+    const long long nr = pr.n_rows, nc = pr.n_cols;
+    const long long lt = t - pr.tile_begin;
+    const long long ti = lt % pr.n_tile_rows, tj = lt / pr.n_tile_rows;
+    const long long i = ti * TILE + tx;
+    if constexpr (NTR > 0) {
+      int q = 0;
+#pragma unroll
+      for (int s = 0; s < NS; ++s)
+        if ((TRMASK >> s) & 1) {
+          const long long vr = tj * TILE + tx;
+#pragma unroll
+          for (int w = 0; w < TILE_Q; ++w) {
+            const long long vc = ti * TILE + ty + TILE_PH * w;
+            stage[q][ty + TILE_PH * w][tx] = (vr < nc && vc < nr) ? IO<S>::load1(at<S>(pr.src[s], vr, vc, pr.ld[s])) : C(0);
+          }
+          ++q;
+        }
+      __syncthreads();
+    }
+    Vals<C, NS, TILE_Q> x;
+#pragma unroll
+    for (int w = 0; w < TILE_Q; ++w) {
+      const long long j = tj * TILE + ty + TILE_PH * w;
+      const bool ok = (i < nr && j < nc);
+      int q = 0;
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        if ((TRMASK >> s) & 1) {
+          x.v[s][w] = stage[q][tx][ty + TILE_PH * w];
+          ++q;
+        } else {
+          x.v[s][w] = ok ? IO<S>::load1(at<S>(pr.src[s], i, j, pr.ld[s])) : C(0);
+        }
+      }
+    }
+    A acc;
+    acc.init();
+#pragma unroll
+    for (int w = 0; w < TILE_Q; ++w) {
+      const long long j = tj * TILE + ty + TILE_PH * w;
+      if (i < nr && j < nc) {
+        C y = eval_elem<T, RED ? RED_SUM : RED_NONE>(x, k, err, w, acc, csq);
+        if (bp.has_out) IO<S>::store1(at_out<S>(pr.out, i, j, pr.out_ld), y);
+      }
+    }
+    if constexpr (RED) {
+      acc = block_reduce(acc, smem);
+      const long long ntile = bp.tile_begin[lo + 1] - pr.tile_begin;
+      if (threadIdx.x == 0) {
+        ((A*)bp.partials)[t] = acc;
+        __threadfence();
+        unsigned int d = atomicAdd(&bp.done[lo], 1u);
+        am_last = (d == (unsigned int)(ntile - 1));
+      }
+      __syncthreads();
+      if (am_last) {
+        // the problem's last tile: combine its tiles' partials in tile order
+        __threadfence();
+        A a;
+        a.init();
+        for (long long s = threadIdx.x; s < ntile; s += blockDim.x)
+          a.merge(load_cg(&((const A*)bp.partials)[pr.tile_begin + s]));
+        a = block_reduce(a, smem);
+        if (threadIdx.x == 0) {
+          typedef typename rtype<C>::type R;
+          if constexpr (is_int_c<C>::value) {
+            ((long long*)bp.red_out)[lo] = a.ivalue();
+          } else {
+            double v = a.value();
+            if (bp.mean) v /= (double)(nr * nc);
+            ((R*)bp.red_out)[lo] = (R)v;
+          }
+          bp.done[lo] = 0u;
+        }
+      }
+    }
+  }
+  if (err) atomicOr(bp.err_flag, err);
+  // the last block out resets the queue for the next launch
+  if (threadIdx.x == 0) {
+    unsigned int e = atomicAdd(&bp.queue[1], 1u);
+    if (e == gridDim.x - 1) {
+      bp.queue[0] = 0u;
+      bp.queue[1] = 0u;
+    }
+  }
+}
+
+}  // namespace coot

@@ -1,0 +1,73 @@
+// coot_params.h -- the one kernel-argument block of every generated kernel.
+// Included by the host library (to fill it) and by the device code compiled
+// through NVRTC (to read it), so the layout is defined once.
+#pragma once
+
+#define COOT_MAX_SLOTS 8
+#define COOT_MAX_SCALARS_DEV 16
+
+namespace coot {
+
+struct Params {
+  // leaf reads ("slots"): device address of element (0,0) of the view read
+  // and its column stride in elements
+  const void* src[COOT_MAX_SLOTS];
+  long long ld[COOT_MAX_SLOTS];
+  // the tree's scalars, bit patterns of the compute type
+  unsigned long long k[COOT_MAX_SCALARS_DEV];
+  // materialised result Y (nullable) and its column stride
+  void* out;
+  long long out_ld;
+  // iteration shape (a contiguous tree is walked as one long column)
+  long long n_rows, n_cols;
+  // kernel-family specific: str -- chunks per column; row -- columns per split
+  long long units_per_col;
+  // row -- number of column splits; tile -- unused
+  long long n_splits;
+  // row -- number of row blocks
+  long long n_row_blocks;
+  // elements reduced (mean / var finals) and divisors
+  long long count;
+  double div;  // mean: count (or length along dim); sum: 1
+  double den;  // var: N-1 or N
+  // reduction result (device) and workspace
+  void* red_out;
+  void* partials;
+  unsigned int* tickets;
+  unsigned int* err_flag;
+  double* mu;
+  // adjoint: gradient outputs per slot (nullable) and the upstream scalar
+  void* grad[COOT_MAX_SLOTS];
+  long long grad_ld[COOT_MAX_SLOTS];
+  const void* upstream;
+  double grad_mult;  // 1 for accu, 1/N for mean
+};
+
+// Batched evaluation: one record per problem, read by the persistent kernel.
+struct BatchProblem {
+  const void* src[COOT_MAX_SLOTS];
+  long long ld[COOT_MAX_SLOTS];
+  void* out;
+  long long out_ld;
+  long long n_rows, n_cols;
+  long long tile_begin;  // first global tile index of this problem
+  long long n_tile_rows; // tiles along the rows
+};
+
+struct BatchParams {
+  const BatchProblem* probs;
+  const long long* tile_begin;  // n_problems + 1 prefix (for the binary search)
+  long long n_problems;
+  long long n_tiles;
+  unsigned long long k[COOT_MAX_SCALARS_DEV];
+  void* red_out;     // one result per problem (nullable)
+  void* partials;    // one accumulator per tile
+  unsigned int* done;    // per-problem tile counters (zero between launches)
+  unsigned int* queue;   // [0] next tile, [1] exited blocks (zero between launches)
+  unsigned int* err_flag;
+  double div_unused;
+  int has_out;
+  int mean;  // divide each problem's sum by its element count
+};
+
+}  // namespace coot

@@ -1,0 +1,38 @@
+// dev_check.cu -- build-time check of the device expression templates.
+//
+// The kernels of this library are generated per expression tree and compiled
+// by NVRTC at run time.  This translation unit instantiates every kernel
+// family once for representative trees and storage types with nvcc for
+// sm_103a, so that an error in the device headers fails the build, and the
+// build log records registers and shared memory per family (-Xptxas -v).
+// The object is not linked into the library.
+#include "coot_kernels.cuh"
+using namespace coot;
+
+// Y = 0.5*A + B % exp(C)
+typedef eGlue<eOp<Leaf<0>, eop_scalar_times<0>>, eGlue<Leaf<1>, eOp<Leaf<2>, eop_exp>, eglue_schur>, eglue_plus> T3;
+// A % B
+typedef eGlue<Leaf<0>, Leaf<1>, eglue_schur> T2;
+// sqrt(abs(exp(A-B) / (1 + abs(C)) % D - E)) % F
+typedef eGlue<eOp<eOp<eGlue<eGlue<eOp<eGlue<Leaf<0>, Leaf<1>, eglue_minus>, eop_exp>,
+                                  eOp<eOp<Leaf<2>, eop_abs>, eop_scalar_plus<0>>, eglue_div>,
+                            Leaf<3>, eglue_schur>, eop_abs>, eop_sqrt>, Leaf<5>, eglue_schur> T6;
+
+#define K(name, bound, body) \
+  extern "C" __global__ void __launch_bounds__(bound) name(const __grid_constant__ Params p) { body(p); }
+
+K(chk_str_f32, 512, (str_kernel<T3, float, 3, 1, RED_SUM, 4, 2, true>))
+K(chk_str_bf16, 512, (str_kernel<T3, bf16, 3, 1, RED_SSQ, 8, 1, true>))
+K(chk_str_f16_var, 512, (str_kernel<T3, f16, 3, 1, RED_CSQ, 8, 2, false>))
+K(chk_str_f64, 512, (str_kernel<T3, double, 3, 1, RED_CSQ, 2, 2, false>))
+K(chk_str_i32_dot, 512, (str_kernel<T2, int, 2, 0, RED_DOT, 4, 2, true>))
+K(chk_str_l8, 512, (str_kernel<T6, float, 6, 1, RED_NONE, 4, 2, true>))
+K(chk_col_f32, 512, (col_kernel<T3, float, 3, 1, RED_SUM, 4, 2, true>))
+K(chk_row_f16, 512, (row_kernel<T3, f16, 3, 1, RED_SUM, 8, 2, true>))
+K(chk_tile_dim0, 256, (tile_kernel<T3, float, 3, 1, RED_SUM, 0, 4, true>))
+K(chk_tile_dim1, 256, (tile_kernel<T3, float, 3, 1, RED_SUM, 1, 5, true>))
+K(chk_tile_f64, 256, (tile_kernel<T3, double, 3, 1, RED_MEAN1, -1, 1, false>))
+K(chk_adj_f32, 512, (adj_kernel<T3, float, 3, 1, 4, 2>))
+extern "C" __global__ void __launch_bounds__(256) chk_batch(const __grid_constant__ BatchParams p) {
+  batch_kernel<T3, float, 3, 1, 4, true>(p);
+}

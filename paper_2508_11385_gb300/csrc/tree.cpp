@@ -1,0 +1,509 @@
+// tree.cpp -- validation, canonicalisation, kernel choice and code generation.
+//
+// A coot_tree is the run-time form of the paper's expression types (Sec. 3):
+// leaves are Mat objects, N_TRANS is Op<T1,op_trans>, the unary and scalar
+// kinds are eOp<T1,eop_type>, N_PLUS..N_DIV are eGlue<T1,T2,eglue_type>.
+// As with Bandicoot's compile-time pattern matching, the whole tree is
+// analysed before anything runs:
+//   - shapes are checked as Armadillo does ("incompatible matrix dimensions");
+//   - trans() is pushed down to the leaves -- trans(A + B) reads A and B
+//     transposed -- so a transpose never materialises (the paper's implicit
+//     transpose of trans(X)*Y, applied to element-wise trees);
+//   - identical leaf reads are merged, so every distinct operand element is
+//     loaded once;
+//   - the tree is spelt as a C++ type over the device expression templates,
+//     which NVRTC instantiates into one kernel per tree (Sec. 4 notes that
+//     Bandicoot otherwise chains predefined kernels; fusing the tree into one
+//     generated kernel is the follow-up the conclusion announces).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <sstream>
+#include <tuple>
+
+#include "coot_internal.h"
+
+namespace cg {
+
+const char* family_name(Family f) {
+  switch (f) {
+    case F_STR: return "str";
+    case F_COL: return "col";
+    case F_ROW: return "row";
+    case F_TILE: return "tile";
+    case F_ADJ: return "adj";
+    case F_BATCH: return "batch";
+  }
+  return "?";
+}
+
+static int esize(int32_t d) {
+  switch (d) {
+    case COOT_F32: return 4;
+    case COOT_F64: return 8;
+    case COOT_BF16: return 2;
+    case COOT_F16: return 2;
+    case COOT_I32: return 4;
+  }
+  return 0;
+}
+
+std::string storage_type_name(coot_dtype d) {
+  switch (d) {
+    case COOT_F32: return "float";
+    case COOT_F64: return "double";
+    case COOT_BF16: return "bf16";
+    case COOT_F16: return "f16";
+    case COOT_I32: return "int";
+  }
+  return "?";
+}
+
+static bool is_unary(int op) {
+  return op == COOT_N_NEG || op == COOT_N_EXP || op == COOT_N_LOG || op == COOT_N_ABS || op == COOT_N_SQUARE ||
+         op == COOT_N_SQRT;
+}
+static bool is_scalar_op(int op) { return op >= COOT_N_SCAL_TIMES && op <= COOT_N_SCAL_DIV_POST; }
+static bool is_binary(int op) { return op >= COOT_N_PLUS && op <= COOT_N_DIV; }
+
+static bool mat_shape_ok(const coot_mat& m) {
+  if (m.n_rows < 0 || m.n_cols < 0) return false;
+  if (m.n_cols > 1 && m.ld < m.n_rows) return false;
+  if (m.n_cols > 1 && m.ld < 1) return false;
+  return true;
+}
+
+static int64_t mat_ld(const coot_mat& m) { return (m.n_cols > 1) ? m.ld : (m.ld > 0 ? m.ld : m.n_rows); }
+
+// byte range [lo, hi) touched by a view of a matrix
+static void view_range(const coot_mat& m, int64_t r0, int64_t c0, int64_t vr, int64_t vc, int esz, uintptr_t* lo,
+                       uintptr_t* hi) {
+  if (vr <= 0 || vc <= 0) {
+    *lo = *hi = 0;
+    return;
+  }
+  int64_t ld = mat_ld(m);
+  uintptr_t base = (uintptr_t)m.data;
+  *lo = base + (uintptr_t)((r0 + c0 * ld) * esz);
+  *hi = base + (uintptr_t)((r0 + vr - 1 + (c0 + vc - 1) * ld + 1) * esz);
+}
+
+coot_status analyse(const coot_tree* tree, const coot_mat* leaves, int32_t n_leaves, const coot_mat* out,
+                    coot_reduce red, Analysis* an) {
+  *an = Analysis();
+  if (!tree || !tree->nodes) return set_error(COOT_ERR_INVALID, "tree or tree->nodes is NULL");
+  const int nn = tree->n_nodes;
+  if (nn < 1 || nn > COOT_MAX_NODES) return set_error(COOT_ERR_INVALID, "n_nodes %d outside 1..%d", nn, COOT_MAX_NODES);
+  if (!leaves || n_leaves < 1 || n_leaves > COOT_MAX_LEAVES)
+    return set_error(COOT_ERR_INVALID, "n_leaves %d outside 1..%d (or leaves NULL)", n_leaves, COOT_MAX_LEAVES);
+  const int32_t dt = leaves[0].dtype;
+  if (esize(dt) == 0) return set_error(COOT_ERR_DTYPE, "leaf 0: unknown dtype %d", dt);
+  for (int i = 0; i < n_leaves; ++i) {
+    if (leaves[i].dtype != dt) return set_error(COOT_ERR_DTYPE, "leaf %d: all leaves must share one dtype", i);
+    if (!mat_shape_ok(leaves[i]))
+      return set_error(COOT_ERR_INVALID, "leaf %d: bad shape %lld x %lld, ld %lld", i, (long long)leaves[i].n_rows,
+                       (long long)leaves[i].n_cols, (long long)leaves[i].ld);
+    if (!leaves[i].data && leaves[i].n_rows * leaves[i].n_cols > 0)
+      return set_error(COOT_ERR_INVALID, "leaf %d: NULL data", i);
+  }
+  an->dtype = (coot_dtype)dt;
+  an->esz = esize(dt);
+  an->ct = (dt == COOT_F64) ? CT_F64 : (dt == COOT_I32 ? CT_I32 : CT_F32);
+  const bool is_int = (an->ct == CT_I32);
+
+  // ---- per-node checks and shape inference
+  std::vector<int64_t> R(nn), Cc(nn);
+  for (int n = 0; n < nn; ++n) {
+    const coot_node& d = tree->nodes[n];
+    const int op = d.op;
+    if (op < 0 || op >= COOT_N_COUNT_) return set_error(COOT_ERR_INVALID, "node %d: unknown op %d", n, op);
+    auto operand = [&](int idx, const char* nm) -> coot_status {
+      if (idx < 0 || idx >= n)
+        return set_error(COOT_ERR_INVALID, "node %d: operand %s = %d must refer to an earlier node", n, nm, idx);
+      return COOT_OK;
+    };
+    coot_status s;
+    if (op == COOT_N_LEAF) {
+      if (d.leaf < 0 || d.leaf >= n_leaves) return set_error(COOT_ERR_INVALID, "node %d: leaf %d not given", n, d.leaf);
+      R[n] = leaves[d.leaf].n_rows;
+      Cc[n] = leaves[d.leaf].n_cols;
+    } else if (op == COOT_N_SUBMAT) {
+      if ((s = operand(d.a, "a"))) return s;
+      if (tree->nodes[d.a].op != COOT_N_LEAF)
+        return set_error(COOT_ERR_INVALID, "node %d: submat must view a leaf node", n);
+      if (d.r0 < 0 || d.c0 < 0 || d.nr < 0 || d.nc < 0 || d.r0 + d.nr > R[d.a] || d.c0 + d.nc > Cc[d.a])
+        return set_error(COOT_ERR_SHAPE, "node %d: submat (%lld,%lld) %lldx%lld outside %lldx%lld", n, (long long)d.r0,
+                         (long long)d.c0, (long long)d.nr, (long long)d.nc, (long long)R[d.a], (long long)Cc[d.a]);
+      R[n] = d.nr;
+      Cc[n] = d.nc;
+    } else if (op == COOT_N_TRANS) {
+      if ((s = operand(d.a, "a"))) return s;
+      R[n] = Cc[d.a];
+      Cc[n] = R[d.a];
+    } else if (is_unary(op) || is_scalar_op(op)) {
+      if ((s = operand(d.a, "a"))) return s;
+      if (is_int && (op == COOT_N_EXP || op == COOT_N_LOG || op == COOT_N_SQRT))
+        return set_error(COOT_ERR_DTYPE, "node %d: exp/log/sqrt are not defined for INT32 trees", n);
+      if (is_scalar_op(op)) {
+        if (is_int && !(std::isfinite(d.k) && d.k > -2147483649.0 && d.k < 2147483648.0))
+          return set_error(COOT_ERR_INVALID, "node %d: scalar %g does not fit INT32", n, d.k);
+      }
+      R[n] = R[d.a];
+      Cc[n] = Cc[d.a];
+    } else if (is_binary(op)) {
+      if ((s = operand(d.a, "a")) || (s = operand(d.b, "b"))) return s;
+      if (R[d.a] != R[d.b] || Cc[d.a] != Cc[d.b])
+        return set_error(COOT_ERR_SHAPE, "node %d: incompatible matrix dimensions: %lldx%lld and %lldx%lld", n,
+                         (long long)R[d.a], (long long)Cc[d.a], (long long)R[d.b], (long long)Cc[d.b]);
+      R[n] = R[d.a];
+      Cc[n] = Cc[d.a];
+    }
+  }
+  const int root = nn - 1;
+  an->nr = R[root];
+  an->nc = Cc[root];
+  an->root_op = tree->nodes[root].op;
+
+  // ---- reduction
+  an->red = red;
+  switch (red.kind) {
+    case COOT_R_NONE: an->red_mode = RED_NONE; break;
+    case COOT_R_ACCU: an->red_mode = RED_SUM; an->red.dim = -1; break;
+    case COOT_R_SUM:
+    case COOT_R_MEAN:
+      if (red.dim < -1 || red.dim > 1) return set_error(COOT_ERR_INVALID, "reduction dim %d not in {-1,0,1}", red.dim);
+      an->red_mode = RED_SUM;
+      break;
+    case COOT_R_DOT:
+      if (an->root_op != COOT_N_SCHUR) return set_error(COOT_ERR_INVALID, "R_DOT needs a root node a %% b");
+      an->red_mode = RED_DOT;
+      an->red.dim = -1;
+      break;
+    case COOT_R_NORM2:
+      if (an->nr != 1 && an->nc != 1)
+        return set_error(COOT_ERR_SHAPE, "R_NORM2 is the vector 2-norm; use R_NORM_FRO for a %lldx%lld matrix",
+                         (long long)an->nr, (long long)an->nc);
+      an->red_mode = RED_SSQ;
+      an->red.dim = -1;
+      break;
+    case COOT_R_NORM_FRO: an->red_mode = RED_SSQ; an->red.dim = -1; break;
+    case COOT_R_VAR:
+      if (red.norm_type != 0 && red.norm_type != 1) return set_error(COOT_ERR_INVALID, "var norm_type must be 0 or 1");
+      an->red_mode = RED_CSQ;
+      an->red.dim = -1;
+      break;
+    default: return set_error(COOT_ERR_INVALID, "unknown reduction kind %d", red.kind);
+  }
+  if (is_int && (red.kind == COOT_R_MEAN || red.kind == COOT_R_NORM2 || red.kind == COOT_R_NORM_FRO ||
+                 red.kind == COOT_R_VAR))
+    return set_error(COOT_ERR_DTYPE, "mean/norm/var are not defined for INT32 trees");
+
+  // ---- canonical form: push trans() down to the leaf reads
+  std::map<std::pair<int, int>, int> memo;
+  std::map<std::tuple<int, int64_t, int64_t, int64_t, int64_t, int>, int> slot_of;
+  std::function<int(int, bool)> canon = [&](int n, bool t) -> int {
+    auto key = std::make_pair(n, (int)t);
+    auto it = memo.find(key);
+    if (it != memo.end()) return it->second;
+    const coot_node& d = tree->nodes[n];
+    CNode c;
+    if (d.op == COOT_N_LEAF || d.op == COOT_N_SUBMAT) {
+      int leaf = (d.op == COOT_N_LEAF) ? d.leaf : tree->nodes[d.a].leaf;
+      const coot_mat& L = leaves[leaf];
+      int64_t r0 = 0, c0 = 0, vr = L.n_rows, vc = L.n_cols;
+      if (d.op == COOT_N_SUBMAT) {
+        r0 = d.r0;
+        c0 = d.c0;
+        vr = d.nr;
+        vc = d.nc;
+      }
+      auto sk = std::make_tuple(leaf, r0, c0, vr, vc, (int)t);
+      auto si = slot_of.find(sk);
+      int s;
+      if (si == slot_of.end()) {
+        s = (int)an->slots.size();
+        Slot sl;
+        sl.leaf = leaf;
+        sl.r0 = r0;
+        sl.c0 = c0;
+        sl.vr = vr;
+        sl.vc = vc;
+        sl.trans = t;
+        sl.full = (r0 == 0 && c0 == 0 && vr == L.n_rows && vc == L.n_cols);
+        an->slots.push_back(sl);
+        slot_of[sk] = s;
+      } else {
+        s = si->second;
+      }
+      c.op = COOT_N_LEAF;
+      c.slot = s;
+    } else if (d.op == COOT_N_TRANS) {
+      int r = canon(d.a, !t);
+      memo[key] = r;
+      return r;
+    } else if (is_unary(d.op) || is_scalar_op(d.op)) {
+      c.op = d.op;
+      c.a = canon(d.a, t);
+      if (is_scalar_op(d.op)) {
+        c.kidx = (int)an->scalars.size();
+        an->scalars.push_back(d.k);
+      }
+    } else {
+      c.op = d.op;
+      c.a = canon(d.a, t);
+      c.b = canon(d.b, t);
+    }
+    int idx = (int)an->cn.size();
+    an->cn.push_back(c);
+    memo[key] = idx;
+    return idx;
+  };
+  an->root = canon(root, false);
+  if ((int)an->slots.size() > COOT_MAX_SLOTS)
+    return set_error(COOT_ERR_UNSUPPORTED, "tree reads %d distinct leaf views; at most %d", (int)an->slots.size(),
+                     COOT_MAX_SLOTS);
+  if ((int)an->scalars.size() > COOT_MAX_SCALARS_DEV)
+    return set_error(COOT_ERR_UNSUPPORTED, "tree has %d scalars; at most %d", (int)an->scalars.size(),
+                     COOT_MAX_SCALARS_DEV);
+  for (size_t s = 0; s < an->slots.size(); ++s)
+    if (an->slots[s].trans) {
+      an->any_trans = true;
+      an->trmask |= (1 << s);
+    }
+
+  // ---- C++ type of the canonical tree
+  std::function<std::string(int)> spell = [&](int i) -> std::string {
+    const CNode& c = an->cn[i];
+    char buf[64];
+    if (c.op == COOT_N_LEAF) {
+      snprintf(buf, sizeof buf, "Leaf<%d>", c.slot);
+      return buf;
+    }
+    const char* eop = nullptr;
+    switch (c.op) {
+      case COOT_N_NEG: eop = "eop_neg"; break;
+      case COOT_N_EXP: eop = "eop_exp"; break;
+      case COOT_N_LOG: eop = "eop_log"; break;
+      case COOT_N_ABS: eop = "eop_abs"; break;
+      case COOT_N_SQUARE: eop = "eop_square"; break;
+      case COOT_N_SQRT: eop = "eop_sqrt"; break;
+      default: break;
+    }
+    if (eop) return "eOp<" + spell(c.a) + ", " + eop + ">";
+    const char* sop = nullptr;
+    switch (c.op) {
+      case COOT_N_SCAL_TIMES: sop = "eop_scalar_times"; break;
+      case COOT_N_SCAL_PLUS: sop = "eop_scalar_plus"; break;
+      case COOT_N_SCAL_MINUS_PRE: sop = "eop_scalar_minus_pre"; break;
+      case COOT_N_SCAL_MINUS_POST: sop = "eop_scalar_minus_post"; break;
+      case COOT_N_SCAL_DIV_PRE: sop = "eop_scalar_div_pre"; break;
+      case COOT_N_SCAL_DIV_POST: sop = "eop_scalar_div_post"; break;
+      default: break;
+    }
+    if (sop) {
+      snprintf(buf, sizeof buf, "%s<%d>", sop, c.kidx);
+      return "eOp<" + spell(c.a) + ", " + buf + ">";
+    }
+    const char* gop = nullptr;
+    switch (c.op) {
+      case COOT_N_PLUS: gop = "eglue_plus"; break;
+      case COOT_N_MINUS: gop = "eglue_minus"; break;
+      case COOT_N_SCHUR: gop = "eglue_schur"; break;
+      case COOT_N_DIV: gop = "eglue_div"; break;
+      default: break;
+    }
+    return "eGlue<" + spell(c.a) + ", " + spell(c.b) + ", " + gop + ">";
+  };
+  an->type_str = spell(an->root);
+
+  // ---- output
+  if (out) {
+    an->has_out = true;
+    if (out->dtype != dt) return set_error(COOT_ERR_DTYPE, "out dtype %d differs from the leaves' %d", out->dtype, dt);
+    if (out->n_rows != an->nr || out->n_cols != an->nc)
+      return set_error(COOT_ERR_SHAPE, "out is %lldx%lld, the tree is %lldx%lld", (long long)out->n_rows,
+                       (long long)out->n_cols, (long long)an->nr, (long long)an->nc);
+    if (!mat_shape_ok(*out)) return set_error(COOT_ERR_INVALID, "out: bad ld");
+    if (!out->data && an->nr * an->nc > 0) return set_error(COOT_ERR_INVALID, "out: NULL data");
+    // aliasing: overlap with a leaf view is allowed only for an identical,
+    // untransposed read (each element is read and written by one thread)
+    uintptr_t olo, ohi;
+    view_range(*out, 0, 0, an->nr, an->nc, an->esz, &olo, &ohi);
+    for (const Slot& s : an->slots) {
+      const coot_mat& L = leaves[s.leaf];
+      int64_t vr = s.trans ? s.vr : s.vr, vc = s.vc;
+      uintptr_t llo, lhi;
+      view_range(L, s.r0, s.c0, vr, vc, an->esz, &llo, &lhi);
+      if (olo < lhi && llo < ohi) {
+        uintptr_t vorig = (uintptr_t)L.data + (uintptr_t)((s.r0 + s.c0 * mat_ld(L)) * an->esz);
+        bool same = !s.trans && vorig == (uintptr_t)out->data && s.vr == an->nr && s.vc == an->nc &&
+                    (an->nc <= 1 || mat_ld(L) == mat_ld(*out));
+        if (!same)
+          return set_error(COOT_ERR_ALIAS,
+                           "out overlaps leaf %d through a %s read; only an identical untransposed read may alias",
+                           s.leaf, s.trans ? "transposed" : "differently shaped");
+      }
+    }
+  }
+  return COOT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// kernel choice
+// ---------------------------------------------------------------------------
+Choice choose(const Analysis& an, const coot_mat* leaves, const coot_mat* out) {
+  Choice ch;
+  ch.it_rows = an.nr;
+  ch.it_cols = an.nc;
+  if (an.any_trans) {
+    ch.fam = F_TILE;
+    return ch;
+  }
+  const int dim = an.red.dim;
+  const bool sumlike = (an.red.kind == COOT_R_SUM || an.red.kind == COOT_R_MEAN);
+  if (sumlike && dim == 0)
+    ch.fam = F_COL;
+  else if (sumlike && dim == 1)
+    ch.fam = F_ROW;
+  else
+    ch.fam = F_STR;
+  // contiguity of every read and of the output
+  bool contig = true;
+  for (const Slot& s : an.slots) {
+    const coot_mat& L = leaves[s.leaf];
+    if (s.vc > 1 && mat_ld(L) != s.vr) contig = false;
+  }
+  if (out && an.nc > 1 && mat_ld(*out) != an.nr) contig = false;
+  if (ch.fam == F_STR && contig) {
+    ch.collapsed = true;
+    ch.it_rows = an.nr * an.nc;
+    ch.it_cols = (ch.it_rows > 0) ? 1 : 0;
+  }
+  // 16-byte alignment of every column start
+  bool vec = true;
+  for (const Slot& s : an.slots) {
+    const coot_mat& L = leaves[s.leaf];
+    uintptr_t org = (uintptr_t)L.data + (uintptr_t)((s.r0 + s.c0 * mat_ld(L)) * an.esz);
+    if (org % 16) vec = false;
+    if (!ch.collapsed && s.vc > 1 && (mat_ld(L) * an.esz) % 16) vec = false;
+  }
+  if (out) {
+    if ((uintptr_t)out->data % 16) vec = false;
+    if (!ch.collapsed && an.nc > 1 && (mat_ld(*out) * an.esz) % 16) vec = false;
+  }
+  ch.vec_ok = vec;
+  return ch;
+}
+
+// ---------------------------------------------------------------------------
+// code generation
+// ---------------------------------------------------------------------------
+static int vmax(const Analysis& an) { return 16 / an.esz; }
+
+Program make_program(const Analysis& an, Family fam, bool var_two_pass) {
+  Program pg;
+  const std::string S = storage_type_name(an.dtype);
+  const int NS = (int)an.slots.size(), NK = (int)an.scalars.size();
+  const bool OUT = an.has_out;
+  const int V = vmax(an);
+  std::ostringstream src, sig;
+  src << "#include \"coot_kernels.cuh\"\nusing namespace coot;\n";
+  src << "typedef " << S << " S_t;\n";
+  src << "typedef " << an.type_str << " T_t;\n";
+  auto wrap = [&](const std::string& name, int bound, const std::string& body, const char* ptype = "Params") {
+    src << "extern \"C\" __global__ void __launch_bounds__(" << bound << ") " << name << "(const __grid_constant__ "
+        << ptype << " p) { " << body << "(p); }\n";
+  };
+  auto add = [&](const std::string& name, int vec, int unroll, int block) {
+    KernelSpec k;
+    k.name = name;
+    k.vec = vec;
+    k.unroll = unroll;
+    k.block = block;
+    pg.kernels.push_back(k);
+  };
+  auto red_name = [](int m) {
+    switch (m) {
+      case RED_NONE: return "RED_NONE";
+      case RED_SUM: return "RED_SUM";
+      case RED_DOT: return "RED_DOT";
+      case RED_SSQ: return "RED_SSQ";
+      case RED_MEAN1: return "RED_MEAN1";
+      case RED_CSQ: return "RED_CSQ";
+    }
+    return "RED_NONE";
+  };
+  const char* outs = OUT ? "true" : "false";
+  char buf[512];
+  // (vector width, unroll) variants of the column-walking families; the
+  // scalar variant serves unaligned calls
+  std::vector<std::pair<int, int>> vu = {{V, 1}, {V, 2}, {V, 4}, {1, 4}};
+  if (fam == F_STR) {
+    for (auto [v, u] : vu) {
+      if (var_two_pass) {
+        snprintf(buf, sizeof buf, "coot_str_p1_v%du%d", v, u);
+        wrap(buf, 512, std::string("str_kernel<T_t, S_t, ") + std::to_string(NS) + ", " + std::to_string(NK) +
+                            ", RED_MEAN1, " + std::to_string(v) + ", " + std::to_string(u) + ", false>");
+        add(buf, v, u, 512);
+        snprintf(buf, sizeof buf, "coot_str_p2_v%du%d", v, u);
+        wrap(buf, 512, std::string("str_kernel<T_t, S_t, ") + std::to_string(NS) + ", " + std::to_string(NK) +
+                            ", RED_CSQ, " + std::to_string(v) + ", " + std::to_string(u) + ", " + outs + ">");
+        add(buf, v, u, 512);
+      } else {
+        snprintf(buf, sizeof buf, "coot_str_v%du%d", v, u);
+        wrap(buf, 512, std::string("str_kernel<T_t, S_t, ") + std::to_string(NS) + ", " + std::to_string(NK) + ", " +
+                            red_name(an.red_mode) + ", " + std::to_string(v) + ", " + std::to_string(u) + ", " + outs +
+                            ">");
+        add(buf, v, u, 512);
+      }
+    }
+  } else if (fam == F_COL || fam == F_ROW) {
+    const char* fn = (fam == F_COL) ? "col" : "row";
+    std::vector<std::pair<int, int>> cvu = {{V, 1}, {V, 2}, {1, 4}};
+    for (auto [v, u] : cvu) {
+      snprintf(buf, sizeof buf, "coot_%s_v%du%d", fn, v, u);
+      wrap(buf, 512, std::string(fn) + "_kernel<T_t, S_t, " + std::to_string(NS) + ", " + std::to_string(NK) + ", " +
+                          red_name(an.red_mode) + ", " + std::to_string(v) + ", " + std::to_string(u) + ", " + outs + ">");
+      add(buf, v, u, 512);
+    }
+  } else if (fam == F_TILE) {
+    const int dim = an.red.dim;
+    if (var_two_pass) {
+      wrap("coot_tile_p1", 256, std::string("tile_kernel<T_t, S_t, ") + std::to_string(NS) + ", " + std::to_string(NK) +
+                                    ", RED_MEAN1, -1, " + std::to_string(an.trmask) + ", false>");
+      add("coot_tile_p1", 1, 1, 256);
+      wrap("coot_tile_p2", 256, std::string("tile_kernel<T_t, S_t, ") + std::to_string(NS) + ", " + std::to_string(NK) +
+                                    ", RED_CSQ, -1, " + std::to_string(an.trmask) + ", " + outs + ">");
+      add("coot_tile_p2", 1, 1, 256);
+    } else {
+      wrap("coot_tile", 256, std::string("tile_kernel<T_t, S_t, ") + std::to_string(NS) + ", " + std::to_string(NK) +
+                                 ", " + red_name(an.red_mode) + ", " + std::to_string(dim) + ", " +
+                                 std::to_string(an.trmask) + ", " + outs + ">");
+      add("coot_tile", 1, 1, 256);
+    }
+  } else if (fam == F_ADJ) {
+    std::vector<std::pair<int, int>> avu = {{V, 1}, {V, 2}, {1, 4}};
+    for (auto [v, u] : avu) {
+      snprintf(buf, sizeof buf, "coot_adj_v%du%d", v, u);
+      wrap(buf, 512, std::string("adj_kernel<T_t, S_t, ") + std::to_string(NS) + ", " + std::to_string(NK) + ", " +
+                          std::to_string(v) + ", " + std::to_string(u) + ">");
+      add(buf, v, u, 512);
+    }
+  } else if (fam == F_BATCH) {
+    const bool red = an.red_mode != RED_NONE;
+    wrap("coot_batch", 256,
+         std::string("batch_kernel<T_t, S_t, ") + std::to_string(NS) + ", " + std::to_string(NK) + ", " +
+             std::to_string(an.trmask) + ", " + (red ? "true" : "false") + ">",
+         "BatchParams");
+    add("coot_batch", 1, 1, 256);
+  }
+  sig << "cootgb1|" << family_name(fam) << "|" << S << "|ns" << NS << "|nk" << NK << "|red" << an.red_mode << "|dim"
+      << an.red.dim << "|out" << OUT << "|tr" << an.trmask << "|var" << var_two_pass << "|" << an.type_str;
+  pg.signature = sig.str();
+  pg.source = src.str();
+  return pg;
+}
+
+}  // namespace cg

@@ -1,0 +1,445 @@
+"""Armadillo-style expressions over column-major device matrices.
+
+Mirrors the user API the paper describes (Sec. 2-3): functions and operators
+do not compute anything, they return expression objects; evaluation happens
+when the expression is assigned (``evaluate`` / ``Mat.eval``) or reduced
+(``accu``, ``sum``, ``mean``, ``dot``, ``norm``, ``var``), and then the whole
+tree is handed to the library as one descriptor so it can run as one fused
+kernel.
+
+    import paper_2508_11385_gb300 as coot
+    A, B, C = (coot.Mat(t) for t in (a, b, c))      # column-major torch tensors
+    Y = coot.evaluate(0.5 * A + B % coot.exp(C))     # materialise Y
+    s = coot.accu(coot.square(0.5 * A + B % coot.exp(C))).eval()
+
+``%`` is the element-wise (Schur) product as in Armadillo; ``*`` is defined
+only between a scalar and a matrix (matrix multiplication is not element-wise
+and is not part of this library).
+"""
+from __future__ import annotations
+
+import numbers
+import os
+import threading
+
+import torch
+
+from . import lib as L
+
+_DTYPE = {torch.float32: "f32", torch.float64: "f64", torch.bfloat16: "bf16", torch.float16: "f16",
+          torch.int32: "i32"}
+_TORCH = {v: k for k, v in _DTYPE.items()}
+_ACC = {"f32": torch.float32, "bf16": torch.float32, "f16": torch.float32, "f64": torch.float64,
+        "i32": torch.int64}
+
+
+# ---------------------------------------------------------------------------
+# contexts (one per device, created on first use)
+# ---------------------------------------------------------------------------
+_ctx_lock = threading.Lock()
+_ctxs = {}
+
+
+def context(device=None):
+    """The library context of a CUDA device (kernel caches, workspace)."""
+    if device is None:
+        device = torch.cuda.current_device()
+    if isinstance(device, torch.device):
+        device = device.index if device.index is not None else torch.cuda.current_device()
+    with _ctx_lock:
+        h = _ctxs.get(device)
+        if h is None:
+            flags = 0
+            if os.environ.get("COOT_TUNE", "") in ("1", "on"):
+                flags |= L.CTX_TUNE
+            h = L.coot_ctx_create(device, flags)
+            _ctxs[device] = h
+        return h
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+# ---------------------------------------------------------------------------
+# expression nodes
+# ---------------------------------------------------------------------------
+class Expr:
+    """A node of an expression tree (eOp / eGlue / Op in the paper's terms)."""
+
+    __array_priority__ = 1000
+
+    def __init__(self, op, children=(), k=0.0, view=None):
+        self.op = op
+        self.children = tuple(children)
+        self.k = float(k)
+        self.view = view  # (r0, c0, nr, nc) for N_SUBMAT
+        self._shape = None
+
+    # ---- shape ---------------------------------------------------------
+    @property
+    def shape(self):
+        if self._shape is None:
+            op = self.op
+            if op == L.N_SUBMAT:
+                self._shape = (self.view[2], self.view[3])
+            elif op == L.N_TRANS:
+                r, c = self.children[0].shape
+                self._shape = (c, r)
+            elif L.N_PLUS <= op <= L.N_DIV:
+                sa, sb = self.children[0].shape, self.children[1].shape
+                if sa != sb:
+                    raise ValueError("incompatible matrix dimensions: %dx%d and %dx%d" % (sa + sb))
+                self._shape = sa
+            else:
+                self._shape = self.children[0].shape
+        return self._shape
+
+    @property
+    def n_rows(self):
+        return self.shape[0]
+
+    @property
+    def n_cols(self):
+        return self.shape[1]
+
+    @property
+    def n_elem(self):
+        return self.shape[0] * self.shape[1]
+
+    # ---- operators -----------------------------------------------------
+    def __add__(self, o):
+        if isinstance(o, numbers.Real):
+            return Expr(L.N_SCAL_PLUS, (self,), k=o)
+        return Expr(L.N_PLUS, (self, _as_expr(o)))
+
+    def __radd__(self, o):
+        if isinstance(o, numbers.Real):
+            return Expr(L.N_SCAL_PLUS, (self,), k=o)
+        return Expr(L.N_PLUS, (_as_expr(o), self))
+
+    def __sub__(self, o):
+        if isinstance(o, numbers.Real):
+            return Expr(L.N_SCAL_MINUS_POST, (self,), k=o)
+        return Expr(L.N_MINUS, (self, _as_expr(o)))
+
+    def __rsub__(self, o):
+        if isinstance(o, numbers.Real):
+            return Expr(L.N_SCAL_MINUS_PRE, (self,), k=o)
+        return Expr(L.N_MINUS, (_as_expr(o), self))
+
+    def __mul__(self, o):
+        if isinstance(o, numbers.Real):
+            return Expr(L.N_SCAL_TIMES, (self,), k=o)
+        raise TypeError("matrix * matrix is matrix multiplication, not element-wise; use % for the Schur product")
+
+    def __rmul__(self, o):
+        if isinstance(o, numbers.Real):
+            return Expr(L.N_SCAL_TIMES, (self,), k=o)
+        raise TypeError("matrix * matrix is matrix multiplication, not element-wise; use % for the Schur product")
+
+    def __truediv__(self, o):
+        if isinstance(o, numbers.Real):
+            return Expr(L.N_SCAL_DIV_POST, (self,), k=o)
+        return Expr(L.N_DIV, (self, _as_expr(o)))
+
+    def __rtruediv__(self, o):
+        if isinstance(o, numbers.Real):
+            return Expr(L.N_SCAL_DIV_PRE, (self,), k=o)
+        return Expr(L.N_DIV, (_as_expr(o), self))
+
+    def __mod__(self, o):
+        return Expr(L.N_SCHUR, (self, _as_expr(o)))
+
+    def __rmod__(self, o):
+        return Expr(L.N_SCHUR, (_as_expr(o), self))
+
+    def __neg__(self):
+        return Expr(L.N_NEG, (self,))
+
+    def t(self):
+        return trans(self)
+
+    def eval(self, out=None, fused=True, stream=None):
+        return evaluate(self, out=out, fused=fused, stream=stream)
+
+
+class Mat(Expr):
+    """A column-major matrix in device memory, wrapping a torch tensor.
+
+    The tensor must be 2-D with unit row stride (element (i,j) at
+    data[i + j*ld], ld = t.stride(1)), e.g. ``torch.empty(n_cols, n_rows).t()``,
+    or 1-D (a column vector)."""
+
+    def __init__(self, t: torch.Tensor):
+        super().__init__(L.N_LEAF)
+        if t.dim() == 1:
+            if t.stride(0) != 1 and t.numel() > 1:
+                raise ValueError("1-D tensors must be contiguous")
+            t2 = t.unsqueeze(1)
+            n_rows, n_cols, ld = t.shape[0], 1, max(t.shape[0], 1)
+        elif t.dim() == 2:
+            t2 = t
+            n_rows, n_cols = t.shape
+            if n_rows > 1 and t.stride(0) != 1:
+                raise ValueError("tensor is not column-major (stride(0) must be 1); use t.t().contiguous().t()")
+            ld = t.stride(1) if n_cols > 1 else max(n_rows, 1)
+            if n_cols > 1 and ld < n_rows:
+                raise ValueError("column stride smaller than the number of rows")
+        else:
+            raise ValueError("Mat wraps 1-D or 2-D tensors")
+        if t.dtype not in _DTYPE:
+            raise TypeError("unsupported dtype %s" % t.dtype)
+        if t.device.type != "cuda":
+            raise ValueError("Mat wraps CUDA tensors (device memory); got %s" % t.device)
+        self.tensor = t2
+        self.dtype = _DTYPE[t.dtype]
+        self.ld = int(ld)
+        self._shape = (int(n_rows), int(n_cols))
+
+    def submat(self, first_row, first_col, last_row, last_col):
+        """Armadillo's X.submat(first_row, first_col, last_row, last_col):
+        inclusive last indices."""
+        nr, nc = last_row - first_row + 1, last_col - first_col + 1
+        if first_row < 0 or first_col < 0 or nr < 0 or nc < 0 or last_row >= self.n_rows or last_col >= self.n_cols:
+            raise IndexError("submat: indices out of bounds")
+        return Expr(L.N_SUBMAT, (self,), view=(first_row, first_col, nr, nc))
+
+    def cmat(self):
+        return L.mat(self.tensor.data_ptr(), L.DTYPE_CODE[self.dtype], self.n_rows, self.n_cols, self.ld)
+
+
+def _as_expr(x):
+    if isinstance(x, Expr):
+        return x
+    if isinstance(x, torch.Tensor):
+        return Mat(x)
+    raise TypeError("expected a matrix expression, got %r" % type(x))
+
+
+# element-wise functions (eOp)
+def trans(x):
+    return Expr(L.N_TRANS, (_as_expr(x),))
+
+
+def exp(x):
+    return Expr(L.N_EXP, (_as_expr(x),))
+
+
+def log(x):
+    return Expr(L.N_LOG, (_as_expr(x),))
+
+
+def abs(x):  # noqa: A001 -- Armadillo's name
+    return Expr(L.N_ABS, (_as_expr(x),))
+
+
+def square(x):
+    return Expr(L.N_SQUARE, (_as_expr(x),))
+
+
+def sqrt(x):
+    return Expr(L.N_SQRT, (_as_expr(x),))
+
+
+# ---------------------------------------------------------------------------
+# lowering to the C descriptor
+# ---------------------------------------------------------------------------
+def lower(expr: Expr):
+    """(coot_tree, [leaf Mat], [coot_mat]) of an expression; shared
+    sub-expressions stay shared (the node list is a DAG)."""
+    nodes, memo, leaves, leaf_idx = [], {}, [], {}
+
+    def visit(e):
+        key = id(e)
+        if key in memo:
+            return memo[key]
+        if e.op == L.N_LEAF:
+            lk = (e.tensor.data_ptr(), e.shape, e.ld, e.dtype)
+            if lk not in leaf_idx:
+                leaf_idx[lk] = len(leaves)
+                leaves.append(e)
+            nodes.append(L.node(L.N_LEAF, leaf=leaf_idx[lk]))
+        elif e.op == L.N_SUBMAT:
+            a = visit(e.children[0])
+            r0, c0, nr, nc = e.view
+            nodes.append(L.node(L.N_SUBMAT, a=a, r0=r0, c0=c0, nr=nr, nc=nc))
+        elif L.N_PLUS <= e.op <= L.N_DIV:
+            a = visit(e.children[0])
+            b = visit(e.children[1])
+            nodes.append(L.node(e.op, a=a, b=b))
+        else:
+            a = visit(e.children[0])
+            nodes.append(L.node(e.op, a=a, k=e.k))
+        memo[key] = len(nodes) - 1
+        return memo[key]
+
+    visit(expr)
+    if len(nodes) > L.MAX_NODES:
+        raise ValueError("expression has %d nodes; at most %d" % (len(nodes), L.MAX_NODES))
+    dtypes = {m.dtype for m in leaves}
+    if len(dtypes) != 1:
+        raise TypeError("all matrices of an expression must share one dtype (got %s)" % sorted(dtypes))
+    return L.make_tree(nodes), leaves, [m.cmat() for m in leaves]
+
+
+def _empty_colmajor(n_rows, n_cols, dtype, device):
+    return torch.empty((n_cols, n_rows), dtype=_TORCH[dtype], device=device).t()
+
+
+class Reduction:
+    """A reduction of an expression; evaluated by ``eval()`` (fused with the
+    expression), or combined linearly first: ``accu(a) + k * accu(b)`` is
+    evaluated as ``accu(a + k * b)`` in one pass."""
+
+    def __init__(self, kind, expr, dim=-1, norm_type=0):
+        self.kind, self.expr, self.dim, self.norm_type = kind, expr, dim, norm_type
+
+    def _linear(self):
+        return self.kind in (L.R_ACCU, L.R_SUM) and self.dim == -1
+
+    def __add__(self, o):
+        if isinstance(o, Reduction) and self._linear() and o._linear() and self.expr.shape == o.expr.shape:
+            return Reduction(L.R_ACCU, self.expr + o.expr)
+        return NotImplemented
+
+    def __sub__(self, o):
+        if isinstance(o, Reduction) and self._linear() and o._linear() and self.expr.shape == o.expr.shape:
+            return Reduction(L.R_ACCU, self.expr - o.expr)
+        return NotImplemented
+
+    def __mul__(self, k):
+        if isinstance(k, numbers.Real) and self._linear():
+            return Reduction(L.R_ACCU, k * self.expr)
+        return NotImplemented
+
+    __rmul__ = __mul__
+
+    def eval(self, out=None, fused=True, stream=None):
+        _, r = evaluate(self.expr, reduction=self, fused=fused, stream=stream, materialise=out)
+        return r
+
+    def __float__(self):
+        return float(self.eval().item())
+
+
+def accu(x):
+    return Reduction(L.R_ACCU, _as_expr(x))
+
+
+def sum(x, dim=None):  # noqa: A001 -- Armadillo's name
+    """Armadillo sum: along dim 0 (per column) for a matrix by default, all
+    elements for a vector; dim=-1 sums everything."""
+    x = _as_expr(x)
+    if dim is None:
+        dim = -1 if (x.n_rows == 1 or x.n_cols == 1) else 0
+    return Reduction(L.R_SUM, x, dim)
+
+
+def mean(x, dim=None):
+    x = _as_expr(x)
+    if dim is None:
+        dim = -1 if (x.n_rows == 1 or x.n_cols == 1) else 0
+    return Reduction(L.R_MEAN, x, dim)
+
+
+def dot(a, b):
+    return Reduction(L.R_DOT, Expr(L.N_SCHUR, (_as_expr(a), _as_expr(b))))
+
+
+def norm(x, p=2):
+    x = _as_expr(x)
+    if p == "fro":
+        return Reduction(L.R_NORM_FRO, x)
+    if p != 2:
+        raise ValueError("norm: p = 2 (vectors) or 'fro'")
+    if x.n_rows != 1 and x.n_cols != 1:
+        raise ValueError("norm(X) of a matrix is the spectral norm, which this library does not compute; "
+                         "use norm(X, 'fro')")
+    return Reduction(L.R_NORM2, x)
+
+
+def var(x, norm_type=0):
+    """Two-pass variance over all elements (norm_type 0: N-1, 1: N)."""
+    return Reduction(L.R_VAR, _as_expr(x), -1, norm_type)
+
+
+# ---------------------------------------------------------------------------
+# evaluation
+# ---------------------------------------------------------------------------
+def evaluate(expr, out=None, reduction=None, red_out=None, fused=True, stream=None, materialise=None):
+    """Evaluate ``expr`` (delayed evaluation on assignment).
+
+    * ``out``: a column-major tensor to receive Y (allocated when None and no
+      reduction is requested, or when ``materialise`` is True);
+    * ``reduction``: a Reduction (or None) fused onto the same pass; its
+      result is returned as a tensor of the accumulation dtype (0-d for a
+      scalar, column-major 1 x n_cols / n_rows x 1 for dim 0 / 1).
+    Returns Y (a tensor) when there is no reduction, else (Y or None, result).
+    """
+    expr = _as_expr(expr)
+    tree, leaves, cmats = lower(expr)
+    dt = leaves[0].dtype
+    dev = leaves[0].tensor.device
+    nr, nc = expr.shape
+    want_y = out is not None or reduction is None or materialise is True
+    if isinstance(materialise, torch.Tensor):
+        out = materialise
+    if want_y and out is None:
+        out = _empty_colmajor(nr, nc, dt, dev)
+    out_m = Mat(out).cmat() if out is not None else None
+    red = L.reduce()
+    rt = None
+    if reduction is not None:
+        red = L.reduce(reduction.kind, reduction.dim, reduction.norm_type)
+        if red_out is None:
+            acc = _ACC[dt]
+            if reduction.dim == 0 and reduction.kind in (L.R_SUM, L.R_MEAN):
+                rt = torch.empty((1, nc), dtype=acc, device=dev)  # a row vector: contiguous either way
+            elif reduction.dim == 1 and reduction.kind in (L.R_SUM, L.R_MEAN):
+                rt = torch.empty((nr, 1), dtype=acc, device=dev)
+            else:
+                rt = torch.empty((), dtype=acc, device=dev)
+        else:
+            rt = red_out
+    with torch.cuda.device(dev):
+        ctx = context(dev)
+        s = _stream_ptr(stream)
+        fn = L.coot_eval if fused else L.coot_eval_unfused
+        fn(ctx, tree, cmats, out_m, red, rt.data_ptr() if rt is not None else None, s)
+    if reduction is None:
+        return out
+    return out, rt
+
+
+def warmup(expr, reduction=None, out=None):
+    """JIT-compile (and tune, when enabled) the kernel of an evaluation."""
+    expr = _as_expr(expr)
+    tree, leaves, cmats = lower(expr)
+    red = L.reduce() if reduction is None else L.reduce(reduction.kind, reduction.dim, reduction.norm_type)
+    out_m = Mat(out).cmat() if out is not None else None
+    dev = leaves[0].tensor.device
+    with torch.cuda.device(dev):
+        L.coot_warmup(context(dev), tree, cmats, out_m, red)
+
+
+def signature(expr, reduction=None, out=None) -> str:
+    expr = _as_expr(expr)
+    tree, leaves, cmats = lower(expr)
+    red = L.reduce() if reduction is None else L.reduce(reduction.kind, reduction.dim, reduction.norm_type)
+    out_m = Mat(out).cmat() if out is not None else None
+    return L.coot_signature(tree, cmats, out_m, red)
+
+
+def last_launch(device=None) -> dict:
+    return L.coot_last_launch(context(device))
+
+
+def check_device_flag(device=None, stream=None) -> int:
+    return L.coot_check_device_flag(context(device), _stream_ptr(stream))
+
+
+__all__ = ["Mat", "Expr", "Reduction", "trans", "exp", "log", "abs", "square", "sqrt", "accu", "sum", "mean",
+           "dot", "norm", "var", "evaluate", "warmup", "signature", "context", "last_launch", "check_device_flag",
+           "lower"]
