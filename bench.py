@@ -1,0 +1,771 @@
+#!/usr/bin/env python
+"""Benchmark: fused expression-tree evaluation on GB300, effective HBM GB/s.
+
+Workload (one "step"): the large memory-bound trees on FP32 8192 x 8192
+column-major matrices A..F drawn normal(0,1) -- the six tree shapes
+  2*A+B,  A%B+C,  trans(A)+B,  exp(A-B)/(1+abs(C)),  sum(square(A-B),0),
+  accu(A.submat(1000,1000,5095,5095))
+and the depth ladder
+  L4 = exp(A-B)/(1+abs(C)) % D, L5 = L4 - E, L6 = abs(L5), L7 = sqrt(L6),
+  L8 = L7 % F
+each evaluated once by one fused kernel.  value = sum of algorithmic bytes
+(distinct operand bytes read + bytes written) / device time of the step.
+
+Besides the headline line the JSON carries: the unfused one-kernel-per-op
+path on the same trees (GB/s and the speed-up per tree), FP64 and INT32
+variants, the batched workload (exprs/s), the CUDA-graph chain, the fused
+adjoint, the roofline of the dominant kernel against the measured HBM copy
+peak, SM clocks sampled during the timed region, an end-to-end number through
+host buffers, and the FP64 CPU oracle timed on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fused-expr effective HBM GB/s (fraction of peak) vs unfused per-op; batched exprs/s"
+N_MAIN = 8192
+FALLBACK_HBM = 6800.0
+
+# (name, RPN program over A..F, depth) -- the config-2 shapes and the ladder
+TREES = [
+    ("axpy", "#2 A * B +", 2),
+    ("schur_plus", "A B % C +", 2),
+    ("trans_plus", "A trans B +", 2),
+    ("exp_div", "A B - exp #1 C abs + /", 4),
+    ("colsum_sq", "A B - square sum:0", 3),
+    ("accu_submat", "A submat:1000:1000:4096:4096 accu", 2),
+    ("L4", "A B - exp #1 C abs + / D %", 5),
+    ("L5", "A B - exp #1 C abs + / D % E -", 6),
+    ("L6", "A B - exp #1 C abs + / D % E - abs", 7),
+    ("L7", "A B - exp #1 C abs + / D % E - abs sqrt", 8),
+    ("L8", "A B - exp #1 C abs + / D % E - abs sqrt F %", 9),
+]
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured", d
+    except Exception:
+        return FALLBACK_HBM, "fallback", {}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def reduce_max(x, world, device=None):
+    """max over ranks (replicas: a barrier and a max of the timings only)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(per_rank_units, per_rank_seconds):
+    """Whole-job throughput of independent replicas: all units over the
+    slowest rank's time."""
+    return sum(per_rank_units) / max(per_rank_seconds)
+
+
+# ---------------------------------------------------------------------------
+# the program-string front end used by the bench (same trees as the tests)
+# ---------------------------------------------------------------------------
+def build_expr(program, mats):
+    import paper_2508_11385_gb300 as coot
+
+    st, red = [], None
+    for tok in program.split():
+        if len(tok) == 1 and "A" <= tok <= "H":
+            st.append(mats[ord(tok) - ord("A")])
+        elif tok.startswith("#"):
+            st.append(float(tok[1:]))
+        elif tok in ("+", "-", "%", "/", "*"):
+            y, x = st.pop(), st.pop()
+            st.append({"+": lambda a, b: a + b, "-": lambda a, b: a - b, "%": lambda a, b: a % b,
+                       "/": lambda a, b: a / b, "*": lambda a, b: a * b}[tok](x, y))
+        elif tok in ("exp", "log", "abs", "square", "sqrt", "trans"):
+            st.append(getattr(coot, tok)(st.pop()))
+        elif tok == "neg":
+            st.append(-st.pop())
+        elif tok.startswith("submat:"):
+            r0, c0, nr, nc = map(int, tok.split(":")[1:])
+            st.append(st.pop().submat(r0, c0, r0 + nr - 1, c0 + nc - 1))
+        elif tok == "accu":
+            red = coot.accu(st[-1])
+        elif tok == "sum:0":
+            red = coot.sum(st[-1], 0)
+        elif tok == "sum:1":
+            red = coot.sum(st[-1], 1)
+        else:
+            raise ValueError(tok)
+    return st[-1], red
+
+
+class Call:
+    """A prepared C-ABI call: descriptor, leaf matrices, output, reduction."""
+
+    def __init__(self, program, tensors, fused=True, ctx=None):
+        import torch
+
+        import paper_2508_11385_gb300 as coot
+        from paper_2508_11385_gb300 import expr as E
+        from paper_2508_11385_gb300 import lib as L
+
+        self.L, self.coot = L, coot
+        mats = [coot.Mat(t) for t in tensors]
+        e, red = build_expr(program, mats)
+        self.tree, self.leaf_mats, self.cmats = E.lower(e)
+        self.fused = fused
+        nr, nc = e.shape
+        dt = self.leaf_mats[0].dtype
+        dev = tensors[0].device
+        if red is None:
+            self.out_t = torch.empty((nc, nr), dtype=tensors[0].dtype, device=dev).t()
+            self.out_m = coot.Mat(self.out_t).cmat()
+            self.red = L.reduce()
+            self.red_t = None
+        else:
+            self.out_t, self.out_m = None, None
+            self.red = L.reduce(red.kind, red.dim, red.norm_type)
+            acc = E._ACC[dt]
+            if red.dim == 0:
+                self.red_t = torch.empty((1, nc), dtype=acc, device=dev)
+            elif red.dim == 1:
+                self.red_t = torch.empty((nr, 1), dtype=acc, device=dev)
+            else:
+                self.red_t = torch.empty((), dtype=acc, device=dev)
+        self.ctx = E.context(dev) if ctx is None else ctx
+        self.red_ptr = self.red_t.data_ptr() if self.red_t is not None else None
+        self.fn = L.coot_eval if fused else L.coot_eval_unfused
+        self.leaf_tensors = [m.tensor for m in self.leaf_mats]
+
+    def __call__(self, stream_ptr):
+        self.fn(self.ctx, self.tree, self.cmats, self.out_m, self.red, self.red_ptr, stream_ptr)
+
+    def info(self):
+        return self.L.coot_last_launch(self.ctx)
+
+    def result(self):
+        return self.out_t if self.red_t is None else self.red_t
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded sample
+# ---------------------------------------------------------------------------
+def cpu_baseline(n=2048, budget_s=20.0):
+    import numpy as np
+
+    import oracle
+    from paper_2508_11385_gb300 import workloads
+
+    oracle.build()
+    leaves = workloads.large_trees("f32", n=n, device="cpu")
+    host = [workloads.to_numpy_colmajor(t) for t in leaves]
+    scale = n / N_MAIN
+    done_bytes, t_total, evals = 0, 0.0, 0
+    t_start = time.perf_counter()
+    while time.perf_counter() - t_start < budget_s:
+        for name, prog, _ in TREES:
+            p = prog.replace("submat:1000:1000:4096:4096",
+                             "submat:%d:%d:%d:%d" % (int(1000 * scale), int(1000 * scale),
+                                                    int(4096 * scale), int(4096 * scale)))
+            t0 = time.perf_counter()
+            oracle.evaluate(p, host, "f32")
+            t_total += time.perf_counter() - t0
+            done_bytes += algorithmic_bytes(p, n, 4)
+            evals += 1
+        if evals >= len(TREES) and time.perf_counter() - t_start > budget_s * 0.5:
+            break
+    return {"value": done_bytes / t_total / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": "the %d trees of the workload at %dx%d FP32 (1/%d of the elements), %d evaluations, "
+                      "single-threaded C FP64 oracle, %.1f s" % (len(TREES), n, n, int(1 / scale ** 2), evals,
+                                                                   t_total)}
+
+
+def algorithmic_bytes(program, n, esz):
+    """distinct operand bytes read + bytes written, for the workload's programs"""
+    toks = program.split()
+    leaves = {t for t in toks if len(t) == 1 and "A" <= t <= "H"}
+    if any(t.startswith("submat:") for t in toks):
+        nr, nc = [int(x) for x in [t for t in toks if t.startswith("submat:")][0].split(":")[3:5]]
+        return nr * nc * esz + 4
+    b = len(leaves) * n * n * esz
+    if toks[-1] == "sum:0":
+        return b + n * 4
+    if toks[-1] == "accu":
+        return b + 4
+    return b + n * n * esz
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2508_11385_gb300 import lib as L
+    from paper_2508_11385_gb300 import workloads
+
+    os.environ.setdefault("COOT_TUNE", "on")
+    n = args.n
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    leaves = workloads.large_trees("f32", n=n, device=dev)
+    calls = [(name, prog, depth, Call(prog, leaves, True)) for name, prog, depth in TREES]
+    # warm the JIT and tuning caches (excluded from timing, as the paper's startup is)
+    for _, _, _, c in calls:
+        c(sp)
+    torch.cuda.synchronize()
+    bytes_per = {}
+    launches_per_step = 0
+    for name, _, _, c in calls:
+        c(sp)
+        info = c.info()
+        bytes_per[name] = info["algorithmic_bytes"]
+    torch.cuda.synchronize()
+    for name, _, _, c in calls:
+        c(sp)
+        launches_per_step += c.info()["n_launches"]
+    torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        for _, _, _, c in calls:
+            c(sp)
+    torch.cuda.synchronize()
+
+    # timed region: K steps, events around every tree's launch on its stream
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in calls]
+          for _ in range(args.steps)]
+    clock = ClockSampler(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+    torch.cuda.synchronize()
+    clock.start()
+    time.sleep(0.3)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k in range(args.steps):
+        for i, (_, _, _, c) in enumerate(calls):
+            ev[k][i][0].record(stream)
+            c(sp)
+            ev[k][i][1].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clock.stop()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+    total_ms = t0.elapsed_time(t1)
+    total_ms = reduce_max(total_ms, world, dev)
+    step_bytes = sum(bytes_per.values())
+    per_tree_ms = {name: statistics.median(ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(args.steps))
+                   for i, (name, _, _, _) in enumerate(calls)}
+    value = world * step_bytes * args.steps / (total_ms / 1e3) / 1e9
+    peak, peak_kind, peaks = load_peaks()
+
+    # dominant kernel: largest share of the step
+    dom = max(per_tree_ms, key=per_tree_ms.get)
+    dom_call = [c for name, _, _, c in calls if name == dom][0]
+    dom_call(sp)
+    torch.cuda.synchronize()
+    dom_info = dom_call.info()
+    achieved = bytes_per[dom] / (per_tree_ms[dom] / 1e3) / 1e9
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tr_path):
+        try:
+            tr = json.load(open(tr_path))
+            ent = tr.get(dom)
+            if ent and ent.get("headers_sha") == headers_sha():
+                traffic = ent["dram_bytes_per_launch"]
+        except Exception:
+            traffic = None
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": dom_info["kernel"],
+                "tree": dom, "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                else "fallback 6.8 TB/s"}
+
+    extras = {}
+    if rank == 0 and not args.quick:
+        extras = run_extras(args, leaves, calls, per_tree_ms, bytes_per, dev, stream, peak)
+
+    # end to end through host buffers: H2D of each tree's operands, eval, D2H of its result
+    e2e = run_e2e(calls, leaves, stream, max(2, min(args.steps, 5)), dev) if rank == 0 else None
+
+    out = {
+        "metric": METRIC,
+        "value": round(value, 1),
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(total_ms / args.steps, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded normal(0,1) FP32 matrices generated on the device)",
+        "config": {"workload": "large memory-bound trees, FP32 %dx%d A..F: 6 shapes + depth ladder L4-L8" % (n, n),
+                   "trees": [t[0] for t in TREES], "l2": "inputs larger than L2 (each operand %d MiB)" %
+                   (n * n * 4 >> 20), "parallelism": "replicas" if world > 1 else "single GPU"},
+        "frac_of_peak": round(value / world / peak, 4),
+        "peak_gbs": peak,
+        "roofline": roofline,
+        "per_tree": {name: {"ms": round(per_tree_ms[name], 4), "gbs": round(bytes_per[name] / per_tree_ms[name] / 1e6, 1),
+                            "bytes": bytes_per[name]} for name in per_tree_ms},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+        "e2e": e2e,
+    }
+    out.update(extras)
+    if rank == 0 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(budget_s=args.cpu_budget)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def headers_sha():
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2508_11385_gb300", "csrc", "dev", "*"))):
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def time_calls(fn, stream, reps=10, warm=2):
+    import torch
+
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def run_e2e(calls, leaves, stream, reps, dev):
+    import torch
+
+    host = [t.cpu().pin_memory() for t in leaves]  # same column-major layout: (n,n) transposed views
+    # pinned outputs per tree
+    h_out = {}
+    for name, _, _, c in calls:
+        r = c.result()
+        h_out[name] = torch.empty(r.shape, dtype=r.dtype).pin_memory() if r.dim() else torch.empty((), dtype=r.dtype).pin_memory()
+    bytes_alg = 0
+    h2d = d2h = 0
+    sp = stream.cuda_stream
+    name_to_leaf = {}
+    for name, prog, _, c in calls:
+        used = sorted({t for t in prog.split() if len(t) == 1 and "A" <= t <= "H"})
+        name_to_leaf[name] = [ord(t) - ord("A") for t in used]
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        for name, _, _, c in calls:
+            for li in name_to_leaf[name]:
+                leaves[li].copy_(host[li], non_blocking=True)
+                h2d += host[li].numel() * host[li].element_size()
+            c(sp)
+            r = c.result()
+            h_out[name].copy_(r, non_blocking=True)
+            d2h += r.numel() * r.element_size()
+            bytes_alg += c.info()["algorithmic_bytes"]
+    b.record(stream)
+    torch.cuda.synchronize()
+    sec = a.elapsed_time(b) / 1e3
+    return {"value": round(bytes_alg / sec / 1e9, 1), "unit": "GB/s", "h2d_bytes_per_step": h2d // reps,
+            "d2h_bytes_per_step": d2h // reps, "steps": reps,
+            "note": "per tree: pinned host->device copy of its operands, the fused call, device->host copy of Y or "
+                    "the reduction; value = algorithmic bytes / wall time on the stream"}
+
+
+def run_extras(args, leaves, calls, per_tree_ms, bytes_per, dev, stream, peak):
+    import torch
+
+    import paper_2508_11385_gb300 as coot
+    from paper_2508_11385_gb300 import lib as L
+    from paper_2508_11385_gb300 import workloads
+
+    sp = stream.cuda_stream
+    res = {}
+    # ---- unfused per-op baseline on the same trees
+    unf = {}
+    for name, prog, depth, _ in calls:
+        c = Call(prog, leaves, fused=False)
+        ms = time_calls(lambda: c(sp), stream, reps=max(5, args.steps // 4))
+        unf[name] = {"ms": round(ms, 4), "gbs": round(bytes_per[name] / ms / 1e6, 1),
+                     "speedup_fused": round(ms / per_tree_ms[name], 2), "depth": depth}
+    deep = [unf[n]["speedup_fused"] for n, _, d, _ in calls if d >= 4]
+    res["unfused"] = {"per_tree": unf, "geomean_speedup_depth_ge4": round(math.exp(sum(map(math.log, deep)) / len(deep)), 2),
+                      "min_speedup_depth_ge4": min(deep)}
+    # ---- FP64 / INT32 variants of the six shapes
+    del_names = ["axpy", "schur_plus", "trans_plus", "exp_div", "colsum_sq", "accu_submat"]
+    for dt in ("f64", "i32"):
+        lv = workloads.large_trees(dt, n=args.n, n_leaves=3, device=dev)
+        d = {}
+        for name, prog, _, _ in calls:
+            if name not in del_names or (dt == "i32" and "exp" in prog):
+                continue
+            c = Call(prog, lv, fused=True)
+            c(sp)
+            torch.cuda.synchronize()
+            ms = time_calls(lambda: c(sp), stream, reps=5)
+            b = c.info()["algorithmic_bytes"]
+            cu = Call(prog, lv, fused=False)
+            msu = time_calls(lambda: cu(sp), stream, reps=3)
+            d[name] = {"ms": round(ms, 4), "gbs": round(b / ms / 1e6, 1), "unfused_ms": round(msu, 4)}
+        res[dt] = d
+        del lv
+        torch.cuda.empty_cache()
+    # ---- batched: 50,000 problems, Y = A % B + 0.1*trans(C), accu(Y)
+    try:
+        res["batched"] = bench_batched(args, dev, stream)
+    except Exception as e:  # reported, not hidden
+        res["batched"] = {"error": repr(e)[:300]}
+    torch.cuda.empty_cache()
+    try:
+        res["graph_chain"] = bench_graph(dev, stream)
+    except Exception as e:
+        res["graph_chain"] = {"error": repr(e)[:300]}
+    try:
+        res["adjoint"] = bench_adjoint(dev, stream)
+    except Exception as e:
+        res["adjoint"] = {"error": repr(e)[:300]}
+    try:
+        res["precision"] = bench_precision(dev, stream)
+    except Exception as e:
+        res["precision"] = {"error": repr(e)[:300]}
+    return res
+
+
+def bench_batched(args, dev, stream):
+    import torch
+
+    import paper_2508_11385_gb300 as coot
+    from paper_2508_11385_gb300 import lib as L
+    from paper_2508_11385_gb300 import workloads
+    from paper_2508_11385_gb300.expr import context
+
+    npb = args.batch_problems
+    rows, cols, A, B, C, pools = workloads.batching(npb, device=dev)
+    outs = [torch.empty((c, r), dtype=torch.float32, device=dev).t() for r, c in zip(rows.tolist(), cols.tolist())]
+    nodes = [L.node(L.N_LEAF, leaf=0), L.node(L.N_LEAF, leaf=1), L.node(L.N_SCHUR, a=0, b=1),
+             L.node(L.N_LEAF, leaf=2), L.node(L.N_TRANS, a=3), L.node(L.N_SCAL_TIMES, a=4, k=0.1),
+             L.node(L.N_PLUS, a=2, b=5)]
+    tree = L.make_tree(nodes)
+    probs = (L.coot_mat * (3 * npb))()
+    for q in range(npb):
+        probs[3 * q] = coot.Mat(A[q]).cmat()
+        probs[3 * q + 1] = coot.Mat(B[q]).cmat()
+        probs[3 * q + 2] = coot.Mat(C[q]).cmat()
+    outm = (L.coot_mat * npb)(*[coot.Mat(o).cmat() for o in outs])
+    red_out = torch.empty(npb, dtype=torch.float32, device=dev)
+    ctx = context(dev)
+    t0 = time.perf_counter()
+    plan = L.coot_batch_create(ctx, tree, npb, 3, probs, outm, L.reduce(L.R_ACCU))
+    plan_s = time.perf_counter() - t0
+    sp = stream.cuda_stream
+    ms = time_calls(lambda: L.coot_batch_run(plan, red_out.data_ptr(), sp), stream, reps=10)
+    info = L.coot_last_launch(ctx)
+    # 50,000 separate fused launches of the same tree (first 2,000 timed, scaled)
+    nsep = min(npb, 2000)
+    sep = []
+    for q in range(nsep):
+        cm = [probs[3 * q], probs[3 * q + 1], probs[3 * q + 2]]
+        sep.append((cm, outm[q]))
+    r1 = torch.empty((), dtype=torch.float32, device=dev)
+
+    def separate():
+        for cm, om in sep:
+            L.coot_eval(ctx, tree, cm, om, L.reduce(L.R_ACCU), r1.data_ptr(), sp)
+
+    sep_ms = time_calls(separate, stream, reps=3, warm=1) * npb / nsep
+    L.coot_batch_destroy(plan)
+    total_elems = int((rows * cols).sum())
+    return {"n_problems": npb, "elements": total_elems, "ms": round(ms, 4),
+            "exprs_per_s": round(npb / (ms / 1e3), 1), "gbs": round(info["algorithmic_bytes"] / ms / 1e6, 1),
+            "algorithmic_bytes": info["algorithmic_bytes"], "plan_create_s": round(plan_s, 3),
+            "separate_launches_ms": round(sep_ms, 2), "separate_exprs_per_s": round(npb / (sep_ms / 1e3), 1),
+            "speedup_vs_separate": round(sep_ms / ms, 2)}
+
+
+def bench_graph(dev, stream):
+    import torch
+
+    import paper_2508_11385_gb300 as coot
+    from paper_2508_11385_gb300 import lib as L
+    from paper_2508_11385_gb300 import workloads
+    from paper_2508_11385_gb300.expr import context
+
+    A, B, C = workloads.graph_chain(device=dev)
+    n = A.shape[0]
+    s = torch.cuda.Stream(device=dev)
+    X = [torch.empty((n, n), dtype=torch.float32, device=dev).t() for _ in range(21)]
+    X[0].copy_(A)
+    shapes = ["#2 X * B +", "X B % C +", "X trans B +", "X B - exp #1 C abs + /", "X B - square", "X"]
+    reds = [None, None, None, None, "sum:0", "accu"]
+    side = torch.empty((1, n), dtype=torch.float32, device=dev)
+    scal = torch.empty((), dtype=torch.float32, device=dev)
+    calls = []
+    for k in range(20):
+        j = k % 6
+        prog = shapes[j].replace("X", "A")
+        ten = [X[k], B, C]
+        mats = [coot.Mat(t) for t in ten]
+        if j == 5:  # accu over the square 2048x2048 view (the whole matrix), X passes through
+            e = mats[0].submat(0, 0, n - 1, n - 1)
+            tree, lm, cm = coot.lower(e)
+            calls.append((tree, cm, coot.Mat(X[k + 1]).cmat(), L.reduce(L.R_ACCU), scal.data_ptr()))
+            continue
+        e, _ = build_expr(prog, mats)
+        tree, lm, cm = coot.lower(e)
+        red = L.reduce(L.R_SUM, 0) if reds[j] == "sum:0" else L.reduce()
+        calls.append((tree, cm, coot.Mat(X[k + 1]).cmat(), red, side.data_ptr() if reds[j] else None))
+    ctx = context(dev)
+
+    def eager(fn=L.coot_eval):
+        for tree, cm, om, red, rp in calls:
+            fn(ctx, tree, cm, om, red, rp, s.cuda_stream)
+
+    eager()
+    torch.cuda.synchronize()
+    L.coot_graph_begin(ctx, s.cuda_stream)
+    eager()
+    g = L.coot_graph_end(ctx, s.cuda_stream)
+    ms_graph = time_calls(lambda: L.coot_graph_launch(g, s.cuda_stream), s, reps=20)
+    ms_eager = time_calls(eager, s, reps=20)
+    ms_unfused = time_calls(lambda: eager(L.coot_eval_unfused), s, reps=5)
+    L.coot_graph_destroy(g)
+    return {"evals": 20, "n": n, "graph_ms": round(ms_graph, 4), "eager_ms": round(ms_eager, 4),
+            "unfused_ms": round(ms_unfused, 4), "graph_exprs_per_s": round(20 / (ms_graph / 1e3), 1),
+            "eager_exprs_per_s": round(20 / (ms_eager / 1e3), 1),
+            "unfused_exprs_per_s": round(20 / (ms_unfused / 1e3), 1),
+            "note": "2048^2 FP32 operands (16 MiB) are L2-resident across the chain"}
+
+
+def bench_adjoint(dev, stream):
+    import torch
+
+    from paper_2508_11385_gb300 import autograd as AG
+    from paper_2508_11385_gb300 import workloads
+
+    W, X, Y = workloads.differentiation(device=dev)
+    Wp = W.clone().requires_grad_(True)
+    Xp = X.clone().requires_grad_(True)
+
+    def fused():
+        loss = AG.loss_l2_schur(Wp, Xp, Y, 1e-3)
+        loss.backward()
+        return loss
+
+    def torch_ref():
+        W2 = W.clone().requires_grad_(True)
+        X2 = X.clone().requires_grad_(True)
+        loss = ((W2 * X2 - Y) ** 2).sum() + 1e-3 * (W2 ** 2).sum()
+        loss.backward()
+
+    ms_f = time_calls(fused, stream, reps=10)
+    ms_t = time_calls(torch_ref, stream, reps=10)
+    n = W.numel()
+    return {"n": W.shape[0], "fused_fwd_bwd_ms": round(ms_f, 4), "torch_autograd_ms": round(ms_t, 4),
+            "speedup": round(ms_t / ms_f, 2), "algorithmic_bytes": 32 * n,
+            "gbs": round(32 * n / ms_f / 1e6, 1)}
+
+
+def bench_precision(dev, stream):
+    import torch
+
+    import paper_2508_11385_gb300 as coot
+    from paper_2508_11385_gb300 import workloads
+
+    out = {}
+    n = 1 << 28
+    for dt in ("f32", "bf16", "f16"):
+        x, y = workloads.precision(dt, n=n, device=dev)
+        X, Yv = coot.Mat(x), coot.Mat(y)
+        d = {}
+        for name, red in (("accu", coot.accu(X)), ("dot", coot.dot(X, Yv)), ("norm", coot.norm(X)),
+                          ("var", coot.var(X))):
+            red.eval()
+            ms = time_calls(lambda: red.eval(), stream, reps=5)
+            b = coot.last_launch(dev)["algorithmic_bytes"]
+            d[name] = {"ms": round(ms, 4), "gbs": round(b / ms / 1e6, 1)}
+        out[dt] = d
+        del x, y
+        torch.cuda.empty_cache()
+    x, _ = workloads.precision("f64", n=n, device=dev)
+    red = coot.var(coot.Mat(x))
+    red.eval()
+    ms = time_calls(lambda: red.eval(), stream, reps=5)
+    out["f64_var"] = {"ms": round(ms, 4), "gbs": round(2 * n * 8 / ms / 1e6, 1)}
+    return out
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 oracle on host cores
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_2508_11385_gb300 import workloads
+
+    oracle.build()
+    n = 1024
+    scale = n / N_MAIN
+    leaves = workloads.large_trees("f32", n=n, device="cpu")
+    host = [workloads.to_numpy_colmajor(t) for t in leaves]
+
+    def step():
+        b = 0
+        for _, prog, _ in TREES:
+            p = prog.replace("submat:1000:1000:4096:4096", "submat:%d:%d:%d:%d" % (
+                int(1000 * scale), int(1000 * scale), int(4096 * scale), int(4096 * scale)))
+            oracle.evaluate(p, host, "f32")
+            b += algorithmic_bytes(p, n, 4)
+        return b
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    total = 0
+    for _ in range(args.steps):
+        total += step()
+    sec = time.perf_counter() - t0
+    value = total / sec / 1e9
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GB/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec * 1e3 / args.steps, 2),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (same recipe, host-generated)",
+           "config": {"workload": "large memory-bound trees, FP32 storage: 6 shapes + depth ladder L4-L8 "
+                                  "(bounded sample %dx%d per step)" % (n, n), "trees": [t[0] for t in TREES]},
+           "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                            "sample": "%d steps of the %d trees at %dx%d" % (args.steps, len(TREES), n, n)},
+           "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_MAIN)
+    ap.add_argument("--batch-problems", type=int, default=50000)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--quick", action="store_true", help="headline only (no side workloads)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

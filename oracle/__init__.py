@@ -148,3 +148,35 @@ def sum_neumaier(x: np.ndarray) -> float:
 
 def ulp(x: float, dtype: str) -> float:
     return _load().orc_ulp(float(x), DTYPES[dtype])
+
+
+def grad(program: str, leaves, dtype: str):
+    """Reverse-mode FP64 gradient of ``program`` (ending in accu / sum / mean)
+    with respect to every leaf.  Returns (loss, [grad_i], [absgrad_i]) with
+    column-major float64 arrays of the leaves' shapes; absgrad_i is the same
+    sweep over absolute values (the scale of the terms summed per element)."""
+    lib = _load()
+    if not hasattr(lib, "_grad_ready"):
+        lib.orc_grad.argtypes = [ctypes.c_char_p, ctypes.POINTER(_Mat), ctypes.c_int32,
+                                 ctypes.POINTER(ctypes.POINTER(ctypes.c_double)),
+                                 ctypes.POINTER(ctypes.POINTER(ctypes.c_double)),
+                                 ctypes.POINTER(ctypes.c_double), ctypes.c_char_p]
+        lib.orc_grad.restype = ctypes.c_int
+        lib._grad_ready = True
+    mats, keep = [], []
+    for a in leaves:
+        m, held = _as_mat(np.asarray(a), dtype)
+        mats.append(m)
+        keep.append(held)
+    arr = (_Mat * len(mats))(*mats)
+    gs = [np.zeros((m.n_rows, m.n_cols), dtype=np.float64, order="F") for m in mats]
+    ags = [np.zeros((m.n_rows, m.n_cols), dtype=np.float64, order="F") for m in mats]
+    DP = ctypes.POINTER(ctypes.c_double)
+    gp = (DP * len(gs))(*[g.ctypes.data_as(DP) for g in gs])
+    ap = (DP * len(ags))(*[g.ctypes.data_as(DP) for g in ags])
+    loss = ctypes.c_double()
+    err = ctypes.create_string_buffer(256)
+    rc = lib.orc_grad(program.encode(), arr, len(mats), gp, ap, ctypes.byref(loss), err)
+    if rc != 0:
+        raise OracleError(err.value.decode())
+    return loss.value, gs, ags

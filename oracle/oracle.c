@@ -753,3 +753,244 @@ void orc_free(orc_result* res) {
   res->v = res->b = NULL;
   res->iv = NULL;
 }
+
+/* ------------------------------------------------------------------ */
+/* gradient of a scalar loss (reverse mode over the materialised tape)  */
+/* ------------------------------------------------------------------ */
+/*
+ * For L = red(tree) with red accu / sum (all elements) / mean, the gradient
+ * with respect to each leaf is the plain chain rule: every node's adjoint
+ * matrix is the sum over its consumers of the consumer's adjoint times the
+ * local derivative, starting from dL/d(root) = 1 (accu) or 1/N (mean).  A
+ * second sweep with the absolute values of every local derivative and
+ * adjoint gives sum |terms| per gradient element, against which the rounding
+ * of a device that evaluates the same sweep in its compute type is bounded.
+ */
+typedef struct {
+  int kind;    /* 0 leaf, 1 scalar, 2 unary, 3 binary, 4 submat */
+  int op;      /* U_* / B_* */
+  int a, b;    /* operand tape indices */
+  int leaf;
+  int64_t r0, c0;
+  val_t v;     /* forward value (materialised) */
+} tape_t;
+
+int orc_grad(const char* program, const orc_mat* leaves, int32_t n_leaves, double** grads, double** absgrads,
+             double* loss, char* err) {
+  err[0] = 0;
+  int dt = leaves[0].dtype;
+  for (int i = 1; i < n_leaves; ++i)
+    if (leaves[i].dtype != dt) {
+      snprintf(err, 256, "all leaves must share one dtype");
+      return -1;
+    }
+  if (dt == ORC_I32) {
+    snprintf(err, 256, "gradients are defined for floating trees only");
+    return -1;
+  }
+  ctx_t cx;
+  cx.is_int = 0;
+  cx.ct = (dt == ORC_F64) ? ORC_F64 : ORC_F32;
+  cx.div0 = 0;
+  cx.err = err;
+  tape_t tp[MAX_STACK];
+  int nt = 0, st[MAX_STACK], sp = 0, rc = -1, red = -1;
+  size_t plen = strlen(program);
+  char* buf = (char*)malloc(plen + 1);
+  memcpy(buf, program, plen + 1);
+  char* save = NULL;
+  for (char* tok = strtok_r(buf, " \t\n", &save); tok; tok = strtok_r(NULL, " \t\n", &save)) {
+    if (red >= 0 || nt >= MAX_STACK - 1) {
+      snprintf(err, 256, "malformed program");
+      goto done;
+    }
+    tape_t* t = &tp[nt];
+    memset(t, 0, sizeof *t);
+    int uop = -1, bop = -1;
+    if (tok[0] >= 'A' && tok[0] <= 'H' && tok[1] == 0) {
+      t->kind = 0;
+      t->leaf = tok[0] - 'A';
+      if (t->leaf >= n_leaves) {
+        snprintf(err, 256, "leaf %c not given", tok[0]);
+        goto done;
+      }
+      if (load_leaf(&cx, &leaves[t->leaf], &t->v)) goto done;
+      st[sp++] = nt++;
+      continue;
+    }
+    if (tok[0] == '#') {
+      int ok;
+      t->kind = 1;
+      t->v.kind = V_SCALAR;
+      t->v.k = to_elem_type(&cx, strtod(tok + 1, NULL), &ok);
+      st[sp++] = nt++;
+      continue;
+    }
+    if (!strcmp(tok, "accu") || !strcmp(tok, "sum") || !strcmp(tok, "mean")) {
+      if (sp != 1) {
+        snprintf(err, 256, "reduction needs one operand");
+        goto done;
+      }
+      red = !strcmp(tok, "mean") ? 1 : 0;
+      continue;
+    }
+    if (!strncmp(tok, "submat:", 7)) {
+      long long r0, c0, nr, nc;
+      if (sp < 1 || sscanf(tok + 7, "%lld:%lld:%lld:%lld", &r0, &c0, &nr, &nc) != 4) {
+        snprintf(err, 256, "bad submat");
+        goto done;
+      }
+      t->kind = 4;
+      t->a = st[sp - 1];
+      t->r0 = r0;
+      t->c0 = c0;
+      if (submat(&cx, &tp[t->a].v, r0, c0, nr, nc, &t->v)) goto done;
+      st[sp - 1] = nt++;
+      continue;
+    }
+    if (!strcmp(tok, "+")) bop = B_PLUS;
+    else if (!strcmp(tok, "-")) bop = B_MINUS;
+    else if (!strcmp(tok, "%")) bop = B_SCHUR;
+    else if (!strcmp(tok, "/")) bop = B_DIV;
+    else if (!strcmp(tok, "*")) bop = B_TIMES;
+    else if (!strcmp(tok, "neg")) uop = U_NEG;
+    else if (!strcmp(tok, "exp")) uop = U_EXP;
+    else if (!strcmp(tok, "log")) uop = U_LOG;
+    else if (!strcmp(tok, "abs")) uop = U_ABS;
+    else if (!strcmp(tok, "square")) uop = U_SQUARE;
+    else if (!strcmp(tok, "sqrt")) uop = U_SQRT;
+    else if (!strcmp(tok, "trans")) uop = U_TRANS;
+    if (bop >= 0) {
+      if (sp < 2) goto underflow;
+      t->kind = 3;
+      t->op = bop;
+      t->a = st[sp - 2];
+      t->b = st[sp - 1];
+      if (binary(&cx, bop, &tp[t->a].v, &tp[t->b].v, &t->v)) goto done;
+      st[sp - 2] = nt++;
+      sp--;
+    } else if (uop >= 0) {
+      if (sp < 1) goto underflow;
+      t->kind = 2;
+      t->op = uop;
+      t->a = st[sp - 1];
+      if (tp[t->a].v.kind != V_MAT) {
+        snprintf(err, 256, "unary op of a scalar");
+        goto done;
+      }
+      if (unary(&cx, uop, &tp[t->a].v, &t->v)) goto done;
+      st[sp - 1] = nt++;
+    } else {
+      snprintf(err, 256, "token '%s' not supported by the gradient", tok);
+      goto done;
+    }
+    continue;
+  underflow:
+    snprintf(err, 256, "stack underflow at '%s'", tok);
+    goto done;
+  }
+  if (red < 0 || sp != 1 || tp[st[0]].v.kind != V_MAT) {
+    snprintf(err, 256, "the program must end with accu / sum / mean of a matrix");
+    goto done;
+  }
+  {
+    const int root = st[0];
+    const int64_t N = tp[root].v.r * tp[root].v.c;
+    *loss = orc_sum_neumaier(tp[root].v.v, N) / (red ? (double)N : 1.0);
+    /* adjoints (value and absolute sweep) per tape entry */
+    double** adj = (double**)calloc((size_t)nt, sizeof(double*));
+    double** aab = (double**)calloc((size_t)nt, sizeof(double*));
+    for (int i = 0; i < nt; ++i)
+      if (tp[i].v.kind == V_MAT) {
+        size_t n = (size_t)(tp[i].v.r * tp[i].v.c);
+        adj[i] = (double*)calloc(n ? n : 1, sizeof(double));
+        aab[i] = (double*)calloc(n ? n : 1, sizeof(double));
+      }
+    for (int64_t q = 0; q < N; ++q) {
+      adj[root][q] = red ? 1.0 / (double)N : 1.0;
+      aab[root][q] = adj[root][q];
+    }
+    for (int li = 0; li < n_leaves; ++li) {
+      size_t n = (size_t)(leaves[li].n_rows * leaves[li].n_cols);
+      memset(grads[li], 0, n * sizeof(double));
+      memset(absgrads[li], 0, n * sizeof(double));
+    }
+    for (int i = nt - 1; i >= 0; --i) {
+      tape_t* t = &tp[i];
+      if (t->v.kind != V_MAT) continue;
+      const int64_t r = t->v.r, c = t->v.c, n = r * c;
+      double *g = adj[i], *ga = aab[i];
+      if (t->kind == 0) {
+        /* a leaf occurrence: accumulate into the leaf's gradient */
+        for (int64_t q = 0; q < n; ++q) {
+          grads[t->leaf][q] += g[q];
+          absgrads[t->leaf][q] += ga[q];
+        }
+      } else if (t->kind == 4) {
+        val_t* x = &tp[t->a].v;
+        for (int64_t j = 0; j < c; ++j)
+          for (int64_t k = 0; k < r; ++k) {
+            int64_t s = (t->r0 + k) + (t->c0 + j) * x->r;
+            adj[t->a][s] += g[k + j * r];
+            aab[t->a][s] += ga[k + j * r];
+          }
+      } else if (t->kind == 2) {
+        val_t* x = &tp[t->a].v;
+        for (int64_t j = 0; j < c; ++j)
+          for (int64_t k = 0; k < r; ++k) {
+            int64_t q = k + j * r;
+            if (t->op == U_TRANS) {
+              /* trans(X)(k,j) = X(j,k) */
+              int64_t s = j + k * x->r;
+              adj[t->a][s] += g[q];
+              aab[t->a][s] += ga[q];
+              continue;
+            }
+            double a = x->v[q], d = 0.0;
+            switch (t->op) {
+              case U_NEG: d = -1.0; break;
+              case U_EXP: d = exp(a); break;
+              case U_LOG: d = 1.0 / a; break;
+              case U_ABS: d = (a > 0) - (a < 0); break;
+              case U_SQUARE: d = 2.0 * a; break;
+              case U_SQRT: d = 0.5 / sqrt(a); break;
+            }
+            adj[t->a][q] += d * g[q];
+            aab[t->a][q] += fabs(d) * ga[q];
+          }
+      } else if (t->kind == 3) {
+        val_t *x = &tp[t->a].v, *y = &tp[t->b].v;
+        int xs = x->kind == V_SCALAR, ys = y->kind == V_SCALAR;
+        for (int64_t q = 0; q < n; ++q) {
+          double a = xs ? x->k : x->v[q], b = ys ? y->k : y->v[q], da = 0.0, db = 0.0;
+          switch (t->op) {
+            case B_PLUS: da = 1.0; db = 1.0; break;
+            case B_MINUS: da = 1.0; db = -1.0; break;
+            case B_SCHUR:
+            case B_TIMES: da = b; db = a; break;
+            case B_DIV: da = 1.0 / b; db = -a / (b * b); break;
+          }
+          if (!xs) {
+            adj[t->a][q] += da * g[q];
+            aab[t->a][q] += fabs(da) * ga[q];
+          }
+          if (!ys) {
+            adj[t->b][q] += db * g[q];
+            aab[t->b][q] += fabs(db) * ga[q];
+          }
+        }
+      }
+    }
+    for (int i = 0; i < nt; ++i) {
+      free(adj[i]);
+      free(aab[i]);
+    }
+    free(adj);
+    free(aab);
+  }
+  rc = 0;
+done:
+  for (int i = 0; i < nt; ++i) val_free(&tp[i].v);
+  free(buf);
+  return rc;
+}

@@ -82,6 +82,15 @@ int orc_eval(const char* program, const orc_mat* leaves, int32_t n_leaves,
 
 void orc_free(orc_result* res);
 
+/* Gradient of L = accu / sum / mean(tree) with respect to every leaf, in
+ * FP64 by reverse mode over the materialised tree (the program ends with
+ * "accu", "sum" or "mean").  grads[i] and absgrads[i] are caller-allocated
+ * contiguous column-major arrays of leaf i's shape; absgrads receives the
+ * same sweep over absolute values (sum of |terms| per element).  *loss gets
+ * L.  Returns 0, or non-zero with a message in err (256 bytes). */
+int orc_grad(const char* program, const orc_mat* leaves, int32_t n_leaves, double** grads, double** absgrads,
+             double* loss, char* err);
+
 /* Neumaier-compensated FP64 sum of x[0..n) (exposed for the pin tests). */
 double orc_sum_neumaier(const double* x, int64_t n);
 

@@ -177,6 +177,14 @@ struct Launch {
 
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// number of values a reduction writes (a vector along dim 0/1 may be empty)
+int64_t n_red_outputs(const cg::Analysis& an) {
+  if (an.red.kind == COOT_R_NONE) return 0;
+  if (an.red.dim == 0) return an.nc;
+  if (an.red.dim == 1) return an.nr;
+  return 1;
+}
+
 // fill the launch shape of a fused program for a given kernel variant/config
 void shape_launch(coot_ctx* ctx, const cg::Analysis& an, const cg::Choice& ch, cg::Module* m,
                   const cg::KernelSpec& k, int block, int bps, Launch* L) {
@@ -527,7 +535,7 @@ extern "C" coot_status coot_eval(coot_ctx* ctx, const coot_tree* tree, const coo
   cg::Analysis an;
   coot_status s = cg::analyse(tree, leaves, n_leaves, out, red, &an);
   if (s) return s;
-  if (red.kind != COOT_R_NONE && !red_out) return set_error(COOT_ERR_INVALID, "red_out is NULL");
+  if (red.kind != COOT_R_NONE && !red_out && n_red_outputs(an) > 0) return set_error(COOT_ERR_INVALID, "red_out is NULL");
   if (red.kind == COOT_R_NONE && !out) return set_error(COOT_ERR_INVALID, "neither out nor a reduction requested");
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);
   DeviceGuard g(ctx->device);
@@ -558,7 +566,7 @@ extern "C" coot_status coot_eval_unfused(coot_ctx* ctx, const coot_tree* tree, c
   if (s) return s;
   if (an.dtype == COOT_BF16 || an.dtype == COOT_F16)
     return set_error(COOT_ERR_UNSUPPORTED, "the unfused baseline keeps temporaries in the storage type; use F32/F64/I32");
-  if (red.kind != COOT_R_NONE && !red_out) return set_error(COOT_ERR_INVALID, "red_out is NULL");
+  if (red.kind != COOT_R_NONE && !red_out && n_red_outputs(an) > 0) return set_error(COOT_ERR_INVALID, "red_out is NULL");
   if (red.kind == COOT_R_NONE && !out) return set_error(COOT_ERR_INVALID, "neither out nor a reduction requested");
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);
   DeviceGuard g(ctx->device);

@@ -62,7 +62,8 @@ def compare_matrix(gpu, res, dtype, what=""):
     if not np.all(fin):
         same = (g[~fin] == v[~fin]) | (np.isnan(g[~fin]) & np.isnan(v[~fin]))
         assert np.all(same), "%s: non-finite oracle values differ" % what
-    err = np.abs(g - v)
+    with np.errstate(invalid="ignore"):
+        err = np.abs(g - v)
     viol = fin & ~(err <= b)
     if np.any(viol):
         i = tuple(np.argwhere(viol)[0])
@@ -84,7 +85,8 @@ def compare_reduction(gpu, res, dtype, what="", rel=None):
         same = (g[~fin] == v[~fin]) | (np.isnan(g[~fin]) & np.isnan(v[~fin]))
         assert np.all(same), "%s: non-finite reduction differs: %s vs %s" % (what, g[~fin][:4], v[~fin][:4])
     tol = rel * np.abs(v) + b
-    err = np.abs(g - v)
+    with np.errstate(invalid="ignore"):
+        err = np.abs(g - v)
     viol = fin & ~(err <= tol)
     if np.any(viol):
         i = tuple(np.argwhere(viol)[0])

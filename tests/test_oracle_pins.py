@@ -455,3 +455,79 @@ def test_compute_type_overflow_is_inf(orc):
 def test_malformed_programs_are_rejected(orc, prog):
     with pytest.raises(orc.OracleError):
         orc.evaluate(prog, [F(np.ones((3, 2))), F(np.ones((2, 3)))], "f64")
+
+
+# ------------------------------------------------------------ gradients
+
+def test_grad_matches_closed_form_of_the_differentiation_loss(orc):
+    """L = accu(square(W%X - Y)) + 1e-3 accu(square(W)):
+    dL/dW = 2 (W%X - Y) % X + 2e-3 W,  dL/dX = 2 (W%X - Y) % W."""
+    nrng = np.random.default_rng(6)
+    W, X, Y = (nrng.normal(size=(64, 64)) for _ in range(3))
+    prog = "A B % C - square #0.001 A square * + accu"
+    loss, (gW, gX, gY), _ = orc.grad(prog, [F(W), F(X), F(Y)], "f64")
+    R = W * X - Y
+    assert loss == pytest.approx(np.sum(R * R) + 1e-3 * np.sum(W * W), rel=1e-13)
+    assert np.allclose(gW, 2 * R * X + 2e-3 * W, rtol=1e-13, atol=1e-13)
+    assert np.allclose(gX, 2 * R * W, rtol=1e-13, atol=1e-13)
+    assert np.allclose(gY, -2 * R, rtol=1e-13, atol=1e-13)
+
+
+def test_grad_matches_central_differences_on_a_64x64_slice(orc):
+    """Central finite differences in FP64 of the oracle's own forward
+    evaluation; L is quadratic in each of W and X, so the central difference
+    is exact up to rounding."""
+    nrng = np.random.default_rng(60)
+    W, X, Y = (nrng.normal(size=(64, 64)) for _ in range(3))
+    prog = "A B % C - square #0.001 A square * + accu"
+    _, (gW, gX, _), _ = orc.grad(prog, [F(W), F(X), F(Y)], "f64")
+    h = 1e-3
+    for which, G in ((0, gW), (1, gX)):
+        for idx in [(i, j) for i in range(0, 64, 3) for j in range(0, 64, 5)]:
+            lv = [W.copy(), X.copy(), Y.copy()]
+            lv[which][idx] += h
+            up = orc.evaluate(prog, [F(x) for x in lv], "f64").value[0, 0]
+            lv[which][idx] -= 2 * h
+            dn = orc.evaluate(prog, [F(x) for x in lv], "f64").value[0, 0]
+            fd = (up - dn) / (2 * h)
+            assert abs(fd - G[idx]) <= 1e-7 * max(1.0, abs(G[idx])), (which, idx, fd, G[idx])
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_grad_of_random_trees_matches_finite_differences(orc, seed):
+    rng = random.Random(500 + seed)
+    nrng = np.random.default_rng(500 + seed)
+    leaves = [nrng.uniform(0.5, 2.0, size=(5, 4)) for _ in range(3)]
+    prog = rpn.random_tree(rng, n_leaves=3, depth=rng.randint(1, 4), ops_un=["neg", "square", "exp", "sqrt", "log"])
+    if rng.random() < 0.3:
+        prog = prog + " trans"
+    prog = prog + (" mean" if seed % 2 else " accu")
+    try:
+        loss, gs, ags = orc.grad(prog, [F(x) for x in leaves], "f64")
+    except orc.OracleError:
+        pytest.skip("tree with a scalar root")
+    if not np.isfinite(loss):
+        pytest.skip("non-finite loss")
+    h = 1e-6
+    for li in range(3):
+        for idx in [(0, 0), (4, 3), (2, 1)]:
+            lv = [x.copy() for x in leaves]
+            lv[li][idx] += h
+            up = orc.evaluate(prog, [F(x) for x in lv], "f64").value[0, 0]
+            lv[li][idx] -= 2 * h
+            dn = orc.evaluate(prog, [F(x) for x in lv], "f64").value[0, 0]
+            fd = (up - dn) / (2 * h)
+            assert abs(fd - gs[li][idx]) <= 1e-5 * max(1.0, abs(gs[li][idx]), ags[li][idx]), (prog, li, idx)
+            assert ags[li][idx] >= abs(gs[li][idx]) * (1 - 1e-12)
+
+
+def test_grad_through_trans_and_submat(orc):
+    nrng = np.random.default_rng(3)
+    A = nrng.normal(size=(6, 9))
+    B = nrng.normal(size=(4, 5))
+    # accu(trans(A.submat(1,2,5,4)) % B): dL/dA is B^T scattered into the view
+    _, (gA, gB), _ = orc.grad("A submat:1:2:5:4 trans B % accu", [F(A), F(B)], "f64")
+    expect = np.zeros_like(A)
+    expect[1:6, 2:6] = B.T
+    assert np.array_equal(gA, expect)
+    assert np.array_equal(gB, A[1:6, 2:6].T)
