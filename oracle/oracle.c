@@ -762,9 +762,11 @@ void orc_free(orc_result* res) {
  * with respect to each leaf is the plain chain rule: every node's adjoint
  * matrix is the sum over its consumers of the consumer's adjoint times the
  * local derivative, starting from dL/d(root) = 1 (accu) or 1/N (mean).  A
- * second sweep with the absolute values of every local derivative and
- * adjoint gives sum |terms| per gradient element, against which the rounding
- * of a device that evaluates the same sweep in its compute type is bounded.
+ * second sweep over magnitudes -- node values formed with absolute values
+ * throughout, |a| + |b| for a +- b and |a||b| for a*b, and the local
+ * derivatives taken from those magnitudes -- gives the scale of every
+ * rounding a device makes in the forward and the reverse sweep, against which
+ * the device gradient is bounded (a running error bound).
  */
 typedef struct {
   int kind;    /* 0 leaf, 1 scalar, 2 unary, 3 binary, 4 submat */
@@ -897,7 +899,43 @@ int orc_grad(const char* program, const orc_mat* leaves, int32_t n_leaves, doubl
     const int root = st[0];
     const int64_t N = tp[root].v.r * tp[root].v.c;
     *loss = orc_sum_neumaier(tp[root].v.v, N) / (red ? (double)N : 1.0);
-    /* adjoints (value and absolute sweep) per tape entry */
+    /* magnitudes of every node, evaluated with absolute values throughout
+     * (|a| + |b| for a +- b, |a||b| for a*b, ...): the scale of the
+     * rounding errors a device makes while forming that node */
+    double** mag = (double**)calloc((size_t)nt, sizeof(double*));
+    for (int i = 0; i < nt; ++i) {
+      tape_t* t = &tp[i];
+      if (t->v.kind != V_MAT) continue;
+      const int64_t r = t->v.r, c = t->v.c, n = r * c;
+      mag[i] = (double*)calloc((size_t)(n ? n : 1), sizeof(double));
+      for (int64_t j = 0; j < c; ++j)
+        for (int64_t k = 0; k < r; ++k) {
+          int64_t q = k + j * r;
+          double m = fabs(t->v.v[q]);
+          if (t->kind == 4) {
+            m = mag[t->a][(t->r0 + k) + (t->c0 + j) * tp[t->a].v.r];
+          } else if (t->kind == 2) {
+            double ma = (t->op == U_TRANS) ? mag[t->a][j + k * tp[t->a].v.r] : mag[t->a][q];
+            switch (t->op) {
+              case U_NEG: case U_ABS: case U_TRANS: m = ma; break;
+              case U_SQUARE: m = ma * ma; break;
+              default: m = fabs(t->v.v[q]); break; /* exp, log, sqrt: their own value */
+            }
+          } else if (t->kind == 3) {
+            val_t *x = &tp[t->a].v, *y = &tp[t->b].v;
+            double ma = (x->kind == V_SCALAR) ? fabs(x->k) : mag[t->a][q];
+            double mb = (y->kind == V_SCALAR) ? fabs(y->k) : mag[t->b][q];
+            double b = (y->kind == V_SCALAR) ? y->k : y->v[q];
+            switch (t->op) {
+              case B_PLUS: case B_MINUS: m = ma + mb; break;
+              case B_SCHUR: case B_TIMES: m = ma * mb; break;
+              case B_DIV: m = ma / fabs(b); break;
+            }
+          }
+          mag[i][q] = m;
+        }
+    }
+    /* adjoints (value and magnitude sweep) per tape entry */
     double** adj = (double**)calloc((size_t)nt, sizeof(double*));
     double** aab = (double**)calloc((size_t)nt, sizeof(double*));
     for (int i = 0; i < nt; ++i)
@@ -946,7 +984,7 @@ int orc_grad(const char* program, const orc_mat* leaves, int32_t n_leaves, doubl
               aab[t->a][s] += ga[q];
               continue;
             }
-            double a = x->v[q], d = 0.0;
+            double a = x->v[q], d = 0.0, dm;
             switch (t->op) {
               case U_NEG: d = -1.0; break;
               case U_EXP: d = exp(a); break;
@@ -955,28 +993,31 @@ int orc_grad(const char* program, const orc_mat* leaves, int32_t n_leaves, doubl
               case U_SQUARE: d = 2.0 * a; break;
               case U_SQRT: d = 0.5 / sqrt(a); break;
             }
+            dm = (t->op == U_SQUARE) ? 2.0 * mag[t->a][q] : (t->op == U_ABS ? 1.0 : fabs(d));
             adj[t->a][q] += d * g[q];
-            aab[t->a][q] += fabs(d) * ga[q];
+            aab[t->a][q] += dm * ga[q];
           }
       } else if (t->kind == 3) {
         val_t *x = &tp[t->a].v, *y = &tp[t->b].v;
         int xs = x->kind == V_SCALAR, ys = y->kind == V_SCALAR;
         for (int64_t q = 0; q < n; ++q) {
           double a = xs ? x->k : x->v[q], b = ys ? y->k : y->v[q], da = 0.0, db = 0.0;
+          double ma = xs ? fabs(x->k) : mag[t->a][q], mb = ys ? fabs(y->k) : mag[t->b][q];
+          double dam = 1.0, dbm = 1.0;
           switch (t->op) {
             case B_PLUS: da = 1.0; db = 1.0; break;
             case B_MINUS: da = 1.0; db = -1.0; break;
             case B_SCHUR:
-            case B_TIMES: da = b; db = a; break;
-            case B_DIV: da = 1.0 / b; db = -a / (b * b); break;
+            case B_TIMES: da = b; db = a; dam = mb; dbm = ma; break;
+            case B_DIV: da = 1.0 / b; db = -a / (b * b); dam = fabs(da); dbm = ma / (b * b); break;
           }
           if (!xs) {
             adj[t->a][q] += da * g[q];
-            aab[t->a][q] += fabs(da) * ga[q];
+            aab[t->a][q] += dam * ga[q];
           }
           if (!ys) {
             adj[t->b][q] += db * g[q];
-            aab[t->b][q] += fabs(db) * ga[q];
+            aab[t->b][q] += dbm * ga[q];
           }
         }
       }
@@ -984,9 +1025,11 @@ int orc_grad(const char* program, const orc_mat* leaves, int32_t n_leaves, doubl
     for (int i = 0; i < nt; ++i) {
       free(adj[i]);
       free(aab[i]);
+      free(mag[i]);
     }
     free(adj);
     free(aab);
+    free(mag);
   }
   rc = 0;
 done:

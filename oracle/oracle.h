@@ -86,7 +86,9 @@ void orc_free(orc_result* res);
  * FP64 by reverse mode over the materialised tree (the program ends with
  * "accu", "sum" or "mean").  grads[i] and absgrads[i] are caller-allocated
  * contiguous column-major arrays of leaf i's shape; absgrads receives the
- * same sweep over absolute values (sum of |terms| per element).  *loss gets
+ * same sweep over magnitudes (forward values formed with absolute values,
+ * |a| + |b| for a +- b, and derivatives taken from them): the scale of the
+ * roundings a device makes along each gradient element.  *loss gets
  * L.  Returns 0, or non-zero with a message in err (256 bytes). */
 int orc_grad(const char* program, const orc_mat* leaves, int32_t n_leaves, double** grads, double** absgrads,
              double* loss, char* err);

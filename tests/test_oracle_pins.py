@@ -531,3 +531,27 @@ def test_grad_through_trans_and_submat(orc):
     expect[1:6, 2:6] = B.T
     assert np.array_equal(gA, expect)
     assert np.array_equal(gB, A[1:6, 2:6].T)
+
+
+def test_grad_bound_covers_an_emulated_fp32_device(orc):
+    """The device's reverse sweep for L = accu(square(W%X - Y)) + lam accu(square(W)),
+    rounded to FP32 at every operation in the order the adjoint kernel uses,
+    stays within 16 u times the oracle's magnitude sweep (including rows where
+    W%X - Y cancels)."""
+    nrng = np.random.default_rng(66)
+    W, X = (nrng.normal(size=(128, 64)).astype(np.float32) for _ in range(2))
+    Y = (W * X).astype(np.float32)  # exact cancellation ...
+    Y[::2] = nrng.uniform(-1, 1, size=Y[::2].shape).astype(np.float32)  # ... on every other row
+    f = np.float32
+    lam = f(1e-3)
+    r = (W * X).astype(f) - Y
+    gW = (f(2) * r * X).astype(f) + ((lam + lam) * W).astype(f)
+    gX = (f(2) * r * W).astype(f)
+    prog = "A B % C - square #0.001 A square * + accu"
+    _, (oW, oX, _), (aW, aX, _) = orc.grad(prog, [F(W), F(X), F(Y)], "f32")
+    u = 2.0 ** -24
+    assert np.all(np.abs(gW.astype(np.float64) - oW) <= 16 * u * aW)
+    assert np.all(np.abs(gX.astype(np.float64) - oX) <= 16 * u * aX)
+    # and the plain |terms| sweep would not have covered the cancelling rows
+    plain = np.abs(2 * (W.astype(np.float64) * X - Y) * X) + 2e-3 * np.abs(W)
+    assert np.any(np.abs(gW.astype(np.float64) - oW) > 16 * u * plain)
