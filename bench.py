@@ -294,7 +294,8 @@ def run_gpu(args):
     stream = torch.cuda.current_stream(dev)
     sp = stream.cuda_stream
     leaves = workloads.large_trees("f32", n=n, device=dev)
-    calls = [(name, prog, depth, Call(prog, leaves, True)) for name, prog, depth in TREES]
+    calls = [(name, prog, depth, Call(prog, leaves, True)) for name, prog, depth in TREES
+             if not args.only or name == args.only]
     # warm the JIT and tuning caches (excluded from timing, as the paper's startup is)
     for _, _, _, c in calls:
         c(sp)
@@ -377,7 +378,7 @@ def run_gpu(args):
         extras = run_extras(args, leaves, calls, per_tree_ms, bytes_per, dev, stream, peak)
 
     # end to end through host buffers: H2D of each tree's operands, eval, D2H of its result
-    e2e = run_e2e(calls, leaves, stream, max(2, min(args.steps, 5)), dev) if rank == 0 else None
+    e2e = run_e2e(calls, leaves, stream, max(2, min(args.steps, 5)), dev) if rank == 0 and not args.quick else None
 
     out = {
         "metric": METRIC,
@@ -645,12 +646,19 @@ def bench_graph(dev, stream):
 def bench_adjoint(dev, stream):
     import torch
 
+    import paper_2508_11385_gb300 as coot
     from paper_2508_11385_gb300 import autograd as AG
     from paper_2508_11385_gb300 import workloads
 
     W, X, Y = workloads.differentiation(device=dev)
     Wp = W.clone().requires_grad_(True)
     Xp = X.clone().requires_grad_(True)
+    f = AG.Loss(lambda w, x, y: coot.accu(coot.square(w % x - y)) + 1e-3 * coot.accu(coot.square(w)), W, X, Y)
+    r = torch.empty((), dtype=torch.float32, device=dev)
+    one = torch.ones((), dtype=torch.float32, device=dev)
+    gW, gX = torch.empty_like(W), torch.empty_like(X)
+    ms_fwd = time_calls(lambda: f.forward(W, X, Y, out=r), stream, reps=20)
+    ms_bwd = time_calls(lambda: f.backward(one, W, X, Y, grads=[gW, gX, None]), stream, reps=20)
 
     def fused():
         loss = AG.loss_l2_schur(Wp, Xp, Y, 1e-3)
@@ -666,9 +674,11 @@ def bench_adjoint(dev, stream):
     ms_f = time_calls(fused, stream, reps=10)
     ms_t = time_calls(torch_ref, stream, reps=10)
     n = W.numel()
-    return {"n": W.shape[0], "fused_fwd_bwd_ms": round(ms_f, 4), "torch_autograd_ms": round(ms_t, 4),
-            "speedup": round(ms_t / ms_f, 2), "algorithmic_bytes": 32 * n,
-            "gbs": round(32 * n / ms_f / 1e6, 1)}
+    return {"n": W.shape[0], "fwd_kernel_ms": round(ms_fwd, 4), "fwd_gbs": round(12 * n / ms_fwd / 1e6, 1),
+            "adjoint_kernel_ms": round(ms_bwd, 4), "adjoint_gbs": round(20 * n / ms_bwd / 1e6, 1),
+            "autograd_step_ms": round(ms_f, 4), "torch_autograd_ms": round(ms_t, 4),
+            "speedup_vs_torch_autograd": round(ms_t / ms_f, 2), "algorithmic_bytes_fwd_bwd": 32 * n,
+            "note": "fwd reads W, X, Y (12N bytes); the adjoint reads them again and writes dW, dX (20N)"}
 
 
 def bench_precision(dev, stream):
@@ -758,7 +768,13 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--quick", action="store_true", help="headline only (no side workloads)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--only", default=None, help="time one tree of the workload (profiling); implies --quick")
     args = ap.parse_args()
+    if args.only:
+        if args.only not in [t[0] for t in TREES]:
+            ap.error("--only: one of %s" % ", ".join(t[0] for t in TREES))
+        args.quick = True
+        args.no_cpu = True
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":

@@ -187,7 +187,7 @@ int64_t n_red_outputs(const cg::Analysis& an) {
 
 // fill the launch shape of a fused program for a given kernel variant/config
 void shape_launch(coot_ctx* ctx, const cg::Analysis& an, const cg::Choice& ch, cg::Module* m,
-                  const cg::KernelSpec& k, int block, int bps, Launch* L) {
+                  const cg::KernelSpec& k, int block, int bps, Launch* L, int split = 0) {
   const int64_t R = ch.it_rows, C = ch.it_cols;
   L->block = block;
   L->vec = k.vec;
@@ -205,7 +205,17 @@ void shape_launch(coot_ctx* ctx, const cg::Analysis& an, const cg::Choice& ch, c
     L->tickets = 1;
   } else if (ch.fam == cg::F_COL) {
     const int64_t wpb = block / 32;
-    L->grid = (int)std::max<int64_t>(1, std::min(ceil_div(C, wpb), resident));
+    // warps per column: enough that every column step fills the GPU, a
+    // divisor of the warps per block
+    int64_t G = split;
+    if (G <= 0) {
+      G = 1;
+      while (G < wpb && (C * 1.0) / (resident * (wpb / G)) < 4.0 && R >= G * 2 * 32 * k.vec * k.unroll) G *= 2;
+    }
+    G = std::max<int64_t>(1, std::min<int64_t>(G, wpb));
+    while (wpb % G) --G;
+    p.n_splits = G;
+    L->grid = (int)std::max<int64_t>(1, std::min(ceil_div(C, wpb / G), resident));
     L->partial_bytes = 0;
     L->tickets = 1;
   } else if (ch.fam == cg::F_ROW) {
@@ -281,6 +291,40 @@ coot_status launch_kernel(cg::Module* m, const std::string& name, int grid, int 
 coot_status tune(coot_ctx* ctx, const cg::Analysis& an, const cg::Choice& ch, const cg::Program& pg, cg::Module* m,
                  Launch base, cudaStream_t stream, cg::LaunchCfg* best);
 
+// persistent tuning cache: one line per tuned (signature, size bucket)
+std::string tune_path(const coot_ctx* ctx) {
+  if ((ctx->flags & COOT_CTX_NO_DISK_CACHE) || ctx->cache_dir.empty()) return std::string();
+  char name[96];
+  snprintf(name, sizeof name, "/tune-%016llx-sm%d.txt", (unsigned long long)cg::headers_hash(), ctx->sms);
+  return ctx->cache_dir + name;
+}
+
+void load_tuning(coot_ctx* ctx) {
+  std::string path = tune_path(ctx);
+  if (path.empty()) return;
+  FILE* f = fopen(path.c_str(), "r");
+  if (!f) return;
+  std::vector<char> line(1 << 16);
+  while (fgets(line.data(), (int)line.size(), f)) {
+    char* tab = strrchr(line.data(), '\t');
+    if (!tab) continue;
+    cg::LaunchCfg c;
+    if (sscanf(tab + 1, "%d %d %d %d", &c.kidx, &c.block, &c.blocks_per_sm, &c.split) != 4) continue;
+    *tab = 0;
+    ctx->tuned[std::string(line.data())] = c;
+  }
+  fclose(f);
+}
+
+void save_tuning(coot_ctx* ctx, const std::string& key, const cg::LaunchCfg& c) {
+  std::string path = tune_path(ctx);
+  if (path.empty()) return;
+  FILE* f = fopen(path.c_str(), "a");  // one short line per append
+  if (!f) return;
+  fprintf(f, "%s\t%d %d %d %d\n", key.c_str(), c.kidx, c.block, c.blocks_per_sm, c.split);
+  fclose(f);
+}
+
 std::string tune_key(const cg::Program& pg, const cg::Choice& ch) {
   int64_t n = ch.it_rows * std::max<int64_t>(ch.it_cols, 1);
   int bucket = 0;
@@ -340,7 +384,8 @@ static coot_status run_fused(coot_ctx* ctx, const cg::Analysis& an, const coot_m
   std::string key = tune_key(pg, ch);
   cg::LaunchCfg cfg;
   auto tu = ctx->tuned.find(key);
-  if (tu != ctx->tuned.end()) {
+  if (tu != ctx->tuned.end() && tu->second.kidx >= 0 && tu->second.kidx < (int)pg.kernels.size() &&
+      (ch.vec_ok || pg.kernels[tu->second.kidx].vec == 1)) {
     cfg = tu->second;
   } else {
     cfg.kidx = default_variant(pg, ch);
@@ -352,10 +397,11 @@ static coot_status run_fused(coot_ctx* ctx, const cg::Analysis& an, const coot_m
       s = tune(ctx, an, ch, pg, m, base, stream, &cfg);
       if (s) return s;
       ctx->tuned[key] = cfg;
+      save_tuning(ctx, key, cfg);
     }
   }
   const cg::KernelSpec& ks = pg.kernels[cfg.kidx];
-  shape_launch(ctx, an, ch, m, ks, cfg.block, cfg.blocks_per_sm, &L);
+  shape_launch(ctx, an, ch, m, ks, cfg.block, cfg.blocks_per_sm, &L, cfg.split);
   L.kname = ks.name;
   if (var) L.kname2 = pair_name(ks.name);
   s = ws_ensure(ctx, L.tickets, L.partial_bytes, stream);
@@ -424,12 +470,16 @@ coot_status tune(coot_ctx* ctx, const cg::Analysis& an, const cg::Choice& ch, co
       int occ = occupancy(m, k.name, block);
       std::vector<int> bpss = {occ};
       for (int b : {1, 2, 4}) if (b < occ) bpss.push_back(b);
-      for (int bps : bpss) {
+      std::vector<int> splits = {0};
+      if (ch.fam == cg::F_COL)
+        for (int g = 1; g <= block / 32; g *= 2) splits.push_back(g);
+      for (int bps : bpss)
+      for (int split : splits) {
         Launch L = base;
         L.p.out = scratch_out;
         if (scratch_out) L.p.out_ld = sld;
         L.p.red_out = scratch_red;
-        shape_launch(ctx, an, ch, m, k, block, bps, &L);
+        shape_launch(ctx, an, ch, m, k, block, bps, &L, split);
         st = ws_ensure(ctx, L.tickets, L.partial_bytes, stream);
         if (st) break;
         L.p.tickets = ctx->tickets;
@@ -453,6 +503,7 @@ coot_status tune(coot_ctx* ctx, const cg::Analysis& an, const cg::Choice& ch, co
           best->kidx = ki;
           best->block = block;
           best->blocks_per_sm = bps;
+          best->split = split;
         }
       }
       if (st) break;
@@ -500,6 +551,7 @@ extern "C" coot_status coot_ctx_create(int device, unsigned flags, coot_ctx** ou
     c->cache_dir = cd;
   else if (getenv("HOME"))
     c->cache_dir = std::string(getenv("HOME")) + "/.cache/cootgb";
+  load_tuning(c);
   {
     DeviceGuard g(device);
     coot_status s = ws_ensure(c, 4096, 1 << 20, nullptr);
@@ -888,7 +940,12 @@ extern "C" coot_status coot_batch_create(coot_ctx* ctx, const coot_tree* tree, i
     tiles += ntr * ntc;
   }
   begin[n_problems] = tiles;
+  if (tiles >= (1ll << 31)) return set_error(COOT_ERR_UNSUPPORTED, "%lld tiles: at most 2^31 - 1", tiles);
   if (red.kind != COOT_R_NONE) bytes += n_problems * rsize(an0.ct);
+  // owning problem of every tile: one load per tile instead of a search
+  std::vector<int> tile_prob((size_t)tiles);
+  for (int64_t q = 0; q < n_problems; ++q)
+    for (long long t = begin[q]; t < begin[q + 1]; ++t) tile_prob[(size_t)t] = (int)q;
 
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);
   DeviceGuard g(ctx->device);
@@ -900,7 +957,8 @@ extern "C" coot_status coot_batch_create(coot_ctx* ctx, const coot_tree* tree, i
   auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t o_probs = 0;
   const size_t o_begin = align(o_probs + probs.size() * sizeof(coot::BatchProblem));
-  const size_t o_done = align(o_begin + begin.size() * sizeof(long long));
+  const size_t o_map = align(o_begin + begin.size() * sizeof(long long));
+  const size_t o_done = align(o_map + tile_prob.size() * sizeof(int));
   const size_t o_queue = align(o_done + (size_t)n_problems * sizeof(unsigned));
   const size_t o_part = align(o_queue + 2 * sizeof(unsigned));
   const size_t total = align(o_part + (size_t)tiles * 8);
@@ -914,6 +972,8 @@ extern "C" coot_status coot_batch_create(coot_ctx* ctx, const coot_tree* tree, i
   if ((e = cudaMemcpy(base + o_probs, probs.data(), probs.size() * sizeof(coot::BatchProblem),
                       cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(base + o_begin, begin.data(), begin.size() * sizeof(long long), cudaMemcpyHostToDevice)) !=
+          cudaSuccess ||
+      (e = cudaMemcpy(base + o_map, tile_prob.data(), tile_prob.size() * sizeof(int), cudaMemcpyHostToDevice)) !=
           cudaSuccess ||
       (e = cudaMemset(base + o_done, 0, o_part - o_done)) != cudaSuccess) {
     cudaFree(b->dev_mem);
@@ -932,8 +992,11 @@ extern "C" coot_status coot_batch_create(coot_ctx* ctx, const coot_tree* tree, i
   memset(&bp, 0, sizeof bp);
   bp.probs = (const coot::BatchProblem*)(base + o_probs);
   bp.tile_begin = (const long long*)(base + o_begin);
+  bp.tile_prob = (const int*)(base + o_map);
   bp.n_problems = n_problems;
   bp.n_tiles = tiles;
+  // a few tiles per queue pop: fewer atomics, still fine-grained balance
+  bp.chunk = std::max<long long>(1, std::min<long long>(8, tiles / ((long long)b->grid * 16)));
   for (size_t i = 0; i < an0.scalars.size(); ++i) bp.k[i] = scalar_bits(an0.scalars[i], an0.ct);
   bp.partials = base + o_part;
   bp.done = (unsigned*)(base + o_done);

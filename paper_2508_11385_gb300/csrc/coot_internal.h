@@ -112,6 +112,7 @@ struct LaunchCfg {
   int kidx = 0;  // index in Program::kernels
   int block = 256;
   int blocks_per_sm = 4;
+  int split = 0;  // col: warps per column (0: heuristic)
 };
 
 }  // namespace cg

@@ -131,8 +131,10 @@ __device__ __forceinline__ void str_kernel(const Params& p) {
   typename CsqOf<C>::type csq;
   if constexpr (RED == RED_CSQ) csq.set_mean(*p.mu);
   u32 err = 0;
-  A acc;
-  acc.init();
+  // one accumulator per vector lane: V independent addition chains
+  A accs[V];
+#pragma unroll
+  for (int l = 0; l < V; ++l) accs[l].init();
   const long long nr = p.n_rows, nc = p.n_cols, cpc = p.units_per_col;
   const long long units = cpc * nc;
   const long long step = (long long)blockDim.x * V;
@@ -161,57 +163,61 @@ __device__ __forceinline__ void str_kernel(const Params& p) {
       const long long i = i0 + g * step;
       if (full[g]) {
         C y[V];
-        if constexpr (sizeof(C) == 8 && RED != RED_NONE) {
-          // FP64: pre-sum the group pairwise, one addition into the chain
-          A part;
-          part.init();
 #pragma unroll
-          for (int l = 0; l < V; ++l) y[l] = eval_elem<T, RED>(x[g], k, err, l, part, csq);
-          acc.merge(part);
-        } else {
-#pragma unroll
-          for (int l = 0; l < V; ++l) y[l] = eval_elem<T, RED>(x[g], k, err, l, acc, csq);
-        }
+        for (int l = 0; l < V; ++l) y[l] = eval_elem<T, RED>(x[g], k, err, l, accs[l], csq);
         if constexpr (OUT) IO<S>::template store<V>(at_out<S>(p.out, i, j, p.out_ld), y);
       } else {
 #pragma unroll
         for (int l = 0; l < V; ++l)
           if (i + l < nr) {
-            C y = eval_elem<T, RED>(x[g], k, err, l, acc, csq);
+            C y = eval_elem<T, RED>(x[g], k, err, l, accs[l], csq);
             if constexpr (OUT) IO<S>::store1(at_out<S>(p.out, i + l, j, p.out_ld), y);
           }
       }
     }
   }
   if (err) atomicOr(p.err_flag, err);
-  if constexpr (RED != RED_NONE) finish_full<C, RED>(p, acc, smem);
+  if constexpr (RED != RED_NONE) {
+#pragma unroll
+    for (int l = 1; l < V; ++l) accs[0].merge(accs[l]);
+    finish_full<C, RED>(p, accs[0], smem);
+  }
 }
 
 // ---------------------------------------------------------------------------
-// col: map + per-column reduction (dim 0), one warp per column
+// col: map + per-column reduction (dim 0).  A group of G warps (G =
+// p.n_splits, a divisor of the warps per block) owns one column at a time and
+// splits its rows; the group's warp results are combined in shared memory in
+// warp order.  Every block runs the same number of column steps, so the
+// barriers are uniform.
 // ---------------------------------------------------------------------------
 template <class T, class S, int NS, int NK, int RED, int V, int U, bool OUT>
 __device__ __forceinline__ void col_kernel(const Params& p) {
   typedef typename ctype<S>::type C;
   typedef typename AccOf<C>::type A;
+  __shared__ A wsum[32];
   Scal<C, NK> k;
 #pragma unroll
   for (int q = 0; q < NK; ++q) k.k[q] = scalar_from_bits<C>(p.k[q]);
   typename CsqOf<C>::type csq;
   u32 err = 0;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long wpb = blockDim.x >> 5;
+  const long long G = p.n_splits;  // warps per column
+  const long long gpb = wpb / G;   // columns per block step
+  const long long gi = warp / G, wm = warp % G;
   const long long nr = p.n_rows, nc = p.n_cols;
   const long long step = 32LL * V;
-  for (long long j = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); j < nc; j += (long long)gridDim.x * wpb) {
+  for (long long base = (long long)blockIdx.x * gpb; base < nc; base += (long long)gridDim.x * gpb) {
+    const long long j = base + gi;
     A acc;
     acc.init();
-    for (long long i0 = (long long)lane * V; i0 < nr; i0 += step * U) {
+    for (long long i0 = (wm * 32 + lane) * V; j < nc && i0 < nr; i0 += G * step * U) {
       Vals<C, NS, V> x[U];
       bool full[U];
 #pragma unroll
       for (int g = 0; g < U; ++g) {
-        const long long i = i0 + g * step;
+        const long long i = i0 + g * G * step;
         full[g] = (i + V <= nr);
         if (full[g]) {
 #pragma unroll
@@ -226,7 +232,7 @@ __device__ __forceinline__ void col_kernel(const Params& p) {
       }
 #pragma unroll
       for (int g = 0; g < U; ++g) {
-        const long long i = i0 + g * step;
+        const long long i = i0 + g * G * step;
         if (full[g]) {
           C y[V];
 #pragma unroll
@@ -243,7 +249,18 @@ __device__ __forceinline__ void col_kernel(const Params& p) {
       }
     }
     acc = warp_reduce(acc);
-    if (lane == 0) write_result<C, RED>(p, acc, j, p.div);
+    if (G == 1) {
+      if (lane == 0 && j < nc) write_result<C, RED>(p, acc, j, p.div);
+    } else {
+      if (lane == 0) wsum[warp] = acc;
+      __syncthreads();
+      if (wm == 0 && lane == 0 && j < nc) {
+        A a = wsum[gi * G];
+        for (long long w = 1; w < G; ++w) a.merge(wsum[gi * G + w]);
+        write_result<C, RED>(p, a, j, p.div);
+      }
+      __syncthreads();
+    }
   }
   if (err) atomicOr(p.err_flag, err);
 }
@@ -569,17 +586,15 @@ __device__ __forceinline__ void batch_kernel(const BatchParams bp) {
   u32 err = 0;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   for (;;) {
-    __syncthreads();  // everyone is done with the previous tile and s_tile
-    if (threadIdx.x == 0) s_tile = (long long)atomicAdd(&bp.queue[0], 1u);
+    __syncthreads();  // everyone is done with the previous chunk and s_tile
+    if (threadIdx.x == 0) s_tile = (long long)atomicAdd(&bp.queue[0], (unsigned int)bp.chunk);
     __syncthreads();
-    const long long t = s_tile;
-    if (t >= bp.n_tiles) break;
-    // problem owning tile t: largest pb with tile_begin[pb] <= t
-    long long lo = 0, hi = bp.n_problems - 1;
-    while (lo < hi) {
-      long long mid = (lo + hi + 1) >> 1;
-      if (bp.tile_begin[mid] <= t) lo = mid; else hi = mid - 1;
-    }
+    const long long t0 = s_tile;
+    if (t0 >= bp.n_tiles) break;
+    const long long t1 = (t0 + bp.chunk < bp.n_tiles) ? t0 + bp.chunk : bp.n_tiles;
+    for (long long t = t0; t < t1; ++t) {
+    if (t > t0) __syncthreads();  // the previous tile's shared-memory reads are done
+    const long long lo = bp.tile_prob[t];
     const BatchProblem& pr = bp.probs[lo];
     const long long nr = pr.n_rows, nc = pr.n_cols;
     const long long lt = t - pr.tile_begin;
@@ -657,6 +672,7 @@ __device__ __forceinline__ void batch_kernel(const BatchParams bp) {
         }
       }
     }
+    }  // tiles of the chunk
   }
   if (err) atomicOr(bp.err_flag, err);
   // the last block out resets the queue for the next launch

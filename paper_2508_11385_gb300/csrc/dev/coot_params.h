@@ -56,9 +56,11 @@ struct BatchProblem {
 
 struct BatchParams {
   const BatchProblem* probs;
-  const long long* tile_begin;  // n_problems + 1 prefix (for the binary search)
+  const long long* tile_begin;  // n_problems + 1 prefix of the tile counts
+  const int* tile_prob;         // owning problem of every tile
   long long n_problems;
   long long n_tiles;
+  long long chunk;              // tiles taken from the queue at a time
   unsigned long long k[COOT_MAX_SCALARS_DEV];
   void* red_out;     // one result per problem (nullable)
   void* partials;    // one accumulator per tile

@@ -461,7 +461,7 @@ Program make_program(const Analysis& an, Family fam, bool var_two_pass) {
     }
   } else if (fam == F_COL || fam == F_ROW) {
     const char* fn = (fam == F_COL) ? "col" : "row";
-    std::vector<std::pair<int, int>> cvu = {{V, 1}, {V, 2}, {1, 4}};
+    std::vector<std::pair<int, int>> cvu = {{V, 1}, {V, 2}, {V, 4}, {1, 4}};
     for (auto [v, u] : cvu) {
       snprintf(buf, sizeof buf, "coot_%s_v%du%d", fn, v, u);
       wrap(buf, 512, std::string(fn) + "_kernel<T_t, S_t, " + std::to_string(NS) + ", " + std::to_string(NK) + ", " +
