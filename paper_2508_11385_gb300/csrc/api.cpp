@@ -498,6 +498,9 @@ coot_status tune(coot_ctx* ctx, const cg::Analysis& an, const cg::Choice& ch, co
         }
         if (st) break;
         std::sort(times, times + 3);
+        if (log_enabled(ctx))
+          fprintf(stderr, "[cootgb]   candidate %s block %d x %d/SM split %d grid %d: %.4f ms\n", k.name.c_str(),
+                  block, bps, split, L.grid, times[1]);
         if (times[1] < best_ms) {
           best_ms = times[1];
           best->kidx = ki;

@@ -6,7 +6,7 @@
 //         optional full reduction; 128-bit vector loads/stores when every
 //         read and the output are 16-byte aligned along columns.
 //   col   the same map with a per-column reduction (sum/mean along dim 0):
-//         one warp per column.
+//         a group of warps per column.
 //   row   the same map with a per-row reduction (dim 1): a thread owns V
 //         consecutive rows and walks a range of columns; column ranges are
 //         combined by the last block of each row block.
@@ -16,8 +16,8 @@
 //   adj   fused adjoint of a scalar loss sum(tree): forward values are
 //         recomputed per element and the reverse sweep writes every leaf's
 //         gradient.
-//   batch persistent kernel over many problems pulling 32x32 tiles from a
-//         queue, with a per-problem reduction.
+//   batch persistent kernel over many problems pulling chunks of 32x32 tiles
+//         from a queue, with a per-problem reduction.
 // Cross-block combines use a ticket counter: the block that arrives last
 // combines the partials in a fixed order and resets the counter.  Nothing
 // ever waits on another block.
@@ -400,6 +400,16 @@ __device__ __forceinline__ void tile_kernel(const Params& p) {
   for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
     const long long ti = t % ntr, tj = t / ntr;
     const long long i = ti * TILE + tx;
+    Vals<C, NS, TILE_Q> x;
+    // direct reads first: they stay in flight while transposed blocks are staged
+#pragma unroll
+    for (int w = 0; w < TILE_Q; ++w) {
+      const long long j = tj * TILE + ty + TILE_PH * w;
+      const bool ok = (i < nr && j < nc);
+#pragma unroll
+      for (int s = 0; s < NS; ++s)
+        if (!((TRMASK >> s) & 1)) x.v[s][w] = ok ? IO<S>::load1(at<S>(p.src[s], i, j, p.ld[s])) : C(0);
+    }
     if constexpr (NTR > 0) {
       __syncthreads();  // the previous tile's shared reads are done
       int q = 0;
@@ -415,22 +425,14 @@ __device__ __forceinline__ void tile_kernel(const Params& p) {
           ++q;
         }
       __syncthreads();
-    }
-    Vals<C, NS, TILE_Q> x;
+      q = 0;
 #pragma unroll
-    for (int w = 0; w < TILE_Q; ++w) {
-      const long long j = tj * TILE + ty + TILE_PH * w;
-      const bool ok = (i < nr && j < nc);
-      int q = 0;
-#pragma unroll
-      for (int s = 0; s < NS; ++s) {
+      for (int s = 0; s < NS; ++s)
         if ((TRMASK >> s) & 1) {
-          x.v[s][w] = stage[q][tx][ty + TILE_PH * w];
+#pragma unroll
+          for (int w = 0; w < TILE_Q; ++w) x.v[s][w] = stage[q][tx][ty + TILE_PH * w];
           ++q;
-        } else {
-          x.v[s][w] = ok ? IO<S>::load1(at<S>(p.src[s], i, j, p.ld[s])) : C(0);
         }
-      }
     }
     A racc;  // per-row partial over this tile's columns (DIM 1)
     racc.init();
@@ -568,8 +570,63 @@ __device__ __forceinline__ void adj_kernel(const Params& p) {
 }
 
 // ---------------------------------------------------------------------------
-// batch: persistent kernel over tiles of many problems
+// batch: persistent kernel over the tiles of many problems.
+//   Blocks take `chunk` consecutive tiles at a time from an atomic queue (the
+//   next pop is issued before the current chunk is processed, so its latency
+//   is hidden).  A problem's tiles inside one chunk are accumulated in
+//   registers and flushed once: a problem whose tiles all lie in one chunk
+//   writes its result directly; otherwise the flush leaves one partial per
+//   tile range and the flush that completes the problem combines its
+//   partials in tile order.  Chunks start at multiples of `chunk`, so the
+//   grouping -- and the result -- does not depend on which block took which
+//   chunk.
 // ---------------------------------------------------------------------------
+template <class C, class A>
+__device__ __forceinline__ void batch_write(const BatchParams& bp, long long p, const A& a, long long count) {
+  typedef typename rtype<C>::type R;
+  if constexpr (is_int_c<C>::value) {
+    ((long long*)bp.red_out)[p] = a.ivalue();
+  } else {
+    double v = a.value();
+    if (bp.mean) v /= (double)count;
+    ((R*)bp.red_out)[p] = (R)v;
+  }
+}
+
+template <class C, class A>
+__device__ __forceinline__ void batch_flush(const BatchParams& bp, long long p, long long ta, long long tb, A acc,
+                                            A* smem, int* am_last) {
+  acc = block_reduce(acc, smem);
+  const BatchProblem& pr = bp.probs[p];
+  const long long ntile = bp.tile_begin[p + 1] - pr.tile_begin;
+  const long long count = pr.n_rows * pr.n_cols;
+  if (tb - ta == ntile) {  // the whole problem is in this group
+    if (threadIdx.x == 0) batch_write<C>(bp, p, acc, count);
+    return;
+  }
+  if (threadIdx.x == 0) {
+    A zero;
+    zero.init();
+    ((A*)bp.partials)[ta] = acc;
+    for (long long t = ta + 1; t < tb; ++t) ((A*)bp.partials)[t] = zero;
+    __threadfence();
+    unsigned int d = atomicAdd(&bp.done[p], (unsigned int)(tb - ta));
+    *am_last = ((long long)d + (tb - ta) == ntile);
+  }
+  __syncthreads();
+  if (*am_last) {
+    __threadfence();
+    A a;
+    a.init();
+    for (long long s = threadIdx.x; s < ntile; s += blockDim.x) a.merge(load_cg(&((const A*)bp.partials)[pr.tile_begin + s]));
+    a = block_reduce(a, smem);
+    if (threadIdx.x == 0) {
+      batch_write<C>(bp, p, a, count);
+      bp.done[p] = 0u;
+    }
+  }
+}
+
 template <class T, class S, int NS, int NK, int TRMASK, bool RED>
 __device__ __forceinline__ void batch_kernel(const BatchParams bp) {
   typedef typename ctype<S>::type C;
@@ -577,7 +634,7 @@ __device__ __forceinline__ void batch_kernel(const BatchParams bp) {
   constexpr int NTR = popc<TRMASK>::value;
   __shared__ C stage[NTR > 0 ? NTR : 1][TILE][TILE + 1];
   __shared__ A smem[32];
-  __shared__ long long s_tile;
+  __shared__ long long s_next;
   __shared__ int am_last;
   Scal<C, NK> k;
 #pragma unroll
@@ -585,94 +642,82 @@ __device__ __forceinline__ void batch_kernel(const BatchParams bp) {
   typename CsqOf<C>::type csq;
   u32 err = 0;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  for (;;) {
-    __syncthreads();  // everyone is done with the previous chunk and s_tile
-    if (threadIdx.x == 0) s_tile = (long long)atomicAdd(&bp.queue[0], (unsigned int)bp.chunk);
-    __syncthreads();
-    const long long t0 = s_tile;
-    if (t0 >= bp.n_tiles) break;
+  if (threadIdx.x == 0) s_next = (long long)atomicAdd(&bp.queue[0], (unsigned int)bp.chunk);
+  __syncthreads();
+  long long t0 = s_next;
+  while (t0 < bp.n_tiles) {
+    unsigned int nxt = 0;
+    if (threadIdx.x == 0) nxt = atomicAdd(&bp.queue[0], (unsigned int)bp.chunk);  // used after the chunk
     const long long t1 = (t0 + bp.chunk < bp.n_tiles) ? t0 + bp.chunk : bp.n_tiles;
-    for (long long t = t0; t < t1; ++t) {
-    if (t > t0) __syncthreads();  // the previous tile's shared-memory reads are done
-    const long long lo = bp.tile_prob[t];
-    const BatchProblem& pr = bp.probs[lo];
-    const long long nr = pr.n_rows, nc = pr.n_cols;
-    const long long lt = t - pr.tile_begin;
-    const long long ti = lt % pr.n_tile_rows, tj = lt / pr.n_tile_rows;
-    const long long i = ti * TILE + tx;
-    if constexpr (NTR > 0) {
-      int q = 0;
-#pragma unroll
-      for (int s = 0; s < NS; ++s)
-        if ((TRMASK >> s) & 1) {
-          const long long vr = tj * TILE + tx;
-#pragma unroll
-          for (int w = 0; w < TILE_Q; ++w) {
-            const long long vc = ti * TILE + ty + TILE_PH * w;
-            stage[q][ty + TILE_PH * w][tx] = (vr < nc && vc < nr) ? IO<S>::load1(at<S>(pr.src[s], vr, vc, pr.ld[s])) : C(0);
-          }
-          ++q;
-        }
-      __syncthreads();
-    }
-    Vals<C, NS, TILE_Q> x;
-#pragma unroll
-    for (int w = 0; w < TILE_Q; ++w) {
-      const long long j = tj * TILE + ty + TILE_PH * w;
-      const bool ok = (i < nr && j < nc);
-      int q = 0;
-#pragma unroll
-      for (int s = 0; s < NS; ++s) {
-        if ((TRMASK >> s) & 1) {
-          x.v[s][w] = stage[q][tx][ty + TILE_PH * w];
-          ++q;
-        } else {
-          x.v[s][w] = ok ? IO<S>::load1(at<S>(pr.src[s], i, j, pr.ld[s])) : C(0);
-        }
-      }
-    }
     A acc;
     acc.init();
-#pragma unroll
-    for (int w = 0; w < TILE_Q; ++w) {
-      const long long j = tj * TILE + ty + TILE_PH * w;
-      if (i < nr && j < nc) {
-        C y = eval_elem<T, RED ? RED_SUM : RED_NONE>(x, k, err, w, acc, csq);
-        if (bp.has_out) IO<S>::store1(at_out<S>(pr.out, i, j, pr.out_ld), y);
-      }
-    }
-    if constexpr (RED) {
-      acc = block_reduce(acc, smem);
-      const long long ntile = bp.tile_begin[lo + 1] - pr.tile_begin;
-      if (threadIdx.x == 0) {
-        ((A*)bp.partials)[t] = acc;
-        __threadfence();
-        unsigned int d = atomicAdd(&bp.done[lo], 1u);
-        am_last = (d == (unsigned int)(ntile - 1));
-      }
-      __syncthreads();
-      if (am_last) {
-        // the problem's last tile: combine its tiles' partials in tile order
-        __threadfence();
-        A a;
-        a.init();
-        for (long long s = threadIdx.x; s < ntile; s += blockDim.x)
-          a.merge(load_cg(&((const A*)bp.partials)[pr.tile_begin + s]));
-        a = block_reduce(a, smem);
-        if (threadIdx.x == 0) {
-          typedef typename rtype<C>::type R;
-          if constexpr (is_int_c<C>::value) {
-            ((long long*)bp.red_out)[lo] = a.ivalue();
-          } else {
-            double v = a.value();
-            if (bp.mean) v /= (double)(nr * nc);
-            ((R*)bp.red_out)[lo] = (R)v;
-          }
-          bp.done[lo] = 0u;
+    long long cur = -1, gfirst = t0;
+    for (long long t = t0; t < t1; ++t) {
+      const long long p = bp.tile_prob[t];
+      if constexpr (RED) {
+        if (p != cur && cur >= 0) {
+          batch_flush<C>(bp, cur, gfirst, t, acc, smem, &am_last);
+          acc.init();
+          gfirst = t;
         }
       }
+      cur = p;
+      const BatchProblem& pr = bp.probs[p];
+      const long long nr = pr.n_rows, nc = pr.n_cols;
+      const long long lt = t - pr.tile_begin;
+      const long long ti = lt % pr.n_tile_rows, tj = lt / pr.n_tile_rows;
+      const long long i = ti * TILE + tx;
+      Vals<C, NS, TILE_Q> x;
+      // direct reads first: they stay in flight while transposed blocks are staged
+#pragma unroll
+      for (int w = 0; w < TILE_Q; ++w) {
+        const long long j = tj * TILE + ty + TILE_PH * w;
+        const bool ok = (i < nr && j < nc);
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+          if (!((TRMASK >> s) & 1)) x.v[s][w] = ok ? IO<S>::load1(at<S>(pr.src[s], i, j, pr.ld[s])) : C(0);
+      }
+      if constexpr (NTR > 0) {
+        int q = 0;
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+          if ((TRMASK >> s) & 1) {
+            const long long vr = tj * TILE + tx;
+#pragma unroll
+            for (int w = 0; w < TILE_Q; ++w) {
+              const long long vc = ti * TILE + ty + TILE_PH * w;
+              stage[q][ty + TILE_PH * w][tx] =
+                  (vr < nc && vc < nr) ? IO<S>::load1(at<S>(pr.src[s], vr, vc, pr.ld[s])) : C(0);
+            }
+            ++q;
+          }
+        __syncthreads();
+        q = 0;
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+          if ((TRMASK >> s) & 1) {
+#pragma unroll
+            for (int w = 0; w < TILE_Q; ++w) x.v[s][w] = stage[q][tx][ty + TILE_PH * w];
+            ++q;
+          }
+      }
+#pragma unroll
+      for (int w = 0; w < TILE_Q; ++w) {
+        const long long j = tj * TILE + ty + TILE_PH * w;
+        if (i < nr && j < nc) {
+          C y = eval_elem<T, RED ? RED_SUM : RED_NONE>(x, k, err, w, acc, csq);
+          if (bp.has_out) IO<S>::store1(at_out<S>(pr.out, i, j, pr.out_ld), y);
+        }
+      }
+      if constexpr (NTR > 0) __syncthreads();  // shared reads done before the next staging
     }
-    }  // tiles of the chunk
+    if constexpr (RED) {
+      if (cur >= 0) batch_flush<C>(bp, cur, gfirst, t1, acc, smem, &am_last);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s_next = (long long)nxt;
+    __syncthreads();
+    t0 = s_next;
   }
   if (err) atomicOr(bp.err_flag, err);
   // the last block out resets the queue for the next launch

@@ -1,0 +1,46 @@
+"""Mistakes planted in a copy of the oracle (on the CPU) must fail its pins:
+each mutation below is a plausible slip -- swapped operands, a wrong index, a
+wrong normalisation, a sign error in the compensation, a dropped term of the
+error bound -- and the pin suite run against the mutated build must fail."""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+MUTATIONS = [
+    ("int minus operands", "case B_MINUS: return wrap32(a - b);", "case B_MINUS: return wrap32(b - a);"),
+    ("fp minus operands", "      r = a - b;\n", "      r = b - a;\n"),
+    ("trans index", "int64_t s = i + j * r, d = j + i * c;", "int64_t s = i + j * r, d = i + j * r;"),
+    ("var normalisation", "double den = (kind == R_VAR0) ? (double)(n - 1) : (double)n;", "double den = (double)n;"),
+    ("compensation sign", "c += (s - t) + x[i];", "c += (t - s) + x[i];"),
+    ("submat offsets", "int64_t s = (r0 + i) + (c0 + j) * x->r, d = i + j * nr;",
+     "int64_t s = (c0 + i) + (r0 + j) * x->r, d = i + j * nr;"),
+    ("product bound term", "e = mulb(a, bb) + mulb(b, ba)", "e = mulb(a, bb)"),
+    ("exp bound propagation", "bv = (ba == 0.0) ? 0.0 : v * expm1(ba);", "bv = 0.0;"),
+    ("mean divisor", "        s = s / (double)len;", "        s = s / (double)nout;"),
+    ("gradient of division", "case B_DIV: da = 1.0 / b; db = -a / (b * b);", "case B_DIV: da = 1.0 / b; db = a / (b * b);"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_planted_mistake_fails_the_pins(tmp_path, name, old, new):
+    src = open(os.path.join(ROOT, "oracle", "oracle.c")).read()
+    assert src.count(old) == 1, "mutation anchor not found: " + name
+    work = tmp_path / "repo"
+    (work / "oracle").mkdir(parents=True)
+    for f in ("oracle.h", "__init__.py"):
+        shutil.copy(os.path.join(ROOT, "oracle", f), work / "oracle" / f)
+    (work / "oracle" / "oracle.c").write_text(src.replace(old, new))
+    shutil.copytree(os.path.join(ROOT, "tests"), work / "tests",
+                    ignore=shutil.ignore_patterns("__pycache__", "test_oracle_mutations.py", "test_gpu*", "test_abi.py",
+                                                  "test_multiproc.py"))
+    shutil.copytree(os.path.join(ROOT, "paper_2508_11385_gb300"), work / "paper_2508_11385_gb300",
+                    ignore=shutil.ignore_patterns("__pycache__", "_build", "*.so", "csrc"))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                        "tests/test_oracle_pins.py"], cwd=work, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, "the pins did not catch the planted mistake '%s'" % name
+    assert "failed" in r.stdout
