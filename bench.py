@@ -119,6 +119,18 @@ def build_expr(program, mats):
             red = coot.sum(st[-1], 0)
         elif tok == "sum:1":
             red = coot.sum(st[-1], 1)
+        elif tok == "mean":
+            red = coot.mean(st[-1], -1)
+        elif tok == "norm":
+            red = coot.norm(st[-1])
+        elif tok == "norm:fro":
+            red = coot.norm(st[-1], "fro")
+        elif tok in ("var", "var:1"):
+            red = coot.var(st[-1], 1 if tok == "var:1" else 0)
+        elif tok == "dot":
+            b, a = st.pop(), st.pop()
+            red = coot.dot(a, b)
+            st.append(red.expr)
         else:
             raise ValueError(tok)
     return st[-1], red
@@ -532,7 +544,7 @@ def run_extras(args, leaves, calls, per_tree_ms, bytes_per, dev, stream, peak):
     except Exception as e:
         res["adjoint"] = {"error": repr(e)[:300]}
     try:
-        res["precision"] = bench_precision(dev, stream)
+        res["precision"] = bench_precision(dev, stream, errors=args.precision_errors)
     except Exception as e:
         res["precision"] = {"error": repr(e)[:300]}
     return res
@@ -700,32 +712,53 @@ def bench_adjoint(dev, stream):
             "note": "fwd reads W, X, Y (12N bytes); the adjoint reads them again and writes dW, dX (20N)"}
 
 
-def bench_precision(dev, stream):
+def bench_precision(dev, stream, errors=False):
+    """Reductions over 2^28-element signed-lognormal vectors (FP32/BF16/FP16,
+    and FP64 var), through prepared C-ABI calls.  With errors=True also the
+    relative error of each result against the FP64 oracle, for float-float
+    (default), Kahan and plain FP32 accumulation."""
     import torch
 
-    import paper_2508_11385_gb300 as coot
     from paper_2508_11385_gb300 import workloads
 
     out = {}
     n = 1 << 28
-    for dt in ("f32", "bf16", "f16"):
+    sp = stream.cuda_stream
+    progs = [("accu", "A accu"), ("dot", "A B dot"), ("norm", "A norm"), ("var", "A var")]
+    for dt in ("f32", "bf16", "f16", "f64"):
         x, y = workloads.precision(dt, n=n, device=dev)
-        X, Yv = coot.Mat(x), coot.Mat(y)
+        host = None
+        if errors:
+            import oracle
+
+            host = [workloads.to_numpy_colmajor(t) for t in (x, y)]
         d = {}
-        for name, red in (("accu", coot.accu(X)), ("dot", coot.dot(X, Yv)), ("norm", coot.norm(X)),
-                          ("var", coot.var(X))):
-            red.eval()
-            ms = time_calls(lambda: red.eval(), stream, reps=5)
-            b = coot.last_launch(dev)["algorithmic_bytes"]
-            d[name] = {"ms": round(ms, 4), "gbs": round(b / ms / 1e6, 1)}
+        for name, prog in progs:
+            if dt == "f64" and name != "var":
+                continue
+            c = Call(prog, [x, y])
+            c(sp)
+            torch.cuda.synchronize()
+            ms = time_calls(lambda: c(sp), stream, reps=10)
+            info = c.info()
+            ent = {"ms": round(ms, 4), "gbs": round(info["algorithmic_bytes"] / ms / 1e6, 1), "kernel": info["kernel"]}
+            if errors:
+                ref = float(oracle.evaluate(prog, host, dt).value[0, 0])
+                ent["rel_err"] = abs(float(c.result().item()) - ref) / abs(ref)
+                if dt != "f64":
+                    for mode in ("kahan", "plain"):
+                        os.environ["COOT_ACCUM"] = mode
+                        try:
+                            c2 = Call(prog, [x, y])
+                            c2(sp)
+                            torch.cuda.synchronize()
+                            ent["rel_err_" + mode] = abs(float(c2.result().item()) - ref) / abs(ref)
+                        finally:
+                            del os.environ["COOT_ACCUM"]
+            d[name] = ent
         out[dt] = d
-        del x, y
+        del x, y, host
         torch.cuda.empty_cache()
-    x, _ = workloads.precision("f64", n=n, device=dev)
-    red = coot.var(coot.Mat(x))
-    red.eval()
-    ms = time_calls(lambda: red.eval(), stream, reps=5)
-    out["f64_var"] = {"ms": round(ms, 4), "gbs": round(2 * n * 8 / ms / 1e6, 1)}
     return out
 
 
@@ -787,6 +820,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--quick", action="store_true", help="headline only (no side workloads)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--precision-errors", action="store_true",
+                    help="also report each precision result's error against the FP64 oracle (slow)")
     ap.add_argument("--only", default=None, help="time one tree of the workload (profiling); implies --quick")
     args = ap.parse_args()
     if args.only:

@@ -62,6 +62,7 @@ struct Analysis {
   int red_mode = RED_NONE;  // device mode of the (last) pass
   bool has_out = false;
   int root_op = -1;         // op of the root (R_DOT needs N_SCHUR)
+  int accum = 0;            // FP32 accumulation: 0 float-float, 1 Kahan, 2 plain ($COOT_ACCUM)
 };
 
 // Validate the call and canonicalise the tree.  `out` and `red_out` checks

@@ -435,21 +435,37 @@ enum { RED_NONE = 0, RED_SUM = 1, RED_DOT = 2, RED_SSQ = 3, RED_MEAN1 = 4, RED_C
 // product", SIAM J. Sci. Comput. 2005, algorithm Sum2/Dot2): hi is the
 // running sum, every TwoSum / TwoProduct error term is added into lo, and
 // the result is hi + lo.  Error ~ u|S| + (n u)^2 sum|x| for chain length n.
+// COOT_ACCUM_PLAIN / COOT_ACCUM_KAHAN (set per tree, for the accuracy
+// comparison) replace the per-term step by a plain FP32 sum or by Kahan's
+// compensated summation (lo holds minus Kahan's correction term).
 struct AccF {
   float hi, lo;
   __device__ __forceinline__ void init() { hi = 0.f; lo = 0.f; }
   __device__ __forceinline__ void add(float x) {
+#if defined(COOT_ACCUM_PLAIN)
+    hi = __fadd_rn(hi, x);
+#elif defined(COOT_ACCUM_KAHAN)
+    float y = __fadd_rn(x, lo);  // lo = -c
+    float t = __fadd_rn(hi, y);
+    lo = __fsub_rn(y, __fsub_rn(t, hi));
+    hi = t;
+#else
     float s = __fadd_rn(hi, x);
     float bp = __fsub_rn(s, hi);
     float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
     hi = s;
     lo = __fadd_rn(lo, e);
+#endif
   }
   __device__ __forceinline__ void add_prod(float a, float b) {
+#if defined(COOT_ACCUM_PLAIN) || defined(COOT_ACCUM_KAHAN)
+    add(__fmul_rn(a, b));
+#else
     float p = __fmul_rn(a, b);
     float e = __fmaf_rn(a, b, -p);  // exact error of the product
     add(p);
     lo = __fadd_rn(lo, e);
+#endif
   }
   __device__ __forceinline__ void merge(const AccF& o) {
     add(o.hi);

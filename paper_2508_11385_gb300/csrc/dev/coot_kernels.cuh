@@ -66,6 +66,32 @@ __device__ __forceinline__ typename X::C eval_elem(const X& x, const K& k, u32& 
   }
 }
 
+// The element's value y and, in c, its term of the reduction, for the
+// pairwise path of 16-bit storage: products and squares of two 16-bit values
+// are exact in FP32 (at most 22 significant bits), and sums of two such terms
+// are exact unless their exponents differ by more than 15, so the V terms of
+// one vector load are summed pairwise in FP32 before a single float-float
+// addition.
+template <class T, int RED, class X, class K, class Q>
+__device__ __forceinline__ typename X::C eval_term(const X& x, const K& k, u32& err, int l, const Q& csq,
+                                                   typename X::C& c) {
+  typedef typename X::C C;
+  if constexpr (RED == RED_DOT) {
+    C a = T::A::ev(x, k, err, l), b = T::B::ev(x, k, err, l);
+    c = op_mul(a, b);
+    return c;
+  } else {
+    C y = T::ev(x, k, err, l);
+    if constexpr (RED == RED_SSQ) c = op_mul(y, y);
+    else if constexpr (RED == RED_CSQ) {
+      C d = csq.centred(y);
+      c = op_mul(d, d);
+    } else
+      c = y;
+    return y;
+  }
+}
+
 // the final value written for one reduction output
 template <class C, int RED, class A>
 __device__ __forceinline__ void write_result(const Params& p, const A& a, long long idx, double div) {
@@ -163,8 +189,21 @@ __device__ __forceinline__ void str_kernel(const Params& p) {
       const long long i = i0 + g * step;
       if (full[g]) {
         C y[V];
+        if constexpr (sizeof(S) == 2 && RED != RED_NONE) {
+          // 16-bit storage: pairwise sum of the vector's terms, then one
+          // float-float addition (spread over the accumulators by group)
+          C c[V];
 #pragma unroll
-        for (int l = 0; l < V; ++l) y[l] = eval_elem<T, RED>(x[g], k, err, l, accs[l], csq);
+          for (int l = 0; l < V; ++l) y[l] = eval_term<T, RED>(x[g], k, err, l, csq, c[l]);
+#pragma unroll
+          for (int w = V / 2; w >= 1; w /= 2)
+#pragma unroll
+            for (int l = 0; l < w; ++l) c[l] = op_add(c[l], c[l + w]);
+          accs[g % V].add(c[0]);
+        } else {
+#pragma unroll
+          for (int l = 0; l < V; ++l) y[l] = eval_elem<T, RED>(x[g], k, err, l, accs[l], csq);
+        }
         if constexpr (OUT) IO<S>::template store<V>(at_out<S>(p.out, i, j, p.out_ld), y);
       } else {
 #pragma unroll

@@ -112,6 +112,13 @@ coot_status analyse(const coot_tree* tree, const coot_mat* leaves, int32_t n_lea
   an->esz = esize(dt);
   an->ct = (dt == COOT_F64) ? CT_F64 : (dt == COOT_I32 ? CT_I32 : CT_F32);
   const bool is_int = (an->ct == CT_I32);
+  // FP32 accumulation mode (float-float unless $COOT_ACCUM selects the
+  // Kahan or plain variant for an accuracy comparison)
+  if (an->ct == CT_F32) {
+    const char* am = getenv("COOT_ACCUM");
+    if (am && !strcmp(am, "kahan")) an->accum = 1;
+    if (am && !strcmp(am, "plain")) an->accum = 2;
+  }
 
   // ---- per-node checks and shape inference
   std::vector<int64_t> R(nn), Cc(nn);
@@ -409,6 +416,8 @@ Program make_program(const Analysis& an, Family fam, bool var_two_pass) {
   const bool OUT = an.has_out;
   const int V = vmax(an);
   std::ostringstream src, sig;
+  if (an.accum == 1) src << "#define COOT_ACCUM_KAHAN 1\n";
+  if (an.accum == 2) src << "#define COOT_ACCUM_PLAIN 1\n";
   src << "#include \"coot_kernels.cuh\"\nusing namespace coot;\n";
   src << "typedef " << S << " S_t;\n";
   src << "typedef " << an.type_str << " T_t;\n";
@@ -500,7 +509,8 @@ Program make_program(const Analysis& an, Family fam, bool var_two_pass) {
     add("coot_batch", 1, 1, 256);
   }
   sig << "cootgb1|" << family_name(fam) << "|" << S << "|ns" << NS << "|nk" << NK << "|red" << an.red_mode << "|dim"
-      << an.red.dim << "|out" << OUT << "|tr" << an.trmask << "|var" << var_two_pass << "|" << an.type_str;
+      << an.red.dim << "|out" << OUT << "|tr" << an.trmask << "|var" << var_two_pass
+      << (an.accum == 1 ? "|kahan" : (an.accum == 2 ? "|plain" : "")) << "|" << an.type_str;
   pg.signature = sig.str();
   pg.source = src.str();
   return pg;
