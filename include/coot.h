@@ -245,6 +245,31 @@ COOT_API coot_status coot_codegen(const coot_tree* tree, const coot_mat* leaves,
 COOT_API coot_status coot_compile(const coot_tree* tree, const coot_mat* leaves, int32_t n_leaves,
                          const coot_mat* out, coot_reduce red, size_t* cubin_bytes);
 
+/* ---- evaluation without allocation -----------------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory while they run (a host framework that owns
+ * every byte it hands out through its own pool or arena, or code in a region
+ * where an allocation would synchronise the device or is not allowed).
+ *
+ * coot_sum_rows_f32_noalloc: per-row sums of an F32 column-major matrix x
+ * (sum(X, 1); mean(X, 1) when mean != 0) written to out[0 .. x->n_rows) on
+ * the device, with the same per-row reduction kernel and float-float
+ * accumulation as coot_eval with R_SUM / R_MEAN along dim 1.  It runs on the
+ * current CUDA device, needs no context, compiles nothing at run time and
+ * allocates nothing: its scratch (one ticket per block of 1024 rows, 256 for
+ * unaligned input, and the partial sums of the column splits) is a static
+ * device array of COOT_NOALLOC_SCRATCH_BYTES that every GPU loading the
+ * library holds until exit.  The first call on a device looks the array's
+ * address up (cudaGetSymbolAddress) and queries the device; make that first
+ * call before any stream capture.  Every call clears the tickets it uses, so
+ * a failed earlier call leaves nothing behind; all calls on a device share
+ * the array, so calls that can run at the same time on the GPU (different
+ * streams without ordering) race -- issue them on one stream.  A matrix with
+ * more rows than the tickets cover (4096 x 1024 = 4,194,304 rows; 1,048,576
+ * when x is not 16-byte aligned) is rejected with COOT_ERR_UNSUPPORTED. */
+#define COOT_NOALLOC_SCRATCH_BYTES (4u << 20)
+COOT_API coot_status coot_sum_rows_f32_noalloc(const coot_mat* x, int32_t mean, float* out, coot_stream stream);
+
 /* ---- errors and diagnostics --------------------------------------------------
  * coot_check_device_flag: wait for `stream`, read and clear the context's
  * device error flags (bit 0: an INT32 division by zero).  Returns

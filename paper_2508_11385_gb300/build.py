@@ -42,7 +42,8 @@ def _dev_headers():
 
 
 def _sources():
-    return sorted(glob.glob(os.path.join(CSRC, "*.cpp")))
+    cu = [p for p in glob.glob(os.path.join(CSRC, "*.cu")) if os.path.basename(p) != "dev_check.cu"]
+    return sorted(glob.glob(os.path.join(CSRC, "*.cpp")) + cu)
 
 
 def _inputs():
@@ -86,7 +87,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     home = cuda_home()
     nvcc = os.path.join(home, "bin", "nvcc")
     inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC, "-I", os.path.join(home, "include")]
-    common = ARCH + ["-std=c++17", "-O2", "-lineinfo", "-Xcompiler", "-fPIC,-Wall,-fvisibility=hidden"] + inc
+    common = ARCH + ["-std=c++17", "-O2", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC,-Wall,-fvisibility=hidden"] + inc
     procs, objs = [], []
     for src in _sources():
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")

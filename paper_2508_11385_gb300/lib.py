@@ -95,6 +95,7 @@ _SIGS = {
     "coot_signature": ([_TP, _MP, ctypes.c_int32, _MP, coot_reduce, ctypes.c_char_p, ctypes.c_size_t], _S),
     "coot_codegen": ([_TP, _MP, ctypes.c_int32, _MP, coot_reduce, ctypes.c_char_p, ctypes.c_size_t], _S),
     "coot_compile": ([_TP, _MP, ctypes.c_int32, _MP, coot_reduce, ctypes.POINTER(ctypes.c_size_t)], _S),
+    "coot_sum_rows_f32_noalloc": ([_MP, ctypes.c_int32, _P, _P], _S),
     "coot_check_device_flag": ([_P, _P, ctypes.POINTER(ctypes.c_uint32)], _S),
     "coot_last_launch": ([_P, ctypes.POINTER(coot_launch_info)], _S),
     "coot_last_error": ([], ctypes.c_char_p),
@@ -227,6 +228,12 @@ def coot_compile(tree, leaves, out, red) -> int:
     lv = _arr(leaves)
     _check(_lib.coot_compile(ctypes.byref(tree), lv, len(leaves), _ptr(out), red, ctypes.byref(n)))
     return n.value
+
+
+def coot_sum_rows_f32_noalloc(x, mean, out_ptr, stream):
+    """Per-row sums (or means) of an F32 matrix into out_ptr without any
+    allocation (see include/coot.h)."""
+    _check(_lib.coot_sum_rows_f32_noalloc(ctypes.byref(x), int(mean), out_ptr, stream))
 
 
 def coot_check_device_flag(ctx, stream) -> int:
