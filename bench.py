@@ -285,6 +285,23 @@ def algorithmic_bytes(program, n, esz):
 # ---------------------------------------------------------------------------
 # the GPU arm
 # ---------------------------------------------------------------------------
+def run_side(args):
+    """One side workload alone (for profiling): prints its JSON."""
+    import torch
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    os.environ.setdefault("COOT_TUNE", "on")
+    stream = torch.cuda.current_stream(dev)
+    fn = {"batched": lambda: bench_batched(args, dev, stream), "adjoint": lambda: bench_adjoint(dev, stream),
+          "precision": lambda: bench_precision(dev, stream, errors=args.precision_errors),
+          "graph_chain": lambda: bench_graph(dev, stream)}[args.only]
+    print(json.dumps({args.only: fn()}))
+
+
 def run_gpu(args):
     import torch
 
@@ -580,7 +597,11 @@ def bench_batched(args, dev, stream):
     ms = time_calls(lambda: L.coot_batch_run(plan, red_out.data_ptr(), sp), stream, reps=10)
     info = L.coot_last_launch(ctx)
     # 50,000 separate fused launches of the same tree (first 2,000 timed, scaled)
-    nsep = min(npb, 2000)
+    nsep = min(npb, args.batch_separate)
+    if nsep == 0:
+        L.coot_batch_destroy(plan)
+        return {"n_problems": npb, "ms": round(ms, 4), "exprs_per_s": round(npb / (ms / 1e3), 1),
+                "gbs": round(info["algorithmic_bytes"] / ms / 1e6, 1)}
     sep = []
     for q in range(nsep):
         cm = [probs[3 * q], probs[3 * q + 1], probs[3 * q + 2]]
@@ -817,6 +838,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_MAIN)
     ap.add_argument("--batch-problems", type=int, default=50000)
+    ap.add_argument("--batch-separate", type=int, default=2000,
+                    help="problems timed as separate launches for the comparison (0: skip)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--quick", action="store_true", help="headline only (no side workloads)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -825,10 +848,14 @@ def main():
     ap.add_argument("--only", default=None, help="time one tree of the workload (profiling); implies --quick")
     args = ap.parse_args()
     if args.only:
-        if args.only not in [t[0] for t in TREES]:
-            ap.error("--only: one of %s" % ", ".join(t[0] for t in TREES))
+        side = ("batched", "adjoint", "precision", "graph_chain")
+        if args.only not in [t[0] for t in TREES] + list(side):
+            ap.error("--only: one of %s" % ", ".join([t[0] for t in TREES] + list(side)))
         args.quick = True
         args.no_cpu = True
+        if args.only in side:
+            run_side(args)
+            return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
