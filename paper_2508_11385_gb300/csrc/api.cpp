@@ -230,7 +230,8 @@ void shape_launch(coot_ctx* ctx, const cg::Analysis& an, const cg::Choice& ch, c
     L->partial_bytes = (nsp > 1) ? (size_t)(nsp * R * 8) : 0;
     L->tickets = (size_t)nrb;
   } else if (ch.fam == cg::F_TILE) {
-    const int64_t ntr = ceil_div(R, 32), ntc = ceil_div(C, 32);
+    // tilev tiles are 32 x vec rows tall; the scalar tile kernel's 32
+    const int64_t ntr = ceil_div(R, 32 * std::max(k.vec, 1)), ntc = ceil_div(C, 32);
     const int64_t tiles = ntr * ntc;
     L->grid = (int)std::max<int64_t>(1, std::min(tiles, resident));
     if (an.red.dim == 0) {
@@ -988,7 +989,16 @@ extern "C" coot_status coot_batch_create(coot_ctx* ctx, const coot_tree* tree, i
   b->kname = "coot_batch";
   b->n_problems = n_problems;
   b->has_red = red.kind != COOT_R_NONE;
-  b->block = 256;
+  {
+    // one warp per tile; as many warps per block as the transposed tiles'
+    // shared memory allows within 48 KiB (the kernel computes the same)
+    int ntr = 0;
+    for (int s = 0; s < 32; ++s) ntr += (an0.trmask >> s) & 1;
+    const int csize = (an0.ct == cg::CT_F64) ? 8 : 4;
+    const int per = 32 * 33 * csize * std::max(ntr, 1);
+    const int warps = (ntr == 0) ? 8 : std::max(1, std::min(8, 49152 / per));
+    b->block = 32 * warps;
+  }
   b->grid = ctx->sms * occupancy(m, b->kname, b->block);
   b->algorithmic_bytes = bytes;
   coot::BatchParams& bp = b->bp;
@@ -999,7 +1009,7 @@ extern "C" coot_status coot_batch_create(coot_ctx* ctx, const coot_tree* tree, i
   bp.n_problems = n_problems;
   bp.n_tiles = tiles;
   // a few tiles per queue pop: fewer atomics, still fine-grained balance
-  bp.chunk = std::max<long long>(1, std::min<long long>(8, tiles / ((long long)b->grid * 16)));
+  bp.chunk = std::max<long long>(1, std::min<long long>(8, tiles / ((long long)b->grid * (b->block / 32) * 8)));
   for (size_t i = 0; i < an0.scalars.size(); ++i) bp.k[i] = scalar_bits(an0.scalars[i], an0.ct);
   bp.partials = base + o_part;
   bp.done = (unsigned*)(base + o_done);

@@ -546,6 +546,139 @@ __device__ __forceinline__ void tile_kernel(const Params& p) {
 }
 
 // ---------------------------------------------------------------------------
+// tilev: vectorised variant of tile for trees without a dim reduction.
+//   Tile of TM = 32 V rows x 32 columns; thread (tx, ty) owns rows
+//   32 V ti + V tx .. + V-1 of columns 32 tj + ty + 8 w (w < 4), so direct
+//   reads and the output move V elements (16 bytes) per access.  A transposed
+//   slot's 32 x TM source block is read with consecutive threads on
+//   consecutive source rows into stage[q][column][row] (row stride TM + 4, a
+//   multiple of 16 bytes) and read back as one 16-byte vector per thread.
+// ---------------------------------------------------------------------------
+// V values of the compute type from 16-byte aligned shared memory, one
+// 16-byte access per 16 bytes
+struct __align__(16) W4 {
+  u32 w[4];
+};
+template <class C> struct FromWords;
+template <> struct FromWords<float> {
+  static constexpr int per = 4;
+  __device__ static float get(const u32* w, int l) { return __uint_as_float(w[l]); }
+};
+template <> struct FromWords<int> {
+  static constexpr int per = 4;
+  __device__ static int get(const u32* w, int l) { return (int)w[l]; }
+};
+template <> struct FromWords<double> {
+  static constexpr int per = 2;
+  __device__ static double get(const u32* w, int l) { return __hiloint2double((int)w[2 * l + 1], (int)w[2 * l]); }
+};
+template <class C, int V> __device__ __forceinline__ void lds_vec(const C* p, C (&v)[V]) {
+  constexpr int PER = FromWords<C>::per;
+  static_assert(V % PER == 0, "whole 16-byte groups");
+  const W4* q = reinterpret_cast<const W4*>(p);
+#pragma unroll
+  for (int n = 0; n < V / PER; ++n) {
+    W4 t = q[n];
+#pragma unroll
+    for (int l = 0; l < PER; ++l) v[n * PER + l] = FromWords<C>::get(t.w, l);
+  }
+}
+
+template <class T, class S, int NS, int NK, int RED, int TRMASK, bool OUT, int V>
+__device__ __forceinline__ void tilev_kernel(const Params& p) {
+  typedef typename ctype<S>::type C;
+  typedef typename AccOf<C>::type A;
+  constexpr int NTR = popc<TRMASK>::value;
+  constexpr int TM = TILE * V;
+  constexpr int SP = TM + 16 / (int)sizeof(C);
+  __shared__ __align__(16) C stage[NTR > 0 ? NTR : 1][TILE][SP];
+  __shared__ A smem[32];
+  Scal<C, NK> k;
+#pragma unroll
+  for (int q = 0; q < NK; ++q) k.k[q] = scalar_from_bits<C>(p.k[q]);
+  typename CsqOf<C>::type csq;
+  if constexpr (RED == RED_CSQ) csq.set_mean(*p.mu);
+  u32 err = 0;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const long long nr = p.n_rows, nc = p.n_cols;
+  const long long ntr = (nr + TM - 1) / TM, ntc = (nc + TILE - 1) / TILE;
+  const long long tiles = ntr * ntc;
+  A accs[V];
+#pragma unroll
+  for (int l = 0; l < V; ++l) accs[l].init();
+  for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const long long ti = t % ntr, tj = t / ntr;
+    const long long i0 = ti * TM + (long long)tx * V;
+    const bool fullr = (i0 + V <= nr);
+    Vals<C, NS, V> x[TILE_Q];
+    // direct reads first: in flight while transposed blocks are staged
+#pragma unroll
+    for (int w = 0; w < TILE_Q; ++w) {
+      const long long j = tj * TILE + ty + TILE_PH * w;
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        if ((TRMASK >> s) & 1) continue;
+        if (j < nc && fullr) {
+          IO<S>::template load<V>(at<S>(p.src[s], i0, j, p.ld[s]), x[w].v[s]);
+        } else {
+#pragma unroll
+          for (int l = 0; l < V; ++l)
+            x[w].v[s][l] = (j < nc && i0 + l < nr) ? IO<S>::load1(at<S>(p.src[s], i0 + l, j, p.ld[s])) : C(0);
+        }
+      }
+    }
+    if constexpr (NTR > 0) {
+      __syncthreads();  // the previous tile's shared reads are done
+      int q = 0;
+#pragma unroll
+      for (int s = 0; s < NS; ++s)
+        if ((TRMASK >> s) & 1) {
+          const long long vr = tj * TILE + tx;  // view row = output column
+#pragma unroll 4
+          for (int m = ty; m < TM; m += TILE_PH) {
+            const long long vc = ti * TM + m;  // view column = output row
+            stage[q][tx][m] = (vr < nc && vc < nr) ? IO<S>::load1(at<S>(p.src[s], vr, vc, p.ld[s])) : C(0);
+          }
+          ++q;
+        }
+      __syncthreads();
+      q = 0;
+#pragma unroll
+      for (int s = 0; s < NS; ++s)
+        if ((TRMASK >> s) & 1) {
+#pragma unroll
+          for (int w = 0; w < TILE_Q; ++w) lds_vec<C, V>(&stage[q][ty + TILE_PH * w][tx * V], x[w].v[s]);
+          ++q;
+        }
+    }
+#pragma unroll
+    for (int w = 0; w < TILE_Q; ++w) {
+      const long long j = tj * TILE + ty + TILE_PH * w;
+      if (j >= nc) continue;
+      if (fullr) {
+        C y[V];
+#pragma unroll
+        for (int l = 0; l < V; ++l) y[l] = eval_elem<T, RED>(x[w], k, err, l, accs[l], csq);
+        if constexpr (OUT) IO<S>::template store<V>(at_out<S>(p.out, i0, j, p.out_ld), y);
+      } else {
+#pragma unroll
+        for (int l = 0; l < V; ++l)
+          if (i0 + l < nr) {
+            C y = eval_elem<T, RED>(x[w], k, err, l, accs[l], csq);
+            if constexpr (OUT) IO<S>::store1(at_out<S>(p.out, i0 + l, j, p.out_ld), y);
+          }
+      }
+    }
+  }
+  if (err) atomicOr(p.err_flag, err);
+  if constexpr (RED != RED_NONE) {
+#pragma unroll
+    for (int l = 1; l < V; ++l) accs[0].merge(accs[l]);
+    finish_full<C, RED>(p, accs[0], smem);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // adj: gradient of L = mult * sum(tree) with respect to every slot
 // ---------------------------------------------------------------------------
 template <class T, class S, int NS, int NK, int V, int U>
@@ -609,17 +742,30 @@ __device__ __forceinline__ void adj_kernel(const Params& p) {
 }
 
 // ---------------------------------------------------------------------------
-// batch: persistent kernel over the tiles of many problems.
-//   Blocks take `chunk` consecutive tiles at a time from an atomic queue (the
-//   next pop is issued before the current chunk is processed, so its latency
-//   is hidden).  A problem's tiles inside one chunk are accumulated in
-//   registers and flushed once: a problem whose tiles all lie in one chunk
-//   writes its result directly; otherwise the flush leaves one partial per
-//   tile range and the flush that completes the problem combines its
-//   partials in tile order.  Chunks start at multiples of `chunk`, so the
-//   grouping -- and the result -- does not depend on which block took which
-//   chunk.
+// batch: persistent kernel over the 32x32 tiles of many problems, one warp
+// per tile.  Every warp takes `chunk` consecutive tiles at a time from an
+// atomic queue (the next pop is issued before the current chunk is worked
+// on, so its latency is hidden) and synchronises only with itself: a
+// transposed read goes through the warp's own padded shared-memory tile.
+// A problem's tiles inside one chunk are accumulated in registers and
+// flushed once -- a problem whose tiles all lie in one chunk writes its
+// result directly; otherwise each flush leaves one partial per tile range and
+// the flush that completes the problem combines its partials in tile order.
+// Chunks start at multiples of `chunk`, so the grouping -- and the result --
+// does not depend on which warp took which chunk.
 // ---------------------------------------------------------------------------
+constexpr int BATCH_WARPS = 8;  // warps per block when shared memory allows
+constexpr int BATCH_COLS = 8;   // tile columns loaded per step
+
+// warps per block: each warp owns NTR padded tiles of the compute type, and
+// the block's static shared memory stays within 48 KiB (the host launches
+// blockDim.x = 32 * batch_warps)
+template <int NTR, int CSIZE> struct BatchWarps {
+  static constexpr int per = TILE * (TILE + 1) * CSIZE * (NTR > 0 ? NTR : 1);
+  static constexpr int fit = 49152 / per;
+  static constexpr int value = NTR == 0 ? BATCH_WARPS : (fit < 1 ? 1 : (fit > BATCH_WARPS ? BATCH_WARPS : fit));
+};
+
 template <class C, class A>
 __device__ __forceinline__ void batch_write(const BatchParams& bp, long long p, const A& a, long long count) {
   typedef typename rtype<C>::type R;
@@ -633,33 +779,32 @@ __device__ __forceinline__ void batch_write(const BatchParams& bp, long long p, 
 }
 
 template <class C, class A>
-__device__ __forceinline__ void batch_flush(const BatchParams& bp, long long p, long long ta, long long tb, A acc,
-                                            A* smem, int* am_last) {
-  acc = block_reduce(acc, smem);
+__device__ __forceinline__ void batch_flush(const BatchParams& bp, long long p, long long ta, long long tb, A acc) {
+  const int lane = threadIdx.x & 31;
+  acc = warp_reduce(acc);  // every lane holds the sum
   const BatchProblem& pr = bp.probs[p];
   const long long ntile = bp.tile_begin[p + 1] - pr.tile_begin;
   const long long count = pr.n_rows * pr.n_cols;
   if (tb - ta == ntile) {  // the whole problem is in this group
-    if (threadIdx.x == 0) batch_write<C>(bp, p, acc, count);
+    if (lane == 0) batch_write<C>(bp, p, acc, count);
     return;
   }
-  if (threadIdx.x == 0) {
-    A zero;
-    zero.init();
-    ((A*)bp.partials)[ta] = acc;
-    for (long long t = ta + 1; t < tb; ++t) ((A*)bp.partials)[t] = zero;
-    __threadfence();
-    unsigned int d = atomicAdd(&bp.done[p], (unsigned int)(tb - ta));
-    *am_last = ((long long)d + (tb - ta) == ntile);
-  }
-  __syncthreads();
-  if (*am_last) {
+  A zero;
+  zero.init();
+  for (long long t = ta + 1 + lane; t < tb; t += 32) ((A*)bp.partials)[t] = zero;
+  if (lane == 0) ((A*)bp.partials)[ta] = acc;
+  __threadfence();
+  __syncwarp();
+  unsigned int d = 0;
+  if (lane == 0) d = atomicAdd(&bp.done[p], (unsigned int)(tb - ta));
+  d = __shfl_sync(0xffffffffu, d, 0);
+  if ((long long)d + (tb - ta) == ntile) {
     __threadfence();
     A a;
     a.init();
-    for (long long s = threadIdx.x; s < ntile; s += blockDim.x) a.merge(load_cg(&((const A*)bp.partials)[pr.tile_begin + s]));
-    a = block_reduce(a, smem);
-    if (threadIdx.x == 0) {
+    for (long long s = lane; s < ntile; s += 32) a.merge(load_cg(&((const A*)bp.partials)[pr.tile_begin + s]));
+    a = warp_reduce(a);
+    if (lane == 0) {
       batch_write<C>(bp, p, a, count);
       bp.done[p] = 0u;
     }
@@ -671,22 +816,21 @@ __device__ __forceinline__ void batch_kernel(const BatchParams bp) {
   typedef typename ctype<S>::type C;
   typedef typename AccOf<C>::type A;
   constexpr int NTR = popc<TRMASK>::value;
-  __shared__ C stage[NTR > 0 ? NTR : 1][TILE][TILE + 1];
-  __shared__ A smem[32];
-  __shared__ long long s_next;
-  __shared__ int am_last;
+  constexpr int BW = BatchWarps<NTR, (int)sizeof(C)>::value;
+  __shared__ C stage_all[BW][NTR > 0 ? NTR : 1][TILE][TILE + 1];
   Scal<C, NK> k;
 #pragma unroll
   for (int q = 0; q < NK; ++q) k.k[q] = scalar_from_bits<C>(bp.k[q]);
   typename CsqOf<C>::type csq;
   u32 err = 0;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  if (threadIdx.x == 0) s_next = (long long)atomicAdd(&bp.queue[0], (unsigned int)bp.chunk);
-  __syncthreads();
-  long long t0 = s_next;
+  const int tx = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  C (*stage)[TILE][TILE + 1] = stage_all[wid];
+  unsigned int pop = 0;
+  if (tx == 0) pop = atomicAdd(&bp.queue[0], (unsigned int)bp.chunk);
+  long long t0 = (long long)__shfl_sync(0xffffffffu, pop, 0);
   while (t0 < bp.n_tiles) {
     unsigned int nxt = 0;
-    if (threadIdx.x == 0) nxt = atomicAdd(&bp.queue[0], (unsigned int)bp.chunk);  // used after the chunk
+    if (tx == 0) nxt = atomicAdd(&bp.queue[0], (unsigned int)bp.chunk);  // used after the chunk
     const long long t1 = (t0 + bp.chunk < bp.n_tiles) ? t0 + bp.chunk : bp.n_tiles;
     A acc;
     acc.init();
@@ -695,7 +839,7 @@ __device__ __forceinline__ void batch_kernel(const BatchParams bp) {
       const long long p = bp.tile_prob[t];
       if constexpr (RED) {
         if (p != cur && cur >= 0) {
-          batch_flush<C>(bp, cur, gfirst, t, acc, smem, &am_last);
+          batch_flush<C>(bp, cur, gfirst, t, acc);
           acc.init();
           gfirst = t;
         }
@@ -705,64 +849,58 @@ __device__ __forceinline__ void batch_kernel(const BatchParams bp) {
       const long long nr = pr.n_rows, nc = pr.n_cols;
       const long long lt = t - pr.tile_begin;
       const long long ti = lt % pr.n_tile_rows, tj = lt / pr.n_tile_rows;
-      const long long i = ti * TILE + tx;
-      Vals<C, NS, TILE_Q> x;
-      // direct reads first: they stay in flight while transposed blocks are staged
-#pragma unroll
-      for (int w = 0; w < TILE_Q; ++w) {
-        const long long j = tj * TILE + ty + TILE_PH * w;
-        const bool ok = (i < nr && j < nc);
-#pragma unroll
-        for (int s = 0; s < NS; ++s)
-          if (!((TRMASK >> s) & 1)) x.v[s][w] = ok ? IO<S>::load1(at<S>(pr.src[s], i, j, pr.ld[s])) : C(0);
-      }
+      const long long r0 = ti * TILE, c0 = tj * TILE;
+      const int nrows = (int)((nr - r0 < TILE) ? nr - r0 : TILE);  // warp-uniform extents
+      const int ncols = (int)((nc - c0 < TILE) ? nc - c0 : TILE);
       if constexpr (NTR > 0) {
+        // stage the transposed blocks: view(c0 + tx, r0 + m) -> stage[q][m][tx]
         int q = 0;
 #pragma unroll
         for (int s = 0; s < NS; ++s)
           if ((TRMASK >> s) & 1) {
-            const long long vr = tj * TILE + tx;
-#pragma unroll
-            for (int w = 0; w < TILE_Q; ++w) {
-              const long long vc = ti * TILE + ty + TILE_PH * w;
-              stage[q][ty + TILE_PH * w][tx] =
-                  (vr < nc && vc < nr) ? IO<S>::load1(at<S>(pr.src[s], vr, vc, pr.ld[s])) : C(0);
-            }
+            for (int m = 0; m < nrows; ++m)
+              stage[q][m][tx] = (tx < ncols) ? IO<S>::load1(at<S>(pr.src[s], c0 + tx, r0 + m, pr.ld[s])) : C(0);
             ++q;
           }
-        __syncthreads();
-        q = 0;
-#pragma unroll
-        for (int s = 0; s < NS; ++s)
-          if ((TRMASK >> s) & 1) {
-#pragma unroll
-            for (int w = 0; w < TILE_Q; ++w) x.v[s][w] = stage[q][tx][ty + TILE_PH * w];
-            ++q;
-          }
+        __syncwarp();
       }
+      const bool row_ok = tx < nrows;
+      for (int jb = 0; jb < ncols; jb += BATCH_COLS) {
+        Vals<C, NS, BATCH_COLS> x;
 #pragma unroll
-      for (int w = 0; w < TILE_Q; ++w) {
-        const long long j = tj * TILE + ty + TILE_PH * w;
-        if (i < nr && j < nc) {
-          C y = eval_elem<T, RED ? RED_SUM : RED_NONE>(x, k, err, w, acc, csq);
-          if (bp.has_out) IO<S>::store1(at_out<S>(pr.out, i, j, pr.out_ld), y);
+        for (int jj = 0; jj < BATCH_COLS; ++jj) {
+          const bool ok = row_ok && (jb + jj < ncols);
+          int q = 0;
+#pragma unroll
+          for (int s = 0; s < NS; ++s) {
+            if ((TRMASK >> s) & 1) {
+              x.v[s][jj] = ok ? stage[q][tx][jb + jj] : C(0);
+              ++q;
+            } else {
+              x.v[s][jj] = ok ? IO<S>::load1(at<S>(pr.src[s], r0 + tx, c0 + jb + jj, pr.ld[s])) : C(0);
+            }
+          }
+        }
+#pragma unroll
+        for (int jj = 0; jj < BATCH_COLS; ++jj) {
+          if (row_ok && jb + jj < ncols) {
+            C y = eval_elem<T, RED ? RED_SUM : RED_NONE>(x, k, err, jj, acc, csq);
+            if (bp.has_out) IO<S>::store1(at_out<S>(pr.out, r0 + tx, c0 + jb + jj, pr.out_ld), y);
+          }
         }
       }
-      if constexpr (NTR > 0) __syncthreads();  // shared reads done before the next staging
+      if constexpr (NTR > 0) __syncwarp();  // stage reads done before the next tile
     }
     if constexpr (RED) {
-      if (cur >= 0) batch_flush<C>(bp, cur, gfirst, t1, acc, smem, &am_last);
+      if (cur >= 0) batch_flush<C>(bp, cur, gfirst, t1, acc);
     }
-    __syncthreads();
-    if (threadIdx.x == 0) s_next = (long long)nxt;
-    __syncthreads();
-    t0 = s_next;
+    t0 = (long long)__shfl_sync(0xffffffffu, nxt, 0);
   }
   if (err) atomicOr(bp.err_flag, err);
-  // the last block out resets the queue for the next launch
-  if (threadIdx.x == 0) {
+  // the last warp out resets the queue for the next launch
+  if (tx == 0) {
     unsigned int e = atomicAdd(&bp.queue[1], 1u);
-    if (e == gridDim.x - 1) {
+    if (e == gridDim.x * (blockDim.x >> 5) - 1) {
       bp.queue[0] = 0u;
       bp.queue[1] = 0u;
     }

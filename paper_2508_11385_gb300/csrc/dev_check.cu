@@ -36,3 +36,12 @@ K(chk_adj_f32, 512, (adj_kernel<T3, float, 3, 1, 4, 2>))
 extern "C" __global__ void __launch_bounds__(256) chk_batch(const __grid_constant__ BatchParams p) {
   batch_kernel<T3, float, 3, 1, 4, true>(p);
 }
+extern "C" __global__ void __launch_bounds__(256) chk_batch_f64_2tr(const __grid_constant__ BatchParams p) {
+  batch_kernel<eGlue<Leaf<0>, Leaf<1>, eglue_plus>, double, 2, 0, 3, true>(p);
+}
+extern "C" __global__ void __launch_bounds__(256) chk_batch_f32_2tr(const __grid_constant__ BatchParams p) {
+  batch_kernel<eGlue<Leaf<0>, Leaf<1>, eglue_plus>, float, 2, 0, 3, false>(p);
+}
+K(chk_tilev_f32, 256, (tilev_kernel<T3, float, 3, 1, RED_NONE, 4, true, 4>))
+K(chk_tilev_bf16, 256, (tilev_kernel<T3, bf16, 3, 1, RED_SUM, 4, true, 8>))
+K(chk_tilev_f64, 256, (tilev_kernel<T3, double, 3, 1, RED_CSQ, 4, false, 2>))

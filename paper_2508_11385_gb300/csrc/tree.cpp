@@ -366,6 +366,17 @@ Choice choose(const Analysis& an, const coot_mat* leaves, const coot_mat* out) {
   ch.it_cols = an.nc;
   if (an.any_trans) {
     ch.fam = F_TILE;
+    // the vectorised tile kernel reads direct slots and writes the output
+    // V elements at a time down each column
+    bool vec = true;
+    for (const Slot& s : an.slots) {
+      if (s.trans) continue;
+      const coot_mat& L = leaves[s.leaf];
+      uintptr_t org = (uintptr_t)L.data + (uintptr_t)((s.r0 + s.c0 * mat_ld(L)) * an.esz);
+      if (org % 16 || (s.vc > 1 && (mat_ld(L) * an.esz) % 16)) vec = false;
+    }
+    if (out && ((uintptr_t)out->data % 16 || (an.nc > 1 && (mat_ld(*out) * an.esz) % 16))) vec = false;
+    ch.vec_ok = vec;
     return ch;
   }
   const int dim = an.red.dim;
@@ -479,7 +490,25 @@ Program make_program(const Analysis& an, Family fam, bool var_two_pass) {
     }
   } else if (fam == F_TILE) {
     const int dim = an.red.dim;
+    // vectorised variant (no dim reduction) when its staged tiles fit in
+    // static shared memory: NTR x 32 x (32 V + pad) values of the compute type
+    int ntr = 0;
+    for (size_t s = 0; s < an.slots.size(); ++s) ntr += an.slots[s].trans ? 1 : 0;
+    const int csize = (an.ct == CT_F64) ? 8 : 4;
+    const int tm = 32 * V, sp = tm + 16 / csize;
+    const bool tv = (dim == -1) && (ntr * 32 * sp * csize + 2048 <= 49152);
+    auto tilev = [&](const char* name, const char* red) {
+      wrap(name, 256, std::string("tilev_kernel<T_t, S_t, ") + std::to_string(NS) + ", " + std::to_string(NK) + ", " +
+                          red + ", " + std::to_string(an.trmask) + ", " +
+                          (std::string(name).find("_p1") != std::string::npos ? "false" : outs) + ", " +
+                          std::to_string(V) + ">");
+      add(name, V, 2, 256);
+    };
     if (var_two_pass) {
+      if (tv) {
+        tilev("coot_tilev_p1", "RED_MEAN1");
+        tilev("coot_tilev_p2", "RED_CSQ");
+      }
       wrap("coot_tile_p1", 256, std::string("tile_kernel<T_t, S_t, ") + std::to_string(NS) + ", " + std::to_string(NK) +
                                     ", RED_MEAN1, -1, " + std::to_string(an.trmask) + ", false>");
       add("coot_tile_p1", 1, 1, 256);
@@ -491,6 +520,7 @@ Program make_program(const Analysis& an, Family fam, bool var_two_pass) {
                                  ", " + red_name(an.red_mode) + ", " + std::to_string(dim) + ", " +
                                  std::to_string(an.trmask) + ", " + outs + ">");
       add("coot_tile", 1, 1, 256);
+      if (tv) tilev("coot_tilev", red_name(an.red_mode));
     }
   } else if (fam == F_ADJ) {
     std::vector<std::pair<int, int>> avu = {{V, 1}, {V, 2}, {1, 4}};
