@@ -329,12 +329,13 @@ def run_gpu(args):
     for _, _, _, c in calls:
         c(sp)
     torch.cuda.synchronize()
-    bytes_per = {}
+    bytes_per, kernel_of = {}, {}
     launches_per_step = 0
     for name, _, _, c in calls:
         c(sp)
         info = c.info()
         bytes_per[name] = info["algorithmic_bytes"]
+        kernel_of[name] = "%s grid %d x %d" % (info["kernel"], info["grid"], info["block"])
     torch.cuda.synchronize()
     for name, _, _, c in calls:
         c(sp)
@@ -429,7 +430,7 @@ def run_gpu(args):
         "peak_gbs": peak,
         "roofline": roofline,
         "per_tree": {name: {"ms": round(per_tree_ms[name], 4), "gbs": round(bytes_per[name] / per_tree_ms[name] / 1e6, 1),
-                            "bytes": bytes_per[name]} for name in per_tree_ms},
+                            "bytes": bytes_per[name], "kernel": kernel_of[name]} for name in per_tree_ms},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
         "e2e": e2e,

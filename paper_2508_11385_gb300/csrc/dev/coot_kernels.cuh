@@ -634,11 +634,14 @@ __device__ __forceinline__ void tilev_kernel(const Params& p) {
       for (int s = 0; s < NS; ++s)
         if ((TRMASK >> s) & 1) {
           const long long vr = tj * TILE + tx;  // view row = output column
-#pragma unroll 4
-          for (int m = ty; m < TM; m += TILE_PH) {
-            const long long vc = ti * TM + m;  // view column = output row
-            stage[q][tx][m] = (vr < nc && vc < nr) ? IO<S>::load1(at<S>(p.src[s], vr, vc, p.ld[s])) : C(0);
+          C v[TM / TILE_PH];  // all of this thread's staging loads in flight at once
+#pragma unroll
+          for (int u = 0; u < TM / TILE_PH; ++u) {
+            const long long vc = ti * TM + ty + TILE_PH * u;  // view column = output row
+            v[u] = (vr < nc && vc < nr) ? IO<S>::load1(at<S>(p.src[s], vr, vc, p.ld[s])) : C(0);
           }
+#pragma unroll
+          for (int u = 0; u < TM / TILE_PH; ++u) stage[q][tx][ty + TILE_PH * u] = v[u];
           ++q;
         }
       __syncthreads();
@@ -832,11 +835,13 @@ __device__ __forceinline__ void batch_kernel(const BatchParams bp) {
     unsigned int nxt = 0;
     if (tx == 0) nxt = atomicAdd(&bp.queue[0], (unsigned int)bp.chunk);  // used after the chunk
     const long long t1 = (t0 + bp.chunk < bp.n_tiles) ? t0 + bp.chunk : bp.n_tiles;
+    // the chunk's owning problems, one lane per tile (chunk <= 32)
+    const int myp = (t0 + tx < t1) ? bp.tile_prob[t0 + tx] : 0;
     A acc;
     acc.init();
     long long cur = -1, gfirst = t0;
     for (long long t = t0; t < t1; ++t) {
-      const long long p = bp.tile_prob[t];
+      const long long p = __shfl_sync(0xffffffffu, myp, (int)(t - t0));
       if constexpr (RED) {
         if (p != cur && cur >= 0) {
           batch_flush<C>(bp, cur, gfirst, t, acc);
@@ -858,8 +863,17 @@ __device__ __forceinline__ void batch_kernel(const BatchParams bp) {
 #pragma unroll
         for (int s = 0; s < NS; ++s)
           if ((TRMASK >> s) & 1) {
-            for (int m = 0; m < nrows; ++m)
-              stage[q][m][tx] = (tx < ncols) ? IO<S>::load1(at<S>(pr.src[s], c0 + tx, r0 + m, pr.ld[s])) : C(0);
+            // 16 loads in flight per lane, then 16 shared stores
+            for (int m0 = 0; m0 < nrows; m0 += 16) {
+              C v[16];
+#pragma unroll
+              for (int u = 0; u < 16; ++u)
+                v[u] = (tx < ncols && m0 + u < nrows) ? IO<S>::load1(at<S>(pr.src[s], c0 + tx, r0 + m0 + u, pr.ld[s]))
+                                                      : C(0);
+#pragma unroll
+              for (int u = 0; u < 16; ++u)
+                if (m0 + u < nrows) stage[q][m0 + u][tx] = v[u];
+            }
             ++q;
           }
         __syncwarp();
