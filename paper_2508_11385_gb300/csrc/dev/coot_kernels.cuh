@@ -758,7 +758,7 @@ __device__ __forceinline__ void adj_kernel(const Params& p) {
 // does not depend on which warp took which chunk.
 // ---------------------------------------------------------------------------
 constexpr int BATCH_WARPS = 8;  // warps per block when shared memory allows
-constexpr int BATCH_COLS = 8;   // tile columns loaded per step
+constexpr int BATCH_COLS = 16;  // tile columns loaded per step
 
 // warps per block: each warp owns NTR padded tiles of the compute type, and
 // the block's static shared memory stays within 48 KiB (the host launches
@@ -850,7 +850,9 @@ __device__ __forceinline__ void batch_kernel(const BatchParams bp) {
         }
       }
       cur = p;
-      const BatchProblem& pr = bp.probs[p];
+      // the problem record in registers: the tile's stores to Y could alias
+      // it as far as the compiler knows, which would reload every field
+      const BatchProblem pr = bp.probs[p];
       const long long nr = pr.n_rows, nc = pr.n_cols;
       const long long lt = t - pr.tile_begin;
       const long long ti = lt % pr.n_tile_rows, tj = lt / pr.n_tile_rows;
@@ -863,15 +865,15 @@ __device__ __forceinline__ void batch_kernel(const BatchParams bp) {
 #pragma unroll
         for (int s = 0; s < NS; ++s)
           if ((TRMASK >> s) & 1) {
-            // 16 loads in flight per lane, then 16 shared stores
-            for (int m0 = 0; m0 < nrows; m0 += 16) {
-              C v[16];
+            // 32 loads in flight per lane, then 32 shared stores
+            for (int m0 = 0; m0 < nrows; m0 += 32) {
+              C v[32];
 #pragma unroll
-              for (int u = 0; u < 16; ++u)
+              for (int u = 0; u < 32; ++u)
                 v[u] = (tx < ncols && m0 + u < nrows) ? IO<S>::load1(at<S>(pr.src[s], c0 + tx, r0 + m0 + u, pr.ld[s]))
                                                       : C(0);
 #pragma unroll
-              for (int u = 0; u < 16; ++u)
+              for (int u = 0; u < 32; ++u)
                 if (m0 + u < nrows) stage[q][m0 + u][tx] = v[u];
             }
             ++q;
