@@ -534,6 +534,168 @@ static int reduce(ctx_t* cx, int kind, val_t* x, val_t* y, orc_result* res) {
 }
 
 /* ------------------------------------------------------------------ */
+/* statistics along a dimension: min, max, index_min, index_max, prod, */
+/* var, stddev (Armadillo's statistics functions, Sec. 2)               */
+/* ------------------------------------------------------------------ */
+/*
+ * dim -1 reduces all elements (index outputs are column-major linear
+ * indices), dim 0 each column (index outputs are row indices), dim 1 each
+ * row (index outputs are column indices).  Readings: NaN elements are passed
+ * over by min/max and their indices; ties give the first occurrence; an empty
+ * set gives NaN (0 for INT32 trees) and index -1.  prod multiplies in order
+ * with a double-double product (error ~ n u^2); INT32 trees multiply modulo
+ * 2^64.  var/stddev are the two-pass definitions of the all-element form.
+ */
+enum { S_MIN, S_MAX, S_IMIN, S_IMAX, S_PROD, S_VAR, S_STD };
+
+static int reduce_stat(ctx_t* cx, int op, int dim, int norm, val_t* x, orc_result* res) {
+  const int64_t r = x->r, c = x->c;
+  const int64_t nout = (dim == -1) ? 1 : (dim == 0 ? c : r);
+  const int64_t len = (dim == -1) ? r * c : (dim == 0 ? r : c);
+  const int idx_out = (op == S_IMIN || op == S_IMAX);
+  if (cx->is_int && (op == S_VAR || op == S_STD)) {
+    snprintf(cx->err, 256, "var/stddev are not defined for INT32 trees");
+    return -1;
+  }
+  const int out_int = cx->is_int || idx_out;
+  res->is_reduction = 1;
+  if (alloc_result(res, out_int, dim == 1 ? r : 1, dim == 0 ? c : 1)) return -1;
+  res->is_int = out_int;
+  double* buf = (double*)malloc((size_t)(len ? len : 1) * sizeof(double));
+  if (!buf) return -1;
+  for (int64_t o = 0; o < nout; ++o) {
+    /* element t of output o sits at column-major position q(t) */
+#define QPOS(t) ((dim == -1) ? (t) : (dim == 0 ? (t) + o * r : o + (t) * r))
+    if (op == S_MIN || op == S_MAX || op == S_IMIN || op == S_IMAX) {
+      const int want_min = (op == S_MIN || op == S_IMIN);
+      int64_t best = -1;
+      double bv = 0.0, bmax = 0.0;
+      int64_t biv = 0;
+      for (int64_t t = 0; t < len; ++t) {
+        const int64_t q = QPOS(t);
+        if (cx->is_int) {
+          const int64_t v = x->iv[q];
+          if (best < 0 || (want_min ? v < biv : v > biv)) {
+            best = t;
+            biv = v;
+          }
+        } else {
+          const double v = x->v[q];
+          if (isnan(v)) continue;
+          if (x->b[q] > bmax) bmax = x->b[q];
+          if (best < 0 || (want_min ? v < bv : v > bv)) {
+            best = t;
+            bv = v;
+          }
+        }
+      }
+      if (idx_out) {
+        res->iv[o] = (best < 0) ? -1 : ((dim == -1) ? QPOS(best) : best);
+      } else if (cx->is_int) {
+        res->iv[o] = (best < 0) ? 0 : biv;
+      } else {
+        res->v[o] = (best < 0) ? NAN : bv;
+        /* any element may become the extreme within its own bound */
+        res->b[o] = (best < 0) ? 0.0 : finite_or_zero_bound(bv, bmax);
+      }
+    } else if (op == S_PROD) {
+      if (cx->is_int) {
+        uint64_t p = 1;
+        for (int64_t t = 0; t < len; ++t) p *= (uint64_t)x->iv[QPOS(t)];
+        res->iv[o] = (int64_t)p;
+      } else {
+        double ph = 1.0, pl = 0.0, rel = 0.0;
+        int zero = 0;
+        for (int64_t t = 0; t < len; ++t) {
+          const int64_t q = QPOS(t);
+          const double v = x->v[q];
+          const double p = ph * v;
+          const double e = fma(ph, v, -p); /* exact error of ph*v */
+          pl = fma(pl, v, e);
+          ph = p;
+          if (v == 0.0)
+            zero = 1;
+          else if (x->b[q] != 0.0)
+            rel += x->b[q] / fabs(v);
+        }
+        const double pv = ph + pl;
+        res->v[o] = pv;
+        res->b[o] = zero ? 0.0 : finite_or_zero_bound(pv, fabs(pv) * rel);
+      }
+    } else { /* S_VAR, S_STD */
+      double s2, e2;
+      if (len == 0) {
+        s2 = NAN;
+        e2 = 0.0;
+      } else if (len == 1) {
+        s2 = 0.0;
+        e2 = 0.0;
+      } else {
+        for (int64_t t = 0; t < len; ++t) buf[t] = x->v[QPOS(t)];
+        const double mu = orc_sum_neumaier(buf, len) / (double)len;
+        double eb = 0.0;
+        for (int64_t t = 0; t < len; ++t) {
+          const double d = buf[t] - mu;
+          eb += mulb(2.0 * d, x->b[QPOS(t)]);
+          buf[t] = d * d;
+        }
+        const double den = (norm == 0) ? (double)(len - 1) : (double)len;
+        s2 = orc_sum_neumaier(buf, len) / den;
+        e2 = eb / den;
+      }
+      if (op == S_VAR) {
+        res->v[o] = s2;
+        res->b[o] = finite_or_zero_bound(s2, e2);
+      } else {
+        const double sd = sqrt(s2);
+        res->v[o] = sd;
+        res->b[o] = finite_or_zero_bound(sd, e2 == 0.0 ? 0.0 : (sd > 0.0 ? e2 / (2.0 * sd) : sqrt(e2)));
+      }
+    }
+#undef QPOS
+  }
+  free(buf);
+  return 0;
+}
+
+/* token -> (op, dim, norm) for reduce_stat; returns 0 if not a statistic */
+static int parse_stat(const char* tok, int* op, int* dim, int* norm) {
+  static const struct { const char* name; int op; } names[] = {
+      {"min", S_MIN}, {"max", S_MAX}, {"index_min", S_IMIN}, {"index_max", S_IMAX}, {"prod", S_PROD}};
+  *dim = -1;
+  *norm = 0;
+  for (size_t i = 0; i < sizeof names / sizeof names[0]; ++i) {
+    size_t n = strlen(names[i].name);
+    if (!strncmp(tok, names[i].name, n) && (tok[n] == 0 || (tok[n] == ':' && (tok[n + 1] == '0' || tok[n + 1] == '1') &&
+                                                              tok[n + 2] == 0))) {
+      *op = names[i].op;
+      if (tok[n] == ':') *dim = tok[n + 1] - '0';
+      return 1;
+    }
+  }
+  if (!strcmp(tok, "stddev") || !strcmp(tok, "stddev:1")) {
+    *op = S_STD;
+    *norm = tok[6] == ':' ? 1 : 0;
+    return 1;
+  }
+  int d, nt;
+  char tail;
+  if (sscanf(tok, "vardim:%d:%d%c", &d, &nt, &tail) == 2 && (d == 0 || d == 1) && (nt == 0 || nt == 1)) {
+    *op = S_VAR;
+    *dim = d;
+    *norm = nt;
+    return 1;
+  }
+  if (sscanf(tok, "stddevdim:%d:%d%c", &d, &nt, &tail) == 2 && (d == 0 || d == 1) && (nt == 0 || nt == 1)) {
+    *op = S_STD;
+    *dim = d;
+    *norm = nt;
+    return 1;
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
 /* program walker                                                      */
 /* ------------------------------------------------------------------ */
 
@@ -641,6 +803,16 @@ int orc_eval(const char* program, const orc_mat* leaves, int32_t n_leaves, int32
     else if (!strcmp(tok, "var") || !strcmp(tok, "var:0")) rop = R_VAR0;
     else if (!strcmp(tok, "var:1")) rop = R_VAR1;
 
+    int sop, sdim, snorm;
+    if (rop < 0 && parse_stat(tok, &sop, &sdim, &snorm)) {
+      if (sp != 1 || st[0].kind != V_MAT) {
+        snprintf(res->err, sizeof res->err, "statistic '%s' needs exactly one matrix operand", tok);
+        goto done;
+      }
+      if (reduce_stat(&cx, sop, sdim, snorm, &st[0], res)) goto done;
+      reduced = 1;
+      continue;
+    }
     if (!strncmp(tok, "submat:", 7)) {
       long long r0, c0, nr, nc;
       if (sscanf(tok + 7, "%lld:%lld:%lld:%lld", &r0, &c0, &nr, &nc) != 4) {

@@ -36,6 +36,12 @@
  * Optionally one final reduction token:
  *   accu  sum:0 sum:1  mean mean:0 mean:1  dot (pops two matrices)
  *   norm (vector 2-norm)  norm:fro  var var:1 (norm_type 0 -> N-1, 1 -> N)
+ *   min max index_min index_max prod  (all elements; index is the column-major
+ *                     linear index)  and  min:D max:D index_min:D index_max:D
+ *                     prod:D  along dimension D (0: per column, 1: per row)
+ *   stddev stddev:1   vardim:D:N stddevdim:D:N  (N is norm_type as for var)
+ *   min/max skip NaN and keep the first of equal values; an empty or all-NaN
+ *   range gives NaN (0 for INT32) and index -1.
  */
 #ifndef COOT_ORACLE_H
 #define COOT_ORACLE_H

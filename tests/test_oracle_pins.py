@@ -555,3 +555,102 @@ def test_grad_bound_covers_an_emulated_fp32_device(orc):
     # and the plain |terms| sweep would not have covered the cancelling rows
     plain = np.abs(2 * (W.astype(np.float64) * X - Y) * X) + 2e-3 * np.abs(W)
     assert np.any(np.abs(gW.astype(np.float64) - oW) > 16 * u * plain)
+
+
+# ------------------------------------------------------------ statistics
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "i32"])
+def test_min_max_and_indices_of_a_permutation(orc, dtype):
+    nrng = np.random.default_rng(70)
+    m, n = 7, 9
+    perm = nrng.permutation(m * n).astype(np.float64) - 20
+    a = perm.reshape((m, n), order="F")
+    h = bits(a, dtype)
+    assert orc.evaluate("A min", [h], dtype).value[0, 0] == a.min()
+    assert orc.evaluate("A max", [h], dtype).value[0, 0] == a.max()
+    assert orc.evaluate("A index_min", [h], dtype).value[0, 0] == np.argmin(a.ravel(order="F"))
+    assert orc.evaluate("A index_max", [h], dtype).value[0, 0] == np.argmax(a.ravel(order="F"))
+    assert np.array_equal(orc.evaluate("A min:0", [h], dtype).value[0], a.min(axis=0))
+    assert np.array_equal(orc.evaluate("A max:1", [h], dtype).value[:, 0], a.max(axis=1))
+    assert np.array_equal(orc.evaluate("A index_min:0", [h], dtype).value[0], np.argmin(a, axis=0))
+    assert np.array_equal(orc.evaluate("A index_max:1", [h], dtype).value[:, 0], np.argmax(a, axis=1))
+
+
+def test_extremes_take_the_first_tie_and_pass_over_nan(orc):
+    a = F(np.array([[2.0, np.nan, 1.0, 1.0, np.nan, 3.0, 3.0]]).T)
+    assert orc.evaluate("A index_min", [a], "f64").value[0, 0] == 2
+    assert orc.evaluate("A index_max", [a], "f64").value[0, 0] == 5
+    assert orc.evaluate("A min", [a], "f64").value[0, 0] == 1.0
+    nan = F(np.full((3, 1), np.nan))
+    assert np.isnan(orc.evaluate("A max", [nan], "f64").value[0, 0])
+    assert orc.evaluate("A index_max", [nan], "f64").value[0, 0] == -1
+    e = F(np.zeros((0, 2)))
+    assert np.array_equal(orc.evaluate("A index_min:0", [e], "f64").value[0], [-1, -1])
+
+
+def test_prod_of_powers_of_two_is_exact(orc):
+    k = np.array([3, -1, 5, 0, -7, 2, 1, -2])
+    a = F((2.0 ** k).reshape(4, 2, order="F") * np.array([[1, -1]] * 4))
+    assert orc.evaluate("A prod", [a], "f64").value[0, 0] == 2.0 ** k.sum() * 1.0  # 4 sign flips
+    assert np.array_equal(orc.evaluate("A prod:0", [a], "f64").value[0], np.prod(a, axis=0))
+    assert np.array_equal(orc.evaluate("A prod:1", [a], "f64").value[:, 0], np.prod(a, axis=1))
+
+
+def test_prod_matches_numpy_and_is_compensated(orc):
+    nrng = np.random.default_rng(71)
+    x = nrng.uniform(0.9, 1.1, size=(200000, 1))
+    p = orc.evaluate("A prod", [F(x)], "f64").value[0, 0]
+    exact = math.fsum(np.log(x.ravel()))  # the product is exp(sum log x) to ~1e-16 relative
+    assert p == pytest.approx(math.exp(exact), rel=1e-12)
+    fr = Fraction(1)
+    for v in x.ravel()[:300]:
+        fr *= Fraction(float(v))
+    assert orc.evaluate("A prod", [F(x[:300])], "f64").value[0, 0] == pytest.approx(float(fr), rel=1e-15)
+
+
+def test_int_prod_wraps_modulo_2_64(orc):
+    a = np.array([[2 ** 31 - 1], [2 ** 31 - 1], [7], [-3]], dtype=np.int32)
+    exact = (2 ** 31 - 1) ** 2 * 7 * -3
+    assert orc.evaluate("A prod", [F(a)], "i32").value[0, 0] == ((exact + 2 ** 63) % 2 ** 64) - 2 ** 63
+
+
+@pytest.mark.parametrize("n", [2, 5, 1001])
+def test_stddev_of_arithmetic_sequence(orc, n):
+    d = 0.75
+    x = (1.5 + d * np.arange(n, dtype=np.float64)).reshape(-1, 1)
+    assert orc.evaluate("A stddev", [F(x)], "f64").value[0, 0] == pytest.approx(
+        math.sqrt(d * d * n * (n + 1) / 12.0), rel=1e-15)
+    assert orc.evaluate("A stddev:1", [F(x)], "f64").value[0, 0] == pytest.approx(
+        math.sqrt(d * d * (n * n - 1) / 12.0), rel=1e-15)
+
+
+@pytest.mark.parametrize("dim", [0, 1])
+@pytest.mark.parametrize("nt", [0, 1])
+def test_var_and_stddev_along_a_dimension_match_numpy(orc, dim, nt):
+    nrng = np.random.default_rng(72)
+    a = nrng.normal(size=(37, 23)) * 3 + 1
+    v = orc.evaluate("A vardim:%d:%d" % (dim, nt), [F(a)], "f64").value.ravel()
+    s = orc.evaluate("A stddevdim:%d:%d" % (dim, nt), [F(a)], "f64").value.ravel()
+    assert np.allclose(v, np.var(a, axis=dim, ddof=1 - nt), rtol=1e-13, atol=0)
+    assert np.allclose(s, np.std(a, axis=dim, ddof=1 - nt), rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("tok", ["min", "max:0", "prod:1", "stddev", "vardim:0:0"])
+def test_statistics_bounds_cover_an_emulated_fp32_device(orc, tok):
+    nrng = np.random.default_rng(73)
+    A = nrng.uniform(0.8, 1.2, size=(50, 20)).astype(np.float32)
+    B = nrng.uniform(0.8, 1.2, size=(50, 20)).astype(np.float32)
+    prog = "A B % #0.5 B * + exp"
+    y = rpn.eval_emulated(prog, [A, B], np.float32).astype(np.float64)
+    r = orc.evaluate(prog + " " + tok, [F(A), F(B)], "f32")
+    if tok == "min":
+        dev = np.array([[y.min()]])
+    elif tok == "max:0":
+        dev = y.max(axis=0)[None, :]
+    elif tok == "prod:1":
+        dev = np.prod(y, axis=1)[:, None]
+    elif tok == "stddev":
+        dev = np.array([[np.std(y, ddof=1)]])
+    else:
+        dev = np.var(y, axis=0, ddof=1)[None, :]
+    assert np.all(np.abs(dev - r.value) <= 1e-6 * np.abs(r.value) + r.bound)
