@@ -542,9 +542,11 @@ static int reduce(ctx_t* cx, int kind, val_t* x, val_t* y, orc_result* res) {
  * indices), dim 0 each column (index outputs are row indices), dim 1 each
  * row (index outputs are column indices).  Readings: NaN elements are passed
  * over by min/max and their indices; ties give the first occurrence; an empty
- * set gives NaN (0 for INT32 trees) and index -1.  prod multiplies in order
- * with a double-double product (error ~ n u^2); INT32 trees multiply modulo
- * 2^64.  var/stddev are the two-pass definitions of the all-element form.
+ * set gives NaN (0 for INT32 trees) and index -1.  prod is the exact product
+ * rounded once to the result type (double-double significands with the
+ * exponent carried apart, error ~ n u^2 before that rounding; an empty
+ * product is 1); INT32 trees multiply modulo 2^64.  var/stddev are the
+ * two-pass definitions of the all-element form.
  */
 enum { S_MIN, S_MAX, S_IMIN, S_IMAX, S_PROD, S_VAR, S_STD };
 
@@ -604,23 +606,47 @@ static int reduce_stat(ctx_t* cx, int op, int dim, int norm, val_t* x, orc_resul
         for (int64_t t = 0; t < len; ++t) p *= (uint64_t)x->iv[QPOS(t)];
         res->iv[o] = (int64_t)p;
       } else {
+        /* v = m 2^k with 0.5 <= |m| < 1 (frexp): the significands multiply in
+         * double-double, the exponents add apart, so no partial product
+         * overflows or underflows; zeros, infinities and NaN follow IEEE
+         * multiplication; the exact product is rounded once at the end */
         double ph = 1.0, pl = 0.0, rel = 0.0;
-        int zero = 0;
+        long long E = 0;
+        int zero = 0, inf = 0, nan = 0, neg = 0;
         for (int64_t t = 0; t < len; ++t) {
           const int64_t q = QPOS(t);
           const double v = x->v[q];
-          const double p = ph * v;
-          const double e = fma(ph, v, -p); /* exact error of ph*v */
-          pl = fma(pl, v, e);
+          if (signbit(v)) neg ^= 1;
+          if (isnan(v)) { nan = 1; continue; }
+          if (isinf(v)) { inf = 1; continue; }
+          if (v == 0.0) { zero = 1; continue; }
+          if (x->b[q] != 0.0) rel += x->b[q] / fabs(v);
+          int k;
+          const double m = fabs(frexp(v, &k));
+          E += k;
+          const double p = ph * m;
+          const double e = fma(ph, m, -p); /* exact error of ph*m */
+          pl = fma(pl, m, e);
           ph = p;
-          if (v == 0.0)
-            zero = 1;
-          else if (x->b[q] != 0.0)
-            rel += x->b[q] / fabs(v);
+          ph = frexp(ph, &k); /* back to [0.5, 1) */
+          pl = ldexp(pl, -k);
+          E += k;
         }
-        const double pv = ph + pl;
+        double pv;
+        if (nan || (inf && zero))
+          pv = NAN;
+        else if (inf)
+          pv = neg ? -INFINITY : INFINITY;
+        else if (zero)
+          pv = neg ? -0.0 : 0.0;
+        else {
+          const double mag = (E > 4000) ? INFINITY : (E < -4000 ? 0.0 : ldexp(ph + pl, (int)E));
+          pv = neg ? -mag : mag;
+        }
+        /* the result has the accumulation type: FP32 trees round to float */
+        if (cx->ct == ORC_F32) pv = (double)(float)pv;
         res->v[o] = pv;
-        res->b[o] = zero ? 0.0 : finite_or_zero_bound(pv, fabs(pv) * rel);
+        res->b[o] = (zero || inf || nan) ? 0.0 : finite_or_zero_bound(pv, fabs(pv) * rel);
       }
     } else { /* S_VAR, S_STD */
       double s2, e2;

@@ -654,3 +654,29 @@ def test_statistics_bounds_cover_an_emulated_fp32_device(orc, tok):
     else:
         dev = np.var(y, axis=0, ddof=1)[None, :]
     assert np.all(np.abs(dev - r.value) <= 1e-6 * np.abs(r.value) + r.bound)
+
+
+@pytest.mark.parametrize("dtype,lo,hi", [("f32", -140, 105), ("f64", -1060, 795)])
+def test_prod_carries_the_exponent_apart(orc, dtype, lo, hi):
+    # 30 subnormal factors 2^lo and 40 factors 2^hi: the exact product is 2^0;
+    # every running product in the format's own range underflows first
+    ft = np.float32 if dtype == "f32" else np.float64
+    a = np.vstack([np.full((30, 1), 2.0 ** lo), np.full((40, 1), 2.0 ** hi)]).astype(ft)
+    assert 30 * lo + 40 * hi == 0
+    assert orc.evaluate("A prod", [F(a)], dtype).value[0, 0] == 1.0
+    assert orc.evaluate("A prod:0", [F(a)], dtype).value[0, 0] == 1.0
+
+
+def test_prod_follows_ieee_special_values_and_rounds_to_the_result_type(orc):
+    f = lambda v: F(np.array(v, dtype=np.float32).reshape(-1, 1))
+    assert np.isnan(orc.evaluate("A prod", [f([0.0, np.inf, 2.0])], "f32").value[0, 0])
+    assert orc.evaluate("A prod", [f([np.inf, -2.0])], "f32").value[0, 0] == -np.inf
+    z = orc.evaluate("A prod", [f([-0.0, 3.0, -5.0])], "f32").value[0, 0]
+    assert z == 0.0 and not np.signbit(z)
+    assert np.isnan(orc.evaluate("A prod", [f([np.nan, 0.0])], "f32").value[0, 0])
+    # 1e30 * 1e30 exceeds FP32: an FP32 tree's product is +inf, FP64 keeps it
+    assert orc.evaluate("A prod", [f([1e30, 1e30])], "f32").value[0, 0] == np.inf
+    assert orc.evaluate("A prod", [F(np.array([[1e30], [1e30]]))], "f64").value[0, 0] == pytest.approx(1e60)
+    # and is rounded once to float: 3 * (1 + 2^-23) * (1 + 2^-23)
+    x = np.float32(1 + 2.0 ** -23)
+    assert orc.evaluate("A prod", [f([3.0, x, x])], "f32").value[0, 0] == float(np.float32(3.0 * float(x) ** 2))
