@@ -124,8 +124,13 @@ typedef struct {
 #define COOT_MAX_LEAVES 8
 #define COOT_MAX_SCALARS 16
 
-/* The reduction fused onto the tree (Sec. 2: accu/sum, "statistics such as
- * mean and variance"; Sec. 5 task 1: summation of all elements). */
+/* The reduction fused onto the tree (Sec. 2: accu/sum and Armadillo's
+ * statistics functions -- mean, var, stddev, min, max, index_min/index_max,
+ * prod; Sec. 5 task 1: summation of all elements).  Results have the
+ * accumulation type: float for F32/BF16/F16 trees, double for F64, int64 for
+ * I32 (sums and products exact modulo 2^64); index kinds are int64 for every
+ * dtype.  Along dim 0 there is one result per column, along dim 1 one per
+ * row; dim -1 gives one result over all elements (column-major order). */
 typedef enum {
   COOT_R_NONE = 0,
   COOT_R_ACCU = 1,     /* sum of all elements -> scalar                           */
@@ -135,14 +140,25 @@ typedef enum {
                           kept exactly (integer: exact int64 products)            */
   COOT_R_NORM2 = 5,    /* vector 2-norm (tree must be a row or column vector)     */
   COOT_R_NORM_FRO = 6, /* Frobenius norm of a matrix                              */
-  COOT_R_VAR = 7       /* two-pass variance over all elements; norm_type 0 -> N-1,
-                          1 -> N; one element gives 0                             */
+  COOT_R_VAR = 7,      /* two-pass variance (dim -1, 0 or 1); norm_type 0 -> N-1,
+                          1 -> N; one element gives 0, none gives NaN; F32/F64  */
+  COOT_R_STDDEV = 8,   /* square root of R_VAR                                     */
+  COOT_R_MIN = 9,      /* smallest element; NaN elements are skipped; none (or all
+                          NaN) gives NaN (0 for I32)                              */
+  COOT_R_MAX = 10,     /* largest element, as R_MIN                                */
+  COOT_R_INDEX_MIN = 11, /* position of the first smallest element: column-major
+                          linear index for dim -1, row index along dim 0, column
+                          index along dim 1; -1 when there is none             */
+  COOT_R_INDEX_MAX = 12, /* position of the first largest element, as above      */
+  COOT_R_PROD = 13     /* product; no intermediate overflow or underflow (the
+                          exponent is carried apart), the result is rounded to
+                          the accumulation type; empty gives 1                 */
 } coot_red_kind;
 
 typedef struct {
   int32_t kind;      /* coot_red_kind                           */
   int32_t dim;       /* -1 all elements, 0 per column, 1 per row */
-  int32_t norm_type; /* R_VAR only                              */
+  int32_t norm_type; /* R_VAR / R_STDDEV only                   */
   int32_t reserved;
 } coot_reduce;
 
@@ -162,7 +178,8 @@ COOT_API coot_status coot_ctx_create(int device, unsigned flags, coot_ctx** out)
 COOT_API coot_status coot_ctx_destroy(coot_ctx* ctx);
 
 /* ---- fused evaluation ----------------------------------------------------
- * Evaluates `tree` over `leaves` in one kernel launch (two for R_VAR):
+ * Evaluates `tree` over `leaves` in one kernel launch (two for R_VAR and
+ * R_STDDEV: the second pass reads the first pass's means):
  *   out     (nullable) receives the element-wise result Y, in the leaves'
  *           dtype; it may alias a leaf only when every read of that leaf is
  *           a full, untransposed read with out's exact layout (B += 3*A form);

@@ -172,23 +172,19 @@ struct Launch {
   std::string kname, kname2;  // kname2: second pass of var
   int grid = 1, block = 256, vec = 1, unroll = 1;
   size_t tickets = 1, partial_bytes = 0;
+  size_t mu_offset = 0;  // var/stddev along a dim: byte offset of the means in the partials
   cg::Params p{};
 };
 
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-// number of values a reduction writes (a vector along dim 0/1 may be empty)
-int64_t n_red_outputs(const cg::Analysis& an) {
-  if (an.red.kind == COOT_R_NONE) return 0;
-  if (an.red.dim == 0) return an.nc;
-  if (an.red.dim == 1) return an.nr;
-  return 1;
-}
+int64_t n_red_outputs(const cg::Analysis& an) { return an.n_outputs(); }
 
 // fill the launch shape of a fused program for a given kernel variant/config
 void shape_launch(coot_ctx* ctx, const cg::Analysis& an, const cg::Choice& ch, cg::Module* m,
                   const cg::KernelSpec& k, int block, int bps, Launch* L, int split = 0) {
   const int64_t R = ch.it_rows, C = ch.it_cols;
+  const int64_t ab = an.acc_bytes();
   L->block = block;
   L->vec = k.vec;
   L->unroll = k.unroll;
@@ -201,7 +197,7 @@ void shape_launch(coot_ctx* ctx, const cg::Analysis& an, const cg::Choice& ch, c
     p.units_per_col = std::max<int64_t>(1, ceil_div(R, chunk));
     const int64_t units = p.units_per_col * C;
     L->grid = (int)std::max<int64_t>(1, std::min(units, resident));
-    L->partial_bytes = (size_t)L->grid * 8;
+    L->partial_bytes = (size_t)L->grid * ab;
     L->tickets = 1;
   } else if (ch.fam == cg::F_COL) {
     const int64_t wpb = block / 32;
@@ -227,7 +223,7 @@ void shape_launch(coot_ctx* ctx, const cg::Analysis& an, const cg::Choice& ch, c
     p.n_splits = nsp;
     p.units_per_col = cps;
     L->grid = (int)(nrb * nsp);
-    L->partial_bytes = (nsp > 1) ? (size_t)(nsp * R * 8) : 0;
+    L->partial_bytes = (nsp > 1) ? (size_t)(nsp * R * ab) : 0;
     L->tickets = (size_t)nrb;
   } else if (ch.fam == cg::F_TILE) {
     // tilev tiles are 32 x vec rows tall; the scalar tile kernel's 32
@@ -235,27 +231,39 @@ void shape_launch(coot_ctx* ctx, const cg::Analysis& an, const cg::Choice& ch, c
     const int64_t tiles = ntr * ntc;
     L->grid = (int)std::max<int64_t>(1, std::min(tiles, resident));
     if (an.red.dim == 0) {
-      L->partial_bytes = (size_t)(ntr * C * 8);
+      L->partial_bytes = (size_t)(ntr * C * ab);
       L->tickets = (size_t)std::max<int64_t>(ntc, 1);
     } else if (an.red.dim == 1) {
-      L->partial_bytes = (size_t)(ntc * R * 8);
+      L->partial_bytes = (size_t)(ntc * R * ab);
       L->tickets = (size_t)std::max<int64_t>(ntr, 1);
     } else {
-      L->partial_bytes = (size_t)L->grid * 8;
+      L->partial_bytes = (size_t)L->grid * ab;
       L->tickets = 1;
     }
   }
+  // var / stddev along a dim: the first pass's means follow the partials
+  if (an.two_pass() && an.red.dim >= 0) {
+    L->mu_offset = (L->partial_bytes + 255) & ~(size_t)255;
+    L->partial_bytes = L->mu_offset + (size_t)std::max<int64_t>(an.n_outputs(), 1) * 8;
+  }
   (void)m;
+}
+
+// workspace pointers of a shaped launch (after ws_ensure)
+void bind_workspace(coot_ctx* ctx, const cg::Analysis& an, Launch* L) {
+  L->p.tickets = ctx->tickets;
+  L->p.err_flag = ctx->err_flag;
+  L->p.partials = ctx->partials;
+  L->p.mu = (an.two_pass() && an.red.dim >= 0) ? (double*)((char*)ctx->partials + L->mu_offset) : ctx->mean_ptr;
 }
 
 int64_t algorithmic_bytes(const cg::Analysis& an, const coot_mat* out) {
   int64_t b = 0;
   for (const cg::Slot& s : an.slots) b += s.vr * s.vc * an.esz;
-  if (an.red.kind == COOT_R_VAR) b *= 2;  // the tree is read by both passes
+  if (an.two_pass()) b *= 2;  // the tree is read by both passes
   if (out) b += an.nr * an.nc * an.esz;
-  int64_t nout = 0;
-  if (an.red.kind != COOT_R_NONE) nout = (an.red.dim == 0) ? an.nc : (an.red.dim == 1 ? an.nr : 1);
-  return b + nout * (an.ct == cg::CT_F32 ? 4 : 8);
+  const bool idx = an.red.kind == COOT_R_INDEX_MIN || an.red.kind == COOT_R_INDEX_MAX;
+  return b + an.n_outputs() * ((an.ct == cg::CT_F32 && !idx) ? 4 : 8);
 }
 
 // pick the default kernel variant of a program for this call: the vector
@@ -341,19 +349,33 @@ std::string tune_key(const cg::Program& pg, const cg::Choice& ch) {
 // ---------------------------------------------------------------------------
 static coot_status run_fused(coot_ctx* ctx, const cg::Analysis& an, const coot_mat* leaves, const coot_mat* out,
                              void* red_out, cudaStream_t stream, bool warm_only) {
-  const bool var = an.red.kind == COOT_R_VAR;
+  const bool var = an.two_pass();
   cg::Choice ch = cg::choose(an, leaves, out);
   const int64_t count = an.nr * an.nc;
-  if (!warm_only && count == 0) {
-    // nothing to read: reductions of no elements
+  if (!warm_only && count == 0 && an.red.kind != COOT_R_PROD) {
+    // nothing to read: reductions of no elements.  All-ones bytes are a NaN
+    // in float and double and -1 in int64.
     if (an.red.kind == COOT_R_NONE) return COOT_OK;
-    int64_t nout = (an.red.dim == 0) ? an.nc : (an.red.dim == 1 ? an.nr : 1);
-    bool nan = (an.red.kind == COOT_R_MEAN || an.red.kind == COOT_R_VAR);
+    const int k = an.red.kind;
+    const bool ones = k == COOT_R_MEAN || k == COOT_R_VAR || k == COOT_R_STDDEV || k == COOT_R_INDEX_MIN ||
+                      k == COOT_R_INDEX_MAX || ((k == COOT_R_MIN || k == COOT_R_MAX) && an.ct != cg::CT_I32);
+    const size_t esz = (k == COOT_R_INDEX_MIN || k == COOT_R_INDEX_MAX) ? 8 : rsize(an.ct);
+    const int64_t nout = an.n_outputs();
     if (nout > 0) {
-      cudaError_t e = cudaMemsetAsync(red_out, nan ? 0xff : 0, (size_t)nout * rsize(an.ct), stream);
+      cudaError_t e = cudaMemsetAsync(red_out, ones ? 0xff : 0, (size_t)nout * esz, stream);
       if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync");
     }
     return COOT_OK;
+  }
+  if (count == 0) {
+    // an empty product is 1 per output: the column / row / flat kernels
+    // write their empty accumulators without reading anything
+    if (an.n_outputs() == 0 && !warm_only) return COOT_OK;
+    ch.fam = an.red.dim == 0 ? cg::F_COL : (an.red.dim == 1 ? cg::F_ROW : cg::F_STR);
+    ch.collapsed = false;
+    ch.vec_ok = false;
+    ch.it_rows = an.nr;
+    ch.it_cols = an.nc;
   }
   cg::Program pg = cg::make_program(an, ch.fam, var);
   if (!ctx->mods.count(pg.signature) && capturing(stream))
@@ -374,11 +396,13 @@ static coot_status run_fused(coot_ctx* ctx, const cg::Analysis& an, const coot_m
   for (size_t i = 0; i < an.scalars.size(); ++i) p.k[i] = scalar_bits(an.scalars[i], an.ct);
   p.out = out ? out->data : nullptr;
   p.out_ld = out ? mat_ld(*out) : 0;
-  p.count = count;
+  // elements per reduction output
+  const int64_t per = (an.red.dim == 0) ? an.nr : (an.red.dim == 1 ? an.nc : count);
+  p.count = per;
   p.div = 1.0;
-  if (an.red.kind == COOT_R_MEAN)
-    p.div = (an.red.dim == 0) ? (double)an.nr : (an.red.dim == 1 ? (double)an.nc : (double)count);
-  p.den = (an.red.norm_type == 1) ? (double)count : (double)(count - 1);
+  if (an.red.kind == COOT_R_MEAN) p.div = (double)per;
+  p.den = (an.red.norm_type == 1) ? (double)per : (double)(per - 1);
+  p.flags = (an.red.kind == COOT_R_STDDEV) ? cg::PF_SQRT : 0u;
   p.red_out = red_out;
 
   // launch configuration: tuned, else the default variant at full occupancy
@@ -407,10 +431,7 @@ static coot_status run_fused(coot_ctx* ctx, const cg::Analysis& an, const coot_m
   if (var) L.kname2 = pair_name(ks.name);
   s = ws_ensure(ctx, L.tickets, L.partial_bytes, stream);
   if (s) return s;
-  p.tickets = ctx->tickets;
-  p.err_flag = ctx->err_flag;
-  p.mu = ctx->mean_ptr;
-  p.partials = ctx->partials;
+  bind_workspace(ctx, an, &L);
   if (warm_only) return COOT_OK;
 
   s = launch_kernel(m, L.kname, L.grid, L.block, &p, stream);
@@ -438,7 +459,7 @@ static coot_status run_fused(coot_ctx* ctx, const cg::Analysis& an, const coot_m
 namespace {
 coot_status tune(coot_ctx* ctx, const cg::Analysis& an, const cg::Choice& ch, const cg::Program& pg, cg::Module* m,
                  Launch base, cudaStream_t stream, cg::LaunchCfg* best) {
-  const bool var = an.red.kind == COOT_R_VAR;
+  const bool var = an.two_pass();
   void* scratch_out = nullptr;
   void* scratch_red = nullptr;
   cudaError_t e;
@@ -483,10 +504,7 @@ coot_status tune(coot_ctx* ctx, const cg::Analysis& an, const cg::Choice& ch, co
         shape_launch(ctx, an, ch, m, k, block, bps, &L, split);
         st = ws_ensure(ctx, L.tickets, L.partial_bytes, stream);
         if (st) break;
-        L.p.tickets = ctx->tickets;
-        L.p.err_flag = ctx->err_flag;
-        L.p.mu = ctx->mean_ptr;
-        L.p.partials = ctx->partials;
+        bind_workspace(ctx, an, &L);
         std::string k2 = pair_name(k.name);
         float times[3];
         for (int rep = 0; rep < 4 && st == COOT_OK; ++rep) {
@@ -1127,7 +1145,7 @@ static coot_status analyse_for_host(const coot_tree* tree, const coot_mat* leave
   coot_status s = cg::analyse(tree, leaves, n_leaves, out, red, an);
   if (s) return s;
   cg::Choice ch = cg::choose(*an, leaves, out);
-  *pg = cg::make_program(*an, ch.fam, red.kind == COOT_R_VAR);
+  *pg = cg::make_program(*an, ch.fam, an->two_pass());
   return COOT_OK;
 }
 

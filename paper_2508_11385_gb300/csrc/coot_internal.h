@@ -17,9 +17,21 @@
 namespace cg {
 
 using coot::Params;
+using coot::PF_SQRT;
 
-// device reduction modes (must match coot_dev.cuh)
-enum { RED_NONE = 0, RED_SUM = 1, RED_DOT = 2, RED_SSQ = 3, RED_MEAN1 = 4, RED_CSQ = 5 };
+using coot::RED_NONE;
+using coot::RED_SUM;
+using coot::RED_DOT;
+using coot::RED_SSQ;
+using coot::RED_MEAN1;
+using coot::RED_CSQ;
+using coot::RED_MIN;
+using coot::RED_MAX;
+using coot::RED_IMIN;
+using coot::RED_IMAX;
+using coot::RED_PROD;
+using coot::red_additive;
+using coot::red_extreme;
 
 enum Family { F_STR = 0, F_COL = 1, F_ROW = 2, F_TILE = 3, F_ADJ = 4, F_BATCH = 5 };
 const char* family_name(Family f);
@@ -63,6 +75,15 @@ struct Analysis {
   bool has_out = false;
   int root_op = -1;         // op of the root (R_DOT needs N_SCHUR)
   int accum = 0;            // FP32 accumulation: 0 float-float, 1 Kahan, 2 plain ($COOT_ACCUM)
+  // var / stddev: a first pass writes the mean(s), a second reduces (y - mean)^2
+  bool two_pass() const { return red.kind == COOT_R_VAR || red.kind == COOT_R_STDDEV; }
+  // bytes of one accumulator in the workspace (partials of cross-block combines)
+  int acc_bytes() const { return (red_mode == RED_NONE || red_additive(red_mode)) ? 8 : 16; }
+  // number of values the reduction writes (a vector along dim 0/1 may be empty)
+  int64_t n_outputs() const {
+    if (red.kind == COOT_R_NONE) return 0;
+    return red.dim == 0 ? nc : (red.dim == 1 ? nr : 1);
+  }
 };
 
 // Validate the call and canonicalise the tree.  `out` and `red_out` checks

@@ -17,6 +17,7 @@
 // contraction into FMA, so the fused result equals the one-op-at-a-time
 // result bit for bit.
 #pragma once
+#include "coot_params.h"
 
 namespace coot {
 
@@ -424,12 +425,7 @@ template <class T1, class T2, class Op> struct eGlue {
 // ---------------------------------------------------------------------------
 // reductions: modes and accumulators
 // ---------------------------------------------------------------------------
-enum { RED_NONE = 0, RED_SUM = 1, RED_DOT = 2, RED_SSQ = 3, RED_MEAN1 = 4, RED_CSQ = 5 };
-// RED_SUM   accu / sum / mean                     sum of y
-// RED_DOT   root a%b                              sum of a*b, products kept exactly
-// RED_SSQ   norm                                  sum of y*y, products kept exactly
-// RED_MEAN1 first pass of var: sum of y, writes the mean to the workspace
-// RED_CSQ   second pass of var: sum of (y - mean)^2
+// reduction modes (RED_*) are defined with the kernel arguments in coot_params.h
 
 // Float-float accumulator (Ogita, Rump and Oishi, "Accurate sum and dot
 // product", SIAM J. Sci. Comput. 2005, algorithm Sum2/Dot2): hi is the
@@ -516,6 +512,190 @@ template <class C> struct AccOf;
 template <> struct AccOf<float> { typedef AccF type; };
 template <> struct AccOf<double> { typedef AccD type; };
 template <> struct AccOf<int> { typedef AccI type; };
+
+// Extreme value and its position (min, max, index_min, index_max).  The
+// empty state is (the identity of the order: +inf for min, -inf for max,
+// INT_MAX / INT_MIN for integers; position "none" = 2^63-1), so that
+//   take y  <=>  y beats v, or y == v and y comes first
+// needs no separate test for NaN (every comparison with NaN is false, so NaN
+// is never taken) nor for the empty state (an empty partner ties on v and
+// loses on position).  Equal values keep the smallest position, which makes
+// the result independent of the order of visits and merges.
+constexpr i64 POS_NONE = 0x7fffffffffffffffll;
+template <class C> struct Lim;
+template <> struct Lim<float> {
+  __device__ static float hi() { return __int_as_float(0x7f800000); }
+  __device__ static float lo() { return __int_as_float((int)0xff800000u); }
+};
+template <> struct Lim<double> {
+  __device__ static double hi() { return __longlong_as_double(0x7ff0000000000000ll); }
+  __device__ static double lo() { return __longlong_as_double((i64)0xfff0000000000000ull); }
+};
+template <> struct Lim<int> {
+  __device__ static int hi() { return 0x7fffffff; }
+  __device__ static int lo() { return (int)0x80000000u; }
+};
+template <class C, bool MAX> struct AccExt {
+  C v;
+  i64 pos;
+  __device__ __forceinline__ void init() {
+    v = MAX ? Lim<C>::lo() : Lim<C>::hi();
+    pos = POS_NONE;
+  }
+  __device__ __forceinline__ void add_at(C y, i64 q) {
+    const bool take = (MAX ? (y > v) : (y < v)) || (y == v && q < pos);
+    v = take ? y : v;
+    pos = take ? q : pos;
+  }
+  __device__ __forceinline__ void merge(const AccExt& o) { add_at(o.v, o.pos); }
+  __device__ __forceinline__ AccExt shfl_xor(int m) const {
+    AccExt o;
+    o.v = __shfl_xor_sync(0xffffffffu, v, m);
+    o.pos = __shfl_xor_sync(0xffffffffu, pos, m);
+    return o;
+  }
+};
+
+// Products keep their binary exponent apart from the significand, so that no
+// partial product overflows or underflows: every factor is split as
+// x = m 2^e with |m| in [0.5, 1) (IEEE 754 fields; subnormals are scaled by
+// 2^64 first), the running significand is renormalised to [0.5, 1) after
+// each step and the exponents are summed in 64-bit integers.  Zeros,
+// infinities and NaN pass through the significand unchanged (exponent 0), so
+// they propagate as in an ordinary product.
+__device__ __forceinline__ float split_exp(float x, i64& e) {
+  u32 b = __float_as_uint(x);
+  int be = (int)((b >> 23) & 0xffu);
+  i64 adj = 0;
+  if (be == 0 && (b & 0x7fffffffu) != 0u) {  // subnormal: scale by 2^64
+    x = __fmul_rn(x, __uint_as_float(0x5f800000u));
+    b = __float_as_uint(x);
+    be = (int)((b >> 23) & 0xffu);
+    adj = -64;
+  }
+  if (be == 0 || be == 255) return x;  // zero, inf, NaN
+  e += (i64)(be - 126) + adj;
+  return __uint_as_float((b & 0x807fffffu) | (126u << 23));
+}
+__device__ __forceinline__ double split_exp(double x, i64& e) {
+  u64 b = (u64)__double_as_longlong(x);
+  int be = (int)((b >> 52) & 0x7ffull);
+  i64 adj = 0;
+  if (be == 0 && (b & 0x7fffffffffffffffull) != 0ull) {
+    x = __dmul_rn(x, __longlong_as_double(0x43f0000000000000ll));  // 2^64
+    b = (u64)__double_as_longlong(x);
+    be = (int)((b >> 52) & 0x7ffull);
+    adj = -64;
+  }
+  if (be == 0 || be == 2047) return x;
+  e += (i64)(be - 1022) + adj;
+  return __longlong_as_double((i64)((b & 0x800fffffffffffffull) | (1022ull << 52)));
+}
+// v 2^e in double, saturating to 0 / inf outside the double range
+__device__ __forceinline__ double scale2(double v, i64 e) {
+  if (v == 0.0 || !(v - v == 0.0)) return v;
+  if (e > 2100) e = 2100;
+  if (e < -2200) e = -2200;
+  return scalbn(v, (int)e);
+}
+
+// FP32: float-float significand (TwoProduct through fma: hi*m exactly equals
+// p + err), relative error ~ (n u)^2 + u.
+struct AccProdF {
+  float hi, lo;
+  i64 e;
+  __device__ __forceinline__ void init() { hi = 1.f; lo = 0.f; e = 0; }
+  __device__ __forceinline__ void renorm() {
+    i64 d = 0;
+    float h = split_exp(hi, d);
+    if (d != 0) {
+      lo = __fmul_rn(lo, __uint_as_float((u32)(127 - d) << 23));  // |d| <= 2 here
+      hi = h;
+      e += d;
+    }
+  }
+  __device__ __forceinline__ void mul(float x) {
+    float m = split_exp(x, e);
+    float p = __fmul_rn(hi, m);
+    float err = __fmaf_rn(hi, m, -p);
+    lo = __fmaf_rn(lo, m, err);
+    hi = p;
+    renorm();
+  }
+  __device__ __forceinline__ void merge(const AccProdF& o) {
+    float p = __fmul_rn(hi, o.hi);
+    float err = __fmaf_rn(hi, o.hi, -p);
+    lo = __fmaf_rn(hi, o.lo, __fmaf_rn(lo, o.hi, err));
+    hi = p;
+    e += o.e;
+    renorm();
+  }
+  __device__ __forceinline__ AccProdF shfl_xor(int m) const {
+    AccProdF o;
+    o.hi = __shfl_xor_sync(0xffffffffu, hi, m);
+    o.lo = __shfl_xor_sync(0xffffffffu, lo, m);
+    o.e = __shfl_xor_sync(0xffffffffu, e, m);
+    return o;
+  }
+  __device__ __forceinline__ double value() const {
+    if (hi == 0.f || !(hi - hi == 0.f)) return (double)hi;
+    return scale2((double)hi + (double)lo, e);
+  }
+};
+// FP64: plain double significand (relative error ~ n u for a chain of n)
+struct AccProdD {
+  double hi;
+  i64 e;
+  __device__ __forceinline__ void init() { hi = 1.0; e = 0; }
+  __device__ __forceinline__ void renorm() {
+    i64 d = 0;
+    double h = split_exp(hi, d);
+    hi = h;
+    e += d;
+  }
+  __device__ __forceinline__ void mul(double x) {
+    double m = split_exp(x, e);
+    hi = __dmul_rn(hi, m);
+    renorm();
+  }
+  __device__ __forceinline__ void merge(const AccProdD& o) {
+    hi = __dmul_rn(hi, o.hi);
+    e += o.e;
+    renorm();
+  }
+  __device__ __forceinline__ AccProdD shfl_xor(int m) const {
+    AccProdD o;
+    o.hi = __shfl_xor_sync(0xffffffffu, hi, m);
+    o.e = __shfl_xor_sync(0xffffffffu, e, m);
+    return o;
+  }
+  __device__ __forceinline__ double value() const { return scale2(hi, e); }
+};
+// INT32: exact product modulo 2^64
+struct AccProdI {
+  u64 s;
+  __device__ __forceinline__ void init() { s = 1ull; }
+  __device__ __forceinline__ void mul(int x) { s *= (u64)(i64)x; }
+  __device__ __forceinline__ void merge(const AccProdI& o) { s *= o.s; }
+  __device__ __forceinline__ AccProdI shfl_xor(int m) const {
+    AccProdI o;
+    o.s = __shfl_xor_sync(0xffffffffu, s, m);
+    return o;
+  }
+  __device__ __forceinline__ i64 ivalue() const { return (i64)s; }
+};
+template <class C> struct ProdOf;
+template <> struct ProdOf<float> { typedef AccProdF type; };
+template <> struct ProdOf<double> { typedef AccProdD type; };
+template <> struct ProdOf<int> { typedef AccProdI type; };
+
+// the accumulator of a reduction mode
+template <class C, int RED> struct AccSel { typedef typename AccOf<C>::type type; };
+template <class C> struct AccSel<C, RED_MIN> { typedef AccExt<C, false> type; };
+template <class C> struct AccSel<C, RED_IMIN> { typedef AccExt<C, false> type; };
+template <class C> struct AccSel<C, RED_MAX> { typedef AccExt<C, true> type; };
+template <class C> struct AccSel<C, RED_IMAX> { typedef AccExt<C, true> type; };
+template <class C> struct AccSel<C, RED_PROD> { typedef typename ProdOf<C>::type type; };
 
 // Centred sum of squares for the second pass of var.  The mean arrives as a
 // double m; FP32 data keeps it as the float pair (mh, ml) = m so that

@@ -47,10 +47,23 @@ template <class S> __device__ __forceinline__ S* at_out(void* base, long long i,
 // ---------------------------------------------------------------------------
 // per-element contribution of the root to the reduction
 // ---------------------------------------------------------------------------
+// pos: the element's position in its reduction (column-major linear index for
+// a full reduction, row index along dim 0, column index along dim 1); only
+// index_min / index_max read it (and min / max, to keep the first of equal
+// values), everywhere else the expression is dead code.
 template <class T, int RED, class X, class K, class A, class Q>
-__device__ __forceinline__ typename X::C eval_elem(const X& x, const K& k, u32& err, int l, A& acc, const Q& csq) {
+__device__ __forceinline__ typename X::C eval_elem(const X& x, const K& k, u32& err, int l, A& acc, const Q& csq,
+                                                   long long pos) {
   typedef typename X::C C;
-  if constexpr (RED == RED_DOT) {
+  if constexpr (red_extreme(RED)) {
+    C y = T::ev(x, k, err, l);
+    acc.add_at(y, pos);
+    return y;
+  } else if constexpr (RED == RED_PROD) {
+    C y = T::ev(x, k, err, l);
+    acc.mul(y);
+    return y;
+  } else if constexpr (RED == RED_DOT) {
     C a = T::A::ev(x, k, err, l), b = T::B::ev(x, k, err, l);
     acc.add_prod(a, b);
     return op_mul(a, b);
@@ -96,24 +109,36 @@ __device__ __forceinline__ typename X::C eval_term(const X& x, const K& k, u32& 
 template <class C, int RED, class A>
 __device__ __forceinline__ void write_result(const Params& p, const A& a, long long idx, double div) {
   typedef typename rtype<C>::type R;
-  if constexpr (is_int_c<C>::value) {
-    // integer trees: exact int64 sums (sum / dot)
+  const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+  if constexpr (RED == RED_IMIN || RED == RED_IMAX) {
+    // positions are int64 for every element type; -1: no element (or all NaN)
+    ((long long*)p.red_out)[idx] = (a.pos == POS_NONE) ? -1ll : (long long)a.pos;
+  } else if constexpr (RED == RED_MIN || RED == RED_MAX) {
+    if constexpr (is_int_c<C>::value)
+      ((long long*)p.red_out)[idx] = (a.pos == POS_NONE) ? 0ll : (long long)a.v;
+    else
+      ((R*)p.red_out)[idx] = (a.pos == POS_NONE) ? (R)qnan : (R)a.v;
+  } else if constexpr (is_int_c<C>::value) {
+    // integer trees: exact int64 sums and products (sum / dot / prod)
     ((long long*)p.red_out)[idx] = a.ivalue();
   } else {
     if constexpr (RED == RED_SUM || RED == RED_DOT) {
       ((R*)p.red_out)[idx] = (R)(a.value() / div);
+    } else if constexpr (RED == RED_PROD) {
+      ((R*)p.red_out)[idx] = (R)a.value();
     } else if constexpr (RED == RED_SSQ) {
       ((R*)p.red_out)[idx] = (R)sqrt(a.value());
     } else if constexpr (RED == RED_MEAN1) {
-      *p.mu = a.value() / (double)p.count;
+      p.mu[idx] = a.value() / (double)p.count;  // count: elements per output
     } else if constexpr (RED == RED_CSQ) {
       double v;
       if (p.count == 0)
-        v = __longlong_as_double(0x7ff8000000000000ll);  // NaN: no elements
+        v = qnan;  // no elements
       else if (p.count == 1)
         v = 0.0;
       else
         v = a.value() / p.den;
+      if (p.flags & PF_SQRT) v = sqrt(v);
       ((R*)p.red_out)[idx] = (R)v;
     }
   }
@@ -149,7 +174,7 @@ template <class C, int RED, class A> __device__ __forceinline__ void finish_full
 template <class T, class S, int NS, int NK, int RED, int V, int U, bool OUT>
 __device__ __forceinline__ void str_kernel(const Params& p) {
   typedef typename ctype<S>::type C;
-  typedef typename AccOf<C>::type A;
+  typedef typename AccSel<C, RED>::type A;
   __shared__ A smem[32];
   Scal<C, NK> k;
 #pragma unroll
@@ -189,7 +214,7 @@ __device__ __forceinline__ void str_kernel(const Params& p) {
       const long long i = i0 + g * step;
       if (full[g]) {
         C y[V];
-        if constexpr (sizeof(S) == 2 && RED != RED_NONE) {
+        if constexpr (sizeof(S) == 2 && red_additive(RED)) {
           // 16-bit storage: pairwise sum of the vector's terms, then one
           // float-float addition (spread over the accumulators by group)
           C c[V];
@@ -202,14 +227,14 @@ __device__ __forceinline__ void str_kernel(const Params& p) {
           accs[g % V].add(c[0]);
         } else {
 #pragma unroll
-          for (int l = 0; l < V; ++l) y[l] = eval_elem<T, RED>(x[g], k, err, l, accs[l], csq);
+          for (int l = 0; l < V; ++l) y[l] = eval_elem<T, RED>(x[g], k, err, l, accs[l], csq, i + l + j * nr);
         }
         if constexpr (OUT) IO<S>::template store<V>(at_out<S>(p.out, i, j, p.out_ld), y);
       } else {
 #pragma unroll
         for (int l = 0; l < V; ++l)
           if (i + l < nr) {
-            C y = eval_elem<T, RED>(x[g], k, err, l, accs[l], csq);
+            C y = eval_elem<T, RED>(x[g], k, err, l, accs[l], csq, i + l + j * nr);
             if constexpr (OUT) IO<S>::store1(at_out<S>(p.out, i + l, j, p.out_ld), y);
           }
       }
@@ -233,7 +258,7 @@ __device__ __forceinline__ void str_kernel(const Params& p) {
 template <class T, class S, int NS, int NK, int RED, int V, int U, bool OUT>
 __device__ __forceinline__ void col_kernel(const Params& p) {
   typedef typename ctype<S>::type C;
-  typedef typename AccOf<C>::type A;
+  typedef typename AccSel<C, RED>::type A;
   __shared__ A wsum[32];
   Scal<C, NK> k;
 #pragma unroll
@@ -251,6 +276,7 @@ __device__ __forceinline__ void col_kernel(const Params& p) {
     const long long j = base + gi;
     A acc;
     acc.init();
+    if constexpr (RED == RED_CSQ) csq.set_mean(p.mu[j < nc ? j : 0]);
     for (long long i0 = (wm * 32 + lane) * V; j < nc && i0 < nr; i0 += G * step * U) {
       Vals<C, NS, V> x[U];
       bool full[U];
@@ -275,13 +301,13 @@ __device__ __forceinline__ void col_kernel(const Params& p) {
         if (full[g]) {
           C y[V];
 #pragma unroll
-          for (int l = 0; l < V; ++l) y[l] = eval_elem<T, RED>(x[g], k, err, l, acc, csq);
+          for (int l = 0; l < V; ++l) y[l] = eval_elem<T, RED>(x[g], k, err, l, acc, csq, i + l);
           if constexpr (OUT) IO<S>::template store<V>(at_out<S>(p.out, i, j, p.out_ld), y);
         } else {
 #pragma unroll
           for (int l = 0; l < V; ++l)
             if (i + l < nr) {
-              C y = eval_elem<T, RED>(x[g], k, err, l, acc, csq);
+              C y = eval_elem<T, RED>(x[g], k, err, l, acc, csq, i + l);
               if constexpr (OUT) IO<S>::store1(at_out<S>(p.out, i + l, j, p.out_ld), y);
             }
         }
@@ -311,12 +337,11 @@ __device__ __forceinline__ void col_kernel(const Params& p) {
 template <class T, class S, int NS, int NK, int RED, int V, int U, bool OUT>
 __device__ __forceinline__ void row_kernel(const Params& p) {
   typedef typename ctype<S>::type C;
-  typedef typename AccOf<C>::type A;
+  typedef typename AccSel<C, RED>::type A;
   __shared__ int am_last;
   Scal<C, NK> k;
 #pragma unroll
   for (int q = 0; q < NK; ++q) k.k[q] = scalar_from_bits<C>(p.k[q]);
-  typename CsqOf<C>::type csq;
   u32 err = 0;
   const long long nr = p.n_rows, nc = p.n_cols;
   const long long nrb = p.n_row_blocks, nsp = p.n_splits, cps = p.units_per_col;
@@ -326,8 +351,12 @@ __device__ __forceinline__ void row_kernel(const Params& p) {
   const long long j1 = (j0 + cps < nc) ? j0 + cps : nc;
   const bool fullv = (i + V <= nr);
   A acc[V];
+  typename CsqOf<C>::type csq[V];  // var along dim 1: one mean per row
 #pragma unroll
-  for (int l = 0; l < V; ++l) acc[l].init();
+  for (int l = 0; l < V; ++l) {
+    acc[l].init();
+    if constexpr (RED == RED_CSQ) csq[l].set_mean(i + l < nr ? p.mu[i + l] : 0.0);
+  }
   if (i < nr) {
     for (long long jb = j0; jb < j1; jb += U) {
       Vals<C, NS, V> x[U];
@@ -354,13 +383,13 @@ __device__ __forceinline__ void row_kernel(const Params& p) {
           if (fullv) {
             C y[V];
 #pragma unroll
-            for (int l = 0; l < V; ++l) y[l] = eval_elem<T, RED>(x[g], k, err, l, acc[l], csq);
+            for (int l = 0; l < V; ++l) y[l] = eval_elem<T, RED>(x[g], k, err, l, acc[l], csq[l], j);
             if constexpr (OUT) IO<S>::template store<V>(at_out<S>(p.out, i, j, p.out_ld), y);
           } else {
 #pragma unroll
             for (int l = 0; l < V; ++l)
               if (i + l < nr) {
-                C y = eval_elem<T, RED>(x[g], k, err, l, acc[l], csq);
+                C y = eval_elem<T, RED>(x[g], k, err, l, acc[l], csq[l], j);
                 if constexpr (OUT) IO<S>::store1(at_out<S>(p.out, i + l, j, p.out_ld), y);
               }
           }
@@ -418,7 +447,7 @@ template <> struct popc<0> { static constexpr int value = 0; };
 template <class T, class S, int NS, int NK, int RED, int DIM, int TRMASK, bool OUT>
 __device__ __forceinline__ void tile_kernel(const Params& p) {
   typedef typename ctype<S>::type C;
-  typedef typename AccOf<C>::type A;
+  typedef typename AccSel<C, RED>::type A;
   constexpr int NTR = popc<TRMASK>::value;
   __shared__ C stage[NTR > 0 ? NTR : 1][TILE][TILE + 1];
   __shared__ A smem[32];
@@ -428,7 +457,7 @@ __device__ __forceinline__ void tile_kernel(const Params& p) {
 #pragma unroll
   for (int q = 0; q < NK; ++q) k.k[q] = scalar_from_bits<C>(p.k[q]);
   typename CsqOf<C>::type csq;
-  if constexpr (RED == RED_CSQ) csq.set_mean(*p.mu);
+  if constexpr (RED == RED_CSQ && DIM == -1) csq.set_mean(*p.mu);
   u32 err = 0;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const long long nr = p.n_rows, nc = p.n_cols;
@@ -483,19 +512,21 @@ __device__ __forceinline__ void tile_kernel(const Params& p) {
         A cacc;
         cacc.init();
         if (ok) {
-          C y = eval_elem<T, RED>(x, k, err, w, cacc, csq);
+          if constexpr (RED == RED_CSQ) csq.set_mean(p.mu[j]);
+          C y = eval_elem<T, RED>(x, k, err, w, cacc, csq, i);
           if constexpr (OUT) IO<S>::store1(at_out<S>(p.out, i, j, p.out_ld), y);
         }
         cacc = warp_reduce(cacc);  // the 32 rows of column j
         if (tx == 0 && j < nc) ((A*)p.partials)[ti * nc + j] = cacc;
       } else if constexpr (DIM == 1) {
         if (ok) {
-          C y = eval_elem<T, RED>(x, k, err, w, racc, csq);
+          if constexpr (RED == RED_CSQ) csq.set_mean(p.mu[i]);
+          C y = eval_elem<T, RED>(x, k, err, w, racc, csq, j);
           if constexpr (OUT) IO<S>::store1(at_out<S>(p.out, i, j, p.out_ld), y);
         }
       } else {
         if (ok) {
-          C y = eval_elem<T, RED>(x, k, err, w, acc, csq);
+          C y = eval_elem<T, RED>(x, k, err, w, acc, csq, i + j * nr);
           if constexpr (OUT) IO<S>::store1(at_out<S>(p.out, i, j, p.out_ld), y);
         }
       }
@@ -587,7 +618,7 @@ template <class C, int V> __device__ __forceinline__ void lds_vec(const C* p, C 
 template <class T, class S, int NS, int NK, int RED, int TRMASK, bool OUT, int V>
 __device__ __forceinline__ void tilev_kernel(const Params& p) {
   typedef typename ctype<S>::type C;
-  typedef typename AccOf<C>::type A;
+  typedef typename AccSel<C, RED>::type A;
   constexpr int NTR = popc<TRMASK>::value;
   constexpr int TM = TILE * V;
   constexpr int SP = TM + 16 / (int)sizeof(C);
@@ -661,13 +692,13 @@ __device__ __forceinline__ void tilev_kernel(const Params& p) {
       if (fullr) {
         C y[V];
 #pragma unroll
-        for (int l = 0; l < V; ++l) y[l] = eval_elem<T, RED>(x[w], k, err, l, accs[l], csq);
+        for (int l = 0; l < V; ++l) y[l] = eval_elem<T, RED>(x[w], k, err, l, accs[l], csq, i0 + l + j * nr);
         if constexpr (OUT) IO<S>::template store<V>(at_out<S>(p.out, i0, j, p.out_ld), y);
       } else {
 #pragma unroll
         for (int l = 0; l < V; ++l)
           if (i0 + l < nr) {
-            C y = eval_elem<T, RED>(x[w], k, err, l, accs[l], csq);
+            C y = eval_elem<T, RED>(x[w], k, err, l, accs[l], csq, i0 + l + j * nr);
             if constexpr (OUT) IO<S>::store1(at_out<S>(p.out, i0 + l, j, p.out_ld), y);
           }
       }
@@ -900,7 +931,7 @@ __device__ __forceinline__ void batch_kernel(const BatchParams bp) {
 #pragma unroll
         for (int jj = 0; jj < BATCH_COLS; ++jj) {
           if (row_ok && jb + jj < ncols) {
-            C y = eval_elem<T, RED ? RED_SUM : RED_NONE>(x, k, err, jj, acc, csq);
+            C y = eval_elem<T, RED ? RED_SUM : RED_NONE>(x, k, err, jj, acc, csq, 0);
             if (bp.has_out) IO<S>::store1(at_out<S>(pr.out, r0 + tx, c0 + jb + jj, pr.out_ld), y);
           }
         }

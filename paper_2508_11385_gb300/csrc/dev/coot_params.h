@@ -6,7 +6,31 @@
 #define COOT_MAX_SLOTS 8
 #define COOT_MAX_SCALARS_DEV 16
 
+#if defined(__CUDACC__)
+#define COOT_HD __host__ __device__
+#else
+#define COOT_HD
+#endif
+
 namespace coot {
+
+// reduction modes of a kernel pass
+enum {
+  RED_NONE = 0, RED_SUM = 1, RED_DOT = 2, RED_SSQ = 3, RED_MEAN1 = 4, RED_CSQ = 5,
+  RED_MIN = 6, RED_MAX = 7, RED_IMIN = 8, RED_IMAX = 9, RED_PROD = 10
+};
+// RED_SUM   accu / sum / mean                     sum of y
+// RED_DOT   root a%b                              sum of a*b, products kept exactly
+// RED_SSQ   norm                                  sum of y*y, products kept exactly
+// RED_MEAN1 first pass of var/stddev: sum of y, writes the mean(s) to the workspace
+// RED_CSQ   second pass of var/stddev: sum of (y - mean)^2
+// RED_MIN / RED_MAX / RED_IMIN / RED_IMAX   extreme value, or its position
+// RED_PROD  product of y
+COOT_HD constexpr bool red_additive(int r) { return r >= RED_SUM && r <= RED_CSQ; }
+COOT_HD constexpr bool red_extreme(int r) { return r >= RED_MIN && r <= RED_IMAX; }
+
+// Params::flags
+enum { PF_SQRT = 1u };
 
 struct Params {
   // leaf reads ("slots"): device address of element (0,0) of the view read
@@ -30,6 +54,7 @@ struct Params {
   long long count;
   double div;  // mean: count (or length along dim); sum: 1
   double den;  // var: N-1 or N
+  unsigned int flags;  // PF_SQRT: var's second pass writes the square root (stddev)
   // reduction result (device) and workspace
   void* red_out;
   void* partials;

@@ -45,3 +45,16 @@ extern "C" __global__ void __launch_bounds__(256) chk_batch_f32_2tr(const __grid
 K(chk_tilev_f32, 256, (tilev_kernel<T3, float, 3, 1, RED_NONE, 4, true, 4>))
 K(chk_tilev_bf16, 256, (tilev_kernel<T3, bf16, 3, 1, RED_SUM, 4, true, 8>))
 K(chk_tilev_f64, 256, (tilev_kernel<T3, double, 3, 1, RED_CSQ, 4, false, 2>))
+// statistics: extremes with positions, products, var along a dim
+K(chk_str_imin_f32, 512, (str_kernel<T3, float, 3, 1, RED_IMIN, 4, 2, false>))
+K(chk_str_max_bf16, 512, (str_kernel<T3, bf16, 3, 1, RED_MAX, 8, 1, false>))
+K(chk_str_prod_f32, 512, (str_kernel<T3, float, 3, 1, RED_PROD, 4, 2, false>))
+K(chk_str_prod_f64, 512, (str_kernel<T3, double, 3, 1, RED_PROD, 2, 2, false>))
+K(chk_str_prod_i32, 512, (str_kernel<T2, int, 2, 0, RED_PROD, 4, 2, false>))
+K(chk_col_min_i32, 512, (col_kernel<T2, int, 2, 0, RED_MIN, 4, 2, false>))
+K(chk_col_csq_f32, 512, (col_kernel<T3, float, 3, 1, RED_CSQ, 4, 2, true>))
+K(chk_row_imax_f64, 512, (row_kernel<T3, double, 3, 1, RED_IMAX, 2, 2, false>))
+K(chk_row_csq_f32, 512, (row_kernel<T3, float, 3, 1, RED_CSQ, 4, 2, false>))
+K(chk_tile_imin_dim0, 256, (tile_kernel<T3, float, 3, 1, RED_IMIN, 0, 4, false>))
+K(chk_tile_csq_dim1, 256, (tile_kernel<T3, double, 3, 1, RED_CSQ, 1, 5, false>))
+K(chk_tilev_prod_f32, 256, (tilev_kernel<T3, float, 3, 1, RED_PROD, 4, false, 4>))

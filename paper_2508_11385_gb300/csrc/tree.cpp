@@ -197,15 +197,29 @@ coot_status analyse(const coot_tree* tree, const coot_mat* leaves, int32_t n_lea
       break;
     case COOT_R_NORM_FRO: an->red_mode = RED_SSQ; an->red.dim = -1; break;
     case COOT_R_VAR:
-      if (red.norm_type != 0 && red.norm_type != 1) return set_error(COOT_ERR_INVALID, "var norm_type must be 0 or 1");
+    case COOT_R_STDDEV:
+      if (red.norm_type != 0 && red.norm_type != 1)
+        return set_error(COOT_ERR_INVALID, "var/stddev norm_type must be 0 or 1");
+      if (red.dim < -1 || red.dim > 1) return set_error(COOT_ERR_INVALID, "reduction dim %d not in {-1,0,1}", red.dim);
       an->red_mode = RED_CSQ;
-      an->red.dim = -1;
+      break;
+    case COOT_R_MIN:
+    case COOT_R_MAX:
+    case COOT_R_INDEX_MIN:
+    case COOT_R_INDEX_MAX:
+    case COOT_R_PROD:
+      if (red.dim < -1 || red.dim > 1) return set_error(COOT_ERR_INVALID, "reduction dim %d not in {-1,0,1}", red.dim);
+      an->red_mode = red.kind == COOT_R_MIN         ? RED_MIN
+                     : red.kind == COOT_R_MAX       ? RED_MAX
+                     : red.kind == COOT_R_INDEX_MIN ? RED_IMIN
+                     : red.kind == COOT_R_INDEX_MAX ? RED_IMAX
+                                                    : RED_PROD;
       break;
     default: return set_error(COOT_ERR_INVALID, "unknown reduction kind %d", red.kind);
   }
   if (is_int && (red.kind == COOT_R_MEAN || red.kind == COOT_R_NORM2 || red.kind == COOT_R_NORM_FRO ||
-                 red.kind == COOT_R_VAR))
-    return set_error(COOT_ERR_DTYPE, "mean/norm/var are not defined for INT32 trees");
+                 red.kind == COOT_R_VAR || red.kind == COOT_R_STDDEV))
+    return set_error(COOT_ERR_DTYPE, "mean/norm/var/stddev are not defined for INT32 trees");
 
   // ---- canonical form: push trans() down to the leaf reads
   std::map<std::pair<int, int>, int> memo;
@@ -380,10 +394,11 @@ Choice choose(const Analysis& an, const coot_mat* leaves, const coot_mat* out) {
     return ch;
   }
   const int dim = an.red.dim;
-  const bool sumlike = (an.red.kind == COOT_R_SUM || an.red.kind == COOT_R_MEAN);
-  if (sumlike && dim == 0)
+  // every kind that takes a dim: sum, mean, var, stddev, min, max, index_*, prod
+  const bool along = an.red.kind != COOT_R_NONE && dim >= 0;
+  if (along && dim == 0)
     ch.fam = F_COL;
-  else if (sumlike && dim == 1)
+  else if (along && dim == 1)
     ch.fam = F_ROW;
   else
     ch.fam = F_STR;
@@ -452,6 +467,11 @@ Program make_program(const Analysis& an, Family fam, bool var_two_pass) {
       case RED_SSQ: return "RED_SSQ";
       case RED_MEAN1: return "RED_MEAN1";
       case RED_CSQ: return "RED_CSQ";
+      case RED_MIN: return "RED_MIN";
+      case RED_MAX: return "RED_MAX";
+      case RED_IMIN: return "RED_IMIN";
+      case RED_IMAX: return "RED_IMAX";
+      case RED_PROD: return "RED_PROD";
     }
     return "RED_NONE";
   };
@@ -482,11 +502,19 @@ Program make_program(const Analysis& an, Family fam, bool var_two_pass) {
   } else if (fam == F_COL || fam == F_ROW) {
     const char* fn = (fam == F_COL) ? "col" : "row";
     std::vector<std::pair<int, int>> cvu = {{V, 1}, {V, 2}, {V, 4}, {1, 4}};
-    for (auto [v, u] : cvu) {
-      snprintf(buf, sizeof buf, "coot_%s_v%du%d", fn, v, u);
+    auto one = [&](const char* pass, const char* red, const char* o, int v, int u) {
+      snprintf(buf, sizeof buf, "coot_%s%s_v%du%d", fn, pass, v, u);
       wrap(buf, 512, std::string(fn) + "_kernel<T_t, S_t, " + std::to_string(NS) + ", " + std::to_string(NK) + ", " +
-                          red_name(an.red_mode) + ", " + std::to_string(v) + ", " + std::to_string(u) + ", " + outs + ">");
+                          red + ", " + std::to_string(v) + ", " + std::to_string(u) + ", " + o + ">");
       add(buf, v, u, 512);
+    };
+    for (auto [v, u] : cvu) {
+      if (var_two_pass) {
+        one("_p1", "RED_MEAN1", "false", v, u);
+        one("_p2", "RED_CSQ", outs, v, u);
+      } else {
+        one("", red_name(an.red_mode), outs, v, u);
+      }
     }
   } else if (fam == F_TILE) {
     const int dim = an.red.dim;
@@ -510,10 +538,12 @@ Program make_program(const Analysis& an, Family fam, bool var_two_pass) {
         tilev("coot_tilev_p2", "RED_CSQ");
       }
       wrap("coot_tile_p1", 256, std::string("tile_kernel<T_t, S_t, ") + std::to_string(NS) + ", " + std::to_string(NK) +
-                                    ", RED_MEAN1, -1, " + std::to_string(an.trmask) + ", false>");
+                                    ", RED_MEAN1, " + std::to_string(dim) + ", " + std::to_string(an.trmask) +
+                                    ", false>");
       add("coot_tile_p1", 1, 1, 256);
       wrap("coot_tile_p2", 256, std::string("tile_kernel<T_t, S_t, ") + std::to_string(NS) + ", " + std::to_string(NK) +
-                                    ", RED_CSQ, -1, " + std::to_string(an.trmask) + ", " + outs + ">");
+                                    ", RED_CSQ, " + std::to_string(dim) + ", " + std::to_string(an.trmask) + ", " + outs +
+                                    ">");
       add("coot_tile_p2", 1, 1, 256);
     } else {
       wrap("coot_tile", 256, std::string("tile_kernel<T_t, S_t, ") + std::to_string(NS) + ", " + std::to_string(NK) +

@@ -3,7 +3,8 @@
 Mirrors the user API the paper describes (Sec. 2-3): functions and operators
 do not compute anything, they return expression objects; evaluation happens
 when the expression is assigned (``evaluate`` / ``Mat.eval``) or reduced
-(``accu``, ``sum``, ``mean``, ``dot``, ``norm``, ``var``), and then the whole
+(``accu``, ``sum``, ``mean``, ``dot``, ``norm``, ``var``, ``stddev``, ``min``,
+``max``, ``index_min``, ``index_max``, ``prod``), and then the whole
 tree is handed to the library as one descriptor so it can run as one fused
 kernel.
 
@@ -18,6 +19,7 @@ and is not part of this library).
 """
 from __future__ import annotations
 
+import builtins
 import numbers
 import os
 import threading
@@ -178,13 +180,13 @@ class Mat(Expr):
             if t.stride(0) != 1 and t.numel() > 1:
                 raise ValueError("1-D tensors must be contiguous")
             t2 = t.unsqueeze(1)
-            n_rows, n_cols, ld = t.shape[0], 1, max(t.shape[0], 1)
+            n_rows, n_cols, ld = t.shape[0], 1, builtins.max(t.shape[0], 1)
         elif t.dim() == 2:
             t2 = t
             n_rows, n_cols = t.shape
             if n_rows > 1 and t.stride(0) != 1:
                 raise ValueError("tensor is not column-major (stride(0) must be 1); use t.t().contiguous().t()")
-            ld = t.stride(1) if n_cols > 1 else max(n_rows, 1)
+            ld = t.stride(1) if n_cols > 1 else builtins.max(n_rows, 1)
             if n_cols > 1 and ld < n_rows:
                 raise ValueError("column stride smaller than the number of rows")
         else:
@@ -360,9 +362,60 @@ def norm(x, p=2):
     return Reduction(L.R_NORM2, x)
 
 
-def var(x, norm_type=0):
-    """Two-pass variance over all elements (norm_type 0: N-1, 1: N)."""
-    return Reduction(L.R_VAR, _as_expr(x), -1, norm_type)
+def _along(x, dim):
+    x = _as_expr(x)
+    if dim is None:
+        dim = -1 if (x.n_rows == 1 or x.n_cols == 1) else 0
+    if dim not in (-1, 0, 1):
+        raise ValueError("dim must be -1 (all elements), 0 (per column) or 1 (per row)")
+    return x, dim
+
+
+def var(x, norm_type=0, dim=-1):
+    """Two-pass variance (norm_type 0: N-1, 1: N) over all elements (dim -1,
+    the default), per column (dim 0) or per row (dim 1)."""
+    x, dim = _along(x, dim)
+    return Reduction(L.R_VAR, x, dim, norm_type)
+
+
+def stddev(x, norm_type=0, dim=-1):
+    """Square root of ``var`` with the same arguments."""
+    x, dim = _along(x, dim)
+    return Reduction(L.R_STDDEV, x, dim, norm_type)
+
+
+def min(x, dim=None):  # noqa: A001 -- Armadillo's name
+    """Smallest element (NaN skipped): per column for a matrix by default, all
+    elements for a vector; dim -1 over everything, 0 per column, 1 per row."""
+    x, dim = _along(x, dim)
+    return Reduction(L.R_MIN, x, dim)
+
+
+def max(x, dim=None):  # noqa: A001 -- Armadillo's name
+    """Largest element, as ``min``."""
+    x, dim = _along(x, dim)
+    return Reduction(L.R_MAX, x, dim)
+
+
+def index_min(x, dim=None):
+    """Position (int64) of the first smallest element: the column-major linear
+    index for dim -1, the row index per column (dim 0), the column index per
+    row (dim 1); -1 where there is none.  Defaults as ``min``."""
+    x, dim = _along(x, dim)
+    return Reduction(L.R_INDEX_MIN, x, dim)
+
+
+def index_max(x, dim=None):
+    """Position of the first largest element, as ``index_min``."""
+    x, dim = _along(x, dim)
+    return Reduction(L.R_INDEX_MAX, x, dim)
+
+
+def prod(x, dim=None):
+    """Product of the elements, defaults as ``min``; no intermediate
+    overflow or underflow, the result is rounded to the accumulation type."""
+    x, dim = _along(x, dim)
+    return Reduction(L.R_PROD, x, dim)
 
 
 # ---------------------------------------------------------------------------
@@ -394,10 +447,10 @@ def evaluate(expr, out=None, reduction=None, red_out=None, fused=True, stream=No
     if reduction is not None:
         red = L.reduce(reduction.kind, reduction.dim, reduction.norm_type)
         if red_out is None:
-            acc = _ACC[dt]
-            if reduction.dim == 0 and reduction.kind in (L.R_SUM, L.R_MEAN):
+            acc = torch.int64 if reduction.kind in (L.R_INDEX_MIN, L.R_INDEX_MAX) else _ACC[dt]
+            if reduction.dim == 0:
                 rt = torch.empty((1, nc), dtype=acc, device=dev)  # a row vector: contiguous either way
-            elif reduction.dim == 1 and reduction.kind in (L.R_SUM, L.R_MEAN):
+            elif reduction.dim == 1:
                 rt = torch.empty((nr, 1), dtype=acc, device=dev)
             else:
                 rt = torch.empty((), dtype=acc, device=dev)

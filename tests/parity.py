@@ -15,11 +15,11 @@ import torch
 
 import coot_rpn
 import oracle
+import rpn
 import paper_2508_11385_gb300 as coot
 from paper_2508_11385_gb300 import workloads
 
 REL = {"f32": 1e-6, "bf16": 1e-6, "f16": 1e-6, "f64": 1e-13, "i32": 0.0}
-RED_TOKENS = coot_rpn._RED
 
 
 def host(tensors):
@@ -28,7 +28,7 @@ def host(tensors):
 
 def split(program):
     toks = program.split()
-    if toks and toks[-1] in RED_TOKENS:
+    if toks and coot_rpn.is_reduction(toks[-1]):
         return " ".join(toks[:-1]), toks[-1]
     return program, None
 
@@ -95,6 +95,87 @@ def compare_reduction(gpu, res, dtype, what="", rel=None):
     return float(np.max(err[fin] / np.maximum(np.abs(v[fin]), 1e-300))) if np.any(fin) else 0.0
 
 
+def host_values(h, dtype):
+    """Values of a host leaf as float64 (BF16/FP16 arrive as uint16 bits)."""
+    if dtype == "bf16":
+        return (h.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    if dtype == "f16":
+        return h.view(np.float16).astype(np.float64)
+    return h.astype(np.float64)
+
+
+def _groups(a, dim):
+    """The reduction groups of a matrix: all elements in column-major order
+    (dim -1), its columns (dim 0) or its rows (dim 1)."""
+    if dim == -1:
+        return [a.ravel(order="F")]
+    if dim == 0:
+        return [a[:, j] for j in range(a.shape[1])]
+    return [a[i, :] for i in range(a.shape[0])]
+
+
+def _first_extreme(vals, want_max):
+    """First position of the smallest (largest) non-NaN value, -1 if none."""
+    best = -1
+    for q, x in enumerate(vals):
+        if np.isnan(x):
+            continue
+        if best < 0 or (x > vals[best] if want_max else x < vals[best]):
+            best = q
+    return best
+
+
+def compare_index(gpu, program, hs, dtype, what=""):
+    """index_min / index_max: where several positions are correct within the
+    oracle's error bounds, the GPU's must be one of them.
+
+    The GPU decides in its compute precision.  A position k is a possible
+    first minimum when some set of values inside the bounds makes it one:
+    lo[k] < hi[j] for every earlier j and lo[k] <= hi[j] for every later j
+    (lo, hi = value -/+ bound; for index_max the same on negated values).  With
+    zero bounds (bare leaves, integer trees) that is the exact first position.
+    Trees of + - * / sqrt only are also replayed with every node rounded to
+    the compute type (rpn.eval_emulated, IEEE round-to-nearest as on the
+    device), and then the position must be the replay's exactly."""
+    tree, tok = split(program)
+    head, _, rest = tok.partition(":")
+    dim = int(rest) if rest else -1
+    want_max = head == "index_max"
+    ry = oracle.evaluate(tree, hs, dtype)
+    ro = oracle.evaluate(program, hs, dtype)
+    g = gpu.detach().cpu().numpy().astype(np.int64).reshape(ro.value.shape)
+    ko = ro.value.astype(np.int64).ravel(order="F")
+    kg = g.ravel(order="F")
+    sign = -1.0 if want_max else 1.0
+    vs = _groups(ry.value * sign, dim)
+    bs = _groups(ry.bound, dim) if dtype != "i32" else _groups(np.zeros_like(ry.value, dtype=np.float64), dim)
+    assert len(vs) == len(kg), (len(vs), kg.shape)
+    for o, (v, b) in enumerate(zip(vs, bs)):
+        k = int(kg[o])
+        if ko[o] < 0:
+            assert k == -1, "%s: output %d: oracle has no element, gpu index %d" % (what, o, k)
+            continue
+        assert 0 <= k < len(v) and not np.isnan(v[k]), "%s: output %d: gpu index %d invalid" % (what, o, k)
+        lo = v - b
+        hi = v + b
+        ok = ~np.isnan(v)
+        early = ok.copy()
+        early[k:] = False
+        late = ok.copy()
+        late[:k + 1] = False
+        assert np.all(lo[k] < hi[early]) and np.all(lo[k] <= hi[late]), (
+            "%s: output %d: gpu index %d (value %r) cannot be the first extreme; oracle index %d (value %r)" % (
+                what, o, k, sign * v[k], ko[o], sign * v[ko[o]]))
+    toks = tree.split()
+    if dtype != "i32" and not any(t in ("exp", "log") or t.startswith("submat") for t in toks):
+        ftype = np.float64 if dtype == "f64" else np.float32
+        y = rpn.eval_emulated(tree, [host_values(h, dtype).astype(ftype) for h in hs], ftype).astype(np.float64)
+        for o, grp in enumerate(_groups(y, dim)):
+            ke = _first_extreme(grp, want_max)
+            assert int(kg[o]) == ke, "%s: output %d: gpu index %d, %s replay %d" % (
+                what, o, int(kg[o]), ftype.__name__, ke)
+
+
 def check(program, tensors, dtype, fused=True, materialise=False, out_dtype=None):
     """Evaluate `program` on the GPU and with the oracle; assert parity.
     Returns (Y, r) of the GPU."""
@@ -106,8 +187,11 @@ def check(program, tensors, dtype, fused=True, materialise=False, out_dtype=None
         ry = oracle.evaluate(tree, hs, dtype, out_dtype)
         compare_matrix(Y, ry, dtype, program)
     if red is not None:
-        rr = oracle.evaluate(program, hs, dtype)
-        compare_reduction(r, rr, dtype, program)
+        if red.partition(":")[0] in ("index_min", "index_max"):
+            compare_index(r, program, hs, dtype, program)
+        else:
+            rr = oracle.evaluate(program, hs, dtype)
+            compare_reduction(r, rr, dtype, program)
     return Y, r
 
 
