@@ -534,6 +534,58 @@ static int reduce(ctx_t* cx, int kind, val_t* x, val_t* y, orc_result* res) {
 }
 
 /* ------------------------------------------------------------------ */
+/* ------------------------------------------------------------------ */
+/* cumsum: prefix sums along a dimension (Armadillo's cumsum, Sec. 2)  */
+/* ------------------------------------------------------------------ */
+/*
+ * dim 0 runs down each column, dim 1 along each row; dim -1 is Armadillo's
+ * default: along the vector for a row or column vector, else dim 0.  The
+ * value is the exact prefix sum (double-double running sum, rounded once to
+ * double).  Bound of output k of a line: the sum of the element bounds plus
+ * (k-1) u |y_1| + ... + |y_k| with u the compute type's unit roundoff -- the
+ * error bound of a sum of k terms in the compute type in any order of
+ * additions -- so that an FP32 prefix sum computed any way passes.  An
+ * FP32 prefix beyond the format's range is +-inf.  INT32 trees wrap modulo
+ * 2^32 like every INT32 node.
+ */
+static int cumsum(ctx_t* cx, int dim, val_t* x, val_t* out) {
+  const int64_t r = x->r, c = x->c;
+  if (dim < 0) dim = (r == 1) ? 1 : 0; /* a row vector runs along dim 1 */
+  if (val_alloc(cx, out, r, c)) return -1;
+  const int64_t nline = (dim == 0) ? c : r, len = (dim == 0) ? r : c;
+  const double u = (cx->ct == ORC_F64) ? ldexp(1.0, -53) : ldexp(1.0, -24);
+  for (int64_t o = 0; o < nline; ++o) {
+    double sh = 0.0, sl = 0.0, plain = 0.0, asum = 0.0, bsum = 0.0;
+    int64_t isum = 0;
+    int special = 0;
+    for (int64_t t = 0; t < len; ++t) {
+      const int64_t q = (dim == 0) ? t + o * r : o + t * r;
+      if (cx->is_int) {
+        isum = (int64_t)((uint64_t)isum + (uint64_t)x->iv[q]);
+        out->iv[q] = wrap32(isum);
+        continue;
+      }
+      const double y = x->v[q];
+      plain += y;
+      if (!isfinite(y)) special = 1;
+      /* TwoSum of the running high part and y, error into the low part */
+      const double s2 = sh + y;
+      const double bp = s2 - sh;
+      const double e = (sh - (s2 - bp)) + (y - bp);
+      sh = s2;
+      sl += e;
+      asum += fabs(y);
+      bsum += x->b[q];
+      double v = special ? plain : sh + sl;
+      double b = special ? 0.0 : bsum + (double)t * u * asum + orc_ulp(v, ORC_F64);
+      clamp_to_range(cx, &v, &b);
+      out->v[q] = v;
+      out->b[q] = finite_or_zero_bound(v, b);
+    }
+  }
+  return 0;
+}
+
 /* statistics along a dimension: min, max, index_min, index_max, prod, */
 /* var, stddev (Armadillo's statistics functions, Sec. 2)               */
 /* ------------------------------------------------------------------ */
@@ -762,13 +814,13 @@ int orc_eval(const char* program, const orc_mat* leaves, int32_t n_leaves, int32
   res->is_int = cx.is_int;
 
   val_t st[MAX_STACK];
-  int sp = 0, rc = -1, reduced = 0;
+  int sp = 0, rc = -1, reduced = 0, scanned = 0;
   size_t plen = strlen(program);
   char* buf = (char*)malloc(plen + 1);
   memcpy(buf, program, plen + 1);
   char* save = NULL;
   for (char* tok = strtok_r(buf, " \t\n", &save); tok; tok = strtok_r(NULL, " \t\n", &save)) {
-    if (reduced) {
+    if (reduced || scanned) {
       snprintf(res->err, sizeof res->err, "tokens after the reduction");
       goto done;
     }
@@ -829,6 +881,18 @@ int orc_eval(const char* program, const orc_mat* leaves, int32_t n_leaves, int32
     else if (!strcmp(tok, "var") || !strcmp(tok, "var:0")) rop = R_VAR0;
     else if (!strcmp(tok, "var:1")) rop = R_VAR1;
 
+    if (!strcmp(tok, "cumsum") || !strcmp(tok, "cumsum:0") || !strcmp(tok, "cumsum:1")) {
+      if (sp != 1 || st[0].kind != V_MAT) {
+        snprintf(res->err, sizeof res->err, "cumsum needs exactly one matrix operand");
+        goto done;
+      }
+      val_t out;
+      if (cumsum(&cx, tok[6] == ':' ? tok[7] - '0' : -1, &st[0], &out)) goto done;
+      val_free(&st[0]);
+      st[0] = out;
+      scanned = 1;
+      continue;
+    }
     int sop, sdim, snorm;
     if (rop < 0 && parse_stat(tok, &sop, &sdim, &snorm)) {
       if (sp != 1 || st[0].kind != V_MAT) {

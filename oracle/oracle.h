@@ -42,6 +42,9 @@
  *   stddev stddev:1   vardim:D:N stddevdim:D:N  (N is norm_type as for var)
  *   min/max skip NaN and keep the first of equal values; an empty or all-NaN
  *   range gives NaN (0 for INT32) and index -1.
+ * or one final scan, which leaves a matrix of the tree's shape:
+ *   cumsum cumsum:0 cumsum:1   prefix sums down each column (0) or along each
+ *                     row (1); plain cumsum runs along a vector, else dim 0
  */
 #ifndef COOT_ORACLE_H
 #define COOT_ORACLE_H

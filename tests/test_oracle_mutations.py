@@ -23,6 +23,12 @@ MUTATIONS = [
     ("exp bound propagation", "bv = (ba == 0.0) ? 0.0 : v * expm1(ba);", "bv = 0.0;"),
     ("mean divisor", "        s = s / (double)len;", "        s = s / (double)nout;"),
     ("gradient of division", "case B_DIV: da = 1.0 / b; db = -a / (b * b);", "case B_DIV: da = 1.0 / b; db = a / (b * b);"),
+    ("extreme keeps the last tie", "if (best < 0 || (want_min ? v < bv : v > bv)) {",
+     "if (best < 0 || (want_min ? v <= bv : v >= bv)) {"),
+    ("product exponent", "          E += k;\n          const double p = ph * m;", "          const double p = ph * m;"),
+    ("cumsum default direction", "if (dim < 0) dim = (r == 1) ? 1 : 0;", "if (dim < 0) dim = (r == 1) ? 0 : 1;"),
+    ("cumsum summation bound", "bsum + (double)t * u * asum + orc_ulp(v, ORC_F64)", "bsum + orc_ulp(v, ORC_F64)"),
+    ("cumsum compensation", "const double e = (sh - (s2 - bp)) + (y - bp);", "const double e = 0.0;"),
 ]
 
 

@@ -680,3 +680,81 @@ def test_prod_follows_ieee_special_values_and_rounds_to_the_result_type(orc):
     # and is rounded once to float: 3 * (1 + 2^-23) * (1 + 2^-23)
     x = np.float32(1 + 2.0 ** -23)
     assert orc.evaluate("A prod", [f([3.0, x, x])], "f32").value[0, 0] == float(np.float32(3.0 * float(x) ** 2))
+
+
+# ------------------------------------------------------------ cumsum
+
+def test_cumsum_of_ones_counts(orc):
+    a = F(np.ones((7, 3)))
+    v = orc.evaluate("A cumsum", [a], "f64").value
+    assert np.array_equal(v, np.tile(np.arange(1, 8, dtype=np.float64)[:, None], (1, 3)))
+    v1 = orc.evaluate("A cumsum:1", [a], "f64").value
+    assert np.array_equal(v1, np.tile(np.arange(1, 4, dtype=np.float64)[None, :], (7, 1)))
+
+
+@pytest.mark.parametrize("dim", [0, 1])
+def test_cumsum_of_integers_matches_numpy_exactly(orc, dim):
+    g = np.random.default_rng(80)
+    a = g.integers(-1000, 1000, size=(33, 17)).astype(np.float64)
+    assert np.array_equal(orc.evaluate("A cumsum:%d" % dim, [F(a)], "f64").value, np.cumsum(a, axis=dim))
+    b = a.astype(np.int32)
+    assert np.array_equal(orc.evaluate("A cumsum:%d" % dim, [F(b)], "i32").value, np.cumsum(b, axis=dim))
+
+
+def test_cumsum_default_runs_along_a_vector(orc):
+    r = F(np.array([[1.0, 2.0, 3.0, 4.0]]))
+    assert np.array_equal(orc.evaluate("A cumsum", [r], "f64").value, [[1.0, 3.0, 6.0, 10.0]])
+    c = F(np.array([[1.0], [2.0], [3.0]]))
+    assert np.array_equal(orc.evaluate("A cumsum", [c], "f64").value, [[1.0], [3.0], [6.0]])
+
+
+def test_cumsum_prefixes_are_exactly_rounded(orc):
+    g = np.random.default_rng(81)
+    x = g.normal(size=(500, 1)) * np.exp(g.normal(size=(500, 1)) * 8)  # wide exponent range: cancellations
+    v = orc.evaluate("A cumsum", [F(x)], "f64").value[:, 0]
+    want = [math.fsum(x[:k + 1, 0]) for k in range(500)]
+    assert np.array_equal(v, want)
+
+
+def test_cumsum_int32_wraps(orc):
+    x = np.array([[2 ** 31 - 1], [5], [-7], [-(2 ** 31)], [-3]], dtype=np.int32)
+    with np.errstate(over="ignore"):
+        want = np.cumsum(x, axis=0, dtype=np.int32)
+    assert np.array_equal(orc.evaluate("A cumsum", [F(x)], "i32").value, want)
+
+
+def test_cumsum_rows_are_cumsum_of_the_transpose(orc):
+    g = np.random.default_rng(82)
+    a = g.normal(size=(9, 14))
+    v1 = orc.evaluate("A cumsum:1", [F(a)], "f64").value
+    v0 = orc.evaluate("A trans cumsum:0", [F(a)], "f64").value
+    assert np.array_equal(v1, v0.T)
+
+
+@pytest.mark.parametrize("dim", [0, 1])
+def test_cumsum_bound_covers_sequential_fp32(orc, dim):
+    # numpy's float32 cumsum adds in order in FP32: the recursive summation
+    # the bound (k-1) u sum|y| is written for
+    g = np.random.default_rng(83)
+    A = g.normal(size=(700, 40)).astype(np.float32)
+    B = g.normal(size=(700, 40)).astype(np.float32)
+    prog = "A B % A +"
+    y = rpn.eval_emulated(prog, [A, B], np.float32)
+    dev = np.cumsum(y, axis=dim, dtype=np.float32).astype(np.float64)
+    r = orc.evaluate(prog + " cumsum:%d" % dim, [F(A), F(B)], "f32")
+    assert np.all(np.abs(dev - r.value) <= r.bound)
+    # a bare leaf: no element error, only the summation's
+    dev = np.cumsum(A, axis=dim, dtype=np.float32).astype(np.float64)
+    r = orc.evaluate("A cumsum:%d" % dim, [F(A)], "f32")
+    assert np.all(np.abs(dev - r.value) <= r.bound)
+    assert np.any(np.abs(dev - r.value) > 0)  # the order of additions shows
+
+
+def test_cumsum_overflow_and_special_values(orc):
+    f = lambda v: F(np.array(v, dtype=np.float32).reshape(-1, 1))
+    # a prefix beyond the FP32 range is inf (prefixes after it are exact
+    # values again, which a running sum cannot return: not compared on the GPU)
+    v = orc.evaluate("A cumsum", [f([3e38, 3e38, -3e38])], "f32").value[:, 0]
+    assert v[0] == np.float32(3e38) and v[1] == np.inf and v[2] == pytest.approx(3e38, rel=1e-7)
+    w = orc.evaluate("A cumsum", [f([1.0, np.inf, 2.0, -np.inf, 5.0])], "f32").value[:, 0]
+    assert w[0] == 1.0 and w[1] == np.inf and w[2] == np.inf and np.isnan(w[3]) and np.isnan(w[4])
