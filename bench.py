@@ -127,6 +127,18 @@ def build_expr(program, mats):
             red = coot.norm(st[-1], "fro")
         elif tok in ("var", "var:1"):
             red = coot.var(st[-1], 1 if tok == "var:1" else 0)
+        elif tok in ("stddev", "stddev:1"):
+            red = coot.stddev(st[-1], 1 if tok == "stddev:1" else 0)
+        elif tok.partition(":")[0] in ("min", "max", "index_min", "index_max", "prod"):
+            head, _, d = tok.partition(":")
+            red = getattr(coot, head)(st[-1], int(d) if d else -1)
+        elif tok.partition(":")[0] == "cumsum":
+            d = tok.partition(":")[2]
+            red = coot.cumsum(st[-1], int(d) if d else None)
+        elif tok.partition(":")[0] in ("vardim", "stddevdim"):
+            head, _, rest = tok.partition(":")
+            d, nt = map(int, rest.split(":"))
+            red = (coot.var if head == "vardim" else coot.stddev)(st[-1], nt, d)
         elif tok == "dot":
             b, a = st.pop(), st.pop()
             red = coot.dot(a, b)
@@ -154,15 +166,16 @@ class Call:
         nr, nc = e.shape
         dt = self.leaf_mats[0].dtype
         dev = tensors[0].device
-        if red is None:
+        if red is None or red.kind == L.R_CUMSUM:
+            # element-wise result, or a scan written where it would be
             self.out_t = torch.empty((nc, nr), dtype=tensors[0].dtype, device=dev).t()
             self.out_m = coot.Mat(self.out_t).cmat()
-            self.red = L.reduce()
+            self.red = L.reduce() if red is None else L.reduce(red.kind, red.dim)
             self.red_t = None
         else:
             self.out_t, self.out_m = None, None
             self.red = L.reduce(red.kind, red.dim, red.norm_type)
-            acc = E._ACC[dt]
+            acc = torch.int64 if red.kind in (L.R_INDEX_MIN, L.R_INDEX_MAX) else E._ACC[dt]
             if red.dim == 0:
                 self.red_t = torch.empty((1, nc), dtype=acc, device=dev)
             elif red.dim == 1:
@@ -298,7 +311,7 @@ def run_side(args):
     stream = torch.cuda.current_stream(dev)
     fn = {"batched": lambda: bench_batched(args, dev, stream), "adjoint": lambda: bench_adjoint(dev, stream),
           "precision": lambda: bench_precision(dev, stream, errors=args.precision_errors),
-          "graph_chain": lambda: bench_graph(dev, stream)}[args.only]
+          "graph_chain": lambda: bench_graph(dev, stream), "stats": lambda: bench_stats(args, dev, stream)}[args.only]
     print(json.dumps({args.only: fn()}))
 
 
@@ -565,7 +578,44 @@ def run_extras(args, leaves, calls, per_tree_ms, bytes_per, dev, stream, peak):
         res["precision"] = bench_precision(dev, stream, errors=args.precision_errors)
     except Exception as e:
         res["precision"] = {"error": repr(e)[:300]}
+    try:
+        res["stats"] = bench_stats(args, dev, stream)
+    except Exception as e:
+        res["stats"] = {"error": repr(e)[:300]}
     return res
+
+
+STATS = ["accu", "min", "index_max", "prod", "stddev", "sum:0", "min:0", "index_max:0", "prod:0", "vardim:0:0",
+         "sum:1", "max:1", "index_min:1", "prod:1", "stddevdim:1:1", "cumsum:0", "cumsum:1"]
+STATS_T = ["accu", "sum:0", "index_min:0", "vardim:0:0", "sum:1", "max:1", "prod:1", "cumsum:0"]
+
+
+def bench_stats(args, dev, stream, peak=None):
+    """Statistics fused onto Y = A % B + C at n x n FP32 (three reads), each
+    through a prepared C-ABI call; accu is the additive reference.  Also the
+    transposed form Y = trans(A) % B + C along both dims."""
+    import torch
+
+    from paper_2508_11385_gb300 import workloads
+
+    peak = peak or load_peaks()[0]
+    lv = workloads.large_trees("f32", n=args.n, n_leaves=3, device=dev)
+    sp = stream.cuda_stream
+    out = {}
+    progs = [("A B % C + " + r, r) for r in STATS]
+    progs += [("A trans B % C + " + r, "trans " + r) for r in STATS_T]
+    for prog, name in progs:
+        c = Call(prog, lv)
+        c(sp)
+        torch.cuda.synchronize()
+        ms = time_calls(lambda: c(sp), stream, reps=10)
+        info = c.info()
+        gbs = info["algorithmic_bytes"] / ms / 1e6
+        out[name] = {"ms": round(ms, 4), "gbs": round(gbs, 1), "frac": round(gbs / peak, 3),
+                     "kernel": info["kernel"], "launches": info["n_launches"]}
+    del lv
+    torch.cuda.empty_cache()
+    return out
 
 
 def bench_batched(args, dev, stream):
@@ -849,7 +899,7 @@ def main():
     ap.add_argument("--only", default=None, help="time one tree of the workload (profiling); implies --quick")
     args = ap.parse_args()
     if args.only:
-        side = ("batched", "adjoint", "precision", "graph_chain")
+        side = ("batched", "adjoint", "precision", "graph_chain", "stats")
         if args.only not in [t[0] for t in TREES] + list(side):
             ap.error("--only: one of %s" % ", ".join([t[0] for t in TREES] + list(side)))
         args.quick = True

@@ -150,9 +150,15 @@ typedef enum {
                           linear index for dim -1, row index along dim 0, column
                           index along dim 1; -1 when there is none             */
   COOT_R_INDEX_MAX = 12, /* position of the first largest element, as above      */
-  COOT_R_PROD = 13     /* product; no intermediate overflow or underflow (the
+  COOT_R_PROD = 13,    /* product; no intermediate overflow or underflow (the
                           exponent is carried apart), the result is rounded to
                           the accumulation type; empty gives 1                 */
+  COOT_R_CUMSUM = 14   /* not a reduction: the prefix sums of Y along dim (0 down
+                          each column, 1 along each row, -1 along a vector or
+                          else dim 0) are written to `out` (required, the
+                          tree's shape and dtype) instead of Y; red_out is
+                          unused.  FP32 compute sums in float-float and rounds
+                          each output once; I32 wraps modulo 2^32           */
 } coot_red_kind;
 
 typedef struct {

@@ -170,6 +170,7 @@ int occupancy(cg::Module* m, const std::string& name, int block) {
 // what one launch of a fused program needs
 struct Launch {
   std::string kname, kname2;  // kname2: second pass of var
+  std::string kname_pre;      // launched before kname: the totals pass of a segmented cumsum
   int grid = 1, block = 256, vec = 1, unroll = 1;
   size_t tickets = 1, partial_bytes = 0;
   size_t mu_offset = 0;  // var/stddev along a dim: byte offset of the means in the partials
@@ -229,16 +230,60 @@ void shape_launch(coot_ctx* ctx, const cg::Analysis& an, const cg::Choice& ch, c
     // tilev tiles are 32 x vec rows tall; the scalar tile kernel's 32
     const int64_t ntr = ceil_div(R, 32 * std::max(k.vec, 1)), ntc = ceil_div(C, 32);
     const int64_t tiles = ntr * ntc;
-    L->grid = (int)std::max<int64_t>(1, std::min(tiles, resident));
-    if (an.red.dim == 0) {
-      L->partial_bytes = (size_t)(ntr * C * ab);
-      L->tickets = (size_t)std::max<int64_t>(ntc, 1);
-    } else if (an.red.dim == 1) {
-      L->partial_bytes = (size_t)(ntc * R * ab);
-      L->tickets = (size_t)std::max<int64_t>(ntr, 1);
+    if (an.red.dim == 0 || an.red.dim == 1) {
+      // blocks = strips x segments; `split` segments per strip when given
+      // (tuning), else about two waves of resident blocks
+      const int64_t strips = std::max<int64_t>(an.red.dim == 0 ? ntc : ntr, 1);
+      const int64_t len = std::max<int64_t>(an.red.dim == 0 ? ntr : ntc, 1);
+      int64_t nseg = split > 0 ? split : ceil_div(2 * resident, strips);
+      nseg = std::max<int64_t>(1, std::min(nseg, len));
+      nseg = ceil_div(len, ceil_div(len, nseg));  // no empty segment
+      p.n_splits = nseg;
+      L->grid = (int)(strips * nseg);
+      const int64_t no = (an.red.dim == 0) ? C : R;
+      L->partial_bytes = (nseg > 1) ? (size_t)(nseg * no * ab) : 0;
+      L->tickets = (size_t)strips;
     } else {
+      L->grid = (int)std::max<int64_t>(1, std::min(tiles, resident));
       L->partial_bytes = (size_t)L->grid * ab;
       L->tickets = 1;
+    }
+  }
+  if (ch.fam == cg::F_SCAN) {
+    const int64_t ab8 = 8;  // one running sum per (line, segment)
+    L->tickets = 1;
+    L->kname_pre.clear();
+    if (an.red.dim == 0) {
+      // a warp per (column, segment) of 32 V-row steps
+      const int64_t wpb = block / 32;
+      const int64_t steps = std::max<int64_t>(1, ceil_div(R, 32 * (int64_t)k.vec));
+      const int64_t resident_warps = resident * wpb;
+      int64_t nseg = split > 0 ? split : ceil_div(2 * resident_warps, std::max<int64_t>(C, 1));
+      nseg = std::max<int64_t>(1, std::min(nseg, steps));
+      const int64_t sps = ceil_div(steps, nseg);
+      nseg = ceil_div(steps, sps);
+      p.n_splits = nseg;
+      p.units_per_col = sps;
+      const int64_t units = std::max<int64_t>(C, 1) * nseg;
+      L->grid = (int)std::max<int64_t>(1, std::min(ceil_div(units, wpb), 4 * resident));
+      L->partial_bytes = (nseg > 1) ? (size_t)(C * nseg * ab8) : 0;
+    } else {
+      // a thread per V rows of a (row block, column segment)
+      const int64_t nrb = std::max<int64_t>(1, ceil_div(R, (int64_t)block * k.vec));
+      int64_t nseg = split > 0 ? split : ceil_div(2 * resident, nrb);
+      nseg = std::max<int64_t>(1, std::min(nseg, std::max<int64_t>(C, 1)));
+      const int64_t cps = std::max<int64_t>(1, ceil_div(std::max<int64_t>(C, 1), nseg));
+      nseg = std::max<int64_t>(1, ceil_div(std::max<int64_t>(C, 1), cps));
+      p.n_row_blocks = nrb;
+      p.n_splits = nseg;
+      p.units_per_col = cps;
+      L->grid = (int)(nrb * nseg);
+      L->partial_bytes = (nseg > 1) ? (size_t)(nseg * R * ab8) : 0;
+    }
+    if (p.n_splits > 1) {
+      std::string pre = k.name;
+      pre.replace(pre.find("coot_scan_"), 10, "coot_scan_t_");
+      L->kname_pre = pre;
     }
   }
   // var / stddev along a dim: the first pass's means follow the partials
@@ -273,7 +318,7 @@ int default_variant(const cg::Program& pg, const cg::Choice& ch) {
   int best = -1;
   for (int i = 0; i < (int)pg.kernels.size(); ++i) {
     const cg::KernelSpec& k = pg.kernels[i];
-    if (k.name.find("_p2") != std::string::npos) continue;
+    if (k.name.find("_p2") != std::string::npos || k.name.find("_t_") != std::string::npos) continue;
     if (!ch.vec_ok && k.vec > 1) continue;
     if (best < 0) best = i;
     if (ch.vec_ok && k.vec > 1 && k.unroll == 2) return i;
@@ -349,6 +394,30 @@ std::string tune_key(const cg::Program& pg, const cg::Choice& ch) {
 // ---------------------------------------------------------------------------
 static coot_status run_fused(coot_ctx* ctx, const cg::Analysis& an, const coot_mat* leaves, const coot_mat* out,
                              void* red_out, cudaStream_t stream, bool warm_only) {
+  if (an.scan() && an.any_trans) {
+    // a tree with transposed reads is first materialised into out by the
+    // tile kernel, then scanned in place (out read and written by the same
+    // thread)
+    cg::Analysis a1 = an;
+    a1.red = coot_reduce{COOT_R_NONE, -1, 0, 0};
+    a1.red_mode = cg::RED_NONE;
+    coot_status s1 = run_fused(ctx, a1, leaves, out, nullptr, stream, warm_only);
+    if (s1) return s1;
+    coot_node leaf{};
+    leaf.op = COOT_N_LEAF;
+    leaf.a = leaf.b = -1;
+    coot_tree lt{1, 0, &leaf};
+    cg::Analysis a2;
+    s1 = cg::analyse(&lt, out, 1, out, an.red, &a2);
+    if (s1) return s1;
+    const int n1 = ctx->last.n_launches;
+    s1 = run_fused(ctx, a2, out, out, nullptr, stream, warm_only);
+    if (s1 || warm_only) return s1;
+    // report the whole evaluation: both steps' launches, the tree's bytes
+    ctx->last.n_launches += n1;
+    ctx->last.algorithmic_bytes = algorithmic_bytes(an, out);
+    return COOT_OK;
+  }
   const bool var = an.two_pass();
   cg::Choice ch = cg::choose(an, leaves, out);
   const int64_t count = an.nr * an.nc;
@@ -434,6 +503,10 @@ static coot_status run_fused(coot_ctx* ctx, const cg::Analysis& an, const coot_m
   bind_workspace(ctx, an, &L);
   if (warm_only) return COOT_OK;
 
+  if (!L.kname_pre.empty()) {
+    s = launch_kernel(m, L.kname_pre, L.grid, L.block, &p, stream);
+    if (s) return s;
+  }
   s = launch_kernel(m, L.kname, L.grid, L.block, &p, stream);
   if (s) return s;
   if (var) {
@@ -447,7 +520,7 @@ static coot_status run_fused(coot_ctx* ctx, const cg::Analysis& an, const coot_m
   li.block = L.block;
   li.vec = L.vec;
   li.unroll = L.unroll;
-  li.n_launches = var ? 2 : 1;
+  li.n_launches = (var || !L.kname_pre.empty()) ? 2 : 1;
   li.algorithmic_bytes = algorithmic_bytes(an, out);
   return COOT_OK;
 }
@@ -481,10 +554,10 @@ coot_status tune(coot_ctx* ctx, const cg::Analysis& an, const cg::Choice& ch, co
   coot_status st = COOT_OK;
   for (int ki = 0; ki < (int)pg.kernels.size() && st == COOT_OK; ++ki) {
     const cg::KernelSpec& k = pg.kernels[ki];
-    if (k.name.find("_p2") != std::string::npos) continue;
+    if (k.name.find("_p2") != std::string::npos || k.name.find("_t_") != std::string::npos) continue;
     if (!ch.vec_ok && k.vec > 1) continue;
     std::vector<int> blocks;
-    if (ch.fam == cg::F_TILE) blocks = {256};
+    if (ch.fam == cg::F_TILE || ch.fam == cg::F_SCAN) blocks = {256};
     else if (ch.fam == cg::F_ROW) blocks = {128, 256, 512};
     else blocks = {256, 512};
     for (int block : blocks) {
@@ -495,6 +568,14 @@ coot_status tune(coot_ctx* ctx, const cg::Analysis& an, const cg::Choice& ch, co
       std::vector<int> splits = {0};
       if (ch.fam == cg::F_COL)
         for (int g = 1; g <= block / 32; g *= 2) splits.push_back(g);
+      if (ch.fam == cg::F_TILE && an.red.dim >= 0) {
+        // segments per strip: one, and about 1/2, 1, 4 waves of resident blocks
+        const int64_t strips = std::max<int64_t>(ceil_div(an.red.dim == 0 ? an.nc : an.nr, 32), 1);
+        const int64_t res = (int64_t)ctx->sms * std::max(occ, 1);
+        splits.push_back(1);
+        for (int64_t w2 : {1, 2, 8}) splits.push_back((int)std::max<int64_t>(1, ceil_div(w2 * res, 2 * strips)));
+      }
+      if (ch.fam == cg::F_SCAN) splits.push_back(1);  // one pass, no segments
       for (int bps : bpss)
       for (int split : splits) {
         Launch L = base;
@@ -509,7 +590,8 @@ coot_status tune(coot_ctx* ctx, const cg::Analysis& an, const cg::Choice& ch, co
         float times[3];
         for (int rep = 0; rep < 4 && st == COOT_OK; ++rep) {
           cudaEventRecord(e0, stream);
-          st = launch_kernel(m, k.name, L.grid, L.block, &L.p, stream);
+          if (!L.kname_pre.empty()) st = launch_kernel(m, L.kname_pre, L.grid, L.block, &L.p, stream);
+          if (!st) st = launch_kernel(m, k.name, L.grid, L.block, &L.p, stream);
           if (!st && var) st = launch_kernel(m, k2, L.grid, L.block, &L.p, stream);
           cudaEventRecord(e1, stream);
           cudaEventSynchronize(e1);
@@ -778,8 +860,9 @@ extern "C" coot_status coot_eval_unfused(coot_ctx* ctx, const coot_tree* tree, c
       mt = coot_tree{1, 0, mini};
     }
     cg::Analysis man;
-    s = cg::analyse(&mt, ops, nops, nullptr, red, &man);
-    if (!s) s = run_fused(ctx, man, ops, nullptr, red_out, stream, false);
+    const coot_mat* ro = (red.kind == COOT_R_CUMSUM) ? out : nullptr;  // cumsum scans out in place
+    s = cg::analyse(&mt, ops, nops, ro, red, &man);
+    if (!s) s = run_fused(ctx, man, ops, ro, red_out, stream, false);
     if (s) {
       release();
       return s;

@@ -33,7 +33,7 @@ using coot::RED_PROD;
 using coot::red_additive;
 using coot::red_extreme;
 
-enum Family { F_STR = 0, F_COL = 1, F_ROW = 2, F_TILE = 3, F_ADJ = 4, F_BATCH = 5 };
+enum Family { F_STR = 0, F_COL = 1, F_ROW = 2, F_TILE = 3, F_ADJ = 4, F_BATCH = 5, F_SCAN = 6 };
 const char* family_name(Family f);
 
 // compute types
@@ -80,8 +80,9 @@ struct Analysis {
   // bytes of one accumulator in the workspace (partials of cross-block combines)
   int acc_bytes() const { return (red_mode == RED_NONE || red_additive(red_mode)) ? 8 : 16; }
   // number of values the reduction writes (a vector along dim 0/1 may be empty)
+  bool scan() const { return red.kind == COOT_R_CUMSUM; }
   int64_t n_outputs() const {
-    if (red.kind == COOT_R_NONE) return 0;
+    if (red.kind == COOT_R_NONE || red.kind == COOT_R_CUMSUM) return 0;
     return red.dim == 0 ? nc : (red.dim == 1 ? nr : 1);
   }
 };

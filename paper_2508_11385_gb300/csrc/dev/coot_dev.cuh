@@ -600,27 +600,36 @@ __device__ __forceinline__ double scale2(double v, i64 e) {
 }
 
 // FP32: float-float significand (TwoProduct through fma: hi*m exactly equals
-// p + err), relative error ~ (n u)^2 + u.
+// p + err), relative error ~ (n u)^2 + u.  The running significand is kept
+// in [2^-32, 2^32] and a factor in that range is used as it is (their
+// product stays inside [2^-64, 2^64], far from overflow and from the
+// subnormal range, also for lo); only other factors are split, and hi is
+// renormalised only when it leaves the range.
 struct AccProdF {
   float hi, lo;
   i64 e;
   __device__ __forceinline__ void init() { hi = 1.f; lo = 0.f; e = 0; }
+  __device__ static __forceinline__ bool in_range(float a) {
+    const float m = fabsf(a);
+    return m >= 2.3283064365386963e-10f && m <= 4294967296.0f;  // 2^-32, 2^32
+  }
   __device__ __forceinline__ void renorm() {
     i64 d = 0;
     float h = split_exp(hi, d);
     if (d != 0) {
-      lo = __fmul_rn(lo, __uint_as_float((u32)(127 - d) << 23));  // |d| <= 2 here
+      lo = __fmul_rn(lo, __uint_as_float((u32)(127 - d) << 23));  // 2^-d, |d| <= 65
       hi = h;
       e += d;
     }
   }
   __device__ __forceinline__ void mul(float x) {
-    float m = split_exp(x, e);
+    float m = x;
+    if (!in_range(x)) m = split_exp(x, e);  // also zero, subnormal, inf, NaN
     float p = __fmul_rn(hi, m);
     float err = __fmaf_rn(hi, m, -p);
     lo = __fmaf_rn(lo, m, err);
     hi = p;
-    renorm();
+    if (!in_range(hi)) renorm();
   }
   __device__ __forceinline__ void merge(const AccProdF& o) {
     float p = __fmul_rn(hi, o.hi);
@@ -642,11 +651,17 @@ struct AccProdF {
     return scale2((double)hi + (double)lo, e);
   }
 };
-// FP64: plain double significand (relative error ~ n u for a chain of n)
+// FP64: plain double significand (relative error ~ n u for a chain of n).
+// Same scheme with the range [2^-300, 2^300], tested on the biased exponent
+// in integer arithmetic (FP64 compares share the slow FP64 pipe).
 struct AccProdD {
   double hi;
   i64 e;
   __device__ __forceinline__ void init() { hi = 1.0; e = 0; }
+  __device__ static __forceinline__ bool in_range(double a) {
+    const u32 be = ((u32)__double2hiint(a) >> 20) & 0x7ffu;
+    return be - (1023u - 300u) <= 600u;
+  }
   __device__ __forceinline__ void renorm() {
     i64 d = 0;
     double h = split_exp(hi, d);
@@ -654,9 +669,10 @@ struct AccProdD {
     e += d;
   }
   __device__ __forceinline__ void mul(double x) {
-    double m = split_exp(x, e);
+    double m = x;
+    if (!in_range(x)) m = split_exp(x, e);
     hi = __dmul_rn(hi, m);
-    renorm();
+    if (!in_range(hi)) renorm();
   }
   __device__ __forceinline__ void merge(const AccProdD& o) {
     hi = __dmul_rn(hi, o.hi);

@@ -435,7 +435,14 @@ __device__ __forceinline__ void row_kernel(const Params& p) {
 //   A transposed slot reads view(j, i): its 32x32 source block is read with
 //   consecutive threads on consecutive source rows and parked in shared
 //   memory with one column of padding, then read back transposed.
-//   DIM: -1 full reduction, 0 per column, 1 per row.
+//   DIM -1 (full reduction or none): blocks stride over all tiles.
+//   DIM 0 / 1 (per column / per row): the outputs of one strip of 32 columns
+//   (DIM 0) or 32 rows (DIM 1) depend on that strip's tiles only.  Block b
+//   owns segment b % n_splits of strip b / n_splits and keeps its
+//   accumulators in registers across the segment's tiles (a thread's four
+//   columns, or its row, stay the same), so it reduces across threads once;
+//   with several segments per strip the last block of the strip (ticket)
+//   combines the segment partials in segment order.
 // ---------------------------------------------------------------------------
 constexpr int TILE = 32;
 constexpr int TILE_PH = 8;  // blockDim.x == TILE * TILE_PH
@@ -443,6 +450,80 @@ constexpr int TILE_Q = TILE / TILE_PH;
 
 template <int M> struct popc { static constexpr int value = (M & 1) + popc<(M >> 1)>::value; };
 template <> struct popc<0> { static constexpr int value = 0; };
+
+// the operand values of this thread's four elements of tile (ti, tj)
+template <class S, int NS, int TRMASK, int NTR, class C>
+__device__ __forceinline__ void tile_load(const Params& p, long long ti, long long tj, Vals<C, NS, TILE_Q>& x,
+                                          C (*stage)[TILE][TILE + 1]) {
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const long long nr = p.n_rows, nc = p.n_cols;
+  const long long i = ti * TILE + tx;
+  // direct reads first: they stay in flight while transposed blocks are staged
+#pragma unroll
+  for (int w = 0; w < TILE_Q; ++w) {
+    const long long j = tj * TILE + ty + TILE_PH * w;
+    const bool ok = (i < nr && j < nc);
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+      if (!((TRMASK >> s) & 1)) x.v[s][w] = ok ? IO<S>::load1(at<S>(p.src[s], i, j, p.ld[s])) : C(0);
+  }
+  if constexpr (NTR > 0) {
+    __syncthreads();  // the previous tile's shared reads are done
+    int q = 0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+      if ((TRMASK >> s) & 1) {
+        const long long vr = tj * TILE + tx;  // view row  = output column
+#pragma unroll
+        for (int w = 0; w < TILE_Q; ++w) {
+          const long long vc = ti * TILE + ty + TILE_PH * w;  // view column = output row
+          stage[q][ty + TILE_PH * w][tx] = (vr < nc && vc < nr) ? IO<S>::load1(at<S>(p.src[s], vr, vc, p.ld[s])) : C(0);
+        }
+        ++q;
+      }
+    __syncthreads();
+    q = 0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+      if ((TRMASK >> s) & 1) {
+#pragma unroll
+        for (int w = 0; w < TILE_Q; ++w) x.v[s][w] = stage[q][tx][ty + TILE_PH * w];
+        ++q;
+      }
+  }
+}
+
+// End of a strip segment: blk[q] holds this block's value for output
+// o = OS strip + q (q < OS).  One segment: write the results.  Several: park
+// the value in the partials (segment-major), and the strip's last block
+// (ticket) merges the segments in order and writes the results.
+template <class C, int RED, int OS, class A>
+__device__ __forceinline__ void strip_finish(const Params& p, const A* blk, long long strip, long long seg,
+                                             long long nseg, long long no, int* am_last) {
+  const int q = threadIdx.x;
+  const long long o = strip * OS + q;
+  if (nseg == 1) {
+    if (q < OS && o < no) write_result<C, RED>(p, blk[q], o, p.div);
+    return;
+  }
+  if (q < OS && o < no) ((A*)p.partials)[seg * no + o] = blk[q];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int tk = atomicAdd(&p.tickets[strip], 1u);
+    *am_last = (tk == (unsigned int)(nseg - 1));
+  }
+  __syncthreads();
+  if (*am_last) {
+    __threadfence();
+    if (q < OS && o < no) {
+      A a = load_cg(&((const A*)p.partials)[o]);
+      for (long long sg = 1; sg < nseg; ++sg) a.merge(load_cg(&((const A*)p.partials)[sg * no + o]));
+      write_result<C, RED>(p, a, o, p.div);
+    }
+    if (threadIdx.x == 0) p.tickets[strip] = 0u;
+  }
+}
 
 template <class T, class S, int NS, int NK, int RED, int DIM, int TRMASK, bool OUT>
 __device__ __forceinline__ void tile_kernel(const Params& p) {
@@ -456,134 +537,103 @@ __device__ __forceinline__ void tile_kernel(const Params& p) {
   Scal<C, NK> k;
 #pragma unroll
   for (int q = 0; q < NK; ++q) k.k[q] = scalar_from_bits<C>(p.k[q]);
-  typename CsqOf<C>::type csq;
-  if constexpr (RED == RED_CSQ && DIM == -1) csq.set_mean(*p.mu);
   u32 err = 0;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const long long nr = p.n_rows, nc = p.n_cols;
   const long long ntr = (nr + TILE - 1) / TILE, ntc = (nc + TILE - 1) / TILE;
-  const long long tiles = ntr * ntc;
-  A acc;
-  acc.init();
-  for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
-    const long long ti = t % ntr, tj = t / ntr;
-    const long long i = ti * TILE + tx;
-    Vals<C, NS, TILE_Q> x;
-    // direct reads first: they stay in flight while transposed blocks are staged
+  if constexpr (DIM == -1) {
+    typename CsqOf<C>::type csq;
+    if constexpr (RED == RED_CSQ) csq.set_mean(*p.mu);
+    const long long tiles = ntr * ntc;
+    A acc;
+    acc.init();
+    for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
+      const long long ti = t % ntr, tj = t / ntr;
+      const long long i = ti * TILE + tx;
+      Vals<C, NS, TILE_Q> x;
+      tile_load<S, NS, TRMASK, NTR>(p, ti, tj, x, stage);
 #pragma unroll
-    for (int w = 0; w < TILE_Q; ++w) {
-      const long long j = tj * TILE + ty + TILE_PH * w;
-      const bool ok = (i < nr && j < nc);
-#pragma unroll
-      for (int s = 0; s < NS; ++s)
-        if (!((TRMASK >> s) & 1)) x.v[s][w] = ok ? IO<S>::load1(at<S>(p.src[s], i, j, p.ld[s])) : C(0);
-    }
-    if constexpr (NTR > 0) {
-      __syncthreads();  // the previous tile's shared reads are done
-      int q = 0;
-#pragma unroll
-      for (int s = 0; s < NS; ++s)
-        if ((TRMASK >> s) & 1) {
-          const long long vr = tj * TILE + tx;  // view row  = output column
-#pragma unroll
-          for (int w = 0; w < TILE_Q; ++w) {
-            const long long vc = ti * TILE + ty + TILE_PH * w;  // view column = output row
-            stage[q][ty + TILE_PH * w][tx] = (vr < nc && vc < nr) ? IO<S>::load1(at<S>(p.src[s], vr, vc, p.ld[s])) : C(0);
-          }
-          ++q;
-        }
-      __syncthreads();
-      q = 0;
-#pragma unroll
-      for (int s = 0; s < NS; ++s)
-        if ((TRMASK >> s) & 1) {
-#pragma unroll
-          for (int w = 0; w < TILE_Q; ++w) x.v[s][w] = stage[q][tx][ty + TILE_PH * w];
-          ++q;
-        }
-    }
-    A racc;  // per-row partial over this tile's columns (DIM 1)
-    racc.init();
-#pragma unroll
-    for (int w = 0; w < TILE_Q; ++w) {
-      const long long j = tj * TILE + ty + TILE_PH * w;
-      const bool ok = (i < nr && j < nc);
-      if constexpr (DIM == 0) {
-        A cacc;
-        cacc.init();
-        if (ok) {
-          if constexpr (RED == RED_CSQ) csq.set_mean(p.mu[j]);
-          C y = eval_elem<T, RED>(x, k, err, w, cacc, csq, i);
-          if constexpr (OUT) IO<S>::store1(at_out<S>(p.out, i, j, p.out_ld), y);
-        }
-        cacc = warp_reduce(cacc);  // the 32 rows of column j
-        if (tx == 0 && j < nc) ((A*)p.partials)[ti * nc + j] = cacc;
-      } else if constexpr (DIM == 1) {
-        if (ok) {
-          if constexpr (RED == RED_CSQ) csq.set_mean(p.mu[i]);
-          C y = eval_elem<T, RED>(x, k, err, w, racc, csq, j);
-          if constexpr (OUT) IO<S>::store1(at_out<S>(p.out, i, j, p.out_ld), y);
-        }
-      } else {
-        if (ok) {
+      for (int w = 0; w < TILE_Q; ++w) {
+        const long long j = tj * TILE + ty + TILE_PH * w;
+        if (i < nr && j < nc) {
           C y = eval_elem<T, RED>(x, k, err, w, acc, csq, i + j * nr);
           if constexpr (OUT) IO<S>::store1(at_out<S>(p.out, i, j, p.out_ld), y);
         }
       }
     }
-    if constexpr (DIM == 1) {
-      rsum[ty][tx] = racc;
+    if (err) atomicOr(p.err_flag, err);
+    if constexpr (RED != RED_NONE) finish_full<C, RED>(p, acc, smem);
+  } else {
+    const long long nseg = p.n_splits;
+    const long long strip = blockIdx.x / nseg, seg = blockIdx.x % nseg;
+    const long long len = (DIM == 0) ? ntr : ntc;  // tiles along the strip
+    const long long per = (len + nseg - 1) / nseg;
+    const long long t0 = seg * per, t1 = (t0 + per < len) ? t0 + per : len;
+    // DIM 0: one accumulator per column phase w (output j = 32 strip + ty + 8 w);
+    // DIM 1: one per thread (output i = 32 strip + tx)
+    A acc[DIM == 0 ? TILE_Q : 1];
+    typename CsqOf<C>::type csq[DIM == 0 ? TILE_Q : 1];
+#pragma unroll
+    for (int w = 0; w < (DIM == 0 ? TILE_Q : 1); ++w) {
+      acc[w].init();
+      if constexpr (RED == RED_CSQ) {
+        const long long o = (DIM == 0) ? strip * TILE + ty + TILE_PH * w : strip * TILE + tx;
+        const long long no = (DIM == 0) ? nc : nr;
+        csq[w].set_mean(o < no ? p.mu[o] : 0.0);
+      }
+    }
+    for (long long t = t0; t < t1; ++t) {
+      const long long ti = (DIM == 0) ? t : strip, tj = (DIM == 0) ? strip : t;
+      const long long i = ti * TILE + tx;
+      Vals<C, NS, TILE_Q> x;
+      tile_load<S, NS, TRMASK, NTR>(p, ti, tj, x, stage);
+#pragma unroll
+      for (int w = 0; w < TILE_Q; ++w) {
+        const long long j = tj * TILE + ty + TILE_PH * w;
+        if (i < nr && j < nc) {
+          C y;
+          if constexpr (DIM == 0)
+            y = eval_elem<T, RED>(x, k, err, w, acc[w], csq[w], i);
+          else
+            y = eval_elem<T, RED>(x, k, err, w, acc[0], csq[0], j);
+          if constexpr (OUT) IO<S>::store1(at_out<S>(p.out, i, j, p.out_ld), y);
+        }
+      }
+    }
+    if (err) atomicOr(p.err_flag, err);
+    const long long no = (DIM == 0) ? nc : nr;
+    // this block's value for each output of the strip: rsum[0][o % 32]
+    if constexpr (DIM == 0) {
+#pragma unroll
+      for (int w = 0; w < TILE_Q; ++w) {
+        A a = warp_reduce(acc[w]);  // the block's rows of column 32 strip + ty + 8 w
+        if (tx == 0) rsum[0][ty + TILE_PH * w] = a;
+      }
+      __syncthreads();
+    } else {
+      rsum[ty][tx] = acc[0];
       __syncthreads();
       if (ty == 0) {
         A a = rsum[0][tx];
         for (int r = 1; r < TILE_PH; ++r) a.merge(rsum[r][tx]);
-        if (i < nr) ((A*)p.partials)[tj * nr + i] = a;
-      }
-    }
-    if constexpr (DIM == 0 || DIM == 1) {
-      // last tile of a column strip (DIM 0) / row strip (DIM 1) combines
-      __threadfence();
-      __syncthreads();
-      const long long strip = (DIM == 0) ? tj : ti;
-      const long long need = (DIM == 0) ? ntr : ntc;
-      if (threadIdx.x == 0) {
-        unsigned int tk = atomicAdd(&p.tickets[strip], 1u);
-        am_last = (tk == (unsigned int)(need - 1));
-      }
-      __syncthreads();
-      if (am_last) {
-        __threadfence();
-        // thread (tx, ty): output o = 32 strip + tx, partials ty, ty+8, ...
-        const long long o = strip * TILE + tx;
-        const long long no = (DIM == 0) ? nc : nr;
-        A a;
-        a.init();
-        if (o < no)
-          for (long long s = ty; s < need; s += TILE_PH) a.merge(load_cg(&((const A*)p.partials)[s * no + o]));
-        rsum[ty][tx] = a;
-        __syncthreads();
-        if (ty == 0 && o < no) {
-          A b = rsum[0][tx];
-          for (int r = 1; r < TILE_PH; ++r) b.merge(rsum[r][tx]);
-          write_result<C, RED>(p, b, o, p.div);
-        }
-        if (threadIdx.x == 0) p.tickets[strip] = 0u;
+        rsum[0][tx] = a;
       }
       __syncthreads();
     }
+    strip_finish<C, RED, TILE>(p, &rsum[0][0], strip, seg, nseg, no, &am_last);
   }
-  if (err) atomicOr(p.err_flag, err);
-  if constexpr (DIM == -1 && RED != RED_NONE) finish_full<C, RED>(p, acc, smem);
 }
 
 // ---------------------------------------------------------------------------
-// tilev: vectorised variant of tile for trees without a dim reduction.
+// tilev: vectorised variant of tile.
 //   Tile of TM = 32 V rows x 32 columns; thread (tx, ty) owns rows
 //   32 V ti + V tx .. + V-1 of columns 32 tj + ty + 8 w (w < 4), so direct
 //   reads and the output move V elements (16 bytes) per access.  A transposed
 //   slot's 32 x TM source block is read with consecutive threads on
 //   consecutive source rows into stage[q][column][row] (row stride TM + 4, a
 //   multiple of 16 bytes) and read back as one 16-byte vector per thread.
+//   Reductions along a dim use the strip segments of the tile kernel, with
+//   strips of 32 columns (DIM 0) or TM rows (DIM 1).
 // ---------------------------------------------------------------------------
 // V values of the compute type from 16-byte aligned shared memory, one
 // 16-byte access per 16 bytes
@@ -603,6 +653,27 @@ template <> struct FromWords<double> {
   static constexpr int per = 2;
   __device__ static double get(const u32* w, int l) { return __hiloint2double((int)w[2 * l + 1], (int)w[2 * l]); }
 };
+template <class C> struct ToWords;
+template <> struct ToWords<float> {
+  __device__ static void put(u32* w, int l, float x) { w[l] = __float_as_uint(x); }
+};
+template <> struct ToWords<int> {
+  __device__ static void put(u32* w, int l, int x) { w[l] = (u32)x; }
+};
+template <> struct ToWords<double> {
+  __device__ static void put(u32* w, int l, double x) {
+    w[2 * l] = (u32)__double2loint(x);
+    w[2 * l + 1] = (u32)__double2hiint(x);
+  }
+};
+// one 16-byte group of the compute type to 16-byte aligned shared memory
+template <class C, int G> __device__ __forceinline__ void sts_group(C* p, const C (&v)[G]) {
+  static_assert(G * sizeof(C) == 16, "one 16-byte group");
+  W4 t;
+#pragma unroll
+  for (int l = 0; l < G; ++l) ToWords<C>::put(t.w, l, v[l]);
+  *reinterpret_cast<W4*>(p) = t;
+}
 template <class C, int V> __device__ __forceinline__ void lds_vec(const C* p, C (&v)[V]) {
   constexpr int PER = FromWords<C>::per;
   static_assert(V % PER == 0, "whole 16-byte groups");
@@ -615,32 +686,77 @@ template <class C, int V> __device__ __forceinline__ void lds_vec(const C* p, C 
   }
 }
 
-template <class T, class S, int NS, int NK, int RED, int TRMASK, bool OUT, int V>
+template <class T, class S, int NS, int NK, int RED, int DIM, int TRMASK, bool OUT, int V>
 __device__ __forceinline__ void tilev_kernel(const Params& p) {
   typedef typename ctype<S>::type C;
   typedef typename AccSel<C, RED>::type A;
   constexpr int NTR = popc<TRMASK>::value;
   constexpr int TM = TILE * V;
   constexpr int SP = TM + 16 / (int)sizeof(C);
+  // DIM -1: V accumulators (one per vector lane); DIM 0: one per column
+  // phase w; DIM 1: one per row of the thread's vector
+  constexpr int NA = (DIM == 0) ? TILE_Q : V;
   __shared__ __align__(16) C stage[NTR > 0 ? NTR : 1][TILE][SP];
   __shared__ A smem[32];
+  __shared__ A rsum[TILE_PH][TILE];
+  __shared__ A blk[DIM == 1 ? TM : TILE];
+  __shared__ int am_last;
   Scal<C, NK> k;
 #pragma unroll
   for (int q = 0; q < NK; ++q) k.k[q] = scalar_from_bits<C>(p.k[q]);
-  typename CsqOf<C>::type csq;
-  if constexpr (RED == RED_CSQ) csq.set_mean(*p.mu);
   u32 err = 0;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const long long nr = p.n_rows, nc = p.n_cols;
   const long long ntr = (nr + TM - 1) / TM, ntc = (nc + TILE - 1) / TILE;
-  const long long tiles = ntr * ntc;
-  A accs[V];
+  // tile range of this block: all tiles strided (DIM -1), or one segment of a
+  // strip (DIM 0: column strip tj, DIM 1: row strip ti)
+  long long t_first, t_end, t_step, strip = 0, seg = 0, nseg = 1;
+  if constexpr (DIM == -1) {
+    t_first = blockIdx.x;
+    t_end = ntr * ntc;
+    t_step = gridDim.x;
+  } else {
+    nseg = p.n_splits;
+    strip = blockIdx.x / nseg;
+    seg = blockIdx.x % nseg;
+    const long long len = (DIM == 0) ? ntr : ntc;
+    const long long per = (len + nseg - 1) / nseg;
+    t_first = seg * per;
+    t_end = (t_first + per < len) ? t_first + per : len;
+    t_step = 1;
+  }
+  A acc[NA];
+  typename CsqOf<C>::type csq[NA];
 #pragma unroll
-  for (int l = 0; l < V; ++l) accs[l].init();
-  for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
-    const long long ti = t % ntr, tj = t / ntr;
+  for (int a = 0; a < NA; ++a) {
+    acc[a].init();
+    if constexpr (RED == RED_CSQ) {
+      if constexpr (DIM == -1) {
+        csq[a].set_mean(*p.mu);
+      } else if constexpr (DIM == 0) {
+        const long long o = strip * TILE + ty + TILE_PH * a;
+        csq[a].set_mean(o < nc ? p.mu[o] : 0.0);
+      } else {
+        const long long o = strip * TM + (long long)tx * V + a;
+        csq[a].set_mean(o < nr ? p.mu[o] : 0.0);
+      }
+    }
+  }
+  for (long long t = t_first; t < t_end; t += t_step) {
+    long long ti, tj;
+    if constexpr (DIM == -1) {
+      ti = t % ntr;
+      tj = t / ntr;
+    } else if constexpr (DIM == 0) {
+      ti = t;
+      tj = strip;
+    } else {
+      ti = strip;
+      tj = t;
+    }
     const long long i0 = ti * TM + (long long)tx * V;
     const bool fullr = (i0 + V <= nr);
+    const bool interior = (ti + 1) * TM <= nr && (tj + 1) * TILE <= nc;  // block-uniform
     Vals<C, NS, V> x[TILE_Q];
     // direct reads first: in flight while transposed blocks are staged
 #pragma unroll
@@ -664,15 +780,34 @@ __device__ __forceinline__ void tilev_kernel(const Params& p) {
 #pragma unroll
       for (int s = 0; s < NS; ++s)
         if ((TRMASK >> s) & 1) {
+          // thread (tx, ty) reads view row tj 32 + tx at the view columns of
+          // 16-byte groups ty, ty + 8, ...: a warp reads 32 consecutive
+          // elements per column, and writes each group with one 16-byte
+          // shared store (row stride TM + GE: eight consecutive rows fall on
+          // eight different 16-byte bank groups, no conflict)
+          constexpr int GE = 16 / (int)sizeof(C);
+          constexpr int NG = TM / GE / TILE_PH;
           const long long vr = tj * TILE + tx;  // view row = output column
-          C v[TM / TILE_PH];  // all of this thread's staging loads in flight at once
+          C v[NG][GE];  // all of this thread's staging loads in flight at once
+          if (interior) {
+            // whole tile inside the view: one base pointer, constant steps
+            const long long ld = p.ld[s];
+            const S* b = at<S>(p.src[s], vr, ti * TM + ty * GE, ld);
 #pragma unroll
-          for (int u = 0; u < TM / TILE_PH; ++u) {
-            const long long vc = ti * TM + ty + TILE_PH * u;  // view column = output row
-            v[u] = (vr < nc && vc < nr) ? IO<S>::load1(at<S>(p.src[s], vr, vc, p.ld[s])) : C(0);
+            for (int g = 0; g < NG; ++g)
+#pragma unroll
+              for (int e = 0; e < GE; ++e) v[g][e] = IO<S>::load1(b + ((long long)(TILE_PH * g * GE + e)) * ld);
+          } else {
+#pragma unroll
+            for (int g = 0; g < NG; ++g)
+#pragma unroll
+              for (int e = 0; e < GE; ++e) {
+                const long long vc = ti * TM + (ty + TILE_PH * g) * GE + e;  // view column = output row
+                v[g][e] = (vr < nc && vc < nr) ? IO<S>::load1(at<S>(p.src[s], vr, vc, p.ld[s])) : C(0);
+              }
           }
 #pragma unroll
-          for (int u = 0; u < TM / TILE_PH; ++u) stage[q][tx][ty + TILE_PH * u] = v[u];
+          for (int g = 0; g < NG; ++g) sts_group<C, GE>(&stage[q][tx][(ty + TILE_PH * g) * GE], v[g]);
           ++q;
         }
       __syncthreads();
@@ -689,27 +824,284 @@ __device__ __forceinline__ void tilev_kernel(const Params& p) {
     for (int w = 0; w < TILE_Q; ++w) {
       const long long j = tj * TILE + ty + TILE_PH * w;
       if (j >= nc) continue;
+      // element (i0 + l, j) into its accumulator, with its position
+      auto elem = [&](int l) -> C {
+        if constexpr (DIM == -1)
+          return eval_elem<T, RED>(x[w], k, err, l, acc[l], csq[l], i0 + l + j * nr);
+        else if constexpr (DIM == 0)
+          return eval_elem<T, RED>(x[w], k, err, l, acc[w], csq[w], i0 + l);
+        else
+          return eval_elem<T, RED>(x[w], k, err, l, acc[l], csq[l], j);
+      };
       if (fullr) {
         C y[V];
 #pragma unroll
-        for (int l = 0; l < V; ++l) y[l] = eval_elem<T, RED>(x[w], k, err, l, accs[l], csq, i0 + l + j * nr);
+        for (int l = 0; l < V; ++l) y[l] = elem(l);
         if constexpr (OUT) IO<S>::template store<V>(at_out<S>(p.out, i0, j, p.out_ld), y);
       } else {
 #pragma unroll
         for (int l = 0; l < V; ++l)
           if (i0 + l < nr) {
-            C y = eval_elem<T, RED>(x[w], k, err, l, accs[l], csq, i0 + l + j * nr);
+            C y = elem(l);
             if constexpr (OUT) IO<S>::store1(at_out<S>(p.out, i0 + l, j, p.out_ld), y);
           }
       }
     }
   }
   if (err) atomicOr(p.err_flag, err);
-  if constexpr (RED != RED_NONE) {
+  if constexpr (DIM == -1) {
+    if constexpr (RED != RED_NONE) {
 #pragma unroll
-    for (int l = 1; l < V; ++l) accs[0].merge(accs[l]);
-    finish_full<C, RED>(p, accs[0], smem);
+      for (int l = 1; l < V; ++l) acc[0].merge(acc[l]);
+      finish_full<C, RED>(p, acc[0], smem);
+    }
+  } else if constexpr (DIM == 0) {
+#pragma unroll
+    for (int w = 0; w < TILE_Q; ++w) {
+      A a = warp_reduce(acc[w]);  // the block's rows of column 32 strip + ty + 8 w
+      if (tx == 0) blk[ty + TILE_PH * w] = a;
+    }
+    __syncthreads();
+    strip_finish<C, RED, TILE>(p, blk, strip, seg, nseg, nc, &am_last);
+  } else {
+    // rows 32 V strip + V tx + l: combine the 8 column phases, one lane at a time
+#pragma unroll
+    for (int l = 0; l < V; ++l) {
+      rsum[ty][tx] = acc[l];
+      __syncthreads();
+      if (ty == 0) {
+        A a = rsum[0][tx];
+        for (int r = 1; r < TILE_PH; ++r) a.merge(rsum[r][tx]);
+        blk[tx * V + l] = a;
+      }
+      __syncthreads();
+    }
+    strip_finish<C, RED, TM>(p, blk, strip, seg, nseg, nr, &am_last);
   }
+}
+
+// ---------------------------------------------------------------------------
+// scan: cumsum of the tree along dim 0 (down each column) or dim 1 (along
+// each row), written to the output in the storage type.
+//   Each scan line is cut into n_splits segments.  With one segment a single
+//   launch scans; with several, a first launch (PASS 1) writes each
+//   segment's total to the partials and the scan (PASS 2) starts each
+//   segment from the sum of the totals before it, in segment order.
+//   dim 0: a warp per (column, segment), 32 V rows per step: each lane sums
+//   its V values, a warp scan of the lane totals gives every lane its start,
+//   the step total carries to the next step.  dim 1: a thread per V rows of
+//   a (row block, segment), walking the segment's columns in order.
+// Running sums: float-float for FP32 compute (the output is hi + lo rounded
+// once), plain FP64, wrapping INT32.
+// ---------------------------------------------------------------------------
+template <class C> struct ScanAcc;
+template <> struct ScanAcc<float> {
+  float hi, lo;
+  __device__ __forceinline__ void init() { hi = 0.f; lo = 0.f; }
+  __device__ __forceinline__ void add(float x) {
+    float s = __fadd_rn(hi, x);
+    float bp = __fsub_rn(s, hi);
+    float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+  }
+  __device__ __forceinline__ void add(const ScanAcc& o) {
+    add(o.hi);
+    lo = __fadd_rn(lo, o.lo);
+  }
+  __device__ __forceinline__ float out() const {
+    return (hi - hi == 0.f) ? __fadd_rn(hi, lo) : hi;  // inf / NaN as they are
+  }
+  __device__ __forceinline__ ScanAcc shfl_up(int d) const {
+    ScanAcc o;
+    o.hi = __shfl_up_sync(0xffffffffu, hi, d);
+    o.lo = __shfl_up_sync(0xffffffffu, lo, d);
+    return o;
+  }
+  __device__ __forceinline__ ScanAcc shfl_xor(int m) const {
+    ScanAcc o;
+    o.hi = __shfl_xor_sync(0xffffffffu, hi, m);
+    o.lo = __shfl_xor_sync(0xffffffffu, lo, m);
+    return o;
+  }
+  __device__ __forceinline__ ScanAcc shfl(int src) const {
+    ScanAcc o;
+    o.hi = __shfl_sync(0xffffffffu, hi, src);
+    o.lo = __shfl_sync(0xffffffffu, lo, src);
+    return o;
+  }
+};
+template <> struct ScanAcc<double> {
+  double s;
+  __device__ __forceinline__ void init() { s = 0.0; }
+  __device__ __forceinline__ void add(double x) { s = __dadd_rn(s, x); }
+  __device__ __forceinline__ void add(const ScanAcc& o) { s = __dadd_rn(s, o.s); }
+  __device__ __forceinline__ double out() const { return s; }
+  __device__ __forceinline__ ScanAcc shfl_up(int d) const { return ScanAcc{__shfl_up_sync(0xffffffffu, s, d)}; }
+  __device__ __forceinline__ ScanAcc shfl_xor(int m) const { return ScanAcc{__shfl_xor_sync(0xffffffffu, s, m)}; }
+  __device__ __forceinline__ ScanAcc shfl(int src) const { return ScanAcc{__shfl_sync(0xffffffffu, s, src)}; }
+};
+template <> struct ScanAcc<int> {
+  u32 s, pad;
+  __device__ __forceinline__ void init() { s = 0u; pad = 0u; }
+  __device__ __forceinline__ void add(int x) { s += (u32)x; }
+  __device__ __forceinline__ void add(const ScanAcc& o) { s += o.s; }
+  __device__ __forceinline__ int out() const { return (int)s; }
+  __device__ __forceinline__ ScanAcc shfl_up(int d) const { return ScanAcc{__shfl_up_sync(0xffffffffu, s, d), 0u}; }
+  __device__ __forceinline__ ScanAcc shfl_xor(int m) const { return ScanAcc{__shfl_xor_sync(0xffffffffu, s, m), 0u}; }
+  __device__ __forceinline__ ScanAcc shfl(int src) const { return ScanAcc{__shfl_sync(0xffffffffu, s, src), 0u}; }
+};
+
+template <class T, class S, int NS, int NK, int V, int PASS>
+__device__ __forceinline__ void scan_col_kernel(const Params& p) {
+  typedef typename ctype<S>::type C;
+  typedef ScanAcc<C> A;
+  Scal<C, NK> k;
+#pragma unroll
+  for (int q = 0; q < NK; ++q) k.k[q] = scalar_from_bits<C>(p.k[q]);
+  u32 err = 0;
+  const int lane = threadIdx.x & 31;
+  const long long nr = p.n_rows, nc = p.n_cols, nseg = p.n_splits;
+  const long long seg_rows = p.units_per_col * 32LL * V;
+  const long long units = nc * nseg;
+  const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long u = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < units; u += nw) {
+    const long long j = u / nseg, sg = u % nseg;
+    const long long r0 = sg * seg_rows;
+    const long long r1 = (r0 + seg_rows < nr) ? r0 + seg_rows : nr;
+    A carry;
+    carry.init();
+    if constexpr (PASS == 2) {
+      for (long long q = 0; q < sg; ++q) carry.add(load_cg(&((const A*)p.partials)[j * nseg + q]));
+    }
+    for (long long c0 = r0; c0 < r1; c0 += 32LL * V) {
+      const long long i = c0 + (long long)lane * V;
+      const bool full = (i + V <= r1);
+      Vals<C, NS, V> x;
+      if (full) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) IO<S>::template load<V>(at<S>(p.src[s], i, j, p.ld[s]), x.v[s]);
+      } else {
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+#pragma unroll
+          for (int l = 0; l < V; ++l) x.v[s][l] = (i + l < r1) ? IO<S>::load1(at<S>(p.src[s], i + l, j, p.ld[s])) : C(0);
+      }
+      C y[V];
+      A tot;
+      tot.init();
+#pragma unroll
+      for (int l = 0; l < V; ++l) {
+        y[l] = (i + l < r1) ? T::ev(x, k, err, l) : C(0);
+        tot.add(y[l]);
+      }
+      // inclusive warp scan of the lane totals (lanes in order)
+      A inc = tot;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        A o = inc.shfl_up(d);
+        if (lane >= d) {
+          o.add(inc);
+          inc = o;
+        }
+      }
+      const A step_total = inc.shfl(31);
+      if constexpr (PASS == 2) {
+        A run = inc.shfl_up(1);  // exclusive: the lanes before this one
+        if (lane == 0) run.init();
+        A base = carry;
+        base.add(run);
+        C out[V];
+#pragma unroll
+        for (int l = 0; l < V; ++l) {
+          base.add(y[l]);
+          out[l] = base.out();
+        }
+        if (full)
+          IO<S>::template store<V>(at_out<S>(p.out, i, j, p.out_ld), out);
+        else
+#pragma unroll
+          for (int l = 0; l < V; ++l)
+            if (i + l < r1) IO<S>::store1(at_out<S>(p.out, i + l, j, p.out_ld), out[l]);
+      }
+      carry.add(step_total);
+    }
+    if constexpr (PASS == 1) {
+      if (lane == 0) ((A*)p.partials)[j * nseg + sg] = carry;
+    }
+  }
+  if (err) atomicOr(p.err_flag, err);
+}
+
+template <class T, class S, int NS, int NK, int V, int U, int PASS>
+__device__ __forceinline__ void scan_row_kernel(const Params& p) {
+  typedef typename ctype<S>::type C;
+  typedef ScanAcc<C> A;
+  Scal<C, NK> k;
+#pragma unroll
+  for (int q = 0; q < NK; ++q) k.k[q] = scalar_from_bits<C>(p.k[q]);
+  u32 err = 0;
+  const long long nr = p.n_rows, nc = p.n_cols;
+  const long long nrb = p.n_row_blocks, nseg = p.n_splits, cps = p.units_per_col;
+  const long long rb = blockIdx.x % nrb, sg = blockIdx.x / nrb;
+  const long long i = (rb * blockDim.x + threadIdx.x) * V;
+  const long long j0 = sg * cps;
+  const long long j1 = (j0 + cps < nc) ? j0 + cps : nc;
+  const bool fullv = (i + V <= nr);
+  if (i >= nr) return;
+  A run[V];
+#pragma unroll
+  for (int l = 0; l < V; ++l) {
+    run[l].init();
+    if constexpr (PASS == 2)
+      if (i + l < nr)
+        for (long long q = 0; q < sg; ++q) run[l].add(load_cg(&((const A*)p.partials)[q * nr + i + l]));
+  }
+  for (long long jb = j0; jb < j1; jb += U) {
+    Vals<C, NS, V> x[U];
+#pragma unroll
+    for (int g = 0; g < U; ++g) {
+      const long long j = jb + g;
+      if (j < j1) {
+        if (fullv) {
+#pragma unroll
+          for (int s = 0; s < NS; ++s) IO<S>::template load<V>(at<S>(p.src[s], i, j, p.ld[s]), x[g].v[s]);
+        } else {
+#pragma unroll
+          for (int s = 0; s < NS; ++s)
+#pragma unroll
+            for (int l = 0; l < V; ++l)
+              x[g].v[s][l] = (i + l < nr) ? IO<S>::load1(at<S>(p.src[s], i + l, j, p.ld[s])) : C(0);
+        }
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < U; ++g) {
+      const long long j = jb + g;
+      if (j < j1) {
+        C out[V];
+#pragma unroll
+        for (int l = 0; l < V; ++l) {
+          run[l].add(T::ev(x[g], k, err, l));
+          out[l] = run[l].out();
+        }
+        if constexpr (PASS == 2) {
+          if (fullv)
+            IO<S>::template store<V>(at_out<S>(p.out, i, j, p.out_ld), out);
+          else
+#pragma unroll
+            for (int l = 0; l < V; ++l)
+              if (i + l < nr) IO<S>::store1(at_out<S>(p.out, i + l, j, p.out_ld), out[l]);
+        }
+      }
+    }
+  }
+  if constexpr (PASS == 1) {
+#pragma unroll
+    for (int l = 0; l < V; ++l)
+      if (i + l < nr) ((A*)p.partials)[sg * nr + i + l] = run[l];
+  }
+  if (err) atomicOr(p.err_flag, err);
 }
 
 // ---------------------------------------------------------------------------

@@ -20,6 +20,9 @@ typedef eGlue<eOp<eOp<eGlue<eGlue<eOp<eGlue<Leaf<0>, Leaf<1>, eglue_minus>, eop_
 
 #define K(name, bound, body) \
   extern "C" __global__ void __launch_bounds__(bound) name(const __grid_constant__ Params p) { body(p); }
+// the tile family with the register caps its generated kernels use
+#define KB(name, bound, minb, body) \
+  extern "C" __global__ void __launch_bounds__(bound, minb) name(const __grid_constant__ Params p) { body(p); }
 
 K(chk_str_f32, 512, (str_kernel<T3, float, 3, 1, RED_SUM, 4, 2, true>))
 K(chk_str_bf16, 512, (str_kernel<T3, bf16, 3, 1, RED_SSQ, 8, 1, true>))
@@ -29,9 +32,9 @@ K(chk_str_i32_dot, 512, (str_kernel<T2, int, 2, 0, RED_DOT, 4, 2, true>))
 K(chk_str_l8, 512, (str_kernel<T6, float, 6, 1, RED_NONE, 4, 2, true>))
 K(chk_col_f32, 512, (col_kernel<T3, float, 3, 1, RED_SUM, 4, 2, true>))
 K(chk_row_f16, 512, (row_kernel<T3, f16, 3, 1, RED_SUM, 8, 2, true>))
-K(chk_tile_dim0, 256, (tile_kernel<T3, float, 3, 1, RED_SUM, 0, 4, true>))
-K(chk_tile_dim1, 256, (tile_kernel<T3, float, 3, 1, RED_SUM, 1, 5, true>))
-K(chk_tile_f64, 256, (tile_kernel<T3, double, 3, 1, RED_MEAN1, -1, 1, false>))
+KB(chk_tile_dim0, 256, 4, (tile_kernel<T3, float, 3, 1, RED_SUM, 0, 4, true>))
+KB(chk_tile_dim1, 256, 4, (tile_kernel<T3, float, 3, 1, RED_SUM, 1, 5, true>))
+KB(chk_tile_f64, 256, 4, (tile_kernel<T3, double, 3, 1, RED_MEAN1, -1, 1, false>))
 K(chk_adj_f32, 512, (adj_kernel<T3, float, 3, 1, 4, 2>))
 extern "C" __global__ void __launch_bounds__(256) chk_batch(const __grid_constant__ BatchParams p) {
   batch_kernel<T3, float, 3, 1, 4, true>(p);
@@ -42,9 +45,9 @@ extern "C" __global__ void __launch_bounds__(256) chk_batch_f64_2tr(const __grid
 extern "C" __global__ void __launch_bounds__(256) chk_batch_f32_2tr(const __grid_constant__ BatchParams p) {
   batch_kernel<eGlue<Leaf<0>, Leaf<1>, eglue_plus>, float, 2, 0, 3, false>(p);
 }
-K(chk_tilev_f32, 256, (tilev_kernel<T3, float, 3, 1, RED_NONE, 4, true, 4>))
-K(chk_tilev_bf16, 256, (tilev_kernel<T3, bf16, 3, 1, RED_SUM, 4, true, 8>))
-K(chk_tilev_f64, 256, (tilev_kernel<T3, double, 3, 1, RED_CSQ, 4, false, 2>))
+KB(chk_tilev_f32, 256, 3, (tilev_kernel<T3, float, 3, 1, RED_NONE, -1, 4, true, 4>))
+KB(chk_tilev_bf16, 256, 2, (tilev_kernel<T3, bf16, 3, 1, RED_SUM, -1, 4, true, 8>))
+KB(chk_tilev_f64, 256, 3, (tilev_kernel<T3, double, 3, 1, RED_CSQ, -1, 4, false, 2>))
 // statistics: extremes with positions, products, var along a dim
 K(chk_str_imin_f32, 512, (str_kernel<T3, float, 3, 1, RED_IMIN, 4, 2, false>))
 K(chk_str_max_bf16, 512, (str_kernel<T3, bf16, 3, 1, RED_MAX, 8, 1, false>))
@@ -55,6 +58,15 @@ K(chk_col_min_i32, 512, (col_kernel<T2, int, 2, 0, RED_MIN, 4, 2, false>))
 K(chk_col_csq_f32, 512, (col_kernel<T3, float, 3, 1, RED_CSQ, 4, 2, true>))
 K(chk_row_imax_f64, 512, (row_kernel<T3, double, 3, 1, RED_IMAX, 2, 2, false>))
 K(chk_row_csq_f32, 512, (row_kernel<T3, float, 3, 1, RED_CSQ, 4, 2, false>))
-K(chk_tile_imin_dim0, 256, (tile_kernel<T3, float, 3, 1, RED_IMIN, 0, 4, false>))
-K(chk_tile_csq_dim1, 256, (tile_kernel<T3, double, 3, 1, RED_CSQ, 1, 5, false>))
-K(chk_tilev_prod_f32, 256, (tilev_kernel<T3, float, 3, 1, RED_PROD, 4, false, 4>))
+KB(chk_tile_imin_dim0, 256, 4, (tile_kernel<T3, float, 3, 1, RED_IMIN, 0, 4, false>))
+KB(chk_tile_csq_dim1, 256, 4, (tile_kernel<T3, double, 3, 1, RED_CSQ, 1, 5, false>))
+KB(chk_tilev_prod_f32, 256, 3, (tilev_kernel<T3, float, 3, 1, RED_PROD, -1, 4, false, 4>))
+KB(chk_tilev_dim0_f32, 256, 3, (tilev_kernel<T3, float, 3, 1, RED_SUM, 0, 4, true, 4>))
+KB(chk_tilev_dim1_bf16, 256, 2, (tilev_kernel<T3, bf16, 3, 1, RED_IMAX, 1, 4, false, 8>))
+KB(chk_tilev_dim1_f64, 256, 3, (tilev_kernel<T3, double, 3, 1, RED_CSQ, 1, 4, false, 2>))
+// cumsum scans
+K(chk_scan_col_f32, 256, (scan_col_kernel<T3, float, 3, 1, 4, 2>))
+K(chk_scan_col_t_f64, 256, (scan_col_kernel<T3, double, 3, 1, 2, 1>))
+K(chk_scan_col_i32, 256, (scan_col_kernel<T2, int, 2, 0, 4, 2>))
+K(chk_scan_row_bf16, 256, (scan_row_kernel<T3, bf16, 3, 1, 8, 2, 2>))
+K(chk_scan_row_t_f32, 256, (scan_row_kernel<T3, float, 3, 1, 4, 4, 1>))

@@ -35,6 +35,7 @@ const char* family_name(Family f) {
     case F_TILE: return "tile";
     case F_ADJ: return "adj";
     case F_BATCH: return "batch";
+    case F_SCAN: return "scan";
   }
   return "?";
 }
@@ -215,6 +216,12 @@ coot_status analyse(const coot_tree* tree, const coot_mat* leaves, int32_t n_lea
                      : red.kind == COOT_R_INDEX_MAX ? RED_IMAX
                                                     : RED_PROD;
       break;
+    case COOT_R_CUMSUM:
+      if (red.dim < -1 || red.dim > 1) return set_error(COOT_ERR_INVALID, "cumsum dim %d not in {-1,0,1}", red.dim);
+      if (!out) return set_error(COOT_ERR_INVALID, "cumsum writes its result to out, which is NULL");
+      if (red.dim == -1) an->red.dim = (an->nr == 1) ? 1 : 0;  // along a row vector, else down the columns
+      an->red_mode = RED_NONE;
+      break;
     default: return set_error(COOT_ERR_INVALID, "unknown reduction kind %d", red.kind);
   }
   if (is_int && (red.kind == COOT_R_MEAN || red.kind == COOT_R_NORM2 || red.kind == COOT_R_NORM_FRO ||
@@ -394,6 +401,20 @@ Choice choose(const Analysis& an, const coot_mat* leaves, const coot_mat* out) {
     return ch;
   }
   const int dim = an.red.dim;
+  if (an.scan()) {
+    // cumsum: warps down the columns or threads along the rows, never
+    // collapsed; vector access needs every column start 16-byte aligned
+    ch.fam = F_SCAN;
+    bool vec = true;
+    for (const Slot& s : an.slots) {
+      const coot_mat& L = leaves[s.leaf];
+      uintptr_t org = (uintptr_t)L.data + (uintptr_t)((s.r0 + s.c0 * mat_ld(L)) * an.esz);
+      if (org % 16 || (s.vc > 1 && (mat_ld(L) * an.esz) % 16)) vec = false;
+    }
+    if ((uintptr_t)out->data % 16 || (an.nc > 1 && (mat_ld(*out) * an.esz) % 16)) vec = false;
+    ch.vec_ok = vec;
+    return ch;
+  }
   // every kind that takes a dim: sum, mean, var, stddev, min, max, index_*, prod
   const bool along = an.red.kind != COOT_R_NONE && dim >= 0;
   if (along && dim == 0)
@@ -447,9 +468,12 @@ Program make_program(const Analysis& an, Family fam, bool var_two_pass) {
   src << "#include \"coot_kernels.cuh\"\nusing namespace coot;\n";
   src << "typedef " << S << " S_t;\n";
   src << "typedef " << an.type_str << " T_t;\n";
-  auto wrap = [&](const std::string& name, int bound, const std::string& body, const char* ptype = "Params") {
-    src << "extern \"C\" __global__ void __launch_bounds__(" << bound << ") " << name << "(const __grid_constant__ "
-        << ptype << " p) { " << body << "(p); }\n";
+  // minb > 0: at least minb resident blocks per SM (caps registers per thread)
+  auto wrap = [&](const std::string& name, int bound, const std::string& body, const char* ptype = "Params",
+                  int minb = 0) {
+    src << "extern \"C\" __global__ void __launch_bounds__(" << bound;
+    if (minb > 0) src << ", " << minb;
+    src << ") " << name << "(const __grid_constant__ " << ptype << " p) { " << body << "(p); }\n";
   };
   auto add = [&](const std::string& name, int vec, int unroll, int block) {
     KernelSpec k;
@@ -524,33 +548,68 @@ Program make_program(const Analysis& an, Family fam, bool var_two_pass) {
     for (size_t s = 0; s < an.slots.size(); ++s) ntr += an.slots[s].trans ? 1 : 0;
     const int csize = (an.ct == CT_F64) ? 8 : 4;
     const int tm = 32 * V, sp = tm + 16 / csize;
-    const bool tv = (dim == -1) && (ntr * 32 * sp * csize + 2048 <= 49152);
-    auto tilev = [&](const char* name, const char* red) {
-      wrap(name, 256, std::string("tilev_kernel<T_t, S_t, ") + std::to_string(NS) + ", " + std::to_string(NK) + ", " +
-                          red + ", " + std::to_string(an.trmask) + ", " +
-                          (std::string(name).find("_p1") != std::string::npos ? "false" : outs) + ", " +
-                          std::to_string(V) + ">");
+    // static shared memory: staged tiles, plus the reduction scratch
+    // (32 + 256 + max(TM, 32) accumulators)
+    const int ab = an.acc_bytes();
+    const bool tv = (ntr * 32 * sp * csize + (32 + 256 + std::max(tm, 32)) * ab + 16 <= 49152);
+    // register caps: the tile kernel at 4 resident blocks (64 registers);
+    // tilev at 3 (80), with 2 and 4 as tuning alternatives; tilev of 16-bit
+    // storage (32-byte vectors, twice the values in flight) at 2
+    auto tilev = [&](const char* name, const char* red, int minb) {
+      wrap(name, 256,
+           std::string("tilev_kernel<T_t, S_t, ") + std::to_string(NS) + ", " + std::to_string(NK) + ", " + red + ", " +
+               std::to_string(dim) + ", " + std::to_string(an.trmask) + ", " +
+               (std::string(name).find("_p1") != std::string::npos ? "false" : outs) + ", " + std::to_string(V) + ">",
+           "Params", minb);
       add(name, V, 2, 256);
     };
+    auto tile = [&](const char* name, const char* red, const char* o) {
+      wrap(name, 256,
+           std::string("tile_kernel<T_t, S_t, ") + std::to_string(NS) + ", " + std::to_string(NK) + ", " + red + ", " +
+               std::to_string(dim) + ", " + std::to_string(an.trmask) + ", " + o + ">",
+           "Params", 4);
+      add(name, 1, 1, 256);
+    };
+    const int tv_minb = (an.esz == 2) ? 2 : 3;
     if (var_two_pass) {
       if (tv) {
-        tilev("coot_tilev_p1", "RED_MEAN1");
-        tilev("coot_tilev_p2", "RED_CSQ");
+        tilev("coot_tilev_p1", "RED_MEAN1", tv_minb);
+        tilev("coot_tilev_p2", "RED_CSQ", tv_minb);
       }
-      wrap("coot_tile_p1", 256, std::string("tile_kernel<T_t, S_t, ") + std::to_string(NS) + ", " + std::to_string(NK) +
-                                    ", RED_MEAN1, " + std::to_string(dim) + ", " + std::to_string(an.trmask) +
-                                    ", false>");
-      add("coot_tile_p1", 1, 1, 256);
-      wrap("coot_tile_p2", 256, std::string("tile_kernel<T_t, S_t, ") + std::to_string(NS) + ", " + std::to_string(NK) +
-                                    ", RED_CSQ, " + std::to_string(dim) + ", " + std::to_string(an.trmask) + ", " + outs +
-                                    ">");
-      add("coot_tile_p2", 1, 1, 256);
+      tile("coot_tile_p1", "RED_MEAN1", "false");
+      tile("coot_tile_p2", "RED_CSQ", outs);
     } else {
-      wrap("coot_tile", 256, std::string("tile_kernel<T_t, S_t, ") + std::to_string(NS) + ", " + std::to_string(NK) +
-                                 ", " + red_name(an.red_mode) + ", " + std::to_string(dim) + ", " +
-                                 std::to_string(an.trmask) + ", " + outs + ">");
-      add("coot_tile", 1, 1, 256);
-      if (tv) tilev("coot_tilev", red_name(an.red_mode));
+      tile("coot_tile", red_name(an.red_mode), outs);
+      if (tv) {
+        tilev("coot_tilev", red_name(an.red_mode), tv_minb);
+        if (an.esz != 2) {
+          tilev("coot_tilev_o2", red_name(an.red_mode), 2);
+          tilev("coot_tilev_o4", red_name(an.red_mode), 4);
+        }
+      }
+    }
+  } else if (fam == F_SCAN) {
+    // cumsum: totals pass (_t_, used when the lines are cut into segments)
+    // and scan pass per vector variant
+    if (an.red.dim == 0) {
+      for (int v : {V, 1}) {
+        for (int pass : {1, 2}) {
+          snprintf(buf, sizeof buf, pass == 1 ? "coot_scan_t_v%d" : "coot_scan_v%d", v);
+          wrap(buf, 256, std::string("scan_col_kernel<T_t, S_t, ") + std::to_string(NS) + ", " + std::to_string(NK) +
+                             ", " + std::to_string(v) + ", " + std::to_string(pass) + ">");
+          add(buf, v, 1, 256);
+        }
+      }
+    } else {
+      std::vector<std::pair<int, int>> svu = {{V, 2}, {V, 4}, {1, 4}};
+      for (auto [v, u] : svu) {
+        for (int pass : {1, 2}) {
+          snprintf(buf, sizeof buf, pass == 1 ? "coot_scan_t_v%du%d" : "coot_scan_v%du%d", v, u);
+          wrap(buf, 256, std::string("scan_row_kernel<T_t, S_t, ") + std::to_string(NS) + ", " + std::to_string(NK) +
+                             ", " + std::to_string(v) + ", " + std::to_string(u) + ", " + std::to_string(pass) + ">");
+          add(buf, v, u, 256);
+        }
+      }
     }
   } else if (fam == F_ADJ) {
     std::vector<std::pair<int, int>> avu = {{V, 1}, {V, 2}, {1, 4}};

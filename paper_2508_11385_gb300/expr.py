@@ -411,6 +411,18 @@ def index_max(x, dim=None):
     return Reduction(L.R_INDEX_MAX, x, dim)
 
 
+def cumsum(x, dim=None):
+    """Prefix sums with the expression's shape: down each column (dim 0, the
+    default for a matrix), along each row (dim 1); along the vector for a
+    vector.  ``cumsum(e).eval()`` returns the matrix."""
+    x = _as_expr(x)
+    if dim is None:
+        dim = 1 if x.n_rows == 1 else 0
+    if dim not in (0, 1):
+        raise ValueError("dim must be 0 (down each column) or 1 (along each row)")
+    return Reduction(L.R_CUMSUM, x, dim)
+
+
 def prod(x, dim=None):
     """Product of the elements, defaults as ``min``; no intermediate
     overflow or underflow, the result is rounded to the accumulation type."""
@@ -436,6 +448,18 @@ def evaluate(expr, out=None, reduction=None, red_out=None, fused=True, stream=No
     dt = leaves[0].dtype
     dev = leaves[0].tensor.device
     nr, nc = expr.shape
+    if reduction is not None and reduction.kind == L.R_CUMSUM:
+        # the scan is written where Y would be: out (allocated when None)
+        if isinstance(materialise, torch.Tensor):
+            out = materialise
+        if out is None:
+            out = _empty_colmajor(nr, nc, dt, dev)
+        red = L.reduce(reduction.kind, reduction.dim, reduction.norm_type)
+        with torch.cuda.device(dev):
+            ctx = context(dev)
+            fn = L.coot_eval if fused else L.coot_eval_unfused
+            fn(ctx, tree, cmats, Mat(out).cmat(), red, None, _stream_ptr(stream))
+        return None, out
     want_y = out is not None or reduction is None or materialise is True
     if isinstance(materialise, torch.Tensor):
         out = materialise
@@ -471,8 +495,10 @@ def warmup(expr, reduction=None, out=None):
     expr = _as_expr(expr)
     tree, leaves, cmats = lower(expr)
     red = L.reduce() if reduction is None else L.reduce(reduction.kind, reduction.dim, reduction.norm_type)
-    out_m = Mat(out).cmat() if out is not None else None
     dev = leaves[0].tensor.device
+    if out is None and reduction is not None and reduction.kind == L.R_CUMSUM:
+        out = _empty_colmajor(expr.n_rows, expr.n_cols, leaves[0].dtype, dev)  # a scan needs its output
+    out_m = Mat(out).cmat() if out is not None else None
     with torch.cuda.device(dev):
         L.coot_warmup(context(dev), tree, cmats, out_m, red)
 

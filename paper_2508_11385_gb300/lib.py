@@ -26,7 +26,7 @@ DTYPE_CODE = {"f32": F32, "f64": F64, "bf16": BF16, "f16": F16, "i32": I32}
  N_SCAL_DIV_POST, N_PLUS, N_MINUS, N_SCHUR, N_DIV, N_NEG, N_EXP, N_LOG, N_ABS, N_SQUARE, N_SQRT) = range(19)
 
 (R_NONE, R_ACCU, R_SUM, R_MEAN, R_DOT, R_NORM2, R_NORM_FRO, R_VAR, R_STDDEV, R_MIN, R_MAX, R_INDEX_MIN,
- R_INDEX_MAX, R_PROD) = range(14)
+ R_INDEX_MAX, R_PROD, R_CUMSUM) = range(15)
 
 CTX_TUNE, CTX_NO_DISK_CACHE, CTX_LOG = 1, 2, 4
 FLAG_INT_DIV_ZERO = 1

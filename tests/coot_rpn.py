@@ -9,7 +9,7 @@ _STATS = {"min": "min", "max": "max", "index_min": "index_min", "index_max": "in
 
 
 def is_reduction(tok: str) -> bool:
-    if tok in _RED:
+    if tok in _RED or tok in ("cumsum", "cumsum:0", "cumsum:1"):
         return True
     head, _, rest = tok.partition(":")
     if head in _STATS:
@@ -22,6 +22,8 @@ def is_reduction(tok: str) -> bool:
 
 def _reduction(tok, x):
     head, _, rest = tok.partition(":")
+    if head == "cumsum":
+        return coot.cumsum(x, int(rest) if rest else None)
     if head in _STATS:
         return getattr(coot, _STATS[head])(x, int(rest) if rest else -1)
     if head in ("vardim", "stddevdim"):

@@ -187,7 +187,9 @@ def check(program, tensors, dtype, fused=True, materialise=False, out_dtype=None
         ry = oracle.evaluate(tree, hs, dtype, out_dtype)
         compare_matrix(Y, ry, dtype, program)
     if red is not None:
-        if red.partition(":")[0] in ("index_min", "index_max"):
+        if red.partition(":")[0] == "cumsum":
+            compare_matrix(r, oracle.evaluate(program, hs, dtype, out_dtype), dtype, program)
+        elif red.partition(":")[0] in ("index_min", "index_max"):
             compare_index(r, program, hs, dtype, program)
         else:
             rr = oracle.evaluate(program, hs, dtype)

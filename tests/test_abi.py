@@ -202,14 +202,23 @@ def _tree_from_rpn(L, prog, shape, dtype):
     ("A B - square", "R_SUM0", "f32"),
     ("A", "R_VAR", "bf16"),
     ("A B - exp #1 C abs + / D % E - abs sqrt F %", "R_NONE", "f32"),
+    ("A B % C +", "R_INDEX_MAX1", "f32"),
+    ("A trans B +", "R_MIN0", "f64"),
+    ("A B + exp", "R_PROD", "bf16"),
+    ("A trans B %", "R_STDDEV1", "f32"),
+    ("A B % C +", "R_CUMSUM0", "f32"),
+    ("A B %", "R_CUMSUM1", "i32"),
+    ("A exp", "R_CUMSUM1", "f16"),
 ])
 def test_generated_kernels_compile_for_sm103a(L, prog, red, dtype):
     shape = (256, 256)
     t, lv = _tree_from_rpn(L, prog, shape, dtype)
     out = None
     r = {"R_ACCU": L.reduce(L.R_ACCU), "R_NONE": L.reduce(), "R_SUM0": L.reduce(L.R_SUM, 0),
-         "R_VAR": L.reduce(L.R_VAR)}[red]
-    if red == "R_NONE":
+         "R_VAR": L.reduce(L.R_VAR), "R_INDEX_MAX1": L.reduce(L.R_INDEX_MAX, 1), "R_MIN0": L.reduce(L.R_MIN, 0),
+         "R_PROD": L.reduce(L.R_PROD), "R_STDDEV1": L.reduce(L.R_STDDEV, 1),
+         "R_CUMSUM0": L.reduce(L.R_CUMSUM, 0), "R_CUMSUM1": L.reduce(L.R_CUMSUM, 1)}[red]
+    if red == "R_NONE" or red.startswith("R_CUMSUM"):
         out = L.mat(BASE + (1 << 34), L.DTYPE_CODE[dtype], *shape)
     src = L.coot_codegen(t, lv, out, r)
     assert 'extern "C" __global__' in src
