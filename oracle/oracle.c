@@ -392,6 +392,65 @@ static int submat(ctx_t* cx, val_t* x, int64_t r0, int64_t c0, int64_t nr, int64
   return 0;
 }
 
+/* Broadcasting (Armadillo's each_col / each_row operands) and diagonal
+ * views (X.diag(k)), Sec. 2: each element of the result is one element of x.
+ *   each_col:n  x is r x 1, result r x n, result(i,j) = x(i,0)
+ *   each_row:n  x is 1 x c, result n x c, result(i,j) = x(0,j)
+ *   diag:k      result(i,0) = x(i + max(-k,0), i + max(k,0)), as many rows as
+ *               the k-th diagonal has elements                              */
+enum { G_EACH_COL, G_EACH_ROW, G_DIAG };
+
+static int broadcast_or_diag(ctx_t* cx, int op, int64_t arg, val_t* x, val_t* out) {
+  int64_t r = 0, c = 0;
+  if (x->kind != V_MAT) {
+    snprintf(cx->err, 256, "each_col/each_row/diag need a matrix");
+    return -1;
+  }
+  if (op == G_EACH_COL) {
+    if (x->c != 1 || arg < 0) {
+      snprintf(cx->err, 256, "each_col repeats a column vector");
+      return -1;
+    }
+    r = x->r;
+    c = arg;
+  } else if (op == G_EACH_ROW) {
+    if (x->r != 1 || arg < 0) {
+      snprintf(cx->err, 256, "each_row repeats a row vector");
+      return -1;
+    }
+    r = arg;
+    c = x->c;
+  } else {
+    if ((arg > 0 && arg >= x->c) || (arg < 0 && -arg >= x->r)) {
+      snprintf(cx->err, 256, "diag: diagonal outside the matrix");
+      return -1;
+    }
+    const int64_t len = (arg >= 0) ? (x->r < x->c - arg ? x->r : x->c - arg) : (x->r + arg < x->c ? x->r + arg : x->c);
+    r = len > 0 ? len : 0;
+    c = 1;
+  }
+  if (val_alloc(cx, out, r, c)) return -1;
+  const int64_t kr = arg < 0 ? -arg : 0, kc = arg > 0 ? arg : 0;
+  for (int64_t j = 0; j < c; ++j)
+    for (int64_t i = 0; i < r; ++i) {
+      int64_t src;
+      if (op == G_EACH_COL)
+        src = i;
+      else if (op == G_EACH_ROW)
+        src = j * x->r;
+      else
+        src = (i + kr) + (i + kc) * x->r;
+      const int64_t d = i + j * r;
+      if (cx->is_int)
+        out->iv[d] = x->iv[src];
+      else {
+        out->v[d] = x->v[src];
+        out->b[d] = x->b[src];
+      }
+    }
+  return 0;
+}
+
 /* ------------------------------------------------------------------ */
 /* reductions                                                          */
 /* ------------------------------------------------------------------ */
@@ -902,6 +961,22 @@ int orc_eval(const char* program, const orc_mat* leaves, int32_t n_leaves, int32
       if (reduce_stat(&cx, sop, sdim, snorm, &st[0], res)) goto done;
       reduced = 1;
       continue;
+    }
+    {
+      long long garg = 0;
+      int gop = -1;
+      if (!strncmp(tok, "each_col:", 9) && sscanf(tok + 9, "%lld", &garg) == 1) gop = G_EACH_COL;
+      else if (!strncmp(tok, "each_row:", 9) && sscanf(tok + 9, "%lld", &garg) == 1) gop = G_EACH_ROW;
+      else if (!strcmp(tok, "diag")) gop = G_DIAG;
+      else if (!strncmp(tok, "diag:", 5) && sscanf(tok + 5, "%lld", &garg) == 1) gop = G_DIAG;
+      if (gop >= 0) {
+        if (sp < 1) goto underflow;
+        val_t out;
+        if (broadcast_or_diag(&cx, gop, garg, &st[sp - 1], &out)) goto done;
+        val_free(&st[sp - 1]);
+        st[sp - 1] = out;
+        continue;
+      }
     }
     if (!strncmp(tok, "submat:", 7)) {
       long long r0, c0, nr, nc;

@@ -33,6 +33,9 @@
  *   neg exp log abs square sqrt trans
  *   submat:r0:c0:nr:nc   view of the matrix on top (0-based first row/col,
  *                        number of rows/cols)
+ *   each_col:n  each_row:n   the column (row) vector on top repeated n times
+ *                        (the operand of X.each_col() / X.each_row())
+ *   diag  diag:k         diagonal k of the matrix on top as a column vector
  * Optionally one final reduction token:
  *   accu  sum:0 sum:1  mean mean:0 mean:1  dot (pops two matrices)
  *   norm (vector 2-norm)  norm:fro  var var:1 (norm_type 0 -> N-1, 1 -> N)

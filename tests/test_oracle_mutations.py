@@ -28,6 +28,9 @@ MUTATIONS = [
     ("product exponent", "          E += k;\n          const double p = ph * m;", "          const double p = ph * m;"),
     ("cumsum default direction", "if (dim < 0) dim = (r == 1) ? 1 : 0;", "if (dim < 0) dim = (r == 1) ? 0 : 1;"),
     ("cumsum summation bound", "bsum + (double)t * u * asum + orc_ulp(v, ORC_F64)", "bsum + orc_ulp(v, ORC_F64)"),
+    ("diag offset direction", "const int64_t kr = arg < 0 ? -arg : 0, kc = arg > 0 ? arg : 0;",
+     "const int64_t kc = arg < 0 ? -arg : 0, kr = arg > 0 ? arg : 0;"),
+    ("each_row source", "        src = j * x->r;", "        src = j;"),
     ("cumsum compensation", "const double e = (sh - (s2 - bp)) + (y - bp);", "const double e = 0.0;"),
 ]
 

@@ -758,3 +758,46 @@ def test_cumsum_overflow_and_special_values(orc):
     assert v[0] == np.float32(3e38) and v[1] == np.inf and v[2] == pytest.approx(3e38, rel=1e-7)
     w = orc.evaluate("A cumsum", [f([1.0, np.inf, 2.0, -np.inf, 5.0])], "f32").value[:, 0]
     assert w[0] == 1.0 and w[1] == np.inf and w[2] == np.inf and np.isnan(w[3]) and np.isnan(w[4])
+
+
+# ------------------------------------------------------------ broadcasting and diagonals
+
+@pytest.mark.parametrize("k", [0, 1, 3, -1, -4])
+def test_diag_matches_numpy(orc, k):
+    g = np.random.default_rng(90)
+    a = g.normal(size=(6, 9))
+    assert np.array_equal(orc.evaluate("A diag:%d" % k, [F(a)], "f64").value.ravel(), np.diag(a, k))
+    assert np.array_equal(orc.evaluate("A trans diag:%d" % -k, [F(a)], "f64").value.ravel(), np.diag(a, k))
+
+
+def test_diag_of_an_expression_is_the_expression_of_diagonals(orc):
+    g = np.random.default_rng(91)
+    a, b = g.normal(size=(7, 7)), g.normal(size=(7, 7))
+    v = orc.evaluate("A B % #2 + diag", [F(a), F(b)], "f64").value.ravel()
+    assert np.array_equal(v, np.diag(a) * np.diag(b) + 2)
+    assert orc.evaluate("A diag accu", [F(np.eye(5) * 3)], "f64").value[0, 0] == 15.0  # trace
+
+
+def test_each_col_and_each_row_repeat_the_vector(orc):
+    g = np.random.default_rng(92)
+    a = g.normal(size=(5, 4))
+    v = g.normal(size=(5, 1))
+    r = g.normal(size=(1, 4))
+    assert np.array_equal(orc.evaluate("A B each_col:4 -", [F(a), F(v)], "f64").value, a - v)
+    assert np.array_equal(orc.evaluate("A B each_row:5 /", [F(a), F(r)], "f64").value, a / r)
+    # column sums of a repeated column are n times it; row sums of a repeated row likewise
+    assert np.array_equal(orc.evaluate("B each_col:4 sum:1", [F(a), F(v)], "f64").value, 4 * v)
+    assert np.array_equal(orc.evaluate("B each_row:5 sum:0", [F(a), F(r)], "f64").value, 5 * r)
+    # each_row of r is each_col of trans(r), transposed
+    w = orc.evaluate("B trans each_col:5 trans", [F(a), F(r)], "f64").value
+    assert np.array_equal(w, orc.evaluate("B each_row:5", [F(a), F(r)], "f64").value)
+
+
+def test_broadcast_keeps_bounds_and_int_values(orc):
+    g = np.random.default_rng(93)
+    v = g.integers(-100, 100, size=(6, 1)).astype(np.int32)
+    a = g.integers(-100, 100, size=(6, 3)).astype(np.int32)
+    assert np.array_equal(orc.evaluate("A B each_col:3 %", [F(a), F(v)], "i32").value, a * v)
+    f = g.normal(size=(6, 1)).astype(np.float32)
+    r = orc.evaluate("A exp each_col:3", [F(f)], "f32")
+    assert np.all(r.bound[:, 0:1] == r.bound[:, 2:3]) and np.all(r.bound > 0)
