@@ -30,7 +30,7 @@ MUTATIONS = [
     ("cumsum summation bound", "bsum + (double)t * u * asum + orc_ulp(v, ORC_F64)", "bsum + orc_ulp(v, ORC_F64)"),
     ("diag offset direction", "const int64_t kr = arg < 0 ? -arg : 0, kc = arg > 0 ? arg : 0;",
      "const int64_t kc = arg < 0 ? -arg : 0, kr = arg > 0 ? arg : 0;"),
-    ("each_row source", "        src = j * x->r;", "        src = j;"),
+    ("each_row shape", "    r = arg;\n    c = x->c;", "    r = x->c;\n    c = arg;"),
     ("cumsum compensation", "const double e = (sh - (s2 - bp)) + (y - bp);", "const double e = 0.0;"),
 ]
 
