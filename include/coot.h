@@ -4,7 +4,7 @@
  *
  * The computation (Bandicoot paper, Sec. 3): a linear-algebra expression is
  * captured as a tree of Op / eOp / Glue / eGlue nodes and evaluated only when
- * it is assigned ("delayed evaluation"), so that the whole tree can be mapped
+ * it is assigned (delayed evaluation), so that the whole tree can be mapped
  * onto a minimal set of GPU calls.  Here the element-wise part of a tree, the
  * transposes and submatrix views of its leaves, and the reduction that
  * consumes it are evaluated in one pass by a kernel generated for that tree
@@ -16,7 +16,8 @@
  *     arrays of coot_mat are HOST memory read during the call only.  The
  *     caller owns every matrix and stream; the library never frees them.
  *   - Element (i,j) of a coot_mat is at data[i + j*ld], ld >= n_rows
- *     (ld is ignored when n_cols <= 1).
+ *     (ld is ignored when n_cols <= 1); a row stride rs > 1 makes it
+ *     data[i*rs + j*ld].
  *   - Every call returns a coot_status and never throws; on failure
  *     coot_last_error() holds a message for the calling thread.
  *   - Launches are asynchronous on the given stream (a cudaStream_t; NULL is
@@ -67,16 +68,21 @@ typedef enum { COOT_F32 = 0, COOT_F64 = 1, COOT_BF16 = 2, COOT_F16 = 3, COOT_I32
 typedef struct {
   void* data;       /* device pointer to element (0,0)               */
   int32_t dtype;    /* coot_dtype                                    */
-  int32_t reserved; /* must be 0                                     */
+  int32_t rs;       /* row stride in elements: 0 or 1 = adjacent rows
+                       (column-major); r > 1 puts element (i,j) at
+                       data[i*r + j*ld] -- a diagonal view has r = ld+1.
+                       An output with r > 1 must not overlap itself.  */
   int64_t n_rows;
   int64_t n_cols;
-  int64_t ld;       /* column stride in elements, >= n_rows          */
+  int64_t ld;       /* column stride in elements, >= n_rows for
+                       adjacent rows                                  */
 } coot_mat;
 
 /* Node kinds (Sec. 3): N_TRANS is Op<T1,op_trans>; the unary and scalar
  * kinds are eOp<T1,eop_type>; N_PLUS..N_DIV are eGlue<T1,T2,eglue_type>
  * (N_SCHUR is Armadillo's element-wise product operator%).  N_SUBMAT is a
- * submatrix view of a leaf (Sec. 2: "diagonal and submatrix views"). */
+ * submatrix view of a leaf; N_EACH_COL / N_EACH_ROW broadcast a vector and
+ * N_DIAG takes a diagonal (Sec. 2, views and broadcasting). */
 typedef enum {
   COOT_N_LEAF = 0,            /* leaf matrix `leaf`                          */
   COOT_N_SUBMAT = 1,          /* view of node a (an N_LEAF): rows r0..r0+nr-1,
@@ -98,7 +104,14 @@ typedef enum {
   COOT_N_ABS = 16,
   COOT_N_SQUARE = 17,
   COOT_N_SQRT = 18,
-  COOT_N_COUNT_ = 19
+  COOT_N_EACH_COL = 19,       /* a (an n x 1 column) repeated as each of nc
+                                 columns: Armadillo's X.each_col() operand  */
+  COOT_N_EACH_ROW = 20,       /* a (a 1 x n row) repeated as each of nr rows:
+                                 X.each_row()'s operand                     */
+  COOT_N_DIAG = 21,           /* diagonal r0 = k of a as a column vector (k > 0
+                                 above the main diagonal, k < 0 below):
+                                 X.diag(k)                                  */
+  COOT_N_COUNT_ = 22
 } coot_opcode;
 
 /* One node of a postfix tree.  Operand indices a, b refer to earlier nodes
@@ -111,7 +124,8 @@ typedef struct {
   int32_t a, b;            /* operand node indices or -1       */
   int32_t leaf;            /* N_LEAF: index into `leaves`      */
   double k;                /* scalar of the N_SCAL_* kinds     */
-  int64_t r0, c0, nr, nc;  /* N_SUBMAT view                    */
+  int64_t r0, c0, nr, nc;  /* N_SUBMAT view; N_EACH_COL: nc;
+                              N_EACH_ROW: nr; N_DIAG: r0 = k   */
 } coot_node;
 
 typedef struct {
@@ -200,8 +214,8 @@ COOT_API coot_status coot_eval(coot_ctx* ctx, const coot_tree* tree, const coot_
                       const coot_mat* out, coot_reduce red, void* red_out, coot_stream stream);
 
 /* Same result computed eagerly, one kernel launch per node, each node
- * materialised in a device temporary of the compute type (the paper's
- * "sequence of calls from a set of predefined GPU kernels", Sec. 4).  This is
+ * materialised in a device temporary of the compute type (the way Sec. 4
+ * describes Bandicoot: one predefined kernel called after another).  This is
  * the unfused baseline; element-wise results are bitwise equal to coot_eval. */
 COOT_API coot_status coot_eval_unfused(coot_ctx* ctx, const coot_tree* tree, const coot_mat* leaves,
                               int32_t n_leaves, const coot_mat* out, coot_reduce red, void* red_out,

@@ -304,7 +304,7 @@ void bind_workspace(coot_ctx* ctx, const cg::Analysis& an, Launch* L) {
 
 int64_t algorithmic_bytes(const cg::Analysis& an, const coot_mat* out) {
   int64_t b = 0;
-  for (const cg::Slot& s : an.slots) b += s.vr * s.vc * an.esz;
+  for (const cg::Slot& s : an.slots) b += s.n_distinct * an.esz;
   if (an.two_pass()) b *= 2;  // the tree is read by both passes
   if (out) b += an.nr * an.nc * an.esz;
   const bool idx = an.red.kind == COOT_R_INDEX_MIN || an.red.kind == COOT_R_INDEX_MAX;
@@ -458,13 +458,16 @@ static coot_status run_fused(coot_ctx* ctx, const cg::Analysis& an, const coot_m
   for (size_t i = 0; i < an.slots.size(); ++i) {
     const cg::Slot& sl = an.slots[i];
     const coot_mat& Lf = leaves[sl.leaf];
-    const int64_t ld = mat_ld(Lf);
-    p.src[i] = (const char*)Lf.data + (sl.r0 + sl.c0 * ld) * an.esz;
-    p.ld[i] = ld;
+    p.src[i] = (const char*)Lf.data + sl.off * an.esz;
+    // a transposed slot's staging walks its view with the leaf's column
+    // stride (the slot's row stride); the others walk columns with cs
+    p.ld[i] = sl.trans ? sl.rs : sl.cs;
+    p.rs[i] = sl.rs;
   }
   for (size_t i = 0; i < an.scalars.size(); ++i) p.k[i] = scalar_bits(an.scalars[i], an.ct);
   p.out = out ? out->data : nullptr;
   p.out_ld = out ? mat_ld(*out) : 0;
+  p.out_rs = an.out_rs;
   // elements per reduction output
   const int64_t per = (an.red.dim == 0) ? an.nr : (an.red.dim == 1 ? an.nc : count);
   p.count = per;
@@ -759,9 +762,23 @@ extern "C" coot_status coot_eval_unfused(coot_ctx* ctx, const coot_tree* tree, c
     }
     if (d.op == COOT_N_SUBMAT) {  // a view: no kernel
       coot_mat v = val[d.a];
-      v.data = (char*)v.data + (d.r0 + d.c0 * v.ld) * an.esz;
+      const int64_t vrs = v.rs > 1 ? v.rs : 1;
+      v.data = (char*)v.data + (d.r0 * vrs + d.c0 * v.ld) * an.esz;
       v.n_rows = d.nr;
       v.n_cols = d.nc;
+      val[n] = v;
+      continue;
+    }
+    if (d.op == COOT_N_DIAG) {  // a strided view: no kernel
+      coot_mat v = val[d.a];
+      const int64_t vrs = v.rs > 1 ? v.rs : 1;
+      const int64_t k = d.r0, kr = k < 0 ? -k : 0, kc = k > 0 ? k : 0;
+      const int64_t len = (k >= 0) ? std::min(v.n_rows, v.n_cols - k) : std::min(v.n_rows + k, v.n_cols);
+      v.data = (char*)v.data + (kr * vrs + kc * v.ld) * an.esz;
+      v.rs = (int32_t)(vrs + v.ld);
+      v.n_rows = std::max<int64_t>(len, 0);
+      v.n_cols = 1;
+      v.ld = std::max<int64_t>(v.n_rows, 1);
       val[n] = v;
       continue;
     }
@@ -789,10 +806,16 @@ extern "C" coot_status coot_eval_unfused(coot_ctx* ctx, const coot_tree* tree, c
     opn.a = 0;
     opn.b = bin ? 1 : -1;
     opn.k = d.k;
+    opn.r0 = d.r0;
+    opn.c0 = d.c0;
+    opn.nr = d.nr;
+    opn.nc = d.nc;
     ++nmini;
     coot_tree mt{nmini, 0, mini};
     int64_t r = (d.op == COOT_N_TRANS) ? ops[0].n_cols : ops[0].n_rows;
     int64_t c = (d.op == COOT_N_TRANS) ? ops[0].n_rows : ops[0].n_cols;
+    if (d.op == COOT_N_EACH_COL) c = d.nc;
+    if (d.op == COOT_N_EACH_ROW) r = d.nr;
     coot_mat dst{};
     if (n == root && out && !dot) {
       dst = *out;
@@ -867,7 +890,9 @@ extern "C" coot_status coot_eval_unfused(coot_ctx* ctx, const coot_tree* tree, c
       release();
       return s;
     }
-  } else if (tree->nodes[root].op == COOT_N_LEAF || tree->nodes[root].op == COOT_N_SUBMAT) {
+  }
+  const int rop = tree->nodes[root].op;
+  if ((rop == COOT_N_LEAF || rop == COOT_N_SUBMAT || rop == COOT_N_DIAG) && out && red.kind != COOT_R_CUMSUM) {
     // a bare leaf or view: one copy kernel
     coot_node mini[1];
     memset(mini, 0, sizeof mini);
@@ -1020,15 +1045,17 @@ extern "C" coot_status coot_batch_create(coot_ctx* ctx, const coot_tree* tree, i
     if (s) return set_error(s, "problem %lld: %s", (long long)q, coot_last_error());
     if (an.dtype != an0.dtype || an.slots.size() != an0.slots.size() || an.trmask != an0.trmask)
       return set_error(COOT_ERR_INVALID, "problem %lld differs in dtype or leaf reads", (long long)q);
+    if (an.gmask)
+      return set_error(COOT_ERR_UNSUPPORTED, "problem %lld: row-broadcast, diagonal or row-strided reads and outputs "
+                       "are not batched", (long long)q);
     coot::BatchProblem& bp = probs[q];
     memset(&bp, 0, sizeof bp);
     for (size_t i = 0; i < an.slots.size(); ++i) {
       const cg::Slot& sl = an.slots[i];
       const coot_mat& L = lv[sl.leaf];
-      const int64_t ld = mat_ld(L);
-      bp.src[i] = (const char*)L.data + (sl.r0 + sl.c0 * ld) * an.esz;
-      bp.ld[i] = ld;
-      bytes += sl.vr * sl.vc * an.esz;
+      bp.src[i] = (const char*)L.data + sl.off * an.esz;
+      bp.ld[i] = sl.trans ? sl.rs : sl.cs;
+      bytes += sl.n_distinct * an.esz;
     }
     if (outs) {
       bp.out = outs[q].data;

@@ -39,15 +39,24 @@ const char* family_name(Family f);
 // compute types
 enum { CT_F32 = 0, CT_F64 = 1, CT_I32 = 2 };
 
-// A leaf read after trans() has been pushed down to the leaves: tree element
-// (i,j) reads view(i,j) (trans == false) or view(j,i) (trans == true), where
-// view(r,c) = leaf(r0 + r, c0 + c).
+// A leaf read after trans(), each_col/each_row and diag() have been pushed
+// down to the leaves: tree element (i,j) reads the leaf element at
+// off + i*rs + j*cs (in elements from the leaf's data).  Three kinds:
+//   direct  (rs == 1): rows adjacent, vector loads; cs is the column stride
+//           (0 for a column broadcast with each_col);
+//   trans   a transposed view of a leaf with adjacent rows: tree (i,j) is
+//           view (j,i) = leaf (r0 + j, c0 + i), staged through shared memory;
+//   general any other stride (each_row broadcast rs = 0, a diagonal
+//           rs = ld + 1, a row-strided leaf): one element at a time.
 struct Slot {
   int leaf;
-  int64_t r0, c0;
-  int64_t vr, vc;  // view shape (rows, cols) of the leaf region read
+  int64_t off, rs, cs;
+  int64_t r0, c0;  // trans: view origin in the leaf
+  int64_t vr, vc;  // trans: view shape (rows, cols)
   bool trans;
-  bool full;  // the view is the whole leaf
+  bool gen;
+  bool full;           // direct read of the whole leaf in its own layout
+  int64_t n_distinct;  // distinct leaf elements read
 };
 
 // canonical node: op from coot_opcode (N_LEAF means "slot"), no N_TRANS/N_SUBMAT
@@ -69,7 +78,9 @@ struct Analysis {
   std::vector<double> scalars;
   std::string type_str;
   int trmask = 0;
+  int gmask = 0;         // general slots (bit s) and a general output (bit COOT_MAX_SLOTS)
   bool any_trans = false;
+  int64_t out_rs = 1;    // row stride of the output
   coot_reduce red{};
   int red_mode = RED_NONE;  // device mode of the (last) pass
   bool has_out = false;

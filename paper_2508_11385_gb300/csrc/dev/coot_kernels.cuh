@@ -44,6 +44,48 @@ template <class S> __device__ __forceinline__ S* at_out(void* base, long long i,
   return (S*)base + (i + j * ld);
 }
 
+// General slots and outputs.  A program defines COOT_GM: bit s (s < 8) marks
+// slot s as general (rows not one element apart: a broadcast row vector, a
+// diagonal, a row-strided view), bit 8 a general output (a diagonal).
+// General reads and writes go one element at a time through the row stride;
+// the others keep their vector accesses.  The slot index is a constant after
+// unrolling, so the tests below fold away.
+#ifndef COOT_GM
+#define COOT_GM 0
+#endif
+constexpr int GM_OUT = 1 << COOT_MAX_SLOTS;
+__device__ __forceinline__ constexpr bool gen_slot(int s) { return (COOT_GM >> s) & 1; }
+
+template <class S> __device__ __forceinline__ const S* at_slot(const Params& p, int s, long long i, long long j) {
+  if (gen_slot(s)) return (const S*)p.src[s] + (i * p.rs[s] + j * p.ld[s]);
+  return at<S>(p.src[s], i, j, p.ld[s]);
+}
+// V consecutive rows of slot s from (i, j), all inside the tree
+template <class S, int V, class C>
+__device__ __forceinline__ void load_rows(const Params& p, int s, long long i, long long j, C (&v)[V]) {
+  if (gen_slot(s)) {
+    const S* b = at_slot<S>(p, s, i, j);
+#pragma unroll
+    for (int l = 0; l < V; ++l) v[l] = IO<S>::load1(b + l * p.rs[s]);
+  } else {
+    IO<S>::template load<V>(at<S>(p.src[s], i, j, p.ld[s]), v);
+  }
+}
+template <class S> __device__ __forceinline__ S* at_out_g(const Params& p, long long i, long long j) {
+  if (COOT_GM & GM_OUT) return (S*)p.out + (i * p.out_rs + j * p.out_ld);
+  return at_out<S>(p.out, i, j, p.out_ld);
+}
+// V consecutive rows of the output from (i, j)
+template <class S, int V, class C> __device__ __forceinline__ void store_rows(const Params& p, long long i, long long j,
+                                                                             const C (&v)[V]) {
+  if (COOT_GM & GM_OUT) {
+#pragma unroll
+    for (int l = 0; l < V; ++l) IO<S>::store1(at_out_g<S>(p, i + l, j), v[l]);
+  } else {
+    IO<S>::template store<V>(at_out<S>(p.out, i, j, p.out_ld), v);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // per-element contribution of the root to the reduction
 // ---------------------------------------------------------------------------
@@ -201,12 +243,12 @@ __device__ __forceinline__ void str_kernel(const Params& p) {
       full[g] = (i + V <= nr);
       if (full[g]) {
 #pragma unroll
-        for (int s = 0; s < NS; ++s) IO<S>::template load<V>(at<S>(p.src[s], i, j, p.ld[s]), x[g].v[s]);
+        for (int s = 0; s < NS; ++s) load_rows<S, V>(p, s, i, j, x[g].v[s]);
       } else {
 #pragma unroll
         for (int s = 0; s < NS; ++s)
 #pragma unroll
-          for (int l = 0; l < V; ++l) x[g].v[s][l] = (i + l < nr) ? IO<S>::load1(at<S>(p.src[s], i + l, j, p.ld[s])) : C(0);
+          for (int l = 0; l < V; ++l) x[g].v[s][l] = (i + l < nr) ? IO<S>::load1(at_slot<S>(p, s, i + l, j)) : C(0);
       }
     }
 #pragma unroll
@@ -229,13 +271,13 @@ __device__ __forceinline__ void str_kernel(const Params& p) {
 #pragma unroll
           for (int l = 0; l < V; ++l) y[l] = eval_elem<T, RED>(x[g], k, err, l, accs[l], csq, i + l + j * nr);
         }
-        if constexpr (OUT) IO<S>::template store<V>(at_out<S>(p.out, i, j, p.out_ld), y);
+        if constexpr (OUT) store_rows<S, V>(p, i, j, y);
       } else {
 #pragma unroll
         for (int l = 0; l < V; ++l)
           if (i + l < nr) {
             C y = eval_elem<T, RED>(x[g], k, err, l, accs[l], csq, i + l + j * nr);
-            if constexpr (OUT) IO<S>::store1(at_out<S>(p.out, i + l, j, p.out_ld), y);
+            if constexpr (OUT) IO<S>::store1(at_out_g<S>(p, i + l, j), y);
           }
       }
     }
@@ -286,13 +328,13 @@ __device__ __forceinline__ void col_kernel(const Params& p) {
         full[g] = (i + V <= nr);
         if (full[g]) {
 #pragma unroll
-          for (int s = 0; s < NS; ++s) IO<S>::template load<V>(at<S>(p.src[s], i, j, p.ld[s]), x[g].v[s]);
+          for (int s = 0; s < NS; ++s) load_rows<S, V>(p, s, i, j, x[g].v[s]);
         } else {
 #pragma unroll
           for (int s = 0; s < NS; ++s)
 #pragma unroll
             for (int l = 0; l < V; ++l)
-              x[g].v[s][l] = (i + l < nr) ? IO<S>::load1(at<S>(p.src[s], i + l, j, p.ld[s])) : C(0);
+              x[g].v[s][l] = (i + l < nr) ? IO<S>::load1(at_slot<S>(p, s, i + l, j)) : C(0);
         }
       }
 #pragma unroll
@@ -302,13 +344,13 @@ __device__ __forceinline__ void col_kernel(const Params& p) {
           C y[V];
 #pragma unroll
           for (int l = 0; l < V; ++l) y[l] = eval_elem<T, RED>(x[g], k, err, l, acc, csq, i + l);
-          if constexpr (OUT) IO<S>::template store<V>(at_out<S>(p.out, i, j, p.out_ld), y);
+          if constexpr (OUT) store_rows<S, V>(p, i, j, y);
         } else {
 #pragma unroll
           for (int l = 0; l < V; ++l)
             if (i + l < nr) {
               C y = eval_elem<T, RED>(x[g], k, err, l, acc, csq, i + l);
-              if constexpr (OUT) IO<S>::store1(at_out<S>(p.out, i + l, j, p.out_ld), y);
+              if constexpr (OUT) IO<S>::store1(at_out_g<S>(p, i + l, j), y);
             }
         }
       }
@@ -366,13 +408,13 @@ __device__ __forceinline__ void row_kernel(const Params& p) {
         if (j < j1) {
           if (fullv) {
 #pragma unroll
-            for (int s = 0; s < NS; ++s) IO<S>::template load<V>(at<S>(p.src[s], i, j, p.ld[s]), x[g].v[s]);
+            for (int s = 0; s < NS; ++s) load_rows<S, V>(p, s, i, j, x[g].v[s]);
           } else {
 #pragma unroll
             for (int s = 0; s < NS; ++s)
 #pragma unroll
               for (int l = 0; l < V; ++l)
-                x[g].v[s][l] = (i + l < nr) ? IO<S>::load1(at<S>(p.src[s], i + l, j, p.ld[s])) : C(0);
+                x[g].v[s][l] = (i + l < nr) ? IO<S>::load1(at_slot<S>(p, s, i + l, j)) : C(0);
           }
         }
       }
@@ -384,13 +426,13 @@ __device__ __forceinline__ void row_kernel(const Params& p) {
             C y[V];
 #pragma unroll
             for (int l = 0; l < V; ++l) y[l] = eval_elem<T, RED>(x[g], k, err, l, acc[l], csq[l], j);
-            if constexpr (OUT) IO<S>::template store<V>(at_out<S>(p.out, i, j, p.out_ld), y);
+            if constexpr (OUT) store_rows<S, V>(p, i, j, y);
           } else {
 #pragma unroll
             for (int l = 0; l < V; ++l)
               if (i + l < nr) {
                 C y = eval_elem<T, RED>(x[g], k, err, l, acc[l], csq[l], j);
-                if constexpr (OUT) IO<S>::store1(at_out<S>(p.out, i + l, j, p.out_ld), y);
+                if constexpr (OUT) IO<S>::store1(at_out_g<S>(p, i + l, j), y);
               }
           }
         }
@@ -465,7 +507,7 @@ __device__ __forceinline__ void tile_load(const Params& p, long long ti, long lo
     const bool ok = (i < nr && j < nc);
 #pragma unroll
     for (int s = 0; s < NS; ++s)
-      if (!((TRMASK >> s) & 1)) x.v[s][w] = ok ? IO<S>::load1(at<S>(p.src[s], i, j, p.ld[s])) : C(0);
+      if (!((TRMASK >> s) & 1)) x.v[s][w] = ok ? IO<S>::load1(at_slot<S>(p, s, i, j)) : C(0);
   }
   if constexpr (NTR > 0) {
     __syncthreads();  // the previous tile's shared reads are done
@@ -557,7 +599,7 @@ __device__ __forceinline__ void tile_kernel(const Params& p) {
         const long long j = tj * TILE + ty + TILE_PH * w;
         if (i < nr && j < nc) {
           C y = eval_elem<T, RED>(x, k, err, w, acc, csq, i + j * nr);
-          if constexpr (OUT) IO<S>::store1(at_out<S>(p.out, i, j, p.out_ld), y);
+          if constexpr (OUT) IO<S>::store1(at_out_g<S>(p, i, j), y);
         }
       }
     }
@@ -596,7 +638,7 @@ __device__ __forceinline__ void tile_kernel(const Params& p) {
             y = eval_elem<T, RED>(x, k, err, w, acc[w], csq[w], i);
           else
             y = eval_elem<T, RED>(x, k, err, w, acc[0], csq[0], j);
-          if constexpr (OUT) IO<S>::store1(at_out<S>(p.out, i, j, p.out_ld), y);
+          if constexpr (OUT) IO<S>::store1(at_out_g<S>(p, i, j), y);
         }
       }
     }
@@ -766,11 +808,11 @@ __device__ __forceinline__ void tilev_kernel(const Params& p) {
       for (int s = 0; s < NS; ++s) {
         if ((TRMASK >> s) & 1) continue;
         if (j < nc && fullr) {
-          IO<S>::template load<V>(at<S>(p.src[s], i0, j, p.ld[s]), x[w].v[s]);
+          load_rows<S, V>(p, s, i0, j, x[w].v[s]);
         } else {
 #pragma unroll
           for (int l = 0; l < V; ++l)
-            x[w].v[s][l] = (j < nc && i0 + l < nr) ? IO<S>::load1(at<S>(p.src[s], i0 + l, j, p.ld[s])) : C(0);
+            x[w].v[s][l] = (j < nc && i0 + l < nr) ? IO<S>::load1(at_slot<S>(p, s, i0 + l, j)) : C(0);
         }
       }
     }
@@ -837,13 +879,13 @@ __device__ __forceinline__ void tilev_kernel(const Params& p) {
         C y[V];
 #pragma unroll
         for (int l = 0; l < V; ++l) y[l] = elem(l);
-        if constexpr (OUT) IO<S>::template store<V>(at_out<S>(p.out, i0, j, p.out_ld), y);
+        if constexpr (OUT) store_rows<S, V>(p, i0, j, y);
       } else {
 #pragma unroll
         for (int l = 0; l < V; ++l)
           if (i0 + l < nr) {
             C y = elem(l);
-            if constexpr (OUT) IO<S>::store1(at_out<S>(p.out, i0 + l, j, p.out_ld), y);
+            if constexpr (OUT) IO<S>::store1(at_out_g<S>(p, i0 + l, j), y);
           }
       }
     }
@@ -980,12 +1022,12 @@ __device__ __forceinline__ void scan_col_kernel(const Params& p) {
       Vals<C, NS, V> x;
       if (full) {
 #pragma unroll
-        for (int s = 0; s < NS; ++s) IO<S>::template load<V>(at<S>(p.src[s], i, j, p.ld[s]), x.v[s]);
+        for (int s = 0; s < NS; ++s) load_rows<S, V>(p, s, i, j, x.v[s]);
       } else {
 #pragma unroll
         for (int s = 0; s < NS; ++s)
 #pragma unroll
-          for (int l = 0; l < V; ++l) x.v[s][l] = (i + l < r1) ? IO<S>::load1(at<S>(p.src[s], i + l, j, p.ld[s])) : C(0);
+          for (int l = 0; l < V; ++l) x.v[s][l] = (i + l < r1) ? IO<S>::load1(at_slot<S>(p, s, i + l, j)) : C(0);
       }
       C y[V];
       A tot;
@@ -1018,11 +1060,11 @@ __device__ __forceinline__ void scan_col_kernel(const Params& p) {
           out[l] = base.out();
         }
         if (full)
-          IO<S>::template store<V>(at_out<S>(p.out, i, j, p.out_ld), out);
+          store_rows<S, V>(p, i, j, out);
         else
 #pragma unroll
           for (int l = 0; l < V; ++l)
-            if (i + l < r1) IO<S>::store1(at_out<S>(p.out, i + l, j, p.out_ld), out[l]);
+            if (i + l < r1) IO<S>::store1(at_out_g<S>(p, i + l, j), out[l]);
       }
       carry.add(step_total);
     }
@@ -1065,13 +1107,13 @@ __device__ __forceinline__ void scan_row_kernel(const Params& p) {
       if (j < j1) {
         if (fullv) {
 #pragma unroll
-          for (int s = 0; s < NS; ++s) IO<S>::template load<V>(at<S>(p.src[s], i, j, p.ld[s]), x[g].v[s]);
+          for (int s = 0; s < NS; ++s) load_rows<S, V>(p, s, i, j, x[g].v[s]);
         } else {
 #pragma unroll
           for (int s = 0; s < NS; ++s)
 #pragma unroll
             for (int l = 0; l < V; ++l)
-              x[g].v[s][l] = (i + l < nr) ? IO<S>::load1(at<S>(p.src[s], i + l, j, p.ld[s])) : C(0);
+              x[g].v[s][l] = (i + l < nr) ? IO<S>::load1(at_slot<S>(p, s, i + l, j)) : C(0);
         }
       }
     }
@@ -1087,11 +1129,11 @@ __device__ __forceinline__ void scan_row_kernel(const Params& p) {
         }
         if constexpr (PASS == 2) {
           if (fullv)
-            IO<S>::template store<V>(at_out<S>(p.out, i, j, p.out_ld), out);
+            store_rows<S, V>(p, i, j, out);
           else
 #pragma unroll
             for (int l = 0; l < V; ++l)
-              if (i + l < nr) IO<S>::store1(at_out<S>(p.out, i + l, j, p.out_ld), out[l]);
+              if (i + l < nr) IO<S>::store1(at_out_g<S>(p, i + l, j), out[l]);
         }
       }
     }
@@ -1130,12 +1172,12 @@ __device__ __forceinline__ void adj_kernel(const Params& p) {
       full[g] = (i + V <= nr);
       if (full[g]) {
 #pragma unroll
-        for (int s = 0; s < NS; ++s) IO<S>::template load<V>(at<S>(p.src[s], i, j, p.ld[s]), x[g].v[s]);
+        for (int s = 0; s < NS; ++s) load_rows<S, V>(p, s, i, j, x[g].v[s]);
       } else {
 #pragma unroll
         for (int s = 0; s < NS; ++s)
 #pragma unroll
-          for (int l = 0; l < V; ++l) x[g].v[s][l] = (i + l < nr) ? IO<S>::load1(at<S>(p.src[s], i + l, j, p.ld[s])) : C(0);
+          for (int l = 0; l < V; ++l) x[g].v[s][l] = (i + l < nr) ? IO<S>::load1(at_slot<S>(p, s, i + l, j)) : C(0);
       }
     }
 #pragma unroll

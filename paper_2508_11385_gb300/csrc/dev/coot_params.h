@@ -37,11 +37,16 @@ struct Params {
   // and its column stride in elements
   const void* src[COOT_MAX_SLOTS];
   long long ld[COOT_MAX_SLOTS];
+  // row strides of general slots (broadcast rows, diagonals, row-strided
+  // views): their element (i,j) is src[s] + i*rs[s] + j*ld[s]; other slots
+  // have rows one element apart
+  long long rs[COOT_MAX_SLOTS];
   // the tree's scalars, bit patterns of the compute type
   unsigned long long k[COOT_MAX_SCALARS_DEV];
   // materialised result Y (nullable) and its column stride
   void* out;
   long long out_ld;
+  long long out_rs;  // row stride of a general output (a diagonal), else unused
   // iteration shape (a contiguous tree is walked as one long column)
   long long n_rows, n_cols;
   // kernel-family specific: str -- chunks per column; row -- columns per split
@@ -72,6 +77,10 @@ struct Params {
 struct BatchProblem {
   const void* src[COOT_MAX_SLOTS];
   long long ld[COOT_MAX_SLOTS];
+  // row strides of general slots (broadcast rows, diagonals, row-strided
+  // views): their element (i,j) is src[s] + i*rs[s] + j*ld[s]; other slots
+  // have rows one element apart
+  long long rs[COOT_MAX_SLOTS];
   void* out;
   long long out_ld;
   long long n_rows, n_cols;

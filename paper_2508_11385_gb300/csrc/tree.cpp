@@ -19,6 +19,7 @@
 #include <cstdio>
 #include <cstring>
 #include <functional>
+#include <array>
 #include <map>
 #include <sstream>
 #include <tuple>
@@ -69,26 +70,27 @@ static bool is_unary(int op) {
 static bool is_scalar_op(int op) { return op >= COOT_N_SCAL_TIMES && op <= COOT_N_SCAL_DIV_POST; }
 static bool is_binary(int op) { return op >= COOT_N_PLUS && op <= COOT_N_DIV; }
 
+static int64_t mat_rs(const coot_mat& m) { return m.rs > 1 ? m.rs : 1; }
+
 static bool mat_shape_ok(const coot_mat& m) {
-  if (m.n_rows < 0 || m.n_cols < 0) return false;
-  if (m.n_cols > 1 && m.ld < m.n_rows) return false;
+  if (m.n_rows < 0 || m.n_cols < 0 || m.rs < 0) return false;
+  if (m.n_cols > 1 && m.ld < (m.n_rows > 0 ? (m.n_rows - 1) * mat_rs(m) + 1 : 0)) return false;
   if (m.n_cols > 1 && m.ld < 1) return false;
   return true;
 }
 
 static int64_t mat_ld(const coot_mat& m) { return (m.n_cols > 1) ? m.ld : (m.ld > 0 ? m.ld : m.n_rows); }
 
-// byte range [lo, hi) touched by a view of a matrix
-static void view_range(const coot_mat& m, int64_t r0, int64_t c0, int64_t vr, int64_t vc, int esz, uintptr_t* lo,
-                       uintptr_t* hi) {
-  if (vr <= 0 || vc <= 0) {
+// byte range [lo, hi) touched by nr x nc elements at base + (off + i*rs + j*cs)*esz
+static void strided_range(const void* data, int64_t off, int64_t rs, int64_t cs, int64_t nr, int64_t nc, int esz,
+                          uintptr_t* lo, uintptr_t* hi) {
+  if (nr <= 0 || nc <= 0) {
     *lo = *hi = 0;
     return;
   }
-  int64_t ld = mat_ld(m);
-  uintptr_t base = (uintptr_t)m.data;
-  *lo = base + (uintptr_t)((r0 + c0 * ld) * esz);
-  *hi = base + (uintptr_t)((r0 + vr - 1 + (c0 + vc - 1) * ld + 1) * esz);
+  uintptr_t base = (uintptr_t)data;
+  *lo = base + (uintptr_t)(off * esz);
+  *hi = base + (uintptr_t)((off + (nr - 1) * rs + (nc - 1) * cs + 1) * esz);
 }
 
 coot_status analyse(const coot_tree* tree, const coot_mat* leaves, int32_t n_leaves, const coot_mat* out,
@@ -150,6 +152,29 @@ coot_status analyse(const coot_tree* tree, const coot_mat* leaves, int32_t n_lea
       if ((s = operand(d.a, "a"))) return s;
       R[n] = Cc[d.a];
       Cc[n] = R[d.a];
+    } else if (op == COOT_N_EACH_COL) {
+      if ((s = operand(d.a, "a"))) return s;
+      if (Cc[d.a] != 1 || d.nc < 0)
+        return set_error(COOT_ERR_SHAPE, "node %d: each_col repeats a column vector (operand is %lldx%lld, nc %lld)", n,
+                         (long long)R[d.a], (long long)Cc[d.a], (long long)d.nc);
+      R[n] = R[d.a];
+      Cc[n] = d.nc;
+    } else if (op == COOT_N_EACH_ROW) {
+      if ((s = operand(d.a, "a"))) return s;
+      if (R[d.a] != 1 || d.nr < 0)
+        return set_error(COOT_ERR_SHAPE, "node %d: each_row repeats a row vector (operand is %lldx%lld, nr %lld)", n,
+                         (long long)R[d.a], (long long)Cc[d.a], (long long)d.nr);
+      R[n] = d.nr;
+      Cc[n] = Cc[d.a];
+    } else if (op == COOT_N_DIAG) {
+      if ((s = operand(d.a, "a"))) return s;
+      const int64_t k = d.r0;
+      const int64_t len = (k >= 0) ? std::min(R[d.a], Cc[d.a] - k) : std::min(R[d.a] + k, Cc[d.a]);
+      if (len < 0 || (k != 0 && (k >= Cc[d.a] || -k >= R[d.a])))
+        return set_error(COOT_ERR_SHAPE, "node %d: diagonal %lld outside a %lldx%lld matrix", n, (long long)k,
+                         (long long)R[d.a], (long long)Cc[d.a]);
+      R[n] = std::max<int64_t>(len, 0);
+      Cc[n] = 1;
     } else if (is_unary(op) || is_scalar_op(op)) {
       if ((s = operand(d.a, "a"))) return s;
       if (is_int && (op == COOT_N_EXP || op == COOT_N_LOG || op == COOT_N_SQRT))
@@ -228,78 +253,113 @@ coot_status analyse(const coot_tree* tree, const coot_mat* leaves, int32_t n_lea
                  red.kind == COOT_R_VAR || red.kind == COOT_R_STDDEV))
     return set_error(COOT_ERR_DTYPE, "mean/norm/var/stddev are not defined for INT32 trees");
 
-  // ---- canonical form: push trans() down to the leaf reads
-  std::map<std::pair<int, int>, int> memo;
-  std::map<std::tuple<int, int64_t, int64_t, int64_t, int64_t, int>, int> slot_of;
-  std::function<int(int, bool)> canon = [&](int n, bool t) -> int {
-    auto key = std::make_pair(n, (int)t);
+  // ---- canonical form: push trans(), each_col / each_row and diag() down to
+  // the leaf reads.  The state carried down is the affine map from the root's
+  // element (i,j) to the current node's element (row, col):
+  //   row = m[0] i + m[1] j + m[2],   col = m[3] i + m[4] j + m[5]
+  // trans swaps the two lines, each_col sets col = 0, each_row sets row = 0,
+  // diag(k) maps (row, 0) to (row + max(-k,0), row + max(k,0)).
+  typedef std::array<int64_t, 6> Map;
+  std::map<std::pair<int, Map>, int> memo;
+  std::map<std::tuple<int, int64_t, int64_t, int64_t, int>, int> slot_of;
+  std::function<int(int, const Map&)> canon = [&](int n, const Map& m) -> int {
+    auto key = std::make_pair(n, m);
     auto it = memo.find(key);
     if (it != memo.end()) return it->second;
     const coot_node& d = tree->nodes[n];
     CNode c;
     if (d.op == COOT_N_LEAF || d.op == COOT_N_SUBMAT) {
-      int leaf = (d.op == COOT_N_LEAF) ? d.leaf : tree->nodes[d.a].leaf;
+      const int leaf = (d.op == COOT_N_LEAF) ? d.leaf : tree->nodes[d.a].leaf;
       const coot_mat& L = leaves[leaf];
-      int64_t r0 = 0, c0 = 0, vr = L.n_rows, vc = L.n_cols;
-      if (d.op == COOT_N_SUBMAT) {
-        r0 = d.r0;
-        c0 = d.c0;
-        vr = d.nr;
-        vc = d.nc;
+      const int64_t r0 = (d.op == COOT_N_SUBMAT) ? d.r0 : 0, c0 = (d.op == COOT_N_SUBMAT) ? d.c0 : 0;
+      const int64_t lrs = mat_rs(L), lld = mat_ld(L);
+      int64_t rs = m[0] * lrs + m[3] * lld, cs = m[1] * lrs + m[4] * lld;
+      const int64_t off = (m[2] + r0) * lrs + (m[5] + c0) * lld;
+      // a transposed view of a leaf with adjacent rows goes through the tile
+      // staging (whatever the shape, so that problems of a batch agree);
+      // adjacent rows are direct; anything else is general
+      const bool tr = (m[0] == 0 && m[1] == 1 && m[3] == 1 && m[4] == 0 && lrs == 1);
+      if (!tr) {
+        // a stride along an extent of one is never used: a single row reads
+        // as adjacent rows, a single column as a contiguous one
+        if (an->nr <= 1) rs = 1;
+        if (an->nc <= 1) cs = an->nr;
       }
-      auto sk = std::make_tuple(leaf, r0, c0, vr, vc, (int)t);
+      const int kind = tr ? 1 : (rs == 1 ? 0 : 2);
+      auto sk = std::make_tuple(leaf, off, rs, cs, kind);
       auto si = slot_of.find(sk);
-      int s;
+      int sidx;
       if (si == slot_of.end()) {
-        s = (int)an->slots.size();
+        sidx = (int)an->slots.size();
         Slot sl;
         sl.leaf = leaf;
-        sl.r0 = r0;
-        sl.c0 = c0;
-        sl.vr = vr;
-        sl.vc = vc;
-        sl.trans = t;
-        sl.full = (r0 == 0 && c0 == 0 && vr == L.n_rows && vc == L.n_cols);
+        sl.off = off;
+        sl.rs = rs;
+        sl.cs = cs;
+        sl.trans = (kind == 1);
+        sl.gen = (kind == 2);
+        sl.r0 = m[2] + r0;  // trans: view origin (row, col) = (r0 + m2, c0 + m5)
+        sl.c0 = m[5] + c0;
+        sl.vr = an->nc;     // trans: view rows = tree columns
+        sl.vc = an->nr;
+        sl.full = (kind == 0 && off == 0 && lrs == 1 && an->nr == L.n_rows && an->nc == L.n_cols &&
+                   (an->nc <= 1 || cs == lld));
+        sl.n_distinct = (rs != 0 ? an->nr : 1) * (cs != 0 ? an->nc : 1);
         an->slots.push_back(sl);
-        slot_of[sk] = s;
+        slot_of[sk] = sidx;
       } else {
-        s = si->second;
+        sidx = si->second;
       }
       c.op = COOT_N_LEAF;
-      c.slot = s;
+      c.slot = sidx;
     } else if (d.op == COOT_N_TRANS) {
-      int r = canon(d.a, !t);
+      int r = canon(d.a, Map{m[3], m[4], m[5], m[0], m[1], m[2]});
+      memo[key] = r;
+      return r;
+    } else if (d.op == COOT_N_EACH_COL) {
+      int r = canon(d.a, Map{m[0], m[1], m[2], 0, 0, 0});
+      memo[key] = r;
+      return r;
+    } else if (d.op == COOT_N_EACH_ROW) {
+      int r = canon(d.a, Map{0, 0, 0, m[3], m[4], m[5]});
+      memo[key] = r;
+      return r;
+    } else if (d.op == COOT_N_DIAG) {
+      const int64_t k = d.r0, kr = k < 0 ? -k : 0, kc = k > 0 ? k : 0;
+      int r = canon(d.a, Map{m[0], m[1], m[2] + kr, m[0], m[1], m[2] + kc});
       memo[key] = r;
       return r;
     } else if (is_unary(d.op) || is_scalar_op(d.op)) {
       c.op = d.op;
-      c.a = canon(d.a, t);
+      c.a = canon(d.a, m);
       if (is_scalar_op(d.op)) {
         c.kidx = (int)an->scalars.size();
         an->scalars.push_back(d.k);
       }
     } else {
       c.op = d.op;
-      c.a = canon(d.a, t);
-      c.b = canon(d.b, t);
+      c.a = canon(d.a, m);
+      c.b = canon(d.b, m);
     }
     int idx = (int)an->cn.size();
     an->cn.push_back(c);
     memo[key] = idx;
     return idx;
   };
-  an->root = canon(root, false);
+  an->root = canon(root, Map{1, 0, 0, 0, 1, 0});
   if ((int)an->slots.size() > COOT_MAX_SLOTS)
     return set_error(COOT_ERR_UNSUPPORTED, "tree reads %d distinct leaf views; at most %d", (int)an->slots.size(),
                      COOT_MAX_SLOTS);
   if ((int)an->scalars.size() > COOT_MAX_SCALARS_DEV)
     return set_error(COOT_ERR_UNSUPPORTED, "tree has %d scalars; at most %d", (int)an->scalars.size(),
                      COOT_MAX_SCALARS_DEV);
-  for (size_t s = 0; s < an->slots.size(); ++s)
+  for (size_t s = 0; s < an->slots.size(); ++s) {
     if (an->slots[s].trans) {
       an->any_trans = true;
       an->trmask |= (1 << s);
     }
+    if (an->slots[s].gen) an->gmask |= (1 << s);
+  }
 
   // ---- C++ type of the canonical tree
   std::function<std::string(int)> spell = [&](int i) -> std::string {
@@ -353,25 +413,31 @@ coot_status analyse(const coot_tree* tree, const coot_mat* leaves, int32_t n_lea
     if (out->n_rows != an->nr || out->n_cols != an->nc)
       return set_error(COOT_ERR_SHAPE, "out is %lldx%lld, the tree is %lldx%lld", (long long)out->n_rows,
                        (long long)out->n_cols, (long long)an->nr, (long long)an->nc);
-    if (!mat_shape_ok(*out)) return set_error(COOT_ERR_INVALID, "out: bad ld");
+    if (!mat_shape_ok(*out)) return set_error(COOT_ERR_INVALID, "out: bad ld or row stride");
     if (!out->data && an->nr * an->nc > 0) return set_error(COOT_ERR_INVALID, "out: NULL data");
-    // aliasing: overlap with a leaf view is allowed only for an identical,
-    // untransposed read (each element is read and written by one thread)
+    an->out_rs = mat_rs(*out);
+    if (an->out_rs != 1 && an->nr > 1) an->gmask |= (1 << COOT_MAX_SLOTS);
+    // aliasing: overlap with a leaf read is allowed only for an identical
+    // read (same elements in the same order: each element is read and
+    // written by one thread)
+    const int64_t ocs = an->nc > 1 ? mat_ld(*out) : 0, ors = an->nr > 1 ? an->out_rs : 0;
     uintptr_t olo, ohi;
-    view_range(*out, 0, 0, an->nr, an->nc, an->esz, &olo, &ohi);
+    strided_range(out->data, 0, an->out_rs, mat_ld(*out), an->nr, an->nc, an->esz, &olo, &ohi);
     for (const Slot& s : an->slots) {
       const coot_mat& L = leaves[s.leaf];
-      int64_t vr = s.trans ? s.vr : s.vr, vc = s.vc;
       uintptr_t llo, lhi;
-      view_range(L, s.r0, s.c0, vr, vc, an->esz, &llo, &lhi);
+      if (s.trans)
+        strided_range(L.data, s.off, s.rs, s.cs, an->nr, an->nc, an->esz, &llo, &lhi);
+      else
+        strided_range(L.data, s.off, s.rs, s.cs, an->nr, an->nc, an->esz, &llo, &lhi);
       if (olo < lhi && llo < ohi) {
-        uintptr_t vorig = (uintptr_t)L.data + (uintptr_t)((s.r0 + s.c0 * mat_ld(L)) * an->esz);
-        bool same = !s.trans && vorig == (uintptr_t)out->data && s.vr == an->nr && s.vc == an->nc &&
-                    (an->nc <= 1 || mat_ld(L) == mat_ld(*out));
+        const uintptr_t vorig = (uintptr_t)L.data + (uintptr_t)(s.off * an->esz);
+        const bool same = !s.trans && vorig == (uintptr_t)out->data && (an->nr <= 1 || s.rs == ors) &&
+                          (an->nc <= 1 || s.cs == ocs);
         if (!same)
           return set_error(COOT_ERR_ALIAS,
-                           "out overlaps leaf %d through a %s read; only an identical untransposed read may alias",
-                           s.leaf, s.trans ? "transposed" : "differently shaped");
+                           "out overlaps leaf %d through a %s read; only an identical read may alias", s.leaf,
+                           s.trans ? "transposed" : "differently shaped or strided");
       }
     }
   }
@@ -385,34 +451,35 @@ Choice choose(const Analysis& an, const coot_mat* leaves, const coot_mat* out) {
   Choice ch;
   ch.it_rows = an.nr;
   ch.it_cols = an.nc;
+  const bool out_gen = (an.gmask >> COOT_MAX_SLOTS) & 1;
+  // vector accesses (16 bytes down a column) need every column start of the
+  // direct reads and of a direct output 16-byte aligned; general reads and
+  // writes go one element at a time and transposed reads through shared
+  // memory, so neither takes part
+  auto aligned = [&](bool collapsed) {
+    for (const Slot& s : an.slots) {
+      if (s.trans || s.gen) continue;
+      const coot_mat& L = leaves[s.leaf];
+      const uintptr_t org = (uintptr_t)L.data + (uintptr_t)(s.off * an.esz);
+      if (org % 16) return false;
+      if (!collapsed && an.nc > 1 && (s.cs * an.esz) % 16) return false;
+    }
+    if (out && !out_gen) {
+      if ((uintptr_t)out->data % 16) return false;
+      if (!collapsed && an.nc > 1 && (mat_ld(*out) * an.esz) % 16) return false;
+    }
+    return true;
+  };
   if (an.any_trans) {
     ch.fam = F_TILE;
-    // the vectorised tile kernel reads direct slots and writes the output
-    // V elements at a time down each column
-    bool vec = true;
-    for (const Slot& s : an.slots) {
-      if (s.trans) continue;
-      const coot_mat& L = leaves[s.leaf];
-      uintptr_t org = (uintptr_t)L.data + (uintptr_t)((s.r0 + s.c0 * mat_ld(L)) * an.esz);
-      if (org % 16 || (s.vc > 1 && (mat_ld(L) * an.esz) % 16)) vec = false;
-    }
-    if (out && ((uintptr_t)out->data % 16 || (an.nc > 1 && (mat_ld(*out) * an.esz) % 16))) vec = false;
-    ch.vec_ok = vec;
+    ch.vec_ok = aligned(false);
     return ch;
   }
   const int dim = an.red.dim;
   if (an.scan()) {
-    // cumsum: warps down the columns or threads along the rows, never
-    // collapsed; vector access needs every column start 16-byte aligned
+    // cumsum: warps down the columns or threads along the rows, never collapsed
     ch.fam = F_SCAN;
-    bool vec = true;
-    for (const Slot& s : an.slots) {
-      const coot_mat& L = leaves[s.leaf];
-      uintptr_t org = (uintptr_t)L.data + (uintptr_t)((s.r0 + s.c0 * mat_ld(L)) * an.esz);
-      if (org % 16 || (s.vc > 1 && (mat_ld(L) * an.esz) % 16)) vec = false;
-    }
-    if ((uintptr_t)out->data % 16 || (an.nc > 1 && (mat_ld(*out) * an.esz) % 16)) vec = false;
-    ch.vec_ok = vec;
+    ch.vec_ok = aligned(false);
     return ch;
   }
   // every kind that takes a dim: sum, mean, var, stddev, min, max, index_*, prod
@@ -423,31 +490,17 @@ Choice choose(const Analysis& an, const coot_mat* leaves, const coot_mat* out) {
     ch.fam = F_ROW;
   else
     ch.fam = F_STR;
-  // contiguity of every read and of the output
+  // contiguity of every read and of the output: the tree is one long column
   bool contig = true;
-  for (const Slot& s : an.slots) {
-    const coot_mat& L = leaves[s.leaf];
-    if (s.vc > 1 && mat_ld(L) != s.vr) contig = false;
-  }
-  if (out && an.nc > 1 && mat_ld(*out) != an.nr) contig = false;
+  for (const Slot& s : an.slots)
+    if (s.gen || (an.nc > 1 && s.cs != an.nr)) contig = false;
+  if (out && (out_gen || (an.nc > 1 && mat_ld(*out) != an.nr))) contig = false;
   if (ch.fam == F_STR && contig) {
     ch.collapsed = true;
     ch.it_rows = an.nr * an.nc;
     ch.it_cols = (ch.it_rows > 0) ? 1 : 0;
   }
-  // 16-byte alignment of every column start
-  bool vec = true;
-  for (const Slot& s : an.slots) {
-    const coot_mat& L = leaves[s.leaf];
-    uintptr_t org = (uintptr_t)L.data + (uintptr_t)((s.r0 + s.c0 * mat_ld(L)) * an.esz);
-    if (org % 16) vec = false;
-    if (!ch.collapsed && s.vc > 1 && (mat_ld(L) * an.esz) % 16) vec = false;
-  }
-  if (out) {
-    if ((uintptr_t)out->data % 16) vec = false;
-    if (!ch.collapsed && an.nc > 1 && (mat_ld(*out) * an.esz) % 16) vec = false;
-  }
-  ch.vec_ok = vec;
+  ch.vec_ok = aligned(ch.collapsed);
   return ch;
 }
 
@@ -463,6 +516,7 @@ Program make_program(const Analysis& an, Family fam, bool var_two_pass) {
   const bool OUT = an.has_out;
   const int V = vmax(an);
   std::ostringstream src, sig;
+  if (an.gmask) src << "#define COOT_GM " << an.gmask << "\n";
   if (an.accum == 1) src << "#define COOT_ACCUM_KAHAN 1\n";
   if (an.accum == 2) src << "#define COOT_ACCUM_PLAIN 1\n";
   src << "#include \"coot_kernels.cuh\"\nusing namespace coot;\n";
@@ -628,7 +682,7 @@ Program make_program(const Analysis& an, Family fam, bool var_two_pass) {
     add("coot_batch", 1, 1, 256);
   }
   sig << "cootgb1|" << family_name(fam) << "|" << S << "|ns" << NS << "|nk" << NK << "|red" << an.red_mode << "|dim"
-      << an.red.dim << "|out" << OUT << "|tr" << an.trmask << "|var" << var_two_pass
+      << an.red.dim << "|out" << OUT << "|tr" << an.trmask << "|gm" << an.gmask << "|var" << var_two_pass
       << (an.accum == 1 ? "|kahan" : (an.accum == 2 ? "|plain" : "")) << "|" << an.type_str;
   pg.signature = sig.str();
   pg.source = src.str();

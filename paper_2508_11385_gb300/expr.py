@@ -86,6 +86,14 @@ class Expr:
             op = self.op
             if op == L.N_SUBMAT:
                 self._shape = (self.view[2], self.view[3])
+            elif op == L.N_EACH_COL:
+                self._shape = (self.children[0].n_rows, self.view)
+            elif op == L.N_EACH_ROW:
+                self._shape = (self.view, self.children[0].n_cols)
+            elif op == L.N_DIAG:
+                r, c = self.children[0].shape
+                k = self.view
+                self._shape = (builtins.max(0, builtins.min(r, c - k) if k >= 0 else builtins.min(r + k, c)), 1)
             elif op == L.N_TRANS:
                 r, c = self.children[0].shape
                 self._shape = (c, r)
@@ -163,41 +171,130 @@ class Expr:
     def t(self):
         return trans(self)
 
+    def diag(self, k=0):
+        """Armadillo's X.diag(k): the k-th diagonal (k > 0 above the main
+        one, k < 0 below) as a column vector.  Of a matrix (or a submatrix
+        view) it is also a view that ``evaluate(..., out=...)`` and the
+        in-place operators can write."""
+        r, c = self.shape
+        if (k >= 0 and k >= c and c > 0) or (k < 0 and -k >= r and r > 0):
+            raise IndexError("diag: diagonal %d outside a %dx%d matrix" % (k, r, c))
+        return Expr(L.N_DIAG, (self,), view=int(k))
+
+    def each_col(self):
+        """Armadillo's X.each_col(): ``X.each_col() + v`` adds the column
+        vector v to every column (also - % / and the reversed forms)."""
+        return _Each(self, L.N_EACH_COL)
+
+    def each_row(self):
+        """Armadillo's X.each_row(): the same with a row vector per row."""
+        return _Each(self, L.N_EACH_ROW)
+
+    # ---- in-place updates of a view (a Mat, a submatrix or a diagonal) ------
+    def _assign(self, value):
+        evaluate(value, out=self)
+        return self
+
+    def __iadd__(self, o):
+        return self._assign(self + o)
+
+    def __isub__(self, o):
+        return self._assign(self - o)
+
+    def __imul__(self, o):
+        return self._assign(self * o)
+
+    def __imod__(self, o):
+        return self._assign(self % o)
+
+    def __itruediv__(self, o):
+        return self._assign(self / o)
+
     def eval(self, out=None, fused=True, stream=None):
         return evaluate(self, out=out, fused=fused, stream=stream)
+
+
+class _Each:
+    """X.each_col() / X.each_row(): the other operand of an arithmetic
+    operator is a column (row) vector repeated over X's columns (rows)."""
+
+    def __init__(self, x, op):
+        self.x, self.op = x, op
+
+    def _rep(self, v):
+        v = _as_expr(v)
+        if self.op == L.N_EACH_COL:
+            if v.n_rows != self.x.n_rows:
+                raise ValueError("each_col: needs a %dx1 column vector, got %dx%d" % (self.x.n_rows, *v.shape))
+            return broadcast_col(v, self.x.n_cols)
+        if v.n_cols != self.x.n_cols:
+            raise ValueError("each_row: needs a 1x%d row vector, got %dx%d" % (self.x.n_cols, *v.shape))
+        return broadcast_row(v, self.x.n_rows)
+
+    def __add__(self, v):
+        return self.x + self._rep(v)
+
+    def __radd__(self, v):
+        return self._rep(v) + self.x
+
+    def __sub__(self, v):
+        return self.x - self._rep(v)
+
+    def __rsub__(self, v):
+        return self._rep(v) - self.x
+
+    def __mod__(self, v):
+        return self.x % self._rep(v)
+
+    def __rmod__(self, v):
+        return self._rep(v) % self.x
+
+    def __truediv__(self, v):
+        return self.x / self._rep(v)
+
+    def __rtruediv__(self, v):
+        return self._rep(v) / self.x
 
 
 class Mat(Expr):
     """A column-major matrix in device memory, wrapping a torch tensor.
 
-    The tensor must be 2-D with unit row stride (element (i,j) at
-    data[i + j*ld], ld = t.stride(1)), e.g. ``torch.empty(n_cols, n_rows).t()``,
-    or 1-D (a column vector)."""
+    The tensor is 2-D with element (i,j) at data[i*rs + j*ld] (rs =
+    t.stride(0), ld = t.stride(1)): column-major when rs == 1, e.g.
+    ``torch.empty(n_cols, n_rows).t()``; rs > 1 reads rows rs elements apart
+    (a diagonal, every k-th row), one element at a time.  A 1-D tensor is a
+    column vector with row stride t.stride(0) (``Z.diagonal()`` works)."""
 
     def __init__(self, t: torch.Tensor):
         super().__init__(L.N_LEAF)
+        rs = 1
         if t.dim() == 1:
-            if t.stride(0) != 1 and t.numel() > 1:
-                raise ValueError("1-D tensors must be contiguous")
             t2 = t.unsqueeze(1)
             n_rows, n_cols, ld = t.shape[0], 1, builtins.max(t.shape[0], 1)
+            rs = t.stride(0) if t.shape[0] > 1 else 1
         elif t.dim() == 2:
             t2 = t
             n_rows, n_cols = t.shape
-            if n_rows > 1 and t.stride(0) != 1:
-                raise ValueError("tensor is not column-major (stride(0) must be 1); use t.t().contiguous().t()")
             ld = t.stride(1) if n_cols > 1 else builtins.max(n_rows, 1)
-            if n_cols > 1 and ld < n_rows:
-                raise ValueError("column stride smaller than the number of rows")
+            if n_rows > 1 and t.stride(0) != 1:
+                if n_cols > 1 and t.stride(1) == 1:
+                    raise ValueError("tensor is row-major (stride(1) == 1): wrap t.t() and use trans(), or "
+                                     "t.t().contiguous().t()")
+                rs = t.stride(0)
+            if n_cols > 1 and ld < (n_rows - 1) * rs + 1 and n_rows > 0:
+                raise ValueError("column stride smaller than the rows it spans")
         else:
             raise ValueError("Mat wraps 1-D or 2-D tensors")
         if t.dtype not in _DTYPE:
             raise TypeError("unsupported dtype %s" % t.dtype)
         if t.device.type != "cuda":
             raise ValueError("Mat wraps CUDA tensors (device memory); got %s" % t.device)
+        if rs < 1:
+            raise ValueError("row stride must be positive")
         self.tensor = t2
         self.dtype = _DTYPE[t.dtype]
         self.ld = int(ld)
+        self.rs = int(rs)
         self._shape = (int(n_rows), int(n_cols))
 
     def submat(self, first_row, first_col, last_row, last_col):
@@ -209,7 +306,25 @@ class Mat(Expr):
         return Expr(L.N_SUBMAT, (self,), view=(first_row, first_col, nr, nc))
 
     def cmat(self):
-        return L.mat(self.tensor.data_ptr(), L.DTYPE_CODE[self.dtype], self.n_rows, self.n_cols, self.ld)
+        return L.mat(self.tensor.data_ptr(), L.DTYPE_CODE[self.dtype], self.n_rows, self.n_cols, self.ld,
+                     self.rs if self.rs > 1 else 0)
+
+
+def broadcast_col(v, n_cols):
+    """The column vector v repeated as n_cols columns (the operand that
+    ``X.each_col() op v`` pairs with X); never materialised."""
+    v = _as_expr(v)
+    if v.n_cols != 1:
+        raise ValueError("broadcast_col: needs a column vector, got %dx%d" % v.shape)
+    return Expr(L.N_EACH_COL, (v,), view=int(n_cols))
+
+
+def broadcast_row(r, n_rows):
+    """The row vector r repeated as n_rows rows (``X.each_row() op r``)."""
+    r = _as_expr(r)
+    if r.n_rows != 1:
+        raise ValueError("broadcast_row: needs a row vector, got %dx%d" % r.shape)
+    return Expr(L.N_EACH_ROW, (r,), view=int(n_rows))
 
 
 def _as_expr(x):
@@ -258,7 +373,7 @@ def lower(expr: Expr):
         if key in memo:
             return memo[key]
         if e.op == L.N_LEAF:
-            lk = (e.tensor.data_ptr(), e.shape, e.ld, e.dtype)
+            lk = (e.tensor.data_ptr(), e.shape, e.ld, e.rs, e.dtype)
             if lk not in leaf_idx:
                 leaf_idx[lk] = len(leaves)
                 leaves.append(e)
@@ -271,6 +386,12 @@ def lower(expr: Expr):
             a = visit(e.children[0])
             b = visit(e.children[1])
             nodes.append(L.node(e.op, a=a, b=b))
+        elif e.op == L.N_EACH_COL:
+            nodes.append(L.node(e.op, a=visit(e.children[0]), nc=e.view))
+        elif e.op == L.N_EACH_ROW:
+            nodes.append(L.node(e.op, a=visit(e.children[0]), nr=e.view))
+        elif e.op == L.N_DIAG:
+            nodes.append(L.node(e.op, a=visit(e.children[0]), r0=e.view))
         else:
             a = visit(e.children[0])
             nodes.append(L.node(e.op, a=a, k=e.k))
@@ -433,11 +554,40 @@ def prod(x, dim=None):
 # ---------------------------------------------------------------------------
 # evaluation
 # ---------------------------------------------------------------------------
+_ESIZE = {"f32": 4, "f64": 8, "bf16": 2, "f16": 2, "i32": 4}
+
+
+def _view_of(e):
+    """(data pointer, dtype, n_rows, n_cols, ld, rs) of a writable view: a
+    Mat, a submatrix of one, or a diagonal of either."""
+    if isinstance(e, Mat):
+        return e.tensor.data_ptr(), e.dtype, e.n_rows, e.n_cols, e.ld, e.rs
+    if e.op == L.N_SUBMAT:
+        ptr, dt, _, _, ld, rs = _view_of(e.children[0])
+        r0, c0, nr, nc = e.view
+        return ptr + (r0 * rs + c0 * ld) * _ESIZE[dt], dt, nr, nc, ld, rs
+    if e.op == L.N_DIAG:
+        ptr, dt, _, _, ld, rs = _view_of(e.children[0])
+        k = e.view
+        kr, kc = (-k, 0) if k < 0 else (0, k)
+        n = e.n_rows
+        return ptr + (kr * rs + kc * ld) * _ESIZE[dt], dt, n, 1, builtins.max(n, 1), rs + ld
+    raise TypeError("out must be a tensor, a Mat, a submatrix view or a diagonal view")
+
+
+def _out_cmat(out):
+    if isinstance(out, torch.Tensor):
+        return Mat(out).cmat()
+    ptr, dt, nr, nc, ld, rs = _view_of(out)
+    return L.mat(ptr, L.DTYPE_CODE[dt], nr, nc, ld, rs if rs > 1 else 0)
+
+
 def evaluate(expr, out=None, reduction=None, red_out=None, fused=True, stream=None, materialise=None):
     """Evaluate ``expr`` (delayed evaluation on assignment).
 
-    * ``out``: a column-major tensor to receive Y (allocated when None and no
-      reduction is requested, or when ``materialise`` is True);
+    * ``out``: a tensor (column-major, or rows rs apart) or a view -- a Mat,
+      ``X.submat(...)``, ``X.diag(k)`` -- to receive Y (allocated when None
+      and no reduction is requested, or when ``materialise`` is True);
     * ``reduction``: a Reduction (or None) fused onto the same pass; its
       result is returned as a tensor of the accumulation dtype (0-d for a
       scalar, column-major 1 x n_cols / n_rows x 1 for dim 0 / 1).
@@ -458,14 +608,14 @@ def evaluate(expr, out=None, reduction=None, red_out=None, fused=True, stream=No
         with torch.cuda.device(dev):
             ctx = context(dev)
             fn = L.coot_eval if fused else L.coot_eval_unfused
-            fn(ctx, tree, cmats, Mat(out).cmat(), red, None, _stream_ptr(stream))
+            fn(ctx, tree, cmats, _out_cmat(out), red, None, _stream_ptr(stream))
         return None, out
     want_y = out is not None or reduction is None or materialise is True
     if isinstance(materialise, torch.Tensor):
         out = materialise
     if want_y and out is None:
         out = _empty_colmajor(nr, nc, dt, dev)
-    out_m = Mat(out).cmat() if out is not None else None
+    out_m = _out_cmat(out) if out is not None else None
     red = L.reduce()
     rt = None
     if reduction is not None:
@@ -498,7 +648,7 @@ def warmup(expr, reduction=None, out=None):
     dev = leaves[0].tensor.device
     if out is None and reduction is not None and reduction.kind == L.R_CUMSUM:
         out = _empty_colmajor(expr.n_rows, expr.n_cols, leaves[0].dtype, dev)  # a scan needs its output
-    out_m = Mat(out).cmat() if out is not None else None
+    out_m = _out_cmat(out) if out is not None else None
     with torch.cuda.device(dev):
         L.coot_warmup(context(dev), tree, cmats, out_m, red)
 
@@ -507,7 +657,7 @@ def signature(expr, reduction=None, out=None) -> str:
     expr = _as_expr(expr)
     tree, leaves, cmats = lower(expr)
     red = L.reduce() if reduction is None else L.reduce(reduction.kind, reduction.dim, reduction.norm_type)
-    out_m = Mat(out).cmat() if out is not None else None
+    out_m = _out_cmat(out) if out is not None else None
     return L.coot_signature(tree, cmats, out_m, red)
 
 

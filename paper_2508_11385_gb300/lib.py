@@ -23,7 +23,8 @@ F32, F64, BF16, F16, I32 = 0, 1, 2, 3, 4
 DTYPE_CODE = {"f32": F32, "f64": F64, "bf16": BF16, "f16": F16, "i32": I32}
 
 (N_LEAF, N_SUBMAT, N_TRANS, N_SCAL_TIMES, N_SCAL_PLUS, N_SCAL_MINUS_PRE, N_SCAL_MINUS_POST, N_SCAL_DIV_PRE,
- N_SCAL_DIV_POST, N_PLUS, N_MINUS, N_SCHUR, N_DIV, N_NEG, N_EXP, N_LOG, N_ABS, N_SQUARE, N_SQRT) = range(19)
+ N_SCAL_DIV_POST, N_PLUS, N_MINUS, N_SCHUR, N_DIV, N_NEG, N_EXP, N_LOG, N_ABS, N_SQUARE, N_SQRT, N_EACH_COL,
+ N_EACH_ROW, N_DIAG) = range(22)
 
 (R_NONE, R_ACCU, R_SUM, R_MEAN, R_DOT, R_NORM2, R_NORM_FRO, R_VAR, R_STDDEV, R_MIN, R_MAX, R_INDEX_MIN,
  R_INDEX_MAX, R_PROD, R_CUMSUM) = range(15)
@@ -34,7 +35,7 @@ MAX_NODES, MAX_LEAVES, MAX_SCALARS = 64, 8, 16
 
 
 class coot_mat(ctypes.Structure):
-    _fields_ = [("data", ctypes.c_void_p), ("dtype", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    _fields_ = [("data", ctypes.c_void_p), ("dtype", ctypes.c_int32), ("rs", ctypes.c_int32),
                 ("n_rows", ctypes.c_int64), ("n_cols", ctypes.c_int64), ("ld", ctypes.c_int64)]
 
 
@@ -268,7 +269,7 @@ def reduce(kind=R_NONE, dim=-1, norm_type=0):
     return coot_reduce(kind, dim, norm_type, 0)
 
 
-def mat(ptr, dtype, n_rows, n_cols, ld=None):
+def mat(ptr, dtype, n_rows, n_cols, ld=None, rs=0):
     if ld is None:
         ld = max(n_rows, 1)
-    return coot_mat(ptr, dtype, 0, n_rows, n_cols, ld)
+    return coot_mat(ptr, dtype, rs, n_rows, n_cols, ld)

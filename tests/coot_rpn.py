@@ -57,6 +57,12 @@ def build(program: str, tensors):
             st.append(-st.pop())
         elif tok in ("exp", "log", "abs", "square", "sqrt", "trans"):
             st.append(getattr(coot, tok)(st.pop()))
+        elif tok.startswith("each_col:"):
+            st.append(coot.broadcast_col(st.pop(), int(tok.split(":")[1])))
+        elif tok.startswith("each_row:"):
+            st.append(coot.broadcast_row(st.pop(), int(tok.split(":")[1])))
+        elif tok == "diag" or tok.startswith("diag:"):
+            st.append(st.pop().diag(int(tok.split(":")[1]) if ":" in tok else 0))
         elif tok.startswith("submat:"):
             r0, c0, nr, nc = map(int, tok.split(":")[1:])
             st.append(st.pop().submat(r0, c0, r0 + nr - 1, c0 + nc - 1))

@@ -173,6 +173,13 @@ def eval_emulated(program: str, leaves, ftype=np.float32):
                 st.append(out)
             elif tok == "trans":
                 st.append(np.ascontiguousarray(st.pop().T))
+            elif tok.startswith("each_col:"):
+                st.append(np.repeat(st.pop(), int(tok.split(":")[1]), axis=1))
+            elif tok.startswith("each_row:"):
+                st.append(np.repeat(st.pop(), int(tok.split(":")[1]), axis=0))
+            elif tok == "diag" or tok.startswith("diag:"):
+                k = int(tok.split(":")[1]) if ":" in tok else 0
+                st.append(np.diag(st.pop(), k).reshape(-1, 1).copy())
             else:
                 raise ValueError(tok)
     assert len(st) == 1
