@@ -132,6 +132,12 @@ def build_expr(program, mats):
         elif tok.partition(":")[0] in ("min", "max", "index_min", "index_max", "prod"):
             head, _, d = tok.partition(":")
             red = getattr(coot, head)(st[-1], int(d) if d else -1)
+        elif tok.startswith("each_col:"):
+            st.append(coot.broadcast_col(st.pop(), int(tok.split(":")[1])))
+        elif tok.startswith("each_row:"):
+            st.append(coot.broadcast_row(st.pop(), int(tok.split(":")[1])))
+        elif tok == "diag" or tok.startswith("diag:"):
+            st.append(st.pop().diag(int(tok.split(":")[1]) if ":" in tok else 0))
         elif tok.partition(":")[0] == "cumsum":
             d = tok.partition(":")[2]
             red = coot.cumsum(st[-1], int(d) if d else None)
@@ -604,8 +610,14 @@ def bench_stats(args, dev, stream, peak=None):
     out = {}
     progs = [("A B % C + " + r, r) for r in STATS]
     progs += [("A trans B % C + " + r, "trans " + r) for r in STATS_T]
-    for prog, name in progs:
-        c = Call(prog, lv)
+    # broadcasting: A n x n, B a column, C a row, each repeated over A
+    n = args.n
+    bv = [lv[0], lv[1][:, :1], lv[2][:1, :]]
+    views = [("A B each_col:%d %% C each_row:%d +" % (n, n), "each_col % each_row + (Y)"),
+             ("A B each_col:%d %% C each_row:%d + accu" % (n, n), "each_col % each_row + accu"),
+             ("A B each_col:%d - square sum:1" % n, "each_col - square sum:1")]
+    for prog, name in progs + [(p, "views " + nm) for p, nm in views]:
+        c = Call(prog, bv if name.startswith("views") else lv)
         c(sp)
         torch.cuda.synchronize()
         ms = time_calls(lambda: c(sp), stream, reps=10)
