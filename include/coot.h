@@ -179,7 +179,12 @@ typedef struct {
   int32_t kind;      /* coot_red_kind                           */
   int32_t dim;       /* -1 all elements, 0 per column, 1 per row */
   int32_t norm_type; /* R_VAR / R_STDDEV only                   */
-  int32_t reserved;
+  int32_t n_seg;     /* dim 1 only, 0 or 1 = one segment: the columns form
+                        n_seg equal segments (n_cols % n_seg == 0), each
+                        reduced (or, for cumsum, scanned) on its own: the
+                        result is n_rows x n_seg, segment s in column s.
+                        A Cube's slices laid side by side are segments
+                        (Sec. 2: Cube, collections of matrices).      */
 } coot_reduce;
 
 typedef struct coot_ctx coot_ctx;

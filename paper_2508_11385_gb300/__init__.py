@@ -13,7 +13,9 @@ __all__ = ["expr", "workloads"]
 def __getattr__(name):
     import importlib
 
-    if name in ("workloads", "expr", "lib", "autograd", "build"):
+    if name in ("workloads", "expr", "lib", "autograd", "build", "cube"):
         return importlib.import_module("." + name, __name__)
+    if name in ("Cube", "cube_empty", "each_slice"):
+        return getattr(importlib.import_module(".cube", __name__), name)
     mod = importlib.import_module(".expr", __name__)
     return getattr(mod, name)

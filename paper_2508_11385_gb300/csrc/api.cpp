@@ -218,13 +218,17 @@ void shape_launch(coot_ctx* ctx, const cg::Analysis& an, const cg::Choice& ch, c
   } else if (ch.fam == cg::F_ROW) {
     const int64_t nrb = std::max<int64_t>(1, ceil_div(R, (int64_t)block * k.vec));
     int64_t nsp = std::max<int64_t>(1, std::min<int64_t>(C, resident / nrb));
-    const int64_t cps = std::max<int64_t>(1, ceil_div(std::max<int64_t>(C, 1), nsp));
+    int64_t cps = std::max<int64_t>(1, ceil_div(std::max<int64_t>(C, 1), nsp));
     nsp = std::max<int64_t>(1, ceil_div(std::max<int64_t>(C, 1), cps));
+    if (an.n_seg() > 1) {  // one split per segment, written separately
+      nsp = an.n_seg();
+      cps = C / nsp;
+    }
     p.n_row_blocks = nrb;
     p.n_splits = nsp;
     p.units_per_col = cps;
     L->grid = (int)(nrb * nsp);
-    L->partial_bytes = (nsp > 1) ? (size_t)(nsp * R * ab) : 0;
+    L->partial_bytes = (nsp > 1 && an.n_seg() == 1) ? (size_t)(nsp * R * ab) : 0;
     L->tickets = (size_t)nrb;
   } else if (ch.fam == cg::F_TILE) {
     // tilev tiles are 32 x vec rows tall; the scalar tile kernel's 32
@@ -272,15 +276,19 @@ void shape_launch(coot_ctx* ctx, const cg::Analysis& an, const cg::Choice& ch, c
       const int64_t nrb = std::max<int64_t>(1, ceil_div(R, (int64_t)block * k.vec));
       int64_t nseg = split > 0 ? split : ceil_div(2 * resident, nrb);
       nseg = std::max<int64_t>(1, std::min(nseg, std::max<int64_t>(C, 1)));
-      const int64_t cps = std::max<int64_t>(1, ceil_div(std::max<int64_t>(C, 1), nseg));
+      int64_t cps = std::max<int64_t>(1, ceil_div(std::max<int64_t>(C, 1), nseg));
       nseg = std::max<int64_t>(1, ceil_div(std::max<int64_t>(C, 1), cps));
+      if (an.n_seg() > 1) {  // a Cube's slices: independent scans, no totals pass
+        nseg = an.n_seg();
+        cps = C / nseg;
+      }
       p.n_row_blocks = nrb;
       p.n_splits = nseg;
       p.units_per_col = cps;
       L->grid = (int)(nrb * nseg);
       L->partial_bytes = (nseg > 1) ? (size_t)(nseg * R * ab8) : 0;
     }
-    if (p.n_splits > 1) {
+    if (p.n_splits > 1 && an.n_seg() == 1) {
       std::string pre = k.name;
       pre.replace(pre.find("coot_scan_"), 10, "coot_scan_t_");
       L->kname_pre = pre;
@@ -469,12 +477,13 @@ static coot_status run_fused(coot_ctx* ctx, const cg::Analysis& an, const coot_m
   p.out_ld = out ? mat_ld(*out) : 0;
   p.out_rs = an.out_rs;
   // elements per reduction output
-  const int64_t per = (an.red.dim == 0) ? an.nr : (an.red.dim == 1 ? an.nc : count);
+  const int64_t per = (an.red.dim == 0) ? an.nr : (an.red.dim == 1 ? an.nc / an.n_seg() : count);
   p.count = per;
   p.div = 1.0;
   if (an.red.kind == COOT_R_MEAN) p.div = (double)per;
   p.den = (an.red.norm_type == 1) ? (double)per : (double)(per - 1);
   p.flags = (an.red.kind == COOT_R_STDDEV) ? cg::PF_SQRT : 0u;
+  if (an.n_seg() > 1) p.flags |= cg::PF_SEGMENTED;
   p.red_out = red_out;
 
   // launch configuration: tuned, else the default variant at full occupancy

@@ -18,6 +18,7 @@ namespace cg {
 
 using coot::Params;
 using coot::PF_SQRT;
+using coot::PF_SEGMENTED;
 
 using coot::RED_NONE;
 using coot::RED_SUM;
@@ -92,9 +93,11 @@ struct Analysis {
   int acc_bytes() const { return (red_mode == RED_NONE || red_additive(red_mode)) ? 8 : 16; }
   // number of values the reduction writes (a vector along dim 0/1 may be empty)
   bool scan() const { return red.kind == COOT_R_CUMSUM; }
+  // dim-1 segments (a Cube's slices side by side): 1 = the whole row
+  int64_t n_seg() const { return red.n_seg > 1 ? red.n_seg : 1; }
   int64_t n_outputs() const {
     if (red.kind == COOT_R_NONE || red.kind == COOT_R_CUMSUM) return 0;
-    return red.dim == 0 ? nc : (red.dim == 1 ? nr : 1);
+    return red.dim == 0 ? nc : (red.dim == 1 ? nr * n_seg() : 1);
   }
 };
 

@@ -392,12 +392,15 @@ __device__ __forceinline__ void row_kernel(const Params& p) {
   const long long j0 = sp * cps;
   const long long j1 = (j0 + cps < nc) ? j0 + cps : nc;
   const bool fullv = (i + V <= nr);
+  // segmented (a Cube's slices side by side): split sp is output column sp
+  const bool segd = (p.flags & PF_SEGMENTED) != 0;
+  const long long o0 = segd ? sp * nr : 0, pbase = segd ? j0 : 0;
   A acc[V];
   typename CsqOf<C>::type csq[V];  // var along dim 1: one mean per row
 #pragma unroll
   for (int l = 0; l < V; ++l) {
     acc[l].init();
-    if constexpr (RED == RED_CSQ) csq[l].set_mean(i + l < nr ? p.mu[i + l] : 0.0);
+    if constexpr (RED == RED_CSQ) csq[l].set_mean(i + l < nr ? p.mu[o0 + i + l] : 0.0);
   }
   if (i < nr) {
     for (long long jb = j0; jb < j1; jb += U) {
@@ -425,13 +428,13 @@ __device__ __forceinline__ void row_kernel(const Params& p) {
           if (fullv) {
             C y[V];
 #pragma unroll
-            for (int l = 0; l < V; ++l) y[l] = eval_elem<T, RED>(x[g], k, err, l, acc[l], csq[l], j);
+            for (int l = 0; l < V; ++l) y[l] = eval_elem<T, RED>(x[g], k, err, l, acc[l], csq[l], j - pbase);
             if constexpr (OUT) store_rows<S, V>(p, i, j, y);
           } else {
 #pragma unroll
             for (int l = 0; l < V; ++l)
               if (i + l < nr) {
-                C y = eval_elem<T, RED>(x[g], k, err, l, acc[l], csq[l], j);
+                C y = eval_elem<T, RED>(x[g], k, err, l, acc[l], csq[l], j - pbase);
                 if constexpr (OUT) IO<S>::store1(at_out_g<S>(p, i + l, j), y);
               }
           }
@@ -440,10 +443,10 @@ __device__ __forceinline__ void row_kernel(const Params& p) {
     }
   }
   if (err) atomicOr(p.err_flag, err);
-  if (nsp == 1) {
+  if (nsp == 1 || segd) {
 #pragma unroll
     for (int l = 0; l < V; ++l)
-      if (i + l < nr) write_result<C, RED>(p, acc[l], i + l, p.div);
+      if (i + l < nr) write_result<C, RED>(p, acc[l], o0 + i + l, p.div);
     return;
   }
 #pragma unroll
@@ -1096,7 +1099,7 @@ __device__ __forceinline__ void scan_row_kernel(const Params& p) {
   for (int l = 0; l < V; ++l) {
     run[l].init();
     if constexpr (PASS == 2)
-      if (i + l < nr)
+      if (i + l < nr && !(p.flags & PF_SEGMENTED))
         for (long long q = 0; q < sg; ++q) run[l].add(load_cg(&((const A*)p.partials)[q * nr + i + l]));
   }
   for (long long jb = j0; jb < j1; jb += U) {

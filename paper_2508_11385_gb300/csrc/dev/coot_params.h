@@ -30,7 +30,11 @@ COOT_HD constexpr bool red_additive(int r) { return r >= RED_SUM && r <= RED_CSQ
 COOT_HD constexpr bool red_extreme(int r) { return r >= RED_MIN && r <= RED_IMAX; }
 
 // Params::flags
-enum { PF_SQRT = 1u };
+//   PF_SQRT       var's second pass writes the square root (stddev)
+//   PF_SEGMENTED  dim-1 reduction / scan: every column split is its own
+//                 segment (no combine across splits; output i + split * n_rows;
+//                 positions relative to the segment)
+enum { PF_SQRT = 1u, PF_SEGMENTED = 2u };
 
 struct Params {
   // leaf reads ("slots"): device address of element (0,0) of the view read
@@ -59,7 +63,7 @@ struct Params {
   long long count;
   double div;  // mean: count (or length along dim); sum: 1
   double den;  // var: N-1 or N
-  unsigned int flags;  // PF_SQRT: var's second pass writes the square root (stddev)
+  unsigned int flags;  // PF_*
   // reduction result (device) and workspace
   void* red_out;
   void* partials;

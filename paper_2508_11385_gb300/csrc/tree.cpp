@@ -252,6 +252,15 @@ coot_status analyse(const coot_tree* tree, const coot_mat* leaves, int32_t n_lea
   if (is_int && (red.kind == COOT_R_MEAN || red.kind == COOT_R_NORM2 || red.kind == COOT_R_NORM_FRO ||
                  red.kind == COOT_R_VAR || red.kind == COOT_R_STDDEV))
     return set_error(COOT_ERR_DTYPE, "mean/norm/var/stddev are not defined for INT32 trees");
+  if (red.n_seg < 0) return set_error(COOT_ERR_INVALID, "n_seg %d is negative", red.n_seg);
+  if (red.n_seg > 1) {
+    const bool along_rows = an->red.dim == 1 && red.kind != COOT_R_ACCU && red.kind != COOT_R_DOT &&
+                            red.kind != COOT_R_NORM2 && red.kind != COOT_R_NORM_FRO && red.kind != COOT_R_NONE;
+    if (!along_rows) return set_error(COOT_ERR_INVALID, "n_seg > 1 segments a reduction or cumsum along dim 1");
+    if (an->nc % red.n_seg)
+      return set_error(COOT_ERR_SHAPE, "n_seg %d does not divide the %lld columns", red.n_seg, (long long)an->nc);
+  }
+  an->red.n_seg = red.n_seg > 1 ? red.n_seg : 1;
 
   // ---- canonical form: push trans(), each_col / each_row and diag() down to
   // the leaf reads.  The state carried down is the affine map from the root's
@@ -360,6 +369,8 @@ coot_status analyse(const coot_tree* tree, const coot_mat* leaves, int32_t n_lea
     }
     if (an->slots[s].gen) an->gmask |= (1 << s);
   }
+  if (an->n_seg() > 1 && an->any_trans && !an->scan())
+    return set_error(COOT_ERR_UNSUPPORTED, "segmented reductions of trees with transposed reads are not implemented");
 
   // ---- C++ type of the canonical tree
   std::function<std::string(int)> spell = [&](int i) -> std::string {

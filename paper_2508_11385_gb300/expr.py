@@ -341,22 +341,32 @@ def trans(x):
 
 
 def exp(x):
+    if hasattr(x, "_cube_unary"):
+        return x._cube_unary(L.N_EXP)
     return Expr(L.N_EXP, (_as_expr(x),))
 
 
 def log(x):
+    if hasattr(x, "_cube_unary"):
+        return x._cube_unary(L.N_LOG)
     return Expr(L.N_LOG, (_as_expr(x),))
 
 
 def abs(x):  # noqa: A001 -- Armadillo's name
+    if hasattr(x, "_cube_unary"):
+        return x._cube_unary(L.N_ABS)
     return Expr(L.N_ABS, (_as_expr(x),))
 
 
 def square(x):
+    if hasattr(x, "_cube_unary"):
+        return x._cube_unary(L.N_SQUARE)
     return Expr(L.N_SQUARE, (_as_expr(x),))
 
 
 def sqrt(x):
+    if hasattr(x, "_cube_unary"):
+        return x._cube_unary(L.N_SQRT)
     return Expr(L.N_SQRT, (_as_expr(x),))
 
 
@@ -416,8 +426,9 @@ class Reduction:
     expression), or combined linearly first: ``accu(a) + k * accu(b)`` is
     evaluated as ``accu(a + k * b)`` in one pass."""
 
-    def __init__(self, kind, expr, dim=-1, norm_type=0):
+    def __init__(self, kind, expr, dim=-1, norm_type=0, n_seg=0):
         self.kind, self.expr, self.dim, self.norm_type = kind, expr, dim, norm_type
+        self.n_seg = n_seg  # dim 1: equal column segments reduced separately (a Cube's slices)
 
     def _linear(self):
         return self.kind in (L.R_ACCU, L.R_SUM) and self.dim == -1
@@ -448,12 +459,16 @@ class Reduction:
 
 
 def accu(x):
+    if hasattr(x, "_cube_reduce"):
+        return x._cube_reduce(L.R_ACCU, -1, 0)
     return Reduction(L.R_ACCU, _as_expr(x))
 
 
 def sum(x, dim=None):  # noqa: A001 -- Armadillo's name
     """Armadillo sum: along dim 0 (per column) for a matrix by default, all
     elements for a vector; dim=-1 sums everything."""
+    if hasattr(x, "_cube_reduce"):
+        return x._cube_reduce(L.R_SUM, 0 if dim is None else dim, 0)
     x = _as_expr(x)
     if dim is None:
         dim = -1 if (x.n_rows == 1 or x.n_cols == 1) else 0
@@ -461,6 +476,8 @@ def sum(x, dim=None):  # noqa: A001 -- Armadillo's name
 
 
 def mean(x, dim=None):
+    if hasattr(x, "_cube_reduce"):
+        return x._cube_reduce(L.R_MEAN, 0 if dim is None else dim, 0)
     x = _as_expr(x)
     if dim is None:
         dim = -1 if (x.n_rows == 1 or x.n_cols == 1) else 0
@@ -495,12 +512,16 @@ def _along(x, dim):
 def var(x, norm_type=0, dim=-1):
     """Two-pass variance (norm_type 0: N-1, 1: N) over all elements (dim -1,
     the default), per column (dim 0) or per row (dim 1)."""
+    if hasattr(x, "_cube_reduce"):
+        return x._cube_reduce(L.R_VAR, dim, norm_type)
     x, dim = _along(x, dim)
     return Reduction(L.R_VAR, x, dim, norm_type)
 
 
 def stddev(x, norm_type=0, dim=-1):
     """Square root of ``var`` with the same arguments."""
+    if hasattr(x, "_cube_reduce"):
+        return x._cube_reduce(L.R_STDDEV, dim, norm_type)
     x, dim = _along(x, dim)
     return Reduction(L.R_STDDEV, x, dim, norm_type)
 
@@ -508,12 +529,16 @@ def stddev(x, norm_type=0, dim=-1):
 def min(x, dim=None):  # noqa: A001 -- Armadillo's name
     """Smallest element (NaN skipped): per column for a matrix by default, all
     elements for a vector; dim -1 over everything, 0 per column, 1 per row."""
+    if hasattr(x, "_cube_reduce"):
+        return x._cube_reduce(L.R_MIN, 0 if dim is None else dim, 0)
     x, dim = _along(x, dim)
     return Reduction(L.R_MIN, x, dim)
 
 
 def max(x, dim=None):  # noqa: A001 -- Armadillo's name
     """Largest element, as ``min``."""
+    if hasattr(x, "_cube_reduce"):
+        return x._cube_reduce(L.R_MAX, 0 if dim is None else dim, 0)
     x, dim = _along(x, dim)
     return Reduction(L.R_MAX, x, dim)
 
@@ -522,12 +547,16 @@ def index_min(x, dim=None):
     """Position (int64) of the first smallest element: the column-major linear
     index for dim -1, the row index per column (dim 0), the column index per
     row (dim 1); -1 where there is none.  Defaults as ``min``."""
+    if hasattr(x, "_cube_reduce"):
+        return x._cube_reduce(L.R_INDEX_MIN, 0 if dim is None else dim, 0)
     x, dim = _along(x, dim)
     return Reduction(L.R_INDEX_MIN, x, dim)
 
 
 def index_max(x, dim=None):
     """Position of the first largest element, as ``index_min``."""
+    if hasattr(x, "_cube_reduce"):
+        return x._cube_reduce(L.R_INDEX_MAX, 0 if dim is None else dim, 0)
     x, dim = _along(x, dim)
     return Reduction(L.R_INDEX_MAX, x, dim)
 
@@ -536,6 +565,8 @@ def cumsum(x, dim=None):
     """Prefix sums with the expression's shape: down each column (dim 0, the
     default for a matrix), along each row (dim 1); along the vector for a
     vector.  ``cumsum(e).eval()`` returns the matrix."""
+    if hasattr(x, "_cube_reduce"):
+        return x._cube_reduce(L.R_CUMSUM, 0 if dim is None else dim, 0)
     x = _as_expr(x)
     if dim is None:
         dim = 1 if x.n_rows == 1 else 0
@@ -547,6 +578,8 @@ def cumsum(x, dim=None):
 def prod(x, dim=None):
     """Product of the elements, defaults as ``min``; no intermediate
     overflow or underflow, the result is rounded to the accumulation type."""
+    if hasattr(x, "_cube_reduce"):
+        return x._cube_reduce(L.R_PROD, 0 if dim is None else dim, 0)
     x, dim = _along(x, dim)
     return Reduction(L.R_PROD, x, dim)
 
@@ -604,7 +637,7 @@ def evaluate(expr, out=None, reduction=None, red_out=None, fused=True, stream=No
             out = materialise
         if out is None:
             out = _empty_colmajor(nr, nc, dt, dev)
-        red = L.reduce(reduction.kind, reduction.dim, reduction.norm_type)
+        red = L.reduce(reduction.kind, reduction.dim, reduction.norm_type, reduction.n_seg)
         with torch.cuda.device(dev):
             ctx = context(dev)
             fn = L.coot_eval if fused else L.coot_eval_unfused
@@ -619,11 +652,13 @@ def evaluate(expr, out=None, reduction=None, red_out=None, fused=True, stream=No
     red = L.reduce()
     rt = None
     if reduction is not None:
-        red = L.reduce(reduction.kind, reduction.dim, reduction.norm_type)
+        red = L.reduce(reduction.kind, reduction.dim, reduction.norm_type, reduction.n_seg)
         if red_out is None:
             acc = torch.int64 if reduction.kind in (L.R_INDEX_MIN, L.R_INDEX_MAX) else _ACC[dt]
             if reduction.dim == 0:
                 rt = torch.empty((1, nc), dtype=acc, device=dev)  # a row vector: contiguous either way
+            elif reduction.dim == 1 and reduction.n_seg > 1:
+                rt = torch.empty((reduction.n_seg, nr), dtype=acc, device=dev).t()  # segment s in column s
             elif reduction.dim == 1:
                 rt = torch.empty((nr, 1), dtype=acc, device=dev)
             else:
@@ -644,7 +679,8 @@ def warmup(expr, reduction=None, out=None):
     """JIT-compile (and tune, when enabled) the kernel of an evaluation."""
     expr = _as_expr(expr)
     tree, leaves, cmats = lower(expr)
-    red = L.reduce() if reduction is None else L.reduce(reduction.kind, reduction.dim, reduction.norm_type)
+    red = L.reduce() if reduction is None else L.reduce(reduction.kind, reduction.dim, reduction.norm_type,
+                                                        reduction.n_seg)
     dev = leaves[0].tensor.device
     if out is None and reduction is not None and reduction.kind == L.R_CUMSUM:
         out = _empty_colmajor(expr.n_rows, expr.n_cols, leaves[0].dtype, dev)  # a scan needs its output
@@ -656,7 +692,8 @@ def warmup(expr, reduction=None, out=None):
 def signature(expr, reduction=None, out=None) -> str:
     expr = _as_expr(expr)
     tree, leaves, cmats = lower(expr)
-    red = L.reduce() if reduction is None else L.reduce(reduction.kind, reduction.dim, reduction.norm_type)
+    red = L.reduce() if reduction is None else L.reduce(reduction.kind, reduction.dim, reduction.norm_type,
+                                                        reduction.n_seg)
     out_m = _out_cmat(out) if out is not None else None
     return L.coot_signature(tree, cmats, out_m, red)
 

@@ -52,7 +52,7 @@ class coot_tree(ctypes.Structure):
 
 class coot_reduce(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("dim", ctypes.c_int32), ("norm_type", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("n_seg", ctypes.c_int32)]
 
 
 class coot_launch_info(ctypes.Structure):
@@ -265,8 +265,8 @@ def node(op, a=-1, b=-1, leaf=0, k=0.0, r0=0, c0=0, nr=0, nc=0):
     return coot_node(op, a, b, leaf, k, r0, c0, nr, nc)
 
 
-def reduce(kind=R_NONE, dim=-1, norm_type=0):
-    return coot_reduce(kind, dim, norm_type, 0)
+def reduce(kind=R_NONE, dim=-1, norm_type=0, n_seg=0):
+    return coot_reduce(kind, dim, norm_type, n_seg)
 
 
 def mat(ptr, dtype, n_rows, n_cols, ld=None, rs=0):
