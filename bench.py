@@ -625,7 +625,52 @@ def bench_stats(args, dev, stream, peak=None):
         gbs = info["algorithmic_bytes"] / ms / 1e6
         out[name] = {"ms": round(ms, 4), "gbs": round(gbs, 1), "frac": round(gbs / peak, 3),
                      "kernel": info["kernel"], "launches": info["n_launches"]}
-    del lv
+    del lv, bv
+    torch.cuda.empty_cache()
+    # cubes: 512 x 512 x 256 FP32 (256 MiB each), reductions within and across
+    # slices, each a prepared C-ABI call on the cube's matrix re-view
+    import paper_2508_11385_gb300 as coot
+    from paper_2508_11385_gb300 import expr as E
+    from paper_2508_11385_gb300 import lib as L
+
+    g = workloads.generator(7, dev)
+    cq = [coot.cube_empty(512, 512, 256, torch.float32, dev) for _ in range(2)]
+    for t in cq:
+        t.copy_(torch.randn(t.shape, generator=g, device=dev))
+    Q, R = coot.Cube(cq[0]), coot.Cube(cq[1])
+    cube_b = 2 * cq[0].numel() * 4
+    ctx = E.context(dev)
+    for name, mode, dim, nseg, nout in (("cube sum(Q%R, 0)", "cols", 0, 0, 512 * 256),
+                                        ("cube sum(Q%R, 1) per slice", "cols", 1, 256, 512 * 256),
+                                        ("cube sum(Q%R, 2) across slices", "elems", 1, 0, 512 * 512)):
+        e = Q.to_expr(mode) % R.to_expr(mode)
+        tree, _, cm = E.lower(e)
+        red = L.reduce(L.R_SUM, dim, 0, nseg)
+        res = torch.empty(nout, dtype=torch.float32, device=dev)
+        fn = lambda: L.coot_eval(ctx, tree, cm, None, red, res.data_ptr(), sp)
+        fn()
+        torch.cuda.synchronize()
+        ms = time_calls(fn, stream, reps=10)
+        info = L.coot_last_launch(ctx)
+        gbs = info["algorithmic_bytes"] / ms / 1e6
+        out[name] = {"ms": round(ms, 4), "gbs": round(gbs, 1), "frac": round(gbs / peak, 3), "kernel": info["kernel"]}
+    # each_slice: 256 problems of one persistent batch kernel
+    e0 = Q.slice(0) % R.slice(0)
+    tree, _, _ = E.lower(e0)
+    probs = (L.coot_mat * 512)()
+    for q in range(256):
+        probs[2 * q] = E.Mat(cq[0][:, :, q]).cmat()
+        probs[2 * q + 1] = E.Mat(cq[1][:, :, q]).cmat()
+    plan = L.coot_batch_create(ctx, tree, 256, 2, probs, None, L.reduce(L.R_ACCU))
+    res = torch.empty(256, dtype=torch.float32, device=dev)
+    fn = lambda: L.coot_batch_run(plan, res.data_ptr(), sp)
+    fn()
+    torch.cuda.synchronize()
+    ms = time_calls(fn, stream, reps=10)
+    gbs = (cube_b + 256 * 4) / ms / 1e6
+    out["cube each_slice accu(Q%R), batched"] = {"ms": round(ms, 4), "gbs": round(gbs, 1), "frac": round(gbs / peak, 3)}
+    L.coot_batch_destroy(plan)
+    del cq, Q, R
     torch.cuda.empty_cache()
     return out
 

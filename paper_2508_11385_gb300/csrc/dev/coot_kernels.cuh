@@ -65,8 +65,14 @@ template <class S, int V, class C>
 __device__ __forceinline__ void load_rows(const Params& p, int s, long long i, long long j, C (&v)[V]) {
   if (gen_slot(s)) {
     const S* b = at_slot<S>(p, s, i, j);
+    if (p.rs[s] == 0) {  // a row broadcast: one element for all V rows
+      const C x = IO<S>::load1(b);
 #pragma unroll
-    for (int l = 0; l < V; ++l) v[l] = IO<S>::load1(b + l * p.rs[s]);
+      for (int l = 0; l < V; ++l) v[l] = x;
+    } else {
+#pragma unroll
+      for (int l = 0; l < V; ++l) v[l] = IO<S>::load1(b + l * p.rs[s]);
+    }
   } else {
     IO<S>::template load<V>(at<S>(p.src[s], i, j, p.ld[s]), v);
   }
