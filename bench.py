@@ -493,12 +493,16 @@ def time_calls(fn, stream, reps=10, warm=2):
 def run_e2e(calls, leaves, stream, reps, dev):
     import torch
 
-    host = [t.cpu().pin_memory() for t in leaves]  # same column-major layout: (n,n) transposed views
-    # pinned outputs per tree
+    # column-major device matrices are transposes of contiguous buffers: copy
+    # the buffers whole (one cudaMemcpyAsync each, pinned host memory)
+    def dense(t):
+        return t.t() if t.dim() == 2 and t.t().is_contiguous() else t
+
+    host = [dense(t).cpu().pin_memory() for t in leaves]
     h_out = {}
     for name, _, _, c in calls:
-        r = c.result()
-        h_out[name] = torch.empty(r.shape, dtype=r.dtype).pin_memory() if r.dim() else torch.empty((), dtype=r.dtype).pin_memory()
+        r = dense(c.result())
+        h_out[name] = torch.empty(r.shape, dtype=r.dtype).pin_memory()
     bytes_alg = 0
     h2d = d2h = 0
     sp = stream.cuda_stream
@@ -512,10 +516,10 @@ def run_e2e(calls, leaves, stream, reps, dev):
     for _ in range(reps):
         for name, _, _, c in calls:
             for li in name_to_leaf[name]:
-                leaves[li].copy_(host[li], non_blocking=True)
+                dense(leaves[li]).copy_(host[li], non_blocking=True)
                 h2d += host[li].numel() * host[li].element_size()
             c(sp)
-            r = c.result()
+            r = dense(c.result())
             h_out[name].copy_(r, non_blocking=True)
             d2h += r.numel() * r.element_size()
             bytes_alg += c.info()["algorithmic_bytes"]
