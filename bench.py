@@ -474,19 +474,23 @@ def headers_sha():
 
 
 def time_calls(fn, stream, reps=10, warm=2):
+    """Device time of one call: `reps` calls enqueued back to back between two
+    events (the host prepares call k+1 while the GPU runs call k, so host
+    overhead is not counted), averaged; the median of three such batches."""
     import torch
 
     for _ in range(warm):
         fn()
     torch.cuda.synchronize()
     ts = []
-    for _ in range(reps):
+    for _ in range(3):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        fn()
+        for _ in range(reps):
+            fn()
         b.record(stream)
         torch.cuda.synchronize()
-        ts.append(a.elapsed_time(b))
+        ts.append(a.elapsed_time(b) / reps)
     return statistics.median(ts)
 
 
@@ -724,7 +728,7 @@ def bench_batched(args, dev, stream):
         for cm, om in sep:
             L.coot_eval(ctx, tree, cm, om, L.reduce(L.R_ACCU), r1.data_ptr(), sp)
 
-    sep_ms = time_calls(separate, stream, reps=3, warm=1) * npb / nsep
+    sep_ms = time_calls(separate, stream, reps=1, warm=1) * npb / nsep
     L.coot_batch_destroy(plan)
     total_elems = int((rows * cols).sum())
     return {"n_problems": npb, "elements": total_elems, "ms": round(ms, 4),
