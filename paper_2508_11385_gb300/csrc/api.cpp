@@ -401,7 +401,7 @@ std::string tune_key(const cg::Program& pg, const cg::Choice& ch) {
 // run one analysed fused evaluation (warm: compile + tune without launching)
 // ---------------------------------------------------------------------------
 static coot_status run_fused(coot_ctx* ctx, const cg::Analysis& an, const coot_mat* leaves, const coot_mat* out,
-                             void* red_out, cudaStream_t stream, bool warm_only) {
+                             void* red_out, cudaStream_t stream, bool warm_only, cg::CallPlan* plan = nullptr) {
   if (an.scan() && an.any_trans) {
     // a tree with transposed reads is first materialised into out by the
     // tile kernel, then scanned in place (out read and written by the same
@@ -427,7 +427,8 @@ static coot_status run_fused(coot_ctx* ctx, const cg::Analysis& an, const coot_m
     return COOT_OK;
   }
   const bool var = an.two_pass();
-  cg::Choice ch = cg::choose(an, leaves, out);
+  const bool hit = plan && plan->m;  // prepared by an earlier call with the same inputs
+  cg::Choice ch = hit ? plan->ch : cg::choose(an, leaves, out);
   const int64_t count = an.nr * an.nc;
   if (!warm_only && count == 0 && an.red.kind != COOT_R_PROD) {
     // nothing to read: reductions of no elements.  All-ones bytes are a NaN
@@ -454,12 +455,23 @@ static coot_status run_fused(coot_ctx* ctx, const cg::Analysis& an, const coot_m
     ch.it_rows = an.nr;
     ch.it_cols = an.nc;
   }
-  cg::Program pg = cg::make_program(an, ch.fam, var);
-  if (!ctx->mods.count(pg.signature) && capturing(stream))
+  cg::Program fresh;
+  if (!hit) fresh = cg::make_program(an, ch.fam, var);
+  const cg::Program& pg = hit ? plan->pg : fresh;
+  if (!hit && !ctx->mods.count(pg.signature) && capturing(stream))
     return set_error(COOT_ERR_INVALID, "this tree's kernel is not compiled yet; call coot_warmup before capturing");
-  cg::Module* m = nullptr;
-  coot_status s = coot_get_module(ctx, pg, &m);
-  if (s) return s;
+  cg::Module* m = hit ? plan->m : nullptr;
+  coot_status s = COOT_OK;
+  if (!hit) {
+    s = coot_get_module(ctx, pg, &m);
+    if (s) return s;
+    if (plan) {
+      plan->ch = ch;
+      plan->pg.signature = pg.signature;
+      plan->pg.kernels = pg.kernels;
+      plan->m = m;
+    }
+  }
 
   Launch L;
   cg::Params& p = L.p;
@@ -486,24 +498,33 @@ static coot_status run_fused(coot_ctx* ctx, const cg::Analysis& an, const coot_m
   if (an.n_seg() > 1) p.flags |= cg::PF_SEGMENTED;
   p.red_out = red_out;
 
-  // launch configuration: tuned, else the default variant at full occupancy
-  std::string key = tune_key(pg, ch);
+  // launch configuration: the call plan's, else tuned, else the default
+  // variant at full occupancy
   cg::LaunchCfg cfg;
-  auto tu = ctx->tuned.find(key);
-  if (tu != ctx->tuned.end() && tu->second.kidx >= 0 && tu->second.kidx < (int)pg.kernels.size() &&
-      (ch.vec_ok || pg.kernels[tu->second.kidx].vec == 1)) {
-    cfg = tu->second;
+  if (hit && plan->have_cfg) {
+    cfg = plan->cfg;
   } else {
-    cfg.kidx = default_variant(pg, ch);
-    cfg.block = pg.kernels[cfg.kidx].block;
-    if (ch.fam == cg::F_ROW) cfg.block = 256;
-    cfg.blocks_per_sm = occupancy(m, pg.kernels[cfg.kidx].name, cfg.block);
-    if ((ctx->flags & COOT_CTX_TUNE) && !capturing(stream) && count > 0) {
-      Launch base = L;
-      s = tune(ctx, an, ch, pg, m, base, stream, &cfg);
-      if (s) return s;
-      ctx->tuned[key] = cfg;
-      save_tuning(ctx, key, cfg);
+    const std::string key = tune_key(pg, ch);
+    auto tu = ctx->tuned.find(key);
+    if (tu != ctx->tuned.end() && tu->second.kidx >= 0 && tu->second.kidx < (int)pg.kernels.size() &&
+        (ch.vec_ok || pg.kernels[tu->second.kidx].vec == 1)) {
+      cfg = tu->second;
+    } else {
+      cfg.kidx = default_variant(pg, ch);
+      cfg.block = pg.kernels[cfg.kidx].block;
+      if (ch.fam == cg::F_ROW) cfg.block = 256;
+      cfg.blocks_per_sm = occupancy(m, pg.kernels[cfg.kidx].name, cfg.block);
+      if ((ctx->flags & COOT_CTX_TUNE) && !capturing(stream) && count > 0) {
+        Launch base = L;
+        s = tune(ctx, an, ch, pg, m, base, stream, &cfg);
+        if (s) return s;
+        ctx->tuned[key] = cfg;
+        save_tuning(ctx, key, cfg);
+      }
+    }
+    if (plan && !capturing(stream)) {
+      plan->cfg = cfg;
+      plan->have_cfg = true;
     }
   }
   const cg::KernelSpec& ks = pg.kernels[cfg.kidx];
@@ -697,17 +718,72 @@ extern "C" coot_status coot_ctx_destroy(coot_ctx* ctx) {
 // ---------------------------------------------------------------------------
 // fused evaluation
 // ---------------------------------------------------------------------------
+// call-cache key: every input a fused call's preparation depends on, except
+// the data pointers themselves (only their 16-byte alignment and whether they
+// are NULL)
+static void call_key(const coot_tree* tree, const coot_mat* leaves, int32_t n_leaves, const coot_mat* out,
+                     coot_reduce red, std::string* key) {
+  key->clear();
+  auto put = [&](const void* p, size_t n) { key->append((const char*)p, n); };
+  put(&tree->n_nodes, sizeof tree->n_nodes);
+  put(tree->nodes, sizeof(coot_node) * (size_t)tree->n_nodes);
+  put(&n_leaves, sizeof n_leaves);
+  auto mat = [&](const coot_mat& m) {
+    put(&m.dtype, sizeof m.dtype);
+    put(&m.rs, sizeof m.rs);
+    put(&m.n_rows, sizeof m.n_rows);
+    put(&m.n_cols, sizeof m.n_cols);
+    put(&m.ld, sizeof m.ld);
+    const unsigned char a = (unsigned char)(((uintptr_t)m.data & 15u) | (m.data ? 0u : 16u));
+    put(&a, 1);
+  };
+  for (int32_t i = 0; i < n_leaves; ++i) mat(leaves[i]);
+  const unsigned char has_out = out ? 1 : 0;
+  put(&has_out, 1);
+  if (out) mat(*out);
+  put(&red, sizeof red);
+  const char* am = getenv("COOT_ACCUM");  // part of the analysis of FP32 trees
+  const unsigned char acc = !am ? 0 : (!strcmp(am, "kahan") ? 1 : (!strcmp(am, "plain") ? 2 : 0));
+  put(&acc, 1);
+}
+
 extern "C" coot_status coot_eval(coot_ctx* ctx, const coot_tree* tree, const coot_mat* leaves, int32_t n_leaves,
                                  const coot_mat* out, coot_reduce red, void* red_out, coot_stream stream) {
   if (!ctx) return set_error(COOT_ERR_INVALID, "ctx is NULL");
+  const bool keyable = tree && tree->nodes && tree->n_nodes >= 1 && tree->n_nodes <= COOT_MAX_NODES && leaves &&
+                       n_leaves >= 1 && n_leaves <= COOT_MAX_LEAVES;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  thread_local std::string key;
+  if (keyable) {
+    call_key(tree, leaves, n_leaves, out, red, &key);
+    auto it = ctx->plans.find(key);
+    if (it != ctx->plans.end()) {
+      // prepared before: only the checks that depend on the pointers remain
+      cg::CallPlan* pl = it->second.get();
+      if (red.kind != COOT_R_NONE && !red_out && n_red_outputs(pl->an) > 0)
+        return set_error(COOT_ERR_INVALID, "red_out is NULL");
+      coot_status s = cg::check_out_alias(pl->an, leaves, out);
+      if (s) return s;
+      DeviceGuard g(ctx->device);
+      return run_fused(ctx, pl->an, leaves, out, red_out, (cudaStream_t)stream, false, pl);
+    }
+  }
   cg::Analysis an;
   coot_status s = cg::analyse(tree, leaves, n_leaves, out, red, &an);
   if (s) return s;
   if (red.kind != COOT_R_NONE && !red_out && n_red_outputs(an) > 0) return set_error(COOT_ERR_INVALID, "red_out is NULL");
   if (red.kind == COOT_R_NONE && !out) return set_error(COOT_ERR_INVALID, "neither out nor a reduction requested");
-  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
   DeviceGuard g(ctx->device);
-  return run_fused(ctx, an, leaves, out, red_out, (cudaStream_t)stream, false);
+  // the empty and the two-step (scan of a transposed tree) paths stay uncached
+  const bool cacheable = keyable && an.nr * an.nc > 0 && !(an.scan() && an.any_trans);
+  if (!cacheable) return run_fused(ctx, an, leaves, out, red_out, (cudaStream_t)stream, false);
+  std::unique_ptr<cg::CallPlan> pl(new cg::CallPlan());
+  pl->an = an;
+  s = run_fused(ctx, pl->an, leaves, out, red_out, (cudaStream_t)stream, false, pl.get());
+  if (s) return s;
+  if (ctx->plans.size() >= 4096) ctx->plans.clear();  // bounded: a workload of many shapes rebuilds plans
+  ctx->plans.emplace(key, std::move(pl));
+  return COOT_OK;
 }
 
 extern "C" coot_status coot_warmup(coot_ctx* ctx, const coot_tree* tree, const coot_mat* leaves, int32_t n_leaves,

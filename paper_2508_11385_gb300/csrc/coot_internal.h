@@ -106,6 +106,10 @@ struct Analysis {
 coot_status analyse(const coot_tree* tree, const coot_mat* leaves, int32_t n_leaves, const coot_mat* out,
                     coot_reduce red, Analysis* an);
 
+// The aliasing rule of an output (part of analyse; the call cache re-checks
+// it with each call's pointers).
+coot_status check_out_alias(const Analysis& an, const coot_mat* leaves, const coot_mat* out);
+
 // Kernel selection for a fused evaluation.
 struct Choice {
   Family fam = F_STR;
@@ -152,6 +156,17 @@ struct LaunchCfg {
   int split = 0;  // col: warps per column (0: heuristic)
 };
 
+// A fused call prepared once per (tree, layouts, alignment, reduction):
+// analysis, kernel family, program and launch configuration.
+struct CallPlan {
+  Analysis an;
+  Choice ch;
+  Program pg;  // signature and kernel list (the source is dropped once compiled)
+  Module* m = nullptr;
+  bool have_cfg = false;
+  LaunchCfg cfg;
+};
+
 }  // namespace cg
 
 struct coot_ctx {
@@ -173,6 +188,9 @@ struct coot_ctx {
   double* mean_ptr = nullptr;
   void* partials = nullptr;
   coot_launch_info last{};
+  // call cache: everything a fused call derives from the tree, the layouts
+  // and the reduction (not from the data pointers), keyed by those inputs
+  std::unordered_map<std::string, std::unique_ptr<cg::CallPlan>> plans;
 };
 
 struct coot_batch {

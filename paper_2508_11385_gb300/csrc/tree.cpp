@@ -428,28 +428,30 @@ coot_status analyse(const coot_tree* tree, const coot_mat* leaves, int32_t n_lea
     if (!out->data && an->nr * an->nc > 0) return set_error(COOT_ERR_INVALID, "out: NULL data");
     an->out_rs = mat_rs(*out);
     if (an->out_rs != 1 && an->nr > 1) an->gmask |= (1 << COOT_MAX_SLOTS);
-    // aliasing: overlap with a leaf read is allowed only for an identical
-    // read (same elements in the same order: each element is read and
-    // written by one thread)
-    const int64_t ocs = an->nc > 1 ? mat_ld(*out) : 0, ors = an->nr > 1 ? an->out_rs : 0;
-    uintptr_t olo, ohi;
-    strided_range(out->data, 0, an->out_rs, mat_ld(*out), an->nr, an->nc, an->esz, &olo, &ohi);
-    for (const Slot& s : an->slots) {
-      const coot_mat& L = leaves[s.leaf];
-      uintptr_t llo, lhi;
-      if (s.trans)
-        strided_range(L.data, s.off, s.rs, s.cs, an->nr, an->nc, an->esz, &llo, &lhi);
-      else
-        strided_range(L.data, s.off, s.rs, s.cs, an->nr, an->nc, an->esz, &llo, &lhi);
-      if (olo < lhi && llo < ohi) {
-        const uintptr_t vorig = (uintptr_t)L.data + (uintptr_t)(s.off * an->esz);
-        const bool same = !s.trans && vorig == (uintptr_t)out->data && (an->nr <= 1 || s.rs == ors) &&
-                          (an->nc <= 1 || s.cs == ocs);
-        if (!same)
-          return set_error(COOT_ERR_ALIAS,
-                           "out overlaps leaf %d through a %s read; only an identical read may alias", s.leaf,
-                           s.trans ? "transposed" : "differently shaped or strided");
-      }
+    return check_out_alias(*an, leaves, out);
+  }
+  return COOT_OK;
+}
+
+// aliasing: overlap of out with a leaf read is allowed only for an identical
+// read (same elements in the same order: each element is read and written by
+// one thread)
+coot_status check_out_alias(const Analysis& an, const coot_mat* leaves, const coot_mat* out) {
+  if (!out) return COOT_OK;
+  const int64_t ocs = an.nc > 1 ? mat_ld(*out) : 0, ors = an.nr > 1 ? an.out_rs : 0;
+  uintptr_t olo, ohi;
+  strided_range(out->data, 0, an.out_rs, mat_ld(*out), an.nr, an.nc, an.esz, &olo, &ohi);
+  for (const Slot& s : an.slots) {
+    const coot_mat& L = leaves[s.leaf];
+    uintptr_t llo, lhi;
+    strided_range(L.data, s.off, s.rs, s.cs, an.nr, an.nc, an.esz, &llo, &lhi);
+    if (olo < lhi && llo < ohi) {
+      const uintptr_t vorig = (uintptr_t)L.data + (uintptr_t)(s.off * an.esz);
+      const bool same = !s.trans && vorig == (uintptr_t)out->data && (an.nr <= 1 || s.rs == ors) &&
+                        (an.nc <= 1 || s.cs == ocs);
+      if (!same)
+        return set_error(COOT_ERR_ALIAS, "out overlaps leaf %d through a %s read; only an identical read may alias",
+                         s.leaf, s.trans ? "transposed" : "differently shaped or strided");
     }
   }
   return COOT_OK;
