@@ -392,6 +392,47 @@ static int submat(ctx_t* cx, val_t* x, int64_t r0, int64_t c0, int64_t nr, int64
   return 0;
 }
 
+/* Matrix product x * y (Armadillo's operator* between matrices; Sec. 3 maps
+ * trans(X)*Y onto one GEMM call with a transposed operand).  Each output is
+ * the exact dot product rounded once to double (double-double sums of the
+ * products, each product exact in double-double via fma).  Bound: the
+ * operands' bounds propagated (sum of |x_ik| b(y_kj) + |y_kj| b(x_ik) + their
+ * product) plus k u sum |x_ik y_kj|, u the compute type's unit roundoff --
+ * the error bound of a k-term dot product in the compute type in any order of
+ * additions, products rounded or exact.  Floating point only. */
+static int matmul(ctx_t* cx, val_t* x, val_t* y, val_t* out) {
+  if (x->kind != V_MAT || y->kind != V_MAT || x->c != y->r) {
+    snprintf(cx->err, 256, "mm: incompatible matrix dimensions");
+    return -1;
+  }
+  if (cx->is_int) {
+    snprintf(cx->err, 256, "mm is not defined for INT32 trees here");
+    return -1;
+  }
+  const int64_t m = x->r, k = x->c, n = y->c;
+  if (val_alloc(cx, out, m, n)) return -1;
+  const double u = (cx->ct == ORC_F64) ? ldexp(1.0, -53) : ldexp(1.0, -24);
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t i = 0; i < m; ++i) {
+      double sh = 0.0, sl = 0.0, asum = 0.0, bsum = 0.0;
+      for (int64_t t = 0; t < k; ++t) {
+        const double a = x->v[i + t * m], b = y->v[t + j * k];
+        const double p = a * b, pe = fma(a, b, -p);
+        const double s2 = sh + p, bp = s2 - sh;
+        sl += (sh - (s2 - bp)) + (p - bp) + pe;
+        sh = s2;
+        asum += fabs(p);
+        bsum += fabs(a) * y->b[t + j * k] + fabs(b) * x->b[i + t * m] + x->b[i + t * m] * y->b[t + j * k];
+      }
+      double v = sh + sl;
+      double b = bsum + (double)k * u * asum + orc_ulp(v, ORC_F64);
+      clamp_to_range(cx, &v, &b);
+      out->v[i + j * m] = v;
+      out->b[i + j * m] = finite_or_zero_bound(v, b);
+    }
+  return 0;
+}
+
 /* Broadcasting (Armadillo's each_col / each_row operands) and diagonal
  * views (X.diag(k)), Sec. 2: each element of the result is one element of x.
  *   each_col:n  x is r x 1, result r x n, result(i,j) = x(i,0)
@@ -965,6 +1006,16 @@ int orc_eval(const char* program, const orc_mat* leaves, int32_t n_leaves, int32
     {
       long long garg = 0;
       int gop = -1;
+      if (!strcmp(tok, "mm")) {
+        if (sp < 2) goto underflow;
+        val_t out;
+        if (matmul(&cx, &st[sp - 2], &st[sp - 1], &out)) goto done;
+        val_free(&st[sp - 2]);
+        val_free(&st[sp - 1]);
+        st[sp - 2] = out;
+        sp--;
+        continue;
+      }
       if (!strncmp(tok, "each_col:", 9) && sscanf(tok + 9, "%lld", &garg) == 1) gop = G_EACH_COL;
       else if (!strncmp(tok, "each_row:", 9) && sscanf(tok + 9, "%lld", &garg) == 1) gop = G_EACH_ROW;
       else if (!strcmp(tok, "diag")) gop = G_DIAG;

@@ -36,6 +36,7 @@
  *   each_col:n  each_row:n   the column (row) vector on top repeated n times
  *                        (the operand of X.each_col() / X.each_row())
  *   diag  diag:k         diagonal k of the matrix on top as a column vector
+ *   mm                   matrix product of the two matrices on top (x y)
  * Optionally one final reduction token:
  *   accu  sum:0 sum:1  mean mean:0 mean:1  dot (pops two matrices)
  *   norm (vector 2-norm)  norm:fro  var var:1 (norm_type 0 -> N-1, 1 -> N)

@@ -31,6 +31,10 @@ MUTATIONS = [
     ("diag offset direction", "const int64_t kr = arg < 0 ? -arg : 0, kc = arg > 0 ? arg : 0;",
      "const int64_t kc = arg < 0 ? -arg : 0, kr = arg > 0 ? arg : 0;"),
     ("each_row shape", "    r = arg;\n    c = x->c;", "    r = x->c;\n    c = arg;"),
+    ("matmul operand index", "const double a = x->v[i + t * m], b = y->v[t + j * k];",
+     "const double a = x->v[t + i * k], b = y->v[t + j * k];"),
+    ("matmul summation bound", "double b = bsum + (double)k * u * asum + orc_ulp(v, ORC_F64);",
+     "double b = bsum + orc_ulp(v, ORC_F64);"),
     ("cumsum compensation", "const double e = (sh - (s2 - bp)) + (y - bp);", "const double e = 0.0;"),
 ]
 

@@ -801,3 +801,49 @@ def test_broadcast_keeps_bounds_and_int_values(orc):
     f = g.normal(size=(6, 1)).astype(np.float32)
     r = orc.evaluate("A exp each_col:3", [F(f)], "f32")
     assert np.all(r.bound[:, 0:1] == r.bound[:, 2:3]) and np.all(r.bound > 0)
+
+
+# ------------------------------------------------------------ matrix product
+
+def test_matmul_exact_cases(orc):
+    g = np.random.default_rng(100)
+    a = g.normal(size=(6, 9))
+    eye = np.eye(9)
+    assert np.array_equal(orc.evaluate("A B mm", [F(a), F(eye)], "f64").value, a)
+    perm = np.eye(6)[g.permutation(6)]
+    assert np.array_equal(orc.evaluate("B A mm", [F(a), F(perm)], "f64").value, perm @ a)
+    # integer-valued operands: every product and sum exact
+    x = g.integers(-50, 50, size=(7, 11)).astype(np.float64)
+    y = g.integers(-50, 50, size=(11, 4)).astype(np.float64)
+    assert np.array_equal(orc.evaluate("A B mm", [F(x), F(y)], "f64").value, x @ y)
+
+
+def test_matmul_of_a_transpose_and_exact_rounding(orc):
+    g = np.random.default_rng(101)
+    x = g.normal(size=(40, 13))   # K x M
+    y = g.normal(size=(40, 17))   # K x N
+    v = orc.evaluate("A trans B mm", [F(x), F(y)], "f64").value
+    exact = np.array([[float(sum(Fraction(float(x[t, i])) * Fraction(float(y[t, j])) for t in range(40)))
+                       for j in range(17)] for i in range(13)])
+    assert np.array_equal(v, exact)
+
+
+@pytest.mark.parametrize("k", [1, 64, 700])
+def test_matmul_bound_covers_fp32_accumulation(orc, k):
+    # products of FP32 values rounded to FP32 and accumulated in FP32 stay
+    # inside the bound: checked for sequential and pairwise orders
+    g = np.random.default_rng(102 + k)
+    x = g.normal(size=(8, k)).astype(np.float32)
+    y = g.normal(size=(k, 5)).astype(np.float32)
+    r = orc.evaluate("A B mm", [F(x), F(y)], "f32")
+    p = x.astype(np.float64)[:, :, None] * y.astype(np.float64)[None, :, :]   # exact in double
+    seq = np.zeros((8, 5), dtype=np.float32)
+    for t in range(k):
+        seq = (seq + p[:, t, :].astype(np.float32)).astype(np.float32)
+    pw = p.astype(np.float32)
+    while pw.shape[1] > 1:
+        if pw.shape[1] % 2:
+            pw = np.concatenate([pw, np.zeros((8, 1, 5), dtype=np.float32)], axis=1)
+        pw = (pw[:, 0::2, :] + pw[:, 1::2, :]).astype(np.float32)
+    for dev in (seq.astype(np.float64), pw[:, 0, :].astype(np.float64)):
+        assert np.all(np.abs(dev - r.value) <= r.bound)
