@@ -231,6 +231,26 @@ COOT_API coot_status coot_eval_unfused(coot_ctx* ctx, const coot_tree* tree, con
 COOT_API coot_status coot_warmup(coot_ctx* ctx, const coot_tree* tree, const coot_mat* leaves, int32_t n_leaves,
                         const coot_mat* out, coot_reduce red);
 
+/* ---- GEMM with a fused epilogue --------------------------------------------
+ * Y = epi(P, extra...) with P = op(A) op(B) (Sec. 3: trans(X)*Y is one GEMM
+ * call with a transposed operand; here the element-wise remainder of the
+ * expression is evaluated on the product inside the same kernel, before Y is
+ * stored):
+ *   A, B     BF16 or FP16, both the same, rows adjacent (rs <= 1);
+ *            op(A) = trans_a ? A^T : A is m x k, op(B) = trans_b ? B^T : B is
+ *            k x n.
+ *   epi      (nullable) a tree whose leaf 0 is the product P, read whole and
+ *            untransposed, and whose leaves 1..n_extra are `extra` (m x n
+ *            reads, not transposed); NULL means Y = P.
+ *   out      m x n, same dtype; must not overlap A or B.
+ * Products are accumulated in FP32 on the tensor cores; the epilogue runs in
+ * FP32 and Y is rounded once.  COOT_ERR_UNSUPPORTED for other dtypes or a
+ * transposed epilogue read.  The first call for an epilogue signature
+ * compiles its kernel. */
+COOT_API coot_status coot_gemm_eval(coot_ctx* ctx, const coot_mat* A, int32_t trans_a, const coot_mat* B,
+                                    int32_t trans_b, const coot_tree* epi, const coot_mat* extra, int32_t n_extra,
+                                    const coot_mat* out, coot_stream stream);
+
 /* ---- adjoint ---------------------------------------------------------------
  * For a scalar loss L = red(tree) with red.kind R_ACCU, R_SUM (dim -1) or
  * R_MEAN (dim -1), writes grads[i] = upstream * dL/dleaves[i] for every i

@@ -1000,6 +1000,123 @@ extern "C" coot_status coot_eval_unfused(coot_ctx* ctx, const coot_tree* tree, c
 }
 
 // ---------------------------------------------------------------------------
+// GEMM with the tree fused onto the product
+// ---------------------------------------------------------------------------
+extern "C" coot_status coot_gemm_eval(coot_ctx* ctx, const coot_mat* A, int32_t trans_a, const coot_mat* B,
+                                      int32_t trans_b, const coot_tree* epi, const coot_mat* extra, int32_t n_extra,
+                                      const coot_mat* out, coot_stream stream_) {
+  if (!ctx || !A || !B || !out) return set_error(COOT_ERR_INVALID, "ctx, A, B or out is NULL");
+  if (n_extra < 0 || n_extra > COOT_MAX_LEAVES - 1 || (n_extra > 0 && !extra))
+    return set_error(COOT_ERR_INVALID, "n_extra %d outside 0..%d (or extra NULL)", n_extra, COOT_MAX_LEAVES - 1);
+  if (A->dtype != B->dtype || A->dtype != out->dtype)
+    return set_error(COOT_ERR_DTYPE, "A, B and out must share one dtype");
+  if (A->dtype != COOT_BF16 && A->dtype != COOT_F16)
+    return set_error(COOT_ERR_UNSUPPORTED, "the fused GEMM takes BF16 or FP16 operands (tensor cores)");
+  if (A->rs > 1 || B->rs > 1) return set_error(COOT_ERR_UNSUPPORTED, "GEMM operands need adjacent rows");
+  const int64_t m = trans_a ? A->n_cols : A->n_rows, k = trans_a ? A->n_rows : A->n_cols;
+  const int64_t kb = trans_b ? B->n_cols : B->n_rows, n = trans_b ? B->n_rows : B->n_cols;
+  if (k != kb)
+    return set_error(COOT_ERR_SHAPE, "op(A) is %lldx%lld, op(B) %lldx%lld", (long long)m, (long long)k,
+                     (long long)kb, (long long)n);
+  if ((m * k > 0 && !A->data) || (k * n > 0 && !B->data)) return set_error(COOT_ERR_INVALID, "A or B: NULL data");
+  const int64_t lda = mat_ld(*A), ldb = mat_ld(*B);
+  if ((A->n_cols > 1 && lda < A->n_rows) || (B->n_cols > 1 && ldb < B->n_rows))
+    return set_error(COOT_ERR_INVALID, "A or B: ld smaller than the rows");
+  // the epilogue tree: leaf 0 is the product, a placeholder with out's storage
+  std::vector<coot_mat> lv(1 + n_extra);
+  lv[0] = coot_mat{out->data, out->dtype, 0, m, n, std::max<int64_t>(m, 1)};
+  for (int i = 0; i < n_extra; ++i) lv[1 + i] = extra[i];
+  coot_node only{};
+  only.op = COOT_N_LEAF;
+  only.a = only.b = -1;
+  const coot_tree single{1, 0, &only};
+  const coot_tree* tree = epi ? epi : &single;
+  cg::Analysis an;
+  coot_status s = cg::analyse(tree, lv.data(), 1 + n_extra, out, coot_reduce{COOT_R_NONE, -1, 0, 0}, &an);
+  if (s) return s;
+  if (an.nr != m || an.nc != n) return set_error(COOT_ERR_SHAPE, "the epilogue is not m x n");
+  if (an.any_trans) return set_error(COOT_ERR_UNSUPPORTED, "transposed reads in a GEMM epilogue");
+  int ps = -1;
+  for (size_t i = 0; i < an.slots.size(); ++i)
+    if (an.slots[i].leaf == 0) {
+      const cg::Slot& sl = an.slots[i];
+      if (ps >= 0 || sl.gen || sl.off != 0 || (an.nc > 1 && sl.cs != m))
+        return set_error(COOT_ERR_UNSUPPORTED, "the product must be read whole and untransposed, once");
+      ps = (int)i;
+    }
+  if (ps < 0) return set_error(COOT_ERR_INVALID, "the epilogue does not read the product (leaf 0)");
+  // out may not overlap the operands
+  auto range = [](const coot_mat& X, int64_t r, int64_t c, uintptr_t* lo, uintptr_t* hi) {
+    const int esz = (X.dtype == COOT_F64) ? 8 : ((X.dtype == COOT_BF16 || X.dtype == COOT_F16) ? 2 : 4);
+    *lo = (uintptr_t)X.data;
+    *hi = (r > 0 && c > 0) ? *lo + (uintptr_t)(((r - 1) + (c - 1) * mat_ld(X) + 1) * esz) : *lo;
+  };
+  uintptr_t olo, ohi, alo, ahi, blo, bhi;
+  range(*out, m, n, &olo, &ohi);
+  range(*A, A->n_rows, A->n_cols, &alo, &ahi);
+  range(*B, B->n_rows, B->n_cols, &blo, &bhi);
+  if ((olo < ahi && alo < ohi) || (olo < bhi && blo < ohi))
+    return set_error(COOT_ERR_ALIAS, "out overlaps a GEMM operand");
+  if (m == 0 || n == 0) return COOT_OK;
+  an.gemm_ps = ps;
+  an.gemm_ka = trans_a != 0;  // A stored k x m: K adjacent
+  an.gemm_kb = trans_b == 0;  // B stored k x n: K adjacent
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  DeviceGuard g(ctx->device);
+  cudaStream_t stream = (cudaStream_t)stream_;
+  cg::Program pg = cg::make_program(an, cg::F_GEMM, false);
+  if (!ctx->mods.count(pg.signature) && capturing(stream))
+    return set_error(COOT_ERR_INVALID, "this GEMM's kernel is not compiled yet; run the call once before capturing");
+  cg::Module* mod = nullptr;
+  s = coot_get_module(ctx, pg, &mod);
+  if (s) return s;
+  s = ws_ensure(ctx, 1, 0, stream);
+  if (s) return s;
+  coot::GemmParams gp{};
+  cg::Params& p = gp.p;
+  for (size_t i = 0; i < an.slots.size(); ++i) {
+    const cg::Slot& sl = an.slots[i];
+    p.src[i] = ((int)i == ps) ? nullptr : (const char*)lv[sl.leaf].data + sl.off * an.esz;
+    p.ld[i] = sl.cs;
+    p.rs[i] = sl.rs;
+  }
+  for (size_t i = 0; i < an.scalars.size(); ++i) p.k[i] = scalar_bits(an.scalars[i], an.ct);
+  p.out = out->data;
+  p.out_ld = mat_ld(*out);
+  p.out_rs = an.out_rs;
+  p.err_flag = ctx->err_flag;
+  gp.a = A->data;
+  gp.b = B->data;
+  gp.lda = lda;
+  gp.ldb = ldb;
+  gp.m = m;
+  gp.n = n;
+  gp.k = k;
+  gp.vec = ((uintptr_t)A->data % 16 == 0 && (uintptr_t)B->data % 16 == 0 && (lda % 8 == 0 || A->n_cols <= 1) &&
+            (ldb % 8 == 0 || B->n_cols <= 1))
+               ? 1
+               : 0;
+  const dim3 grid((unsigned)ceil_div(m, coot::GEMM_TILE), (unsigned)ceil_div(n, coot::GEMM_TILE));
+  if (grid.y > 65535u) return set_error(COOT_ERR_UNSUPPORTED, "n = %lld is too large for one launch", (long long)n);
+  void* args[] = {&gp};
+  cudaError_t e = cudaLaunchKernel((const void*)mod->kernels["coot_gemm"], grid, dim3(256), args, 0, stream);
+  if (e != cudaSuccess) return cuda_error(e, "coot_gemm");
+  coot_launch_info& li = ctx->last;
+  memset(&li, 0, sizeof li);
+  snprintf(li.kernel, sizeof li.kernel, "coot_gemm");
+  li.grid = (int)(grid.x * grid.y);
+  li.block = 256;
+  li.vec = gp.vec ? 8 : 1;
+  li.unroll = 1;
+  li.n_launches = 1;
+  int64_t extra_bytes = 0;
+  for (size_t i = 0; i < an.slots.size(); ++i)
+    if ((int)i != ps) extra_bytes += an.slots[i].n_distinct * an.esz;
+  li.algorithmic_bytes = (m * k + k * n + m * n) * an.esz + extra_bytes;
+  return COOT_OK;
+}
+
+// ---------------------------------------------------------------------------
 // adjoint
 // ---------------------------------------------------------------------------
 extern "C" coot_status coot_eval_adjoint(coot_ctx* ctx, const coot_tree* tree, const coot_mat* leaves,

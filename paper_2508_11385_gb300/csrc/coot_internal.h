@@ -34,7 +34,7 @@ using coot::RED_PROD;
 using coot::red_additive;
 using coot::red_extreme;
 
-enum Family { F_STR = 0, F_COL = 1, F_ROW = 2, F_TILE = 3, F_ADJ = 4, F_BATCH = 5, F_SCAN = 6 };
+enum Family { F_STR = 0, F_COL = 1, F_ROW = 2, F_TILE = 3, F_ADJ = 4, F_BATCH = 5, F_SCAN = 6, F_GEMM = 7 };
 const char* family_name(Family f);
 
 // compute types
@@ -87,6 +87,9 @@ struct Analysis {
   bool has_out = false;
   int root_op = -1;         // op of the root (R_DOT needs N_SCHUR)
   int accum = 0;            // FP32 accumulation: 0 float-float, 1 Kahan, 2 plain ($COOT_ACCUM)
+  // GEMM epilogue trees: the slot holding the product, and the operands' layouts
+  int gemm_ps = -1;
+  bool gemm_ka = false, gemm_kb = false;
   // var / stddev: a first pass writes the mean(s), a second reduces (y - mean)^2
   bool two_pass() const { return red.kind == COOT_R_VAR || red.kind == COOT_R_STDDEV; }
   // bytes of one accumulator in the workspace (partials of cross-block combines)

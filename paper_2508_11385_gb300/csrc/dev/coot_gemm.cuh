@@ -1,0 +1,232 @@
+// coot_gemm.cuh -- op(A) * op(B) on the tensor cores with the tree fused
+// onto the product (Sec. 3: trans(X)*Y maps onto one GEMM call with a
+// transposed operand; the element-wise part of the expression is evaluated
+// on the product before it is stored).
+//
+// BF16 / FP16 operands, FP32 accumulation, mma.sync m16n8k16.  CTA tile
+// 128 x 128 x 32, 8 warps as 2 (M) x 4 (N), warp tile 64 x 32.  Operand
+// tiles go global -> shared with 16-byte cp.async (zero-filled past the
+// edges), two stages, and shared -> registers with ldmatrix; a K-contiguous
+// operand is stored [row][k] and loaded as is, an M- or N-contiguous one is
+// stored [k][row] and loaded with ldmatrix.trans.  16-byte chunks are
+// XOR-swizzled per row so that the eight row addresses of an ldmatrix fall
+// on different bank groups.  The epilogue evaluates the tree on each product
+// element in registers (the product is slot PS of the tree; the other slots
+// are read at the same (i, j)) and writes Y.
+#pragma once
+#include "coot_kernels.cuh"
+
+namespace coot {
+
+constexpr int GEMM_BM = GEMM_TILE, GEMM_BN = GEMM_TILE, GEMM_BK = 32, GEMM_THREADS = 256;
+
+template <class S> struct Mma;
+template <> struct Mma<bf16> {
+  __device__ static void run(float (&d)[4], const u32 (&a)[4], u32 b0, u32 b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+  }
+};
+template <> struct Mma<f16> {
+  __device__ static void run(float (&d)[4], const u32 (&a)[4], u32 b0, u32 b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+  }
+};
+
+__device__ __forceinline__ u32 smem_u32(const void* p) { return (u32)__cvta_generic_to_shared(p); }
+
+template <bool TRANS> __device__ __forceinline__ void ldsm_x4(u32 (&r)[4], u32 addr) {
+  if constexpr (TRANS)
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+  else
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+
+// 16 bytes global -> shared, zero-filled when !ok (src is then not read)
+__device__ __forceinline__ void cp_async16(u32 dst, const void* src, bool ok) {
+  const int n = ok ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(n));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N)); }
+
+// One operand tile in shared memory: ROWS x 32 (K-contiguous: rows are M or
+// N, 4 chunks of 8 along K) or 32 x COLS (not K-contiguous: rows are K, the
+// chunks run along M or N).  Chunk (r, c) lives at r * CPR + (c ^ swz(r)).
+template <bool KCONT> struct TileLayout {
+  static constexpr int CPR = KCONT ? GEMM_BK / 8 : GEMM_BM / 8;  // 16-byte chunks per row
+  static constexpr int ROWS = KCONT ? GEMM_BM : GEMM_BK;
+  __device__ static int swz(int r) { return KCONT ? ((r >> 1) & 3) : (r & 7); }
+  __device__ static int chunk(int r, int c) { return r * CPR + (c ^ swz(r)); }
+};
+
+// global -> shared for one operand tile.  KCONT: element (row, k) of op(X) at
+// X[k + row * ld]; else at X[row + k * ld].  row0/k0: tile origin; nrow/nk:
+// extents of op(X).  16-byte cp.async when the whole chunk is inside and
+// aligned, else element by element (zeros outside).
+template <class S, bool KCONT>
+__device__ __forceinline__ void load_tile(u32 sbase, const S* X, long long ld, long long row0, long long k0,
+                                          long long nrow, long long nk, bool vec) {
+  typedef TileLayout<KCONT> Lt;
+  constexpr int NCH = Lt::ROWS * Lt::CPR;  // 512
+#pragma unroll
+  for (int q = 0; q < NCH / GEMM_THREADS; ++q) {
+    const int ch = threadIdx.x + q * GEMM_THREADS;
+    const int r = ch / Lt::CPR, c = ch % Lt::CPR;
+    // the chunk's first element and the stride of its 8 elements
+    long long orow, ok0;
+    if constexpr (KCONT) {
+      orow = row0 + r;
+      ok0 = k0 + 8 * c;
+    } else {
+      orow = row0 + 8 * c;
+      ok0 = k0 + r;
+    }
+    const u32 dst = sbase + 16u * (u32)Lt::chunk(r, c);
+    const S* src = KCONT ? X + (ok0 + orow * ld) : X + (orow + ok0 * ld);
+    const bool inside = KCONT ? (orow < nrow && ok0 + 8 <= nk) : (ok0 < nk && orow + 8 <= nrow);
+    if (vec && inside) {
+      cp_async16(dst, src, true);
+    } else {
+      // ragged edge or unaligned operand: element by element
+      u16 e[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const bool ok = KCONT ? (orow < nrow && ok0 + t < nk) : (ok0 < nk && orow + t < nrow);
+        e[t] = ok ? ldg_u16(src + t) : (u16)0;  // the 8 elements are adjacent in memory either way
+      }
+      const u32 w0 = (u32)e[0] | ((u32)e[1] << 16), w1 = (u32)e[2] | ((u32)e[3] << 16);
+      const u32 w2 = (u32)e[4] | ((u32)e[5] << 16), w3 = (u32)e[6] | ((u32)e[7] << 16);
+      asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};" ::"r"(dst), "r"(w0), "r"(w1), "r"(w2), "r"(w3));
+    }
+  }
+}
+
+template <class T, class S, int NS, int NK, int PS, bool KA, bool KB>
+__device__ __forceinline__ void gemm_kernel(const GemmParams& gp) {
+  typedef float C;
+  typedef TileLayout<KA> LA;
+  typedef TileLayout<KB> LB;
+  constexpr int A_BYTES = LA::ROWS * LA::CPR * 16, B_BYTES = LB::ROWS * LB::CPR * 16;
+  __shared__ __align__(128) unsigned char smem[2][A_BYTES + B_BYTES];
+  const Params& p = gp.p;
+  const S* A = (const S*)gp.a;
+  const S* B = (const S*)gp.b;
+  const long long M = gp.m, N = gp.n, K = gp.k;
+  const long long m0 = (long long)blockIdx.x * GEMM_BM, n0 = (long long)blockIdx.y * GEMM_BN;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int wm = warp & 1, wn = warp >> 1;  // warp tile: rows 64 wm.., cols 32 wn..
+  const bool vec = gp.vec != 0;
+  float acc[4][4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+
+  const long long nkt = (K + GEMM_BK - 1) / GEMM_BK;
+  auto stage_a = [&](int st) { return smem_u32(&smem[st][0]); };
+  auto stage_b = [&](int st) { return smem_u32(&smem[st][A_BYTES]); };
+  if (nkt > 0) {
+    load_tile<S, KA>(stage_a(0), A, gp.lda, m0, 0, M, K, vec);
+    load_tile<S, KB>(stage_b(0), B, gp.ldb, n0, 0, N, K, vec);
+  }
+  cp_async_commit();
+  for (long long kt = 0; kt < nkt; ++kt) {
+    const int st = (int)(kt & 1);
+    if (kt + 1 < nkt) {
+      load_tile<S, KA>(stage_a(st ^ 1), A, gp.lda, m0, (kt + 1) * GEMM_BK, M, K, vec);
+      load_tile<S, KB>(stage_b(st ^ 1), B, gp.ldb, n0, (kt + 1) * GEMM_BK, N, K, vec);
+    }
+    cp_async_commit();
+    cp_async_wait<1>();  // this stage's group has landed
+    __syncthreads();
+    const u32 sa = stage_a(st), sb = stage_b(st);
+#pragma unroll
+    for (int kk = 0; kk < GEMM_BK; kk += 16) {
+      // A fragments: four 16 x 16 tiles of the warp's 64 rows
+      u32 af[4][4];
+      const int mat = lane >> 3, r8 = lane & 7;
+#pragma unroll
+      for (int mt = 0; mt < 4; ++mt) {
+        const int mrow = wm * 64 + mt * 16;
+        int rr, cc;
+        if constexpr (KA) {  // [m][k]: rows m, chunks along k
+          rr = mrow + r8 + (mat & 1) * 8;
+          cc = kk / 8 + (mat >> 1);
+        } else {  // [k][m]: rows k, chunks along m
+          rr = kk + r8 + (mat >> 1) * 8;
+          cc = (mrow + (mat & 1) * 8) / 8;
+        }
+        ldsm_x4<!KA>(af[mt], sa + 16u * (u32)LA::chunk(rr, cc));
+      }
+      // B fragments: four 16 x 8 tiles of the warp's 32 columns, two per ldmatrix
+      u32 bf[4][2];
+#pragma unroll
+      for (int np = 0; np < 2; ++np) {
+        const int ncol = wn * 32 + np * 16;
+        int rr, cc;
+        u32 t[4];
+        if constexpr (KB) {  // [n][k]
+          rr = ncol + r8 + (mat >> 1) * 8;
+          cc = kk / 8 + (mat & 1);
+        } else {  // [k][n]
+          rr = kk + r8 + (mat & 1) * 8;
+          cc = (ncol + (mat >> 1) * 8) / 8;
+        }
+        ldsm_x4<!KB>(t, sb + 16u * (u32)LB::chunk(rr, cc));
+        bf[2 * np][0] = t[0];
+        bf[2 * np][1] = t[1];
+        bf[2 * np + 1][0] = t[2];
+        bf[2 * np + 1][1] = t[3];
+      }
+#pragma unroll
+      for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) Mma<S>::run(acc[mt][nt], af[mt], bf[nt][0], bf[nt][1]);
+    }
+    __syncthreads();  // the stage is free for the load two steps ahead
+  }
+  cp_async_wait<0>();
+
+  // epilogue: the tree on every product element of the warp tile
+  Scal<C, NK> k;
+#pragma unroll
+  for (int q = 0; q < NK; ++q) k.k[q] = scalar_from_bits<C>(p.k[q]);
+  u32 err = 0;
+  const int g = lane >> 2, tq = lane & 3;
+#pragma unroll
+  for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const long long i = m0 + wm * 64 + mt * 16 + g + 8 * h;
+          const long long j = n0 + wn * 32 + nt * 8 + 2 * tq + e;
+          if (i < M && j < N) {
+            Vals<C, NS, 1> x;
+#pragma unroll
+            for (int s = 0; s < NS; ++s)
+              x.v[s][0] = (s == PS) ? acc[mt][nt][2 * h + e] : IO<S>::load1(at_slot<S>(p, s, i, j));
+            const C y = T::ev(x, k, err, 0);
+            IO<S>::store1(at_out_g<S>(p, i, j), y);
+          }
+        }
+  if (err) atomicOr(p.err_flag, err);
+}
+
+}  // namespace coot

@@ -77,6 +77,20 @@ struct Params {
   double grad_mult;  // 1 for accu, 1/N for mean
 };
 
+// GEMM with the tree fused onto the product: Y = tree(op(A) op(B), leaves).
+// op(A) is m x k, op(B) is k x n, both BF16 or FP16.  ka: op(A)(i,t) at
+// a[t + i*lda] (K adjacent), else a[i + t*lda]; kb: op(B)(t,j) at
+// b[t + j*ldb], else b[j + t*ldb] (the kernel's template flags).
+constexpr int GEMM_TILE = 128;  // output rows and columns per block
+struct GemmParams {
+  Params p;  // the epilogue: slots, scalars, output (the product is a slot without memory)
+  const void* a;
+  const void* b;
+  long long lda, ldb;
+  long long m, n, k;
+  int vec;  // 16-byte copies: aligned bases, lda and ldb multiples of 8
+};
+
 // Batched evaluation: one record per problem, read by the persistent kernel.
 struct BatchProblem {
   const void* src[COOT_MAX_SLOTS];

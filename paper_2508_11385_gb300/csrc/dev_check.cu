@@ -70,3 +70,12 @@ K(chk_scan_col_t_f64, 256, (scan_col_kernel<T3, double, 3, 1, 2, 1>))
 K(chk_scan_col_i32, 256, (scan_col_kernel<T2, int, 2, 0, 4, 2>))
 K(chk_scan_row_bf16, 256, (scan_row_kernel<T3, bf16, 3, 1, 8, 2, 2>))
 K(chk_scan_row_t_f32, 256, (scan_row_kernel<T3, float, 3, 1, 4, 4, 1>))
+// GEMM with a fused epilogue: 2 * P + C (P the product, slot 0), every operand layout
+#include "coot_gemm.cuh"
+typedef eGlue<eOp<Leaf<0>, eop_scalar_times<0>>, Leaf<1>, eglue_plus> TG;
+#define KG(name, body) \
+  extern "C" __global__ void __launch_bounds__(256, 2) name(const __grid_constant__ GemmParams p) { body(p); }
+KG(chk_gemm_bf16_kk, (gemm_kernel<TG, bf16, 2, 1, 0, true, true>))
+KG(chk_gemm_bf16_mn, (gemm_kernel<TG, bf16, 2, 1, 0, false, false>))
+KG(chk_gemm_f16_km, (gemm_kernel<TG, f16, 2, 1, 0, true, false>))
+KG(chk_gemm_bf16_mk, (gemm_kernel<Leaf<0>, bf16, 1, 0, 0, false, true>))

@@ -37,6 +37,7 @@ const char* family_name(Family f) {
     case F_ADJ: return "adj";
     case F_BATCH: return "batch";
     case F_SCAN: return "scan";
+    case F_GEMM: return "gemm";
   }
   return "?";
 }
@@ -532,7 +533,8 @@ Program make_program(const Analysis& an, Family fam, bool var_two_pass) {
   if (an.gmask) src << "#define COOT_GM " << an.gmask << "\n";
   if (an.accum == 1) src << "#define COOT_ACCUM_KAHAN 1\n";
   if (an.accum == 2) src << "#define COOT_ACCUM_PLAIN 1\n";
-  src << "#include \"coot_kernels.cuh\"\nusing namespace coot;\n";
+  src << (fam == F_GEMM ? "#include \"coot_gemm.cuh\"\n" : "#include \"coot_kernels.cuh\"\n")
+      << "using namespace coot;\n";
   src << "typedef " << S << " S_t;\n";
   src << "typedef " << an.type_str << " T_t;\n";
   // minb > 0: at least minb resident blocks per SM (caps registers per thread)
@@ -678,6 +680,14 @@ Program make_program(const Analysis& an, Family fam, bool var_two_pass) {
         }
       }
     }
+  } else if (fam == F_GEMM) {
+    // 256 threads, at least 2 blocks per SM (128 registers)
+    wrap("coot_gemm", 256,
+         std::string("gemm_kernel<T_t, S_t, ") + std::to_string(NS) + ", " + std::to_string(NK) + ", " +
+             std::to_string(an.gemm_ps) + ", " + (an.gemm_ka ? "true" : "false") + ", " +
+             (an.gemm_kb ? "true" : "false") + ">",
+         "GemmParams", 2);
+    add("coot_gemm", 1, 1, 256);
   } else if (fam == F_ADJ) {
     std::vector<std::pair<int, int>> avu = {{V, 1}, {V, 2}, {1, 4}};
     for (auto [v, u] : avu) {
@@ -696,6 +706,8 @@ Program make_program(const Analysis& an, Family fam, bool var_two_pass) {
   }
   sig << "cootgb1|" << family_name(fam) << "|" << S << "|ns" << NS << "|nk" << NK << "|red" << an.red_mode << "|dim"
       << an.red.dim << "|out" << OUT << "|tr" << an.trmask << "|gm" << an.gmask << "|var" << var_two_pass
+      << (fam == F_GEMM ? "|ps" + std::to_string(an.gemm_ps) + (an.gemm_ka ? "ka" : "ma") + (an.gemm_kb ? "kb" : "nb")
+                        : std::string())
       << (an.accum == 1 ? "|kahan" : (an.accum == 2 ? "|plain" : "")) << "|" << an.type_str;
   pg.signature = sig.str();
   pg.source = src.str();

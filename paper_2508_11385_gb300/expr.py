@@ -67,6 +67,9 @@ def _stream_ptr(stream=None):
 # ---------------------------------------------------------------------------
 # expression nodes
 # ---------------------------------------------------------------------------
+MATMUL = "matmul"  # the matrix product: evaluated by the GEMM kernel with the rest fused onto it
+
+
 class Expr:
     """A node of an expression tree (eOp / eGlue / Op in the paper's terms)."""
 
@@ -97,6 +100,8 @@ class Expr:
             elif op == L.N_TRANS:
                 r, c = self.children[0].shape
                 self._shape = (c, r)
+            elif op == MATMUL:
+                self._shape = (self.children[0].n_rows, self.children[1].n_cols)
             elif L.N_PLUS <= op <= L.N_DIV:
                 sa, sb = self.children[0].shape, self.children[1].shape
                 if sa != sb:
@@ -142,12 +147,16 @@ class Expr:
     def __mul__(self, o):
         if isinstance(o, numbers.Real):
             return Expr(L.N_SCAL_TIMES, (self,), k=o)
-        raise TypeError("matrix * matrix is matrix multiplication, not element-wise; use % for the Schur product")
+        # matrix * matrix is the matrix product (% is the element-wise one)
+        o = _as_expr(o)
+        if self.n_cols != o.n_rows:
+            raise ValueError("matrix product: %dx%d times %dx%d" % (*self.shape, *o.shape))
+        return Expr(MATMUL, (self, o))
 
     def __rmul__(self, o):
         if isinstance(o, numbers.Real):
             return Expr(L.N_SCAL_TIMES, (self,), k=o)
-        raise TypeError("matrix * matrix is matrix multiplication, not element-wise; use % for the Schur product")
+        return _as_expr(o).__mul__(self)
 
     def __truediv__(self, o):
         if isinstance(o, numbers.Real):
@@ -373,16 +382,24 @@ def sqrt(x):
 # ---------------------------------------------------------------------------
 # lowering to the C descriptor
 # ---------------------------------------------------------------------------
-def lower(expr: Expr):
+def lower(expr: Expr, product=None):
     """(coot_tree, [leaf Mat], [coot_mat]) of an expression; shared
-    sub-expressions stay shared (the node list is a DAG)."""
+    sub-expressions stay shared (the node list is a DAG).  `product`: a
+    matrix-product node that becomes leaf 0 (a GEMM epilogue; the leaf lists
+    then start with None)."""
     nodes, memo, leaves, leaf_idx = [], {}, [], {}
+    if product is not None:
+        leaves.append(None)
 
     def visit(e):
         key = id(e)
         if key in memo:
             return memo[key]
-        if e.op == L.N_LEAF:
+        if e is product:
+            nodes.append(L.node(L.N_LEAF, leaf=0))
+        elif e.op == MATMUL:
+            raise NotImplementedError("one matrix product per expression")
+        elif e.op == L.N_LEAF:
             lk = (e.tensor.data_ptr(), e.shape, e.ld, e.rs, e.dtype)
             if lk not in leaf_idx:
                 leaf_idx[lk] = len(leaves)
@@ -411,10 +428,51 @@ def lower(expr: Expr):
     visit(expr)
     if len(nodes) > L.MAX_NODES:
         raise ValueError("expression has %d nodes; at most %d" % (len(nodes), L.MAX_NODES))
-    dtypes = {m.dtype for m in leaves}
-    if len(dtypes) != 1:
+    dtypes = {m.dtype for m in leaves if m is not None}
+    if len(dtypes) > 1:
         raise TypeError("all matrices of an expression must share one dtype (got %s)" % sorted(dtypes))
-    return L.make_tree(nodes), leaves, [m.cmat() for m in leaves]
+    return L.make_tree(nodes), leaves, [m.cmat() if m is not None else None for m in leaves]
+
+
+def _products(e, found, seen):
+    if id(e) in seen:
+        return
+    seen.add(id(e))
+    if e.op == MATMUL:
+        found.append(e)
+    for c in e.children:
+        if isinstance(c, Expr):
+            _products(c, found, seen)
+
+
+def _gemm_operand(e):
+    t = False
+    while e.op == L.N_TRANS:
+        e, t = e.children[0], not t
+    if not isinstance(e, Mat):
+        raise NotImplementedError("a matrix product takes matrices or their transposes (evaluate the operand first)")
+    return e, t
+
+
+def _evaluate_gemm(expr, mm, out, stream):
+    """expr with one matrix product mm: the GEMM kernel computes op(A) op(B)
+    and evaluates the rest of expr on it before storing (Sec. 3: trans(X)*Y
+    as one GEMM call with a transposed operand)."""
+    (A, ta), (B, tb) = _gemm_operand(mm.children[0]), _gemm_operand(mm.children[1])
+    nr, nc = expr.shape
+    dev = A.tensor.device
+    if out is None:
+        out = _empty_colmajor(nr, nc, A.dtype, dev)
+    if expr is mm:
+        tree, extra = None, []
+    else:
+        tree, leaves, cm = lower(expr, product=mm)
+        extra = cm[1:]
+        if any(m.dtype != A.dtype for m in leaves[1:]):
+            raise TypeError("all matrices of an expression must share one dtype")
+    with torch.cuda.device(dev):
+        L.coot_gemm_eval(context(dev), A.cmat(), ta, B.cmat(), tb, tree, extra, _out_cmat(out), _stream_ptr(stream))
+    return out
 
 
 def _empty_colmajor(n_rows, n_cols, dtype, device):
@@ -627,6 +685,15 @@ def evaluate(expr, out=None, reduction=None, red_out=None, fused=True, stream=No
     Returns Y (a tensor) when there is no reduction, else (Y or None, result).
     """
     expr = _as_expr(expr)
+    mms = []
+    _products(expr, mms, set())
+    if mms:
+        if len(mms) > 1:
+            raise NotImplementedError("one matrix product per expression")
+        if reduction is not None:
+            raise NotImplementedError("a reduction of a matrix product is not fused; evaluate the product first")
+        return _evaluate_gemm(expr, mms[0], out if out is not None else
+                              (materialise if isinstance(materialise, torch.Tensor) else None), stream)
     tree, leaves, cmats = lower(expr)
     dt = leaves[0].dtype
     dev = leaves[0].tensor.device

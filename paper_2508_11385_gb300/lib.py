@@ -86,6 +86,7 @@ _SIGS = {
     "coot_eval_unfused": ([_P, _TP, _MP, ctypes.c_int32, _MP, coot_reduce, _P, _P], _S),
     "coot_warmup": ([_P, _TP, _MP, ctypes.c_int32, _MP, coot_reduce], _S),
     "coot_eval_adjoint": ([_P, _TP, _MP, ctypes.c_int32, coot_reduce, _P, _MP, _P], _S),
+    "coot_gemm_eval": ([_P, _MP, ctypes.c_int32, _MP, ctypes.c_int32, _TP, _MP, ctypes.c_int32, _MP, _P], _S),
     "coot_batch_create": ([_P, _TP, ctypes.c_int64, ctypes.c_int32, _MP, _MP, coot_reduce, ctypes.POINTER(_P)], _S),
     "coot_batch_run": ([_P, _P, _P], _S),
     "coot_batch_destroy": ([_P], _S),
@@ -171,6 +172,13 @@ def coot_eval_adjoint(ctx, tree, leaves, red, upstream, grads, stream):
     lv = _arr(leaves)
     gv = _arr(grads)
     _check(_lib.coot_eval_adjoint(ctx, ctypes.byref(tree), lv, len(leaves), red, upstream, gv, stream))
+
+
+def coot_gemm_eval(ctx, a, trans_a, b, trans_b, epi, extra, out, stream):
+    ev = _arr(extra) if extra else None
+    _check(_lib.coot_gemm_eval(ctx, ctypes.byref(a), int(trans_a), ctypes.byref(b), int(trans_b),
+                               ctypes.byref(epi) if epi is not None else None, ev, len(extra) if extra else 0,
+                               ctypes.byref(out), stream))
 
 
 def coot_batch_create(ctx, tree, n_problems, n_leaves, problems, outs, red):
