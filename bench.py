@@ -317,7 +317,8 @@ def run_side(args):
     stream = torch.cuda.current_stream(dev)
     fn = {"batched": lambda: bench_batched(args, dev, stream), "adjoint": lambda: bench_adjoint(dev, stream),
           "precision": lambda: bench_precision(dev, stream, errors=args.precision_errors),
-          "graph_chain": lambda: bench_graph(dev, stream), "stats": lambda: bench_stats(args, dev, stream)}[args.only]
+          "graph_chain": lambda: bench_graph(dev, stream), "stats": lambda: bench_stats(args, dev, stream),
+          "gemm": lambda: bench_gemm(args, dev, stream)}[args.only]
     print(json.dumps({args.only: fn()}))
 
 
@@ -596,12 +597,60 @@ def run_extras(args, leaves, calls, per_tree_ms, bytes_per, dev, stream, peak):
         res["stats"] = bench_stats(args, dev, stream)
     except Exception as e:
         res["stats"] = {"error": repr(e)[:300]}
+    try:
+        res["gemm"] = bench_gemm(args, dev, stream)
+    except Exception as e:
+        res["gemm"] = {"error": repr(e)[:300]}
     return res
 
 
 STATS = ["accu", "min", "index_max", "prod", "stddev", "sum:0", "min:0", "index_max:0", "prod:0", "vardim:0:0",
          "sum:1", "max:1", "index_min:1", "prod:1", "stddevdim:1:1", "cumsum:0", "cumsum:1"]
 STATS_T = ["accu", "sum:0", "index_min:0", "vardim:0:0", "sum:1", "max:1", "prod:1", "cumsum:0"]
+
+
+def bench_gemm(args, dev, stream):
+    """trans(X) * Y at 8192^3 BF16 (the paper's implicit-transpose form) with
+    a fused epilogue Y = 2 * P + C, through the C ABI; TFLOP/s against the
+    measured cuBLAS BF16 peak (burst), beside torch.matmul on the same
+    operands."""
+    import torch
+
+    import paper_2508_11385_gb300 as coot
+    from paper_2508_11385_gb300 import expr as E
+    from paper_2508_11385_gb300 import lib as L
+    from paper_2508_11385_gb300 import workloads
+
+    _, _, peaks = load_peaks()
+    bf_peak = float(peaks.get("bf16_tflops", 1900.0))
+    g = workloads.generator(8, dev)
+    n = 8192
+    X = workloads.normal(n, n, "bf16", g, dev)
+    Y = workloads.normal(n, n, "bf16", g, dev)
+    Cm = workloads.normal(n, n, "bf16", g, dev)
+    out = torch.empty((n, n), dtype=torch.bfloat16, device=dev).t()
+    sp = stream.cuda_stream
+    ctx = E.context(dev)
+    res = {}
+    for name, e in (("trans(X)*Y", coot.trans(coot.Mat(X)) * coot.Mat(Y)),
+                    ("2*trans(X)*Y + C (fused)", 2 * (coot.trans(coot.Mat(X)) * coot.Mat(Y)) + coot.Mat(Cm)),
+                    ("X*Y", coot.Mat(X) * coot.Mat(Y))):
+        coot.evaluate(e, out=out)
+        torch.cuda.synchronize()
+        ms = time_calls(lambda: coot.evaluate(e, out=out), stream, reps=5, warm=1)
+        tf = 2.0 * n ** 3 / (ms / 1e3) / 1e12
+        res[name] = {"ms": round(ms, 3), "tflops": round(tf, 1), "frac": round(tf / bf_peak, 3),
+                     "kernel": L.coot_last_launch(ctx)["kernel"]}
+    xt = X.t()
+    torch.matmul(xt, Y)
+    torch.cuda.synchronize()
+    ms = time_calls(lambda: torch.matmul(xt, Y), stream, reps=5, warm=1)
+    res["torch.matmul (cuBLAS), same operands"] = {"ms": round(ms, 3), "tflops": round(2.0 * n ** 3 / (ms / 1e3) / 1e12, 1)}
+    res["peak"] = {"bf16_tflops": bf_peak, "source": "MEASURED_PEAKS.json bf16_tflops (burst)",
+                   "path": "mma.sync m16n8k16 (the legacy tensor-core path; tcgen05 not used)"}
+    del X, Y, Cm, out
+    torch.cuda.empty_cache()
+    return res
 
 
 def bench_stats(args, dev, stream, peak=None):
@@ -964,7 +1013,7 @@ def main():
     ap.add_argument("--only", default=None, help="time one tree of the workload (profiling); implies --quick")
     args = ap.parse_args()
     if args.only:
-        side = ("batched", "adjoint", "precision", "graph_chain", "stats")
+        side = ("batched", "adjoint", "precision", "graph_chain", "stats", "gemm")
         if args.only not in [t[0] for t in TREES] + list(side):
             ap.error("--only: one of %s" % ", ".join([t[0] for t in TREES] + list(side)))
         args.quick = True
