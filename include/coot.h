@@ -199,6 +199,7 @@ typedef struct coot_graph coot_graph;
 #define COOT_CTX_TUNE 1u          /* autotune launch configs on first use    */
 #define COOT_CTX_NO_DISK_CACHE 2u /* keep compiled kernels in memory only    */
 #define COOT_CTX_LOG 4u           /* print JIT / cache / tuning decisions    */
+#define COOT_CTX_NO_TCGEN05 8u    /* GEMM: always the mma.sync kernel        */
 COOT_API coot_status coot_ctx_create(int device, unsigned flags, coot_ctx** out);
 COOT_API coot_status coot_ctx_destroy(coot_ctx* ctx);
 
@@ -244,9 +245,14 @@ COOT_API coot_status coot_warmup(coot_ctx* ctx, const coot_tree* tree, const coo
  *            reads, not transposed); NULL means Y = P.
  *   out      m x n, same dtype; must not overlap A or B.
  * Products are accumulated in FP32 on the tensor cores; the epilogue runs in
- * FP32 and Y is rounded once.  COOT_ERR_UNSUPPORTED for other dtypes or a
- * transposed epilogue read.  The first call for an epilogue signature
- * compiles its kernel. */
+ * FP32 and Y is rounded once.  The form trans(X) * Y (trans_a = 1,
+ * trans_b = 0) with m and n multiples of 128, k a multiple of 32, 16-byte
+ * aligned operands and ld multiples of 8 runs on tcgen05 with the
+ * accumulator in tensor memory (unless the context has COOT_CTX_NO_TCGEN05);
+ * every other case on mma.sync.  A tcgen05 wait that runs past its time
+ * limit sets device flag COOT_FLAG_WAIT_TIMEOUT (Y is then undefined).
+ * COOT_ERR_UNSUPPORTED for other dtypes or a transposed epilogue read.  The
+ * first call for an epilogue signature compiles its kernel. */
 COOT_API coot_status coot_gemm_eval(coot_ctx* ctx, const coot_mat* A, int32_t trans_a, const coot_mat* B,
                                     int32_t trans_b, const coot_tree* epi, const coot_mat* extra, int32_t n_extra,
                                     const coot_mat* out, coot_stream stream);
@@ -334,9 +340,11 @@ COOT_API coot_status coot_sum_rows_f32_noalloc(const coot_mat* x, int32_t mean, 
 
 /* ---- errors and diagnostics --------------------------------------------------
  * coot_check_device_flag: wait for `stream`, read and clear the context's
- * device error flags (bit 0: an INT32 division by zero).  Returns
- * COOT_ERR_DEVICE_FLAG when any flag was set. */
+ * device error flags (bit 0: an INT32 division by zero; bit 1: a bounded
+ * wait of the tcgen05 GEMM timed out).  Returns COOT_ERR_DEVICE_FLAG when
+ * any flag was set. */
 #define COOT_FLAG_INT_DIV_ZERO 1u
+#define COOT_FLAG_WAIT_TIMEOUT 2u
 COOT_API coot_status coot_check_device_flag(coot_ctx* ctx, coot_stream stream, uint32_t* flags);
 
 /* Description of the last launch made by coot_eval on this context (kernel

@@ -1,4 +1,5 @@
 // api.cpp -- the C ABI of libcootgb (see include/coot.h).
+#include <cuda.h>  // CUtensorMap and its enums (the encoder is fetched through the runtime)
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -1002,6 +1003,47 @@ extern "C" coot_status coot_eval_unfused(coot_ctx* ctx, const coot_tree* tree, c
 // ---------------------------------------------------------------------------
 // GEMM with the tree fused onto the product
 // ---------------------------------------------------------------------------
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return (EncodeTiledFn) nullptr;
+    return (EncodeTiledFn)f;
+  }();
+  return fn;
+}
+
+// TMA descriptor of a K x rows operand with K adjacent (column stride ld
+// elements), boxes of 64 K values x box_rows rows, 128-byte swizzle, zeros
+// outside; false when the driver rejects it
+bool tma_map(unsigned long long* dst, const void* data, int dtype, int64_t k, int64_t rows, int64_t ld,
+             int box_rows) {
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return false;
+  alignas(64) CUtensorMap map;
+  const cuuint64_t dims[2] = {(cuuint64_t)k, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)coot::GEMM_TC_BK, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(&map, dtype == COOT_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+                   const_cast<void*>(data), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return false;
+  static_assert(sizeof(CUtensorMap) == 16 * sizeof(unsigned long long), "CUtensorMap is 128 bytes");
+  memcpy(dst, &map, sizeof map);
+  return true;
+}
+
+}  // namespace
+
 extern "C" coot_status coot_gemm_eval(coot_ctx* ctx, const coot_mat* A, int32_t trans_a, const coot_mat* B,
                                       int32_t trans_b, const coot_tree* epi, const coot_mat* extra, int32_t n_extra,
                                       const coot_mat* out, coot_stream stream_) {
@@ -1022,9 +1064,10 @@ extern "C" coot_status coot_gemm_eval(coot_ctx* ctx, const coot_mat* A, int32_t 
   const int64_t lda = mat_ld(*A), ldb = mat_ld(*B);
   if ((A->n_cols > 1 && lda < A->n_rows) || (B->n_cols > 1 && ldb < B->n_rows))
     return set_error(COOT_ERR_INVALID, "A or B: ld smaller than the rows");
-  // the epilogue tree: leaf 0 is the product, a placeholder with out's storage
+  // the epilogue tree: leaf 0 is the product, a placeholder with out's exact
+  // layout (never read; out then aliases it only through an identical view)
   std::vector<coot_mat> lv(1 + n_extra);
-  lv[0] = coot_mat{out->data, out->dtype, 0, m, n, std::max<int64_t>(m, 1)};
+  lv[0] = *out;
   for (int i = 0; i < n_extra; ++i) lv[1 + i] = extra[i];
   coot_node only{};
   only.op = COOT_N_LEAF;
@@ -1040,7 +1083,7 @@ extern "C" coot_status coot_gemm_eval(coot_ctx* ctx, const coot_mat* A, int32_t 
   for (size_t i = 0; i < an.slots.size(); ++i)
     if (an.slots[i].leaf == 0) {
       const cg::Slot& sl = an.slots[i];
-      if (ps >= 0 || sl.gen || sl.off != 0 || (an.nc > 1 && sl.cs != m))
+      if (ps >= 0 || sl.gen || sl.off != 0 || (an.nc > 1 && sl.cs != mat_ld(*out)))
         return set_error(COOT_ERR_UNSUPPORTED, "the product must be read whole and untransposed, once");
       ps = (int)i;
     }
@@ -1098,14 +1141,41 @@ extern "C" coot_status coot_gemm_eval(coot_ctx* ctx, const coot_mat* A, int32_t 
                : 0;
   const dim3 grid((unsigned)ceil_div(m, coot::GEMM_TILE), (unsigned)ceil_div(n, coot::GEMM_TILE));
   if (grid.y > 65535u) return set_error(COOT_ERR_UNSUPPORTED, "n = %lld is too large for one launch", (long long)n);
+  // tcgen05 path: both operands K-adjacent, 16-byte aligned bases and
+  // column strides (TMA), coordinates within int32
+  const int64_t lim = (int64_t)1 << 31;
+  bool tc = an.gemm_ka && an.gemm_kb && !(ctx->flags & COOT_CTX_NO_TCGEN05) && k > 0 && m < lim && n < lim &&
+            k < lim && (uintptr_t)A->data % 16 == 0 && (uintptr_t)B->data % 16 == 0 && lda % 8 == 0 && ldb % 8 == 0;
+  if (tc)
+    tc = tma_map(gp.tma_a, A->data, A->dtype, k, m, lda, coot::GEMM_TC_BM) &&
+         tma_map(gp.tma_b, B->data, B->dtype, k, n, ldb, coot::GEMM_TC_BN);
+  cudaError_t e;
+  const char* kname = tc ? "coot_gemm_tc" : "coot_gemm";
+  int block = 256;
+  unsigned n_blocks = grid.x * grid.y;
   void* args[] = {&gp};
-  cudaError_t e = cudaLaunchKernel((const void*)mod->kernels["coot_gemm"], grid, dim3(256), args, 0, stream);
-  if (e != cudaSuccess) return cuda_error(e, "coot_gemm");
+  if (tc) {
+    gp.tiles_m = ceil_div(m, coot::GEMM_TC_BM);
+    gp.tiles_n = ceil_div(n, coot::GEMM_TC_BN);
+    if (gp.tiles_m * gp.tiles_n >= lim) return set_error(COOT_ERR_UNSUPPORTED, "too many output tiles");
+    const void* kf = (const void*)mod->kernels[kname];
+    if (!mod->gemm_tc_smem) {
+      e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, coot::GEMM_TC_SMEM);
+      if (e != cudaSuccess) return cuda_error(e, "coot_gemm_tc shared memory");
+      mod->gemm_tc_smem = true;
+    }
+    block = 128;
+    n_blocks = (unsigned)(gp.tiles_m * gp.tiles_n);
+    e = cudaLaunchKernel(kf, dim3(n_blocks), dim3(block), args, coot::GEMM_TC_SMEM, stream);
+  } else {
+    e = cudaLaunchKernel((const void*)mod->kernels[kname], grid, dim3(block), args, 0, stream);
+  }
+  if (e != cudaSuccess) return cuda_error(e, kname);
   coot_launch_info& li = ctx->last;
   memset(&li, 0, sizeof li);
-  snprintf(li.kernel, sizeof li.kernel, "coot_gemm");
-  li.grid = (int)(grid.x * grid.y);
-  li.block = 256;
+  snprintf(li.kernel, sizeof li.kernel, "%s", kname);
+  li.grid = (int)n_blocks;
+  li.block = block;
   li.vec = gp.vec ? 8 : 1;
   li.unroll = 1;
   li.n_launches = 1;

@@ -144,6 +144,7 @@ struct Module {
   std::map<std::string, cudaKernel_t> kernels;
   std::map<std::string, cudaFuncAttributes> attrs;
   size_t cubin_bytes = 0;
+  bool gemm_tc_smem = false;  // coot_gemm_tc: dynamic shared memory limit raised
 };
 
 // NVRTC-compile `source` for sm_103a; no device needed.

@@ -229,4 +229,211 @@ __device__ __forceinline__ void gemm_kernel(const GemmParams& gp) {
   if (err) atomicOr(p.err_flag, err);
 }
 
+// ---------------------------------------------------------------------------
+// The same GEMM on the 5th-generation tensor cores (tcgen05), for the
+// paper's form trans(X) * Y, where both operands have K adjacent.
+//   Output tile 128 x 256 per CTA, one CTA per SM (192 KiB of stages), 128
+//   threads.  The FP32 accumulator lives in tensor memory (lane = row of the
+//   tile, column = column; 256 columns allocated by warp 0).
+//   Operand tiles of 64 (K) x 128 or 256 rows are fetched by TMA with the
+//   128-byte swizzle into a 4-stage ring: each row of a tile is 64 K values
+//   = 128 bytes, 8-row groups form 1 KiB swizzle atoms, which is the
+//   K-major SWIZZLE_128B operand layout the MMA reads (stride between 8-row
+//   groups 1 KiB; a K = 16 step moves the start address by 32 bytes).
+//   TMA fills rows and K values past the matrix with zeros, so ragged m, n
+//   and k need no special case; the epilogue stores only inside.
+//   Roles: thread 0 of warp 0 issues the TMA loads (waiting for a stage to
+//   be empty, announcing its bytes on the stage's "full" barrier); thread 0
+//   of warp 1 waits for "full", issues the four K = 16 MMAs of the stage and
+//   commits them to the stage's "empty" barrier, and after the last stage
+//   to the accumulator barrier, on which all four warps wait before the
+//   epilogue.
+//   Every wait is bounded by the global timer, 2 s from the CTA's start:
+//   past it the kernel raises device flag COOT_FLAG_WAIT_TIMEOUT (results
+//   are then undefined) and its remaining waits give up at once, as do
+//   those of CTAs that start with the flag already raised; tensor memory is
+//   always released.
+//   Epilogue: warp w reads lanes 32w..32w+31 (rows) of the accumulator, 16
+//   columns at a time, applies the tree and stores Y (consecutive lanes:
+//   consecutive rows of the column-major result).
+//   Tiles are visited in groups of 16 tile rows (M), N-major inside a
+//   group, so that the CTAs in flight share their A and B tiles in L2.
+// ---------------------------------------------------------------------------
+constexpr int TC_BM = GEMM_TC_BM, TC_BN = GEMM_TC_BN, TC_BK = GEMM_TC_BK, TC_ST = GEMM_TC_STAGES;
+constexpr int TC_A_BYTES = TC_BM * TC_BK * 2, TC_B_BYTES = TC_BN * TC_BK * 2;
+constexpr int TC_BAR_OFF = TC_ST * (TC_A_BYTES + TC_B_BYTES);
+constexpr int TC_GROUP_M = 16;
+constexpr unsigned long long TC_WAIT_NS = 2000000000ull;  // 2 s
+
+template <class S> struct TcFmt;
+template <> struct TcFmt<bf16> { static constexpr u32 v = 1; };
+template <> struct TcFmt<f16> { static constexpr u32 v = 0; };
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 1 KiB between
+// 8-row groups (the leading byte offset is not used by this layout)
+__device__ __forceinline__ unsigned long long tc_desc(u32 saddr) {
+  const unsigned long long start = (saddr >> 4) & 0x3FFFull;
+  const unsigned long long lbo = 1, sbo = 1024u >> 4;
+  return start | (lbo << 16) | (sbo << 32) | (1ull << 46) | (2ull << 61);  // version 1; SWIZZLE_128B
+}
+// instruction descriptor of kind::f16: FP32 accumulator, A and B of the
+// storage type, both K-major, M = 128, N = 256
+template <class S> __device__ __forceinline__ u32 tc_idesc() {
+  return (1u << 4) | (TcFmt<S>::v << 7) | (TcFmt<S>::v << 10) | ((u32)(TC_BN >> 3) << 17) |
+         ((u32)(TC_BM >> 4) << 24);
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// wait until the barrier's phase of the given parity has completed; false
+// once the global timer has passed `deadline`
+__device__ __forceinline__ bool mbar_wait(u32 mbar, u32 parity, unsigned long long deadline) {
+  for (unsigned it = 0;; ++it) {
+    u32 done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 63) == 63 && global_ns() > deadline) return false;
+  }
+}
+
+// TMA: box (k0.., row0..) of a K x rows tensor into shared memory, completing
+// its bytes on mbar
+__device__ __forceinline__ void tma_load_2d(u32 dst, const void* map, int k0, int row0, u32 mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(map), "r"(k0), "r"(row0), "r"(mbar)
+      : "memory");
+}
+
+template <class T, class S, int NS, int NK, int PS>
+__device__ __forceinline__ void gemm_tc_kernel(const GemmParams& gp) {
+  typedef float C;
+  extern __shared__ unsigned char tc_dyn[];
+  const Params& p = gp.p;
+  const long long M = gp.m, N = gp.n, K = gp.k;
+  // tile of this CTA: groups of TC_GROUP_M tile rows, N-major inside a group
+  const long long tid = blockIdx.x, per_group = (long long)TC_GROUP_M * gp.tiles_n;
+  const long long first_m = (tid / per_group) * TC_GROUP_M;
+  const long long gm = (gp.tiles_m - first_m) < TC_GROUP_M ? (gp.tiles_m - first_m) : TC_GROUP_M;
+  const long long tm = first_m + (tid % per_group) % gm, tn = (tid % per_group) / gm;
+  const long long m0 = tm * TC_BM, n0 = tn * TC_BN;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const u32 sbase = (smem_u32(tc_dyn) + 1023u) & ~1023u;
+  const u32 full0 = sbase + TC_BAR_OFF, empty0 = full0 + 8 * TC_ST, accb = empty0 + 8 * TC_ST;
+  const u32 tslot = accb + 8;
+  u32 err = 0;
+  unsigned long long deadline = global_ns();
+  if (!(*(volatile unsigned*)p.err_flag & 2u)) deadline += TC_WAIT_NS;
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < TC_ST; ++st) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full0 + 8 * st));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(empty0 + 8 * st));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(accb));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(gp.tma_a) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(gp.tma_b) : "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tslot), "r"(TC_BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  u32 tmem;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(tmem) : "r"(tslot) : "memory");
+
+  const int nkt = (int)((K + TC_BK - 1) / TC_BK);
+  if (warp == 0) {
+    if (lane == 0) {
+      // producer
+      for (int kt = 0; kt < nkt; ++kt) {
+        const int st = kt % TC_ST;
+        const u32 ph = (u32)((kt / TC_ST) & 1);
+        if (!mbar_wait(empty0 + 8 * st, ph ^ 1u, deadline)) err |= 2u, deadline = 0;  // first pass: all empty
+        const u32 fb = full0 + 8 * st;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(TC_A_BYTES + TC_B_BYTES)
+                     : "memory");
+        tma_load_2d(sbase + (u32)(st * TC_A_BYTES), gp.tma_a, kt * TC_BK, (int)m0, fb);
+        tma_load_2d(sbase + (u32)(TC_ST * TC_A_BYTES + st * TC_B_BYTES), gp.tma_b, kt * TC_BK, (int)n0, fb);
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issue
+      const u32 idesc = tc_idesc<S>();
+      for (int kt = 0; kt < nkt; ++kt) {
+        const int st = kt % TC_ST;
+        const u32 ph = (u32)((kt / TC_ST) & 1);
+        if (!mbar_wait(full0 + 8 * st, ph, deadline)) err |= 2u, deadline = 0;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const unsigned long long ad = tc_desc(sbase + (u32)(st * TC_A_BYTES));
+        const unsigned long long bd = tc_desc(sbase + (u32)(TC_ST * TC_A_BYTES + st * TC_B_BYTES));
+#pragma unroll
+        for (int kk = 0; kk < TC_BK / 16; ++kk) {
+          const u32 accum = (kt > 0 || kk > 0) ? 1u : 0u;
+          // K = 16 per MMA: 32 bytes further along each swizzled row (2 in the descriptor's 16-byte units)
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+              "l"(ad + 2ull * kk), "l"(bd + 2ull * kk), "r"(idesc), "r"(accum));
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         empty0 + 8 * st)
+                     : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(accb)
+                   : "memory");
+    }
+    __syncwarp();
+  }
+  if (!mbar_wait(accb, 0, deadline)) err |= 2u;
+  __syncwarp();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+
+  Scal<C, NK> k;
+#pragma unroll
+  for (int q = 0; q < NK; ++q) k.k[q] = scalar_from_bits<C>(p.k[q]);
+  const long long i = m0 + 32 * warp + lane;
+#pragma unroll 1
+  for (int cc = 0; cc < TC_BN / 16; ++cc) {
+    if (n0 + 16 * cc >= N) break;  // warp-uniform
+    u32 v[16];
+    const u32 taddr = tmem + ((u32)(32 * warp) << 16) + (u32)(16 * cc);
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+      const long long j = n0 + 16 * cc + t;
+      if (i < M && j < N) {
+        Vals<C, NS, 1> x;
+#pragma unroll
+        for (int s2 = 0; s2 < NS; ++s2)
+          x.v[s2][0] = (s2 == PS) ? __uint_as_float(v[t]) : IO<S>::load1(at_slot<S>(p, s2, i, j));
+        const C y = T::ev(x, k, err, 0);
+        IO<S>::store1(at_out_g<S>(p, i, j), y);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN));
+  if (err) atomicOr(p.err_flag, err);
+}
+
 }  // namespace coot

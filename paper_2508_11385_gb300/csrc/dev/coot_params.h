@@ -89,7 +89,16 @@ struct GemmParams {
   long long lda, ldb;
   long long m, n, k;
   int vec;  // 16-byte copies: aligned bases, lda and ldb multiples of 8
+  // tcgen05 kernel: TMA descriptors (CUtensorMap, 128 bytes) of op(A) and
+  // op(B) as K x rows arrays, and the output tile grid
+  alignas(64) unsigned long long tma_a[16];
+  alignas(64) unsigned long long tma_b[16];
+  long long tiles_m, tiles_n;
 };
+constexpr int GEMM_TC_BM = 128, GEMM_TC_BN = 256, GEMM_TC_BK = 64, GEMM_TC_STAGES = 4;
+// dynamic shared memory of the tcgen05 kernel: the stages, barriers and
+// 1 KiB of slack to align the stages to the 1 KiB swizzle atom
+constexpr int GEMM_TC_SMEM = GEMM_TC_STAGES * (GEMM_TC_BM + GEMM_TC_BN) * GEMM_TC_BK * 2 + 256 + 1024;
 
 // Batched evaluation: one record per problem, read by the persistent kernel.
 struct BatchProblem {

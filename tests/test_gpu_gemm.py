@@ -99,3 +99,102 @@ def test_edge_cases_and_errors():
         coot.evaluate(coot.trans(coot.Mat(F)) * coot.Mat(G))
     with pytest.raises(L.CootError, match="ALIAS"):
         coot.evaluate(coot.trans(X) * Y, out=A[:40, :30])   # out overlaps an operand
+
+
+# the tcgen05 kernel: trans(X) * Y with 16-byte aligned operands and column
+# strides (k a multiple of 8 here); ragged m, n and k come in as TMA zeros
+TC_SHAPES = [(128, 256, 64), (256, 512, 96), (128, 768, 1024), (1024, 256, 160), (130, 260, 72), (1, 1, 8),
+             (300, 20, 8), (1000, 40, 8), (64, 64, 1000)]
+
+
+def _no_tc_context(dev):
+    """A second context whose GEMMs always take the mma.sync kernel."""
+    return L.coot_ctx_create(torch.device(dev).index or 0, L.CTX_NO_TCGEN05)
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+@pytest.mark.parametrize("shape", TC_SHAPES)
+def test_tcgen05_product(dtype, shape):
+    m, n, k = shape
+    A = operand(k, m, dtype, 21)
+    B = operand(k, n, dtype, 22)
+    out = coot.evaluate(coot.trans(coot.Mat(A)) * coot.Mat(B))
+    torch.cuda.synchronize()
+    assert coot.last_launch()["kernel"] == "coot_gemm_tc"
+    assert coot.check_device_flag() == 0
+    parity.compare_matrix(out, oracle.evaluate("A trans B mm", parity.host([A, B]), dtype), dtype, "tc")
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+@pytest.mark.parametrize("epi", ["P #2 * C +", "P C % D - abs sqrt", "#1 P -"])
+@pytest.mark.parametrize("shape", [(256, 512, 320), (200, 300, 136)])
+def test_tcgen05_fused_epilogues(dtype, epi, shape):
+    m, n, k = shape
+    A = operand(k, m, dtype, 23) * 0.1
+    B = operand(k, n, dtype, 24) * 0.1
+    C = operand(m, n, dtype, 25)
+    D = operand(m, n, dtype, 26)
+    X, Y, Cm, Dm = coot.Mat(A), coot.Mat(B), coot.Mat(C), coot.Mat(D)
+    P = coot.trans(X) * Y
+    e = {"P #2 * C +": lambda: 2 * P + Cm, "P C % D - abs sqrt": lambda: coot.sqrt(coot.abs(P % Cm - Dm)),
+         "#1 P -": lambda: 1 - P}[epi]()
+    out = coot.evaluate(e)
+    torch.cuda.synchronize()
+    assert coot.last_launch()["kernel"] == "coot_gemm_tc"
+    prog = epi.replace("P", "A trans B mm")
+    parity.compare_matrix(out, oracle.evaluate(prog, parity.host([A, B, C, D]), dtype), dtype, prog)
+
+
+def test_tcgen05_and_mma_sync_agree_within_the_bound():
+    # the same call through both kernels, each within the oracle's bound
+    m, n, k = 384, 512, 512
+    A = operand(k, m, "bf16", 27)
+    B = operand(k, n, "bf16", 28)
+    X, Y = coot.Mat(A), coot.Mat(B)
+    tc = coot.evaluate(coot.trans(X) * Y)
+    torch.cuda.synchronize()
+    assert coot.last_launch()["kernel"] == "coot_gemm_tc"
+    ctx = _no_tc_context("cuda")
+    try:
+        ms = torch.empty((n, m), dtype=torch.bfloat16, device="cuda").t()
+        L.coot_gemm_eval(ctx, X.cmat(), 1, Y.cmat(), 0, None, [], coot.Mat(ms).cmat(),
+                         torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        assert L.coot_last_launch(ctx)["kernel"] == "coot_gemm"
+    finally:
+        L.coot_ctx_destroy(ctx)
+    ref = oracle.evaluate("A trans B mm", parity.host([A, B]), "bf16")
+    parity.compare_matrix(tc, ref, "bf16", "tcgen05")
+    parity.compare_matrix(ms, ref, "bf16", "mma.sync")
+
+
+def test_tcgen05_output_view_and_many_tiles():
+    # a strided output view and a grid of many tile groups (ragged last group)
+    m, n, k = 2176, 768, 256
+    A = operand(k, m, "bf16", 31)
+    B = operand(k, n, "bf16", 32)
+    big = torch.zeros((n + 5, m + 9), dtype=torch.bfloat16, device="cuda").t()
+    out = big[3:3 + m, 2:2 + n]
+    coot.evaluate(coot.trans(coot.Mat(A)) * coot.Mat(B) + 0.5, out=out)
+    torch.cuda.synchronize()
+    assert coot.last_launch()["kernel"] == "coot_gemm_tc"
+    parity.compare_matrix(out, oracle.evaluate("A trans B mm #0.5 +", parity.host([A, B]), "bf16"), "bf16", "view")
+    assert float(big[:3].abs().sum()) == 0.0 and float(big[3 + m:].abs().sum()) == 0.0
+    assert float(big[:, :2].abs().sum()) == 0.0 and float(big[:, 2 + n:].abs().sum()) == 0.0
+
+
+@pytest.mark.parametrize("case", ["k=61 (column stride not a multiple of 8)", "unaligned base", "X*Y layout"])
+def test_tcgen05_declines(case):
+    m, n, k = 128, 256, 64
+    if case.startswith("k=61"):
+        A, B, ta = operand(61, m, "bf16", 33), operand(61, n, "bf16", 34), True
+    elif case == "unaligned base":
+        A, B, ta = operand(k, m, "bf16", 33, offset=1), operand(k, n, "bf16", 34), True
+    else:
+        A, B, ta = operand(m, k, "bf16", 33), operand(k, n, "bf16", 34), False
+    X, Y = coot.Mat(A), coot.Mat(B)
+    out = coot.evaluate((coot.trans(X) if ta else X) * Y)
+    torch.cuda.synchronize()
+    assert coot.last_launch()["kernel"] == "coot_gemm", case
+    prog = "A" + (" trans" if ta else "") + " B mm"
+    parity.compare_matrix(out, oracle.evaluate(prog, parity.host([A, B]), "bf16"), "bf16", case)
