@@ -232,32 +232,34 @@ __device__ __forceinline__ void gemm_kernel(const GemmParams& gp) {
 // ---------------------------------------------------------------------------
 // The same GEMM on the 5th-generation tensor cores (tcgen05), for the
 // paper's form trans(X) * Y, where both operands have K adjacent.
-//   Output tile 128 x 256 per CTA, one CTA per SM (192 KiB of stages), 128
-//   threads.  The FP32 accumulator lives in tensor memory (lane = row of the
-//   tile, column = column; 256 columns allocated by warp 0).
-//   Operand tiles of 64 (K) x 128 or 256 rows are fetched by TMA with the
-//   128-byte swizzle into a 4-stage ring: each row of a tile is 64 K values
-//   = 128 bytes, 8-row groups form 1 KiB swizzle atoms, which is the
-//   K-major SWIZZLE_128B operand layout the MMA reads (stride between 8-row
-//   groups 1 KiB; a K = 16 step moves the start address by 32 bytes).
-//   TMA fills rows and K values past the matrix with zeros, so ragged m, n
-//   and k need no special case; the epilogue stores only inside.
-//   Roles: thread 0 of warp 0 issues the TMA loads (waiting for a stage to
-//   be empty, announcing its bytes on the stage's "full" barrier); thread 0
-//   of warp 1 waits for "full", issues the four K = 16 MMAs of the stage and
-//   commits them to the stage's "empty" barrier, and after the last stage
-//   to the accumulator barrier, on which all four warps wait before the
-//   epilogue.
-//   Every wait is bounded by the global timer, 2 s from the CTA's start:
-//   past it the kernel raises device flag COOT_FLAG_WAIT_TIMEOUT (results
-//   are then undefined) and its remaining waits give up at once, as do
-//   those of CTAs that start with the flag already raised; tensor memory is
-//   always released.
-//   Epilogue: warp w reads lanes 32w..32w+31 (rows) of the accumulator, 16
-//   columns at a time, applies the tree and stores Y (consecutive lanes:
-//   consecutive rows of the column-major result).
-//   Tiles are visited in groups of 16 tile rows (M), N-major inside a
-//   group, so that the CTAs in flight share their A and B tiles in L2.
+//   Persistent: one CTA per SM (192 KiB of operand stages) walks output
+//   tiles of 128 x 256, 192 threads in three roles:
+//   * warp 0, one thread: TMA loads of the operand tiles (64 K values x 128
+//     or 256 rows, 128-byte swizzle) into a 4-stage ring; it waits for a
+//     stage's "empty" barrier and announces the stage's bytes on its "full"
+//     barrier.  Each tile row is 64 K values = 128 bytes and 8-row groups
+//     form 1 KiB swizzle atoms: the K-major SWIZZLE_128B operand layout of
+//     the MMA (1 KiB between 8-row groups; a K = 16 step moves the start
+//     address 32 bytes).  TMA fills rows and K values past the matrix with
+//     zeros, so ragged m, n and k need no special case.
+//   * warp 1, one thread: waits for "full", issues the four K = 16 MMAs of a
+//     stage and commits them to its "empty" barrier.  The FP32 accumulator
+//     lives in tensor memory, double-buffered (2 x 256 columns, lane = tile
+//     row): a tile's MMAs go to one buffer while the epilogue drains the
+//     other; the last commit of a tile arrives on the buffer's "acc full"
+//     barrier.
+//   * warps 2-5, the epilogue: warp w reads lanes 32 (w % 4).. (rows) of the
+//     accumulator, 32 or 16 columns at a time, loads the tree's other leaves
+//     at the same (i, j) ahead of the tensor-memory read, applies the tree
+//     and stores Y (consecutive lanes: consecutive rows of the column-major
+//     result); it then releases the buffer on its "acc empty" barrier.
+//   Tiles are numbered in groups of 16 tile rows (M), N-major inside a
+//   group, and CTA b takes tiles b, b + grid, ...: the tiles in flight share
+//   their A and B tiles in L2.
+//   Every wait is bounded by the global timer (2 s): past it the thread
+//   raises device flag COOT_FLAG_WAIT_TIMEOUT (results are then undefined)
+//   and its remaining waits give up at once, as do those of CTAs that start
+//   with the flag already raised; tensor memory is always released.
 // ---------------------------------------------------------------------------
 constexpr int TC_BM = GEMM_TC_BM, TC_BN = GEMM_TC_BN, TC_BK = GEMM_TC_BK, TC_ST = GEMM_TC_STAGES;
 constexpr int TC_A_BYTES = TC_BM * TC_BK * 2, TC_B_BYTES = TC_BN * TC_BK * 2;
@@ -289,20 +291,30 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// wait until the barrier's phase of the given parity has completed; false
-// once the global timer has passed `deadline`
-__device__ __forceinline__ bool mbar_wait(u32 mbar, u32 parity, unsigned long long deadline) {
-  for (unsigned it = 0;; ++it) {
-    u32 done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(mbar), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if ((it & 63) == 63 && global_ns() > deadline) return false;
+// a thread's bounded waits: wait until the barrier's phase of the given
+// parity has completed, at most TC_WAIT_NS; once one wait has failed
+// (`dead`), later ones only probe
+struct TcWait {
+  bool dead;
+  u32 err;
+  __device__ void operator()(u32 mbar, u32 parity) {
+    const unsigned long long t0 = global_ns();
+    for (unsigned it = 0;; ++it) {
+      u32 done;
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(done)
+          : "r"(mbar), "r"(parity)
+          : "memory");
+      if (done) return;
+      if ((it & 63) == 63 && (dead || global_ns() - t0 > TC_WAIT_NS)) {
+        dead = true;
+        err |= 2u;
+        return;
+      }
+    }
   }
-}
+};
 
 // TMA: box (k0.., row0..) of a K x rows tensor into shared memory, completing
 // its bytes on mbar
@@ -314,37 +326,61 @@ __device__ __forceinline__ void tma_load_2d(u32 dst, const void* map, int k0, in
       : "memory");
 }
 
+__device__ __forceinline__ void tc_tile_origin(const GemmParams& gp, long long tile, long long& m0, long long& n0) {
+  const long long per_group = (long long)TC_GROUP_M * gp.tiles_n;
+  const long long first_m = (tile / per_group) * TC_GROUP_M;
+  const long long gm = (gp.tiles_m - first_m) < TC_GROUP_M ? (gp.tiles_m - first_m) : TC_GROUP_M;
+  m0 = (first_m + (tile % per_group) % gm) * TC_BM;
+  n0 = ((tile % per_group) / gm) * TC_BN;
+}
+
+template <int W> __device__ __forceinline__ void tmem_ld(u32 taddr, u32 (&v)[W]);
+template <> __device__ __forceinline__ void tmem_ld<16>(u32 taddr, u32 (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+template <> __device__ __forceinline__ void tmem_ld<32>(u32 taddr, u32 (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+}
+
 template <class T, class S, int NS, int NK, int PS>
 __device__ __forceinline__ void gemm_tc_kernel(const GemmParams& gp) {
   typedef float C;
+  constexpr int W = NS <= 3 ? 32 : 16;  // accumulator columns per epilogue step
   extern __shared__ unsigned char tc_dyn[];
   const Params& p = gp.p;
   const long long M = gp.m, N = gp.n, K = gp.k;
-  // tile of this CTA: groups of TC_GROUP_M tile rows, N-major inside a group
-  const long long tid = blockIdx.x, per_group = (long long)TC_GROUP_M * gp.tiles_n;
-  const long long first_m = (tid / per_group) * TC_GROUP_M;
-  const long long gm = (gp.tiles_m - first_m) < TC_GROUP_M ? (gp.tiles_m - first_m) : TC_GROUP_M;
-  const long long tm = first_m + (tid % per_group) % gm, tn = (tid % per_group) / gm;
-  const long long m0 = tm * TC_BM, n0 = tn * TC_BN;
+  const long long n_tiles = gp.tiles_m * gp.tiles_n;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const u32 sbase = (smem_u32(tc_dyn) + 1023u) & ~1023u;
-  const u32 full0 = sbase + TC_BAR_OFF, empty0 = full0 + 8 * TC_ST, accb = empty0 + 8 * TC_ST;
-  const u32 tslot = accb + 8;
-  u32 err = 0;
-  unsigned long long deadline = global_ns();
-  if (!(*(volatile unsigned*)p.err_flag & 2u)) deadline += TC_WAIT_NS;
+  const u32 full0 = sbase + TC_BAR_OFF, empty0 = full0 + 8 * TC_ST;
+  const u32 afull0 = empty0 + 8 * TC_ST, aempty0 = afull0 + 16, tslot = aempty0 + 16;
+  TcWait wait{(*(volatile unsigned*)p.err_flag & 2u) != 0, 0};
   if (threadIdx.x == 0) {
     for (int st = 0; st < TC_ST; ++st) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full0 + 8 * st));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(empty0 + 8 * st));
     }
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(accb));
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(afull0 + 8 * b));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(aempty0 + 8 * b));
+    }
     asm volatile("fence.mbarrier_init.release.cluster;");
     asm volatile("prefetch.tensormap [%0];" ::"l"(gp.tma_a) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(gp.tma_b) : "memory");
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tslot), "r"(TC_BN));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tslot), "r"(2 * TC_BN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -356,16 +392,21 @@ __device__ __forceinline__ void gemm_tc_kernel(const GemmParams& gp) {
   const int nkt = (int)((K + TC_BK - 1) / TC_BK);
   if (warp == 0) {
     if (lane == 0) {
-      // producer
-      for (int kt = 0; kt < nkt; ++kt) {
-        const int st = kt % TC_ST;
-        const u32 ph = (u32)((kt / TC_ST) & 1);
-        if (!mbar_wait(empty0 + 8 * st, ph ^ 1u, deadline)) err |= 2u, deadline = 0;  // first pass: all empty
-        const u32 fb = full0 + 8 * st;
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(TC_A_BYTES + TC_B_BYTES)
-                     : "memory");
-        tma_load_2d(sbase + (u32)(st * TC_A_BYTES), gp.tma_a, kt * TC_BK, (int)m0, fb);
-        tma_load_2d(sbase + (u32)(TC_ST * TC_A_BYTES + st * TC_B_BYTES), gp.tma_b, kt * TC_BK, (int)n0, fb);
+      // producer: one ring position per K step, across tiles
+      unsigned it = 0;
+      for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        long long m0, n0;
+        tc_tile_origin(gp, tile, m0, n0);
+        for (int kt = 0; kt < nkt; ++kt, ++it) {
+          const int st = (int)(it % TC_ST);
+          wait(empty0 + 8 * st, ((it / TC_ST) & 1u) ^ 1u);  // the first pass finds every stage empty
+          const u32 fb = full0 + 8 * st;
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
+                       "r"(TC_A_BYTES + TC_B_BYTES)
+                       : "memory");
+          tma_load_2d(sbase + (u32)(st * TC_A_BYTES), gp.tma_a, kt * TC_BK, (int)m0, fb);
+          tma_load_2d(sbase + (u32)(TC_ST * TC_A_BYTES + st * TC_B_BYTES), gp.tma_b, kt * TC_BK, (int)n0, fb);
+        }
       }
     }
     __syncwarp();
@@ -373,67 +414,84 @@ __device__ __forceinline__ void gemm_tc_kernel(const GemmParams& gp) {
     if (lane == 0) {
       // MMA issue
       const u32 idesc = tc_idesc<S>();
-      for (int kt = 0; kt < nkt; ++kt) {
-        const int st = kt % TC_ST;
-        const u32 ph = (u32)((kt / TC_ST) & 1);
-        if (!mbar_wait(full0 + 8 * st, ph, deadline)) err |= 2u, deadline = 0;
+      unsigned it = 0, lt = 0;
+      for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++lt) {
+        const u32 ab = lt & 1u;
+        wait(aempty0 + 8 * ab, ((lt >> 1) & 1u) ^ 1u);  // the epilogue has drained this buffer
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const unsigned long long ad = tc_desc(sbase + (u32)(st * TC_A_BYTES));
-        const unsigned long long bd = tc_desc(sbase + (u32)(TC_ST * TC_A_BYTES + st * TC_B_BYTES));
+        const u32 acc = tmem + ab * (u32)TC_BN;
+        for (int kt = 0; kt < nkt; ++kt, ++it) {
+          const int st = (int)(it % TC_ST);
+          wait(full0 + 8 * st, (it / TC_ST) & 1u);
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const unsigned long long ad = tc_desc(sbase + (u32)(st * TC_A_BYTES));
+          const unsigned long long bd = tc_desc(sbase + (u32)(TC_ST * TC_A_BYTES + st * TC_B_BYTES));
 #pragma unroll
-        for (int kk = 0; kk < TC_BK / 16; ++kk) {
-          const u32 accum = (kt > 0 || kk > 0) ? 1u : 0u;
-          // K = 16 per MMA: 32 bytes further along each swizzled row (2 in the descriptor's 16-byte units)
-          asm volatile(
-              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-              "l"(ad + 2ull * kk), "l"(bd + 2ull * kk), "r"(idesc), "r"(accum));
+          for (int kk = 0; kk < TC_BK / 16; ++kk) {
+            const u32 accum = (kt > 0 || kk > 0) ? 1u : 0u;
+            // K = 16 per MMA: 32 bytes further along each swizzled row (2 in the descriptor's 16-byte units)
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc),
+                "l"(ad + 2ull * kk), "l"(bd + 2ull * kk), "r"(idesc), "r"(accum));
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           empty0 + 8 * st)
+                       : "memory");
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         empty0 + 8 * st)
+                         afull0 + 8 * ab)
                      : "memory");
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(accb)
-                   : "memory");
     }
     __syncwarp();
-  }
-  if (!mbar_wait(accb, 0, deadline)) err |= 2u;
-  __syncwarp();
-  asm volatile("tcgen05.fence::after_thread_sync;");
-
-  Scal<C, NK> k;
+  } else {
+    // epilogue
+    Scal<C, NK> k;
 #pragma unroll
-  for (int q = 0; q < NK; ++q) k.k[q] = scalar_from_bits<C>(p.k[q]);
-  const long long i = m0 + 32 * warp + lane;
+    for (int q = 0; q < NK; ++q) k.k[q] = scalar_from_bits<C>(p.k[q]);
+    const int quarter = warp & 3;
+    unsigned lt = 0;
+    for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++lt) {
+      long long m0, n0;
+      tc_tile_origin(gp, tile, m0, n0);
+      const u32 ab = lt & 1u;
+      wait(afull0 + 8 * ab, (lt >> 1) & 1u);
+      __syncwarp();
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const long long i = m0 + 32 * quarter + lane;
 #pragma unroll 1
-  for (int cc = 0; cc < TC_BN / 16; ++cc) {
-    if (n0 + 16 * cc >= N) break;  // warp-uniform
-    u32 v[16];
-    const u32 taddr = tmem + ((u32)(32 * warp) << 16) + (u32)(16 * cc);
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      for (int cc = 0; cc < TC_BN / W; ++cc) {
+        if (n0 + W * cc >= N) break;  // warp-uniform
+        // the other leaves first, then the accumulator
+        Vals<C, NS, 1> x[W];
 #pragma unroll
-    for (int t = 0; t < 16; ++t) {
-      const long long j = n0 + 16 * cc + t;
-      if (i < M && j < N) {
-        Vals<C, NS, 1> x;
+        for (int t = 0; t < W; ++t) {
+          const long long j = n0 + W * cc + t;
 #pragma unroll
-        for (int s2 = 0; s2 < NS; ++s2)
-          x.v[s2][0] = (s2 == PS) ? __uint_as_float(v[t]) : IO<S>::load1(at_slot<S>(p, s2, i, j));
-        const C y = T::ev(x, k, err, 0);
-        IO<S>::store1(at_out_g<S>(p, i, j), y);
+          for (int s2 = 0; s2 < NS; ++s2)
+            if (s2 != PS) x[t].v[s2][0] = (i < M && j < N) ? IO<S>::load1(at_slot<S>(p, s2, i, j)) : C(0);
+        }
+        u32 v[W];
+        tmem_ld<W>(tmem + ab * (u32)TC_BN + ((u32)(32 * quarter) << 16) + (u32)(W * cc), v);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int t = 0; t < W; ++t) {
+          const long long j = n0 + W * cc + t;
+          x[t].v[PS][0] = __uint_as_float(v[t]);
+          const C y = T::ev(x[t], k, wait.err, 0);
+          if (i < M && j < N) IO<S>::store1(at_out_g<S>(p, i, j), y);
+        }
       }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(aempty0 + 8 * ab) : "memory");
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN));
-  if (err) atomicOr(p.err_flag, err);
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_BN));
+  if (wait.err) atomicOr(p.err_flag, wait.err);
 }
 
 }  // namespace coot

@@ -689,12 +689,12 @@ Program make_program(const Analysis& an, Family fam, bool var_two_pass) {
          "GemmParams", 2);
     add("coot_gemm", 1, 1, 256);
     if (an.gemm_ka && an.gemm_kb) {
-      // trans(X) * Y: tcgen05 with TMA loads, accumulator in tensor memory, one CTA per SM
-      wrap("coot_gemm_tc", 128,
+      // trans(X) * Y: persistent tcgen05 kernel, TMA loads, accumulator in tensor memory, one CTA per SM
+      wrap("coot_gemm_tc", 192,
            std::string("gemm_tc_kernel<T_t, S_t, ") + std::to_string(NS) + ", " + std::to_string(NK) + ", " +
                std::to_string(an.gemm_ps) + ">",
            "GemmParams", 1);
-      add("coot_gemm_tc", 1, 1, 128);
+      add("coot_gemm_tc", 1, 1, 192);
     }
   } else if (fam == F_ADJ) {
     std::vector<std::pair<int, int>> avu = {{V, 1}, {V, 2}, {1, 4}};

@@ -198,3 +198,25 @@ def test_tcgen05_declines(case):
     assert coot.last_launch()["kernel"] == "coot_gemm", case
     prog = "A" + (" trans" if ta else "") + " B mm"
     parity.compare_matrix(out, oracle.evaluate(prog, parity.host([A, B]), "bf16"), "bf16", case)
+
+
+def test_tcgen05_persistent_many_tiles_sampled():
+    # 32 x 17 = 544 output tiles on at most one CTA per SM: every CTA walks
+    # several tiles through both accumulator buffers.  Sampled rows and
+    # columns of the result against the oracle on the matching operand columns.
+    m, n, k = 4096, 4352 - 40, 200
+    A = operand(k, m, "bf16", 35)
+    B = operand(k, n, "bf16", 36)
+    C = operand(m, n, "bf16", 37)
+    out = coot.evaluate(coot.trans(coot.Mat(A)) * coot.Mat(B) - coot.Mat(C))
+    torch.cuda.synchronize()
+    assert coot.last_launch()["kernel"] == "coot_gemm_tc"
+    g = torch.Generator().manual_seed(38)
+    rows = torch.cat([torch.randperm(m, generator=g)[:120], torch.tensor([0, 127, 128, m - 1])]).tolist()
+    cols = torch.cat([torch.randperm(n, generator=g)[:120], torch.tensor([0, 255, 256, n - 1])]).tolist()
+    ri, ci = torch.tensor(rows, device="cuda"), torch.tensor(cols, device="cuda")
+    As, Bs = A[:, ri].contiguous(), B[:, ci].contiguous()
+    Cs = C[ri][:, ci].t().contiguous().t()
+    got = out[ri][:, ci]
+    ref = oracle.evaluate("A trans B mm C -", parity.host([As, Bs, Cs]), "bf16")
+    parity.compare_matrix(got, ref, "bf16", "sampled")
