@@ -647,8 +647,8 @@ def bench_gemm(args, dev, stream):
     ms = time_calls(lambda: torch.matmul(xt, Y), stream, reps=5, warm=1)
     res["torch.matmul (cuBLAS), same operands"] = {"ms": round(ms, 3), "tflops": round(2.0 * n ** 3 / (ms / 1e3) / 1e12, 1)}
     res["peak"] = {"bf16_tflops": bf_peak, "source": "MEASURED_PEAKS.json bf16_tflops (burst)",
-                   "path": "trans(X)*Y: persistent tcgen05 kernel (TMA, accumulator in tensor memory); "
-                           "X*Y: mma.sync m16n8k16"}
+                   "path": "persistent tcgen05 kernel (TMA loads, accumulator in tensor memory), every "
+                           "operand layout; mma.sync m16n8k16 only for unaligned operands"}
     del X, Y, Cm, out
     torch.cuda.empty_cache()
     return res

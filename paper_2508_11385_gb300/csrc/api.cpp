@@ -1021,17 +1021,19 @@ EncodeTiledFn encode_tiled() {
   return fn;
 }
 
-// TMA descriptor of a K x rows operand with K adjacent (column stride ld
-// elements), boxes of 64 K values x box_rows rows, 128-byte swizzle, zeros
-// outside; false when the driver rejects it
-bool tma_map(unsigned long long* dst, const void* data, int dtype, int64_t k, int64_t rows, int64_t ld,
+// TMA descriptor of an operand stored column-major (column stride ld
+// elements), 128-byte swizzle, zeros outside; false when the driver rejects
+// it.  K adjacent: a K x rows array read in boxes of 64 K values x box_rows
+// rows; else a rows x K array read in boxes of 64 rows x 64 K values.
+bool tma_map(unsigned long long* dst, const void* data, int dtype, bool kmaj, int64_t k, int64_t rows, int64_t ld,
              int box_rows) {
   EncodeTiledFn enc = encode_tiled();
   if (!enc) return false;
   alignas(64) CUtensorMap map;
-  const cuuint64_t dims[2] = {(cuuint64_t)k, (cuuint64_t)rows};
+  const cuuint64_t dims[2] = {(cuuint64_t)(kmaj ? k : rows), (cuuint64_t)(kmaj ? rows : k)};
   const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-  const cuuint32_t box[2] = {(cuuint32_t)coot::GEMM_TC_BK, (cuuint32_t)box_rows};
+  const cuuint32_t box[2] = {(cuuint32_t)(kmaj ? coot::GEMM_TC_BK : 64),
+                             (cuuint32_t)(kmaj ? box_rows : coot::GEMM_TC_BK)};
   const cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(&map, dtype == COOT_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
                    const_cast<void*>(data), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -1141,14 +1143,14 @@ extern "C" coot_status coot_gemm_eval(coot_ctx* ctx, const coot_mat* A, int32_t 
                : 0;
   const dim3 grid((unsigned)ceil_div(m, coot::GEMM_TILE), (unsigned)ceil_div(n, coot::GEMM_TILE));
   if (grid.y > 65535u) return set_error(COOT_ERR_UNSUPPORTED, "n = %lld is too large for one launch", (long long)n);
-  // tcgen05 path: both operands K-adjacent, 16-byte aligned bases and
-  // column strides (TMA), coordinates within int32
+  // tcgen05 path: 16-byte aligned bases and column strides (TMA),
+  // coordinates within int32
   const int64_t lim = (int64_t)1 << 31;
-  bool tc = an.gemm_ka && an.gemm_kb && !(ctx->flags & COOT_CTX_NO_TCGEN05) && k > 0 && m < lim && n < lim &&
-            k < lim && (uintptr_t)A->data % 16 == 0 && (uintptr_t)B->data % 16 == 0 && lda % 8 == 0 && ldb % 8 == 0;
+  bool tc = !(ctx->flags & COOT_CTX_NO_TCGEN05) && k > 0 && m < lim && n < lim && k < lim &&
+            (uintptr_t)A->data % 16 == 0 && (uintptr_t)B->data % 16 == 0 && lda % 8 == 0 && ldb % 8 == 0;
   if (tc)
-    tc = tma_map(gp.tma_a, A->data, A->dtype, k, m, lda, coot::GEMM_TC_BM) &&
-         tma_map(gp.tma_b, B->data, B->dtype, k, n, ldb, coot::GEMM_TC_BN);
+    tc = tma_map(gp.tma_a, A->data, A->dtype, an.gemm_ka, k, m, lda, coot::GEMM_TC_BM) &&
+         tma_map(gp.tma_b, B->data, B->dtype, an.gemm_kb, k, n, ldb, coot::GEMM_TC_BN);
   cudaError_t e;
   const char* kname = tc ? "coot_gemm_tc" : "coot_gemm";
   int block = 256;

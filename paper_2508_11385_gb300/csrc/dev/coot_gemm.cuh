@@ -230,18 +230,23 @@ __device__ __forceinline__ void gemm_kernel(const GemmParams& gp) {
 }
 
 // ---------------------------------------------------------------------------
-// The same GEMM on the 5th-generation tensor cores (tcgen05), for the
-// paper's form trans(X) * Y, where both operands have K adjacent.
+// The same GEMM on the 5th-generation tensor cores (tcgen05), for every
+// operand layout: an operand with K adjacent (op(A) of trans(X), op(B) of
+// Y) is "K-major", one with M or N adjacent "MN-major".
 //   Persistent: one CTA per SM (192 KiB of operand stages) walks output
 //   tiles of 128 x 256, 192 threads in three roles:
 //   * warp 0, one thread: TMA loads of the operand tiles (64 K values x 128
 //     or 256 rows, 128-byte swizzle) into a 4-stage ring; it waits for a
 //     stage's "empty" barrier and announces the stage's bytes on its "full"
-//     barrier.  Each tile row is 64 K values = 128 bytes and 8-row groups
-//     form 1 KiB swizzle atoms: the K-major SWIZZLE_128B operand layout of
-//     the MMA (1 KiB between 8-row groups; a K = 16 step moves the start
-//     address 32 bytes).  TMA fills rows and K values past the matrix with
-//     zeros, so ragged m, n and k need no special case.
+//     barrier.  K-major: one box per operand, each tile row 64 K values =
+//     128 bytes, 8-row groups forming 1 KiB swizzle atoms -- the K-major
+//     SWIZZLE_128B layout of the MMA (1 KiB between 8-row groups; a K = 16
+//     step moves the start address 32 bytes).  MN-major: boxes of 64 rows
+//     (128 bytes, the adjacent dimension) x 64 K values, one per 64 rows of
+//     the tile, 8 KiB apart -- the MN-major SWIZZLE_128B layout (8 KiB
+//     between 64-row blocks, 1 KiB between groups of 8 K values; a K = 16
+//     step moves the start address 2 KiB).  TMA fills rows and K values
+//     past the matrix with zeros, so ragged m, n and k need no special case.
 //   * warp 1, one thread: waits for "full", issues the four K = 16 MMAs of a
 //     stage and commits them to its "empty" barrier.  The FP32 accumulator
 //     lives in tensor memory, double-buffered (2 x 256 columns, lane = tile
@@ -271,18 +276,22 @@ template <class S> struct TcFmt;
 template <> struct TcFmt<bf16> { static constexpr u32 v = 1; };
 template <> struct TcFmt<f16> { static constexpr u32 v = 0; };
 
-// shared-memory matrix descriptor: K-major, 128-byte swizzle, 1 KiB between
-// 8-row groups (the leading byte offset is not used by this layout)
-__device__ __forceinline__ unsigned long long tc_desc(u32 saddr) {
+// shared-memory matrix descriptor, 128-byte swizzle.  K-major: 1 KiB
+// between 8-row groups (the leading byte offset is not used).  MN-major:
+// leading byte offset 8 KiB between 64-row blocks, stride byte offset 1 KiB
+// between groups of 8 K values.
+template <bool KMAJ> __device__ __forceinline__ unsigned long long tc_desc(u32 saddr) {
   const unsigned long long start = (saddr >> 4) & 0x3FFFull;
-  const unsigned long long lbo = 1, sbo = 1024u >> 4;
+  const unsigned long long lbo = KMAJ ? 1 : (8192u >> 4), sbo = 1024u >> 4;
   return start | (lbo << 16) | (sbo << 32) | (1ull << 46) | (2ull << 61);  // version 1; SWIZZLE_128B
 }
+// start-address step of one K = 16 MMA, in the descriptor's 16-byte units
+template <bool KMAJ> __device__ constexpr unsigned long long tc_kstep() { return KMAJ ? 32u >> 4 : 2048u >> 4; }
 // instruction descriptor of kind::f16: FP32 accumulator, A and B of the
-// storage type, both K-major, M = 128, N = 256
-template <class S> __device__ __forceinline__ u32 tc_idesc() {
-  return (1u << 4) | (TcFmt<S>::v << 7) | (TcFmt<S>::v << 10) | ((u32)(TC_BN >> 3) << 17) |
-         ((u32)(TC_BM >> 4) << 24);
+// storage type, M = 128, N = 256; bits 15 / 16 mark an MN-major A / B
+template <class S, bool KA, bool KB> __device__ __forceinline__ u32 tc_idesc() {
+  return (1u << 4) | (TcFmt<S>::v << 7) | (TcFmt<S>::v << 10) | ((KA ? 0u : 1u) << 15) | ((KB ? 0u : 1u) << 16) |
+         ((u32)(TC_BN >> 3) << 17) | ((u32)(TC_BM >> 4) << 24);
 }
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -353,7 +362,18 @@ template <> __device__ __forceinline__ void tmem_ld<32>(u32 taddr, u32 (&v)[32])
       : "r"(taddr));
 }
 
-template <class T, class S, int NS, int NK, int PS>
+// one operand tile of a stage: ROWS rows from row0, K values from k0
+template <bool KMAJ, int ROWS>
+__device__ __forceinline__ void tc_load_operand(u32 dst, const void* map, int k0, int row0, u32 mbar) {
+  if constexpr (KMAJ) {
+    tma_load_2d(dst, map, k0, row0, mbar);
+  } else {
+#pragma unroll
+    for (int b = 0; b < ROWS / 64; ++b) tma_load_2d(dst + 8192u * b, map, row0 + 64 * b, k0, mbar);
+  }
+}
+
+template <class T, class S, int NS, int NK, int PS, bool KA, bool KB>
 __device__ __forceinline__ void gemm_tc_kernel(const GemmParams& gp) {
   typedef float C;
   constexpr int W = NS <= 3 ? 32 : 16;  // accumulator columns per epilogue step
@@ -404,8 +424,9 @@ __device__ __forceinline__ void gemm_tc_kernel(const GemmParams& gp) {
           asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
                        "r"(TC_A_BYTES + TC_B_BYTES)
                        : "memory");
-          tma_load_2d(sbase + (u32)(st * TC_A_BYTES), gp.tma_a, kt * TC_BK, (int)m0, fb);
-          tma_load_2d(sbase + (u32)(TC_ST * TC_A_BYTES + st * TC_B_BYTES), gp.tma_b, kt * TC_BK, (int)n0, fb);
+          tc_load_operand<KA, TC_BM>(sbase + (u32)(st * TC_A_BYTES), gp.tma_a, kt * TC_BK, (int)m0, fb);
+          tc_load_operand<KB, TC_BN>(sbase + (u32)(TC_ST * TC_A_BYTES + st * TC_B_BYTES), gp.tma_b, kt * TC_BK,
+                                     (int)n0, fb);
         }
       }
     }
@@ -413,7 +434,7 @@ __device__ __forceinline__ void gemm_tc_kernel(const GemmParams& gp) {
   } else if (warp == 1) {
     if (lane == 0) {
       // MMA issue
-      const u32 idesc = tc_idesc<S>();
+      const u32 idesc = tc_idesc<S, KA, KB>();
       unsigned it = 0, lt = 0;
       for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++lt) {
         const u32 ab = lt & 1u;
@@ -424,16 +445,15 @@ __device__ __forceinline__ void gemm_tc_kernel(const GemmParams& gp) {
           const int st = (int)(it % TC_ST);
           wait(full0 + 8 * st, (it / TC_ST) & 1u);
           asm volatile("tcgen05.fence::after_thread_sync;");
-          const unsigned long long ad = tc_desc(sbase + (u32)(st * TC_A_BYTES));
-          const unsigned long long bd = tc_desc(sbase + (u32)(TC_ST * TC_A_BYTES + st * TC_B_BYTES));
+          const unsigned long long ad = tc_desc<KA>(sbase + (u32)(st * TC_A_BYTES));
+          const unsigned long long bd = tc_desc<KB>(sbase + (u32)(TC_ST * TC_A_BYTES + st * TC_B_BYTES));
 #pragma unroll
           for (int kk = 0; kk < TC_BK / 16; ++kk) {
             const u32 accum = (kt > 0 || kk > 0) ? 1u : 0u;
-            // K = 16 per MMA: 32 bytes further along each swizzled row (2 in the descriptor's 16-byte units)
             asm volatile(
                 "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc),
-                "l"(ad + 2ull * kk), "l"(bd + 2ull * kk), "r"(idesc), "r"(accum));
+                "l"(ad + tc_kstep<KA>() * kk), "l"(bd + tc_kstep<KB>() * kk), "r"(idesc), "r"(accum));
           }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                            empty0 + 8 * st)

@@ -688,14 +688,13 @@ Program make_program(const Analysis& an, Family fam, bool var_two_pass) {
              (an.gemm_kb ? "true" : "false") + ">",
          "GemmParams", 2);
     add("coot_gemm", 1, 1, 256);
-    if (an.gemm_ka && an.gemm_kb) {
-      // trans(X) * Y: persistent tcgen05 kernel, TMA loads, accumulator in tensor memory, one CTA per SM
-      wrap("coot_gemm_tc", 192,
-           std::string("gemm_tc_kernel<T_t, S_t, ") + std::to_string(NS) + ", " + std::to_string(NK) + ", " +
-               std::to_string(an.gemm_ps) + ">",
-           "GemmParams", 1);
-      add("coot_gemm_tc", 1, 1, 192);
-    }
+    // persistent tcgen05 kernel: TMA loads, accumulator in tensor memory, one CTA per SM
+    wrap("coot_gemm_tc", 192,
+         std::string("gemm_tc_kernel<T_t, S_t, ") + std::to_string(NS) + ", " + std::to_string(NK) + ", " +
+             std::to_string(an.gemm_ps) + ", " + (an.gemm_ka ? "true" : "false") + ", " +
+             (an.gemm_kb ? "true" : "false") + ">",
+         "GemmParams", 1);
+    add("coot_gemm_tc", 1, 1, 192);
   } else if (fam == F_ADJ) {
     std::vector<std::pair<int, int>> avu = {{V, 1}, {V, 2}, {1, 4}};
     for (auto [v, u] : avu) {

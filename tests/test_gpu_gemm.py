@@ -112,17 +112,28 @@ def _no_tc_context(dev):
     return L.coot_ctx_create(torch.device(dev).index or 0, L.CTX_NO_TCGEN05)
 
 
+def _tc_expected(m, n, k, ta, tb):
+    # contiguous operands: TMA needs the column strides to be multiples of 8 elements
+    lda = k if ta else m
+    ldb = n if tb else k
+    return "coot_gemm_tc" if lda % 8 == 0 and ldb % 8 == 0 else "coot_gemm"
+
+
 @pytest.mark.parametrize("dtype", ["bf16", "f16"])
+@pytest.mark.parametrize("ta,tb", [(True, False), (False, False), (True, True), (False, True)])
 @pytest.mark.parametrize("shape", TC_SHAPES)
-def test_tcgen05_product(dtype, shape):
+def test_tcgen05_product(dtype, ta, tb, shape):
+    # K-major (trans(X), Y) and MN-major (X, trans(Y)) operands
     m, n, k = shape
-    A = operand(k, m, dtype, 21)
-    B = operand(k, n, dtype, 22)
-    out = coot.evaluate(coot.trans(coot.Mat(A)) * coot.Mat(B))
+    A = operand(k, m, dtype, 21) if ta else operand(m, k, dtype, 21)
+    B = operand(n, k, dtype, 22) if tb else operand(k, n, dtype, 22)
+    X, Y = coot.Mat(A), coot.Mat(B)
+    out = coot.evaluate((coot.trans(X) if ta else X) * (coot.trans(Y) if tb else Y))
     torch.cuda.synchronize()
-    assert coot.last_launch()["kernel"] == "coot_gemm_tc"
+    assert coot.last_launch()["kernel"] == _tc_expected(m, n, k, ta, tb)
     assert coot.check_device_flag() == 0
-    parity.compare_matrix(out, oracle.evaluate("A trans B mm", parity.host([A, B]), dtype), dtype, "tc")
+    prog = "A" + (" trans" if ta else "") + " B" + (" trans" if tb else "") + " mm"
+    parity.compare_matrix(out, oracle.evaluate(prog, parity.host([A, B]), dtype), dtype, prog)
 
 
 @pytest.mark.parametrize("dtype", ["bf16", "f16"])
@@ -183,7 +194,8 @@ def test_tcgen05_output_view_and_many_tiles():
     assert float(big[:, :2].abs().sum()) == 0.0 and float(big[:, 2 + n:].abs().sum()) == 0.0
 
 
-@pytest.mark.parametrize("case", ["k=61 (column stride not a multiple of 8)", "unaligned base", "X*Y layout"])
+@pytest.mark.parametrize("case", ["k=61 (column stride not a multiple of 8)", "unaligned base",
+                                  "X*Y with m=130 (column stride of X)"])
 def test_tcgen05_declines(case):
     m, n, k = 128, 256, 64
     if case.startswith("k=61"):
@@ -191,7 +203,7 @@ def test_tcgen05_declines(case):
     elif case == "unaligned base":
         A, B, ta = operand(k, m, "bf16", 33, offset=1), operand(k, n, "bf16", 34), True
     else:
-        A, B, ta = operand(m, k, "bf16", 33), operand(k, n, "bf16", 34), False
+        A, B, ta = operand(130, k, "bf16", 33), operand(k, n, "bf16", 34), False
     X, Y = coot.Mat(A), coot.Mat(B)
     out = coot.evaluate((coot.trans(X) if ta else X) * Y)
     torch.cuda.synchronize()
