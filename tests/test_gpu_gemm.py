@@ -232,3 +232,51 @@ def test_tcgen05_persistent_many_tiles_sampled():
     got = out[ri][:, ci]
     ref = oracle.evaluate("A trans B mm C -", parity.host([As, Bs, Cs]), "bf16")
     parity.compare_matrix(got, ref, "bf16", "sampled")
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+@pytest.mark.parametrize("ta,tb", [(False, False), (False, True), (True, True)])
+def test_tcgen05_mn_major_operands_with_fused_epilogue(dtype, ta, tb):
+    # MN-major operands (X, trans(Y)) on the tcgen05 kernel with the tree's
+    # other leaves and a scalar fused into the epilogue
+    m, n, k = 256, 384, 200
+    A = (operand(k, m, dtype, 41) if ta else operand(m, k, dtype, 41)) * 0.1
+    B = (operand(n, k, dtype, 42) if tb else operand(k, n, dtype, 42)) * 0.1
+    C = operand(m, n, dtype, 43)
+    X, Y, Cm = coot.Mat(A), coot.Mat(B), coot.Mat(C)
+    P = (coot.trans(X) if ta else X) * (coot.trans(Y) if tb else Y)
+    out = coot.evaluate(2 * P + Cm)
+    torch.cuda.synchronize()
+    assert coot.last_launch()["kernel"] == "coot_gemm_tc"
+    prog = "A" + (" trans" if ta else "") + " B" + (" trans" if tb else "") + " mm #2 * C +"
+    parity.compare_matrix(out, oracle.evaluate(prog, parity.host([A, B, C]), dtype), dtype, prog)
+
+
+def test_tcgen05_gemm_in_a_graph_replays_bitwise():
+    # a warmed GEMM call captured with the library's graph API: the TMA
+    # descriptors travel in the kernel arguments, so the replay is exact
+    m, n, k = 384, 512, 256
+    A = operand(k, m, "bf16", 44)
+    B = operand(k, n, "bf16", 45)
+    X, Y = coot.Mat(A), coot.Mat(B)
+    out = torch.empty((n, m), dtype=torch.bfloat16, device="cuda").t()
+    ctx = coot.context()
+    s = torch.cuda.Stream()
+    call = lambda: L.coot_gemm_eval(ctx, X.cmat(), 1, Y.cmat(), 0, None, [], coot.Mat(out).cmat(), s.cuda_stream)
+    call()
+    torch.cuda.synchronize()
+    assert L.coot_last_launch(ctx)["kernel"] == "coot_gemm_tc"
+    eager = out.clone()
+    out.zero_()
+    torch.cuda.synchronize()
+    L.coot_graph_begin(ctx, s.cuda_stream)
+    call()
+    g = L.coot_graph_end(ctx, s.cuda_stream)
+    out.zero_()
+    torch.cuda.synchronize()
+    L.coot_graph_launch(g, s.cuda_stream)
+    torch.cuda.synchronize()
+    L.coot_graph_destroy(g)
+    assert torch.equal(out, eager)
+    assert coot.check_device_flag() == 0
+    parity.compare_matrix(out, oracle.evaluate("A trans B mm", parity.host([A, B]), "bf16"), "bf16", "graph")
