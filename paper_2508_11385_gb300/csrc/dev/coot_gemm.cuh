@@ -1,9 +1,11 @@
 // coot_gemm.cuh -- op(A) * op(B) on the tensor cores with the tree fused
 // onto the product (Sec. 3: trans(X)*Y maps onto one GEMM call with a
 // transposed operand; the element-wise part of the expression is evaluated
-// on the product before it is stored).
+// on the product before it is stored).  Two kernels: gemm_tc_kernel
+// (tcgen05, further below) for every operand layout TMA can address, and
+// gemm_kernel (mma.sync) for the rest.
 //
-// BF16 / FP16 operands, FP32 accumulation, mma.sync m16n8k16.  CTA tile
+// gemm_kernel: BF16 / FP16 operands, FP32 accumulation, mma.sync m16n8k16.  CTA tile
 // 128 x 128 x 32, 8 warps as 2 (M) x 4 (N), warp tile 64 x 32.  Operand
 // tiles go global -> shared with 16-byte cp.async (zero-filled past the
 // edges), two stages, and shared -> registers with ldmatrix; a K-contiguous
