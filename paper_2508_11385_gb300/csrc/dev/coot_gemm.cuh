@@ -265,8 +265,9 @@ __device__ __forceinline__ void gemm_kernel(const GemmParams& gp) {
 //   their A and B tiles in L2.
 //   Every wait is bounded by the global timer (2 s): past it the thread
 //   raises device flag COOT_FLAG_WAIT_TIMEOUT (results are then undefined)
-//   and its remaining waits give up at once, as do those of CTAs that start
-//   with the flag already raised; tensor memory is always released.
+//   and its remaining waits give up at once; tensor memory is always
+//   released.  A launch whose barriers never complete therefore ends after
+//   one 2 s wait per thread.
 // ---------------------------------------------------------------------------
 constexpr int TC_BM = GEMM_TC_BM, TC_BN = GEMM_TC_BN, TC_BK = GEMM_TC_BK, TC_ST = GEMM_TC_STAGES;
 constexpr int TC_A_BYTES = TC_BM * TC_BK * 2, TC_B_BYTES = TC_BN * TC_BK * 2;
@@ -387,7 +388,7 @@ __device__ __forceinline__ void gemm_tc_kernel(const GemmParams& gp) {
   const u32 sbase = (smem_u32(tc_dyn) + 1023u) & ~1023u;
   const u32 full0 = sbase + TC_BAR_OFF, empty0 = full0 + 8 * TC_ST;
   const u32 afull0 = empty0 + 8 * TC_ST, aempty0 = afull0 + 16, tslot = aempty0 + 16;
-  TcWait wait{(*(volatile unsigned*)p.err_flag & 2u) != 0, 0};
+  TcWait wait{false, 0};
   if (threadIdx.x == 0) {
     for (int st = 0; st < TC_ST; ++st) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full0 + 8 * st));
