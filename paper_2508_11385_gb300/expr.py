@@ -382,12 +382,14 @@ def sqrt(x):
 # ---------------------------------------------------------------------------
 # lowering to the C descriptor
 # ---------------------------------------------------------------------------
-def lower(expr: Expr, product=None):
+def lower(expr: Expr, product=None, done=None):
     """(coot_tree, [leaf Mat], [coot_mat]) of an expression; shared
     sub-expressions stay shared (the node list is a DAG).  `product`: a
     matrix-product node that becomes leaf 0 (a GEMM epilogue; the leaf lists
-    then start with None)."""
+    then start with None).  `done`: {id(product node): Mat} of products
+    already evaluated into temporaries, read as leaves."""
     nodes, memo, leaves, leaf_idx = [], {}, [], {}
+    done = done or {}
     if product is not None:
         leaves.append(None)
 
@@ -395,6 +397,8 @@ def lower(expr: Expr, product=None):
         key = id(e)
         if key in memo:
             return memo[key]
+        if id(e) in done:
+            e = done[id(e)]
         if e is product:
             nodes.append(L.node(L.N_LEAF, leaf=0))
         elif e.op == MATMUL:
@@ -435,30 +439,38 @@ def lower(expr: Expr, product=None):
 
 
 def _products(e, found, seen):
+    """The matrix products of e that are not inside another product's operand."""
     if id(e) in seen:
         return
     seen.add(id(e))
     if e.op == MATMUL:
         found.append(e)
+        return
     for c in e.children:
         if isinstance(c, Expr):
             _products(c, found, seen)
 
 
-def _gemm_operand(e):
+def _gemm_operand(e, stream):
+    """(Mat, transposed) of a product operand.  An operand that is an
+    expression rather than a matrix (or its transpose) is evaluated first
+    into a temporary of the storage type, as Armadillo evaluates it into a
+    temporary matrix; the fused element-wise kernel (or, for a product, the
+    GEMM) computes it."""
     t = False
     while e.op == L.N_TRANS:
         e, t = e.children[0], not t
     if not isinstance(e, Mat):
-        raise NotImplementedError("a matrix product takes matrices or their transposes (evaluate the operand first)")
+        e = Mat(evaluate(e, stream=stream))
     return e, t
 
 
-def _evaluate_gemm(expr, mm, out, stream):
+def _evaluate_gemm(expr, mm, out, stream, done=None):
     """expr with one matrix product mm: the GEMM kernel computes op(A) op(B)
     and evaluates the rest of expr on it before storing (Sec. 3: trans(X)*Y
-    as one GEMM call with a transposed operand)."""
-    (A, ta), (B, tb) = _gemm_operand(mm.children[0]), _gemm_operand(mm.children[1])
+    as one GEMM call with a transposed operand).  `done`: other products of
+    expr, already evaluated into temporaries."""
+    (A, ta), (B, tb) = _gemm_operand(mm.children[0], stream), _gemm_operand(mm.children[1], stream)
     nr, nc = expr.shape
     dev = A.tensor.device
     if out is None:
@@ -466,7 +478,7 @@ def _evaluate_gemm(expr, mm, out, stream):
     if expr is mm:
         tree, extra = None, []
     else:
-        tree, leaves, cm = lower(expr, product=mm)
+        tree, leaves, cm = lower(expr, product=mm, done=done)
         extra = cm[1:]
         if any(m.dtype != A.dtype for m in leaves[1:]):
             raise TypeError("all matrices of an expression must share one dtype")
@@ -688,12 +700,7 @@ def evaluate(expr, out=None, reduction=None, red_out=None, fused=True, stream=No
     mms = []
     _products(expr, mms, set())
     if mms:
-        if len(mms) > 1:
-            raise NotImplementedError("one matrix product per expression")
-        if reduction is not None:
-            raise NotImplementedError("a reduction of a matrix product is not fused; evaluate the product first")
-        return _evaluate_gemm(expr, mms[0], out if out is not None else
-                              (materialise if isinstance(materialise, torch.Tensor) else None), stream)
+        return _evaluate_with_products(expr, mms, out, reduction, red_out, fused, stream, materialise)
     tree, leaves, cmats = lower(expr)
     dt = leaves[0].dtype
     dev = leaves[0].tensor.device
@@ -740,6 +747,31 @@ def evaluate(expr, out=None, reduction=None, red_out=None, fused=True, stream=No
     if reduction is None:
         return out
     return out, rt
+
+
+def _evaluate_with_products(expr, mms, out, reduction, red_out, fused, stream, materialise):
+    """An expression with matrix products.  The first product carries the
+    rest of the expression as its fused epilogue; every other product is
+    evaluated first into a temporary of the storage type (Armadillo's
+    temporaries).  A reduction of such an expression runs over its evaluated
+    result: the GEMM with its epilogue, then the fused reduction."""
+    done = {id(mm): Mat(evaluate(mm, stream=stream)) for mm in mms[1:]}
+    if reduction is None:
+        return _evaluate_gemm(expr, mms[0], out if out is not None else
+                              (materialise if isinstance(materialise, torch.Tensor) else None), stream, done)
+    if reduction.expr is not expr:
+        raise NotImplementedError("a reduction of a matrix product reduces the expression being evaluated")
+    if reduction.kind == L.R_CUMSUM:
+        y = Mat(_evaluate_gemm(expr, mms[0], None, stream, done))
+        return evaluate(y, reduction=Reduction(L.R_CUMSUM, y, reduction.dim, 0, reduction.n_seg), out=out,
+                        fused=fused, stream=stream, materialise=materialise)
+    keep = out if out is not None else (materialise if isinstance(materialise, torch.Tensor) else None)
+    yt = _evaluate_gemm(expr, mms[0], keep, stream, done)
+    y = Mat(yt)
+    _, r = evaluate(y, reduction=Reduction(reduction.kind, y, reduction.dim, reduction.norm_type, reduction.n_seg),
+                    red_out=red_out, fused=fused, stream=stream)
+    want_y = out is not None or materialise is True or isinstance(materialise, torch.Tensor)
+    return (yt if want_y else None), r
 
 
 def warmup(expr, reduction=None, out=None):

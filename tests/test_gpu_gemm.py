@@ -280,3 +280,66 @@ def test_tcgen05_gemm_in_a_graph_replays_bitwise():
     assert torch.equal(out, eager)
     assert coot.check_device_flag() == 0
     parity.compare_matrix(out, oracle.evaluate("A trans B mm", parity.host([A, B]), "bf16"), "bf16", "graph")
+
+
+# Expressions around the fused product.  Armadillo evaluates an operand
+# expression, a second product, or the product under a reduction into a
+# temporary of the element type first; here the temporaries come from the
+# same kernels, so each case equals its decomposition bit for bit, and the
+# decomposition's pieces are checked against the oracle.
+
+def test_operand_expressions_are_evaluated_first():
+    m, n, k = 192, 256, 160
+    A = operand(m, k, "bf16", 51) * 0.1
+    B = operand(k, n, "bf16", 52)
+    X, Y = coot.Mat(A), coot.Mat(B)
+    out = coot.evaluate(coot.exp(X) * coot.trans(2 * coot.trans(Y) + 1))
+    T1 = coot.evaluate(coot.exp(X))
+    T2 = coot.evaluate(2 * coot.trans(Y) + 1)
+    ref = coot.evaluate(coot.Mat(T1) * coot.trans(coot.Mat(T2)))
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+    parity.compare_matrix(T1, oracle.evaluate("A exp", parity.host([A]), "bf16"), "bf16", "exp(X)")
+    parity.compare_matrix(ref, oracle.evaluate("A B trans mm", parity.host([T1, T2]), "bf16"), "bf16", "product")
+
+
+def test_two_products_and_a_chained_product():
+    m, n, k = 128, 192, 96
+    A, B = operand(m, k, "bf16", 53), operand(k, n, "bf16", 54)
+    C, D = operand(m, k, "bf16", 55), operand(k, n, "bf16", 56)
+    E = operand(n, 64, "bf16", 57)
+    Am, Bm, Cm, Dm, Em = (coot.Mat(t) for t in (A, B, C, D, E))
+    two = coot.evaluate(Am * Bm + 0.5 * (Cm * Dm))
+    Tcd = coot.evaluate(Cm * Dm)
+    ref2 = coot.evaluate(Am * Bm + 0.5 * coot.Mat(Tcd))
+    chained = coot.evaluate((Am * Bm) * Em)
+    Tab = coot.evaluate(Am * Bm)
+    ref3 = coot.evaluate(coot.Mat(Tab) * Em)
+    torch.cuda.synchronize()
+    assert torch.equal(two, ref2)
+    assert torch.equal(chained, ref3)
+    parity.compare_matrix(ref2, oracle.evaluate("A B mm #0.5 C * +", parity.host([A, B, Tcd]), "bf16"), "bf16",
+                          "A*B + 0.5*T")
+    parity.compare_matrix(ref3, oracle.evaluate("A B mm", parity.host([Tab, E]), "bf16"), "bf16", "T*E")
+
+
+@pytest.mark.parametrize("kind", ["accu", "sum0", "sum1", "max", "cumsum0"])
+def test_reductions_of_a_product(kind):
+    m, n, k = 160, 224, 128
+    A = operand(k, m, "bf16", 58)
+    B = operand(k, n, "bf16", 59)
+    C = operand(m, n, "bf16", 60)
+    P = coot.trans(coot.Mat(A)) * coot.Mat(B) + coot.Mat(C)
+    red = {"accu": lambda e: coot.accu(e), "sum0": lambda e: coot.sum(e, 0), "sum1": lambda e: coot.sum(e, 1),
+           "max": lambda e: coot.max(e, 0), "cumsum0": lambda e: coot.cumsum(e, 0)}[kind]
+    got = red(P).eval()
+    Y = coot.evaluate(P)
+    ref = red(coot.Mat(Y)).eval()
+    torch.cuda.synchronize()
+    assert torch.equal(got, ref)
+    tok = {"accu": "accu", "sum0": "sum:0", "sum1": "sum:1", "max": "max:0", "cumsum0": "cumsum:0"}[kind]
+    hy = parity.host([Y])
+    if kind == "cumsum0":
+        parity.compare_matrix(ref, oracle.evaluate("A " + tok, hy, "bf16"), "bf16", tok)
+    else:
+        parity.compare_reduction(ref, oracle.evaluate("A " + tok, hy, "bf16"), "bf16", tok)
