@@ -683,9 +683,32 @@ def bench_gemm(args, dev, stream):
     torch.cuda.synchronize()
     ms = time_calls(lambda: torch.matmul(xt, Y), stream, reps=5, warm=1)
     res["torch.matmul (cuBLAS), same operands"] = {"ms": round(ms, 3), "tflops": round(2.0 * n ** 3 / (ms / 1e3) / 1e12, 1)}
+    # FP32 operands on the CUDA cores, beside cuBLAS SGEMM (TF32 off) on the same operands
+    xf, yf = X.float(), Y.float()
+    outf = torch.empty((n, n), dtype=torch.float32, device=dev).t()
+    ef = coot.trans(coot.Mat(xf)) * coot.Mat(yf)
+    coot.evaluate(ef, out=outf)
+    torch.cuda.synchronize()
+    ms = time_calls(lambda: coot.evaluate(ef, out=outf), stream, reps=3, warm=1)
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 lanes x FMA x max SM clock
+    tf = 2.0 * n ** 3 / (ms / 1e3) / 1e12
+    res["trans(X)*Y FP32 (CUDA cores)"] = {"ms": round(ms, 3), "tflops": round(tf, 1), "frac": round(tf / fp32_peak, 3),
+                                          "bound": "alu", "peak_tflops": round(fp32_peak, 1),
+                                          "kernel": L.coot_last_launch(ctx)["kernel"]}
+    allow = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    xft = xf.t()
+    torch.matmul(xft, yf)
+    torch.cuda.synchronize()
+    ms = time_calls(lambda: torch.matmul(xft, yf), stream, reps=3, warm=1)
+    torch.backends.cuda.matmul.allow_tf32 = allow
+    res["torch.matmul FP32 (cuBLAS, TF32 off), same operands"] = {"ms": round(ms, 3),
+                                                                   "tflops": round(2.0 * n ** 3 / (ms / 1e3) / 1e12, 1)}
+    del xf, yf, outf
     res["peak"] = {"bf16_tflops": bf_peak, "source": "MEASURED_PEAKS.json bf16_tflops (burst)",
-                   "path": "persistent tcgen05 kernel (TMA loads, accumulator in tensor memory), every "
-                           "operand layout; mma.sync m16n8k16 only for unaligned operands"}
+                   "path": "BF16: persistent tcgen05 kernel (TMA loads, accumulator in tensor memory), every "
+                           "operand layout; mma.sync m16n8k16 only for unaligned operands. FP32: CUDA-core "
+                           "kernel, peak derived from FP32 lanes x 2 x max SM clock"}
     del X, Y, Cm, out
     torch.cuda.empty_cache()
     return res

@@ -237,22 +237,24 @@ COOT_API coot_status coot_warmup(coot_ctx* ctx, const coot_tree* tree, const coo
  * call with a transposed operand; here the element-wise remainder of the
  * expression is evaluated on the product inside the same kernel, before Y is
  * stored):
- *   A, B     BF16 or FP16, both the same, rows adjacent (rs <= 1);
- *            op(A) = trans_a ? A^T : A is m x k, op(B) = trans_b ? B^T : B is
- *            k x n.
+ *   A, B     BF16, FP16, FP32 or FP64, both the same, rows adjacent
+ *            (rs <= 1); op(A) = trans_a ? A^T : A is m x k, op(B) =
+ *            trans_b ? B^T : B is k x n.
  *   epi      (nullable) a tree whose leaf 0 is the product P, read whole and
  *            untransposed, and whose leaves 1..n_extra are `extra` (m x n
  *            reads, not transposed); NULL means Y = P.
  *   out      m x n, same dtype; must not overlap A or B.
- * Products are accumulated in FP32 on the tensor cores; the epilogue runs in
- * FP32 and Y is rounded once.  The form trans(X) * Y (trans_a = 1,
- * trans_b = 0) with m and n multiples of 128, k a multiple of 32, 16-byte
- * aligned operands and ld multiples of 8 runs on tcgen05 with the
- * accumulator in tensor memory (unless the context has COOT_CTX_NO_TCGEN05);
- * every other case on mma.sync.  A tcgen05 wait that runs past its time
- * limit sets device flag COOT_FLAG_WAIT_TIMEOUT (Y is then undefined).
- * COOT_ERR_UNSUPPORTED for other dtypes or a transposed epilogue read.  The
- * first call for an epilogue signature compiles its kernel. */
+ * BF16 / FP16: products accumulated in FP32 on the tensor cores.  Operands
+ * with 16-byte aligned bases and column strides that are multiples of 8
+ * elements (any layout, any m, n, k >= 1) run on the persistent tcgen05
+ * kernel (TMA loads, accumulator in tensor memory) unless the context has
+ * COOT_CTX_NO_TCGEN05; others on mma.sync.  FP32 / FP64: products
+ * accumulated in the storage type with fused multiply-adds on the CUDA
+ * cores.  The epilogue runs in the compute type (FP32, or FP64 for FP64)
+ * and Y is rounded once.  A tcgen05 wait that runs past its time limit sets
+ * device flag COOT_FLAG_WAIT_TIMEOUT (Y is then undefined).
+ * COOT_ERR_UNSUPPORTED for INT32 or a transposed epilogue read.  The first
+ * call for an epilogue signature compiles its kernel. */
 COOT_API coot_status coot_gemm_eval(coot_ctx* ctx, const coot_mat* A, int32_t trans_a, const coot_mat* B,
                                     int32_t trans_b, const coot_tree* epi, const coot_mat* extra, int32_t n_extra,
                                     const coot_mat* out, coot_stream stream);

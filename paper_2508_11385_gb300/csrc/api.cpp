@@ -1054,8 +1054,8 @@ extern "C" coot_status coot_gemm_eval(coot_ctx* ctx, const coot_mat* A, int32_t 
     return set_error(COOT_ERR_INVALID, "n_extra %d outside 0..%d (or extra NULL)", n_extra, COOT_MAX_LEAVES - 1);
   if (A->dtype != B->dtype || A->dtype != out->dtype)
     return set_error(COOT_ERR_DTYPE, "A, B and out must share one dtype");
-  if (A->dtype != COOT_BF16 && A->dtype != COOT_F16)
-    return set_error(COOT_ERR_UNSUPPORTED, "the fused GEMM takes BF16 or FP16 operands (tensor cores)");
+  if (A->dtype == COOT_I32) return set_error(COOT_ERR_UNSUPPORTED, "the fused GEMM takes BF16, FP16, FP32 or FP64");
+  const bool simt = A->dtype == COOT_F32 || A->dtype == COOT_F64;  // CUDA-core kernel
   if (A->rs > 1 || B->rs > 1) return set_error(COOT_ERR_UNSUPPORTED, "GEMM operands need adjacent rows");
   const int64_t m = trans_a ? A->n_cols : A->n_rows, k = trans_a ? A->n_rows : A->n_cols;
   const int64_t kb = trans_b ? B->n_cols : B->n_rows, n = trans_b ? B->n_rows : B->n_cols;
@@ -1141,18 +1141,20 @@ extern "C" coot_status coot_gemm_eval(coot_ctx* ctx, const coot_mat* A, int32_t 
             (ldb % 8 == 0 || B->n_cols <= 1))
                ? 1
                : 0;
-  const dim3 grid((unsigned)ceil_div(m, coot::GEMM_TILE), (unsigned)ceil_div(n, coot::GEMM_TILE));
-  if (grid.y > 65535u) return set_error(COOT_ERR_UNSUPPORTED, "n = %lld is too large for one launch", (long long)n);
+  const int64_t tile = simt ? (A->dtype == COOT_F32 ? 128 : 64) : coot::GEMM_TILE;
+  const dim3 grid((unsigned)ceil_div(m, tile), (unsigned)ceil_div(n, tile));
+  if (ceil_div(n, tile) > 65535 || ceil_div(m, tile) >= ((int64_t)1 << 31))
+    return set_error(COOT_ERR_UNSUPPORTED, "%lld x %lld is too large for one launch", (long long)m, (long long)n);
   // tcgen05 path: 16-byte aligned bases and column strides (TMA),
   // coordinates within int32
   const int64_t lim = (int64_t)1 << 31;
-  bool tc = !(ctx->flags & COOT_CTX_NO_TCGEN05) && k > 0 && m < lim && n < lim && k < lim &&
+  bool tc = !simt && !(ctx->flags & COOT_CTX_NO_TCGEN05) && k > 0 && m < lim && n < lim && k < lim &&
             (uintptr_t)A->data % 16 == 0 && (uintptr_t)B->data % 16 == 0 && lda % 8 == 0 && ldb % 8 == 0;
   if (tc)
     tc = tma_map(gp.tma_a, A->data, A->dtype, an.gemm_ka, k, m, lda, coot::GEMM_TC_BM) &&
          tma_map(gp.tma_b, B->data, B->dtype, an.gemm_kb, k, n, ldb, coot::GEMM_TC_BN);
   cudaError_t e;
-  const char* kname = tc ? "coot_gemm_tc" : "coot_gemm";
+  const char* kname = simt ? "coot_gemm_simt" : (tc ? "coot_gemm_tc" : "coot_gemm");
   int block = 256;
   unsigned n_blocks = grid.x * grid.y;
   void* args[] = {&gp};

@@ -517,4 +517,143 @@ __device__ __forceinline__ void gemm_tc_kernel(const GemmParams& gp) {
   if (wait.err) atomicOr(p.err_flag, wait.err);
 }
 
+// ---------------------------------------------------------------------------
+// The same GEMM for FP32 and FP64 operands on the CUDA cores (no tensor-core
+// kind computes them exactly): accumulation in the storage type with fused
+// multiply-adds, the same epilogue.
+//   256 threads as 16 x 16, each owning TM x TN outputs (8 x 8 for FP32 in a
+//   128 x 128 tile, 4 x 4 for FP64 in 64 x 64) as two halves of rows (and of
+//   columns) half a tile apart, so that each fragment is read from shared
+//   memory as 16-byte vectors with the 16 lanes of a half-warp on adjacent
+//   chunks (no bank conflict).  Per K step of 8, the A and B
+//   tiles are read from global memory into registers (threads walk the
+//   operand's adjacent dimension, zeros past the edges), stored to shared
+//   memory as [k][row] (rows padded by 4 so the stores of a K-adjacent
+//   operand do not collide on a bank), and the next step's reads are issued
+//   before this step's products, over two shared buffers.
+// ---------------------------------------------------------------------------
+template <class S> struct SimtCfg;
+template <> struct SimtCfg<float> { static constexpr int BM = 128, BN = 128, TM = 8, TN = 8; };
+template <> struct SimtCfg<double> { static constexpr int BM = 64, BN = 64, TM = 4, TN = 4; };
+constexpr int SIMT_BK = 8, SIMT_THREADS = 256;
+
+__device__ __forceinline__ float simt_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double simt_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// element (row, k) of op(X): K adjacent -> X[k + row * ld], else X[row + k * ld]
+template <class S, bool KMAJ, int ROWS>
+__device__ __forceinline__ void simt_fetch(S (&r)[ROWS * SIMT_BK / SIMT_THREADS], const S* X, long long ld,
+                                           long long row0, long long k0, long long nrow, long long nk) {
+  constexpr int PER = ROWS * SIMT_BK / SIMT_THREADS;
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int idx = threadIdx.x + q * SIMT_THREADS;
+    // walk the adjacent dimension with consecutive threads
+    const int row = KMAJ ? idx / SIMT_BK : idx % ROWS;
+    const int kk = KMAJ ? idx % SIMT_BK : idx / ROWS;
+    const long long gr = row0 + row, gk = k0 + kk;
+    r[q] = (gr < nrow && gk < nk) ? IO<S>::load1(KMAJ ? X + (gk + gr * ld) : X + (gr + gk * ld)) : S(0);
+  }
+}
+template <class S, bool KMAJ, int ROWS>
+__device__ __forceinline__ void simt_store(S (*sh)[ROWS + 4], const S (&r)[ROWS * SIMT_BK / SIMT_THREADS]) {
+  constexpr int PER = ROWS * SIMT_BK / SIMT_THREADS;
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int idx = threadIdx.x + q * SIMT_THREADS;
+    const int row = KMAJ ? idx / SIMT_BK : idx % ROWS;
+    const int kk = KMAJ ? idx % SIMT_BK : idx / ROWS;
+    sh[kk][row] = r[q];
+  }
+}
+
+// position in the tile of a thread's i-th row (or column): halves of T/2
+// at t * T/2 and TILE/2 + t * T/2
+template <int T, int TILE_> __device__ __forceinline__ int simt_pos(int t, int i) {
+  return (i < T / 2) ? t * (T / 2) + i : TILE_ / 2 + t * (T / 2) + (i - T / 2);
+}
+// a thread's T values of one shared row, as two 16-byte vectors
+template <class S, int T, int TILE_> __device__ __forceinline__ void simt_frag(S (&v)[T], const S* row, int t);
+template <> __device__ __forceinline__ void simt_frag<float, 8, 128>(float (&v)[8], const float* row, int t) {
+  const float4 x = *(const float4*)(row + t * 4), y = *(const float4*)(row + 64 + t * 4);
+  v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+  v[4] = y.x; v[5] = y.y; v[6] = y.z; v[7] = y.w;
+}
+template <> __device__ __forceinline__ void simt_frag<double, 4, 64>(double (&v)[4], const double* row, int t) {
+  const double2 x = *(const double2*)(row + t * 2), y = *(const double2*)(row + 32 + t * 2);
+  v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
+}
+
+template <class T, class S, int NS, int NK, int PS, bool KA, bool KB>
+__device__ __forceinline__ void gemm_simt_kernel(const GemmParams& gp) {
+  typedef SimtCfg<S> G;
+  constexpr int BM = G::BM, BN = G::BN, TM = G::TM, TN = G::TN, BK = SIMT_BK;
+  constexpr int PA = BM * BK / SIMT_THREADS, PB = BN * BK / SIMT_THREADS;
+  __shared__ __align__(16) S As[2][BK][BM + 4];
+  __shared__ __align__(16) S Bs[2][BK][BN + 4];
+  const Params& p = gp.p;
+  const S* A = (const S*)gp.a;
+  const S* B = (const S*)gp.b;
+  const long long M = gp.m, N = gp.n, K = gp.k;
+  const long long m0 = (long long)blockIdx.x * BM, n0 = (long long)blockIdx.y * BN;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  S acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = S(0);
+  const long long nkt = (K + BK - 1) / BK;
+  S ra[PA], rb[PB];
+  if (nkt > 0) {
+    simt_fetch<S, KA, BM>(ra, A, gp.lda, m0, 0, M, K);
+    simt_fetch<S, KB, BN>(rb, B, gp.ldb, n0, 0, N, K);
+    simt_store<S, KA, BM>(As[0], ra);
+    simt_store<S, KB, BN>(Bs[0], rb);
+  }
+  __syncthreads();
+  for (long long kt = 0; kt < nkt; ++kt) {
+    const int st = (int)(kt & 1);
+    if (kt + 1 < nkt) {  // next step's reads in flight during this step's products
+      simt_fetch<S, KA, BM>(ra, A, gp.lda, m0, (kt + 1) * BK, M, K);
+      simt_fetch<S, KB, BN>(rb, B, gp.ldb, n0, (kt + 1) * BK, N, K);
+    }
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      S a[TM], b[TN];
+      simt_frag<S, TM, BM>(a, &As[st][kk][0], ty);
+      simt_frag<S, TN, BN>(b, &Bs[st][kk][0], tx);
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = simt_fma(a[i], b[j], acc[i][j]);
+    }
+    if (kt + 1 < nkt) {
+      simt_store<S, KA, BM>(As[st ^ 1], ra);
+      simt_store<S, KB, BN>(Bs[st ^ 1], rb);
+    }
+    __syncthreads();
+  }
+
+  // epilogue: the tree on every product element of the thread's block
+  typedef S C;
+  Scal<C, NK> k;
+#pragma unroll
+  for (int q = 0; q < NK; ++q) k.k[q] = scalar_from_bits<C>(p.k[q]);
+  u32 err = 0;
+#pragma unroll
+  for (int j = 0; j < TN; ++j)
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      const long long gi = m0 + simt_pos<TM, BM>(ty, i), gj = n0 + simt_pos<TN, BN>(tx, j);
+      if (gi < M && gj < N) {
+        Vals<C, NS, 1> x;
+#pragma unroll
+        for (int s2 = 0; s2 < NS; ++s2)
+          x.v[s2][0] = (s2 == PS) ? acc[i][j] : IO<S>::load1(at_slot<S>(p, s2, gi, gj));
+        IO<S>::store1(at_out_g<S>(p, gi, gj), T::ev(x, k, err, 0));
+      }
+    }
+  if (err) atomicOr(p.err_flag, err);
+}
+
 }  // namespace coot

@@ -85,3 +85,8 @@ KT(chk_gemm_tc_bf16_kk, (gemm_tc_kernel<TG, bf16, 2, 1, 0, true, true>))
 KT(chk_gemm_tc_f16_kk, (gemm_tc_kernel<Leaf<0>, f16, 1, 0, 0, true, true>))
 KT(chk_gemm_tc_bf16_mn, (gemm_tc_kernel<TG, bf16, 2, 1, 0, false, false>))
 KT(chk_gemm_tc_bf16_km, (gemm_tc_kernel<Leaf<0>, bf16, 1, 0, 0, true, false>))
+#define KS(name, body) \
+  extern "C" __global__ void __launch_bounds__(256, 2) name(const __grid_constant__ GemmParams p) { body(p); }
+KS(chk_gemm_simt_f32_kk, (gemm_simt_kernel<TG, float, 2, 1, 0, true, true>))
+KS(chk_gemm_simt_f32_mn, (gemm_simt_kernel<Leaf<0>, float, 1, 0, 0, false, false>))
+KS(chk_gemm_simt_f64_km, (gemm_simt_kernel<TG, double, 2, 1, 0, true, false>))

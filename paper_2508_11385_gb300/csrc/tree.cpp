@@ -680,6 +680,14 @@ Program make_program(const Analysis& an, Family fam, bool var_two_pass) {
         }
       }
     }
+  } else if (fam == F_GEMM && an.esz != 2) {
+    // FP32 / FP64 operands: the CUDA-core kernel, 256 threads, 2 blocks per SM
+    wrap("coot_gemm_simt", 256,
+         std::string("gemm_simt_kernel<T_t, S_t, ") + std::to_string(NS) + ", " + std::to_string(NK) + ", " +
+             std::to_string(an.gemm_ps) + ", " + (an.gemm_ka ? "true" : "false") + ", " +
+             (an.gemm_kb ? "true" : "false") + ">",
+         "GemmParams", 2);
+    add("coot_gemm_simt", 1, 1, 256);
   } else if (fam == F_GEMM) {
     // 256 threads, at least 2 blocks per SM (128 registers)
     wrap("coot_gemm", 256,

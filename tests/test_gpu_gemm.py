@@ -1,5 +1,6 @@
 """The matrix product with the tree fused onto it (trans(X)*Y and the other
-operand layouts), BF16/FP16 on the tensor cores with FP32 accumulation, vs
+operand layouts), BF16/FP16 on the tensor cores with FP32 accumulation and
+FP32/FP64 on the CUDA cores, vs
 the FP64 oracle: element by element within the bound k u sum|a b| plus the
 epilogue's node bounds and the rounding to the storage type.  Ragged shapes
 across several 128 x 128 tiles and 32-deep K steps, unaligned operands (the
@@ -94,8 +95,8 @@ def test_edge_cases_and_errors():
     with pytest.raises(ValueError):
         X * Y                                    # 50x40 times 50x30
     with pytest.raises(L.CootError, match="UNSUPPORTED"):
-        F = parity.rand(50, 40, "f32", seed=11)
-        G = parity.rand(50, 30, "f32", seed=12)
+        F = parity.rand(50, 40, "i32", seed=11)
+        G = parity.rand(50, 30, "i32", seed=12)
         coot.evaluate(coot.trans(coot.Mat(F)) * coot.Mat(G))
     with pytest.raises(L.CootError, match="ALIAS"):
         coot.evaluate(coot.trans(X) * Y, out=A[:40, :30])   # out overlaps an operand
@@ -343,3 +344,53 @@ def test_reductions_of_a_product(kind):
         parity.compare_matrix(ref, oracle.evaluate("A " + tok, hy, "bf16"), "bf16", tok)
     else:
         parity.compare_reduction(ref, oracle.evaluate("A " + tok, hy, "bf16"), "bf16", tok)
+
+
+# FP32 / FP64 operands: the CUDA-core kernel, accumulation in the storage type
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("ta,tb", [(True, False), (False, False), (True, True), (False, True)])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_simt_product_every_layout(dtype, ta, tb, shape):
+    m, n, k = shape
+    A = operand(k, m, dtype, 61) if ta else operand(m, k, dtype, 61)
+    B = operand(n, k, dtype, 62) if tb else operand(k, n, dtype, 62)
+    X, Y = coot.Mat(A), coot.Mat(B)
+    out = coot.evaluate((coot.trans(X) if ta else X) * (coot.trans(Y) if tb else Y))
+    torch.cuda.synchronize()
+    assert coot.last_launch()["kernel"] == "coot_gemm_simt"
+    prog = "A" + (" trans" if ta else "") + " B" + (" trans" if tb else "") + " mm"
+    parity.compare_matrix(out, oracle.evaluate(prog, parity.host([A, B]), dtype), dtype, prog)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("epi", ["P #2 * C +", "P C % D - abs sqrt", "P exp"])
+def test_simt_fused_epilogues(dtype, epi):
+    m, n, k = 257, 130, 75
+    A = operand(k, m, dtype, 63, offset=1) * 0.1   # unaligned, strided
+    B = operand(k, n, dtype, 64) * 0.1
+    C = operand(m, n, dtype, 65)
+    D = operand(m, n, dtype, 66)
+    X, Y, Cm, Dm = coot.Mat(A), coot.Mat(B), coot.Mat(C), coot.Mat(D)
+    P = coot.trans(X) * Y
+    e = {"P #2 * C +": lambda: 2 * P + Cm, "P C % D - abs sqrt": lambda: coot.sqrt(coot.abs(P % Cm - Dm)),
+         "P exp": lambda: coot.exp(P)}[epi]()
+    out = coot.evaluate(e)
+    torch.cuda.synchronize()
+    assert coot.last_launch()["kernel"] == "coot_gemm_simt"
+    prog = epi.replace("P", "A trans B mm")
+    parity.compare_matrix(out, oracle.evaluate(prog, parity.host([A, B, C, D]), dtype), dtype, prog)
+
+
+def test_simt_large_sampled():
+    # many 128 x 128 tiles with ragged edges: sampled rows and columns
+    m, n, k = 1100, 700, 333
+    A = operand(m, k, "f32", 67)
+    B = operand(k, n, "f32", 68)
+    out = coot.evaluate(coot.Mat(A) * coot.Mat(B))
+    torch.cuda.synchronize()
+    g = torch.Generator().manual_seed(69)
+    rows = torch.cat([torch.randperm(m, generator=g)[:60], torch.tensor([0, 127, 128, m - 1])]).tolist()
+    cols = torch.cat([torch.randperm(n, generator=g)[:60], torch.tensor([0, 127, 128, n - 1])]).tolist()
+    ri, ci = torch.tensor(rows, device="cuda"), torch.tensor(cols, device="cuda")
+    As, Bs = A[ri].t().contiguous().t(), B[:, ci].contiguous()
+    parity.compare_matrix(out[ri][:, ci], oracle.evaluate("A B mm", parity.host([As, Bs]), "f32"), "f32", "sampled")
