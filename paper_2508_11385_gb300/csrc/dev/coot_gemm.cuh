@@ -525,7 +525,7 @@ __device__ __forceinline__ void gemm_tc_kernel(const GemmParams& gp) {
 //   128 x 128 tile, 4 x 4 for FP64 in 64 x 64) as two halves of rows (and of
 //   columns) half a tile apart, so that each fragment is read from shared
 //   memory as 16-byte vectors with the 16 lanes of a half-warp on adjacent
-//   chunks (no bank conflict).  Per K step of 8, the A and B
+//   chunks (no bank conflict).  Per K step of 16, the A and B
 //   tiles are read from global memory into registers (threads walk the
 //   operand's adjacent dimension, zeros past the edges), stored to shared
 //   memory as [k][row] (rows padded by 4 so the stores of a K-adjacent
@@ -535,7 +535,7 @@ __device__ __forceinline__ void gemm_tc_kernel(const GemmParams& gp) {
 template <class S> struct SimtCfg;
 template <> struct SimtCfg<float> { static constexpr int BM = 128, BN = 128, TM = 8, TN = 8; };
 template <> struct SimtCfg<double> { static constexpr int BM = 64, BN = 64, TM = 4, TN = 4; };
-constexpr int SIMT_BK = 8, SIMT_THREADS = 256;
+constexpr int SIMT_BK = 16, SIMT_THREADS = 256;
 
 __device__ __forceinline__ float simt_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double simt_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
