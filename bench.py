@@ -321,6 +321,41 @@ def run_side(args):
     print(json.dumps({args.only: fn()}))
 
 
+def run_prog(args):
+    """One RPN program alone over the workload's leaves (for profiling): A..F
+    are FP32 n x n; a leaf followed by each_col:n / each_row:n is cut to a
+    column / row.  Default launch configuration (no tuning unless COOT_TUNE
+    is set): `steps` calls timed after `warmup`."""
+    import torch
+
+    from paper_2508_11385_gb300 import workloads
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    stream = torch.cuda.current_stream(dev)
+    lv = workloads.large_trees("f32", n=args.n, n_leaves=6, device=dev)
+    toks = args.prog.split()
+    for i, t in enumerate(toks[:-1]):
+        if len(t) == 1 and "A" <= t <= "F":
+            li = ord(t) - ord("A")
+            if toks[i + 1].startswith("each_col:"):
+                lv[li] = lv[li][:, :1]
+            elif toks[i + 1].startswith("each_row:"):
+                lv[li] = lv[li][:1, :]
+    c = Call(args.prog, lv)
+    sp = stream.cuda_stream
+    for _ in range(args.warmup):
+        c(sp)
+    torch.cuda.synchronize()
+    ms = time_calls(lambda: c(sp), stream, reps=args.steps, warm=0)
+    info = c.info()
+    print(json.dumps({"prog": args.prog, "ms": round(ms, 4), "gbs": round(info["algorithmic_bytes"] / ms / 1e6, 1),
+                      "kernel": info["kernel"], "grid": info["grid"], "block": info["block"]}))
+
+
 def run_gpu(args):
     import torch
 
@@ -1072,7 +1107,11 @@ def main():
     ap.add_argument("--precision-errors", action="store_true",
                     help="also report each precision result's error against the FP64 oracle (slow)")
     ap.add_argument("--only", default=None, help="time one tree of the workload (profiling); implies --quick")
+    ap.add_argument("--prog", default=None, help="time one RPN program over the workload's leaves (profiling)")
     args = ap.parse_args()
+    if args.prog:
+        run_prog(args)
+        return
     if args.only:
         side = ("batched", "adjoint", "precision", "graph_chain", "stats", "gemm")
         if args.only not in [t[0] for t in TREES] + list(side):
