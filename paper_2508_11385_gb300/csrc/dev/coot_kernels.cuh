@@ -60,11 +60,19 @@ template <class S> __device__ __forceinline__ const S* at_slot(const Params& p, 
   if (gen_slot(s)) return (const S*)p.src[s] + (i * p.rs[s] + j * p.ld[s]);
   return at<S>(p.src[s], i, j, p.ld[s]);
 }
-// V consecutive rows of slot s from (i, j), all inside the tree
+// column j of slot s (row 0), and row i of a column of slot s
+template <class S> __device__ __forceinline__ const S* col_of(const Params& p, int s, long long j) {
+  return (const S*)p.src[s] + j * p.ld[s];
+}
+template <class S> __device__ __forceinline__ const S* row_in(const Params& p, int s, const S* col, long long i) {
+  return gen_slot(s) ? col + i * p.rs[s] : col + i;
+}
+// V consecutive rows of slot s from row i of the column that starts at col,
+// all inside the tree
 template <class S, int V, class C>
-__device__ __forceinline__ void load_rows(const Params& p, int s, long long i, long long j, C (&v)[V]) {
+__device__ __forceinline__ void load_rows_at(const Params& p, int s, const S* col, long long i, C (&v)[V]) {
   if (gen_slot(s)) {
-    const S* b = at_slot<S>(p, s, i, j);
+    const S* b = col + i * p.rs[s];
     if (p.rs[s] == 0) {  // a row broadcast: one element for all V rows
       const C x = IO<S>::load1(b);
 #pragma unroll
@@ -74,12 +82,34 @@ __device__ __forceinline__ void load_rows(const Params& p, int s, long long i, l
       for (int l = 0; l < V; ++l) v[l] = IO<S>::load1(b + l * p.rs[s]);
     }
   } else {
-    IO<S>::template load<V>(at<S>(p.src[s], i, j, p.ld[s]), v);
+    IO<S>::template load<V>(col + i, v);
   }
+}
+// V consecutive rows of slot s from (i, j), all inside the tree
+template <class S, int V, class C>
+__device__ __forceinline__ void load_rows(const Params& p, int s, long long i, long long j, C (&v)[V]) {
+  load_rows_at<S, V>(p, s, col_of<S>(p, s, j), i, v);
 }
 template <class S> __device__ __forceinline__ S* at_out_g(const Params& p, long long i, long long j) {
   if (COOT_GM & GM_OUT) return (S*)p.out + (i * p.out_rs + j * p.out_ld);
   return at_out<S>(p.out, i, j, p.out_ld);
+}
+// column j of the output (row 0), and row i of a column of the output
+template <class S> __device__ __forceinline__ S* out_col(const Params& p, long long j) {
+  return (S*)p.out + j * p.out_ld;
+}
+template <class S> __device__ __forceinline__ S* out_row_in(const Params& p, S* col, long long i) {
+  return (COOT_GM & GM_OUT) ? col + i * p.out_rs : col + i;
+}
+// V consecutive rows of the output from row i of the column that starts at col
+template <class S, int V, class C>
+__device__ __forceinline__ void store_rows_at(const Params& p, S* col, long long i, const C (&v)[V]) {
+  if (COOT_GM & GM_OUT) {
+#pragma unroll
+    for (int l = 0; l < V; ++l) IO<S>::store1(col + (i + l) * p.out_rs, v[l]);
+  } else {
+    IO<S>::template store<V>(col + i, v);
+  }
 }
 // V consecutive rows of the output from (i, j)
 template <class S, int V, class C> __device__ __forceinline__ void store_rows(const Params& p, long long i, long long j,
@@ -217,6 +247,32 @@ template <class C, int RED, class A> __device__ __forceinline__ void finish_full
 }
 
 // ---------------------------------------------------------------------------
+// The units of a grid-stride 2-D walk: u = blockIdx.x, blockIdx.x + gridDim.x,
+// ... over units_per_col chunks per column, kept as (column j, chunk r within
+// the column) and advanced by additions (one division per block, not one per
+// unit).  Invariant: u = j * cpc + r with 0 <= r < cpc, so u < cpc * n_cols
+// exactly when j < n_cols.
+// ---------------------------------------------------------------------------
+struct UnitWalk {
+  long long j, r;
+  const long long cpc, qg, rg;
+  __device__ __forceinline__ explicit UnitWalk(long long cpc_)
+      : j((long long)blockIdx.x / cpc_),
+        r((long long)blockIdx.x - j * cpc_),
+        cpc(cpc_),
+        qg((long long)gridDim.x / cpc_),
+        rg((long long)gridDim.x - qg * cpc_) {}
+  __device__ __forceinline__ void next() {
+    j += qg;
+    r += rg;
+    if (r >= cpc) {
+      r -= cpc;
+      ++j;
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
 // str: map (+ full reduction) over n_rows x n_cols, no transposed reads
 // ---------------------------------------------------------------------------
 template <class T, class S, int NS, int NK, int RED, int V, int U, bool OUT>
@@ -235,12 +291,17 @@ __device__ __forceinline__ void str_kernel(const Params& p) {
 #pragma unroll
   for (int l = 0; l < V; ++l) accs[l].init();
   const long long nr = p.n_rows, nc = p.n_cols, cpc = p.units_per_col;
-  const long long units = cpc * nc;
   const long long step = (long long)blockDim.x * V;
   const long long CH = step * U;
-  for (long long u = blockIdx.x; u < units; u += gridDim.x) {
-    const long long j = (nc == 1) ? 0 : u / cpc;
-    const long long i0 = (u - j * cpc) * CH + (long long)threadIdx.x * V;
+  for (UnitWalk walk(cpc); walk.j < nc; walk.next()) {
+    const long long j = walk.j;
+    const long long i0 = walk.r * CH + (long long)threadIdx.x * V;
+    // the unit's column of every slot and of the output, formed once
+    const S* col[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) col[s] = col_of<S>(p, s, j);
+    S* ocol = nullptr;
+    if constexpr (OUT) ocol = out_col<S>(p, j);
     Vals<C, NS, V> x[U];
     bool full[U];
 #pragma unroll
@@ -249,12 +310,12 @@ __device__ __forceinline__ void str_kernel(const Params& p) {
       full[g] = (i + V <= nr);
       if (full[g]) {
 #pragma unroll
-        for (int s = 0; s < NS; ++s) load_rows<S, V>(p, s, i, j, x[g].v[s]);
+        for (int s = 0; s < NS; ++s) load_rows_at<S, V>(p, s, col[s], i, x[g].v[s]);
       } else {
 #pragma unroll
         for (int s = 0; s < NS; ++s)
 #pragma unroll
-          for (int l = 0; l < V; ++l) x[g].v[s][l] = (i + l < nr) ? IO<S>::load1(at_slot<S>(p, s, i + l, j)) : C(0);
+          for (int l = 0; l < V; ++l) x[g].v[s][l] = (i + l < nr) ? IO<S>::load1(row_in<S>(p, s, col[s], i + l)) : C(0);
       }
     }
 #pragma unroll
@@ -277,13 +338,13 @@ __device__ __forceinline__ void str_kernel(const Params& p) {
 #pragma unroll
           for (int l = 0; l < V; ++l) y[l] = eval_elem<T, RED>(x[g], k, err, l, accs[l], csq, i + l + j * nr);
         }
-        if constexpr (OUT) store_rows<S, V>(p, i, j, y);
+        if constexpr (OUT) store_rows_at<S, V>(p, ocol, i, y);
       } else {
 #pragma unroll
         for (int l = 0; l < V; ++l)
           if (i + l < nr) {
             C y = eval_elem<T, RED>(x[g], k, err, l, accs[l], csq, i + l + j * nr);
-            if constexpr (OUT) IO<S>::store1(at_out_g<S>(p, i + l, j), y);
+            if constexpr (OUT) IO<S>::store1(out_row_in<S>(p, ocol, i + l), y);
           }
       }
     }
@@ -1167,12 +1228,11 @@ __device__ __forceinline__ void adj_kernel(const Params& p) {
   u32 err = 0;
   const C g0 = (C)((double)(*(const C*)p.upstream) * p.grad_mult);
   const long long nr = p.n_rows, nc = p.n_cols, cpc = p.units_per_col;
-  const long long units = cpc * nc;
   const long long step = (long long)blockDim.x * V;
   const long long CH = step * U;
-  for (long long u = blockIdx.x; u < units; u += gridDim.x) {
-    const long long j = (nc == 1) ? 0 : u / cpc;
-    const long long i0 = (u - j * cpc) * CH + (long long)threadIdx.x * V;
+  for (UnitWalk walk(cpc); walk.j < nc; walk.next()) {
+    const long long j = walk.j;
+    const long long i0 = walk.r * CH + (long long)threadIdx.x * V;
     Vals<C, NS, V> x[U];
     bool full[U];
 #pragma unroll
