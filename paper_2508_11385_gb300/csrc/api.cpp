@@ -195,9 +195,13 @@ void shape_launch(coot_ctx* ctx, const cg::Analysis& an, const cg::Choice& ch, c
   p.n_rows = R;
   p.n_cols = C;
   if (ch.fam == cg::F_STR || ch.fam == cg::F_ADJ) {
-    const int64_t chunk = (int64_t)block * k.vec * k.unroll;
+    // str: chunks of block * vec rows per column, a unit is `unroll`
+    // consecutive chunks in column-major order (it may span columns); adj: a
+    // unit is one chunk of block * vec * unroll rows of one column
+    const bool str = ch.fam == cg::F_STR;
+    const int64_t chunk = (int64_t)block * k.vec * (str ? 1 : k.unroll);
     p.units_per_col = std::max<int64_t>(1, ceil_div(R, chunk));
-    const int64_t units = p.units_per_col * C;
+    const int64_t units = str ? ceil_div(p.units_per_col * C, k.unroll) : p.units_per_col * C;
     L->grid = (int)std::max<int64_t>(1, std::min(units, resident));
     L->partial_bytes = (size_t)L->grid * ab;
     L->tickets = 1;

@@ -247,21 +247,22 @@ template <class C, int RED, class A> __device__ __forceinline__ void finish_full
 }
 
 // ---------------------------------------------------------------------------
-// The units of a grid-stride 2-D walk: u = blockIdx.x, blockIdx.x + gridDim.x,
-// ... over units_per_col chunks per column, kept as (column j, chunk r within
-// the column) and advanced by additions (one division per block, not one per
-// unit).  Invariant: u = j * cpc + r with 0 <= r < cpc, so u < cpc * n_cols
-// exactly when j < n_cols.
+// The units of a grid-stride 2-D walk over cpc chunks per column, each unit
+// `per` consecutive chunks in column-major chunk order: the first chunk of
+// unit u is q = u * per, for u = blockIdx.x, blockIdx.x + gridDim.x, ...  It
+// is kept as (column j, chunk r within the column) and advanced by additions
+// (one division per block, not one per unit).  Invariant: q = j * cpc + r
+// with 0 <= r < cpc, so q < cpc * n_cols exactly when j < n_cols.
 // ---------------------------------------------------------------------------
 struct UnitWalk {
   long long j, r;
   const long long cpc, qg, rg;
-  __device__ __forceinline__ explicit UnitWalk(long long cpc_)
-      : j((long long)blockIdx.x / cpc_),
-        r((long long)blockIdx.x - j * cpc_),
+  __device__ __forceinline__ UnitWalk(long long cpc_, long long per = 1)
+      : j((long long)blockIdx.x * per / cpc_),
+        r((long long)blockIdx.x * per - j * cpc_),
         cpc(cpc_),
-        qg((long long)gridDim.x / cpc_),
-        rg((long long)gridDim.x - qg * cpc_) {}
+        qg((long long)gridDim.x * per / cpc_),
+        rg((long long)gridDim.x * per - qg * cpc_) {}
   __device__ __forceinline__ void next() {
     j += qg;
     r += rg;
@@ -290,24 +291,34 @@ __device__ __forceinline__ void str_kernel(const Params& p) {
   A accs[V];
 #pragma unroll
   for (int l = 0; l < V; ++l) accs[l].init();
+  // chunks of `step` rows, cpc of them per column; a unit is U consecutive
+  // chunks in column-major order, so a unit continues into the next column
+  // when columns are shorter than U chunks and every thread keeps U vector
+  // loads in flight whatever the column length
   const long long nr = p.n_rows, nc = p.n_cols, cpc = p.units_per_col;
   const long long step = (long long)blockDim.x * V;
-  const long long CH = step * U;
-  for (UnitWalk walk(cpc); walk.j < nc; walk.next()) {
-    const long long j = walk.j;
-    const long long i0 = walk.r * CH + (long long)threadIdx.x * V;
-    // the unit's column of every slot and of the output, formed once
+  const long long tv = (long long)threadIdx.x * V;
+  for (UnitWalk walk(cpc, U); walk.j < nc; walk.next()) {
+    // the current chunk's column of every slot and of the output: formed once
+    // per unit, then moved one column on when the chunks wrap
+    long long j = walk.j, r = walk.r;
     const S* col[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) col[s] = col_of<S>(p, s, j);
-    S* ocol = nullptr;
-    if constexpr (OUT) ocol = out_col<S>(p, j);
+    S* oc = nullptr;
+    if constexpr (OUT) oc = out_col<S>(p, j);
     Vals<C, NS, V> x[U];
-    bool full[U];
+    bool valid[U], full[U];
+    long long ig[U], jg[U];
+    S* og[U];
 #pragma unroll
     for (int g = 0; g < U; ++g) {
-      const long long i = i0 + g * step;
-      full[g] = (i + V <= nr);
+      const long long i = r * step + tv;
+      valid[g] = (j < nc);
+      full[g] = valid[g] && (i + V <= nr);
+      ig[g] = i;
+      jg[g] = j;
+      og[g] = oc;
       if (full[g]) {
 #pragma unroll
         for (int s = 0; s < NS; ++s) load_rows_at<S, V>(p, s, col[s], i, x[g].v[s]);
@@ -315,12 +326,20 @@ __device__ __forceinline__ void str_kernel(const Params& p) {
 #pragma unroll
         for (int s = 0; s < NS; ++s)
 #pragma unroll
-          for (int l = 0; l < V; ++l) x[g].v[s][l] = (i + l < nr) ? IO<S>::load1(row_in<S>(p, s, col[s], i + l)) : C(0);
+          for (int l = 0; l < V; ++l)
+            x[g].v[s][l] = (valid[g] && i + l < nr) ? IO<S>::load1(row_in<S>(p, s, col[s], i + l)) : C(0);
+      }
+      if (g + 1 < U && ++r == cpc) {  // the next chunk starts the next column
+        r = 0;
+        ++j;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) col[s] += p.ld[s];
+        if constexpr (OUT) oc += p.out_ld;
       }
     }
 #pragma unroll
     for (int g = 0; g < U; ++g) {
-      const long long i = i0 + g * step;
+      const long long i = ig[g];
       if (full[g]) {
         C y[V];
         if constexpr (sizeof(S) == 2 && red_additive(RED)) {
@@ -336,15 +355,15 @@ __device__ __forceinline__ void str_kernel(const Params& p) {
           accs[g % V].add(c[0]);
         } else {
 #pragma unroll
-          for (int l = 0; l < V; ++l) y[l] = eval_elem<T, RED>(x[g], k, err, l, accs[l], csq, i + l + j * nr);
+          for (int l = 0; l < V; ++l) y[l] = eval_elem<T, RED>(x[g], k, err, l, accs[l], csq, i + l + jg[g] * nr);
         }
-        if constexpr (OUT) store_rows_at<S, V>(p, ocol, i, y);
-      } else {
+        if constexpr (OUT) store_rows_at<S, V>(p, og[g], i, y);
+      } else if (valid[g]) {
 #pragma unroll
         for (int l = 0; l < V; ++l)
           if (i + l < nr) {
-            C y = eval_elem<T, RED>(x[g], k, err, l, accs[l], csq, i + l + j * nr);
-            if constexpr (OUT) IO<S>::store1(out_row_in<S>(p, ocol, i + l), y);
+            C y = eval_elem<T, RED>(x[g], k, err, l, accs[l], csq, i + l + jg[g] * nr);
+            if constexpr (OUT) IO<S>::store1(out_row_in<S>(p, og[g], i + l), y);
           }
       }
     }
