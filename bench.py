@@ -317,8 +317,24 @@ def run_side(args):
     fn = {"batched": lambda: bench_batched(args, dev, stream), "adjoint": lambda: bench_adjoint(dev, stream),
           "precision": lambda: bench_precision(dev, stream, errors=args.precision_errors),
           "graph_chain": lambda: bench_graph(dev, stream), "stats": lambda: bench_stats(args, dev, stream),
-          "gemm": lambda: bench_gemm(args, dev, stream)}[args.only]
+          "gemm": lambda: bench_gemm(args, dev, stream), "e2e": lambda: bench_e2e(args, dev, stream)}[args.only]
     print(json.dumps({args.only: fn()}))
+
+
+def bench_e2e(args, dev, stream):
+    """The end-to-end measurement of the headline step alone (the trees'
+    calls prepared and tuned first, untimed)."""
+    import torch
+
+    from paper_2508_11385_gb300 import workloads
+
+    leaves = workloads.large_trees("f32", n=args.n, device=dev)
+    calls = [(name, prog, depth, Call(prog, leaves, True)) for name, prog, depth in TREES]
+    for _ in range(2):
+        for _, _, _, c in calls:
+            c(stream.cuda_stream)
+    torch.cuda.synchronize()
+    return run_e2e(calls, leaves, stream, max(2, min(args.steps, 5)), dev, args.h2d_streams)
 
 
 def run_prog(args):
@@ -462,7 +478,8 @@ def run_gpu(args):
         extras = run_extras(args, leaves, calls, per_tree_ms, bytes_per, dev, stream, peak)
 
     # end to end through host buffers: H2D of each tree's operands, eval, D2H of its result
-    e2e = run_e2e(calls, leaves, stream, max(2, min(args.steps, 5)), dev) if rank == 0 and not args.quick else None
+    e2e = (run_e2e(calls, leaves, stream, max(2, min(args.steps, 5)), dev, args.h2d_streams)
+           if rank == 0 and not args.quick else None)
 
     out = {
         "metric": METRIC,
@@ -549,13 +566,14 @@ def time_calls(fn, stream, reps=10, warm=2, flush=None):
     return statistics.median(ts)
 
 
-def run_e2e(calls, leaves, stream, reps, dev):
+def run_e2e(calls, leaves, stream, reps, dev, h2d_streams=1):
     """Every tree of every step through host buffers: H2D of its operands from
     pinned host memory, the fused C-ABI call, D2H of its result.  Two device
     copies of the operands and of the prepared calls alternate, so the next
-    tree's operands move host->device (one copy stream) while the current tree
-    runs (the bench stream) and the previous result moves device->host (a
-    third stream); events order each buffer's reuse."""
+    tree's operands move host->device (on `h2d_streams` copy streams, the
+    operands dealt out in turn) while the current tree runs (the bench
+    stream) and the previous result moves device->host (one more stream);
+    events order each buffer's reuse."""
     import torch
 
     # column-major device matrices are transposes of contiguous buffers: copy
@@ -579,24 +597,28 @@ def run_e2e(calls, leaves, stream, reps, dev):
     for c in sets[1][1]:  # the second set's calls prepared once, untimed
         c(sp)
     torch.cuda.synchronize()
-    s_h2d, s_d2h = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    s_h2ds = [torch.cuda.Stream(device=dev) for _ in range(max(1, h2d_streams))]
+    s_d2h = torch.cuda.Stream(device=dev)
     seq = [i for _ in range(reps) for i in range(len(calls))]
     kdone, ddone = [None] * len(seq), [None] * len(seq)
     bytes_alg = h2d = d2h = 0
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
-    s_h2d.wait_stream(stream)
+    for s_h2d in s_h2ds:
+        s_h2d.wait_stream(stream)
     for q, i in enumerate(seq):
         name = calls[i][0]
         lv, cs = sets[q % 2]
         c = cs[i]
-        if q >= 2:
-            s_h2d.wait_event(kdone[q - 2])  # this set's operands were read by step q - 2
-        with torch.cuda.stream(s_h2d):
-            for li in name_to_leaf[name]:
+        for k, li in enumerate(name_to_leaf[name]):
+            s_h2d = s_h2ds[k % len(s_h2ds)]
+            if q >= 2:
+                s_h2d.wait_event(kdone[q - 2])  # this set's operands were read by step q - 2
+            with torch.cuda.stream(s_h2d):
                 dense(lv[li]).copy_(host[li], non_blocking=True)
-                h2d += host[li].numel() * host[li].element_size()
-        stream.wait_event(s_h2d.record_event())
+            h2d += host[li].numel() * host[li].element_size()
+        for s_h2d in s_h2ds:
+            stream.wait_event(s_h2d.record_event())
         if q >= 2:
             stream.wait_event(ddone[q - 2])  # this set's results were read by step q - 2
         c(sp)
@@ -608,7 +630,8 @@ def run_e2e(calls, leaves, stream, reps, dev):
             h_out[name].copy_(r, non_blocking=True)
             d2h += r.numel() * r.element_size()
         ddone[q] = s_d2h.record_event()
-    stream.wait_stream(s_h2d)
+    for s_h2d in s_h2ds:
+        stream.wait_stream(s_h2d)
     stream.wait_stream(s_d2h)
     b.record(stream)
     torch.cuda.synchronize()
@@ -617,9 +640,11 @@ def run_e2e(calls, leaves, stream, reps, dev):
     torch.cuda.empty_cache()
     return {"value": round(bytes_alg / sec / 1e9, 1), "unit": "GB/s", "h2d_bytes_per_step": h2d // reps,
             "d2h_bytes_per_step": d2h // reps, "steps": reps,
+            "h2d_streams": len(s_h2ds),
             "note": "per tree: pinned host->device copy of its operands, the fused call, device->host copy of Y or "
-                    "the reduction, pipelined over two device buffer sets on three streams; value = algorithmic "
-                    "bytes / wall time of the whole sequence"}
+                    "the reduction, pipelined over two device buffer sets (operand copies on %d stream(s), the "
+                    "calls on the bench stream, result copies on one more); value = algorithmic bytes / wall "
+                    "time of the whole sequence" % len(s_h2ds)}
 
 
 def run_extras(args, leaves, calls, per_tree_ms, bytes_per, dev, stream, peak):
@@ -1123,6 +1148,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--precision-errors", action="store_true",
                     help="also report each precision result's error against the FP64 oracle (slow)")
+    ap.add_argument("--h2d-streams", type=int, default=1,
+                    help="copy streams for the host->device operand copies of the end-to-end measurement")
     ap.add_argument("--only", default=None, help="time one tree of the workload (profiling); implies --quick")
     ap.add_argument("--prog", default=None, help="time one RPN program over the workload's leaves (profiling)")
     args = ap.parse_args()
@@ -1130,7 +1157,7 @@ def main():
         run_prog(args)
         return
     if args.only:
-        side = ("batched", "adjoint", "precision", "graph_chain", "stats", "gemm")
+        side = ("batched", "adjoint", "precision", "graph_chain", "stats", "gemm", "e2e")
         if args.only not in [t[0] for t in TREES] + list(side):
             ap.error("--only: one of %s" % ", ".join([t[0] for t in TREES] + list(side)))
         args.quick = True
