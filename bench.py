@@ -473,13 +473,13 @@ def run_gpu(args):
                 "tree": dom, "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                 else "fallback 6.8 TB/s"}
 
-    extras = {}
-    if rank == 0 and not args.quick:
-        extras = run_extras(args, leaves, calls, per_tree_ms, bytes_per, dev, stream, peak)
-
     # end to end through host buffers: H2D of each tree's operands, eval, D2H of its result
     e2e = (run_e2e(calls, leaves, stream, max(2, min(args.steps, 5)), dev, args.h2d_streams)
            if rank == 0 and not args.quick else None)
+
+    extras = {}
+    if rank == 0 and not args.quick:
+        extras = run_extras(args, leaves, calls, per_tree_ms, bytes_per, dev, stream, peak)
 
     out = {
         "metric": METRIC,
