@@ -78,3 +78,16 @@ def test_cpu_baseline_is_bounded_and_labelled(orc, budget):
     assert time.time() - t0 < 60
     assert out["kind"] == "oracle" and out["cores"] == 1 and out["unit"] == "GB/s"
     assert out["value"] > 0 and "256x256" in out["sample"]
+
+
+def test_algorithmic_bytes_of_the_workload_trees():
+    # distinct operand bytes read plus bytes written, FP32 at 8192 x 8192:
+    # axpy 12N, A%B+C 16N, trans(A)+B 12N, exp_div 16N, the depth ladder
+    # 20N / 24N / 24N / 24N / 28N, the column sums 8N + 4 n, the view 4 * 4096^2 + 4
+    n = 8192
+    N = n * n
+    want = {"axpy": 12 * N, "schur_plus": 16 * N, "trans_plus": 12 * N, "exp_div": 16 * N,
+            "colsum_sq": 8 * N + 4 * n, "accu_submat": 4 * 4096 * 4096 + 4, "L4": 20 * N, "L5": 24 * N,
+            "L6": 24 * N, "L7": 24 * N, "L8": 28 * N}
+    got = {name: bench.algorithmic_bytes(prog, n, 4) for name, prog, _ in bench.TREES}
+    assert got == want
