@@ -57,3 +57,32 @@ def test_planted_mistake_fails_the_pins(tmp_path, name, old, new):
                         "tests/test_oracle_pins.py"], cwd=work, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, "the pins did not catch the planted mistake '%s'" % name
     assert "failed" in r.stdout
+
+
+# mistakes whose effect on a value the hand-written worked cases in
+# tests/golden/ fix (the others change only error bounds, gradients, or
+# results of exact integer sums): those cases alone must catch them too
+GOLDEN_CATCHES = ["trans index", "var normalisation", "submat offsets", "mean divisor", "extreme keeps the last tie",
+                  "product exponent", "cumsum default direction", "diag offset direction", "each_row shape",
+                  "matmul operand index"]
+
+
+@pytest.mark.parametrize("name", GOLDEN_CATCHES)
+def test_planted_mistake_fails_the_worked_cases(tmp_path, name):
+    old, new = [(o, n) for m, o, n in MUTATIONS if m == name][0]
+    src = open(os.path.join(ROOT, "oracle", "oracle.c")).read()
+    assert src.count(old) == 1, "mutation anchor not found: " + name
+    work = tmp_path / "repo"
+    (work / "oracle").mkdir(parents=True)
+    for f in ("oracle.h", "__init__.py"):
+        shutil.copy(os.path.join(ROOT, "oracle", f), work / "oracle" / f)
+    (work / "oracle" / "oracle.c").write_text(src.replace(old, new))
+    (work / "tests").mkdir()
+    for f in ("conftest.py", "golden_cases.py", "test_golden.py"):
+        shutil.copy(os.path.join(ROOT, "tests", f), work / "tests" / f)
+    shutil.copytree(os.path.join(ROOT, "tests", "golden"), work / "tests" / "golden")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider", "tests/test_golden.py"],
+                       cwd=work, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, "the worked cases did not catch the planted mistake '%s'" % name
+    assert "failed" in r.stdout
+
