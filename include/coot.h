@@ -58,7 +58,11 @@ typedef enum {
   COOT_ERR_OOM = 6,          /* device allocation failed                    */
   COOT_ERR_CUDA = 7,         /* a CUDA runtime call failed                  */
   COOT_ERR_DEVICE_FLAG = 8,  /* a kernel raised a device-side error flag    */
-  COOT_ERR_TIMEOUT = 9,      /* reserved: no kernel here waits on anything  */
+  COOT_ERR_TIMEOUT = 9,      /* reserved; no call returns it: the one kernel
+                                that waits (the tcgen05 GEMM, on its own
+                                mbarriers) bounds every wait and reports a
+                                wait that ran out as device flag
+                                COOT_FLAG_WAIT_TIMEOUT instead              */
   COOT_ERR_UNSUPPORTED = 10  /* valid request outside what is implemented   */
 } coot_status;
 
@@ -192,10 +196,17 @@ typedef struct coot_batch coot_batch;
 typedef struct coot_graph coot_graph;
 
 /* ---- context -------------------------------------------------------------
- * coot_ctx_create: bind a context to CUDA device `device` (Sec. 2, coot_init
- * picks the device).  The context owns the per-tree kernel cache (in memory
- * and on disk under $COOT_CACHE_DIR, default ~/.cache/cootgb), the tuning
- * cache and a device workspace that grows on demand.  Flags: */
+ * coot_ctx_create: bind a context to CUDA device `device`.  Defined by Sec. 2
+ * (Fig. coot_init): a program optionally picks the backend and the GPU once,
+ * at start-up, and may ask for information to be printed; here the backend is
+ * always CUDA on sm_103a, `device` is the CUDA device ID and COOT_CTX_LOG is
+ * the print-information switch.  The context owns the per-tree kernel cache
+ * (in memory and on disk under $COOT_CACHE_DIR, default ~/.cache/cootgb; the
+ * cache of run-time compiled kernels is Sec. 4's third difference), the
+ * tuning cache and a device workspace that grows on demand.  Returns
+ * COOT_ERR_CUDA when the device cannot be used; coot_ctx_destroy releases
+ * what the context owns (never caller memory) after synchronising its
+ * device.  Flags: */
 #define COOT_CTX_TUNE 1u          /* autotune launch configs on first use    */
 #define COOT_CTX_NO_DISK_CACHE 2u /* keep compiled kernels in memory only    */
 #define COOT_CTX_LOG 4u           /* print JIT / cache / tuning decisions    */
@@ -204,8 +215,15 @@ COOT_API coot_status coot_ctx_create(int device, unsigned flags, coot_ctx** out)
 COOT_API coot_status coot_ctx_destroy(coot_ctx* ctx);
 
 /* ---- fused evaluation ----------------------------------------------------
- * Evaluates `tree` over `leaves` in one kernel launch (two for R_VAR and
- * R_STDDEV: the second pass reads the first pass's means):
+ * Defined by Sec. 3 (delayed evaluation): an expression is a tree of Op /
+ * eOp / Glue / eGlue types that is evaluated only when it is assigned, and
+ * the whole tree is analysed to pick the fewest GPU calls; Sec. 4 (fourth
+ * difference) names the alternative this replaces -- a chain of calls to
+ * predefined kernels -- and Sec. 7 announces kernels generated per expression
+ * as follow-up work.  coot_eval is that assignment: it evaluates `tree` over
+ * `leaves` in one kernel launch (two for R_VAR and R_STDDEV: the second pass
+ * reads the first pass's means); the reductions are Sec. 2's sums and
+ * statistics functions:
  *   out     (nullable) receives the element-wise result Y, in the leaves'
  *           dtype; it may alias a leaf only when every read of that leaf is
  *           a full, untransposed read with out's exact layout (B += 3*A form);
@@ -228,7 +246,11 @@ COOT_API coot_status coot_eval_unfused(coot_ctx* ctx, const coot_tree* tree, con
                               coot_stream stream);
 
 /* JIT-compile (and, with COOT_CTX_TUNE, autotune) the kernel for this call
- * without writing to out or red_out. */
+ * without writing to out or red_out.  Defined by Sec. 4 (third difference):
+ * GPU kernels are compiled at run time for the device that is found and
+ * cached, a one-time start-up cost that Sec. 5 leaves out of every timing;
+ * coot_warmup pays it ahead of time (and must precede a stream capture).
+ * Errors as coot_eval; nothing is launched. */
 COOT_API coot_status coot_warmup(coot_ctx* ctx, const coot_tree* tree, const coot_mat* leaves, int32_t n_leaves,
                         const coot_mat* out, coot_reduce red);
 
@@ -260,6 +282,10 @@ COOT_API coot_status coot_gemm_eval(coot_ctx* ctx, const coot_mat* A, int32_t tr
                                     const coot_mat* out, coot_stream stream);
 
 /* ---- adjoint ---------------------------------------------------------------
+ * The paper defines no gradient; Sec. 7 names the numerical optimisation
+ * library ensmallen and the machine-learning library mlpack as the next users
+ * of these expressions, and their optimisers consume the gradient of a scalar
+ * loss written as such an expression -- this entry point computes it.
  * For a scalar loss L = red(tree) with red.kind R_ACCU, R_SUM (dim -1) or
  * R_MEAN (dim -1), writes grads[i] = upstream * dL/dleaves[i] for every i
  * whose grads[i].data is non-NULL (same shape/dtype as the leaf; F32/F64).
@@ -272,6 +298,10 @@ COOT_API coot_status coot_eval_adjoint(coot_ctx* ctx, const coot_tree* tree, con
                               const coot_mat* grads, coot_stream stream);
 
 /* ---- batched evaluation ----------------------------------------------------
+ * Sec. 4 (second difference): a GPU is fast only when all of its cores are
+ * busy, so one small matrix per call loses to the CPU below roughly
+ * 1000 x 1000 elements.  Batching many small problems into one launch keeps
+ * the GPU busy without changing any problem's result.
  * Many independent problems of the same tree, each with its own leaf shapes
  * (n_problems * n_leaves coot_mat in `problems`, problem-major, HOST array),
  * evaluated by one persistent kernel that pulls tiles from a work queue.
@@ -293,16 +323,28 @@ COOT_API coot_status coot_eval_batched(coot_ctx* ctx, const coot_tree* tree, int
                               void* red_out, coot_stream stream);
 
 /* ---- CUDA graphs ------------------------------------------------------------
+ * The paper has no graphs; Sec. 3 and Sec. 4 describe a program as the
+ * sequence of GPU calls its assignments generate, issued from host code one
+ * after another.  Recording such a sequence once and replaying it removes
+ * the host's per-call launch cost while the kernels stay the same.
  * coot_graph_begin starts capturing `stream`; the coot_eval calls that follow
  * on it are recorded (their kernels must already be compiled: coot_warmup);
  * coot_graph_end ends the capture and instantiates the graph;
- * coot_graph_launch replays it on a stream. */
+ * coot_graph_launch replays it on a stream.  Errors: COOT_ERR_INVALID for a
+ * NULL context or graph, or capture of the legacy default stream;
+ * COOT_ERR_CUDA when capture, instantiation or replay fails (ending a stream
+ * that is not being captured included); a coot_eval during capture whose
+ * kernel is not compiled yet is refused (COOT_ERR_INVALID) and nothing is
+ * recorded for it. */
 COOT_API coot_status coot_graph_begin(coot_ctx* ctx, coot_stream stream);
 COOT_API coot_status coot_graph_end(coot_ctx* ctx, coot_stream stream, coot_graph** out);
 COOT_API coot_status coot_graph_launch(coot_graph* graph, coot_stream stream);
 COOT_API coot_status coot_graph_destroy(coot_graph* graph);
 
 /* ---- host-side introspection (no GPU needed) ---------------------------------
+ * Sec. 3: an expression's structure is captured as a type, and Sec. 4 (third
+ * difference): the kernels are compiled at run time for the device and
+ * cached.  The signature is the cache key of one expression type here.
  * coot_signature: validate the call and write its canonical signature (the
  * kernel-cache key: dtype, op structure, leaf layout classes, reduction) to
  * buf.  coot_codegen: write the generated CUDA source of the tree's kernel.
@@ -334,13 +376,21 @@ COOT_API coot_status coot_compile(const coot_tree* tree, const coot_mat* leaves,
  * call before any stream capture.  Every call clears the tickets it uses, so
  * a failed earlier call leaves nothing behind; all calls on a device share
  * the array, so calls that can run at the same time on the GPU (different
- * streams without ordering) race -- issue them on one stream.  A matrix with
- * more rows than the tickets cover (4096 x 1024 = 4,194,304 rows; 1,048,576
- * when x is not 16-byte aligned) is rejected with COOT_ERR_UNSUPPORTED. */
+ * streams without ordering) race -- issue them on one stream.  The address
+ * found by the first call is kept for the process: do not call this entry
+ * point on a device after cudaDeviceReset.  x must have adjacent rows
+ * (rs 0 or 1; any ld >= n_rows): rs > 1 (a diagonal or row-strided view) is
+ * COOT_ERR_UNSUPPORTED, rs < 0 COOT_ERR_INVALID.  A matrix with more rows
+ * than the tickets cover (4096 x 1024 = 4,194,304 rows; 1,048,576 when x is
+ * not 16-byte aligned) is rejected with COOT_ERR_UNSUPPORTED. */
 #define COOT_NOALLOC_SCRATCH_BYTES (4u << 20)
 COOT_API coot_status coot_sum_rows_f32_noalloc(const coot_mat* x, int32_t mean, float* out, coot_stream stream);
 
 /* ---- errors and diagnostics --------------------------------------------------
+ * Sec. 2 (Fig. coot_init) has an optional print-information switch and Sec. 4
+ * (last difference) points out that reading device data from the host is a
+ * transfer; errors here are therefore status codes with a host-side message,
+ * and device-side conditions are gathered in one flag word read on demand.
  * coot_check_device_flag: wait for `stream`, read and clear the context's
  * device error flags (bit 0: an INT32 division by zero; bit 1: a bounded
  * wait of the tcgen05 GEMM timed out).  Returns COOT_ERR_DEVICE_FLAG when
@@ -350,7 +400,9 @@ COOT_API coot_status coot_sum_rows_f32_noalloc(const coot_mat* x, int32_t mean, 
 COOT_API coot_status coot_check_device_flag(coot_ctx* ctx, coot_stream stream, uint32_t* flags);
 
 /* Description of the last launch made by coot_eval on this context (kernel
- * family and launch shape, for profiling and the roofline). */
+ * family and launch shape, for profiling and the roofline; Sec. 5 times
+ * whole operations, this reports what one of them launched).  Returns
+ * COOT_ERR_INVALID for a NULL context or info. */
 typedef struct {
   char kernel[64];
   int32_t grid, block;
@@ -360,8 +412,11 @@ typedef struct {
 } coot_launch_info;
 COOT_API coot_status coot_last_launch(coot_ctx* ctx, coot_launch_info* info);
 
-COOT_API const char* coot_last_error(void);            /* thread-local, never NULL */
-COOT_API const char* coot_status_string(coot_status s); /* static string            */
+/* coot_last_error: the message of the calling thread's last failed call
+ * (thread-local, never NULL, valid until that thread's next call).
+ * coot_status_string: a static name for a status code. */
+COOT_API const char* coot_last_error(void);
+COOT_API const char* coot_status_string(coot_status s);
 COOT_API void coot_version(int32_t* major, int32_t* minor);
 
 #ifdef __cplusplus

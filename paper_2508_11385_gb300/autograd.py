@@ -7,7 +7,7 @@ backward, runs one fused adjoint kernel that recomputes the tree's forward
 values per element and sweeps back through the node types, writing every
 input's gradient.  Nothing but the inputs is saved between the passes.  The
 paper's motivation for gradients is the optimisation library built on top of
-it (Sec. 6: ensmallen and mlpack on Bandicoot).
+it (Sec. 7: ensmallen and mlpack being adapted to Bandicoot).
 """
 from __future__ import annotations
 

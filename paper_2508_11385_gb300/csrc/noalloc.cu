@@ -15,10 +15,21 @@
 // library, held until the process exits.  Every call on a device shares it:
 // calls whose work can overlap on the GPU (different streams, or threads
 // without ordering) race on it; calls on one stream are ordered and safe.
+//
+// Its device address is looked up once per device (the first call on it) and
+// kept for the life of the process, so the entry point must not be used on a
+// device after cudaDeviceReset: the reset unloads the module that holds the
+// array and the kept address would no longer be valid.
+//
+// Test hook: with COOT_NOALLOC_POISON_SCRATCH=1 in the environment, the set-up
+// fills the whole array with the byte 0xA5 (a cudaMemset, not an allocation),
+// which stands for tickets and partials left behind by an earlier call that
+// failed part-way; every later call must still give correct sums.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -67,6 +78,12 @@ coot_status setup(int dev) {
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o4, coot_noalloc_row_v4, kBlock, 0)) != cudaSuccess ||
       (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, coot_noalloc_row_v1, kBlock, 0)) != cudaSuccess)
     return cuda_error(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  const char* poison = getenv("COOT_NOALLOC_POISON_SCRATCH");
+  if (poison && poison[0] == '1') {
+    if ((e = cudaMemset(ptr, 0xA5, kScratchBytes)) != cudaSuccess ||
+        (e = cudaDeviceSynchronize()) != cudaSuccess)
+      return cuda_error(e, "cudaMemset (poisoned scratch)");
+  }
   g_sms[dev] = sms;
   g_occ[0][dev] = std::max(o4, 1);
   g_occ[1][dev] = std::max(o1, 1);
@@ -82,6 +99,14 @@ extern "C" coot_status coot_sum_rows_f32_noalloc(const coot_mat* x, int32_t mean
   if (x->dtype != COOT_F32) return set_error(COOT_ERR_DTYPE, "coot_sum_rows_f32_noalloc takes an F32 matrix");
   const int64_t R = x->n_rows, C = x->n_cols;
   if (R < 0 || C < 0) return set_error(COOT_ERR_INVALID, "negative shape");
+  // only adjacent rows (element (i,j) at data[i + j*ld]): the kernel reads V
+  // consecutive elements per thread
+  if (x->rs < 0) return set_error(COOT_ERR_INVALID, "negative row stride %d", (int)x->rs);
+  if (x->rs > 1)
+    return set_error(COOT_ERR_UNSUPPORTED,
+                     "coot_sum_rows_f32_noalloc takes matrices with adjacent rows (rs 0 or 1), not rs = %d; use "
+                     "coot_eval with R_SUM dim 1",
+                     (int)x->rs);
   const int64_t ld = (C > 1) ? x->ld : std::max<int64_t>(x->ld, R);
   if (C > 1 && ld < R) return set_error(COOT_ERR_INVALID, "ld %lld < n_rows %lld", (long long)ld, (long long)R);
   if (R == 0) return COOT_OK;  // no outputs
