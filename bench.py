@@ -258,15 +258,33 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle on a bounded sample
 # ---------------------------------------------------------------------------
-def cpu_baseline(n=2048, budget_s=20.0):
-    import numpy as np
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    import platform
 
+    try:
+        out = subprocess.run(["lscpu"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, timeout=10).stdout.decode()
+        for line in out.splitlines():
+            k, _, v = line.partition(":")
+            if k.strip() in ("Model name", "Model Name") and v.strip():
+                return v.strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            k, _, v = line.partition(":")
+            if k.strip() in ("model name", "Model") and v.strip():
+                return v.strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def _oracle_rate(host, n, budget_s, parallel):
+    """GB/s of the oracle over the workload's trees at n x n (the view scaled
+    with n), repeated until about budget_s of evaluation time."""
     import oracle
-    from paper_2508_11385_gb300 import workloads
 
-    oracle.build()
-    leaves = workloads.large_trees("f32", n=n, device="cpu")
-    host = [workloads.to_numpy_colmajor(t) for t in leaves]
     scale = n / N_MAIN
     done_bytes, t_total, evals = 0, 0.0, 0
     t_start = time.perf_counter()
@@ -276,16 +294,42 @@ def cpu_baseline(n=2048, budget_s=20.0):
                              "submat:%d:%d:%d:%d" % (int(1000 * scale), int(1000 * scale),
                                                     int(4096 * scale), int(4096 * scale)))
             t0 = time.perf_counter()
-            oracle.evaluate(p, host, "f32")
+            oracle.evaluate(p, host, "f32", parallel=parallel)
             t_total += time.perf_counter() - t0
             done_bytes += algorithmic_bytes(p, n, 4)
             evals += 1
         if evals >= len(TREES) and time.perf_counter() - t_start > budget_s * 0.5:
             break
-    return {"value": done_bytes / t_total / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": "the %d trees of the workload at %dx%d FP32 (1/%d of the elements), %d evaluations, "
-                      "single-threaded C FP64 oracle, %.1f s" % (len(TREES), n, n, int(1 / scale ** 2), evals,
-                                                                   t_total)}
+    return done_bytes / t_total / 1e9, evals, t_total
+
+
+def cpu_baseline(n=2048, budget_s=20.0):
+    """The FP64 oracle on a bounded sample of the workload: single-threaded,
+    and (when the OpenMP build exists) with its element-wise loops on all
+    host cores.  `value` and `cores` are the all-core run's when there is one."""
+    import oracle
+    from paper_2508_11385_gb300 import workloads
+
+    oracle.build()
+    leaves = workloads.large_trees("f32", n=n, device="cpu")
+    host = [workloads.to_numpy_colmajor(t) for t in leaves]
+    scale = n / N_MAIN
+    v1, e1, t1 = _oracle_rate(host, n, budget_s / 2, False)
+    out = {"value": v1, "unit": "GB/s", "cores": 1, "kind": "oracle", "host_cpus": os.cpu_count(),
+           "cpu_model": cpu_model(), "single_thread": {"value": v1, "cores": 1, "evals": e1, "seconds": round(t1, 2)}}
+    try:
+        cores = oracle.threads(parallel=True)
+        vp, ep, tp = _oracle_rate(host, n, budget_s / 2, True)
+        out.update({"value": vp, "cores": cores,
+                    "all_cores": {"value": vp, "cores": cores, "evals": ep, "seconds": round(tp, 2)}})
+    except oracle.OracleError as e:
+        out["all_cores"] = {"unavailable": str(e)}
+    out["sample"] = ("the %d trees of the workload at %dx%d FP32 (1/%d of the elements); C FP64 oracle, "
+                     "single-threaded (%d evaluations) and with its element-wise loops on %s threads "
+                     "(reductions sequential, results bit-identical)" % (
+                         len(TREES), n, n, int(1 / scale ** 2), e1, out["cores"] if "all_cores" in out and
+                         "value" in out["all_cores"] else "no"))
+    return out
 
 
 def algorithmic_bytes(program, n, esz):
@@ -320,7 +364,8 @@ def run_side(args):
     fn = {"batched": lambda: bench_batched(args, dev, stream), "adjoint": lambda: bench_adjoint(dev, stream),
           "precision": lambda: bench_precision(dev, stream, errors=args.precision_errors),
           "graph_chain": lambda: bench_graph(dev, stream), "stats": lambda: bench_stats(args, dev, stream),
-          "gemm": lambda: bench_gemm(args, dev, stream), "e2e": lambda: bench_e2e(args, dev, stream)}[args.only]
+          "gemm": lambda: bench_gemm(args, dev, stream), "e2e": lambda: bench_e2e(args, dev, stream),
+          "probe": lambda: bench_probe(dev)}[args.only]
     print(json.dumps({args.only: fn()}))
 
 
@@ -650,6 +695,41 @@ def run_e2e(calls, leaves, stream, reps, dev, h2d_streams=1):
                     "time of the whole sequence" % len(s_h2ds)}
 
 
+def bench_probe(dev):
+    """Arithmetic and memory rates of the device (coot_probe_device: small
+    hand-written kernels timed with CUDA events), in T operations/s and GB/s."""
+    from paper_2508_11385_gb300 import lib as L
+
+    r = L.coot_probe_device(dev.index if dev.index is not None else 0)
+    out = {k: round(r[k] / 1e12, 4) for k in ("f32_add", "f32_fma", "f32_div", "f32_exp", "f64_add", "f64_fma",
+                                             "f64_div", "f64_exp")}
+    out.update({"read_gbs": round(r["read_gbs"], 1), "copy_gbs": round(r["copy_gbs"], 1),
+                "l2_bytes": r["l2_bytes"], "sms": r["sms"], "sm_clock_khz": r["sm_clock_khz"],
+                "buffer_bytes": r["buffer_bytes"],
+                "unit": "T operations/s for f32_* / f64_* (exp: one exp + one FMA per step); GB/s for read/copy",
+                "how": "8 independent chains per thread, grid = SMs x occupancy, best of 3 CUDA-event timings; "
+                       "16-byte vector read / copy over a buffer of 8x L2, best of 5"})
+    return out
+
+
+# FP64 operations per element of a program (the reduction's accumulation
+# included); abs, trans and views use no FP64 arithmetic
+_F64_OPS = {"+": "add", "-": "add", "%": "mul", "*": "mul", "/": "div", "exp": "exp", "square": "mul",
+            "sqrt": "div", "accu": "add", "sum:0": "add", "sum:1": "add"}
+
+
+def f64_alu_bound_ms(program, n_elements, probe):
+    """Time the FP64 pipe needs for `program` over n_elements: the sum over
+    its FP64 operations of n_elements / probed rate (add and mul at the add
+    and FMA rates, div at the division rate, exp at the exp+FMA step rate
+    less one FMA)."""
+    fma = probe["f64_fma"] * 1e12
+    per = {"add": 1 / (probe["f64_add"] * 1e12), "mul": 1 / fma, "div": 1 / (probe["f64_div"] * 1e12),
+           "exp": max(1 / (probe["f64_exp"] * 1e12) - 1 / fma, 0.0)}
+    ops = [_F64_OPS[t] for t in program.split() if t in _F64_OPS]
+    return n_elements * sum(per[o] for o in ops) * 1e3, ops
+
+
 def run_extras(args, leaves, calls, per_tree_ms, bytes_per, dev, stream, peak):
     import torch
 
@@ -659,6 +739,11 @@ def run_extras(args, leaves, calls, per_tree_ms, bytes_per, dev, stream, peak):
 
     sp = stream.cuda_stream
     res = {}
+    try:
+        res["probe"] = probe = bench_probe(dev)
+    except Exception as e:  # reported, not hidden
+        res["probe"] = {"error": repr(e)[:300]}
+        probe = None
     # L2 is overwritten before every timed call of the per-tree comparisons,
     # so that the 64 MiB view is read from HBM as in the headline step
     flush = torch.empty(2 * torch.cuda.get_device_properties(dev).L2_cache_size, dtype=torch.uint8, device=dev)
@@ -688,6 +773,17 @@ def run_extras(args, leaves, calls, per_tree_ms, bytes_per, dev, stream, peak):
             cu = Call(prog, lv, fused=False)
             msu = time_calls(lambda: cu(sp), stream, reps=3, flush=flush)
             d[name] = {"ms": round(ms, 4), "gbs": round(b / ms / 1e6, 1), "unfused_ms": round(msu, 4)}
+            if dt == "f64" and probe is not None:
+                # roofline against the larger of the HBM time and the FP64-pipe time
+                toks = prog.split()
+                sub = [t for t in toks if t.startswith("submat:")]
+                ne = (int(sub[0].split(":")[3]) * int(sub[0].split(":")[4])) if sub else args.n * args.n
+                alu_ms, ops = f64_alu_bound_ms(prog, ne, probe)
+                hbm_ms = b / (peak * 1e6)
+                bound_ms = max(alu_ms, hbm_ms)
+                d[name]["roofline"] = {"bound": "alu" if alu_ms > hbm_ms else "hbm", "bound_ms": round(bound_ms, 4),
+                                       "alu_ms": round(alu_ms, 4), "hbm_ms": round(hbm_ms, 4),
+                                       "frac": round(bound_ms / ms, 4), "f64_ops_per_element": ops}
         res[dt] = d
         del lv
         torch.cuda.empty_cache()
@@ -1102,17 +1198,21 @@ def run_reference(args):
     from paper_2508_11385_gb300 import workloads
 
     oracle.build()
-    n = 1024
+    n = 2048
     scale = n / N_MAIN
     leaves = workloads.large_trees("f32", n=n, device="cpu")
     host = [workloads.to_numpy_colmajor(t) for t in leaves]
+    try:
+        cores, parallel = oracle.threads(parallel=True), True
+    except oracle.OracleError:
+        cores, parallel = 1, False
 
     def step():
         b = 0
         for _, prog, _ in TREES:
             p = prog.replace("submat:1000:1000:4096:4096", "submat:%d:%d:%d:%d" % (
                 int(1000 * scale), int(1000 * scale), int(4096 * scale), int(4096 * scale)))
-            oracle.evaluate(p, host, "f32")
+            oracle.evaluate(p, host, "f32", parallel=parallel)
             b += algorithmic_bytes(p, n, 4)
         return b
 
@@ -1130,8 +1230,10 @@ def run_reference(args):
            "data": "synthetic (same recipe, host-generated)",
            "config": {"workload": "large memory-bound trees, FP32 storage: 6 shapes + depth ladder L4-L8 "
                                   "(bounded sample %dx%d per step)" % (n, n), "trees": [t[0] for t in TREES]},
-           "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                            "sample": "%d steps of the %d trees at %dx%d" % (args.steps, len(TREES), n, n)},
+           "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": cores, "kind": "oracle",
+                            "host_cpus": os.cpu_count(), "cpu_model": cpu_model(),
+                            "sample": "%d steps of the %d trees at %dx%d, element-wise loops on %d thread(s)" % (
+                                args.steps, len(TREES), n, n, cores)},
            "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 

@@ -412,6 +412,26 @@ typedef struct {
 } coot_launch_info;
 COOT_API coot_status coot_last_launch(coot_ctx* ctx, coot_launch_info* info);
 
+/* Arithmetic and memory rates of a device, for the rooflines of kernels that
+ * are not bound by HBM (Sec. 4, first difference: GPUs run 32-bit floating
+ * point much faster than 64-bit, so FP64 trees can be bound by the FP64
+ * pipe).  coot_probe_device runs small kernels on `device` (about a second;
+ * it allocates 1 GiB or 8x the L2 size, whichever is larger, and frees it)
+ * and reports the best of several CUDA-event timings: operations per second
+ * of independent dependency chains per thread (exp: one exp and one FMA per
+ * step), and GB/s of a 16-byte-vector read and copy over buffers larger than
+ * L2.  Returns COOT_ERR_OOM or COOT_ERR_CUDA when the device refuses. */
+typedef struct {
+  double f32_add, f32_fma, f32_div, f32_exp;  /* operations per second */
+  double f64_add, f64_fma, f64_div, f64_exp;
+  double read_gbs, copy_gbs;                  /* copy: bytes read + written */
+  int64_t buffer_bytes;                       /* bytes read per read probe  */
+  int64_t l2_bytes;
+  int32_t sms;
+  int32_t sm_clock_khz;                       /* the device's rated SM clock */
+} coot_probe_result;
+COOT_API coot_status coot_probe_device(int device, coot_probe_result* result);
+
 /* coot_last_error: the message of the calling thread's last failed call
  * (thread-local, never NULL, valid until that thread's next call).
  * coot_status_string: a static name for a status code. */

@@ -21,26 +21,57 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "liborc.so")
+# the same source built with -fopenmp: element-wise loops on all host cores,
+# reductions sequential, results bit-identical to liborc.so
+_OMP_PATH = os.path.join(_HERE, "liborc_omp.so")
 _lock = threading.Lock()
 _lib = None
+_omp = None
 
 DTYPES = {"f32": 0, "f64": 1, "bf16": 2, "f16": 3, "i32": 4}
 _NP_OF = {"f32": np.float32, "f64": np.float64, "bf16": np.uint16, "f16": np.uint16, "i32": np.int32}
 
 
-def build(force: bool = False) -> str:
-    """Compile oracle.c into liborc.so with gcc (no FMA contraction, no fast-math)."""
+def _compile(path, extra) -> None:
     src = os.path.join(_HERE, "oracle.c")
-    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= max(
-        os.path.getmtime(src), os.path.getmtime(os.path.join(_HERE, "oracle.h"))
-    ):
-        return _LIB_PATH
-    tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
+    tmp = path + ".%d.tmp" % os.getpid()
     cmd = ["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
-           "-D_POSIX_C_SOURCE=200809L", "-Wall", "-o", tmp, src, "-lm"]
+           "-D_POSIX_C_SOURCE=200809L", "-Wall", "-Wno-unknown-pragmas"] + extra + ["-o", tmp, src, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
+    os.replace(tmp, path)
+
+
+def _fresh(path) -> bool:
+    src = os.path.join(_HERE, "oracle.c")
+    return os.path.exists(path) and os.path.getmtime(path) >= max(
+        os.path.getmtime(src), os.path.getmtime(os.path.join(_HERE, "oracle.h")))
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liborc.so with gcc (no FMA contraction, no
+    fast-math), and into liborc_omp.so with -fopenmp when the compiler has
+    OpenMP (the multi-core CPU baseline; skipped silently otherwise)."""
+    if force or not _fresh(_LIB_PATH):
+        _compile(_LIB_PATH, [])
+    if force or not _fresh(_OMP_PATH):
+        try:
+            _compile(_OMP_PATH, ["-fopenmp"])
+        except (subprocess.CalledProcessError, OSError):
+            pass
     return _LIB_PATH
+
+
+def _bind(lib):
+    lib.orc_eval.argtypes = [ctypes.c_char_p, ctypes.POINTER(_Mat), ctypes.c_int32,
+                             ctypes.c_int32, ctypes.POINTER(_Res)]
+    lib.orc_eval.restype = ctypes.c_int
+    lib.orc_free.argtypes = [ctypes.POINTER(_Res)]
+    lib.orc_sum_neumaier.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.c_int64]
+    lib.orc_sum_neumaier.restype = ctypes.c_double
+    lib.orc_ulp.argtypes = [ctypes.c_double, ctypes.c_int32]
+    lib.orc_ulp.restype = ctypes.c_double
+    lib.orc_threads.restype = ctypes.c_int
+    return lib
 
 
 class _Mat(ctypes.Structure):
@@ -56,22 +87,24 @@ class _Res(ctypes.Structure):
                 ("err", ctypes.c_char * 256)]
 
 
-def _load():
-    global _lib
+def _load(parallel: bool = False):
+    """The single-threaded build, or with parallel=True the OpenMP build
+    (OracleError when it could not be built)."""
+    global _lib, _omp
     with _lock:
         if _lib is None:
             build()
-            lib = ctypes.CDLL(_LIB_PATH)
-            lib.orc_eval.argtypes = [ctypes.c_char_p, ctypes.POINTER(_Mat), ctypes.c_int32,
-                                     ctypes.c_int32, ctypes.POINTER(_Res)]
-            lib.orc_eval.restype = ctypes.c_int
-            lib.orc_free.argtypes = [ctypes.POINTER(_Res)]
-            lib.orc_sum_neumaier.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.c_int64]
-            lib.orc_sum_neumaier.restype = ctypes.c_double
-            lib.orc_ulp.argtypes = [ctypes.c_double, ctypes.c_int32]
-            lib.orc_ulp.restype = ctypes.c_double
-            _lib = lib
-    return _lib
+            _lib = _bind(ctypes.CDLL(_LIB_PATH))
+        if parallel and _omp is None:
+            if not os.path.exists(_OMP_PATH):
+                raise OracleError("liborc_omp.so is not built (no OpenMP in the C compiler)")
+            _omp = _bind(ctypes.CDLL(_OMP_PATH))
+    return _omp if parallel else _lib
+
+
+def threads(parallel: bool = False) -> int:
+    """Threads the element-wise loops of the chosen build use."""
+    return _load(parallel).orc_threads()
 
 
 class OracleError(RuntimeError):
@@ -110,11 +143,12 @@ def _as_mat(a: np.ndarray, dtype: str):
     return _Mat(a.ctypes.data, DTYPES[dtype], n_rows, n_cols, max(ld, n_rows)), a
 
 
-def evaluate(program: str, leaves, dtype: str, out_dtype: str | None = None) -> Result:
+def evaluate(program: str, leaves, dtype: str, out_dtype: str | None = None, parallel: bool = False) -> Result:
     """Evaluate an RPN ``program`` over host ``leaves`` (all of ``dtype``).
 
-    BF16/FP16 leaves are passed as uint16 bit patterns."""
-    lib = _load()
+    BF16/FP16 leaves are passed as uint16 bit patterns.  parallel=True runs
+    the element-wise loops on all host cores (bit-identical results)."""
+    lib = _load(parallel)
     mats, keep = [], []
     for a in leaves:
         m, held = _as_mat(np.asarray(a), dtype)

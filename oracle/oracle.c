@@ -22,6 +22,12 @@
  *     (modulo 2^64); dot multiplies exactly in int64;
  *   - var uses N-1 (norm_type 0) or N (norm_type 1), two passes; N==1 gives 0;
  *   - norm of a vector is the 2-norm; matrices take the Frobenius norm only.
+ *
+ * Threads: the element-wise loops (every element computed on its own) carry
+ * OpenMP pragmas.  Built with -fopenmp (liborc_omp.so) they run on all host
+ * cores; without it (liborc.so) the pragmas are ignored.  Every reduction is
+ * one sequential pass in either build, so the two builds give bit-identical
+ * values and bounds.
  */
 #include "oracle.h"
 
@@ -29,6 +35,18 @@
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* threads the element-wise loops of this build use */
+int orc_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------ */
 /* helpers                                                             */
@@ -187,6 +205,7 @@ static int load_leaf(ctx_t* cx, const orc_mat* m, val_t* out) {
     snprintf(cx->err, 256, "out of memory");
     return -1;
   }
+#pragma omp parallel for collapse(2) schedule(static)
   for (int64_t j = 0; j < m->n_cols; ++j)
     for (int64_t i = 0; i < m->n_rows; ++i) {
       int64_t s = i + j * m->ld, d = i + j * m->n_rows;
@@ -212,6 +231,7 @@ static int unary(ctx_t* cx, int op, val_t* x, val_t* out) {
   int64_t r = x->r, c = x->c, n = r * c;
   if (op == U_TRANS) {
     if (val_alloc(cx, out, c, r)) return -1;
+#pragma omp parallel for collapse(2) schedule(static)
     for (int64_t j = 0; j < c; ++j)
       for (int64_t i = 0; i < r; ++i) {
         /* trans(X)(j,i) = X(i,j) */
@@ -227,19 +247,22 @@ static int unary(ctx_t* cx, int op, val_t* x, val_t* out) {
   }
   if (val_alloc(cx, out, r, c)) return -1;
   if (cx->is_int) {
+    if (op != U_NEG && op != U_ABS && op != U_SQUARE) {
+      snprintf(cx->err, 256, "exp/log/sqrt are not defined for INT32 trees");
+      return -1;
+    }
+#pragma omp parallel for schedule(static)
     for (int64_t t = 0; t < n; ++t) {
       int64_t a = x->iv[t];
       switch (op) {
         case U_NEG: out->iv[t] = wrap32(-a); break;
         case U_ABS: out->iv[t] = wrap32(a < 0 ? -a : a); break;
-        case U_SQUARE: out->iv[t] = wrap32((int64_t)((uint64_t)a * (uint64_t)a)); break;
-        default:
-          snprintf(cx->err, 256, "exp/log/sqrt are not defined for INT32 trees");
-          return -1;
+        default: out->iv[t] = wrap32((int64_t)((uint64_t)a * (uint64_t)a)); break; /* U_SQUARE */
       }
     }
     return 0;
   }
+#pragma omp parallel for schedule(static)
   for (int64_t t = 0; t < n; ++t) {
     double a = x->v[t], ba = x->b[t], v = 0.0, bv = 0.0;
     switch (op) {
@@ -286,7 +309,7 @@ static int unary(ctx_t* cx, int op, val_t* x, val_t* out) {
 }
 
 /* integer binary op with the INT32 tree semantics */
-static int64_t ibin(ctx_t* cx, int op, int64_t a, int64_t b) {
+static int64_t ibin(int op, int64_t a, int64_t b, int* div0) {
   switch (op) {
     case B_PLUS: return wrap32(a + b);
     case B_MINUS: return wrap32(a - b);
@@ -294,7 +317,7 @@ static int64_t ibin(ctx_t* cx, int op, int64_t a, int64_t b) {
     case B_TIMES: return wrap32((int64_t)((uint64_t)a * (uint64_t)b));
     case B_DIV:
       if (b == 0) {
-        cx->div0 = 1;
+        *div0 = 1;
         return 0;
       }
       return wrap32(a / b); /* C99 division truncates toward zero */
@@ -358,17 +381,20 @@ static int binary(ctx_t* cx, int op, val_t* x, val_t* y, val_t* out) {
   val_t* m = xs ? y : x;
   if (val_alloc(cx, out, m->r, m->c)) return -1;
   int64_t n = m->r * m->c;
+  int div0 = 0;
+#pragma omp parallel for schedule(static) reduction(| : div0)
   for (int64_t t = 0; t < n; ++t) {
     if (cx->is_int) {
       int64_t a = xs ? (int64_t)x->k : x->iv[t];
       int64_t b = ys ? (int64_t)y->k : y->iv[t];
-      out->iv[t] = ibin(cx, op, a, b);
+      out->iv[t] = ibin(op, a, b, &div0);
     } else {
       double a = xs ? x->k : x->v[t], ba = xs ? 0.0 : x->b[t];
       double b = ys ? y->k : y->v[t], bb = ys ? 0.0 : y->b[t];
       fbin(cx, op, a, ba, b, bb, &out->v[t], &out->b[t]);
     }
   }
+  if (div0) cx->div0 = 1;
   return 0;
 }
 
@@ -378,6 +404,7 @@ static int submat(ctx_t* cx, val_t* x, int64_t r0, int64_t c0, int64_t nr, int64
     return -1;
   }
   if (val_alloc(cx, out, nr, nc)) return -1;
+#pragma omp parallel for collapse(2) schedule(static)
   for (int64_t j = 0; j < nc; ++j)
     for (int64_t i = 0; i < nr; ++i) {
       /* submat(i,j) = X(r0+i, c0+j) */
@@ -412,6 +439,7 @@ static int matmul(ctx_t* cx, val_t* x, val_t* y, val_t* out) {
   const int64_t m = x->r, k = x->c, n = y->c;
   if (val_alloc(cx, out, m, n)) return -1;
   const double u = (cx->ct == ORC_F64) ? ldexp(1.0, -53) : ldexp(1.0, -24);
+#pragma omp parallel for collapse(2) schedule(static)
   for (int64_t j = 0; j < n; ++j)
     for (int64_t i = 0; i < m; ++i) {
       double sh = 0.0, sl = 0.0, asum = 0.0, bsum = 0.0;
@@ -472,6 +500,7 @@ static int broadcast_or_diag(ctx_t* cx, int op, int64_t arg, val_t* x, val_t* ou
   }
   if (val_alloc(cx, out, r, c)) return -1;
   const int64_t kr = arg < 0 ? -arg : 0, kc = arg > 0 ? arg : 0;
+#pragma omp parallel for collapse(2) schedule(static)
   for (int64_t j = 0; j < c; ++j)
     for (int64_t i = 0; i < r; ++i) {
       int64_t src;

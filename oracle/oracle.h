@@ -112,6 +112,10 @@ double orc_sum_neumaier(const double* x, int64_t n);
 /* ulp of |x| in the given floating dtype (spacing of that format at x). */
 double orc_ulp(double x, int32_t dtype);
 
+/* Threads the element-wise loops use: 1 in the plain build, the OpenMP
+ * thread count in the -fopenmp build. */
+int orc_threads(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -62,6 +62,13 @@ class coot_launch_info(ctypes.Structure):
                 ("algorithmic_bytes", ctypes.c_int64)]
 
 
+class coot_probe_result(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_double) for f in ("f32_add", "f32_fma", "f32_div", "f32_exp", "f64_add", "f64_fma",
+                                               "f64_div", "f64_exp", "read_gbs", "copy_gbs")] + [
+        ("buffer_bytes", ctypes.c_int64), ("l2_bytes", ctypes.c_int64), ("sms", ctypes.c_int32),
+        ("sm_clock_khz", ctypes.c_int32)]
+
+
 class CootError(RuntimeError):
     def __init__(self, status, message):
         self.status = status
@@ -102,6 +109,7 @@ _SIGS = {
     "coot_sum_rows_f32_noalloc": ([_MP, ctypes.c_int32, _P, _P], _S),
     "coot_check_device_flag": ([_P, _P, ctypes.POINTER(ctypes.c_uint32)], _S),
     "coot_last_launch": ([_P, ctypes.POINTER(coot_launch_info)], _S),
+    "coot_probe_device": ([ctypes.c_int, ctypes.POINTER(coot_probe_result)], _S),
     "coot_last_error": ([], ctypes.c_char_p),
     "coot_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "coot_version": ([ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)], None),
@@ -260,6 +268,12 @@ def coot_last_launch(ctx) -> dict:
     _check(_lib.coot_last_launch(ctx, ctypes.byref(info)))
     return {"kernel": info.kernel.decode(), "grid": info.grid, "block": info.block, "vec": info.vec,
             "unroll": info.unroll, "n_launches": info.n_launches, "algorithmic_bytes": info.algorithmic_bytes}
+
+
+def coot_probe_device(device: int = 0) -> dict:
+    r = coot_probe_result()
+    _check(_lib.coot_probe_device(device, ctypes.byref(r)))
+    return {f: getattr(r, f) for f, _ in coot_probe_result._fields_}
 
 
 def make_tree(nodes):

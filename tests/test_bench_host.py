@@ -76,8 +76,11 @@ def test_cpu_baseline_is_bounded_and_labelled(orc, budget):
     t0 = time.time()
     out = bench.cpu_baseline(n=256, budget_s=budget)
     assert time.time() - t0 < 60
-    assert out["kind"] == "oracle" and out["cores"] == 1 and out["unit"] == "GB/s"
-    assert out["value"] > 0 and "256x256" in out["sample"]
+    assert out["kind"] == "oracle" and out["unit"] == "GB/s" and out["value"] > 0 and "256x256" in out["sample"]
+    assert out["single_thread"]["cores"] == 1 and out["single_thread"]["value"] > 0
+    assert out["host_cpus"] == os.cpu_count() and out["cpu_model"]
+    if "value" in out["all_cores"]:  # the OpenMP build exists
+        assert out["cores"] == out["all_cores"]["cores"] >= 1 and out["value"] == out["all_cores"]["value"]
 
 
 def test_algorithmic_bytes_of_the_workload_trees():
