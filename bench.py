@@ -695,6 +695,42 @@ def run_e2e(calls, leaves, stream, reps, dev, h2d_streams=1):
                     "time of the whole sequence" % len(s_h2ds)}
 
 
+def torch_eager_fn(program, tensors):
+    """The same tree as eager torch calls, one call per op (the RPN program
+    over A..F read as the column-major tensors given)."""
+    import torch
+
+    toks = program.split()
+
+    def run():
+        st = []
+        for tok in toks:
+            if len(tok) == 1 and "A" <= tok <= "H":
+                st.append(tensors[ord(tok) - ord("A")])
+            elif tok.startswith("#"):
+                st.append(float(tok[1:]))
+            elif tok in ("+", "-", "%", "/", "*"):
+                y, x = st.pop(), st.pop()
+                st.append({"+": lambda a, b: a + b, "-": lambda a, b: a - b, "%": lambda a, b: a * b,
+                           "/": lambda a, b: a / b, "*": lambda a, b: a * b}[tok](x, y))
+            elif tok == "trans":
+                st.append(st.pop().t())
+            elif tok in ("exp", "abs", "sqrt", "square", "log"):
+                st.append(getattr(torch, tok)(st.pop()))
+            elif tok.startswith("submat:"):
+                r0, c0, nr, nc = map(int, tok.split(":")[1:])
+                st.append(st.pop()[r0:r0 + nr, c0:c0 + nc])
+            elif tok == "accu":
+                st.append(torch.sum(st.pop()))
+            elif tok == "sum:0":
+                st.append(torch.sum(st.pop(), dim=0))
+            else:
+                raise ValueError(tok)
+        return st[-1]
+
+    return run
+
+
 def bench_probe(dev):
     """Arithmetic and memory rates of the device (coot_probe_device: small
     hand-written kernels timed with CUDA events), in T operations/s and GB/s."""
@@ -757,6 +793,18 @@ def run_extras(args, leaves, calls, per_tree_ms, bytes_per, dev, stream, peak):
     deep = [unf[n]["speedup_fused"] for n, _, d, _ in calls if d >= 4]
     res["unfused"] = {"per_tree": unf, "geomean_speedup_depth_ge4": round(math.exp(sum(map(math.log, deep)) / len(deep)), 2),
                       "min_speedup_depth_ge4": min(deep)}
+    # ---- torch eager: the same ops as torch calls on the same column-major tensors
+    te = {}
+    for name, prog, depth, _ in calls:
+        fn = torch_eager_fn(prog, leaves)
+        ms = time_calls(lambda: fn(), stream, reps=max(5, args.steps // 4), flush=flush)
+        te[name] = {"ms": round(ms, 4), "gbs": round(bytes_per[name] / ms / 1e6, 1),
+                    "speedup_fused": round(ms / per_tree_ms[name], 2), "depth": depth}
+    deep = [te[n]["speedup_fused"] for n, _, d, _ in calls if d >= 4]
+    res["torch_eager"] = {"per_tree": te, "geomean_speedup_depth_ge4": round(math.exp(sum(map(math.log, deep)) / len(deep)), 2),
+                          "note": "each tree as eager torch calls (one kernel per op, temporaries allocated by "
+                                  "torch's caching allocator), L2 overwritten before every timed call"}
+    torch.cuda.empty_cache()
     # ---- FP64 / INT32 variants of the six shapes
     del_names = ["axpy", "schur_plus", "trans_plus", "exp_div", "colsum_sq", "accu_submat"]
     for dt in ("f64", "i32"):
@@ -1262,7 +1310,7 @@ def main():
         run_prog(args)
         return
     if args.only:
-        side = ("batched", "adjoint", "precision", "graph_chain", "stats", "gemm", "e2e")
+        side = ("batched", "adjoint", "precision", "graph_chain", "stats", "gemm", "e2e", "probe")
         if args.only not in [t[0] for t in TREES] + list(side):
             ap.error("--only: one of %s" % ", ".join([t[0] for t in TREES] + list(side)))
         args.quick = True

@@ -1368,12 +1368,55 @@ extern "C" coot_status coot_batch_create(coot_ctx* ctx, const coot_tree* tree, i
     tiles += ntr * ntc;
   }
   begin[n_problems] = tiles;
-  if (tiles >= (1ll << 31)) return set_error(COOT_ERR_UNSUPPORTED, "%lld tiles: at most 2^31 - 1", tiles);
   if (red.kind != COOT_R_NONE) bytes += n_problems * rsize(an0.ct);
+  // the kernel: the flat walk over work items unless COOT_BATCH_KERNEL=tile
+  const char* kenv = getenv("COOT_BATCH_KERNEL");
+  const bool flat = !(kenv && strcmp(kenv, "tile") == 0);
+  if (!flat && tiles >= (1ll << 31)) return set_error(COOT_ERR_UNSUPPORTED, "%lld tiles: at most 2^31 - 1", tiles);
   // owning problem of every tile: one load per tile instead of a search
-  std::vector<int> tile_prob((size_t)tiles);
-  for (int64_t q = 0; q < n_problems; ++q)
-    for (long long t = begin[q]; t < begin[q + 1]; ++t) tile_prob[(size_t)t] = (int)q;
+  std::vector<int> tile_prob(flat ? 0 : (size_t)tiles);
+  if (!flat)
+    for (int64_t q = 0; q < n_problems; ++q)
+      for (long long t = begin[q]; t < begin[q + 1]; ++t) tile_prob[(size_t)t] = (int)q;
+  // flat kernel: cut every problem into rectangles of whole columns (or, for
+  // problems taller than an item, row chunks of one column) with
+  // w * (h | 1) <= BE elements, in problem order
+  std::vector<coot::BatchItem> items;
+  if (flat) {
+    int ntr = 0;
+    for (int s = 0; s < 32; ++s) ntr += (an0.trmask >> s) & 1;
+    const int64_t BE = coot::batchf_elems(ntr, (an0.ct == cg::CT_F64) ? 8 : 4);
+    items.reserve((size_t)n_problems * 2);
+    for (int64_t q = 0; q < n_problems; ++q) {
+      const int64_t r = probs[q].n_rows, c = probs[q].n_cols;
+      const size_t first = items.size();
+      auto push = [&](int64_t i0, int64_t j0, int64_t h, int64_t w) {
+        coot::BatchItem it;
+        it.q = (int)q;
+        it.i0 = (int)i0;
+        it.j0 = (int)j0;
+        it.h = (int)h;
+        it.w = (int)w;
+        it.k = (int)(items.size() - first);
+        it.nk = 0;
+        it.first = (int)first;
+        items.push_back(it);
+      };
+      if (r == 0 || c == 0) {
+        push(0, 0, r, c);  // nothing to walk: writes the empty result
+      } else if ((r | 1) <= BE) {
+        const int64_t w = std::max<int64_t>(1, BE / (r | 1));
+        for (int64_t j0 = 0; j0 < c; j0 += w) push(0, j0, r, std::min(w, c - j0));
+      } else {
+        const int64_t hh = ((BE - 1) % 2) ? BE - 1 : BE - 2;  // odd: h | 1 = h
+        for (int64_t j0 = 0; j0 < c; ++j0)
+          for (int64_t i0 = 0; i0 < r; i0 += hh) push(i0, j0, std::min(hh, r - i0), 1);
+      }
+      for (size_t t = first; t < items.size(); ++t) items[t].nk = (int)(items.size() - first);
+    }
+    if (items.size() >= (size_t)INT32_MAX)
+      return set_error(COOT_ERR_UNSUPPORTED, "%zu work items: at most 2^31 - 1", items.size());
+  }
 
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);
   DeviceGuard g(ctx->device);
@@ -1386,10 +1429,11 @@ extern "C" coot_status coot_batch_create(coot_ctx* ctx, const coot_tree* tree, i
   const size_t o_probs = 0;
   const size_t o_begin = align(o_probs + probs.size() * sizeof(coot::BatchProblem));
   const size_t o_map = align(o_begin + begin.size() * sizeof(long long));
-  const size_t o_done = align(o_map + tile_prob.size() * sizeof(int));
+  const size_t o_items = align(o_map + tile_prob.size() * sizeof(int));
+  const size_t o_done = align(o_items + items.size() * sizeof(coot::BatchItem));
   const size_t o_queue = align(o_done + (size_t)n_problems * sizeof(unsigned));
   const size_t o_part = align(o_queue + 2 * sizeof(unsigned));
-  const size_t total = align(o_part + (size_t)tiles * 8);
+  const size_t total = align(o_part + (size_t)(flat ? (int64_t)items.size() : tiles) * 8);
   coot_batch* b = new coot_batch();
   cudaError_t e = cudaMalloc(&b->dev_mem, total);
   if (e != cudaSuccess) {
@@ -1403,6 +1447,8 @@ extern "C" coot_status coot_batch_create(coot_ctx* ctx, const coot_tree* tree, i
           cudaSuccess ||
       (e = cudaMemcpy(base + o_map, tile_prob.data(), tile_prob.size() * sizeof(int), cudaMemcpyHostToDevice)) !=
           cudaSuccess ||
+      (e = cudaMemcpy(base + o_items, items.data(), items.size() * sizeof(coot::BatchItem),
+                      cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemset(base + o_done, 0, o_part - o_done)) != cudaSuccess) {
     cudaFree(b->dev_mem);
     delete b;
@@ -1410,7 +1456,7 @@ extern "C" coot_status coot_batch_create(coot_ctx* ctx, const coot_tree* tree, i
   }
   b->ctx = ctx;
   b->mod = m;
-  b->kname = "coot_batch";
+  b->kname = flat ? "coot_batchf" : "coot_batch";
   b->n_problems = n_problems;
   b->has_red = red.kind != COOT_R_NONE;
   {
@@ -1421,7 +1467,7 @@ extern "C" coot_status coot_batch_create(coot_ctx* ctx, const coot_tree* tree, i
     const int csize = (an0.ct == cg::CT_F64) ? 8 : 4;
     const int per = 32 * 33 * csize * std::max(ntr, 1);
     const int warps = (ntr == 0) ? 8 : std::max(1, std::min(8, 49152 / per));
-    b->block = 32 * warps;
+    b->block = flat ? coot::BATCHF_BLOCK : 32 * warps;
   }
   b->grid = ctx->sms * occupancy(m, b->kname, b->block);
   b->algorithmic_bytes = bytes;
@@ -1430,6 +1476,8 @@ extern "C" coot_status coot_batch_create(coot_ctx* ctx, const coot_tree* tree, i
   bp.probs = (const coot::BatchProblem*)(base + o_probs);
   bp.tile_begin = (const long long*)(base + o_begin);
   bp.tile_prob = (const int*)(base + o_map);
+  bp.items = (const coot::BatchItem*)(base + o_items);
+  bp.n_items = (long long)items.size();
   bp.n_problems = n_problems;
   bp.n_tiles = tiles;
   // a few tiles per queue pop: fewer atomics, still fine-grained balance

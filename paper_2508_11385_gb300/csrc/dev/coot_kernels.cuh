@@ -1476,4 +1476,202 @@ __device__ __forceinline__ void batch_kernel(const BatchParams bp) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// batchf: persistent kernel over work items (rectangles of one problem each,
+// see BatchItem), one block per item at a time.  The block first copies the
+// item's block of every transposed slot into shared memory (coalesced runs
+// along the source's columns, stored with an odd row stride so that both the
+// stores and the later reads are free of bank conflicts), then walks the
+// item's elements in column-major order -- consecutive threads on
+// consecutive rows, so direct slots and the output are read and written in
+// coalesced runs, U elements per thread in flight.  The block's sum of the
+// item is one partial; a problem with one item writes its result directly,
+// otherwise the block that completes the problem (a per-problem counter)
+// combines the partials in item order.  The next item is popped from the
+// queue before the current one is worked on.
+// ---------------------------------------------------------------------------
+constexpr int BATCHF_U = 4;
+
+// The element walk of one item.  Thread tid takes elements e = tid + NB u in
+// column-major order of the item (row i = e % h, column j = e / h, advanced by
+// additions).  CONTIG: every direct slot and the output hold the item's
+// columns back to back (column stride h, first row 0), so element e of a slot
+// is base + e; otherwise each access forms (i0 + i) + (j0 + j) ld.
+template <bool CONTIG, class T, class S, int NS, int TRMASK, bool RED, class C, class K, class A, class Q>
+__device__ __forceinline__ void batchf_walk(const BatchParams& bp, const S* const (&src)[NS], const long long (&ld)[NS],
+                                            S* out, long long out_ld, int i0, int j0, int h, int n, int sst,
+                                            const C* stage, const K& k, A& acc, const Q& csq, u32& err) {
+  constexpr int NB = BATCHF_BLOCK;
+  constexpr int BE = batchf_elems(popc<TRMASK>::value, (int)sizeof(C));
+  const int di = NB % h, dj = NB / h;
+  int e = threadIdx.x, i = e % h, j = e / h;
+  for (; e < n; e += BATCHF_U * NB) {
+    Vals<C, NS, BATCHF_U> x;
+    int ig[BATCHF_U], jg[BATCHF_U];
+#pragma unroll
+    for (int g = 0; g < BATCHF_U; ++g) {
+      const int eg = e + g * NB;
+      const bool ok = eg < n;
+      ig[g] = i;
+      jg[g] = j;
+      int q = 0;
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        if ((TRMASK >> s) & 1) {
+          x.v[s][g] = ok ? stage[q * BE + j * sst + i] : C(0);
+          ++q;
+        } else if (CONTIG) {
+          x.v[s][g] = ok ? IO<S>::load1(src[s] + eg) : C(0);
+        } else {
+          x.v[s][g] = ok ? IO<S>::load1(src[s] + ((long long)(i0 + i) + (long long)(j0 + j) * ld[s])) : C(0);
+        }
+      }
+      i += di;
+      j += dj;
+      if (i >= h) {
+        i -= h;
+        ++j;
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < BATCHF_U; ++g) {
+      const int eg = e + g * NB;
+      if (eg < n) {
+        C y = eval_elem<T, RED ? RED_SUM : RED_NONE>(x, k, err, g, acc, csq, 0);
+        if (bp.has_out) {
+          if (CONTIG)
+            IO<S>::store1(out + eg, y);
+          else
+            IO<S>::store1(out + ((long long)(i0 + ig[g]) + (long long)(j0 + jg[g]) * out_ld), y);
+        }
+      }
+    }
+  }
+}
+
+template <class T, class S, int NS, int NK, int TRMASK, bool RED>
+__device__ __forceinline__ void batchf_kernel(const BatchParams bp) {
+  typedef typename ctype<S>::type C;
+  typedef typename AccOf<C>::type A;
+  constexpr int NTR = popc<TRMASK>::value;
+  constexpr int BE = batchf_elems(NTR, (int)sizeof(C));
+  constexpr int NB = BATCHF_BLOCK;
+  __shared__ C stage[NTR > 0 ? NTR * BE : 1];
+  __shared__ A smem[32];
+  __shared__ long long next_item;
+  Scal<C, NK> k;
+#pragma unroll
+  for (int q = 0; q < NK; ++q) k.k[q] = scalar_from_bits<C>(bp.k[q]);
+  typename CsqOf<C>::type csq;
+  u32 err = 0;
+  const int tid = threadIdx.x;
+  if (tid == 0) next_item = (long long)atomicAdd(&bp.queue[0], 1u);
+  __syncthreads();
+  long long it = next_item;
+  while (it < bp.n_items) {
+    __syncthreads();  // every thread has read next_item; the last item's stage reads are done
+    if (tid == 0) next_item = (long long)atomicAdd(&bp.queue[0], 1u);  // used after this item
+    const BatchItem item = bp.items[it];
+    const BatchProblem& pr = bp.probs[item.q];
+    const int h = item.h, w = item.w, n = h * w, i0 = item.i0, j0 = item.j0;
+    const int sst = h | 1;  // odd row stride of the staged blocks
+    if constexpr (NTR > 0) {
+      // staged element (jj, ii) = view(j0 + jj, i0 + ii) = src[(j0 + jj) + (i0 + ii) ld]
+      if (n > 0) {
+        const int dj = NB % w, di = NB / w;
+        int q = 0;
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+          if ((TRMASK >> s) & 1) {
+            const S* b = (const S*)pr.src[s] + j0;
+            const long long lds = pr.ld[s];
+            int e = tid, jj = e % w, ii = e / w;
+            for (; e < n; e += 2 * NB) {
+              // two loads in flight per thread
+              const bool wrap = jj + dj >= w;
+              const int jb = wrap ? jj + dj - w : jj + dj;
+              const int ib = ii + di + (wrap ? 1 : 0);
+              const bool okb = e + NB < n;
+              const C va = IO<S>::load1(b + (jj + (long long)(i0 + ii) * lds));
+              const C vb = okb ? IO<S>::load1(b + (jb + (long long)(i0 + ib) * lds)) : C(0);
+              stage[q * BE + jj * sst + ii] = va;
+              if (okb) stage[q * BE + jb * sst + ib] = vb;
+              jj = jb + dj;
+              ii = ib + di;
+              if (jj >= w) {
+                jj -= w;
+                ++ii;
+              }
+            }
+            ++q;
+          }
+      }
+      __syncthreads();
+    }
+    A acc;
+    acc.init();
+    if (n > 0) {
+      // contiguous item: every direct slot and the output have column stride h
+      // and the item starts at row 0
+      bool contig = (i0 == 0) && (!bp.has_out || pr.out_ld == h);
+#pragma unroll
+      for (int s = 0; s < NS; ++s)
+        if (!((TRMASK >> s) & 1)) contig = contig && pr.ld[s] == h;
+      const S* src[NS];
+      long long ld[NS];
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        ld[s] = pr.ld[s];
+        src[s] = (const S*)pr.src[s] + (contig ? (long long)j0 * ld[s] : 0);
+      }
+      S* out = (S*)pr.out + (contig ? (long long)j0 * pr.out_ld : 0);
+      if (contig)
+        batchf_walk<true, T, S, NS, TRMASK, RED>(bp, src, ld, out, pr.out_ld, i0, j0, h, n, sst, stage, k, acc, csq,
+                                                 err);
+      else
+        batchf_walk<false, T, S, NS, TRMASK, RED>(bp, src, ld, out, pr.out_ld, i0, j0, h, n, sst, stage, k, acc, csq,
+                                                  err);
+    }
+    if constexpr (RED) {
+      acc = block_reduce(acc, smem);  // every lane of warp 0 holds the block's sum
+      if (tid < 32) {
+        const long long count = pr.n_rows * pr.n_cols;
+        if (item.nk == 1) {
+          if (tid == 0) batch_write<C>(bp, item.q, acc, count);
+        } else {
+          unsigned int d = 0;
+          if (tid == 0) {
+            ((A*)bp.partials)[it] = acc;
+            __threadfence();
+            d = atomicAdd(&bp.done[item.q], 1u);
+          }
+          d = __shfl_sync(0xffffffffu, d, 0);
+          if (d == (unsigned int)(item.nk - 1)) {  // the problem's last item: combine in item order
+            __threadfence();
+            A a;
+            a.init();
+            for (int kk = tid; kk < item.nk; kk += 32) a.merge(load_cg(&((const A*)bp.partials)[item.first + kk]));
+            a = warp_reduce(a);
+            if (tid == 0) {
+              batch_write<C>(bp, item.q, a, count);
+              bp.done[item.q] = 0u;
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();  // thread 0's next_item is visible
+    it = next_item;
+  }
+  if (err) atomicOr(bp.err_flag, err);
+  // the last block out resets the queue for the next launch
+  if (tid == 0) {
+    unsigned int e = atomicAdd(&bp.queue[1], 1u);
+    if (e == gridDim.x - 1) {
+      bp.queue[0] = 0u;
+      bp.queue[1] = 0u;
+    }
+  }
+}
+
 }  // namespace coot

@@ -115,8 +115,31 @@ struct BatchProblem {
   long long n_tile_rows; // tiles along the rows
 };
 
+// Work item of the flat batched kernel: a rectangle of one problem's tree,
+// rows i0 .. i0+h-1 and columns j0 .. j0+w-1.  Items are listed in problem
+// order, a problem's items consecutively (item k of nk, the first at index
+// `first`), so a problem's partial results are combined in a fixed order.
+struct BatchItem {
+  int q;
+  int i0, j0;
+  int h, w;
+  int k, nk;
+  int first;
+};
+// Elements of one item: every transposed slot stages its w x h block in
+// shared memory with a row stride of h rounded up to odd, and the host keeps
+// w * (h | 1) within this count (the blocks of all transposed slots stay
+// within 40 KiB of static shared memory; without transposed slots it bounds
+// the item's work).
+COOT_HD constexpr int batchf_elems(int ntr, int csize) {
+  return (ntr <= 0 || 40960 / (ntr * csize) >= 4096) ? 4096 : 40960 / (ntr * csize);
+}
+constexpr int BATCHF_BLOCK = 256;
+
 struct BatchParams {
   const BatchProblem* probs;
+  const BatchItem* items;  // flat kernel: the work items
+  long long n_items;
   const long long* tile_begin;  // n_problems + 1 prefix of the tile counts
   const int* tile_prob;         // owning problem of every tile
   long long n_problems;

@@ -718,6 +718,12 @@ Program make_program(const Analysis& an, Family fam, bool var_two_pass) {
              std::to_string(an.trmask) + ", " + (red ? "true" : "false") + ">",
          "BatchParams");
     add("coot_batch", 1, 1, 256);
+    // the flat walk over work items (the default)
+    wrap("coot_batchf", 256,
+         std::string("batchf_kernel<T_t, S_t, ") + std::to_string(NS) + ", " + std::to_string(NK) + ", " +
+             std::to_string(an.trmask) + ", " + (red ? "true" : "false") + ">",
+         "BatchParams");
+    add("coot_batchf", 1, 1, 256);
   }
   sig << "cootgb1|" << family_name(fam) << "|" << S << "|ns" << NS << "|nk" << NK << "|red" << an.red_mode << "|dim"
       << an.red.dim << "|out" << OUT << "|tr" << an.trmask << "|gm" << an.gmask << "|var" << var_two_pass

@@ -96,6 +96,65 @@ def test_batched_equals_single_calls():
         assert abs(r.item() - res[q].item()) <= 2e-6 * abs(r.item()) + 1e-6
 
 
+def _mixed_problems():
+    """Problems that exercise every path of the flat batched kernel: taller
+    than one work item (row chunks), wider than one (column chunks), tiny,
+    empty, views with a column stride above their row count (non-contiguous
+    items) and an output view with its own column stride."""
+    g = workloads.generator(41, "cuda")
+    shapes = [(5000, 3), (3, 5000), (4097, 2), (513, 40), (4, 4), (1, 1), (0, 7), (33, 65), (250, 251)]
+    A, B, C, outs = [], [], [], []
+    for q, (r, c) in enumerate(shapes):
+        if q % 3 == 2:  # strided views: ld = r + 5
+            A.append(workloads.normal(r + 5, c, "f32", g, "cuda")[:r, :])
+            B.append(workloads.normal(r + 5, c, "f32", g, "cuda")[2:2 + r, :])
+            C.append(workloads.normal(c + 3, r, "f32", g, "cuda")[1:1 + c, :])
+            outs.append(torch.empty((c, r + 7), dtype=torch.float32, device="cuda").t()[3:3 + r, :])
+        else:
+            A.append(workloads.normal(r, c, "f32", g, "cuda"))
+            B.append(workloads.normal(r, c, "f32", g, "cuda"))
+            C.append(workloads.normal(c, r, "f32", g, "cuda"))
+            outs.append(torch.empty((c, r), dtype=torch.float32, device="cuda").t())
+    n = len(shapes)
+    probs = (L.coot_mat * (3 * n))()
+    for q in range(n):
+        probs[3 * q] = coot.Mat(A[q]).cmat()
+        probs[3 * q + 1] = coot.Mat(B[q]).cmat()
+        probs[3 * q + 2] = coot.Mat(C[q]).cmat()
+    outm = (L.coot_mat * n)(*[coot.Mat(o).cmat() for o in outs])
+    return A, B, C, outs, probs, outm
+
+
+@pytest.mark.parametrize("kernel", ["flat", "tile"])
+def test_batched_mixed_shapes_match_oracle(kernel, monkeypatch):
+    if kernel == "tile":
+        monkeypatch.setenv("COOT_BATCH_KERNEL", "tile")
+    else:
+        monkeypatch.delenv("COOT_BATCH_KERNEL", raising=False)
+    A, B, C, outs, probs, outm = _mixed_problems()
+    n = len(A)
+    ctx = coot.context()
+    res = torch.full((n,), float("nan"), dtype=torch.float32, device="cuda")
+    plan = L.coot_batch_create(ctx, L.make_tree(BATCH_TREE), n, 3, probs, outm, L.reduce(L.R_ACCU))
+    s = torch.cuda.current_stream().cuda_stream
+    for _ in range(2):  # the queue and the per-problem counters reset themselves
+        for o in outs:
+            o.fill_(float("nan"))
+        L.coot_batch_run(plan, res.data_ptr(), s)
+        torch.cuda.synchronize()
+        for q in range(n):
+            hs = parity.host([A[q], B[q], C[q]])
+            if A[q].numel() == 0:
+                assert res[q].item() == 0.0
+                continue
+            parity.compare_matrix(outs[q], oracle.evaluate(BATCH_PROG, hs, "f32"), "f32", "%s problem %d" % (kernel, q))
+            parity.compare_reduction(res[q:q + 1], oracle.evaluate(BATCH_PROG + " accu", hs, "f32"), "f32",
+                                     "%s problem %d" % (kernel, q))
+    info = L.coot_last_launch(ctx)
+    assert info["kernel"] == ("coot_batch" if kernel == "tile" else "coot_batchf")
+    L.coot_batch_destroy(plan)
+
+
 def test_batch_rejects_mismatched_problem():
     A, B, C, outs, probs, outm, _ = _batch(8)
     bad = L.mat(probs[3 * 5 + 1].data, L.F32, probs[3 * 5 + 1].n_rows + 1, probs[3 * 5 + 1].n_cols,
