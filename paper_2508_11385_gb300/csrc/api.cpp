@@ -1385,32 +1385,66 @@ extern "C" coot_status coot_batch_create(coot_ctx* ctx, const coot_tree* tree, i
   if (flat) {
     int ntr = 0;
     for (int s = 0; s < 32; ++s) ntr += (an0.trmask >> s) & 1;
-    const int64_t BE = coot::batchf_elems(ntr, (an0.ct == cg::CT_F64) ? 8 : 4);
+    // elements per item (COOT_BATCH_BE, 1024 .. 8192, for measurements) and
+    // the register cap (COOT_BATCH_MINB resident blocks, 2 .. 6)
+    int base = 8192;
+    if (const char* be = getenv("COOT_BATCH_BE")) base = std::min(8192, std::max(1024, atoi(be)));
+    if (const char* mb = getenv("COOT_BATCH_MINB")) an0.batch_minb = std::min(6, std::max(2, atoi(mb)));
+    const int64_t BE = coot::batchf_elems(ntr, (an0.ct == cg::CT_F64) ? 8 : 4, base);
+    an0.batch_be = (int)BE;
+    const char* ienv = getenv("COOT_BATCH_ITEMS");
+    const bool cols_items = !(ienv && strcmp(ienv, "tiles") == 0);
     items.reserve((size_t)n_problems * 2);
     for (int64_t q = 0; q < n_problems; ++q) {
       const int64_t r = probs[q].n_rows, c = probs[q].n_cols;
       const size_t first = items.size();
       auto push = [&](int64_t i0, int64_t j0, int64_t h, int64_t w) {
         coot::BatchItem it;
+        memset(&it, 0, sizeof it);
         it.q = (int)q;
         it.i0 = (int)i0;
         it.j0 = (int)j0;
         it.h = (int)h;
         it.w = (int)w;
-        it.k = (int)(items.size() - first);
-        it.nk = 0;
         it.first = (int)first;
+        const int NB = coot::BATCHF_BLOCK;
+        if (h > 0 && w > 0) {
+          it.mh = (unsigned)(((1ull << 24) + (uint64_t)h - 1) / (uint64_t)h);
+          it.mw = (unsigned)(((1ull << 24) + (uint64_t)w - 1) / (uint64_t)w);
+          it.dih = (int)(NB % h);
+          it.djh = (int)(NB / h);
+          it.diw = (int)(NB % w);
+          it.djw = (int)(NB / w);
+        }
         items.push_back(it);
       };
+      // item shape H x W: whole columns when they are short; otherwise runs
+      // of at least 32 elements along both dimensions, so that the direct
+      // reads (runs along columns) and the staged transposed reads (runs
+      // along rows) both stay coalesced
+      int64_t H, W;
+      if (cols_items && (r | 1) <= BE) {  // whole columns whenever they fit
+        H = r;
+        W = std::max<int64_t>(1, BE / (r | 1));
+      } else if (r <= 127) {
+        H = r;
+        W = std::max<int64_t>(1, BE / (r | 1));
+      } else if (c <= 32) {
+        W = c;
+        H = BE / W;
+        if (H >= r)
+          H = ((r | 1) * W <= BE) ? r : r - 1;  // r - 1 is odd when r is even
+        else if (H % 2 == 0)
+          H -= 1;  // odd, so that every chunk keeps w * (h | 1) <= BE
+      } else {
+        H = 127;
+        W = std::min<int64_t>(32, BE / 127);
+      }
       if (r == 0 || c == 0) {
         push(0, 0, r, c);  // nothing to walk: writes the empty result
-      } else if ((r | 1) <= BE) {
-        const int64_t w = std::max<int64_t>(1, BE / (r | 1));
-        for (int64_t j0 = 0; j0 < c; j0 += w) push(0, j0, r, std::min(w, c - j0));
       } else {
-        const int64_t hh = ((BE - 1) % 2) ? BE - 1 : BE - 2;  // odd: h | 1 = h
-        for (int64_t j0 = 0; j0 < c; ++j0)
-          for (int64_t i0 = 0; i0 < r; i0 += hh) push(i0, j0, std::min(hh, r - i0), 1);
+        for (int64_t j0 = 0; j0 < c; j0 += W)
+          for (int64_t i0 = 0; i0 < r; i0 += H) push(i0, j0, std::min(H, r - i0), std::min(W, c - j0));
       }
       for (size_t t = first; t < items.size(); ++t) items[t].nk = (int)(items.size() - first);
     }
@@ -1467,7 +1501,7 @@ extern "C" coot_status coot_batch_create(coot_ctx* ctx, const coot_tree* tree, i
     const int csize = (an0.ct == cg::CT_F64) ? 8 : 4;
     const int per = 32 * 33 * csize * std::max(ntr, 1);
     const int warps = (ntr == 0) ? 8 : std::max(1, std::min(8, 49152 / per));
-    b->block = flat ? coot::BATCHF_BLOCK : 32 * warps;
+    b->block = flat ? coot::BATCHF_THREADS : 32 * warps;
   }
   b->grid = ctx->sms * occupancy(m, b->kname, b->block);
   b->algorithmic_bytes = bytes;

@@ -87,6 +87,8 @@ struct Analysis {
   bool has_out = false;
   int root_op = -1;         // op of the root (R_DOT needs N_SCHUR)
   int accum = 0;            // FP32 accumulation: 0 float-float, 1 Kahan, 2 plain ($COOT_ACCUM)
+  int batch_be = 8192;      // flat batched kernel: elements per work item
+  int batch_minb = 5;       // flat batched kernel: resident blocks per SM the registers are capped for
   // GEMM epilogue trees: the slot holding the product, and the operands' layouts
   int gemm_ps = -1;
   bool gemm_ka = false, gemm_kb = false;

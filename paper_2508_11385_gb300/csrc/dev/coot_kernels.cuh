@@ -1478,126 +1478,229 @@ __device__ __forceinline__ void batch_kernel(const BatchParams bp) {
 
 // ---------------------------------------------------------------------------
 // batchf: persistent kernel over work items (rectangles of one problem each,
-// see BatchItem), one block per item at a time.  The block first copies the
-// item's block of every transposed slot into shared memory (coalesced runs
-// along the source's columns, stored with an odd row stride so that both the
-// stores and the later reads are free of bank conflicts), then walks the
-// item's elements in column-major order -- consecutive threads on
-// consecutive rows, so direct slots and the output are read and written in
-// coalesced runs, U elements per thread in flight.  The block's sum of the
-// item is one partial; a problem with one item writes its result directly,
+// see BatchItem), one block per item at a time.  The block's 8 worker warps
+// first copy the item's block of every transposed slot into shared memory
+// (coalesced runs along the source's columns, stored with an odd row stride
+// so that both the stores and the later reads are free of bank conflicts),
+// then walk the item's elements in column-major order -- consecutive threads
+// on consecutive rows, so direct slots and the output are read and written in
+// coalesced runs, U elements per thread in flight.  A ninth warp meanwhile
+// pops the next item from the queue and loads its records (item, problem
+// pointers and strides) into the other half of a double buffer, so workers
+// never wait on that chain of dependent loads.  The block's sum of the item
+// is one partial; a problem with one item writes its result directly,
 // otherwise the block that completes the problem (a per-problem counter)
-// combines the partials in item order.  The next item is popped from the
-// queue before the current one is worked on.
+// combines the partials in item order.
 // ---------------------------------------------------------------------------
-constexpr int BATCHF_U = 4;
+constexpr int BATCHF_U = 8;
 
-// The element walk of one item.  Thread tid takes elements e = tid + NB u in
-// column-major order of the item (row i = e % h, column j = e / h, advanced by
-// additions).  CONTIG: every direct slot and the output hold the item's
-// columns back to back (column stride h, first row 0), so element e of a slot
-// is base + e; otherwise each access forms (i0 + i) + (j0 + j) ld.
-template <bool CONTIG, class T, class S, int NS, int TRMASK, bool RED, class C, class K, class A, class Q>
-__device__ __forceinline__ void batchf_walk(const BatchParams& bp, const S* const (&src)[NS], const long long (&ld)[NS],
-                                            S* out, long long out_ld, int i0, int j0, int h, int n, int sst,
-                                            const C* stage, const K& k, A& acc, const Q& csq, u32& err) {
-  constexpr int NB = BATCHF_BLOCK;
-  constexpr int BE = batchf_elems(popc<TRMASK>::value, (int)sizeof(C));
-  const int di = NB % h, dj = NB / h;
-  int e = threadIdx.x, i = e % h, j = e / h;
-  for (; e < n; e += BATCHF_U * NB) {
-    Vals<C, NS, BATCHF_U> x;
-    int ig[BATCHF_U], jg[BATCHF_U];
-#pragma unroll
-    for (int g = 0; g < BATCHF_U; ++g) {
-      const int eg = e + g * NB;
-      const bool ok = eg < n;
-      ig[g] = i;
-      jg[g] = j;
-      int q = 0;
-#pragma unroll
-      for (int s = 0; s < NS; ++s) {
-        if ((TRMASK >> s) & 1) {
-          x.v[s][g] = ok ? stage[q * BE + j * sst + i] : C(0);
-          ++q;
-        } else if (CONTIG) {
-          x.v[s][g] = ok ? IO<S>::load1(src[s] + eg) : C(0);
-        } else {
-          x.v[s][g] = ok ? IO<S>::load1(src[s] + ((long long)(i0 + i) + (long long)(j0 + j) * ld[s])) : C(0);
-        }
-      }
-      i += di;
-      j += dj;
-      if (i >= h) {
-        i -= h;
-        ++j;
-      }
-    }
-#pragma unroll
-    for (int g = 0; g < BATCHF_U; ++g) {
-      const int eg = e + g * NB;
-      if (eg < n) {
-        C y = eval_elem<T, RED ? RED_SUM : RED_NONE>(x, k, err, g, acc, csq, 0);
-        if (bp.has_out) {
-          if (CONTIG)
-            IO<S>::store1(out + eg, y);
-          else
-            IO<S>::store1(out + ((long long)(i0 + ig[g]) + (long long)(j0 + jg[g]) * out_ld), y);
-        }
-      }
-    }
+// what the workers need of one item (filled by the fetch warp)
+template <int NS> struct BatchfInfo {
+  long long idx;  // item index (>= n_items: no more items)
+  const void* src[NS];
+  long long ld[NS];
+  void* out;
+  long long out_ld;
+  long long count;  // elements of the problem (mean)
+  int q, i0, j0, h, w, nk, first;
+  unsigned mh, mw;
+  int dih, djh, diw, djw;
+};
+
+template <int NS>
+__device__ __forceinline__ void batchf_fetch(const BatchParams& bp, BatchfInfo<NS>& f, int lane) {
+  unsigned int pop = 0;
+  if (lane == 0) pop = atomicAdd(&bp.queue[0], 1u);
+  const long long idx = (long long)__shfl_sync(0xffffffffu, pop, 0);
+  if (lane == 0) f.idx = idx;
+  if (idx >= bp.n_items) return;
+  const BatchItem it = bp.items[idx];
+  const BatchProblem& pr = bp.probs[it.q];
+  if (lane < NS) {
+    f.src[lane] = pr.src[lane];
+    f.ld[lane] = pr.ld[lane];
+  }
+  if (lane == 0) {
+    f.out = pr.out;
+    f.out_ld = pr.out_ld;
+    f.count = pr.n_rows * pr.n_cols;
+    f.q = it.q;
+    f.i0 = it.i0;
+    f.j0 = it.j0;
+    f.h = it.h;
+    f.w = it.w;
+    f.nk = it.nk;
+    f.first = it.first;
+    f.mh = it.mh;
+    f.mw = it.mw;
+    f.dih = it.dih;
+    f.djh = it.djh;
+    f.diw = it.diw;
+    f.djw = it.djw;
   }
 }
 
-template <class T, class S, int NS, int NK, int TRMASK, bool RED>
+// The element walk of one item by the worker threads.  Thread tid takes
+// elements e = tid + NB u in column-major order of the item (row i, column
+// j, advanced by additions).  CONTIG: every direct slot and the output hold
+// the item's columns back to back (column stride h, first row 0), so element
+// e of a slot is base + e; otherwise a pointer per slot and for the output
+// follows (i, j).  The walk takes U = 8 elements per thread per step while 8
+// remain, then one step each of 4, 2 and 1 as needed, so no step carries
+// elements that are switched off.
+template <bool CONTIG, int NS, class S> struct BatchfPos {
+  int e, i, si;
+  const S* ps[CONTIG ? 1 : NS];
+  S* po;
+};
+
+template <int U, bool CONTIG, int BE, class T, class S, int NS, int TRMASK, bool RED, class C, class K, class A,
+          class Q>
+__device__ __forceinline__ void batchf_step(const BatchParams& bp, const S* const (&src)[NS],
+                                            const long long (&ld)[NS], S* out, long long out_ld, int h, int di,
+                                            int dj, int ds, int dw, BatchfPos<CONTIG, NS, S>& p, const C* stage,
+                                            const K& k, A& acc, const Q& csq, u32& err) {
+  constexpr int NB = BATCHF_BLOCK;
+  Vals<C, NS, U> x;
+  S* og[CONTIG ? 1 : U];
+#pragma unroll
+  for (int g = 0; g < U; ++g) {
+    const int eg = p.e + g * NB;
+    if constexpr (!CONTIG) og[g] = p.po;
+    int q = 0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      if ((TRMASK >> s) & 1) {
+        x.v[s][g] = stage[q * BE + p.si];
+        ++q;
+      } else if constexpr (CONTIG) {
+        x.v[s][g] = IO<S>::load1(src[s] + eg);
+      } else {
+        x.v[s][g] = IO<S>::load1(p.ps[s]);
+      }
+    }
+    p.i += di;
+    p.si += ds;
+    const bool wrap = p.i >= h;
+    if (wrap) {
+      p.i -= h;
+      p.si += dw;
+    }
+    if constexpr (!CONTIG) {
+#pragma unroll
+      for (int s = 0; s < NS; ++s)
+        if (!((TRMASK >> s) & 1)) p.ps[s] += di + dj * ld[s] + (wrap ? ld[s] - h : 0);
+      p.po += di + dj * out_ld + (wrap ? out_ld - h : 0);
+    }
+  }
+#pragma unroll
+  for (int g = 0; g < U; ++g) {
+    C y = eval_elem<T, RED ? RED_SUM : RED_NONE>(x, k, err, g, acc, csq, 0);
+    if (bp.has_out) {
+      if constexpr (CONTIG)
+        IO<S>::store1(out + (p.e + g * NB), y);
+      else
+        IO<S>::store1(og[g], y);
+    }
+  }
+  p.e += U * NB;
+}
+
+template <bool CONTIG, int BE, class T, class S, int NS, int TRMASK, bool RED, class C, class K, class A, class Q,
+          class F>
+__device__ __forceinline__ void batchf_walk(const BatchParams& bp, const S* const (&src)[NS], const long long (&ld)[NS],
+                                            S* out, long long out_ld, const F& f, int n, int sst, const C* stage,
+                                            const K& k, A& acc, const Q& csq, u32& err) {
+  constexpr int NB = BATCHF_BLOCK;
+  const int h = f.h, di = f.dih, dj = f.djh;
+  // the staged index j sst + i moves with (i, j): + dj sst + di, and
+  // sst - h more when i wraps into the next column
+  const int ds = dj * sst + di, dw = sst - h;
+  BatchfPos<CONTIG, NS, S> p;
+  p.e = threadIdx.x;
+  const int j = (int)(((unsigned long long)(unsigned)p.e * f.mh) >> 24);
+  p.i = p.e - j * h;
+  p.si = j * sst + p.i;
+  if constexpr (!CONTIG) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) p.ps[s] = src[s] + ((long long)p.i + (long long)j * ld[s]);
+    p.po = out + ((long long)p.i + (long long)j * out_ld);
+  }
+  constexpr int UM = CONTIG ? BATCHF_U : BATCHF_U / 2;  // the general walk keeps a pointer per element
+  while (p.e + (UM - 1) * NB < n)
+    batchf_step<UM, CONTIG, BE, T, S, NS, TRMASK, RED>(bp, src, ld, out, out_ld, h, di, dj, ds, dw, p, stage, k, acc,
+                                                       csq, err);
+  if (UM > 4 && p.e + 3 * NB < n)
+    batchf_step<4, CONTIG, BE, T, S, NS, TRMASK, RED>(bp, src, ld, out, out_ld, h, di, dj, ds, dw, p, stage, k, acc,
+                                                      csq, err);
+  if (p.e + NB < n)
+    batchf_step<2, CONTIG, BE, T, S, NS, TRMASK, RED>(bp, src, ld, out, out_ld, h, di, dj, ds, dw, p, stage, k, acc,
+                                                      csq, err);
+  if (p.e < n)
+    batchf_step<1, CONTIG, BE, T, S, NS, TRMASK, RED>(bp, src, ld, out, out_ld, h, di, dj, ds, dw, p, stage, k, acc,
+                                                      csq, err);
+}
+
+template <class T, class S, int NS, int NK, int TRMASK, bool RED, int BE>
 __device__ __forceinline__ void batchf_kernel(const BatchParams bp) {
   typedef typename ctype<S>::type C;
   typedef typename AccOf<C>::type A;
   constexpr int NTR = popc<TRMASK>::value;
-  constexpr int BE = batchf_elems(NTR, (int)sizeof(C));
   constexpr int NB = BATCHF_BLOCK;
+  constexpr int SU = 4;  // staging loads in flight per thread
   __shared__ C stage[NTR > 0 ? NTR * BE : 1];
   __shared__ A smem[32];
-  __shared__ long long next_item;
+  __shared__ BatchfInfo<NS> info[2];
   Scal<C, NK> k;
 #pragma unroll
   for (int q = 0; q < NK; ++q) k.k[q] = scalar_from_bits<C>(bp.k[q]);
   typename CsqOf<C>::type csq;
   u32 err = 0;
   const int tid = threadIdx.x;
-  if (tid == 0) next_item = (long long)atomicAdd(&bp.queue[0], 1u);
+  const bool worker = tid < NB;
+  if (tid >= NB) batchf_fetch<NS>(bp, info[0], tid - NB);
   __syncthreads();
-  long long it = next_item;
-  while (it < bp.n_items) {
-    __syncthreads();  // every thread has read next_item; the last item's stage reads are done
-    if (tid == 0) next_item = (long long)atomicAdd(&bp.queue[0], 1u);  // used after this item
-    const BatchItem item = bp.items[it];
-    const BatchProblem& pr = bp.probs[item.q];
-    const int h = item.h, w = item.w, n = h * w, i0 = item.i0, j0 = item.j0;
+  int cur = 0;
+  while (info[cur].idx < bp.n_items) {
+    const BatchfInfo<NS>& f = info[cur];
+    const long long it = f.idx;
+    const int h = f.h, w = f.w, n = h * w, i0 = f.i0, j0 = f.j0;
     const int sst = h | 1;  // odd row stride of the staged blocks
+    if (!worker) batchf_fetch<NS>(bp, info[cur ^ 1], tid - NB);  // the next item, while this one runs
     if constexpr (NTR > 0) {
       // staged element (jj, ii) = view(j0 + jj, i0 + ii) = src[(j0 + jj) + (i0 + ii) ld]
-      if (n > 0) {
-        const int dj = NB % w, di = NB / w;
+      if (worker && n > 0) {
+        const int dj = f.diw, di = f.djw;
         int q = 0;
 #pragma unroll
         for (int s = 0; s < NS; ++s)
           if ((TRMASK >> s) & 1) {
-            const S* b = (const S*)pr.src[s] + j0;
-            const long long lds = pr.ld[s];
-            int e = tid, jj = e % w, ii = e / w;
-            for (; e < n; e += 2 * NB) {
-              // two loads in flight per thread
-              const bool wrap = jj + dj >= w;
-              const int jb = wrap ? jj + dj - w : jj + dj;
-              const int ib = ii + di + (wrap ? 1 : 0);
-              const bool okb = e + NB < n;
-              const C va = IO<S>::load1(b + (jj + (long long)(i0 + ii) * lds));
-              const C vb = okb ? IO<S>::load1(b + (jb + (long long)(i0 + ib) * lds)) : C(0);
-              stage[q * BE + jj * sst + ii] = va;
-              if (okb) stage[q * BE + jb * sst + ib] = vb;
-              jj = jb + dj;
-              ii = ib + di;
+            const S* b = (const S*)f.src[s] + j0;
+            const long long lds = f.ld[s];
+            int e = tid, ii = (int)(((unsigned long long)(unsigned)e * f.mw) >> 24), jj = e - ii * w;
+            // SU loads in flight per step while SU elements remain, then one at a time
+            for (; e + (SU - 1) * NB < n; e += SU * NB) {
+              C v[SU];
+              int pj[SU], pi[SU];
+#pragma unroll
+              for (int g = 0; g < SU; ++g) {
+                pj[g] = jj;
+                pi[g] = ii;
+                v[g] = IO<S>::load1(b + (jj + (long long)(i0 + ii) * lds));
+                jj += dj;
+                ii += di;
+                if (jj >= w) {
+                  jj -= w;
+                  ++ii;
+                }
+              }
+#pragma unroll
+              for (int g = 0; g < SU; ++g) stage[q * BE + pj[g] * sst + pi[g]] = v[g];
+            }
+            for (; e < n; e += NB) {
+              stage[q * BE + jj * sst + ii] = IO<S>::load1(b + (jj + (long long)(i0 + ii) * lds));
+              jj += dj;
+              ii += di;
               if (jj >= w) {
                 jj -= w;
                 ++ii;
@@ -1610,58 +1713,58 @@ __device__ __forceinline__ void batchf_kernel(const BatchParams bp) {
     }
     A acc;
     acc.init();
-    if (n > 0) {
+    if (worker && n > 0) {
       // contiguous item: every direct slot and the output have column stride h
       // and the item starts at row 0
-      bool contig = (i0 == 0) && (!bp.has_out || pr.out_ld == h);
+      bool contig = (i0 == 0) && (!bp.has_out || f.out_ld == h);
 #pragma unroll
       for (int s = 0; s < NS; ++s)
-        if (!((TRMASK >> s) & 1)) contig = contig && pr.ld[s] == h;
+        if (!((TRMASK >> s) & 1)) contig = contig && f.ld[s] == h;
+      // every slot and the output from the item's first element (i0, j0)
       const S* src[NS];
       long long ld[NS];
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
-        ld[s] = pr.ld[s];
-        src[s] = (const S*)pr.src[s] + (contig ? (long long)j0 * ld[s] : 0);
+        ld[s] = f.ld[s];
+        src[s] = (const S*)f.src[s] + ((long long)i0 + (long long)j0 * ld[s]);
       }
-      S* out = (S*)pr.out + (contig ? (long long)j0 * pr.out_ld : 0);
+      S* out = (S*)f.out + ((long long)i0 + (long long)j0 * f.out_ld);
       if (contig)
-        batchf_walk<true, T, S, NS, TRMASK, RED>(bp, src, ld, out, pr.out_ld, i0, j0, h, n, sst, stage, k, acc, csq,
-                                                 err);
+        batchf_walk<true, BE, T, S, NS, TRMASK, RED>(bp, src, ld, out, f.out_ld, f, n, sst, stage, k, acc, csq, err);
       else
-        batchf_walk<false, T, S, NS, TRMASK, RED>(bp, src, ld, out, pr.out_ld, i0, j0, h, n, sst, stage, k, acc, csq,
-                                                  err);
+        batchf_walk<false, BE, T, S, NS, TRMASK, RED>(bp, src, ld, out, f.out_ld, f, n, sst, stage, k, acc, csq, err);
     }
     if constexpr (RED) {
       acc = block_reduce(acc, smem);  // every lane of warp 0 holds the block's sum
       if (tid < 32) {
-        const long long count = pr.n_rows * pr.n_cols;
-        if (item.nk == 1) {
-          if (tid == 0) batch_write<C>(bp, item.q, acc, count);
+        if (f.nk == 1) {
+          if (tid == 0) batch_write<C>(bp, f.q, acc, f.count);
         } else {
           unsigned int d = 0;
           if (tid == 0) {
             ((A*)bp.partials)[it] = acc;
             __threadfence();
-            d = atomicAdd(&bp.done[item.q], 1u);
+            d = atomicAdd(&bp.done[f.q], 1u);
           }
           d = __shfl_sync(0xffffffffu, d, 0);
-          if (d == (unsigned int)(item.nk - 1)) {  // the problem's last item: combine in item order
+          if (d == (unsigned int)(f.nk - 1)) {  // the problem's last item: combine in item order
             __threadfence();
             A a;
             a.init();
-            for (int kk = tid; kk < item.nk; kk += 32) a.merge(load_cg(&((const A*)bp.partials)[item.first + kk]));
+            for (int kk = tid; kk < f.nk; kk += 32) a.merge(load_cg(&((const A*)bp.partials)[f.first + kk]));
             a = warp_reduce(a);
             if (tid == 0) {
-              batch_write<C>(bp, item.q, a, count);
-              bp.done[item.q] = 0u;
+              batch_write<C>(bp, f.q, a, f.count);
+              bp.done[f.q] = 0u;
             }
           }
         }
       }
     }
-    __syncthreads();  // thread 0's next_item is visible
-    it = next_item;
+    // the next item's records are in place, and nobody reads this item's
+    // stage or records any more
+    __syncthreads();
+    cur ^= 1;
   }
   if (err) atomicOr(bp.err_flag, err);
   // the last block out resets the queue for the next launch

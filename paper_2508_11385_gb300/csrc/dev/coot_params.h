@@ -119,22 +119,31 @@ struct BatchProblem {
 // rows i0 .. i0+h-1 and columns j0 .. j0+w-1.  Items are listed in problem
 // order, a problem's items consecutively (item k of nk, the first at index
 // `first`), so a problem's partial results are combined in a fixed order.
+// The per-item constants of the walks are computed on the host: a thread
+// t < 256 starts at row t % h, column t / h, found as j = (t * mh) >> 24 with
+// mh = ceil(2^24 / h) (exact for t < 256 and h < 2^14), and moves by
+// (NB % h, NB / h) per step; the staging walk likewise over (w, h).
 struct BatchItem {
   int q;
   int i0, j0;
   int h, w;
-  int k, nk;
+  int nk;
   int first;
+  unsigned mh, mw;
+  int dih, djh, diw, djw;
+  int pad[3];
 };
 // Elements of one item: every transposed slot stages its w x h block in
 // shared memory with a row stride of h rounded up to odd, and the host keeps
 // w * (h | 1) within this count (the blocks of all transposed slots stay
 // within 40 KiB of static shared memory; without transposed slots it bounds
-// the item's work).
-COOT_HD constexpr int batchf_elems(int ntr, int csize) {
-  return (ntr <= 0 || 40960 / (ntr * csize) >= 4096) ? 4096 : 40960 / (ntr * csize);
+// the item's work).  `base` is the count without that limit.
+COOT_HD constexpr int batchf_elems(int ntr, int csize, int base = 4096) {
+  return (ntr <= 0 || 40960 / (ntr * csize) >= base) ? base : 40960 / (ntr * csize);
 }
+// worker threads of a block; one more warp fetches the next item's records
 constexpr int BATCHF_BLOCK = 256;
+constexpr int BATCHF_THREADS = BATCHF_BLOCK + 32;
 
 struct BatchParams {
   const BatchProblem* probs;

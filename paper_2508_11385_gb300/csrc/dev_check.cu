@@ -39,11 +39,11 @@ K(chk_adj_f32, 512, (adj_kernel<T3, float, 3, 1, 4, 2>))
 extern "C" __global__ void __launch_bounds__(256) chk_batch(const __grid_constant__ BatchParams p) {
   batch_kernel<T3, float, 3, 1, 4, true>(p);
 }
-extern "C" __global__ void __launch_bounds__(256) chk_batchf(const __grid_constant__ BatchParams p) {
-  batchf_kernel<T3, float, 3, 1, 4, true>(p);
+extern "C" __global__ void __launch_bounds__(BATCHF_THREADS, 5) chk_batchf(const __grid_constant__ BatchParams p) {
+  batchf_kernel<T3, float, 3, 1, 4, true, 8192>(p);
 }
-extern "C" __global__ void __launch_bounds__(256) chk_batchf_f64_2tr(const __grid_constant__ BatchParams p) {
-  batchf_kernel<eGlue<Leaf<0>, Leaf<1>, eglue_plus>, double, 2, 0, 3, true>(p);
+extern "C" __global__ void __launch_bounds__(BATCHF_THREADS, 5) chk_batchf_f64_2tr(const __grid_constant__ BatchParams p) {
+  batchf_kernel<eGlue<Leaf<0>, Leaf<1>, eglue_plus>, double, 2, 0, 3, true, 2560>(p);
 }
 extern "C" __global__ void __launch_bounds__(256) chk_batch_f64_2tr(const __grid_constant__ BatchParams p) {
   batch_kernel<eGlue<Leaf<0>, Leaf<1>, eglue_plus>, double, 2, 0, 3, true>(p);

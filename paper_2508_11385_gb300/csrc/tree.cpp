@@ -719,17 +719,19 @@ Program make_program(const Analysis& an, Family fam, bool var_two_pass) {
          "BatchParams");
     add("coot_batch", 1, 1, 256);
     // the flat walk over work items (the default)
-    wrap("coot_batchf", 256,
+    wrap("coot_batchf", coot::BATCHF_THREADS,
          std::string("batchf_kernel<T_t, S_t, ") + std::to_string(NS) + ", " + std::to_string(NK) + ", " +
-             std::to_string(an.trmask) + ", " + (red ? "true" : "false") + ">",
-         "BatchParams");
-    add("coot_batchf", 1, 1, 256);
+             std::to_string(an.trmask) + ", " + (red ? "true" : "false") + ", " + std::to_string(an.batch_be) + ">",
+         "BatchParams", an.batch_minb);
+    add("coot_batchf", 1, 1, coot::BATCHF_THREADS);
   }
   sig << "cootgb1|" << family_name(fam) << "|" << S << "|ns" << NS << "|nk" << NK << "|red" << an.red_mode << "|dim"
       << an.red.dim << "|out" << OUT << "|tr" << an.trmask << "|gm" << an.gmask << "|var" << var_two_pass
       << (fam == F_GEMM ? "|ps" + std::to_string(an.gemm_ps) + (an.gemm_ka ? "ka" : "ma") + (an.gemm_kb ? "kb" : "nb")
                         : std::string())
-      << (an.accum == 1 ? "|kahan" : (an.accum == 2 ? "|plain" : "")) << "|" << an.type_str;
+      << (an.accum == 1 ? "|kahan" : (an.accum == 2 ? "|plain" : ""))
+      << (fam == F_BATCH ? "|be" + std::to_string(an.batch_be) + "b" + std::to_string(an.batch_minb) : std::string())
+      << "|" << an.type_str;
   pg.signature = sig.str();
   pg.source = src.str();
   return pg;
