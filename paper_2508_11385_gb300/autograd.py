@@ -11,6 +11,7 @@ it (Sec. 7: ensmallen and mlpack being adapted to Bandicoot).
 """
 from __future__ import annotations
 
+import ctypes
 import threading
 
 import torch
@@ -30,7 +31,12 @@ def _cmat(t: torch.Tensor):
 
 
 class Loss:
-    """A scalar loss lowered once for inputs of fixed shapes and layouts."""
+    """A scalar loss lowered once for inputs of fixed shapes and layouts.
+
+    The C-ABI arguments of both calls (the leaves' coot_mat arrays, the
+    gradients' arrays) are built once per set of device pointers and kept,
+    so a repeated step with the same tensors costs two launches and little
+    host work."""
 
     def __init__(self, fn, *examples):
         mats = [E.Mat(t.detach()) for t in examples]
@@ -44,27 +50,59 @@ class Loss:
         self.acc = E._ACC[leaves[0].dtype]
         self.signature = tuple((tuple(t.shape), tuple(t.stride()), t.dtype) for t in examples)
         self.n_inputs = len(examples)
+        self._tree_ref = ctypes.byref(self.tree)
+        self._leaf_arrays = {}  # device pointers of the inputs -> coot_mat array of the leaves
+        self._grad_arrays = {}  # (input pointers, gradient pointers) -> coot_mat array of the gradients
+        self._ctx = {}
 
     def __call__(self, *tensors):
         return _LossFn.apply(self, *tensors)
+
+    def _context(self, dev):
+        h = self._ctx.get(dev)
+        if h is None:
+            h = self._ctx[dev] = E.context(dev)
+        return h
+
+    def _leaves(self, tensors):
+        key = tuple((t.data_ptr(), t.shape, t.stride(), t.dtype) for t in tensors)
+        arr = self._leaf_arrays.get(key)
+        if arr is None:
+            if len(self._leaf_arrays) > 64:
+                self._leaf_arrays.clear()
+            arr = (L.coot_mat * len(self.leaf_pos))(*[_cmat(tensors[p].detach()) for p in self.leaf_pos])
+            self._leaf_arrays[key] = arr
+        return key, arr
 
     # the two C-ABI calls, usable without autograd
     def forward(self, *tensors, out=None):
         dev = tensors[0].device
         r = torch.empty((), dtype=self.acc, device=dev) if out is None else out
-        cm = [_cmat(tensors[p].detach()) for p in self.leaf_pos]
-        L.coot_eval(E.context(dev), self.tree, cm, None, self.red, r.data_ptr(), E._stream_ptr())
+        _, arr = self._leaves(tensors)
+        L._check(L._lib.coot_eval(self._context(dev), self._tree_ref, arr, len(self.leaf_pos), None, self.red,
+                                  r.data_ptr(), torch.cuda.current_stream(dev).cuda_stream))
         return r
 
     def backward(self, upstream, *tensors, grads=None):
         dev = tensors[0].device
         if grads is None:
             grads = [_grad_like(t) for t in tensors]
-        cm = [_cmat(tensors[p].detach()) for p in self.leaf_pos]
-        gm = [(_cmat(grads[p]) if grads[p] is not None else L.mat(None, cm[i].dtype, cm[i].n_rows, cm[i].n_cols))
-              for i, p in enumerate(self.leaf_pos)]
-        up = upstream.detach().to(dtype=self.acc).reshape(()).contiguous()
-        L.coot_eval_adjoint(E.context(dev), self.tree, cm, self.red, up.data_ptr(), gm, E._stream_ptr())
+        key, arr = self._leaves(tensors)
+        gkey = (key, tuple(g.data_ptr() if g is not None else 0 for g in grads))
+        garr = self._grad_arrays.get(gkey)
+        if garr is None:
+            if len(self._grad_arrays) > 64:
+                self._grad_arrays.clear()
+            gm = [(_cmat(grads[p]) if grads[p] is not None else L.mat(None, arr[i].dtype, arr[i].n_rows,
+                                                                         arr[i].n_cols))
+                  for i, p in enumerate(self.leaf_pos)]
+            garr = (L.coot_mat * len(gm))(*gm)
+            self._grad_arrays[gkey] = garr
+        up = upstream.detach()
+        if up.dtype != self.acc or up.dim() != 0 or not up.is_contiguous():
+            up = up.to(dtype=self.acc).reshape(()).contiguous()
+        L._check(L._lib.coot_eval_adjoint(self._context(dev), self._tree_ref, arr, len(self.leaf_pos), self.red,
+                                          up.data_ptr(), garr, torch.cuda.current_stream(dev).cuda_stream))
         return grads
 
 
@@ -97,10 +135,11 @@ _cache_lock = threading.Lock()
 def loss_l2_schur(W, X, Y, lam=1e-3):
     """L = accu(square(W % X - Y)) + lam * accu(square(W)) (the
     differentiation workload), fused into one accu by linearity."""
-    key = (lam,) + tuple((tuple(t.shape), tuple(t.stride()), t.dtype, t.device) for t in (W, X, Y))
-    with _cache_lock:
-        f = _cache.get(key)
-        if f is None:
+    key = (lam, W.shape, W.stride(), X.stride(), Y.stride(), W.dtype, W.device)
+    f = _cache.get(key)
+    if f is None or (X.shape, Y.shape, X.dtype, Y.dtype) != (W.shape, W.shape, W.dtype, W.dtype):
+        with _cache_lock:
             f = Loss(lambda w, x, y: E.accu(E.square(w % x - y)) + lam * E.accu(E.square(w)), W, X, Y)
-            _cache[key] = f
+            if (X.shape, Y.shape, X.dtype, Y.dtype) == (W.shape, W.shape, W.dtype, W.dtype):
+                _cache[key] = f
     return f(W, X, Y)

@@ -506,7 +506,19 @@ static coot_status run_fused(coot_ctx* ctx, const cg::Analysis& an, const coot_m
   // launch configuration: the call plan's, else tuned, else the default
   // variant at full occupancy
   cg::LaunchCfg cfg;
-  if (hit && plan->have_cfg) {
+  // COOT_FORCE_KERNEL=<kernel name>: that variant of the program at its
+  // default launch shape, when the program has it (tests of every variant)
+  int forced = -1;
+  if (const char* fk = getenv("COOT_FORCE_KERNEL")) {
+    for (int i = 0; i < (int)pg.kernels.size(); ++i)
+      if (pg.kernels[i].name == fk && (ch.vec_ok || pg.kernels[i].vec == 1)) forced = i;
+  }
+  if (forced >= 0) {
+    cfg.kidx = forced;
+    cfg.block = std::min(pg.kernels[forced].block, 256);
+    cfg.blocks_per_sm = occupancy(m, pg.kernels[forced].name, cfg.block);
+    cfg.split = 0;
+  } else if (hit && plan->have_cfg) {
     cfg = plan->cfg;
   } else {
     const std::string key = tune_key(pg, ch);
