@@ -44,6 +44,8 @@ template <> struct rtype<int> { typedef i64 type; };
 
 template <class C> struct is_int_c { static constexpr bool value = false; };
 template <> struct is_int_c<int> { static constexpr bool value = true; };
+template <class C> struct is_f32_c { static constexpr bool value = false; };
+template <> struct is_f32_c<float> { static constexpr bool value = true; };
 
 // ---------------------------------------------------------------------------
 // element conversion between 32-bit words and values
@@ -204,6 +206,14 @@ template <> struct IO<bf16> {
     }
   }
   __device__ static C load1(const bf16* p) { return __uint_as_float(((u32)ldg_u16(p)) << 16); }
+  // V values from V/2 words already loaded (element 2q in the low half of word q)
+  template <int V> __device__ static void convert(const u32 (&w)[V / 2], C (&v)[V]) {
+#pragma unroll
+    for (int q = 0; q < V / 2; ++q) {
+      v[2 * q] = bf16_lo(w[q]);
+      v[2 * q + 1] = bf16_hi(w[q]);
+    }
+  }
   template <int V> __device__ static void store(bf16* p, const C (&v)[V]) {
     if constexpr (V == 1) {
       stg_u16(p, to_bf16(v[0]));
@@ -233,6 +243,13 @@ template <> struct IO<f16> {
     }
   }
   __device__ static C load1(const f16* p) { return f16_to_f32(ldg_u16(p)); }
+  template <int V> __device__ static void convert(const u32 (&w)[V / 2], C (&v)[V]) {
+#pragma unroll
+    for (int q = 0; q < V / 2; ++q) {
+      v[2 * q] = f16_to_f32((u16)(w[q] & 0xffffu));
+      v[2 * q + 1] = f16_to_f32((u16)(w[q] >> 16));
+    }
+  }
   template <int V> __device__ static void store(f16* p, const C (&v)[V]) {
     if constexpr (V == 1) {
       stg_u16(p, to_f16(v[0]));
@@ -714,10 +731,12 @@ template <class C> struct AccSel<C, RED_IMAX> { typedef AccExt<C, true> type; };
 template <class C> struct AccSel<C, RED_PROD> { typedef typename ProdOf<C>::type type; };
 
 // Centred sum of squares for the second pass of var.  The mean arrives as a
-// double m; FP32 data keeps it as the float pair (mh, ml) = m so that
-// d = x - m is formed with one TwoSum and rounded once (relative error <= u
-// per d, for any ratio of mean to spread), and d*d (all terms positive, so
-// their rounding errors cannot cancel into a large relative error) is
+// double m; FP32 data keeps it as the float pair (mh, ml) = m and forms
+// d = (x - mh) - ml: each subtraction's rounding error is at most u |d| (the
+// first result is d + ml, the second d), so d carries a relative error of at
+// most 2u for any ratio of mean to spread, and the low part ml removes the
+// bias a rounded mean would add to every term.  The d*d are all positive, so
+// their rounding errors cannot cancel into a large relative error; they are
 // accumulated in float-float.  FP64 data uses plain FP64.
 struct CsqF {
   float mh, ml;
@@ -725,12 +744,7 @@ struct CsqF {
     mh = __double2float_rn(m);
     ml = __double2float_rn(m - (double)mh);
   }
-  __device__ __forceinline__ float centred(float x) const {
-    float s = __fsub_rn(x, mh);
-    float bp = __fsub_rn(s, x);
-    float e = __fadd_rn(__fsub_rn(x, __fsub_rn(s, bp)), __fsub_rn(-mh, bp));
-    return __fadd_rn(s, __fsub_rn(e, ml));
-  }
+  __device__ __forceinline__ float centred(float x) const { return __fsub_rn(__fsub_rn(x, mh), ml); }
 };
 struct CsqD {
   double m;

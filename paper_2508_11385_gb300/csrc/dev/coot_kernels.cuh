@@ -85,6 +85,25 @@ __device__ __forceinline__ void load_rows_at(const Params& p, int s, const S* co
     IO<S>::template load<V>(col + i, v);
   }
 }
+// 16-bit storage: the same V rows as V/2 raw words (element 2q in the low
+// half of word q), converted only when they are used, so that several
+// loads in flight cost half the registers; rows at or past `lim` read 0
+template <class S, int V>
+__device__ __forceinline__ void load_rows_raw(const Params& p, int s, const S* col, long long i, long long lim,
+                                              u32 (&w)[V / 2]) {
+  static_assert(sizeof(S) == 2 && V % 2 == 0, "16-bit storage, whole words");
+  if (!gen_slot(s) && i + V <= lim) {
+    ldg_words(col + i, w);
+    return;
+  }
+#pragma unroll
+  for (int q = 0; q < V / 2; ++q) {
+    const long long r0 = i + 2 * q, r1 = r0 + 1;
+    const u32 lo = (r0 < lim) ? (u32)ldg_u16(row_in<S>(p, s, col, r0)) : 0u;
+    const u32 hi = (r1 < lim) ? (u32)ldg_u16(row_in<S>(p, s, col, r1)) : 0u;
+    w[q] = lo | (hi << 16);
+  }
+}
 // V consecutive rows of slot s from (i, j), all inside the tree
 template <class S, int V, class C>
 __device__ __forceinline__ void load_rows(const Params& p, int s, long long i, long long j, C (&v)[V]) {
@@ -158,11 +177,14 @@ __device__ __forceinline__ typename X::C eval_elem(const X& x, const K& k, u32& 
 }
 
 // The element's value y and, in c, its term of the reduction, for the
-// pairwise path of 16-bit storage: products and squares of two 16-bit values
-// are exact in FP32 (at most 22 significant bits), and sums of two such terms
-// are exact unless their exponents differ by more than 15, so the V terms of
-// one vector load are summed pairwise in FP32 before a single float-float
-// addition.
+// pairwise path: the V terms of one vector load are summed pairwise in FP32
+// before a single float-float addition.  16-bit storage: products and
+// squares of two 16-bit values are exact in FP32 (at most 22 significant
+// bits), and sums of two such terms are exact unless their exponents differ
+// by more than 15.  FP32 sums of squares (norm, var's second pass): every
+// term is positive, so a rounded square (relative error u) and the pairwise
+// sums (u per level) add at most (1 + log2 V) u to the relative error of the
+// result -- rounding errors of positive terms cannot cancel into more.
 template <class T, int RED, class X, class K, class Q>
 __device__ __forceinline__ typename X::C eval_term(const X& x, const K& k, u32& err, int l, const Q& csq,
                                                    typename X::C& c) {
@@ -307,7 +329,10 @@ __device__ __forceinline__ void str_kernel(const Params& p) {
     for (int s = 0; s < NS; ++s) col[s] = col_of<S>(p, s, j);
     S* oc = nullptr;
     if constexpr (OUT) oc = out_col<S>(p, j);
-    Vals<C, NS, V> x[U];
+    // 16-bit storage keeps its loads as raw words until they are used
+    constexpr bool RAW = sizeof(S) == 2 && V >= 2;
+    Vals<C, NS, V> x[RAW ? 1 : U];
+    u32 raw[RAW ? U : 1][RAW ? NS : 1][RAW ? V / 2 : 1];
     bool valid[U], full[U];
     long long ig[U], jg[U];
     S* og[U];
@@ -319,7 +344,10 @@ __device__ __forceinline__ void str_kernel(const Params& p) {
       ig[g] = i;
       jg[g] = j;
       og[g] = oc;
-      if (full[g]) {
+      if constexpr (RAW) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) load_rows_raw<S, V>(p, s, col[s], i, valid[g] ? nr : 0, raw[g][s]);
+      } else if (full[g]) {
 #pragma unroll
         for (int s = 0; s < NS; ++s) load_rows_at<S, V>(p, s, col[s], i, x[g].v[s]);
       } else {
@@ -340,14 +368,22 @@ __device__ __forceinline__ void str_kernel(const Params& p) {
 #pragma unroll
     for (int g = 0; g < U; ++g) {
       const long long i = ig[g];
+      const Vals<C, NS, V>* xg = &x[RAW ? 0 : g];
+      if constexpr (RAW) {
+        if (valid[g]) {
+#pragma unroll
+          for (int s = 0; s < NS; ++s) IO<S>::template convert<V>(raw[g][s], x[0].v[s]);
+        }
+      }
       if (full[g]) {
         C y[V];
-        if constexpr (sizeof(S) == 2 && red_additive(RED)) {
-          // 16-bit storage: pairwise sum of the vector's terms, then one
-          // float-float addition (spread over the accumulators by group)
+        if constexpr ((sizeof(S) == 2 && red_additive(RED)) ||
+                      (is_f32_c<S>::value && (RED == RED_SSQ || RED == RED_CSQ))) {
+          // pairwise sum of the vector's terms, then one float-float
+          // addition (spread over the accumulators by group)
           C c[V];
 #pragma unroll
-          for (int l = 0; l < V; ++l) y[l] = eval_term<T, RED>(x[g], k, err, l, csq, c[l]);
+          for (int l = 0; l < V; ++l) y[l] = eval_term<T, RED>(*xg, k, err, l, csq, c[l]);
 #pragma unroll
           for (int w = V / 2; w >= 1; w /= 2)
 #pragma unroll
@@ -355,14 +391,14 @@ __device__ __forceinline__ void str_kernel(const Params& p) {
           accs[g % V].add(c[0]);
         } else {
 #pragma unroll
-          for (int l = 0; l < V; ++l) y[l] = eval_elem<T, RED>(x[g], k, err, l, accs[l], csq, i + l + jg[g] * nr);
+          for (int l = 0; l < V; ++l) y[l] = eval_elem<T, RED>(*xg, k, err, l, accs[l], csq, i + l + jg[g] * nr);
         }
         if constexpr (OUT) store_rows_at<S, V>(p, og[g], i, y);
       } else if (valid[g]) {
 #pragma unroll
         for (int l = 0; l < V; ++l)
           if (i + l < nr) {
-            C y = eval_elem<T, RED>(x[g], k, err, l, accs[l], csq, i + l + jg[g] * nr);
+            C y = eval_elem<T, RED>(*xg, k, err, l, accs[l], csq, i + l + jg[g] * nr);
             if constexpr (OUT) IO<S>::store1(out_row_in<S>(p, og[g], i + l), y);
           }
       }
