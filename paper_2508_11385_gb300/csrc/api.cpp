@@ -240,15 +240,17 @@ void shape_launch(coot_ctx* ctx, const cg::Analysis& an, const cg::Choice& ch, c
     const int64_t ntr = ceil_div(R, 32 * std::max(k.vec, 1)), ntc = ceil_div(C, 32);
     const int64_t tiles = ntr * ntc;
     if (an.red.dim == 0 || an.red.dim == 1) {
-      // blocks = strips x segments; `split` segments per strip when given
-      // (tuning), else about two waves of resident blocks
+      // units = strips x segments, taken in turn by a grid of at most the
+      // resident blocks; `split` segments per strip when given (tuning),
+      // else about eight units per resident block, so that the last round
+      // of units costs little
       const int64_t strips = std::max<int64_t>(an.red.dim == 0 ? ntc : ntr, 1);
       const int64_t len = std::max<int64_t>(an.red.dim == 0 ? ntr : ntc, 1);
-      int64_t nseg = split > 0 ? split : ceil_div(2 * resident, strips);
+      int64_t nseg = split > 0 ? split : ceil_div(8 * resident, strips);
       nseg = std::max<int64_t>(1, std::min(nseg, len));
       nseg = ceil_div(len, ceil_div(len, nseg));  // no empty segment
       p.n_splits = nseg;
-      L->grid = (int)(strips * nseg);
+      L->grid = (int)std::min<int64_t>(strips * nseg, resident);
       const int64_t no = (an.red.dim == 0) ? C : R;
       L->partial_bytes = (nseg > 1) ? (size_t)(nseg * no * ab) : 0;
       L->tickets = (size_t)strips;
@@ -633,11 +635,13 @@ coot_status tune(coot_ctx* ctx, const cg::Analysis& an, const cg::Choice& ch, co
       if (ch.fam == cg::F_COL)
         for (int g = 1; g <= block / 32; g *= 2) splits.push_back(g);
       if (ch.fam == cg::F_TILE && an.red.dim >= 0) {
-        // segments per strip: one, and about 1/2, 1, 4 waves of resident blocks
-        const int64_t strips = std::max<int64_t>(ceil_div(an.red.dim == 0 ? an.nc : an.nr, 32), 1);
+        // segments per strip: one, and about 1, 2, 4, 8, 16 units per
+        // resident block
+        const int64_t tall = (an.red.dim == 0) ? 32 : 32 * std::max(k.vec, 1);
+        const int64_t strips = std::max<int64_t>(ceil_div(an.red.dim == 0 ? an.nc : an.nr, tall), 1);
         const int64_t res = (int64_t)ctx->sms * std::max(occ, 1);
         splits.push_back(1);
-        for (int64_t w2 : {1, 2, 8}) splits.push_back((int)std::max<int64_t>(1, ceil_div(w2 * res, 2 * strips)));
+        for (int64_t w2 : {1, 2, 4, 8, 16}) splits.push_back((int)std::max<int64_t>(1, ceil_div(w2 * res, strips)));
       }
       if (ch.fam == cg::F_SCAN) splits.push_back(1);  // one pass, no segments
       for (int bps : bpss)

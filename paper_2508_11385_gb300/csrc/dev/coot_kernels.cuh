@@ -732,7 +732,10 @@ __device__ __forceinline__ void tile_kernel(const Params& p) {
     if constexpr (RED != RED_NONE) finish_full<C, RED>(p, acc, smem);
   } else {
     const long long nseg = p.n_splits;
-    const long long strip = blockIdx.x / nseg, seg = blockIdx.x % nseg;
+    // the strips' segments, taken by the blocks in turn
+    const long long units = ((DIM == 0) ? ntc : ntr) * nseg;
+    for (long long unit = blockIdx.x; unit < units; unit += gridDim.x) {
+    const long long strip = unit / nseg, seg = unit % nseg;
     const long long len = (DIM == 0) ? ntr : ntc;  // tiles along the strip
     const long long per = (len + nseg - 1) / nseg;
     const long long t0 = seg * per, t1 = (t0 + per < len) ? t0 + per : len;
@@ -767,7 +770,6 @@ __device__ __forceinline__ void tile_kernel(const Params& p) {
         }
       }
     }
-    if (err) atomicOr(p.err_flag, err);
     const long long no = (DIM == 0) ? nc : nr;
     // this block's value for each output of the strip: rsum[0][o % 32]
     if constexpr (DIM == 0) {
@@ -788,6 +790,9 @@ __device__ __forceinline__ void tile_kernel(const Params& p) {
       __syncthreads();
     }
     strip_finish<C, RED, TILE>(p, &rsum[0][0], strip, seg, nseg, no, &am_last);
+    __syncthreads();  // rsum is read by the finish before the next unit writes it
+    }  // units
+    if (err) atomicOr(p.err_flag, err);
   }
 }
 
@@ -875,17 +880,21 @@ __device__ __forceinline__ void tilev_kernel(const Params& p) {
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const long long nr = p.n_rows, nc = p.n_cols;
   const long long ntr = (nr + TM - 1) / TM, ntc = (nc + TILE - 1) / TILE;
-  // tile range of this block: all tiles strided (DIM -1), or one segment of a
-  // strip (DIM 0: column strip tj, DIM 1: row strip ti)
-  long long t_first, t_end, t_step, strip = 0, seg = 0, nseg = 1;
+  // work units: DIM -1, one unit, all tiles strided over the grid; DIM 0 / 1,
+  // the segments of the strips (DIM 0: column strip tj, DIM 1: row strip ti),
+  // strips x n_splits of them, taken by the blocks in turn (a grid of about
+  // the resident blocks, so no partial last wave)
+  const long long nseg = (DIM == -1) ? 1 : p.n_splits;
+  const long long units = (DIM == -1) ? 1 : ((DIM == 0) ? ntc : ntr) * nseg;
+  for (long long unit = (DIM == -1) ? 0 : blockIdx.x; unit < units; unit += (DIM == -1) ? 1 : gridDim.x) {
+  long long t_first, t_end, t_step, strip = 0, seg = 0;
   if constexpr (DIM == -1) {
     t_first = blockIdx.x;
     t_end = ntr * ntc;
     t_step = gridDim.x;
   } else {
-    nseg = p.n_splits;
-    strip = blockIdx.x / nseg;
-    seg = blockIdx.x % nseg;
+    strip = unit / nseg;
+    seg = unit % nseg;
     const long long len = (DIM == 0) ? ntr : ntc;
     const long long per = (len + nseg - 1) / nseg;
     t_first = seg * per;
@@ -1015,7 +1024,6 @@ __device__ __forceinline__ void tilev_kernel(const Params& p) {
       }
     }
   }
-  if (err) atomicOr(p.err_flag, err);
   if constexpr (DIM == -1) {
     if constexpr (RED != RED_NONE) {
 #pragma unroll
@@ -1045,6 +1053,9 @@ __device__ __forceinline__ void tilev_kernel(const Params& p) {
     }
     strip_finish<C, RED, TM>(p, blk, strip, seg, nseg, nr, &am_last);
   }
+  if constexpr (DIM != -1) __syncthreads();  // blk is read by the finish before the next unit writes it
+  }  // units
+  if (err) atomicOr(p.err_flag, err);
 }
 
 // ---------------------------------------------------------------------------
