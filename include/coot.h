@@ -211,6 +211,15 @@ typedef struct coot_graph coot_graph;
 #define COOT_CTX_NO_DISK_CACHE 2u /* keep compiled kernels in memory only    */
 #define COOT_CTX_LOG 4u           /* print JIT / cache / tuning decisions    */
 #define COOT_CTX_NO_TCGEN05 8u    /* GEMM: always the mma.sync kernel        */
+#define COOT_CTX_DEBUG_BOUNDS 16u /* bounds-check build of the streaming
+                                     kernels (str, col, row, tile, scan, adj):
+                                     every leaf read and output write is
+                                     checked against the extent computed from
+                                     its matrix's shape and strides; an access
+                                     outside it is skipped (a read gives 0) and
+                                     raises COOT_FLAG_OUT_OF_BOUNDS.  Slower;
+                                     for testing.  Batches and the GEMM are not
+                                     checked.                                 */
 COOT_API coot_status coot_ctx_create(int device, unsigned flags, coot_ctx** out);
 COOT_API coot_status coot_ctx_destroy(coot_ctx* ctx);
 
@@ -393,10 +402,12 @@ COOT_API coot_status coot_sum_rows_f32_noalloc(const coot_mat* x, int32_t mean, 
  * and device-side conditions are gathered in one flag word read on demand.
  * coot_check_device_flag: wait for `stream`, read and clear the context's
  * device error flags (bit 0: an INT32 division by zero; bit 1: a bounded
- * wait of the tcgen05 GEMM timed out).  Returns COOT_ERR_DEVICE_FLAG when
- * any flag was set. */
+ * wait of the tcgen05 GEMM timed out; bit 2: the bounds-check build found
+ * an access outside a matrix).  Returns COOT_ERR_DEVICE_FLAG when any flag
+ * was set. */
 #define COOT_FLAG_INT_DIV_ZERO 1u
 #define COOT_FLAG_WAIT_TIMEOUT 2u
+#define COOT_FLAG_OUT_OF_BOUNDS 4u
 COOT_API coot_status coot_check_device_flag(coot_ctx* ctx, coot_stream stream, uint32_t* flags);
 
 /* Description of the last launch made by coot_eval on this context (kernel

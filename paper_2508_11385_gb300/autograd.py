@@ -21,7 +21,23 @@ from . import lib as L
 
 
 def _grad_like(t: torch.Tensor) -> torch.Tensor:
+    # empty_like keeps the strides of a dense tensor (a column-major leaf gets
+    # a column-major gradient); anything else gets them spelled out
+    if t.is_non_overlapping_and_dense():
+        return torch.empty_like(t)
     return torch.empty_strided(t.shape, t.stride(), dtype=t.dtype, device=t.device)
+
+
+# the current stream's raw handle of a device: torch's direct query where it
+# has one (no Stream object is built), else the public API
+_raw_stream = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+
+
+def _stream_of(dev: torch.device) -> int:
+    idx = dev.index if dev.index is not None else torch.cuda.current_device()
+    if _raw_stream is not None:
+        return _raw_stream(idx)
+    return torch.cuda.current_stream(dev).cuda_stream
 
 
 def _cmat(t: torch.Tensor):
@@ -80,7 +96,7 @@ class Loss:
         r = torch.empty((), dtype=self.acc, device=dev) if out is None else out
         _, arr = self._leaves(tensors)
         L._check(L._lib.coot_eval(self._context(dev), self._tree_ref, arr, len(self.leaf_pos), None, self.red,
-                                  r.data_ptr(), torch.cuda.current_stream(dev).cuda_stream))
+                                  r.data_ptr(), _stream_of(dev)))
         return r
 
     def backward(self, upstream, *tensors, grads=None):
@@ -102,7 +118,7 @@ class Loss:
         if up.dtype != self.acc or up.dim() != 0 or not up.is_contiguous():
             up = up.to(dtype=self.acc).reshape(()).contiguous()
         L._check(L._lib.coot_eval_adjoint(self._context(dev), self._tree_ref, arr, len(self.leaf_pos), self.red,
-                                          up.data_ptr(), garr, torch.cuda.current_stream(dev).cuda_stream))
+                                          up.data_ptr(), garr, _stream_of(dev)))
         return grads
 
 

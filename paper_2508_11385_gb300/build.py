@@ -99,6 +99,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
     procs.append((chk, subprocess.Popen([nvcc] + ARCH + ["-std=c++17", "-O3", "-fmad=false", "-Xptxas", "-v",
                                                          "-I", DEV, "-c", chk, "-o", chk_obj],
                                         stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+    # the same kernels in the bounds-check build (COOT_DEBUG_BOUNDS)
+    procs.append((chk + " (bounds)", subprocess.Popen(
+        [nvcc] + ARCH + ["-std=c++17", "-O3", "-fmad=false", "-DCOOT_DEBUG_BOUNDS=1", "-I", DEV, "-c", chk, "-o",
+                         os.path.join(BUILD, "dev_check_bounds.o")],
+        stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
     failed = []
     for src, p in procs:
         out, _ = p.communicate()

@@ -82,6 +82,29 @@ int64_t mat_ld(const coot_mat& m) { return (m.n_cols > 1) ? m.ld : (m.ld > 0 ? m
 
 int rsize(int ct) { return ct == cg::CT_F32 ? 4 : 8; }
 
+// elements addressable from a matrix's first element: its last element's
+// offset plus one (0 for an empty matrix)
+int64_t mat_extent(const coot_mat& m) {
+  if (m.n_rows <= 0 || m.n_cols <= 0) return 0;
+  const int64_t rs = m.rs > 1 ? m.rs : 1;
+  const int64_t ld = m.n_cols > 1 ? m.ld : 0;
+  return (m.n_rows - 1) * rs + (m.n_cols - 1) * ld + 1;
+}
+
+// the bounds-check build's extents of a launch's slots and output;
+// COOT_DEBUG_BOUNDS_SHRINK=1 (tests of the check itself) declares every
+// extent one element short, so that the kernel skips and reports the last
+// element of each leaf instead of reading it
+void set_extents(const cg::Analysis& an, const coot_mat* leaves, const coot_mat* out, cg::Params* p) {
+  const char* sh = getenv("COOT_DEBUG_BOUNDS_SHRINK");
+  const int64_t cut = (sh && sh[0] == '1') ? 1 : 0;
+  for (size_t i = 0; i < an.slots.size(); ++i) {
+    const cg::Slot& sl = an.slots[i];
+    p->ext[i] = std::max<int64_t>(0, mat_extent(leaves[sl.leaf]) - sl.off - cut);
+  }
+  p->out_ext = out ? std::max<int64_t>(0, mat_extent(*out) - cut) : 0;
+}
+
 bool capturing(cudaStream_t s) {
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
@@ -463,7 +486,8 @@ static coot_status run_fused(coot_ctx* ctx, const cg::Analysis& an, const coot_m
     ch.it_cols = an.nc;
   }
   cg::Program fresh;
-  if (!hit) fresh = cg::make_program(an, ch.fam, var);
+  const bool bounds = (ctx->flags & COOT_CTX_DEBUG_BOUNDS) != 0;
+  if (!hit) fresh = cg::make_program(an, ch.fam, var, bounds);
   const cg::Program& pg = hit ? plan->pg : fresh;
   if (!hit && !ctx->mods.count(pg.signature) && capturing(stream))
     return set_error(COOT_ERR_INVALID, "this tree's kernel is not compiled yet; call coot_warmup before capturing");
@@ -491,6 +515,7 @@ static coot_status run_fused(coot_ctx* ctx, const cg::Analysis& an, const coot_m
     p.ld[i] = sl.trans ? sl.rs : sl.cs;
     p.rs[i] = sl.rs;
   }
+  if (bounds) set_extents(an, leaves, out, &p);
   for (size_t i = 0; i < an.scalars.size(); ++i) p.k[i] = scalar_bits(an.scalars[i], an.ct);
   p.out = out ? out->data : nullptr;
   p.out_ld = out ? mat_ld(*out) : 0;
@@ -584,6 +609,7 @@ static coot_status run_fused(coot_ctx* ctx, const cg::Analysis& an, const coot_m
 namespace {
 coot_status tune(coot_ctx* ctx, const cg::Analysis& an, const cg::Choice& ch, const cg::Program& pg, cg::Module* m,
                  Launch base, cudaStream_t stream, cg::LaunchCfg* best) {
+  NvtxRange nvtx_range("cootgb tune");
   const bool var = an.two_pass();
   void* scratch_out = nullptr;
   void* scratch_red = nullptr;
@@ -786,6 +812,7 @@ static void call_key(const coot_tree* tree, const coot_mat* leaves, int32_t n_le
 
 extern "C" coot_status coot_eval(coot_ctx* ctx, const coot_tree* tree, const coot_mat* leaves, int32_t n_leaves,
                                  const coot_mat* out, coot_reduce red, void* red_out, coot_stream stream) {
+  NvtxRange nvtx_range("cootgb eval");
   if (!ctx) return set_error(COOT_ERR_INVALID, "ctx is NULL");
   const bool keyable = tree && tree->nodes && tree->n_nodes >= 1 && tree->n_nodes <= COOT_MAX_NODES && leaves &&
                        n_leaves >= 1 && n_leaves <= COOT_MAX_LEAVES;
@@ -840,6 +867,7 @@ extern "C" coot_status coot_warmup(coot_ctx* ctx, const coot_tree* tree, const c
 extern "C" coot_status coot_eval_unfused(coot_ctx* ctx, const coot_tree* tree, const coot_mat* leaves,
                                          int32_t n_leaves, const coot_mat* out, coot_reduce red, void* red_out,
                                          coot_stream stream_) {
+  NvtxRange nvtx_range("cootgb eval unfused");
   if (!ctx) return set_error(COOT_ERR_INVALID, "ctx is NULL");
   cudaStream_t stream = (cudaStream_t)stream_;
   cg::Analysis an;
@@ -1085,6 +1113,7 @@ bool tma_map(unsigned long long* dst, const void* data, int dtype, bool kmaj, in
 extern "C" coot_status coot_gemm_eval(coot_ctx* ctx, const coot_mat* A, int32_t trans_a, const coot_mat* B,
                                       int32_t trans_b, const coot_tree* epi, const coot_mat* extra, int32_t n_extra,
                                       const coot_mat* out, coot_stream stream_) {
+  NvtxRange nvtx_range("cootgb gemm");
   if (!ctx || !A || !B || !out) return set_error(COOT_ERR_INVALID, "ctx, A, B or out is NULL");
   if (n_extra < 0 || n_extra > COOT_MAX_LEAVES - 1 || (n_extra > 0 && !extra))
     return set_error(COOT_ERR_INVALID, "n_extra %d outside 0..%d (or extra NULL)", n_extra, COOT_MAX_LEAVES - 1);
@@ -1232,6 +1261,7 @@ extern "C" coot_status coot_gemm_eval(coot_ctx* ctx, const coot_mat* A, int32_t 
 extern "C" coot_status coot_eval_adjoint(coot_ctx* ctx, const coot_tree* tree, const coot_mat* leaves,
                                          int32_t n_leaves, coot_reduce red, const void* upstream,
                                          const coot_mat* grads, coot_stream stream_) {
+  NvtxRange nvtx_range("cootgb adjoint");
   if (!ctx) return set_error(COOT_ERR_INVALID, "ctx is NULL");
   cudaStream_t stream = (cudaStream_t)stream_;
   if (!upstream || !grads) return set_error(COOT_ERR_INVALID, "upstream or grads is NULL");
@@ -1285,7 +1315,8 @@ extern "C" coot_status coot_eval_adjoint(coot_ctx* ctx, const coot_tree* tree, c
   ch.vec_ok = vec;
   ch.it_rows = contig ? count : an.nr;
   ch.it_cols = contig ? 1 : an.nc;
-  cg::Program pg = cg::make_program(an, cg::F_ADJ, false);
+  const bool bounds = (ctx->flags & COOT_CTX_DEBUG_BOUNDS) != 0;
+  cg::Program pg = cg::make_program(an, cg::F_ADJ, false, bounds);
   if (!ctx->mods.count(pg.signature) && capturing(stream))
     return set_error(COOT_ERR_INVALID, "compile the adjoint before capturing");
   cg::Module* m = nullptr;
@@ -1300,6 +1331,7 @@ extern "C" coot_status coot_eval_adjoint(coot_ctx* ctx, const coot_tree* tree, c
     p.grad[i] = G.data;
     p.grad_ld[i] = G.data ? mat_ld(G) : 0;
   }
+  if (bounds) set_extents(an, leaves, nullptr, &p);
   for (size_t i = 0; i < an.scalars.size(); ++i) p.k[i] = scalar_bits(an.scalars[i], an.ct);
   p.upstream = upstream;
   p.grad_mult = (red.kind == COOT_R_MEAN) ? 1.0 / (double)count : 1.0;
@@ -1544,6 +1576,7 @@ extern "C" coot_status coot_batch_create(coot_ctx* ctx, const coot_tree* tree, i
 }
 
 extern "C" coot_status coot_batch_run(coot_batch* b, void* red_out, coot_stream stream) {
+  NvtxRange nvtx_range("cootgb batch");
   if (!b) return set_error(COOT_ERR_INVALID, "batch is NULL");
   if (b->has_red && !red_out) return set_error(COOT_ERR_INVALID, "red_out is NULL");
   std::lock_guard<std::recursive_mutex> lk(b->ctx->mu);
@@ -1702,7 +1735,11 @@ extern "C" coot_status coot_check_device_flag(coot_ctx* ctx, coot_stream stream,
     return cuda_error(e, "read device flag");
   if (f && (e = cudaMemset(ctx->err_flag, 0, sizeof f)) != cudaSuccess) return cuda_error(e, "clear device flag");
   if (flags) *flags = f;
-  if (f) return set_error(COOT_ERR_DEVICE_FLAG, "device flag 0x%x (bit 0: INT32 division by zero)", f);
+  if (f)
+    return set_error(COOT_ERR_DEVICE_FLAG,
+                     "device flag 0x%x (bit 0: INT32 division by zero; bit 1: a bounded wait timed out; bit 2: an "
+                     "access outside a matrix)",
+                     f);
   return COOT_OK;
 }
 

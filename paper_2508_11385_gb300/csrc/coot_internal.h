@@ -11,8 +11,20 @@
 #include <unordered_map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "coot.h"
 #include "dev/coot_params.h"
+
+// A named NVTX range for the lifetime of the object: profilers (nsys, ncu's
+// NVTX filters) see the library's JIT compiles, tuning runs and launches as
+// ranges; without a tool attached a push or pop costs a few nanoseconds.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 namespace cg {
 
@@ -137,7 +149,9 @@ struct Program {
 };
 
 // Build the program (signature + source + kernel list) for a family.
-Program make_program(const Analysis& an, Family fam, bool var_two_pass);
+// bounds: compile the bounds-check build (COOT_DEBUG_BOUNDS defined; its own
+// signature and cache entries)
+Program make_program(const Analysis& an, Family fam, bool var_two_pass, bool bounds = false);
 std::string storage_type_name(coot_dtype d);
 
 // ---- JIT ------------------------------------------------------------------

@@ -56,6 +56,38 @@ template <class S> __device__ __forceinline__ S* at_out(void* base, long long i,
 constexpr int GM_OUT = 1 << COOT_MAX_SLOTS;
 __device__ __forceinline__ constexpr bool gen_slot(int s) { return (COOT_GM >> s) & 1; }
 
+// Bounds-check build: with COOT_DEBUG_BOUNDS defined, every slot read and
+// every output write of the Params kernel families is checked against the
+// extent the host computed from the leaf's (or output's) shape and strides;
+// an access outside it is not made (a read gives 0) and sets device flag
+// bit 2 (COOT_FLAG_OUT_OF_BOUNDS).  Without it the checks compile away.
+#ifdef COOT_DEBUG_BOUNDS
+template <class S> __device__ __forceinline__ bool slot_ok(const Params& p, int s, const S* ptr, long long n) {
+  const long long off = ptr - (const S*)p.src[s];
+  const bool ok = off >= 0 && off + n <= p.ext[s];
+  if (!ok) atomicOr(p.err_flag, 4u);
+  return ok;
+}
+template <class S> __device__ __forceinline__ bool out_ok(const Params& p, const S* ptr, long long n) {
+  const long long off = ptr - (const S*)p.out;
+  const bool ok = off >= 0 && off + n <= p.out_ext;
+  if (!ok) atomicOr(p.err_flag, 4u);
+  return ok;
+}
+#else
+template <class S> __device__ __forceinline__ constexpr bool slot_ok(const Params&, int, const S*, long long) {
+  return true;
+}
+template <class S> __device__ __forceinline__ constexpr bool out_ok(const Params&, const S*, long long) { return true; }
+#endif
+// one element of slot s / of the output, checked in the bounds-check build
+template <class S> __device__ __forceinline__ typename IO<S>::C sload1(const Params& p, int s, const S* ptr) {
+  return slot_ok<S>(p, s, ptr, 1) ? IO<S>::load1(ptr) : typename IO<S>::C(0);
+}
+template <class S> __device__ __forceinline__ void sstore1(const Params& p, S* ptr, typename IO<S>::C v) {
+  if (out_ok<S>(p, ptr, 1)) IO<S>::store1(ptr, v);
+}
+
 template <class S> __device__ __forceinline__ const S* at_slot(const Params& p, int s, long long i, long long j) {
   if (gen_slot(s)) return (const S*)p.src[s] + (i * p.rs[s] + j * p.ld[s]);
   return at<S>(p.src[s], i, j, p.ld[s]);
@@ -74,15 +106,18 @@ __device__ __forceinline__ void load_rows_at(const Params& p, int s, const S* co
   if (gen_slot(s)) {
     const S* b = col + i * p.rs[s];
     if (p.rs[s] == 0) {  // a row broadcast: one element for all V rows
-      const C x = IO<S>::load1(b);
+      const C x = sload1<S>(p, s, b);
 #pragma unroll
       for (int l = 0; l < V; ++l) v[l] = x;
     } else {
 #pragma unroll
-      for (int l = 0; l < V; ++l) v[l] = IO<S>::load1(b + l * p.rs[s]);
+      for (int l = 0; l < V; ++l) v[l] = sload1<S>(p, s, b + l * p.rs[s]);
     }
-  } else {
+  } else if (slot_ok<S>(p, s, col + i, V)) {
     IO<S>::template load<V>(col + i, v);
+  } else {
+#pragma unroll
+    for (int l = 0; l < V; ++l) v[l] = C(0);
   }
 }
 // 16-bit storage: the same V rows as V/2 raw words (element 2q in the low
@@ -93,14 +128,21 @@ __device__ __forceinline__ void load_rows_raw(const Params& p, int s, const S* c
                                               u32 (&w)[V / 2]) {
   static_assert(sizeof(S) == 2 && V % 2 == 0, "16-bit storage, whole words");
   if (!gen_slot(s) && i + V <= lim) {
-    ldg_words(col + i, w);
+    if (slot_ok<S>(p, s, col + i, V)) {
+      ldg_words(col + i, w);
+    } else {
+#pragma unroll
+      for (int q = 0; q < V / 2; ++q) w[q] = 0u;
+    }
     return;
   }
 #pragma unroll
   for (int q = 0; q < V / 2; ++q) {
     const long long r0 = i + 2 * q, r1 = r0 + 1;
-    const u32 lo = (r0 < lim) ? (u32)ldg_u16(row_in<S>(p, s, col, r0)) : 0u;
-    const u32 hi = (r1 < lim) ? (u32)ldg_u16(row_in<S>(p, s, col, r1)) : 0u;
+    const S* a0 = row_in<S>(p, s, col, r0);
+    const S* a1 = row_in<S>(p, s, col, r1);
+    const u32 lo = (r0 < lim && slot_ok<S>(p, s, a0, 1)) ? (u32)ldg_u16(a0) : 0u;
+    const u32 hi = (r1 < lim && slot_ok<S>(p, s, a1, 1)) ? (u32)ldg_u16(a1) : 0u;
     w[q] = lo | (hi << 16);
   }
 }
@@ -125,8 +167,8 @@ template <class S, int V, class C>
 __device__ __forceinline__ void store_rows_at(const Params& p, S* col, long long i, const C (&v)[V]) {
   if (COOT_GM & GM_OUT) {
 #pragma unroll
-    for (int l = 0; l < V; ++l) IO<S>::store1(col + (i + l) * p.out_rs, v[l]);
-  } else {
+    for (int l = 0; l < V; ++l) sstore1<S>(p, col + (i + l) * p.out_rs, v[l]);
+  } else if (out_ok<S>(p, col + i, V)) {
     IO<S>::template store<V>(col + i, v);
   }
 }
@@ -135,8 +177,8 @@ template <class S, int V, class C> __device__ __forceinline__ void store_rows(co
                                                                              const C (&v)[V]) {
   if (COOT_GM & GM_OUT) {
 #pragma unroll
-    for (int l = 0; l < V; ++l) IO<S>::store1(at_out_g<S>(p, i + l, j), v[l]);
-  } else {
+    for (int l = 0; l < V; ++l) sstore1<S>(p, at_out_g<S>(p, i + l, j), v[l]);
+  } else if (out_ok<S>(p, at_out<S>(p.out, i, j, p.out_ld), V)) {
     IO<S>::template store<V>(at_out<S>(p.out, i, j, p.out_ld), v);
   }
 }
@@ -355,7 +397,7 @@ __device__ __forceinline__ void str_kernel(const Params& p) {
         for (int s = 0; s < NS; ++s)
 #pragma unroll
           for (int l = 0; l < V; ++l)
-            x[g].v[s][l] = (valid[g] && i + l < nr) ? IO<S>::load1(row_in<S>(p, s, col[s], i + l)) : C(0);
+            x[g].v[s][l] = (valid[g] && i + l < nr) ? sload1<S>(p, s, row_in<S>(p, s, col[s], i + l)) : C(0);
       }
       if (g + 1 < U && ++r == cpc) {  // the next chunk starts the next column
         r = 0;
@@ -399,7 +441,7 @@ __device__ __forceinline__ void str_kernel(const Params& p) {
         for (int l = 0; l < V; ++l)
           if (i + l < nr) {
             C y = eval_elem<T, RED>(*xg, k, err, l, accs[l], csq, i + l + jg[g] * nr);
-            if constexpr (OUT) IO<S>::store1(out_row_in<S>(p, og[g], i + l), y);
+            if constexpr (OUT) sstore1<S>(p, out_row_in<S>(p, og[g], i + l), y);
           }
       }
     }
@@ -456,7 +498,7 @@ __device__ __forceinline__ void col_kernel(const Params& p) {
           for (int s = 0; s < NS; ++s)
 #pragma unroll
             for (int l = 0; l < V; ++l)
-              x[g].v[s][l] = (i + l < nr) ? IO<S>::load1(at_slot<S>(p, s, i + l, j)) : C(0);
+              x[g].v[s][l] = (i + l < nr) ? sload1<S>(p, s, at_slot<S>(p, s, i + l, j)) : C(0);
         }
       }
 #pragma unroll
@@ -472,7 +514,7 @@ __device__ __forceinline__ void col_kernel(const Params& p) {
           for (int l = 0; l < V; ++l)
             if (i + l < nr) {
               C y = eval_elem<T, RED>(x[g], k, err, l, acc, csq, i + l);
-              if constexpr (OUT) IO<S>::store1(at_out_g<S>(p, i + l, j), y);
+              if constexpr (OUT) sstore1<S>(p, at_out_g<S>(p, i + l, j), y);
             }
         }
       }
@@ -539,7 +581,7 @@ __device__ __forceinline__ void row_kernel(const Params& p) {
             for (int s = 0; s < NS; ++s)
 #pragma unroll
               for (int l = 0; l < V; ++l)
-                x[g].v[s][l] = (i + l < nr) ? IO<S>::load1(at_slot<S>(p, s, i + l, j)) : C(0);
+                x[g].v[s][l] = (i + l < nr) ? sload1<S>(p, s, at_slot<S>(p, s, i + l, j)) : C(0);
           }
         }
       }
@@ -557,7 +599,7 @@ __device__ __forceinline__ void row_kernel(const Params& p) {
             for (int l = 0; l < V; ++l)
               if (i + l < nr) {
                 C y = eval_elem<T, RED>(x[g], k, err, l, acc[l], csq[l], j - pbase);
-                if constexpr (OUT) IO<S>::store1(at_out_g<S>(p, i + l, j), y);
+                if constexpr (OUT) sstore1<S>(p, at_out_g<S>(p, i + l, j), y);
               }
           }
         }
@@ -632,7 +674,7 @@ __device__ __forceinline__ void tile_load(const Params& p, long long ti, long lo
     const bool ok = (i < nr && j < nc);
 #pragma unroll
     for (int s = 0; s < NS; ++s)
-      if (!((TRMASK >> s) & 1)) x.v[s][w] = ok ? IO<S>::load1(at_slot<S>(p, s, i, j)) : C(0);
+      if (!((TRMASK >> s) & 1)) x.v[s][w] = ok ? sload1<S>(p, s, at_slot<S>(p, s, i, j)) : C(0);
   }
   if constexpr (NTR > 0) {
     __syncthreads();  // the previous tile's shared reads are done
@@ -644,7 +686,7 @@ __device__ __forceinline__ void tile_load(const Params& p, long long ti, long lo
 #pragma unroll
         for (int w = 0; w < TILE_Q; ++w) {
           const long long vc = ti * TILE + ty + TILE_PH * w;  // view column = output row
-          stage[q][ty + TILE_PH * w][tx] = (vr < nc && vc < nr) ? IO<S>::load1(at<S>(p.src[s], vr, vc, p.ld[s])) : C(0);
+          stage[q][ty + TILE_PH * w][tx] = (vr < nc && vc < nr) ? sload1<S>(p, s, at<S>(p.src[s], vr, vc, p.ld[s])) : C(0);
         }
         ++q;
       }
@@ -724,7 +766,7 @@ __device__ __forceinline__ void tile_kernel(const Params& p) {
         const long long j = tj * TILE + ty + TILE_PH * w;
         if (i < nr && j < nc) {
           C y = eval_elem<T, RED>(x, k, err, w, acc, csq, i + j * nr);
-          if constexpr (OUT) IO<S>::store1(at_out_g<S>(p, i, j), y);
+          if constexpr (OUT) sstore1<S>(p, at_out_g<S>(p, i, j), y);
         }
       }
     }
@@ -766,7 +808,7 @@ __device__ __forceinline__ void tile_kernel(const Params& p) {
             y = eval_elem<T, RED>(x, k, err, w, acc[w], csq[w], i);
           else
             y = eval_elem<T, RED>(x, k, err, w, acc[0], csq[0], j);
-          if constexpr (OUT) IO<S>::store1(at_out_g<S>(p, i, j), y);
+          if constexpr (OUT) sstore1<S>(p, at_out_g<S>(p, i, j), y);
         }
       }
     }
@@ -946,7 +988,7 @@ __device__ __forceinline__ void tilev_kernel(const Params& p) {
         } else {
 #pragma unroll
           for (int l = 0; l < V; ++l)
-            x[w].v[s][l] = (j < nc && i0 + l < nr) ? IO<S>::load1(at_slot<S>(p, s, i0 + l, j)) : C(0);
+            x[w].v[s][l] = (j < nc && i0 + l < nr) ? sload1<S>(p, s, at_slot<S>(p, s, i0 + l, j)) : C(0);
         }
       }
     }
@@ -972,14 +1014,14 @@ __device__ __forceinline__ void tilev_kernel(const Params& p) {
 #pragma unroll
             for (int g = 0; g < NG; ++g)
 #pragma unroll
-              for (int e = 0; e < GE; ++e) v[g][e] = IO<S>::load1(b + ((long long)(TILE_PH * g * GE + e)) * ld);
+              for (int e = 0; e < GE; ++e) v[g][e] = sload1<S>(p, s, b + ((long long)(TILE_PH * g * GE + e)) * ld);
           } else {
 #pragma unroll
             for (int g = 0; g < NG; ++g)
 #pragma unroll
               for (int e = 0; e < GE; ++e) {
                 const long long vc = ti * TM + (ty + TILE_PH * g) * GE + e;  // view column = output row
-                v[g][e] = (vr < nc && vc < nr) ? IO<S>::load1(at<S>(p.src[s], vr, vc, p.ld[s])) : C(0);
+                v[g][e] = (vr < nc && vc < nr) ? sload1<S>(p, s, at<S>(p.src[s], vr, vc, p.ld[s])) : C(0);
               }
           }
 #pragma unroll
@@ -1019,7 +1061,7 @@ __device__ __forceinline__ void tilev_kernel(const Params& p) {
         for (int l = 0; l < V; ++l)
           if (i0 + l < nr) {
             C y = elem(l);
-            if constexpr (OUT) IO<S>::store1(at_out_g<S>(p, i0 + l, j), y);
+            if constexpr (OUT) sstore1<S>(p, at_out_g<S>(p, i0 + l, j), y);
           }
       }
     }
@@ -1163,7 +1205,7 @@ __device__ __forceinline__ void scan_col_kernel(const Params& p) {
 #pragma unroll
         for (int s = 0; s < NS; ++s)
 #pragma unroll
-          for (int l = 0; l < V; ++l) x.v[s][l] = (i + l < r1) ? IO<S>::load1(at_slot<S>(p, s, i + l, j)) : C(0);
+          for (int l = 0; l < V; ++l) x.v[s][l] = (i + l < r1) ? sload1<S>(p, s, at_slot<S>(p, s, i + l, j)) : C(0);
       }
       C y[V];
       A tot;
@@ -1200,7 +1242,7 @@ __device__ __forceinline__ void scan_col_kernel(const Params& p) {
         else
 #pragma unroll
           for (int l = 0; l < V; ++l)
-            if (i + l < r1) IO<S>::store1(at_out_g<S>(p, i + l, j), out[l]);
+            if (i + l < r1) sstore1<S>(p, at_out_g<S>(p, i + l, j), out[l]);
       }
       carry.add(step_total);
     }
@@ -1249,7 +1291,7 @@ __device__ __forceinline__ void scan_row_kernel(const Params& p) {
           for (int s = 0; s < NS; ++s)
 #pragma unroll
             for (int l = 0; l < V; ++l)
-              x[g].v[s][l] = (i + l < nr) ? IO<S>::load1(at_slot<S>(p, s, i + l, j)) : C(0);
+              x[g].v[s][l] = (i + l < nr) ? sload1<S>(p, s, at_slot<S>(p, s, i + l, j)) : C(0);
         }
       }
     }
@@ -1269,7 +1311,7 @@ __device__ __forceinline__ void scan_row_kernel(const Params& p) {
           else
 #pragma unroll
             for (int l = 0; l < V; ++l)
-              if (i + l < nr) IO<S>::store1(at_out_g<S>(p, i + l, j), out[l]);
+              if (i + l < nr) sstore1<S>(p, at_out_g<S>(p, i + l, j), out[l]);
         }
       }
     }
@@ -1312,7 +1354,7 @@ __device__ __forceinline__ void adj_kernel(const Params& p) {
 #pragma unroll
         for (int s = 0; s < NS; ++s)
 #pragma unroll
-          for (int l = 0; l < V; ++l) x[g].v[s][l] = (i + l < nr) ? IO<S>::load1(at_slot<S>(p, s, i + l, j)) : C(0);
+          for (int l = 0; l < V; ++l) x[g].v[s][l] = (i + l < nr) ? sload1<S>(p, s, at_slot<S>(p, s, i + l, j)) : C(0);
       }
     }
 #pragma unroll

@@ -70,6 +70,10 @@ struct Params {
   unsigned int* tickets;
   unsigned int* err_flag;
   double* mu;
+  // bounds-check build (COOT_DEBUG_BOUNDS): elements addressable from src[s]
+  // and from out (the leaf's extent past the slot's first element)
+  long long ext[COOT_MAX_SLOTS];
+  long long out_ext;
   // adjoint: gradient outputs per slot (nullable) and the upstream scalar
   void* grad[COOT_MAX_SLOTS];
   long long grad_ld[COOT_MAX_SLOTS];

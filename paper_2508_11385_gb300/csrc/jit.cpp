@@ -147,6 +147,7 @@ coot_status coot_get_module(coot_ctx* ctx, const cg::Program& pg, cg::Module** o
     *out = it->second.get();
     return COOT_OK;
   }
+  NvtxRange nvtx_range("cootgb jit (disk cache or NVRTC)");
   const uint64_t sig_hash = cg::fnv1a(pg.signature.data(), pg.signature.size(), cg::headers_hash());
   std::vector<char> cubin;
   bool from_disk = false;

@@ -523,7 +523,7 @@ Choice choose(const Analysis& an, const coot_mat* leaves, const coot_mat* out) {
 // ---------------------------------------------------------------------------
 static int vmax(const Analysis& an) { return 16 / an.esz; }
 
-Program make_program(const Analysis& an, Family fam, bool var_two_pass) {
+Program make_program(const Analysis& an, Family fam, bool var_two_pass, bool bounds) {
   Program pg;
   const std::string S = storage_type_name(an.dtype);
   const int NS = (int)an.slots.size(), NK = (int)an.scalars.size();
@@ -531,6 +531,7 @@ Program make_program(const Analysis& an, Family fam, bool var_two_pass) {
   const int V = vmax(an);
   std::ostringstream src, sig;
   if (an.gmask) src << "#define COOT_GM " << an.gmask << "\n";
+  if (bounds) src << "#define COOT_DEBUG_BOUNDS 1\n";
   if (an.accum == 1) src << "#define COOT_ACCUM_KAHAN 1\n";
   if (an.accum == 2) src << "#define COOT_ACCUM_PLAIN 1\n";
   src << (fam == F_GEMM ? "#include \"coot_gemm.cuh\"\n" : "#include \"coot_kernels.cuh\"\n")
@@ -731,6 +732,7 @@ Program make_program(const Analysis& an, Family fam, bool var_two_pass) {
                         : std::string())
       << (an.accum == 1 ? "|kahan" : (an.accum == 2 ? "|plain" : ""))
       << (fam == F_BATCH ? "|be" + std::to_string(an.batch_be) + "b" + std::to_string(an.batch_minb) : std::string())
+      << (bounds ? "|bounds" : "")
       << "|" << an.type_str;
   pg.signature = sig.str();
   pg.source = src.str();

@@ -29,9 +29,10 @@ DTYPE_CODE = {"f32": F32, "f64": F64, "bf16": BF16, "f16": F16, "i32": I32}
 (R_NONE, R_ACCU, R_SUM, R_MEAN, R_DOT, R_NORM2, R_NORM_FRO, R_VAR, R_STDDEV, R_MIN, R_MAX, R_INDEX_MIN,
  R_INDEX_MAX, R_PROD, R_CUMSUM) = range(15)
 
-CTX_TUNE, CTX_NO_DISK_CACHE, CTX_LOG, CTX_NO_TCGEN05 = 1, 2, 4, 8
+CTX_TUNE, CTX_NO_DISK_CACHE, CTX_LOG, CTX_NO_TCGEN05, CTX_DEBUG_BOUNDS = 1, 2, 4, 8, 16
 FLAG_INT_DIV_ZERO = 1
 FLAG_WAIT_TIMEOUT = 2
+FLAG_OUT_OF_BOUNDS = 4
 MAX_NODES, MAX_LEAVES, MAX_SCALARS = 64, 8, 16
 
 
