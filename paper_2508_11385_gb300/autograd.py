@@ -23,7 +23,7 @@ from . import lib as L
 def _grad_like(t: torch.Tensor) -> torch.Tensor:
     # empty_like keeps the strides of a dense tensor (a column-major leaf gets
     # a column-major gradient); anything else gets them spelled out
-    if t.is_non_overlapping_and_dense():
+    if t.is_contiguous() or (t.dim() == 2 and t.t().is_contiguous()):
         return torch.empty_like(t)
     return torch.empty_strided(t.shape, t.stride(), dtype=t.dtype, device=t.device)
 
