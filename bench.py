@@ -1180,15 +1180,21 @@ def bench_graph(dev, stream):
     s = torch.cuda.Stream(device=dev)
     X = [torch.empty((n, n), dtype=torch.float32, device=dev).t() for _ in range(21)]
     X[0].copy_(A)
-    shapes = ["#2 X * B +", "X B % C +", "X trans B +", "X B - exp #1 C abs + /", "X B - square", "X"]
+    # the six large-tree shapes; X enters exp(A-B)/(1+abs(C)) as its C operand
+    # so that the chain stays finite (as A it overflows FP32 after two cycles)
+    shapes = ["#2 X * B +", "X B % C +", "X trans B +", "A B - exp #1 X abs + /", "X B - square", "X"]
     reds = [None, None, None, None, "sum:0", "accu"]
     side = torch.empty((1, n), dtype=torch.float32, device=dev)
     scal = torch.empty((), dtype=torch.float32, device=dev)
     calls = []
     for k in range(20):
         j = k % 6
-        prog = shapes[j].replace("X", "A")
-        ten = [X[k], B, C]
+        if j == 3:
+            prog = shapes[j].replace("X", "C")
+            ten = [A, B, X[k]]
+        else:
+            prog = shapes[j].replace("X", "A")
+            ten = [X[k], B, C]
         mats = [coot.Mat(t) for t in ten]
         if j == 5:  # accu over the square 2048x2048 view (the whole matrix), X passes through
             e = mats[0].submat(0, 0, n - 1, n - 1)
