@@ -417,7 +417,10 @@ def run_prog(args):
     for _ in range(args.warmup):
         c(sp)
     torch.cuda.synchronize()
-    ms = time_calls(lambda: c(sp), stream, reps=args.steps, warm=0)
+    flush = None
+    if args.flush:  # every call alone after a buffer twice the L2 size is overwritten
+        flush = torch.empty(2 * torch.cuda.get_device_properties(dev).L2_cache_size, dtype=torch.uint8, device=dev)
+    ms = time_calls(lambda: c(sp), stream, reps=args.steps, warm=0, flush=flush)
     info = c.info()
     print(json.dumps({"prog": args.prog, "ms": round(ms, 4), "gbs": round(info["algorithmic_bytes"] / ms / 1e6, 1),
                       "kernel": info["kernel"], "grid": info["grid"], "block": info["block"]}))
@@ -1421,6 +1424,7 @@ def main():
                     help="copy streams for the host->device operand copies of the end-to-end measurement")
     ap.add_argument("--only", default=None, help="time one tree of the workload (profiling); implies --quick")
     ap.add_argument("--prog", default=None, help="time one RPN program over the workload's leaves (profiling)")
+    ap.add_argument("--flush", action="store_true", help="--prog: time every call after overwriting the L2")
     args = ap.parse_args()
     if args.prog:
         run_prog(args)
