@@ -418,7 +418,7 @@ def run_prog(args):
         c(sp)
     torch.cuda.synchronize()
     flush = None
-    if args.flush:  # every call alone after a buffer twice the L2 size is overwritten
+    if args.flush:  # every call alone after a buffer twice the L2 size is read through L2
         flush = torch.empty(2 * torch.cuda.get_device_properties(dev).L2_cache_size, dtype=torch.uint8, device=dev)
     ms = time_calls(lambda: c(sp), stream, reps=args.steps, warm=0, flush=flush)
     info = c.info()
@@ -561,7 +561,7 @@ def run_gpu(args):
         "data": "synthetic (seeded normal(0,1) FP32 matrices generated on the device)",
         "config": {"workload": "large memory-bound trees, FP32 %dx%d A..F: 6 shapes + depth ladder L4-L8" % (n, n),
                    "trees": [t[0] for t in TREES], "l2": "inputs larger than L2 (each operand %d MiB; between two runs of a "
-                   "tree the others stream GBs); the per-tree side comparisons overwrite a buffer twice the "
+                   "tree the others stream GBs); the per-tree side comparisons read a buffer twice the "
                    "L2 size before every timed call" % (n * n * 4 >> 20), "parallelism": "replicas" if world > 1 else "single GPU"},
         "frac_of_peak": round(value / world / peak, 4),
         "peak_gbs": peak,
@@ -603,7 +603,9 @@ def time_calls(fn, stream, reps=10, warm=2, flush=None):
     events (the host prepares call k+1 while the GPU runs call k, so host
     overhead is not counted), averaged; the median of three such batches.
     With `flush` (a device buffer larger than L2), every call is timed alone
-    after the buffer is overwritten, and the median is returned: operands
+    after the buffer is read through L2 (its clean lines replace the cache's
+    contents, so no dirty line is written back inside the timed call), and the
+    median is returned: operands
     that fit in L2 are then read from HBM, as in the headline step."""
     import torch
 
@@ -613,7 +615,7 @@ def time_calls(fn, stream, reps=10, warm=2, flush=None):
     if flush is not None:
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
         for a, b in ev:
-            flush.zero_()
+            flush.sum(dtype=torch.int32)
             a.record(stream)
             fn()
             b.record(stream)
@@ -878,7 +880,7 @@ def run_extras(args, leaves, calls, per_tree_ms, bytes_per, dev, stream, peak):
     except Exception as e:  # reported, not hidden
         res["probe"] = {"error": repr(e)[:300]}
         probe = None
-    # L2 is overwritten before every timed call of the per-tree comparisons,
+    # L2 is refilled with clean lines before every timed call of the per-tree comparisons,
     # so that the 64 MiB view is read from HBM as in the headline step
     flush = torch.empty(2 * torch.cuda.get_device_properties(dev).L2_cache_size, dtype=torch.uint8, device=dev)
     # ---- unfused per-op baseline on the same trees
@@ -901,7 +903,7 @@ def run_extras(args, leaves, calls, per_tree_ms, bytes_per, dev, stream, peak):
     deep = [te[n]["speedup_fused"] for n, _, d, _ in calls if d >= 4]
     res["torch_eager"] = {"per_tree": te, "geomean_speedup_depth_ge4": round(math.exp(sum(map(math.log, deep)) / len(deep)), 2),
                           "note": "each tree as eager torch calls (one kernel per op, temporaries allocated by "
-                                  "torch's caching allocator), L2 overwritten before every timed call"}
+                                  "torch's caching allocator), L2 refilled with clean lines before every timed call"}
     torch.cuda.empty_cache()
     # ---- FP64 / INT32 variants of the six shapes
     del_names = ["axpy", "schur_plus", "trans_plus", "exp_div", "colsum_sq", "accu_submat"]
@@ -1424,7 +1426,7 @@ def main():
                     help="copy streams for the host->device operand copies of the end-to-end measurement")
     ap.add_argument("--only", default=None, help="time one tree of the workload (profiling); implies --quick")
     ap.add_argument("--prog", default=None, help="time one RPN program over the workload's leaves (profiling)")
-    ap.add_argument("--flush", action="store_true", help="--prog: time every call after overwriting the L2")
+    ap.add_argument("--flush", action="store_true", help="--prog: time every call after refilling the L2 with clean lines")
     args = ap.parse_args()
     if args.prog:
         run_prog(args)
