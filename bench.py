@@ -759,6 +759,7 @@ def bench_probe(dev):
     out = {k: round(r[k] / 1e12, 4) for k in ("f32_add", "f32_fma", "f32_div", "f32_exp", "f64_add", "f64_fma",
                                              "f64_div", "f64_exp")}
     out.update({"read_gbs": round(r["read_gbs"], 1), "copy_gbs": round(r["copy_gbs"], 1),
+                "host_read_gbs": round(r["host_read_gbs"], 1), "host_write_gbs": round(r["host_write_gbs"], 1),
                 "l2_bytes": r["l2_bytes"], "sms": r["sms"], "sm_clock_khz": r["sm_clock_khz"],
                 "buffer_bytes": r["buffer_bytes"],
                 "unit": "T operations/s for f32_* / f64_* (exp: one exp + one FMA per step); GB/s for read/copy",

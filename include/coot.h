@@ -430,12 +430,15 @@ COOT_API coot_status coot_last_launch(coot_ctx* ctx, coot_launch_info* info);
  * it allocates 1 GiB or 8x the L2 size, whichever is larger, and frees it)
  * and reports the best of several CUDA-event timings: operations per second
  * of independent dependency chains per thread (exp: one exp and one FMA per
- * step), and GB/s of a 16-byte-vector read and copy over buffers larger than
- * L2.  Returns COOT_ERR_OOM or COOT_ERR_CUDA when the device refuses. */
+ * step), GB/s of a 16-byte-vector read and copy over buffers larger than
+ * L2, and GB/s of a kernel reading and writing 256 MiB of pinned host
+ * memory (the host link as kernels see it).  Returns COOT_ERR_OOM or
+ * COOT_ERR_CUDA when the device refuses. */
 typedef struct {
   double f32_add, f32_fma, f32_div, f32_exp;  /* operations per second */
   double f64_add, f64_fma, f64_div, f64_exp;
   double read_gbs, copy_gbs;                  /* copy: bytes read + written */
+  double host_read_gbs, host_write_gbs;       /* kernel access to pinned host memory */
   int64_t buffer_bytes;                       /* bytes read per read probe  */
   int64_t l2_bytes;
   int32_t sms;

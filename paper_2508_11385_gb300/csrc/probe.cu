@@ -14,7 +14,9 @@
 // so nothing is dead code.  The exp kernels follow each exp with one fused
 // multiply-add that keeps the argument inside [-1, 1] (reported as
 // exp+FMA steps per second).  The memory kernels read (and copy) 16-byte
-// vectors over buffers several times larger than L2, grid-stride.
+// vectors over buffers several times larger than L2, grid-stride; the same
+// read and a write over 256 MiB of pinned host memory give the host link's
+// rates as a kernel sees them.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -88,6 +90,12 @@ __global__ void __launch_bounds__(kBlock) probe_read(const float4* p, long long 
   }
   const float s = acc.x + acc.y + acc.z + acc.w;
   if (s == never) sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kBlock) probe_fill(float4* dst, long long n4, float v) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride)
+    dst[i] = make_float4(v, v, v, v);
 }
 
 __global__ void __launch_bounds__(kBlock) probe_copy(const float4* src, float4* dst, long long n4) {
@@ -168,6 +176,7 @@ extern "C" coot_status coot_probe_device(int device, coot_probe_result* r) {
   const size_t bytes = std::max<size_t>((size_t)1 << 30, ((size_t)l2 * 8 + 4095) & ~(size_t)4095);
   void* buf = nullptr;
   void* sink = nullptr;
+  void* hbuf = nullptr;
   Timer t;
   coot_status st = COOT_OK;
   do {
@@ -210,7 +219,33 @@ extern "C" coot_status coot_probe_device(int device, coot_probe_result* r) {
     }
     r->copy_gbs = (double)(2 * h4 * 16) / (ms * 1e-3) / 1e9;
     r->buffer_bytes = (int64_t)bytes;
+    // the host link: kernels reading and writing pinned host memory (device
+    // addresses of host memory under unified addressing)
+    const size_t hbytes = (size_t)256 << 20;
+    if ((e = cudaHostAlloc(&hbuf, hbytes, cudaHostAllocMapped)) != cudaSuccess) {
+      st = cuda_error(e, "cudaHostAlloc (probe)");
+      break;
+    }
+    void* hdev = nullptr;
+    if ((e = cudaHostGetDevicePointer(&hdev, hbuf, 0)) != cudaSuccess) {
+      st = cuda_error(e, "cudaHostGetDevicePointer");
+      break;
+    }
+    memset(hbuf, 0, hbytes);
+    const long long hn4 = (long long)(hbytes / 16);
+    if ((e = best_ms(t, 3, [&] { probe_read<<<grid, kBlock>>>((const float4*)hdev, hn4, -1.f, (float*)sink); },
+                     &ms)) != cudaSuccess) {
+      st = cuda_error(e, "host read probe");
+      break;
+    }
+    r->host_read_gbs = (double)hbytes / (ms * 1e-3) / 1e9;
+    if ((e = best_ms(t, 3, [&] { probe_fill<<<gridc, kBlock>>>((float4*)hdev, hn4, 1.f); }, &ms)) != cudaSuccess) {
+      st = cuda_error(e, "host write probe");
+      break;
+    }
+    r->host_write_gbs = (double)hbytes / (ms * 1e-3) / 1e9;
   } while (0);
+  if (hbuf) cudaFreeHost(hbuf);
   if (buf) cudaFree(buf);
   if (sink) cudaFree(sink);
   cudaSetDevice(prev);

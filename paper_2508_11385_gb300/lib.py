@@ -65,7 +65,8 @@ class coot_launch_info(ctypes.Structure):
 
 class coot_probe_result(ctypes.Structure):
     _fields_ = [(f, ctypes.c_double) for f in ("f32_add", "f32_fma", "f32_div", "f32_exp", "f64_add", "f64_fma",
-                                               "f64_div", "f64_exp", "read_gbs", "copy_gbs")] + [
+                                               "f64_div", "f64_exp", "read_gbs", "copy_gbs", "host_read_gbs",
+                                               "host_write_gbs")] + [
         ("buffer_bytes", ctypes.c_int64), ("l2_bytes", ctypes.c_int64), ("sms", ctypes.c_int32),
         ("sm_clock_khz", ctypes.c_int32)]
 

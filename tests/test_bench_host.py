@@ -94,3 +94,40 @@ def test_algorithmic_bytes_of_the_workload_trees():
             "L6": 24 * N, "L7": 24 * N, "L8": 28 * N}
     got = {name: bench.algorithmic_bytes(prog, n, 4) for name, prog, _ in bench.TREES}
     assert got == want
+
+
+def test_f64_alu_bound_counts_the_trees_fp64_operations():
+    # rates in T operations/s: add 1, fma 2, div 0.5, exp+fma 0.25 -> exp alone 1/0.25 - 1/2 = 3.5 ps
+    probe = {"f64_add": 1.0, "f64_fma": 2.0, "f64_div": 0.5, "f64_exp": 0.25}
+    n = 10 ** 6
+    ms, ops = bench.f64_alu_bound_ms("A B - exp #1 C abs + /", n, probe)
+    assert ops == ["add", "exp", "add", "div"]  # abs uses no FP64 arithmetic
+    want = n * (1.0 + 3.5 + 1.0 + 2.0) * 1e-12 * 1e3
+    assert abs(ms - want) <= 1e-12 * want
+    ms, ops = bench.f64_alu_bound_ms("A B - square sum:0", n, probe)
+    assert ops == ["add", "mul", "add"]
+    assert abs(ms - n * (1.0 + 0.5 + 1.0) * 1e-9) <= 1e-15
+    ms, ops = bench.f64_alu_bound_ms("A submat:1:1:4:4 accu", 16, probe)
+    assert ops == ["add"]
+
+
+def test_torch_eager_trees_match_the_oracle():
+    """The torch-eager baseline computes the same trees as the library (on CPU
+    tensors here, column-major like the workload's leaves)."""
+    import numpy as np
+
+    import oracle
+    from paper_2508_11385_gb300 import workloads
+
+    n = 48
+    lv = workloads.large_trees("f32", n=n, device="cpu")
+    host = [workloads.to_numpy_colmajor(t) for t in lv]
+    for name, prog, _ in bench.TREES:
+        p = prog.replace("submat:1000:1000:4096:4096", "submat:5:7:30:31")
+        y = bench.torch_eager_fn(p, lv)()
+        r = oracle.evaluate(p, host, "f32")
+        g = y.double().numpy().reshape(r.value.shape) if y.dim() > 0 else np.array([[y.item()]])
+        # FP32 eager arithmetic against the FP64 oracle: within the oracle's
+        # propagated FP32 bound plus the FP32 summation of up to n*n terms
+        tol = r.bound + 1e-6 * np.abs(r.value) + (n * n) * 2.0 ** -24 * np.abs(r.value)
+        assert np.all(np.abs(g - r.value) <= tol), name
