@@ -1392,6 +1392,9 @@ extern "C" coot_status coot_batch_create(coot_ctx* ctx, const coot_tree* tree, i
     if (an.gmask)
       return set_error(COOT_ERR_UNSUPPORTED, "problem %lld: row-broadcast, diagonal or row-strided reads and outputs "
                        "are not batched", (long long)q);
+    if (an.nr >= INT32_MAX || an.nc >= INT32_MAX)
+      return set_error(COOT_ERR_UNSUPPORTED, "problem %lld: %lld x %lld; batched problems have fewer than 2^31 - 1 "
+                       "rows and columns", (long long)q, (long long)an.nr, (long long)an.nc);
     coot::BatchProblem& bp = probs[q];
     memset(&bp, 0, sizeof bp);
     for (size_t i = 0; i < an.slots.size(); ++i) {
