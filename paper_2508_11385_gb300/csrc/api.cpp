@@ -1233,7 +1233,7 @@ extern "C" coot_status coot_gemm_eval(coot_ctx* ctx, const coot_mat* A, int32_t 
       if (e != cudaSuccess) return cuda_error(e, "coot_gemm_tc shared memory");
       mod->gemm_tc_smem = true;
     }
-    block = 192;  // persistent: at most one CTA per SM
+    block = coot::GEMM_TC_THREADS;  // persistent: at most one CTA per SM
     n_blocks = (unsigned)std::min<int64_t>(gp.tiles_m * gp.tiles_n, std::max(ctx->sms, 1));
     e = cudaLaunchKernel(kf, dim3(n_blocks), dim3(block), args, coot::GEMM_TC_SMEM, stream);
   } else {

@@ -236,9 +236,9 @@ __device__ __forceinline__ void gemm_kernel(const GemmParams& gp) {
 // operand layout: an operand with K adjacent (op(A) of trans(X), op(B) of
 // Y) is "K-major", one with M or N adjacent "MN-major".
 //   Persistent: one CTA per SM (192 KiB of operand stages) walks output
-//   tiles of 128 x 256, 192 threads in three roles:
-//   * warp 0, one thread: TMA loads of the operand tiles (64 K values x 128
-//     or 256 rows, 128-byte swizzle) into a 4-stage ring; it waits for a
+//   tiles of 256 x 256, 320 threads in three roles:
+//   * warp 0, one thread: TMA loads of the operand tiles (64 K values x 256
+//     rows each, 128-byte swizzle) into a 3-stage ring; it waits for a
 //     stage's "empty" barrier and announces the stage's bytes on its "full"
 //     barrier.  K-major: one box per operand, each tile row 64 K values =
 //     128 bytes, 8-row groups forming 1 KiB swizzle atoms -- the K-major
@@ -247,19 +247,27 @@ __device__ __forceinline__ void gemm_kernel(const GemmParams& gp) {
 //     (128 bytes, the adjacent dimension) x 64 K values, one per 64 rows of
 //     the tile, 8 KiB apart -- the MN-major SWIZZLE_128B layout (8 KiB
 //     between 64-row blocks, 1 KiB between groups of 8 K values; a K = 16
-//     step moves the start address 2 KiB).  TMA fills rows and K values
-//     past the matrix with zeros, so ragged m, n and k need no special case.
-//   * warp 1, one thread: waits for "full", issues the four K = 16 MMAs of a
-//     stage and commits them to its "empty" barrier.  The FP32 accumulator
-//     lives in tensor memory, double-buffered (2 x 256 columns, lane = tile
-//     row): a tile's MMAs go to one buffer while the epilogue drains the
-//     other; the last commit of a tile arrives on the buffer's "acc full"
-//     barrier.
-//   * warps 2-5, the epilogue: warp w reads lanes 32 (w % 4).. (rows) of the
-//     accumulator, 32 or 16 columns at a time, loads the tree's other leaves
-//     at the same (i, j) ahead of the tensor-memory read, applies the tree
-//     and stores Y (consecutive lanes: consecutive rows of the column-major
-//     result); it then releases the buffer on its "acc empty" barrier.
+//     step moves the start address 2 KiB).  Either way the tile's rows
+//     128-255 start 16 KiB after its rows 0-127.  TMA fills rows and K
+//     values past the matrix with zeros, so ragged m, n and k need no
+//     special case.
+//   * warp 1, one thread: waits for "full" and issues, per K = 16 step, two
+//     M = 128, N = 256 MMAs sharing the B tile: rows 0-127 into accumulator
+//     columns 0-255 and rows 128-255 into columns 256-511 (FP32 in tensor
+//     memory, lane = row within the half); it commits each stage to its
+//     "empty" barrier and the tile's last step to "acc full".  A 256 x 256
+//     tile does 128 FLOP per operand byte staged (a 128 x 256 tile 85), so
+//     the three stages hold 1.5x the MMA work of four 128 x 256 stages in
+//     the same shared memory -- the ring's depth against the TMA round trip
+//     is what bounded the smaller tile.  The accumulator fills tensor
+//     memory, so a tile's MMAs start once the epilogue has drained the
+//     previous tile ("acc empty"); the producer keeps loading meanwhile.
+//   * warps 2-9, the epilogue: warp w reads lanes 32 (w % 4).. (rows) of
+//     each half of the accumulator -- columns 0-127 for warps 2-5, 128-255
+//     for warps 6-9 -- 32 or 16 columns at a time, loads the
+//     tree's other leaves at the same (i, j) ahead of the tensor-memory read,
+//     applies the tree and stores Y (consecutive lanes: consecutive rows of
+//     the column-major result); it then releases the accumulator.
 //   Tiles are numbered in groups of 16 tile rows (M), N-major inside a
 //   group, and CTA b takes tiles b, b + grid, ...: the tiles in flight share
 //   their A and B tiles in L2.
@@ -294,7 +302,7 @@ template <bool KMAJ> __device__ constexpr unsigned long long tc_kstep() { return
 // storage type, M = 128, N = 256; bits 15 / 16 mark an MN-major A / B
 template <class S, bool KA, bool KB> __device__ __forceinline__ u32 tc_idesc() {
   return (1u << 4) | (TcFmt<S>::v << 7) | (TcFmt<S>::v << 10) | ((KA ? 0u : 1u) << 15) | ((KB ? 0u : 1u) << 16) |
-         ((u32)(TC_BN >> 3) << 17) | ((u32)(TC_BM >> 4) << 24);
+         ((u32)(TC_BN >> 3) << 17) | ((u32)(GEMM_TC_MMA_M >> 4) << 24);
 }
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -388,16 +396,17 @@ __device__ __forceinline__ void gemm_tc_kernel(const GemmParams& gp) {
   const u32 sbase = (smem_u32(tc_dyn) + 1023u) & ~1023u;
   const u32 full0 = sbase + TC_BAR_OFF, empty0 = full0 + 8 * TC_ST;
   const u32 afull0 = empty0 + 8 * TC_ST, aempty0 = afull0 + 16, tslot = aempty0 + 16;
+  // the A tile's two halves of 128 rows: K-major, 128 rows of 128 bytes; MN-major,
+  // two boxes of 64 rows (8 KiB each) -- 16 KiB apart either way
+  constexpr u32 A_HALF = 16384;
   TcWait wait{false, 0};
   if (threadIdx.x == 0) {
     for (int st = 0; st < TC_ST; ++st) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full0 + 8 * st));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(empty0 + 8 * st));
     }
-    for (int b = 0; b < 2; ++b) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(afull0 + 8 * b));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(aempty0 + 8 * b));
-    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(afull0));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(aempty0), "n"(GEMM_TC_THREADS - 64));
     asm volatile("fence.mbarrier_init.release.cluster;");
     asm volatile("prefetch.tensormap [%0];" ::"l"(gp.tma_a) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(gp.tma_b) : "memory");
@@ -436,78 +445,88 @@ __device__ __forceinline__ void gemm_tc_kernel(const GemmParams& gp) {
     __syncwarp();
   } else if (warp == 1) {
     if (lane == 0) {
-      // MMA issue
+      // MMA issue: per K = 16 step, rows 0-127 of the tile into accumulator
+      // columns 0-255 and rows 128-255 into columns 256-511, both with the
+      // whole B tile
       const u32 idesc = tc_idesc<S, KA, KB>();
       unsigned it = 0, lt = 0;
       for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++lt) {
-        const u32 ab = lt & 1u;
-        wait(aempty0 + 8 * ab, ((lt >> 1) & 1u) ^ 1u);  // the epilogue has drained this buffer
+        wait(aempty0, (lt & 1u) ^ 1u);  // the epilogue has drained the accumulator
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const u32 acc = tmem + ab * (u32)TC_BN;
         for (int kt = 0; kt < nkt; ++kt, ++it) {
           const int st = (int)(it % TC_ST);
           wait(full0 + 8 * st, (it / TC_ST) & 1u);
           asm volatile("tcgen05.fence::after_thread_sync;");
-          const unsigned long long ad = tc_desc<KA>(sbase + (u32)(st * TC_A_BYTES));
+          const u32 abase = sbase + (u32)(st * TC_A_BYTES);
+          const unsigned long long ad0 = tc_desc<KA>(abase);
+          const unsigned long long ad1 = tc_desc<KA>(abase + A_HALF);
           const unsigned long long bd = tc_desc<KB>(sbase + (u32)(TC_ST * TC_A_BYTES + st * TC_B_BYTES));
 #pragma unroll
           for (int kk = 0; kk < TC_BK / 16; ++kk) {
             const u32 accum = (kt > 0 || kk > 0) ? 1u : 0u;
             asm volatile(
                 "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc),
-                "l"(ad + tc_kstep<KA>() * kk), "l"(bd + tc_kstep<KB>() * kk), "r"(idesc), "r"(accum));
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                "l"(ad0 + tc_kstep<KA>() * kk), "l"(bd + tc_kstep<KB>() * kk), "r"(idesc), "r"(accum));
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + (u32)TC_BN),
+                "l"(ad1 + tc_kstep<KA>() * kk), "l"(bd + tc_kstep<KB>() * kk), "r"(idesc), "r"(accum));
           }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                            empty0 + 8 * st)
                        : "memory");
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         afull0 + 8 * ab)
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(afull0)
                      : "memory");
       }
     }
     __syncwarp();
   } else {
-    // epilogue
+    // epilogue: the tile's two halves of rows, each from its 256 accumulator
+    // columns; warp w takes lane quarter w % 4 and columns 128 (w - 2) / 4 ..
     Scal<C, NK> k;
 #pragma unroll
     for (int q = 0; q < NK; ++q) k.k[q] = scalar_from_bits<C>(p.k[q]);
     const int quarter = warp & 3;
+    const int c0 = (TC_BN / 2) * ((warp - 2) >> 2);
     unsigned lt = 0;
     for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++lt) {
       long long m0, n0;
       tc_tile_origin(gp, tile, m0, n0);
-      const u32 ab = lt & 1u;
-      wait(afull0 + 8 * ab, (lt >> 1) & 1u);
+      wait(afull0, lt & 1u);
       __syncwarp();
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const long long i = m0 + 32 * quarter + lane;
 #pragma unroll 1
-      for (int cc = 0; cc < TC_BN / W; ++cc) {
-        if (n0 + W * cc >= N) break;  // warp-uniform
-        // the other leaves first, then the accumulator
-        Vals<C, NS, 1> x[W];
+      for (int half = 0; half < 2; ++half) {
+        const long long i = m0 + GEMM_TC_MMA_M * half + 32 * quarter + lane;
+        if (m0 + GEMM_TC_MMA_M * half >= M) break;  // warp-uniform
+#pragma unroll 1
+        for (int cc = c0 / W; cc < (c0 + TC_BN / 2) / W; ++cc) {
+          if (n0 + W * cc >= N) break;  // warp-uniform
+          // the other leaves first, then the accumulator
+          Vals<C, NS, 1> x[W];
 #pragma unroll
-        for (int t = 0; t < W; ++t) {
-          const long long j = n0 + W * cc + t;
+          for (int t = 0; t < W; ++t) {
+            const long long j = n0 + W * cc + t;
 #pragma unroll
-          for (int s2 = 0; s2 < NS; ++s2)
-            if (s2 != PS) x[t].v[s2][0] = (i < M && j < N) ? IO<S>::load1(at_slot<S>(p, s2, i, j)) : C(0);
-        }
-        u32 v[W];
-        tmem_ld<W>(tmem + ab * (u32)TC_BN + ((u32)(32 * quarter) << 16) + (u32)(W * cc), v);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            for (int s2 = 0; s2 < NS; ++s2)
+              if (s2 != PS) x[t].v[s2][0] = (i < M && j < N) ? IO<S>::load1(at_slot<S>(p, s2, i, j)) : C(0);
+          }
+          u32 v[W];
+          tmem_ld<W>(tmem + (u32)(TC_BN * half) + ((u32)(32 * quarter) << 16) + (u32)(W * cc), v);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int t = 0; t < W; ++t) {
-          const long long j = n0 + W * cc + t;
-          x[t].v[PS][0] = __uint_as_float(v[t]);
-          const C y = T::ev(x[t], k, wait.err, 0);
-          if (i < M && j < N) IO<S>::store1(at_out_g<S>(p, i, j), y);
+          for (int t = 0; t < W; ++t) {
+            const long long j = n0 + W * cc + t;
+            x[t].v[PS][0] = __uint_as_float(v[t]);
+            const C y = T::ev(x[t], k, wait.err, 0);
+            if (i < M && j < N) IO<S>::store1(at_out_g<S>(p, i, j), y);
+          }
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(aempty0 + 8 * ab) : "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(aempty0) : "memory");
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");

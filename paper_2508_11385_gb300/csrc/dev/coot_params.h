@@ -99,7 +99,14 @@ struct GemmParams {
   alignas(64) unsigned long long tma_b[16];
   long long tiles_m, tiles_n;
 };
-constexpr int GEMM_TC_BM = 128, GEMM_TC_BN = 256, GEMM_TC_BK = 64, GEMM_TC_STAGES = 4;
+// tcgen05 kernel: 256 x 256 output tiles (two M = 128 MMAs per K step, one
+// for each half of the rows), 64 K values per stage, 3 stages
+constexpr int GEMM_TC_BM = 256, GEMM_TC_BN = 256, GEMM_TC_BK = 64, GEMM_TC_STAGES = 3;
+constexpr int GEMM_TC_MMA_M = 128;
+// threads of the tcgen05 kernel: a producer warp, an MMA warp and 8
+// epilogue warps (two per quarter of the tensor-memory lanes, each taking
+// half of the accumulator's columns)
+constexpr int GEMM_TC_THREADS = 320;
 // dynamic shared memory of the tcgen05 kernel: the stages, barriers and
 // 1 KiB of slack to align the stages to the 1 KiB swizzle atom
 constexpr int GEMM_TC_SMEM = GEMM_TC_STAGES * (GEMM_TC_BM + GEMM_TC_BN) * GEMM_TC_BK * 2 + 256 + 1024;

@@ -86,7 +86,7 @@ KG(chk_gemm_bf16_mn, (gemm_kernel<TG, bf16, 2, 1, 0, false, false>))
 KG(chk_gemm_f16_km, (gemm_kernel<TG, f16, 2, 1, 0, true, false>))
 KG(chk_gemm_bf16_mk, (gemm_kernel<Leaf<0>, bf16, 1, 0, 0, false, true>))
 #define KT(name, body) \
-  extern "C" __global__ void __launch_bounds__(192, 1) name(const __grid_constant__ GemmParams p) { body(p); }
+  extern "C" __global__ void __launch_bounds__(GEMM_TC_THREADS, 1) name(const __grid_constant__ GemmParams p) { body(p); }
 KT(chk_gemm_tc_bf16_kk, (gemm_tc_kernel<TG, bf16, 2, 1, 0, true, true>))
 KT(chk_gemm_tc_f16_kk, (gemm_tc_kernel<Leaf<0>, f16, 1, 0, 0, true, true>))
 KT(chk_gemm_tc_bf16_mn, (gemm_tc_kernel<TG, bf16, 2, 1, 0, false, false>))

@@ -698,12 +698,12 @@ Program make_program(const Analysis& an, Family fam, bool var_two_pass, bool bou
          "GemmParams", 2);
     add("coot_gemm", 1, 1, 256);
     // persistent tcgen05 kernel: TMA loads, accumulator in tensor memory, one CTA per SM
-    wrap("coot_gemm_tc", 192,
+    wrap("coot_gemm_tc", coot::GEMM_TC_THREADS,
          std::string("gemm_tc_kernel<T_t, S_t, ") + std::to_string(NS) + ", " + std::to_string(NK) + ", " +
              std::to_string(an.gemm_ps) + ", " + (an.gemm_ka ? "true" : "false") + ", " +
              (an.gemm_kb ? "true" : "false") + ">",
          "GemmParams", 1);
-    add("coot_gemm_tc", 1, 1, 192);
+    add("coot_gemm_tc", 1, 1, coot::GEMM_TC_THREADS);
   } else if (fam == F_ADJ) {
     std::vector<std::pair<int, int>> avu = {{V, 1}, {V, 2}, {1, 4}};
     for (auto [v, u] : avu) {
