@@ -403,7 +403,7 @@ def run_prog(args):
 
     __graft_entry__.build()
     stream = torch.cuda.current_stream(dev)
-    lv = workloads.large_trees("f32", n=args.n, n_leaves=6, device=dev)
+    lv = workloads.large_trees(args.prog_dtype, n=args.n, n_leaves=6, device=dev, m=args.prog_cols)
     toks = args.prog.split()
     for i, t in enumerate(toks[:-1]):
         if len(t) == 1 and "A" <= t <= "F":
@@ -1446,6 +1446,9 @@ def main():
     ap.add_argument("--only", default=None, help="time one tree of the workload (profiling); implies --quick")
     ap.add_argument("--prog", default=None, help="time one RPN program over the workload's leaves (profiling)")
     ap.add_argument("--flush", action="store_true", help="--prog: time every call after refilling the L2 with clean lines")
+    ap.add_argument("--prog-dtype", default="f32", choices=["f32", "f64", "bf16", "f16", "i32"],
+                    help="--prog: storage type of the leaves")
+    ap.add_argument("--prog-cols", type=int, default=None, help="--prog: columns of the leaves (default n)")
     args = ap.parse_args()
     if args.prog:
         run_prog(args)

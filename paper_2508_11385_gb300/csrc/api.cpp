@@ -203,6 +203,15 @@ struct Launch {
 
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+bool is_scanp(const std::string& name) { return name.compare(0, 11, "coot_scanp_") == 0; }
+
+// the one-pass scan along rows serves plain matrices (not a Cube's slices)
+// with at least one band of 32 rows per SM; else the segmented two-pass scan
+bool scanp_fits(const cg::Analysis& an, int sms) {
+  return an.scan() && an.red.dim == 1 && an.n_seg() == 1 && an.nr >= 32LL * sms;
+}
+
+
 int64_t n_red_outputs(const cg::Analysis& an) { return an.n_outputs(); }
 
 // fill the launch shape of a fused program for a given kernel variant/config
@@ -301,6 +310,15 @@ void shape_launch(coot_ctx* ctx, const cg::Analysis& an, const cg::Choice& ch, c
       const int64_t units = std::max<int64_t>(C, 1) * nseg;
       L->grid = (int)std::max<int64_t>(1, std::min(ceil_div(units, wpb), 4 * resident));
       L->partial_bytes = (nseg > 1) ? (size_t)(C * nseg * ab8) : 0;
+    } else if (is_scanp(k.name)) {
+      // one pass: a block (of the kernel's own size) per band of 32 V rows
+      L->block = k.block;
+      const int64_t nrb = std::max<int64_t>(1, ceil_div(R, 32 * (int64_t)k.vec));
+      p.n_row_blocks = nrb;
+      p.n_splits = 1;
+      p.units_per_col = std::max<int64_t>(C, 1);
+      L->grid = (int)nrb;
+      L->partial_bytes = 0;
     } else {
       // a thread per V rows of a (row block, column segment)
       const int64_t nrb = std::max<int64_t>(1, ceil_div(R, (int64_t)block * k.vec));
@@ -357,6 +375,7 @@ int default_variant(const cg::Program& pg, const cg::Choice& ch) {
   for (int i = 0; i < (int)pg.kernels.size(); ++i) {
     const cg::KernelSpec& k = pg.kernels[i];
     if (k.name.find("_p2") != std::string::npos || k.name.find("_t_") != std::string::npos) continue;
+    if (is_scanp(k.name)) continue;
     if (!ch.vec_ok && k.vec > 1) continue;
     if (best < 0) best = i;
     if (ch.vec_ok && k.vec > 1 && k.unroll == 2) return i;
@@ -538,7 +557,9 @@ static coot_status run_fused(coot_ctx* ctx, const cg::Analysis& an, const coot_m
   int forced = -1;
   if (const char* fk = getenv("COOT_FORCE_KERNEL")) {
     for (int i = 0; i < (int)pg.kernels.size(); ++i)
-      if (pg.kernels[i].name == fk && (ch.vec_ok || pg.kernels[i].vec == 1)) forced = i;
+      if (pg.kernels[i].name == fk && (ch.vec_ok || pg.kernels[i].vec == 1) &&
+          (!is_scanp(fk) || an.n_seg() == 1))
+        forced = i;
   }
   if (forced >= 0) {
     cfg.kidx = forced;
@@ -555,6 +576,10 @@ static coot_status run_fused(coot_ctx* ctx, const cg::Analysis& an, const coot_m
       cfg = tu->second;
     } else {
       cfg.kidx = default_variant(pg, ch);
+      if (scanp_fits(an, ctx->sms)) {
+        for (int i = 0; i < (int)pg.kernels.size(); ++i)
+          if (pg.kernels[i].name == "coot_scanp_v1u16w8") cfg.kidx = i;
+      }
       cfg.block = pg.kernels[cfg.kidx].block;
       if (ch.fam == cg::F_ROW) cfg.block = 256;
       cfg.blocks_per_sm = occupancy(m, pg.kernels[cfg.kidx].name, cfg.block);
@@ -648,6 +673,8 @@ coot_status tune(coot_ctx* ctx, const cg::Analysis& an, const cg::Choice& ch, co
     const cg::KernelSpec& k = pg.kernels[ki];
     if (k.name.find("_p2") != std::string::npos || k.name.find("_t_") != std::string::npos) continue;
     if (!ch.vec_ok && k.vec > 1) continue;
+    const bool one_pass = is_scanp(k.name);  // its grid is fixed by the rows
+    if (one_pass && an.n_seg() != 1) continue;
     std::vector<int> blocks;
     if (ch.fam == cg::F_TILE || ch.fam == cg::F_SCAN) blocks = {256};
     else if (ch.fam == cg::F_ROW) blocks = {128, 256, 512};
@@ -656,7 +683,7 @@ coot_status tune(coot_ctx* ctx, const cg::Analysis& an, const cg::Choice& ch, co
       if (block > k.block) continue;
       int occ = occupancy(m, k.name, block);
       std::vector<int> bpss = {occ};
-      for (int b : {1, 2, 4}) if (b < occ) bpss.push_back(b);
+      for (int b : {1, 2, 4}) if (b < occ && !one_pass) bpss.push_back(b);
       std::vector<int> splits = {0};
       if (ch.fam == cg::F_COL)
         for (int g = 1; g <= block / 32; g *= 2) splits.push_back(g);
@@ -669,7 +696,7 @@ coot_status tune(coot_ctx* ctx, const cg::Analysis& an, const cg::Choice& ch, co
         splits.push_back(1);
         for (int64_t w2 : {1, 2, 4, 8, 16}) splits.push_back((int)std::max<int64_t>(1, ceil_div(w2 * res, strips)));
       }
-      if (ch.fam == cg::F_SCAN) splits.push_back(1);  // one pass, no segments
+      if (ch.fam == cg::F_SCAN && !one_pass) splits.push_back(1);  // one pass, no segments
       for (int bps : bpss)
       for (int split : splits) {
         Launch L = base;

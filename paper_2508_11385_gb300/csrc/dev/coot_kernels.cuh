@@ -1302,7 +1302,7 @@ __device__ __forceinline__ void scan_row_kernel(const Params& p) {
         C out[V];
 #pragma unroll
         for (int l = 0; l < V; ++l) {
-          run[l].add(T::ev(x[g], k, err, l));
+          if (i + l < nr) run[l].add(T::ev(x[g], k, err, l));  // rows past the end are not evaluated
           out[l] = run[l].out();
         }
         if constexpr (PASS == 2) {
@@ -1320,6 +1320,206 @@ __device__ __forceinline__ void scan_row_kernel(const Params& p) {
 #pragma unroll
     for (int l = 0; l < V; ++l)
       if (i + l < nr) ((A*)p.partials)[sg * nr + i + l] = run[l];
+  }
+  if (err) atomicOr(p.err_flag, err);
+}
+
+// ---------------------------------------------------------------------------
+// scanp: cumsum along dim 1 in one pass.  A block owns a band of 32 V rows
+// (lane = V rows) and walks the columns in panels of NW x UC: warp w takes
+// UC consecutive columns of the panel, evaluates the tree there and forms its
+// rows' partial sums; the partials go to shared memory, and after one block
+// barrier warp w starts from the band's carry plus the partials of warps
+// 0 .. w-1, in that order, and writes its columns.  The last warp forms the
+// next panel's carry.  Every row is read and written once and no block waits
+// on another; the order of additions is fixed by (V, UC, NW), so results are
+// deterministic.  The next panel's loads are issued before the barrier.
+// ---------------------------------------------------------------------------
+// V rows of slot s from q, the address of this thread's first row in some
+// column (a row broadcast reads one element for all V rows)
+template <class S, int V, class C>
+__device__ __forceinline__ void scanp_rows(const Params& p, int s, const S* q, C (&v)[V]) {
+  if (gen_slot(s)) {
+    if (p.rs[s] == 0) {
+      const C x = sload1<S>(p, s, q);
+#pragma unroll
+      for (int l = 0; l < V; ++l) v[l] = x;
+    } else {
+#pragma unroll
+      for (int l = 0; l < V; ++l) v[l] = sload1<S>(p, s, q + l * p.rs[s]);
+    }
+  } else if (slot_ok<S>(p, s, q, V)) {
+    IO<S>::template load<V>(q, v);
+  } else {
+#pragma unroll
+    for (int l = 0; l < V; ++l) v[l] = C(0);
+  }
+}
+
+// the UC columns from c0 of every slot at this thread's rows.  FULL: all V
+// rows and all UC columns are inside the tree (no checks); else rows at or
+// past nr read 0 and columns at or past nc are not read.
+template <bool FULL, class S, int NS, int V, int UC, class X>
+__device__ __forceinline__ void scanp_load(const Params& p, const S* const (&rp)[NS], long long i, long long c0,
+                                           long long nr, long long nc, X (&x)[UC]) {
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const long long ld = p.ld[s];
+    const S* q = rp[s] + c0 * ld;
+#pragma unroll
+    for (int u = 0; u < UC; ++u, q += ld) {
+      if constexpr (FULL) {
+        scanp_rows<S, V>(p, s, q, x[u].v[s]);
+      } else if (c0 + u < nc) {
+#pragma unroll
+        for (int l = 0; l < V; ++l)
+          x[u].v[s][l] = (i + l < nr) ? sload1<S>(p, s, gen_slot(s) ? q + l * p.rs[s] : q + l) : typename X::C(0);
+      }
+    }
+  }
+}
+
+// One panel of warp w in two halves around the block barrier, which stays in
+// scanp_kernel: a thread takes the checked (FULL = false) or the unchecked
+// form of each half by its own rows and columns, so the forms may differ
+// between the lanes of a warp and neither half may hold a barrier.
+// First half: evaluate the tree on the loaded columns, form the rows' partial
+// sums, issue the next panel's loads, publish the partial sums.
+template <bool FULL, class T, class S, int NS, int V, int UC, int NW, class X, class K, class C>
+__device__ __forceinline__ void scanp_eval(const Params& p, const K& k, u32& err, X (&x)[UC], C (&y)[UC][V],
+                                           ScanAcc<C> (&agg)[V], ScanAcc<C> (&aggs)[NW][32 * V], bool more,
+                                           bool more_full, const S* const (&rp)[NS], long long i, long long c0,
+                                           long long nr, long long nc) {
+  constexpr int PW = NW * UC;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int l = 0; l < V; ++l) agg[l].init();
+#pragma unroll
+  for (int u = 0; u < UC; ++u)
+#pragma unroll
+    for (int l = 0; l < V; ++l) {
+      if (FULL || ((c0 + u < nc) && (i + l < nr))) {
+        y[u][l] = T::ev(x[u], k, err, l);
+        agg[l].add(y[u][l]);
+      } else {
+        y[u][l] = C(0);
+      }
+    }
+  if (more) {
+    if (more_full)
+      scanp_load<true, S, NS, V, UC>(p, rp, i, c0 + PW, nr, nc, x);
+    else if (i < nr)
+      scanp_load<false, S, NS, V, UC>(p, rp, i, c0 + PW, nr, nc, x);
+  }
+#pragma unroll
+  for (int l = 0; l < V; ++l) aggs[w][lane * V + l] = agg[l];
+}
+
+// Second half: start from the band's carry plus the partial sums of the warps
+// before this one (in warp order), write the panel's columns; the last warp
+// forms the next panel's carry.
+template <bool FULL, class S, int V, int UC, int NW, class C>
+__device__ __forceinline__ void scanp_write(const Params& p, const C (&y)[UC][V], const ScanAcc<C> (&agg)[V],
+                                            const ScanAcc<C> (&aggs)[NW][32 * V], const ScanAcc<C> (&carry_in)[32 * V],
+                                            ScanAcc<C> (&carry_out)[32 * V], S* op, long long i, long long c0,
+                                            long long nr, long long nc) {
+  typedef ScanAcc<C> A;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  A base[V];
+#pragma unroll
+  for (int l = 0; l < V; ++l) {
+    base[l] = carry_in[lane * V + l];
+    for (int q = 0; q < w; ++q) base[l].add(aggs[q][lane * V + l]);
+  }
+  if (w == NW - 1) {
+#pragma unroll
+    for (int l = 0; l < V; ++l) {
+      A nx = base[l];
+      nx.add(agg[l]);
+      carry_out[lane * V + l] = nx;
+    }
+  }
+  if (!FULL && i >= nr) return;
+  const long long old = p.out_ld;
+  S* o = op + c0 * old;
+#pragma unroll
+  for (int u = 0; u < UC; ++u, o += old) {
+    if (!FULL && c0 + u >= nc) break;
+    C out[V];
+#pragma unroll
+    for (int l = 0; l < V; ++l) {
+      base[l].add(y[u][l]);
+      out[l] = base[l].out();
+    }
+    if (COOT_GM & GM_OUT) {
+#pragma unroll
+      for (int l = 0; l < V; ++l)
+        if (FULL || i + l < nr) sstore1<S>(p, o + l * p.out_rs, out[l]);
+    } else if (FULL) {
+      if (out_ok<S>(p, o, V)) IO<S>::template store<V>(o, out);
+    } else {
+#pragma unroll
+      for (int l = 0; l < V; ++l)
+        if (i + l < nr) sstore1<S>(p, o + l, out[l]);
+    }
+  }
+}
+
+template <class T, class S, int NS, int NK, int V, int UC, int NW>
+__device__ __forceinline__ void scanp_kernel(const Params& p) {
+  typedef typename ctype<S>::type C;
+  typedef ScanAcc<C> A;
+  constexpr int RB = 32 * V, PW = NW * UC;
+  __shared__ A aggs[2][NW][RB];
+  __shared__ A carry_s[2][RB];
+  if (blockDim.x != 32 * NW) return;  // the panel needs exactly NW warps (uniform over the block)
+  Scal<C, NK> k;
+#pragma unroll
+  for (int q = 0; q < NK; ++q) k.k[q] = scalar_from_bits<C>(p.k[q]);
+  u32 err = 0;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long nr = p.n_rows, nc = p.n_cols;
+  const long long i = (long long)blockIdx.x * RB + (long long)lane * V;
+  const bool fullv = (i + V <= nr);
+  if (w == 0) {
+#pragma unroll
+    for (int l = 0; l < V; ++l) carry_s[0][lane * V + l].init();
+  }
+  // this thread's first row in column 0 of every slot and of the output
+  // (formed only for rows inside the tree)
+  const long long ii = (i < nr) ? i : 0;
+  const S* rp[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) rp[s] = (const S*)p.src[s] + (gen_slot(s) ? ii * p.rs[s] : ii);
+  S* op = (S*)p.out + ((COOT_GM & GM_OUT) ? ii * p.out_rs : ii);
+  const long long npan = (nc + PW - 1) / PW;
+  Vals<C, NS, V> x[UC];
+  {
+    const long long c0 = (long long)w * UC;
+    if (fullv && c0 + UC <= nc)
+      scanp_load<true, S, NS, V, UC>(p, rp, i, c0, nr, nc, x);
+    else if (i < nr)
+      scanp_load<false, S, NS, V, UC>(p, rp, i, c0, nr, nc, x);
+  }
+  // every thread runs every panel and reaches the one barrier below once per
+  // panel, whatever form of the halves it takes
+  for (long long pan = 0; pan < npan; ++pan) {
+    const int b = (int)(pan & 1);
+    const long long c0 = pan * PW + (long long)w * UC;
+    const bool full = fullv && (c0 + UC <= nc);
+    const bool more = pan + 1 < npan;
+    const bool more_full = fullv && (c0 + PW + UC <= nc);
+    C y[UC][V];
+    A agg[V];
+    if (full)
+      scanp_eval<true, T, S, NS, V, UC, NW>(p, k, err, x, y, agg, aggs[b], more, more_full, rp, i, c0, nr, nc);
+    else
+      scanp_eval<false, T, S, NS, V, UC, NW>(p, k, err, x, y, agg, aggs[b], more, more_full, rp, i, c0, nr, nc);
+    __syncthreads();
+    if (full)
+      scanp_write<true, S, V, UC, NW>(p, y, agg, aggs[b], carry_s[b], carry_s[b ^ 1], op, i, c0, nr, nc);
+    else
+      scanp_write<false, S, V, UC, NW>(p, y, agg, aggs[b], carry_s[b], carry_s[b ^ 1], op, i, c0, nr, nc);
   }
   if (err) atomicOr(p.err_flag, err);
 }

@@ -76,6 +76,10 @@ K(chk_scan_col_t_f64, 256, (scan_col_kernel<T3, double, 3, 1, 2, 1>))
 K(chk_scan_col_i32, 256, (scan_col_kernel<T2, int, 2, 0, 4, 2>))
 K(chk_scan_row_bf16, 256, (scan_row_kernel<T3, bf16, 3, 1, 8, 2, 2>))
 K(chk_scan_row_t_f32, 256, (scan_row_kernel<T3, float, 3, 1, 4, 4, 1>))
+KB(chk_scanp_f32, 256, 2, (scanp_kernel<T3, float, 3, 1, 1, 16, 8>))
+K(chk_scanp_bf16, 256, (scanp_kernel<T3, bf16, 3, 1, 2, 8, 8>))
+K(chk_scanp_f64, 256, (scanp_kernel<T3, double, 3, 1, 2, 8, 8>))
+KB(chk_scanp_i32, 256, 2, (scanp_kernel<T2, int, 2, 0, 1, 16, 8>))
 // GEMM with a fused epilogue: 2 * P + C (P the product, slot 0), every operand layout
 #include "coot_gemm.cuh"
 typedef eGlue<eOp<Leaf<0>, eop_scalar_times<0>>, Leaf<1>, eglue_plus> TG;

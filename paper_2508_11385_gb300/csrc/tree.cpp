@@ -680,6 +680,20 @@ Program make_program(const Analysis& an, Family fam, bool var_two_pass, bool bou
           add(buf, v, u, 256);
         }
       }
+      // one pass over bands of 32 v rows, panels of nw warps x uc columns
+      struct Pv { int v, uc, nw, minb; };
+      // (V = 1: two resident blocks per SM, as the bands of a tall matrix
+      // outnumber the SMs by less than two)
+      std::vector<Pv> pvu = {{1, 16, 8, 2}};
+      if (V >= 2) pvu.push_back({2, 8, 8, 0});
+      for (const Pv& q : pvu) {
+        snprintf(buf, sizeof buf, "coot_scanp_v%du%dw%d", q.v, q.uc, q.nw);
+        wrap(buf, 32 * q.nw,
+             std::string("scanp_kernel<T_t, S_t, ") + std::to_string(NS) + ", " + std::to_string(NK) + ", " +
+                 std::to_string(q.v) + ", " + std::to_string(q.uc) + ", " + std::to_string(q.nw) + ">",
+             "Params", q.minb);
+        add(buf, q.v, q.uc, 32 * q.nw);
+      }
     }
   } else if (fam == F_GEMM && an.esz != 2) {
     // FP32 / FP64 operands: the CUDA-core kernel, 256 threads, 2 blocks per SM

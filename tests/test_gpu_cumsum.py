@@ -112,3 +112,127 @@ def test_fp32_cumsum_is_float_float_accurate():
     # float-float: within one ulp of the exactly rounded prefix (a plain
     # FP32 running sum of 2^18 terms drifts by many ulps)
     assert np.all(np.abs(y - exact_f32) <= ulp)
+
+
+# ---------------------------------------------------------------------------
+# the one-pass row scan (coot_scanp_*): bands of 32 V rows, panels of 8 warps
+# x UC columns; every variant forced in turn
+# ---------------------------------------------------------------------------
+SCANP = [(1, 16, 8), (2, 8, 8)]
+TDT = {"f32": torch.float32, "f64": torch.float64, "bf16": torch.bfloat16, "f16": torch.float16,
+       "i32": torch.int32}
+
+
+def _scanp_names(dtype):
+    vmax = 16 // TDT[dtype].itemsize
+    return ["coot_scanp_v%du%dw%d" % (v, uc, nw) for v, uc, nw in SCANP if v <= vmax]
+
+
+def _ld(m):
+    return m + 8 + (-m) % 8  # columns 16-byte aligned for every dtype
+
+
+def _aligned(m, n, dtype, seed, kind="normal"):
+    return parity.strided(m, n, dtype, ld_extra=_ld(m) - m, seed=seed, kind=kind)
+
+
+def _aligned_out(m, n, dtype):
+    return torch.zeros((n, _ld(m)), dtype=TDT[dtype], device="cuda").t()[:m, :]
+
+
+def _scan_into(prog, tensors, out):
+    import coot_rpn
+
+    e, red = coot_rpn.build(prog, tensors)
+    coot.evaluate(e, reduction=red, materialise=out)
+    torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64", "bf16", "f16", "i32"])
+@pytest.mark.parametrize("shape", [(1, 1), (33, 1), (5, 200), (257, 64), (1001, 300), (4100, 129)])
+def test_one_pass_row_scan_every_variant(dtype, shape, monkeypatch):
+    # ragged bands (rows not a multiple of 32 V), ragged panels (columns not
+    # a multiple of 8 UC), partial vectors at the bottom of the last band
+    m, n = shape
+    A, B, C = (_aligned(m, n, dtype, seed=20 + s) for s in range(3))
+    prog = "A B % C + cumsum:1"
+    want = oracle.evaluate(prog, parity.host([A, B, C]), dtype)
+    for kname in _scanp_names(dtype):
+        monkeypatch.setenv("COOT_FORCE_KERNEL", kname)
+        out = _aligned_out(m, n, dtype)
+        _scan_into(prog, [A, B, C], out)
+        info = coot.last_launch()
+        assert info["kernel"] == kname and info["n_launches"] == 1, info
+        parity.compare_matrix(out, want, dtype, "%s %s %dx%d" % (kname, dtype, m, n))
+
+
+@pytest.mark.parametrize("dtype", ["f32", "i32"])
+def test_one_pass_row_scan_of_views_transposed_trees_and_in_place(dtype, monkeypatch):
+    for kname in _scanp_names(dtype):
+        monkeypatch.setenv("COOT_FORCE_KERNEL", kname)
+        # unaligned strided views (scalar variant only)
+        A = parity.strided(301, 150, dtype, ld_extra=5, offset=1, seed=30)
+        B = parity.strided(301, 150, dtype, ld_extra=2, offset=1, seed=31)
+        if kname == "coot_scanp_v1u16w8":
+            parity.check("A B % cumsum:1", [A, B], dtype)
+            assert coot.last_launch()["kernel"] == kname
+        # a transposed tree: materialised by the tile kernel, then scanned in place
+        P = parity.rand(130, 290, dtype, seed=32)
+        Q = parity.rand(290, 130, dtype, seed=33)
+        parity.check("A trans B + cumsum:1", [P, Q], dtype)
+        # in place: the scan's output is its own input
+        X = _aligned(700, 90, dtype, seed=34)
+        hs = parity.host([X])
+        want = oracle.evaluate("A cumsum:1", hs, dtype)
+        M = coot.Mat(X)
+        coot.evaluate(M, reduction=coot.cumsum(M, 1), materialise=X)
+        torch.cuda.synchronize()
+        assert coot.last_launch()["kernel"] == kname
+        parity.compare_matrix(X, want, dtype, "in-place " + kname)
+
+
+def test_one_pass_row_scan_is_the_default_for_tall_matrices():
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    m = 32 * sms + 7
+    A, B = (parity.rand(m, 40, "f32", seed=s) for s in (40, 41))
+    parity.check("A B - cumsum:1", [A, B], "f32")
+    info = coot.last_launch()
+    assert info["kernel"].startswith("coot_scanp_") and info["n_launches"] == 1, info
+    # fewer rows than one band per SM: the segmented scan
+    A, B = (parity.rand(300, 4000, "f32", seed=s) for s in (42, 43))
+    parity.check("A B - cumsum:1", [A, B], "f32")
+    assert not coot.last_launch()["kernel"].startswith("coot_scanp_")
+
+
+@pytest.mark.parametrize("kname", ["coot_scan_v4u2", "coot_scan_v4u4", "coot_scanp_v1u16w8", "coot_scanp_v2u8w8"])
+def test_row_scans_do_not_evaluate_rows_past_the_end(kname, monkeypatch):
+    # INT32 division: the padding rows of the last partial vector hold zeros,
+    # and evaluating them would raise the division-by-zero flag
+    m, n = 1001, 70
+    A = _aligned(m, n, "i32", seed=50)
+    B = _aligned(m, n, "i32", seed=51)
+    B.copy_(B.abs() + 1)
+    monkeypatch.setenv("COOT_FORCE_KERNEL", kname)
+    coot.check_device_flag()  # clear
+    out = _aligned_out(m, n, "i32")
+    _scan_into("A B / cumsum:1", [A, B], out)
+    assert coot.last_launch()["kernel"] == kname
+    assert coot.check_device_flag() == 0
+    parity.compare_matrix(out, oracle.evaluate("A B / cumsum:1", parity.host([A, B]), "i32"), "i32", kname)
+
+
+def test_one_pass_row_scan_is_float_float_accurate(monkeypatch):
+    # long rows through the one-pass scan: every prefix within one ulp of the
+    # exactly rounded prefix, as for the column scan
+    monkeypatch.setenv("COOT_FORCE_KERNEL", "coot_scanp_v1u16w8")
+    g = torch.Generator(device="cuda").manual_seed(14)
+    a = (torch.rand((1 << 16, 40), generator=g, device="cuda") * 2 - 1).float().t()  # 40 x 65536 column-major
+    hs = parity.host([a])
+    r = oracle.evaluate("A cumsum:1", hs, "f32")
+    y = coot.cumsum(coot.Mat(a), 1).eval()
+    torch.cuda.synchronize()
+    assert coot.last_launch()["kernel"] == "coot_scanp_v1u16w8"
+    y = y.cpu().double().numpy()
+    exact_f32 = r.value.astype(np.float32).astype(np.float64)
+    ulp = np.spacing(np.abs(exact_f32).astype(np.float32)).astype(np.float64)
+    assert np.all(np.abs(y - exact_f32) <= ulp)
