@@ -340,6 +340,104 @@ struct UnitWalk {
 // ---------------------------------------------------------------------------
 // str: map (+ full reduction) over n_rows x n_cols, no transposed reads
 // ---------------------------------------------------------------------------
+// One unit of the walk: U chunks from chunk r of column j.  FAST: the unit
+// stays inside column j and every row of its chunks is inside the tree (the
+// same for the whole block), so nothing is checked and no chunk wraps.
+template <bool FAST, class T, class S, int NS, int NK, int RED, int V, int U, bool OUT, class A, class K, class Q>
+__device__ __forceinline__ void str_unit(const Params& p, const K& k, const Q& csq, u32& err, A (&accs)[V],
+                                         long long j, long long r) {
+  typedef typename ctype<S>::type C;
+  const long long nr = p.n_rows, nc = p.n_cols, cpc = p.units_per_col;
+  const long long step = (long long)blockDim.x * V;
+  const long long tv = (long long)threadIdx.x * V;
+  // the current chunk's column of every slot and of the output: formed once
+  // per unit, then moved one column on when the chunks wrap
+  const S* col[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) col[s] = col_of<S>(p, s, j);
+  S* oc = nullptr;
+  if constexpr (OUT) oc = out_col<S>(p, j);
+  // 16-bit storage keeps its loads as raw words until they are used
+  constexpr bool RAW = sizeof(S) == 2 && V >= 2;
+  Vals<C, NS, V> x[RAW ? 1 : U];
+  u32 raw[RAW ? U : 1][RAW ? NS : 1][RAW ? V / 2 : 1];
+  bool valid[U], full[U];
+  long long ig[U], jg[U];
+  S* og[U];
+#pragma unroll
+  for (int g = 0; g < U; ++g) {
+    const long long i = r * step + tv;
+    valid[g] = FAST || (j < nc);
+    full[g] = FAST || (valid[g] && (i + V <= nr));
+    ig[g] = i;
+    jg[g] = j;
+    og[g] = oc;
+    if constexpr (RAW) {
+#pragma unroll
+      for (int s = 0; s < NS; ++s) load_rows_raw<S, V>(p, s, col[s], i, (FAST || valid[g]) ? nr : 0, raw[g][s]);
+    } else if (full[g]) {
+#pragma unroll
+      for (int s = 0; s < NS; ++s) load_rows_at<S, V>(p, s, col[s], i, x[g].v[s]);
+    } else {
+#pragma unroll
+      for (int s = 0; s < NS; ++s)
+#pragma unroll
+        for (int l = 0; l < V; ++l)
+          x[g].v[s][l] = (valid[g] && i + l < nr) ? sload1<S>(p, s, row_in<S>(p, s, col[s], i + l)) : C(0);
+    }
+    if constexpr (FAST) {
+      ++r;
+    } else if (g + 1 < U && ++r == cpc) {  // the next chunk starts the next column
+      r = 0;
+      ++j;
+#pragma unroll
+      for (int s = 0; s < NS; ++s) col[s] += p.ld[s];
+      if constexpr (OUT) oc += p.out_ld;
+    }
+  }
+#pragma unroll
+  for (int g = 0; g < U; ++g) {
+    const long long i = ig[g];
+    const Vals<C, NS, V>* xg = &x[RAW ? 0 : g];
+    if constexpr (RAW) {
+      if (valid[g]) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) IO<S>::template convert<V>(raw[g][s], x[0].v[s]);
+      }
+    }
+    if (full[g]) {
+      C y[V];
+      if constexpr ((sizeof(S) == 2 && red_additive(RED)) ||
+                    (is_f32_c<S>::value && (RED == RED_SSQ || RED == RED_CSQ))) {
+        // pairwise sum of the vector's terms, then one float-float
+        // addition (spread over the accumulators by group)
+        C c[V];
+#pragma unroll
+        for (int l = 0; l < V; ++l) y[l] = eval_term<T, RED>(*xg, k, err, l, csq, c[l]);
+#pragma unroll
+        for (int w = V / 2; w >= 1; w /= 2)
+#pragma unroll
+          for (int l = 0; l < w; ++l) c[l] = op_add(c[l], c[l + w]);
+        accs[g % V].add(c[0]);
+      } else {
+#pragma unroll
+        for (int l = 0; l < V; ++l) y[l] = eval_elem<T, RED>(*xg, k, err, l, accs[l], csq, i + l + jg[g] * nr);
+      }
+      if constexpr (OUT) store_rows_at<S, V>(p, og[g], i, y);
+    } else if (valid[g]) {
+#pragma unroll
+      for (int l = 0; l < V; ++l)
+        if (i + l < nr) {
+          C y = eval_elem<T, RED>(*xg, k, err, l, accs[l], csq, i + l + jg[g] * nr);
+          if constexpr (OUT) sstore1<S>(p, out_row_in<S>(p, og[g], i + l), y);
+        }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// str: map (+ full reduction) over n_rows x n_cols, no transposed reads
+// ---------------------------------------------------------------------------
 template <class T, class S, int NS, int NK, int RED, int V, int U, bool OUT>
 __device__ __forceinline__ void str_kernel(const Params& p) {
   typedef typename ctype<S>::type C;
@@ -361,90 +459,11 @@ __device__ __forceinline__ void str_kernel(const Params& p) {
   // loads in flight whatever the column length
   const long long nr = p.n_rows, nc = p.n_cols, cpc = p.units_per_col;
   const long long step = (long long)blockDim.x * V;
-  const long long tv = (long long)threadIdx.x * V;
   for (UnitWalk walk(cpc, U); walk.j < nc; walk.next()) {
-    // the current chunk's column of every slot and of the output: formed once
-    // per unit, then moved one column on when the chunks wrap
-    long long j = walk.j, r = walk.r;
-    const S* col[NS];
-#pragma unroll
-    for (int s = 0; s < NS; ++s) col[s] = col_of<S>(p, s, j);
-    S* oc = nullptr;
-    if constexpr (OUT) oc = out_col<S>(p, j);
-    // 16-bit storage keeps its loads as raw words until they are used
-    constexpr bool RAW = sizeof(S) == 2 && V >= 2;
-    Vals<C, NS, V> x[RAW ? 1 : U];
-    u32 raw[RAW ? U : 1][RAW ? NS : 1][RAW ? V / 2 : 1];
-    bool valid[U], full[U];
-    long long ig[U], jg[U];
-    S* og[U];
-#pragma unroll
-    for (int g = 0; g < U; ++g) {
-      const long long i = r * step + tv;
-      valid[g] = (j < nc);
-      full[g] = valid[g] && (i + V <= nr);
-      ig[g] = i;
-      jg[g] = j;
-      og[g] = oc;
-      if constexpr (RAW) {
-#pragma unroll
-        for (int s = 0; s < NS; ++s) load_rows_raw<S, V>(p, s, col[s], i, valid[g] ? nr : 0, raw[g][s]);
-      } else if (full[g]) {
-#pragma unroll
-        for (int s = 0; s < NS; ++s) load_rows_at<S, V>(p, s, col[s], i, x[g].v[s]);
-      } else {
-#pragma unroll
-        for (int s = 0; s < NS; ++s)
-#pragma unroll
-          for (int l = 0; l < V; ++l)
-            x[g].v[s][l] = (valid[g] && i + l < nr) ? sload1<S>(p, s, row_in<S>(p, s, col[s], i + l)) : C(0);
-      }
-      if (g + 1 < U && ++r == cpc) {  // the next chunk starts the next column
-        r = 0;
-        ++j;
-#pragma unroll
-        for (int s = 0; s < NS; ++s) col[s] += p.ld[s];
-        if constexpr (OUT) oc += p.out_ld;
-      }
-    }
-#pragma unroll
-    for (int g = 0; g < U; ++g) {
-      const long long i = ig[g];
-      const Vals<C, NS, V>* xg = &x[RAW ? 0 : g];
-      if constexpr (RAW) {
-        if (valid[g]) {
-#pragma unroll
-          for (int s = 0; s < NS; ++s) IO<S>::template convert<V>(raw[g][s], x[0].v[s]);
-        }
-      }
-      if (full[g]) {
-        C y[V];
-        if constexpr ((sizeof(S) == 2 && red_additive(RED)) ||
-                      (is_f32_c<S>::value && (RED == RED_SSQ || RED == RED_CSQ))) {
-          // pairwise sum of the vector's terms, then one float-float
-          // addition (spread over the accumulators by group)
-          C c[V];
-#pragma unroll
-          for (int l = 0; l < V; ++l) y[l] = eval_term<T, RED>(*xg, k, err, l, csq, c[l]);
-#pragma unroll
-          for (int w = V / 2; w >= 1; w /= 2)
-#pragma unroll
-            for (int l = 0; l < w; ++l) c[l] = op_add(c[l], c[l + w]);
-          accs[g % V].add(c[0]);
-        } else {
-#pragma unroll
-          for (int l = 0; l < V; ++l) y[l] = eval_elem<T, RED>(*xg, k, err, l, accs[l], csq, i + l + jg[g] * nr);
-        }
-        if constexpr (OUT) store_rows_at<S, V>(p, og[g], i, y);
-      } else if (valid[g]) {
-#pragma unroll
-        for (int l = 0; l < V; ++l)
-          if (i + l < nr) {
-            C y = eval_elem<T, RED>(*xg, k, err, l, accs[l], csq, i + l + jg[g] * nr);
-            if constexpr (OUT) sstore1<S>(p, out_row_in<S>(p, og[g], i + l), y);
-          }
-      }
-    }
+    if (walk.r + U <= cpc && (walk.r + U) * step <= nr)
+      str_unit<true, T, S, NS, NK, RED, V, U, OUT>(p, k, csq, err, accs, walk.j, walk.r);
+    else
+      str_unit<false, T, S, NS, NK, RED, V, U, OUT>(p, k, csq, err, accs, walk.j, walk.r);
   }
   if (err) atomicOr(p.err_flag, err);
   if constexpr (RED != RED_NONE) {

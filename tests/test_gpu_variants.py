@@ -26,14 +26,14 @@ def _variants(dtype, two_pass):
             "coot_str%s_v1u4" % p]
 
 
-def _leaves(dtype, seed):
+def _leaves(dtype, seed, R=R, C=C, square=True):
     # column stride R + 16: 16-byte aligned columns for every dtype
     big = [parity.rand(R + 16, C + 5, dtype, seed=seed + i, kind="positive") for i in range(2)]
     A = big[0][8:8 + R, 2:2 + C]            # a view with 16-byte aligned columns
     B = big[1][1:1 + R, 4:4 + C]            # unaligned start: scalar variants only
     col = parity.rand(R, 1, dtype, seed=seed + 7, kind="positive")
     row = parity.rand(1, C, dtype, seed=seed + 8, kind="positive")
-    sq = parity.rand(R + 1, R + 1, dtype, seed=seed + 9, kind="positive")
+    sq = parity.rand(R + 1, (R if square else C) + 1, dtype, seed=seed + 9, kind="positive")
     return [A, B, col, row, sq]
 
 
@@ -79,3 +79,29 @@ def test_forced_variant_is_the_one_launched(monkeypatch):
         parity.check("A C each_col:37 % accu", leaves, "f32")
         torch.cuda.synchronize()
         assert coot.last_launch()["kernel"] == kname
+
+
+# columns long enough that most units of the walk lie inside one column with
+# every row inside the tree (the walk's check-free form), and a ragged last
+# chunk per column (the checked form)
+RL, CL = 20011, 6
+TREES_LONG = [
+    ("A B % {red}", False),
+    ("A C each_col:6 % D each_row:20011 + {red}", False),
+    ("A C each_col:6 - {red}", True),
+    ("E submat:1:1:20011:6 A + {red}", False),
+]
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "i32"])
+@pytest.mark.parametrize("red", ["accu", "min", "index_max", "var"])
+def test_every_variant_on_long_columns(dtype, red, monkeypatch):
+    if dtype == "i32" and red == "var":
+        pytest.skip("not defined for INT32 trees")
+    leaves = _leaves(dtype, 31, RL, CL, square=False)
+    for tree, materialise in TREES_LONG:
+        prog = tree.format(red=red)
+        for kname in _variants(dtype, red == "var"):
+            monkeypatch.setenv("COOT_FORCE_KERNEL", kname)
+            parity.check(prog, leaves, dtype, materialise=materialise)
+    monkeypatch.delenv("COOT_FORCE_KERNEL")
