@@ -151,6 +151,27 @@ template <class S, int V, class C>
 __device__ __forceinline__ void load_rows(const Params& p, int s, long long i, long long j, C (&v)[V]) {
   load_rows_at<S, V>(p, s, col_of<S>(p, s, j), i, v);
 }
+// V rows of slot s from q, the address of this thread's first row in some
+// column (a row broadcast reads one element for all V rows)
+template <class S, int V, class C>
+__device__ __forceinline__ void rows_from(const Params& p, int s, const S* q, C (&v)[V]) {
+  if (gen_slot(s)) {
+    if (p.rs[s] == 0) {
+      const C x = sload1<S>(p, s, q);
+#pragma unroll
+      for (int l = 0; l < V; ++l) v[l] = x;
+    } else {
+#pragma unroll
+      for (int l = 0; l < V; ++l) v[l] = sload1<S>(p, s, q + l * p.rs[s]);
+    }
+  } else if (slot_ok<S>(p, s, q, V)) {
+    IO<S>::template load<V>(q, v);
+  } else {
+#pragma unroll
+    for (int l = 0; l < V; ++l) v[l] = C(0);
+  }
+}
+
 template <class S> __device__ __forceinline__ S* at_out_g(const Params& p, long long i, long long j) {
   if (COOT_GM & GM_OUT) return (S*)p.out + (i * p.out_rs + j * p.out_ld);
   return at_out<S>(p.out, i, j, p.out_ld);
@@ -170,6 +191,22 @@ __device__ __forceinline__ void store_rows_at(const Params& p, S* col, long long
     for (int l = 0; l < V; ++l) sstore1<S>(p, col + (i + l) * p.out_rs, v[l]);
   } else if (out_ok<S>(p, col + i, V)) {
     IO<S>::template store<V>(col + i, v);
+  }
+}
+// V rows of the output at o, this thread's first row in some output column
+// (FULL: all V rows inside the tree; else rows from `lim` on are skipped)
+template <bool FULL, class S, int V, class C>
+__device__ __forceinline__ void rows_to(const Params& p, S* o, long long i, long long lim, const C (&v)[V]) {
+  if (COOT_GM & GM_OUT) {
+#pragma unroll
+    for (int l = 0; l < V; ++l)
+      if (FULL || i + l < lim) sstore1<S>(p, o + l * p.out_rs, v[l]);
+  } else if (FULL) {
+    if (out_ok<S>(p, o, V)) IO<S>::template store<V>(o, v);
+  } else {
+#pragma unroll
+    for (int l = 0; l < V; ++l)
+      if (i + l < lim) sstore1<S>(p, o + l, v[l]);
   }
 }
 // V consecutive rows of the output from (i, j)
@@ -502,8 +539,30 @@ __device__ __forceinline__ void col_kernel(const Params& p) {
     A acc;
     acc.init();
     if constexpr (RED == RED_CSQ) csq.set_mean(p.mu[j < nc ? j : 0]);
+    // column j of every slot (row 0), formed once per column
+    const S* cj[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) cj[s] = col_of<S>(p, s, j < nc ? j : 0);
     for (long long i0 = (wm * 32 + lane) * V; j < nc && i0 < nr; i0 += G * step * U) {
       Vals<C, NS, V> x[U];
+      if (i0 + (U - 1) * G * step + V <= nr) {
+        // every group's V rows inside the tree: nothing checked
+#pragma unroll
+        for (int g = 0; g < U; ++g) {
+          const long long i = i0 + g * G * step;
+#pragma unroll
+          for (int s = 0; s < NS; ++s) rows_from<S, V>(p, s, row_in<S>(p, s, cj[s], i), x[g].v[s]);
+        }
+#pragma unroll
+        for (int g = 0; g < U; ++g) {
+          const long long i = i0 + g * G * step;
+          C y[V];
+#pragma unroll
+          for (int l = 0; l < V; ++l) y[l] = eval_elem<T, RED>(x[g], k, err, l, acc, csq, i + l);
+          if constexpr (OUT) store_rows<S, V>(p, i, j, y);
+        }
+        continue;
+      }
       bool full[U];
 #pragma unroll
       for (int g = 0; g < U; ++g) {
@@ -586,7 +645,34 @@ __device__ __forceinline__ void row_kernel(const Params& p) {
     if constexpr (RED == RED_CSQ) csq[l].set_mean(i + l < nr ? p.mu[o0 + i + l] : 0.0);
   }
   if (i < nr) {
-    for (long long jb = j0; jb < j1; jb += U) {
+    long long jb = j0;
+    if (fullv) {
+      // groups of U columns inside the segment with all V rows inside the
+      // tree: row pointers stepped by the column strides, nothing checked
+      const S* rp[NS];
+#pragma unroll
+      for (int s = 0; s < NS; ++s) rp[s] = (const S*)p.src[s] + (gen_slot(s) ? i * p.rs[s] : i);
+      S* op = nullptr;
+      if constexpr (OUT) op = (S*)p.out + ((COOT_GM & GM_OUT) ? i * p.out_rs : i);
+      for (; jb + U <= j1; jb += U) {
+        Vals<C, NS, V> x[U];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+          const long long ld = p.ld[s];
+          const S* q = rp[s] + jb * ld;
+#pragma unroll
+          for (int g = 0; g < U; ++g, q += ld) rows_from<S, V>(p, s, q, x[g].v[s]);
+        }
+#pragma unroll
+        for (int g = 0; g < U; ++g) {
+          C y[V];
+#pragma unroll
+          for (int l = 0; l < V; ++l) y[l] = eval_elem<T, RED>(x[g], k, err, l, acc[l], csq[l], jb + g - pbase);
+          if constexpr (OUT) rows_to<true, S, V>(p, op + (jb + g) * p.out_ld, i, nr, y);
+        }
+      }
+    }
+    for (; jb < j1; jb += U) {
       Vals<C, NS, V> x[U];
 #pragma unroll
       for (int g = 0; g < U; ++g) {
@@ -1354,27 +1440,6 @@ __device__ __forceinline__ void scan_row_kernel(const Params& p) {
 // on another; the order of additions is fixed by (V, UC, NW), so results are
 // deterministic.  The next panel's loads are issued before the barrier.
 // ---------------------------------------------------------------------------
-// V rows of slot s from q, the address of this thread's first row in some
-// column (a row broadcast reads one element for all V rows)
-template <class S, int V, class C>
-__device__ __forceinline__ void scanp_rows(const Params& p, int s, const S* q, C (&v)[V]) {
-  if (gen_slot(s)) {
-    if (p.rs[s] == 0) {
-      const C x = sload1<S>(p, s, q);
-#pragma unroll
-      for (int l = 0; l < V; ++l) v[l] = x;
-    } else {
-#pragma unroll
-      for (int l = 0; l < V; ++l) v[l] = sload1<S>(p, s, q + l * p.rs[s]);
-    }
-  } else if (slot_ok<S>(p, s, q, V)) {
-    IO<S>::template load<V>(q, v);
-  } else {
-#pragma unroll
-    for (int l = 0; l < V; ++l) v[l] = C(0);
-  }
-}
-
 // the UC columns from c0 of every slot at this thread's rows.  FULL: all V
 // rows and all UC columns are inside the tree (no checks); else rows at or
 // past nr read 0 and columns at or past nc are not read.
@@ -1388,7 +1453,7 @@ __device__ __forceinline__ void scanp_load(const Params& p, const S* const (&rp)
 #pragma unroll
     for (int u = 0; u < UC; ++u, q += ld) {
       if constexpr (FULL) {
-        scanp_rows<S, V>(p, s, q, x[u].v[s]);
+        rows_from<S, V>(p, s, q, x[u].v[s]);
       } else if (c0 + u < nc) {
 #pragma unroll
         for (int l = 0; l < V; ++l)
