@@ -42,13 +42,14 @@ def _dev_headers():
 
 
 def _sources():
-    cu = [p for p in glob.glob(os.path.join(CSRC, "*.cu")) if os.path.basename(p) != "dev_check.cu"]
+    cu = [p for p in glob.glob(os.path.join(CSRC, "*.cu")) if not os.path.basename(p).startswith("dev_check")]
     return sorted(glob.glob(os.path.join(CSRC, "*.cpp")) + cu)
 
 
 def _inputs():
     return (_dev_headers() + _sources() + glob.glob(os.path.join(CSRC, "*.h"))
-            + [os.path.join(ROOT, "include", "coot.h"), os.path.join(CSRC, "dev_check.cu"), __file__])
+            + [os.path.join(ROOT, "include", "coot.h"), os.path.join(CSRC, "dev_check.cu"),
+               os.path.join(CSRC, "dev_check_gm.cu"), __file__])
 
 
 def embed_headers() -> str:
@@ -103,6 +104,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
     procs.append((chk + " (bounds)", subprocess.Popen(
         [nvcc] + ARCH + ["-std=c++17", "-O3", "-fmad=false", "-DCOOT_DEBUG_BOUNDS=1", "-I", DEV, "-c", chk, "-o",
                          os.path.join(BUILD, "dev_check_bounds.o")],
+        stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+    # kernels that write a general output (their own translation unit: the
+    # output kind is a define of the whole program)
+    chk_gm = os.path.join(CSRC, "dev_check_gm.cu")
+    procs.append((chk_gm, subprocess.Popen(
+        [nvcc] + ARCH + ["-std=c++17", "-O3", "-fmad=false", "-I", DEV, "-c", chk_gm, "-o",
+                         os.path.join(BUILD, "dev_check_gm.o")],
         stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
     failed = []
     for src, p in procs:

@@ -446,12 +446,67 @@ std::string tune_key(const cg::Program& pg, const cg::Choice& ch) {
 
 }  // namespace
 
+// The transposed problem: element (i, j) of its result is element (j, i) of
+// an's.  Each slot's row and column strides swap; a slot whose columns become
+// one element apart is read as a transposed slot (rows rs apart, a thread's
+// consecutive columns consecutive in memory), one whose rows become adjacent
+// as a direct slot, the others as general slots.  The output view swaps the
+// same way (into *out_t).  A cumsum along dim 0 of a tree with transposed
+// reads is the cumsum along dim 1 of this problem.
+static cg::Analysis transposed_problem(const cg::Analysis& an, const coot_mat& out, coot_mat* out_t) {
+  cg::Analysis f = an;
+  std::swap(f.nr, f.nc);
+  f.trmask = 0;
+  f.gmask = 0;
+  f.any_trans = false;
+  for (size_t s = 0; s < f.slots.size(); ++s) {
+    cg::Slot& sl = f.slots[s];
+    std::swap(sl.rs, sl.cs);
+    std::swap(sl.r0, sl.c0);
+    std::swap(sl.vr, sl.vc);
+    sl.full = false;
+    sl.trans = (sl.cs == 1 && sl.rs != 1);
+    sl.gen = !sl.trans && sl.rs != 1;
+    if (sl.trans) {
+      f.any_trans = true;
+      f.trmask |= 1 << s;
+    }
+    if (sl.gen) f.gmask |= 1 << s;
+  }
+  // out_t: n_cols x n_rows, rows mat_ld(out) apart, columns out_rs apart
+  *out_t = out;
+  out_t->n_rows = out.n_cols;
+  out_t->n_cols = out.n_rows;
+  out_t->rs = mat_ld(out);
+  out_t->ld = an.out_rs;
+  f.out_rs = out_t->rs;
+  if (f.out_rs != 1 && f.nr > 1) f.gmask |= 1 << COOT_MAX_SLOTS;
+  if (f.red.kind == COOT_R_CUMSUM) f.red.dim = 1 - f.red.dim;
+  return f;
+}
+
 // ---------------------------------------------------------------------------
 // run one analysed fused evaluation (warm: compile + tune without launching)
 // ---------------------------------------------------------------------------
 static coot_status run_fused(coot_ctx* ctx, const cg::Analysis& an, const coot_mat* leaves, const coot_mat* out,
                              void* red_out, cudaStream_t stream, bool warm_only, cg::CallPlan* plan = nullptr) {
-  if (an.scan() && an.any_trans) {
+  if (an.scan() && an.any_trans && !an.scan_direct && an.n_seg() == 1 && out && an.nr > 1 && an.nc > 1) {
+    // one pass of the row scan, which reads transposed slots along each
+    // thread's runs of columns: along dim 1 directly, along dim 0 over the
+    // transposed problem, when its rows fill the SMs
+    if (an.red.dim == 1 && scanp_fits(an, ctx->sms)) {
+      cg::Analysis d = an;
+      d.scan_direct = true;
+      return run_fused(ctx, d, leaves, out, red_out, stream, warm_only);
+    }
+    if (an.red.dim == 0 && an.nc >= 32LL * ctx->sms) {
+      coot_mat out_t;
+      cg::Analysis d = transposed_problem(an, *out, &out_t);
+      d.scan_direct = true;
+      return run_fused(ctx, d, leaves, &out_t, red_out, stream, warm_only);
+    }
+  }
+  if (an.scan() && an.any_trans && !an.scan_direct) {
     // a tree with transposed reads is first materialised into out by the
     // tile kernel, then scanned in place (out read and written by the same
     // thread)
@@ -547,6 +602,18 @@ static coot_status run_fused(coot_ctx* ctx, const cg::Analysis& an, const coot_m
   p.den = (an.red.norm_type == 1) ? (double)per : (double)(per - 1);
   p.flags = (an.red.kind == COOT_R_STDDEV) ? cg::PF_SQRT : 0u;
   if (an.n_seg() > 1) p.flags |= cg::PF_SEGMENTED;
+  if (ch.fam == cg::F_SCAN && an.red.dim == 1) {
+    // the row scan's runs of 16 consecutive columns (transposed slots, a
+    // transposed output): vectors where every run starts 16-byte aligned
+    for (size_t i = 0; i < an.slots.size(); ++i) {
+      const cg::Slot& sl = an.slots[i];
+      if (sl.trans && (uintptr_t)p.src[i] % 16 == 0 && (sl.rs * an.esz) % 16 == 0)
+        p.flags |= cg::PF_TRUN0 << i;
+    }
+    if (out && ((an.gmask >> COOT_MAX_SLOTS) & 1) && p.out_ld == 1 && (uintptr_t)out->data % 16 == 0 &&
+        (an.out_rs * an.esz) % 16 == 0)
+      p.flags |= cg::PF_OUT_RUN;
+  }
   p.red_out = red_out;
 
   // launch configuration: the call plan's, else tuned, else the default
@@ -701,7 +768,13 @@ coot_status tune(coot_ctx* ctx, const cg::Analysis& an, const cg::Choice& ch, co
       for (int split : splits) {
         Launch L = base;
         L.p.out = scratch_out;
-        if (scratch_out) L.p.out_ld = sld;
+        if (scratch_out) {
+          // the scratch output is plain column-major (rows adjacent, columns
+          // sld apart), whatever the strides of the call's output
+          L.p.out_ld = sld;
+          L.p.out_rs = 1;
+          L.p.flags &= ~(unsigned)cg::PF_OUT_RUN;
+        }
         L.p.red_out = scratch_red;
         shape_launch(ctx, an, ch, m, k, block, bps, &L, split);
         st = ws_ensure(ctx, L.tickets, L.partial_bytes, stream);

@@ -31,6 +31,8 @@ namespace cg {
 using coot::Params;
 using coot::PF_SQRT;
 using coot::PF_SEGMENTED;
+using coot::PF_OUT_RUN;
+using coot::PF_TRUN0;
 
 using coot::RED_NONE;
 using coot::RED_SUM;
@@ -101,6 +103,10 @@ struct Analysis {
   int accum = 0;            // FP32 accumulation: 0 float-float, 1 Kahan, 2 plain ($COOT_ACCUM)
   int batch_be = 8192;      // flat batched kernel: elements per work item
   int batch_minb = 5;       // flat batched kernel: resident blocks per SM the registers are capped for
+  // cumsum of a tree with transposed reads: scanned in one pass by the row
+  // scan (set by the launcher when that kernel fits the shape), else the tree
+  // is materialised first
+  bool scan_direct = false;
   // GEMM epilogue trees: the slot holding the product, and the operands' layouts
   int gemm_ps = -1;
   bool gemm_ka = false, gemm_kb = false;

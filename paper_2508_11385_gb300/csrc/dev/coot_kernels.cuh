@@ -1442,12 +1442,35 @@ __device__ __forceinline__ void scan_row_kernel(const Params& p) {
 // ---------------------------------------------------------------------------
 // the UC columns from c0 of every slot at this thread's rows.  FULL: all V
 // rows and all UC columns are inside the tree (no checks); else rows at or
-// past nr read 0 and columns at or past nc are not read.
-template <bool FULL, class S, int NS, int V, int UC, class X>
+// past nr read 0 and columns at or past nc are not read.  A transposed slot
+// (bit s of TRMASK; V = 1) has its columns one element apart: the thread's
+// UC values are consecutive in memory, read as 16-byte vectors when the host
+// found them aligned (flag PF_TRUN0 << s).
+template <bool FULL, int TRMASK, class S, int NS, int V, int UC, class X>
 __device__ __forceinline__ void scanp_load(const Params& p, const S* const (&rp)[NS], long long i, long long c0,
                                            long long nr, long long nc, X (&x)[UC]) {
+  typedef typename X::C C;
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
+    if ((TRMASK >> s) & 1) {
+      static_assert(TRMASK == 0 || V == 1, "transposed slots: one row per thread");
+      const S* q = rp[s] + c0;
+      constexpr int PER = 16 / (int)sizeof(S);
+      if (FULL && UC % PER == 0 && (p.flags & (PF_TRUN0 << s)) && slot_ok<S>(p, s, q, UC)) {
+#pragma unroll
+        for (int g = 0; g < UC / PER; ++g) {
+          C t[PER];
+          IO<S>::template load<PER>(q + g * PER, t);
+#pragma unroll
+          for (int e = 0; e < PER; ++e) x[g * PER + e].v[s][0] = t[e];
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < UC; ++u)
+          if (FULL || (c0 + u < nc && i < nr)) x[u].v[s][0] = sload1<S>(p, s, q + u);
+      }
+      continue;
+    }
     const long long ld = p.ld[s];
     const S* q = rp[s] + c0 * ld;
 #pragma unroll
@@ -1457,7 +1480,7 @@ __device__ __forceinline__ void scanp_load(const Params& p, const S* const (&rp)
       } else if (c0 + u < nc) {
 #pragma unroll
         for (int l = 0; l < V; ++l)
-          x[u].v[s][l] = (i + l < nr) ? sload1<S>(p, s, gen_slot(s) ? q + l * p.rs[s] : q + l) : typename X::C(0);
+          x[u].v[s][l] = (i + l < nr) ? sload1<S>(p, s, gen_slot(s) ? q + l * p.rs[s] : q + l) : C(0);
       }
     }
   }
@@ -1469,7 +1492,7 @@ __device__ __forceinline__ void scanp_load(const Params& p, const S* const (&rp)
 // between the lanes of a warp and neither half may hold a barrier.
 // First half: evaluate the tree on the loaded columns, form the rows' partial
 // sums, issue the next panel's loads, publish the partial sums.
-template <bool FULL, class T, class S, int NS, int V, int UC, int NW, class X, class K, class C>
+template <bool FULL, int TRMASK, class T, class S, int NS, int V, int UC, int NW, class X, class K, class C>
 __device__ __forceinline__ void scanp_eval(const Params& p, const K& k, u32& err, X (&x)[UC], C (&y)[UC][V],
                                            ScanAcc<C> (&agg)[V], ScanAcc<C> (&aggs)[NW][32 * V], bool more,
                                            bool more_full, const S* const (&rp)[NS], long long i, long long c0,
@@ -1491,9 +1514,9 @@ __device__ __forceinline__ void scanp_eval(const Params& p, const K& k, u32& err
     }
   if (more) {
     if (more_full)
-      scanp_load<true, S, NS, V, UC>(p, rp, i, c0 + PW, nr, nc, x);
+      scanp_load<true, TRMASK, S, NS, V, UC>(p, rp, i, c0 + PW, nr, nc, x);
     else if (i < nr)
-      scanp_load<false, S, NS, V, UC>(p, rp, i, c0 + PW, nr, nc, x);
+      scanp_load<false, TRMASK, S, NS, V, UC>(p, rp, i, c0 + PW, nr, nc, x);
   }
 #pragma unroll
   for (int l = 0; l < V; ++l) aggs[w][lane * V + l] = agg[l];
@@ -1526,6 +1549,23 @@ __device__ __forceinline__ void scanp_write(const Params& p, const C (&y)[UC][V]
   if (!FULL && i >= nr) return;
   const long long old = p.out_ld;
   S* o = op + c0 * old;
+  constexpr int PER = 16 / (int)sizeof(S);
+  if constexpr (V == 1 && UC % PER == 0 && (COOT_GM & GM_OUT) != 0) {
+    // a transposed output: the thread's UC results are consecutive
+    if (FULL && (p.flags & PF_OUT_RUN) && out_ok<S>(p, o, UC)) {
+#pragma unroll
+      for (int g = 0; g < UC / PER; ++g) {
+        C t[PER];
+#pragma unroll
+        for (int e = 0; e < PER; ++e) {
+          base[0].add(y[g * PER + e][0]);
+          t[e] = base[0].out();
+        }
+        IO<S>::template store<PER>(o + g * PER, t);
+      }
+      return;
+    }
+  }
 #pragma unroll
   for (int u = 0; u < UC; ++u, o += old) {
     if (!FULL && c0 + u >= nc) break;
@@ -1549,7 +1589,7 @@ __device__ __forceinline__ void scanp_write(const Params& p, const C (&y)[UC][V]
   }
 }
 
-template <class T, class S, int NS, int NK, int V, int UC, int NW>
+template <class T, class S, int NS, int NK, int V, int UC, int NW, int TRMASK = 0>
 __device__ __forceinline__ void scanp_kernel(const Params& p) {
   typedef typename ctype<S>::type C;
   typedef ScanAcc<C> A;
@@ -1574,16 +1614,17 @@ __device__ __forceinline__ void scanp_kernel(const Params& p) {
   const long long ii = (i < nr) ? i : 0;
   const S* rp[NS];
 #pragma unroll
-  for (int s = 0; s < NS; ++s) rp[s] = (const S*)p.src[s] + (gen_slot(s) ? ii * p.rs[s] : ii);
+  for (int s = 0; s < NS; ++s)
+    rp[s] = (const S*)p.src[s] + ((gen_slot(s) || ((TRMASK >> s) & 1)) ? ii * p.rs[s] : ii);
   S* op = (S*)p.out + ((COOT_GM & GM_OUT) ? ii * p.out_rs : ii);
   const long long npan = (nc + PW - 1) / PW;
   Vals<C, NS, V> x[UC];
   {
     const long long c0 = (long long)w * UC;
     if (fullv && c0 + UC <= nc)
-      scanp_load<true, S, NS, V, UC>(p, rp, i, c0, nr, nc, x);
+      scanp_load<true, TRMASK, S, NS, V, UC>(p, rp, i, c0, nr, nc, x);
     else if (i < nr)
-      scanp_load<false, S, NS, V, UC>(p, rp, i, c0, nr, nc, x);
+      scanp_load<false, TRMASK, S, NS, V, UC>(p, rp, i, c0, nr, nc, x);
   }
   // every thread runs every panel and reaches the one barrier below once per
   // panel, whatever form of the halves it takes
@@ -1596,9 +1637,11 @@ __device__ __forceinline__ void scanp_kernel(const Params& p) {
     C y[UC][V];
     A agg[V];
     if (full)
-      scanp_eval<true, T, S, NS, V, UC, NW>(p, k, err, x, y, agg, aggs[b], more, more_full, rp, i, c0, nr, nc);
+      scanp_eval<true, TRMASK, T, S, NS, V, UC, NW>(p, k, err, x, y, agg, aggs[b], more, more_full, rp, i, c0, nr,
+                                                    nc);
     else
-      scanp_eval<false, T, S, NS, V, UC, NW>(p, k, err, x, y, agg, aggs[b], more, more_full, rp, i, c0, nr, nc);
+      scanp_eval<false, TRMASK, T, S, NS, V, UC, NW>(p, k, err, x, y, agg, aggs[b], more, more_full, rp, i, c0, nr,
+                                                     nc);
     __syncthreads();
     if (full)
       scanp_write<true, S, V, UC, NW>(p, y, agg, aggs[b], carry_s[b], carry_s[b ^ 1], op, i, c0, nr, nc);

@@ -34,7 +34,12 @@ COOT_HD constexpr bool red_extreme(int r) { return r >= RED_MIN && r <= RED_IMAX
 //   PF_SEGMENTED  dim-1 reduction / scan: every column split is its own
 //                 segment (no combine across splits; output i + split * n_rows;
 //                 positions relative to the segment)
-enum { PF_SQRT = 1u, PF_SEGMENTED = 2u };
+//   PF_OUT_RUN    one-pass row scan with a general output of column stride 1
+//                 (a transposed output): each thread's runs of consecutive
+//                 columns are 16-byte aligned and written as vectors
+//   PF_TRUN0 << s one-pass row scan, transposed slot s: each thread's runs of
+//                 consecutive columns are 16-byte aligned and read as vectors
+enum { PF_SQRT = 1u, PF_SEGMENTED = 2u, PF_OUT_RUN = 4u, PF_TRUN0 = 256u };
 
 struct Params {
   // leaf reads ("slots"): device address of element (0,0) of the view read

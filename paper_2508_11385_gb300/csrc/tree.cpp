@@ -484,7 +484,7 @@ Choice choose(const Analysis& an, const coot_mat* leaves, const coot_mat* out) {
     }
     return true;
   };
-  if (an.any_trans) {
+  if (an.any_trans && !(an.scan() && an.scan_direct)) {
     ch.fam = F_TILE;
     ch.vec_ok = aligned(false);
     return ch;
@@ -670,6 +670,15 @@ Program make_program(const Analysis& an, Family fam, bool var_two_pass, bool bou
           add(buf, v, 1, 256);
         }
       }
+    } else if (an.any_trans) {
+      // transposed reads: the one-pass row scan only (a row per thread, the
+      // transposed slots read along the thread's runs of columns)
+      snprintf(buf, sizeof buf, "coot_scanp_v1u16w8");
+      wrap(buf, 256,
+           std::string("scanp_kernel<T_t, S_t, ") + std::to_string(NS) + ", " + std::to_string(NK) + ", 1, 16, 8, " +
+               std::to_string(an.trmask) + ">",
+           "Params", 2);
+      add(buf, 1, 16, 256);
     } else {
       std::vector<std::pair<int, int>> svu = {{V, 2}, {V, 4}, {1, 4}};
       for (auto [v, u] : svu) {

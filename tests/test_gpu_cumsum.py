@@ -236,3 +236,83 @@ def test_one_pass_row_scan_is_float_float_accurate(monkeypatch):
     exact_f32 = r.value.astype(np.float32).astype(np.float64)
     ulp = np.spacing(np.abs(exact_f32).astype(np.float32)).astype(np.float64)
     assert np.all(np.abs(y - exact_f32) <= ulp)
+
+
+# ---------------------------------------------------------------------------
+# trees with transposed reads scanned in one pass: along dim 1 directly (the
+# transposed slots read along each thread's run of columns), along dim 0 over
+# the transposed problem (the output written transposed); both when the scan
+# lines outnumber 32 x the SMs.  16-byte aligned runs are read and written as
+# vectors, others element by element.
+# ---------------------------------------------------------------------------
+def _sms():
+    return torch.cuda.get_device_properties(0).multi_processor_count
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64", "bf16", "f16", "i32"])
+@pytest.mark.parametrize("dim", [0, 1])
+@pytest.mark.parametrize("ragged", [0, 1])
+def test_transposed_tree_scanned_in_one_pass(dtype, dim, ragged):
+    long_, short = 32 * _sms() + 7, 300 + ragged  # ragged: runs of the output not 16-byte aligned
+    m, n = (long_, short) if dim == 1 else (short, long_)
+    A = parity.rand(n, m, dtype, seed=60)      # read transposed
+    B = parity.rand(m, n, dtype, seed=61)
+    C = parity.rand(m, n, dtype, seed=62)
+    prog = "A trans B %% C + cumsum:%d" % dim
+    parity.check(prog, [A, B, C], dtype)
+    info = coot.last_launch()
+    assert info["kernel"] == "coot_scanp_v1u16w8" and info["n_launches"] == 1, info
+
+
+@pytest.mark.parametrize("dtype", ["f32", "i32"])
+@pytest.mark.parametrize("dim", [0, 1])
+def test_transposed_scan_of_unaligned_and_broadcast_views(dtype, dim):
+    long_, short = 32 * _sms() + 3, 97
+    m, n = (long_, short) if dim == 1 else (short, long_)
+    # transposed reads of views that start one element into their buffer (no
+    # vector runs), a column and a row repeated over the tree
+    A = parity.strided(n, m, dtype, ld_extra=5, offset=1, seed=63)
+    B = parity.strided(m, n, dtype, ld_extra=2, offset=1, seed=64)
+    col = parity.rand(m, 1, dtype, seed=65)
+    row = parity.rand(1, n, dtype, seed=66)
+    prog = "A trans B - C each_col:%d %% D each_row:%d + cumsum:%d" % (n, m, dim)
+    parity.check(prog, [A, B, col, row], dtype)
+    assert coot.last_launch()["kernel"] == "coot_scanp_v1u16w8"
+
+
+def test_transposed_scan_falls_back_to_two_steps_for_short_lines():
+    # fewer scan lines than 32 x the SMs: materialised, then scanned
+    A = parity.rand(500, 200, "f32", seed=67)
+    B = parity.rand(200, 500, "f32", seed=68)
+    parity.check("A trans B + cumsum:1", [A, B], "f32")
+    assert coot.last_launch()["n_launches"] >= 2
+
+
+@pytest.fixture
+def tuned(monkeypatch):
+    # the module's context swapped for an autotuning one (the benchmark's
+    # configuration): every kernel variant runs on the tuner's scratch output
+    from paper_2508_11385_gb300 import expr as E
+    from paper_2508_11385_gb300 import lib as L
+
+    dev = torch.cuda.current_device()
+    ctx = L.coot_ctx_create(dev, L.CTX_TUNE | L.CTX_NO_DISK_CACHE)
+    monkeypatch.setitem(E._ctxs, dev, ctx)
+    yield ctx
+    torch.cuda.synchronize()
+    monkeypatch.undo()
+    L.coot_ctx_destroy(ctx)
+
+
+@pytest.mark.parametrize("prog", ["A trans B %% C + cumsum:%d", "A trans cumsum:%d"])
+@pytest.mark.parametrize("dim", [0, 1])
+def test_transposed_scans_with_autotuning(tuned, prog, dim):
+    # the tuner times every variant on a plain scratch output, whatever the
+    # call's output (here transposed, for dim 0)
+    long_, short = 32 * _sms() + 40, 600
+    m, n = (long_, short) if dim == 1 else (short, long_)
+    A = parity.rand(n, m, "f32", seed=70)
+    B = parity.rand(m, n, "f32", seed=71)
+    C = parity.rand(m, n, "f32", seed=72)
+    p = prog % dim
+    parity.check(p, [A, B, C] if "B" in p else [A], "f32")

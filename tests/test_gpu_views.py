@@ -150,3 +150,29 @@ def test_views_are_rejected_where_unsupported():
     up = torch.ones((), dtype=torch.float32, device="cuda")
     with pytest.raises(coot.lib.CootError, match="UNSUPPORTED"):
         loss.backward(up, A, v)
+
+
+def test_diagonal_output_with_autotuning(monkeypatch):
+    # Z.diag() += 1 in an autotuning context: the tuner's scratch output is
+    # plain column-major, whatever the strides of the call's output
+    from paper_2508_11385_gb300 import expr as E
+    from paper_2508_11385_gb300 import lib as L
+
+    dev = torch.cuda.current_device()
+    ctx = L.coot_ctx_create(dev, L.CTX_TUNE | L.CTX_NO_DISK_CACHE)
+    monkeypatch.setitem(E._ctxs, dev, ctx)
+    try:
+        Z = parity.rand(3000, 2900, "f32", seed=16)
+        before = Z.clone()
+        want = oracle.evaluate("A diag:3 #1 +", parity.host([Z]), "f32")
+        d = coot.Mat(Z).diag(3)
+        d += 1
+        torch.cuda.synchronize()
+        parity.compare_matrix(Z.diagonal(3).reshape(-1, 1), want, "f32", "Z.diag(3) += 1, tuned")
+        mask = torch.ones_like(Z, dtype=torch.bool)
+        mask.diagonal(3).fill_(False)
+        assert torch.equal(Z[mask], before[mask])
+    finally:
+        torch.cuda.synchronize()
+        monkeypatch.undo()
+        L.coot_ctx_destroy(ctx)
