@@ -986,7 +986,7 @@ def run_extras(args, leaves, calls, per_tree_ms, bytes_per, dev, stream, peak, p
 
 STATS = ["accu", "min", "index_max", "prod", "stddev", "sum:0", "min:0", "index_max:0", "prod:0", "vardim:0:0",
          "sum:1", "max:1", "index_min:1", "prod:1", "stddevdim:1:1", "cumsum:0", "cumsum:1"]
-STATS_T = ["accu", "sum:0", "index_min:0", "vardim:0:0", "sum:1", "max:1", "prod:1", "cumsum:0"]
+STATS_T = ["accu", "sum:0", "index_min:0", "vardim:0:0", "sum:1", "max:1", "prod:1", "vardim:1:1", "cumsum:0", "cumsum:1"]
 
 
 def bench_gemm(args, dev, stream):

@@ -256,6 +256,9 @@ void shape_launch(coot_ctx* ctx, const cg::Analysis& an, const cg::Choice& ch, c
     const int64_t nrb = std::max<int64_t>(1, ceil_div(R, (int64_t)block * k.vec));
     int64_t nsp = std::max<int64_t>(1, std::min<int64_t>(C, resident / nrb));
     int64_t cps = std::max<int64_t>(1, ceil_div(std::max<int64_t>(C, 1), nsp));
+    // transposed reads go along each row's columns in 16-byte vectors: every
+    // segment starts on a multiple of 16 columns
+    if (an.any_trans) cps = ceil_div(cps, 16) * 16;
     nsp = std::max<int64_t>(1, ceil_div(std::max<int64_t>(C, 1), cps));
     if (an.n_seg() > 1) {  // one split per segment, written separately
       nsp = an.n_seg();
@@ -602,7 +605,7 @@ static coot_status run_fused(coot_ctx* ctx, const cg::Analysis& an, const coot_m
   p.den = (an.red.norm_type == 1) ? (double)per : (double)(per - 1);
   p.flags = (an.red.kind == COOT_R_STDDEV) ? cg::PF_SQRT : 0u;
   if (an.n_seg() > 1) p.flags |= cg::PF_SEGMENTED;
-  if (ch.fam == cg::F_SCAN && an.red.dim == 1) {
+  if ((ch.fam == cg::F_SCAN || ch.fam == cg::F_ROW) && an.red.dim == 1) {
     // the row scan's runs of 16 consecutive columns (transposed slots, a
     // transposed output): vectors where every run starts 16-byte aligned
     for (size_t i = 0; i < an.slots.size(); ++i) {

@@ -618,8 +618,9 @@ __device__ __forceinline__ void col_kernel(const Params& p) {
 // row: map + per-row reduction (dim 1)
 //   block b -> row block rb = b % n_row_blocks, column split sp = b / n_row_blocks
 // ---------------------------------------------------------------------------
-template <class T, class S, int NS, int NK, int RED, int V, int U, bool OUT>
+template <class T, class S, int NS, int NK, int RED, int V, int U, bool OUT, int TRMASK = 0>
 __device__ __forceinline__ void row_kernel(const Params& p) {
+  static_assert(TRMASK == 0 || V == 1, "transposed slots: one row per thread");
   typedef typename ctype<S>::type C;
   typedef typename AccSel<C, RED>::type A;
   __shared__ int am_last;
@@ -651,13 +652,34 @@ __device__ __forceinline__ void row_kernel(const Params& p) {
       // tree: row pointers stepped by the column strides, nothing checked
       const S* rp[NS];
 #pragma unroll
-      for (int s = 0; s < NS; ++s) rp[s] = (const S*)p.src[s] + (gen_slot(s) ? i * p.rs[s] : i);
+      for (int s = 0; s < NS; ++s)
+        rp[s] = (const S*)p.src[s] + ((gen_slot(s) || ((TRMASK >> s) & 1)) ? i * p.rs[s] : i);
       S* op = nullptr;
       if constexpr (OUT) op = (S*)p.out + ((COOT_GM & GM_OUT) ? i * p.out_rs : i);
       for (; jb + U <= j1; jb += U) {
         Vals<C, NS, V> x[U];
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
+          if ((TRMASK >> s) & 1) {
+            // a transposed slot: this row's U columns are consecutive in
+            // memory (16-byte vectors where the host found the rows aligned
+            // and the segment starts on a whole vector)
+            const S* q = rp[s] + jb;
+            constexpr int PER = 16 / (int)sizeof(S);
+            if (U % PER == 0 && j0 % PER == 0 && (p.flags & (PF_TRUN0 << s)) && slot_ok<S>(p, s, q, U)) {
+#pragma unroll
+              for (int g0 = 0; g0 < U / PER; ++g0) {
+                C t[PER];
+                IO<S>::template load<PER>(q + g0 * PER, t);
+#pragma unroll
+                for (int e = 0; e < PER; ++e) x[g0 * PER + e].v[s][0] = t[e];
+              }
+            } else {
+#pragma unroll
+              for (int g = 0; g < U; ++g) x[g].v[s][0] = sload1<S>(p, s, q + g);
+            }
+            continue;
+          }
           const long long ld = p.ld[s];
           const S* q = rp[s] + jb * ld;
 #pragma unroll
@@ -678,15 +700,17 @@ __device__ __forceinline__ void row_kernel(const Params& p) {
       for (int g = 0; g < U; ++g) {
         const long long j = jb + g;
         if (j < j1) {
-          if (fullv) {
 #pragma unroll
-            for (int s = 0; s < NS; ++s) load_rows<S, V>(p, s, i, j, x[g].v[s]);
-          } else {
-#pragma unroll
-            for (int s = 0; s < NS; ++s)
+          for (int s = 0; s < NS; ++s) {
+            if ((TRMASK >> s) & 1) {  // element (i, j) at i rs + j
+              x[g].v[s][0] = sload1<S>(p, s, (const S*)p.src[s] + (i * p.rs[s] + j));
+            } else if (fullv) {
+              load_rows<S, V>(p, s, i, j, x[g].v[s]);
+            } else {
 #pragma unroll
               for (int l = 0; l < V; ++l)
                 x[g].v[s][l] = (i + l < nr) ? sload1<S>(p, s, at_slot<S>(p, s, i + l, j)) : C(0);
+            }
           }
         }
       }

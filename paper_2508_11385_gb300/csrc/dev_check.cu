@@ -64,6 +64,9 @@ K(chk_col_min_i32, 512, (col_kernel<T2, int, 2, 0, RED_MIN, 4, 2, false>))
 K(chk_col_csq_f32, 512, (col_kernel<T3, float, 3, 1, RED_CSQ, 4, 2, true>))
 K(chk_row_imax_f64, 512, (row_kernel<T3, double, 3, 1, RED_IMAX, 2, 2, false>))
 K(chk_row_csq_f32, 512, (row_kernel<T3, float, 3, 1, RED_CSQ, 4, 2, false>))
+K(chk_row_tr_f32, 512, (row_kernel<T3, float, 3, 1, RED_SUM, 1, 16, false, 5>))
+K(chk_row_tr_bf16, 512, (row_kernel<T3, bf16, 3, 1, RED_MAX, 1, 8, false, 2>))
+K(chk_row_tr_prod_f64, 512, (row_kernel<T3, double, 3, 1, RED_PROD, 1, 16, false, 1>))
 KB(chk_tile_imin_dim0, 256, 4, (tile_kernel<T3, float, 3, 1, RED_IMIN, 0, 4, false>))
 KB(chk_tile_csq_dim1, 256, 4, (tile_kernel<T3, double, 3, 1, RED_CSQ, 1, 5, false>))
 KB(chk_tilev_prod_f32, 256, 3, (tilev_kernel<T3, float, 3, 1, RED_PROD, -1, 4, false, 4>))

@@ -485,7 +485,17 @@ Choice choose(const Analysis& an, const coot_mat* leaves, const coot_mat* out) {
     return true;
   };
   if (an.any_trans && !(an.scan() && an.scan_direct)) {
-    ch.fam = F_TILE;
+    // a reduction along dim 1 whose transposed reads are no more than its
+    // direct streams: the row walk, reading each transposed slot along the
+    // thread's run of columns; else the tiles, staged through shared memory
+    int ntr = 0, ndir = 0;
+    for (const Slot& s : an.slots) {
+      if (s.trans) ++ntr;
+      else if (!s.gen) ++ndir;
+    }
+    if (out) ++ndir;
+    const bool along1 = an.red.kind != COOT_R_NONE && !an.scan() && an.red.dim == 1 && an.n_seg() == 1;
+    ch.fam = (along1 && ntr <= ndir) ? F_ROW : F_TILE;
     ch.vec_ok = aligned(false);
     return ch;
   }
@@ -596,10 +606,21 @@ Program make_program(const Analysis& an, Family fam, bool var_two_pass, bool bou
   } else if (fam == F_COL || fam == F_ROW) {
     const char* fn = (fam == F_COL) ? "col" : "row";
     std::vector<std::pair<int, int>> cvu = {{V, 1}, {V, 2}, {V, 4}, {1, 4}};
+    // transposed reads (the row walk only): a row per thread, runs of
+    // consecutive columns (the first length listed is the default)
+    if (an.any_trans) {
+      if (an.esz == 8)
+        cvu = {{1, 8}, {1, 4}, {1, 16}};  // 64-byte runs of 8-byte values
+      else
+        cvu = {{1, 16}, {1, 8}, {1, 4}};
+    }
+    // (an empty reduction of a transposed tree may take the column family:
+    // it reads nothing, so its kernels need no transposed form)
+    const std::string tr = (an.any_trans && fam == F_ROW) ? ", " + std::to_string(an.trmask) : std::string();
     auto one = [&](const char* pass, const char* red, const char* o, int v, int u) {
       snprintf(buf, sizeof buf, "coot_%s%s_v%du%d", fn, pass, v, u);
       wrap(buf, 512, std::string(fn) + "_kernel<T_t, S_t, " + std::to_string(NS) + ", " + std::to_string(NK) + ", " +
-                          red + ", " + std::to_string(v) + ", " + std::to_string(u) + ", " + o + ">");
+                          red + ", " + std::to_string(v) + ", " + std::to_string(u) + ", " + o + tr + ">");
       add(buf, v, u, 512);
     };
     for (auto [v, u] : cvu) {

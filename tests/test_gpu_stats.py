@@ -207,3 +207,43 @@ def test_python_defaults_follow_armadillo():
     assert coot.prod(A, 1).eval().shape == (40, 1)
     assert coot.stddev(A).eval().shape == ()            # var/stddev: all elements unless dim given
     assert coot.var(A, 1, 0).eval().shape == (1, 30)
+
+
+# reductions along dim 1 of trees with transposed reads: the row walk, each
+# transposed slot read along the thread's run of columns (16-byte vectors when
+# the runs are aligned: leading dimension 300; element by element: 301);
+# every run length forced in turn, ragged segments and rows
+ROW_TR = ["sum:1", "mean:1", "max:1", "index_min:1", "prod:1", "vardim:1:1", "stddevdim:1:0"]
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64", "bf16", "i32"])
+@pytest.mark.parametrize("red", ROW_TR)
+@pytest.mark.parametrize("shape", [(1003, 300), (1003, 301), (600, 4100), (70, 9001)])
+def test_row_walk_with_transposed_reads(dtype, red, shape, monkeypatch):
+    # (600, 4100) and (70, 9001): many column segments per row block, whose
+    # starts must fall on whole vectors of the transposed reads
+    if dtype == "i32" and ("var" in red or "stddev" in red or "mean" in red):
+        pytest.skip("not defined for INT32 trees")
+    m, n = shape
+    if red.startswith("prod"):
+        A = _near_one(n, m, dtype, 11)
+        B = _near_one(m, n, dtype, 12)
+        prog = ("A trans B % " if dtype == "i32" else "A trans B + exp ") + red
+    else:
+        A = parity.rand(n, m, dtype, seed=11)
+        B = parity.rand(m, n, dtype, seed=12)
+        prog = "A trans B % B + " + red
+    two = "var" in red or "stddev" in red
+    for u in (16, 8, 4):
+        kname = "coot_row%s_v1u%d" % ("_p1" if two else "", u)
+        monkeypatch.setenv("COOT_FORCE_KERNEL", kname)
+        parity.check(prog, [A, B], dtype)
+        assert coot.last_launch()["kernel"] == kname, coot.last_launch()
+
+
+def test_transposed_majority_stays_on_tiles():
+    # more transposed reads than direct streams: the tile kernels
+    A = parity.rand(300, 1003, "f32", seed=13)
+    B = parity.rand(300, 1003, "f32", seed=14)
+    parity.check("A trans B trans - sum:1", [A, B], "f32")
+    assert coot.last_launch()["kernel"].startswith("coot_tile")
