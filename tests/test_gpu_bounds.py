@@ -100,3 +100,31 @@ def test_a_short_extent_is_caught_and_not_read(bounds_ctx, monkeypatch):
         torch.cuda.synchronize()
         f = L.coot_check_device_flag(bounds_ctx, s)
         assert f & L.FLAG_OUT_OF_BOUNDS, "%s: the short extent was not reported" % prog
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "i32"])
+def test_bounds_build_one_pass_scans(bounds_ctx, dtype, monkeypatch):
+    # the one-pass row scan, forced on the mixed leaves (unaligned view,
+    # broadcasts), then on trees with transposed reads scanned in one pass
+    # along dim 1 (tall) and along dim 0 over the transposed problem (wide)
+    s = torch.cuda.current_stream().cuda_stream
+    leaves = _leaves(dtype, 6)
+    monkeypatch.setenv("COOT_FORCE_KERNEL", "coot_scanp_v1u16w8")
+    for prog in ("A B % cumsum:1", "A D each_col:203 % E each_row:517 + cumsum:1"):
+        for materialise in (False, True):
+            parity.check(prog, leaves, dtype, materialise=materialise)
+            assert coot.last_launch()["kernel"] == "coot_scanp_v1u16w8"
+            assert L.coot_check_device_flag(bounds_ctx, s) == 0, "%s (%s): device flag raised" % (prog, dtype)
+    monkeypatch.delenv("COOT_FORCE_KERNEL")
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    g = workloads.generator(7, "cuda")
+    mk = (lambda r, c: workloads.int_uniform(r, c, -1000, 1000, g, "cuda")) if dtype == "i32" else \
+        (lambda r, c: workloads.uniform(r, c, 0.5, 2.0, dtype, g, "cuda"))
+    long_ = 32 * sms + 5
+    for m, n, dim in ((long_, 37, 1), (37, long_, 0)):
+        At = mk(n + 3, m)[1:1 + n, :]   # read transposed, one element into its buffer
+        B = mk(m, n)
+        prog = "A trans B - cumsum:%d" % dim
+        parity.check(prog, [At, B], dtype)
+        assert coot.last_launch()["kernel"] == "coot_scanp_v1u16w8"
+        assert L.coot_check_device_flag(bounds_ctx, s) == 0, "%s (%s): device flag raised" % (prog, dtype)
