@@ -423,7 +423,9 @@ void load_tuning(coot_ctx* ctx) {
     char* tab = strrchr(line.data(), '\t');
     if (!tab) continue;
     cg::LaunchCfg c;
-    if (sscanf(tab + 1, "%d %d %d %d", &c.kidx, &c.block, &c.blocks_per_sm, &c.split) != 4) continue;
+    char name[128];
+    if (sscanf(tab + 1, "%d %d %d %d %127s", &c.kidx, &c.block, &c.blocks_per_sm, &c.split, name) != 5) continue;
+    c.kname = name;
     *tab = 0;
     ctx->tuned[std::string(line.data())] = c;
   }
@@ -435,7 +437,7 @@ void save_tuning(coot_ctx* ctx, const std::string& key, const cg::LaunchCfg& c) 
   if (path.empty()) return;
   FILE* f = fopen(path.c_str(), "a");  // one short line per append
   if (!f) return;
-  fprintf(f, "%s\t%d %d %d %d\n", key.c_str(), c.kidx, c.block, c.blocks_per_sm, c.split);
+  fprintf(f, "%s\t%d %d %d %d %s\n", key.c_str(), c.kidx, c.block, c.blocks_per_sm, c.split, c.kname.c_str());
   fclose(f);
 }
 
@@ -642,7 +644,7 @@ static coot_status run_fused(coot_ctx* ctx, const cg::Analysis& an, const coot_m
     const std::string key = tune_key(pg, ch);
     auto tu = ctx->tuned.find(key);
     if (tu != ctx->tuned.end() && tu->second.kidx >= 0 && tu->second.kidx < (int)pg.kernels.size() &&
-        (ch.vec_ok || pg.kernels[tu->second.kidx].vec == 1)) {
+        pg.kernels[tu->second.kidx].name == tu->second.kname && (ch.vec_ok || pg.kernels[tu->second.kidx].vec == 1)) {
       cfg = tu->second;
     } else {
       cfg.kidx = default_variant(pg, ch);
@@ -657,6 +659,7 @@ static coot_status run_fused(coot_ctx* ctx, const cg::Analysis& an, const coot_m
         Launch base = L;
         s = tune(ctx, an, ch, pg, m, base, stream, &cfg);
         if (s) return s;
+        cfg.kname = pg.kernels[cfg.kidx].name;
         ctx->tuned[key] = cfg;
         save_tuning(ctx, key, cfg);
       }
@@ -803,6 +806,7 @@ coot_status tune(coot_ctx* ctx, const cg::Analysis& an, const cg::Choice& ch, co
         if (times[1] < best_ms) {
           best_ms = times[1];
           best->kidx = ki;
+          best->kname = k.name;
           best->block = block;
           best->blocks_per_sm = bps;
           best->split = split;

@@ -180,6 +180,7 @@ struct LaunchCfg {
   int block = 256;
   int blocks_per_sm = 4;
   int split = 0;  // col: warps per column (0: heuristic)
+  std::string kname;  // the kernel's name (a stored tuning is used only if it still names kernel kidx)
 };
 
 // A fused call prepared once per (tree, layouts, alignment, reduction):

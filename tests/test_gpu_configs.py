@@ -147,3 +147,36 @@ def test_differentiation_full_size_sampled():
         for g, ref, ab in ((Wp.grad, gW, aW), (Xp.grad, gX, aX)):
             gg = g[r0:r0 + b, c0:c0 + b].double().cpu().numpy()
             assert np.all(np.abs(gg - ref) <= 16 * u * ab + 1e-30)
+
+
+def test_stored_tuning_names_its_kernel(tmp_path, monkeypatch, capfd):
+    # the tuning file stores the chosen kernel's name beside its index; an
+    # entry whose name no longer matches the program's kernel at that index
+    # (a program whose variant list changed) is ignored and the call re-tuned
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    monkeypatch.setenv("COOT_CACHE_DIR", str(tmp_path))
+    leaves = workloads.large_trees("f32", n=1024, n_leaves=3, device="cuda")
+    prog = "A B % C + sum:1"
+    sp = torch.cuda.current_stream().cuda_stream
+
+    def run(flags):
+        ctx = L.coot_ctx_create(0, flags)
+        try:
+            bench.Call(prog, leaves, True, ctx=ctx)(sp)
+            torch.cuda.synchronize()
+        finally:
+            L.coot_ctx_destroy(ctx)
+
+    run(L.CTX_TUNE)
+    files = list(tmp_path.glob("tune-*.txt"))
+    assert len(files) == 1
+    lines = [ln for ln in files[0].read_text().splitlines() if ln.strip()]
+    assert lines and all(len(ln.split("\t")[1].split()) == 5 for ln in lines)
+    assert all(ln.split()[-1].startswith("coot_") for ln in lines)
+    capfd.readouterr()
+    run(L.CTX_TUNE | L.CTX_LOG)  # the stored entry is used: no candidates timed
+    assert "candidate" not in capfd.readouterr().err
+    files[0].write_text("".join(ln.rsplit(" ", 1)[0] + " coot_no_such_kernel\n" for ln in lines))
+    run(L.CTX_TUNE | L.CTX_LOG)  # a stale name: tuned again
+    assert "candidate" in capfd.readouterr().err
