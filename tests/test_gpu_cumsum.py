@@ -316,3 +316,16 @@ def test_transposed_scans_with_autotuning(tuned, prog, dim):
     C = parity.rand(m, n, "f32", seed=72)
     p = prog % dim
     parity.check(p, [A, B, C] if "B" in p else [A], "f32")
+
+
+@pytest.mark.parametrize("dtype", ["f32", "i32"])
+def test_transposed_scan_along_dim0_of_views(dtype):
+    # the transposed problem of trees with a diagonal broadcast (a general
+    # read with column stride 0) and a submatrix view (column stride of its
+    # parent), scanned along dim 0
+    n = 32 * _sms() + 9
+    A = parity.rand(n, 37, dtype, seed=80)        # read transposed: 37 x n
+    B = parity.rand(40, n + 6, dtype, seed=81)    # its 37 x n block from (1, 2)
+    C = parity.rand(37, 37, dtype, seed=82)       # diag: 37 x 1, repeated over n columns
+    parity.check("A trans B submat:1:2:37:%d - C diag each_col:%d + cumsum:0" % (n, n), [A, B, C], dtype)
+    assert coot.last_launch()["kernel"] == "coot_scanp_v1u16w8"
