@@ -1472,7 +1472,7 @@ __device__ __forceinline__ void scan_row_kernel(const Params& p) {
 // found them aligned (flag PF_TRUN0 << s).
 template <bool FULL, int TRMASK, class S, int NS, int V, int UC, class X>
 __device__ __forceinline__ void scanp_load(const Params& p, const S* const (&rp)[NS], long long i, long long c0,
-                                           long long nr, long long nc, X (&x)[UC]) {
+                                           long long nr, long long nc, X (&x)[UC], bool coop, long long i0) {
   typedef typename X::C C;
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
@@ -1480,7 +1480,28 @@ __device__ __forceinline__ void scanp_load(const Params& p, const S* const (&rp)
       static_assert(TRMASK == 0 || V == 1, "transposed slots: one row per thread");
       const S* q = rp[s] + c0;
       constexpr int PER = 16 / (int)sizeof(S);
-      if (FULL && UC % PER == 0 && (p.flags & (PF_TRUN0 << s)) && slot_ok<S>(p, s, q, UC)) {
+      constexpr int CPR = UC / PER > 0 ? UC / PER : 1;  // 16-byte pieces of a row's run
+      if (FULL && UC % PER == 0 && 32 % CPR == 0 && coop && (p.flags & (PF_TRUN0 << s))) {
+        // the warp reads the band's runs together: lanes CPR apart take
+        // consecutive pieces of one row, so a load instruction covers
+        // 32 / CPR whole runs; x[] holds the pieces until scanp_unstage
+        // hands every lane its own row
+        const int lane = threadIdx.x & 31;
+#pragma unroll
+        for (int g = 0; g < CPR; ++g) {
+          const long long row = i0 + g * (32 / CPR) + lane / CPR;
+          const S* qq = (const S*)p.src[s] + row * p.rs[s] + c0 + (lane % CPR) * PER;
+          C t[PER];
+          if (slot_ok<S>(p, s, qq, PER)) {
+            IO<S>::template load<PER>(qq, t);
+          } else {
+#pragma unroll
+            for (int e = 0; e < PER; ++e) t[e] = C(0);
+          }
+#pragma unroll
+          for (int e = 0; e < PER; ++e) x[g * PER + e].v[s][0] = t[e];
+        }
+      } else if (FULL && UC % PER == 0 && (p.flags & (PF_TRUN0 << s)) && slot_ok<S>(p, s, q, UC)) {
 #pragma unroll
         for (int g = 0; g < UC / PER; ++g) {
           C t[PER];
@@ -1510,6 +1531,39 @@ __device__ __forceinline__ void scanp_load(const Params& p, const S* const (&rp)
   }
 }
 
+// The pieces of the cooperatively read transposed slots go through the warp's
+// shared-memory tile (32 rows of UC values, rows padded by 16 bytes), and
+// every lane takes back its own row's UC values.  Called with the whole warp
+// (the cooperative form is uniform over it).
+template <int TRMASK, class S, int NS, int UC, class X>
+__device__ __forceinline__ void scanp_unstage(const Params& p, X (&x)[UC], typename X::C* tile) {
+  typedef typename X::C C;
+  constexpr int PER = 16 / (int)sizeof(S), CPR = UC / PER > 0 ? UC / PER : 1;
+  constexpr int GC = 16 / (int)sizeof(C), TRS = UC + GC;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    if (!((TRMASK >> s) & 1) || !(p.flags & (PF_TRUN0 << s))) continue;
+    __syncwarp();
+#pragma unroll
+    for (int g = 0; g < CPR; ++g) {
+      C* d = tile + (g * (32 / CPR) + lane / CPR) * TRS + (lane % CPR) * PER;
+#pragma unroll
+      for (int e0 = 0; e0 < PER; e0 += GC) {
+        C v[GC];
+#pragma unroll
+        for (int e = 0; e < GC; ++e) v[e] = x[g * PER + e0 + e].v[s][0];
+        sts_group<C, GC>(d + e0, v);
+      }
+    }
+    __syncwarp();
+    C r[UC];
+    lds_vec<C, UC>(tile + lane * TRS, r);
+#pragma unroll
+    for (int u = 0; u < UC; ++u) x[u].v[s][0] = r[u];
+  }
+}
+
 // One panel of warp w in two halves around the block barrier, which stays in
 // scanp_kernel: a thread takes the checked (FULL = false) or the unchecked
 // form of each half by its own rows and columns, so the forms may differ
@@ -1520,9 +1574,13 @@ template <bool FULL, int TRMASK, class T, class S, int NS, int V, int UC, int NW
 __device__ __forceinline__ void scanp_eval(const Params& p, const K& k, u32& err, X (&x)[UC], C (&y)[UC][V],
                                            ScanAcc<C> (&agg)[V], ScanAcc<C> (&aggs)[NW][32 * V], bool more,
                                            bool more_full, const S* const (&rp)[NS], long long i, long long c0,
-                                           long long nr, long long nc) {
+                                           long long nr, long long nc, bool coop, bool more_coop, long long i0,
+                                           C* tile) {
   constexpr int PW = NW * UC;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if constexpr (FULL && TRMASK != 0 && V == 1 && UC % (16 / (int)sizeof(S)) == 0) {
+    if (coop) scanp_unstage<TRMASK, S, NS, UC>(p, x, tile);
+  }
 #pragma unroll
   for (int l = 0; l < V; ++l) agg[l].init();
 #pragma unroll
@@ -1538,9 +1596,9 @@ __device__ __forceinline__ void scanp_eval(const Params& p, const K& k, u32& err
     }
   if (more) {
     if (more_full)
-      scanp_load<true, TRMASK, S, NS, V, UC>(p, rp, i, c0 + PW, nr, nc, x);
+      scanp_load<true, TRMASK, S, NS, V, UC>(p, rp, i, c0 + PW, nr, nc, x, more_coop, i0);
     else if (i < nr)
-      scanp_load<false, TRMASK, S, NS, V, UC>(p, rp, i, c0 + PW, nr, nc, x);
+      scanp_load<false, TRMASK, S, NS, V, UC>(p, rp, i, c0 + PW, nr, nc, x, false, i0);
   }
 #pragma unroll
   for (int l = 0; l < V; ++l) aggs[w][lane * V + l] = agg[l];
@@ -1553,7 +1611,7 @@ template <bool FULL, class S, int V, int UC, int NW, class C>
 __device__ __forceinline__ void scanp_write(const Params& p, const C (&y)[UC][V], const ScanAcc<C> (&agg)[V],
                                             const ScanAcc<C> (&aggs)[NW][32 * V], const ScanAcc<C> (&carry_in)[32 * V],
                                             ScanAcc<C> (&carry_out)[32 * V], S* op, long long i, long long c0,
-                                            long long nr, long long nc) {
+                                            long long nr, long long nc, bool coop, long long i0, C* tile) {
   typedef ScanAcc<C> A;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   A base[V];
@@ -1575,6 +1633,38 @@ __device__ __forceinline__ void scanp_write(const Params& p, const C (&y)[UC][V]
   S* o = op + c0 * old;
   constexpr int PER = 16 / (int)sizeof(S);
   if constexpr (V == 1 && UC % PER == 0 && (COOT_GM & GM_OUT) != 0) {
+    constexpr int CPR = UC / PER, GC = 16 / (int)sizeof(C), TRS = UC + GC;
+    if constexpr (FULL && 32 % CPR == 0) {
+      if (coop && (p.flags & PF_OUT_RUN)) {
+        // a transposed output written by the whole warp: every lane puts its
+        // row's UC results in the warp's tile, then lanes CPR apart write
+        // consecutive 16-byte pieces of one row's run
+        C t[UC];
+#pragma unroll
+        for (int u = 0; u < UC; ++u) {
+          base[0].add(y[u][0]);
+          t[u] = base[0].out();
+        }
+        __syncwarp();
+#pragma unroll
+        for (int g = 0; g < UC / GC; ++g) {
+          C v[GC];
+#pragma unroll
+          for (int e = 0; e < GC; ++e) v[e] = t[g * GC + e];
+          sts_group<C, GC>(tile + lane * TRS + g * GC, v);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int g = 0; g < CPR; ++g) {
+          const int row = g * (32 / CPR) + lane / CPR, ch = lane % CPR;
+          C v[PER];
+          lds_vec<C, PER>(tile + row * TRS + ch * PER, v);
+          S* d = (S*)p.out + (i0 + row) * p.out_rs + c0 * p.out_ld + ch * PER;
+          if (out_ok<S>(p, d, PER)) IO<S>::template store<PER>(d, v);
+        }
+        return;
+      }
+    }
     // a transposed output: the thread's UC results are consecutive
     if (FULL && (p.flags & PF_OUT_RUN) && out_ok<S>(p, o, UC)) {
 #pragma unroll
@@ -1620,6 +1710,11 @@ __device__ __forceinline__ void scanp_kernel(const Params& p) {
   constexpr int RB = 32 * V, PW = NW * UC;
   __shared__ A aggs[2][NW][RB];
   __shared__ A carry_s[2][RB];
+  // a warp's tile for its band's transposed runs (reads and a transposed
+  // output): 32 rows of UC values, rows padded by 16 bytes
+  constexpr bool STAGE = V == 1 && (TRMASK != 0 || (COOT_GM & GM_OUT) != 0);
+  constexpr int TRS = UC + 16 / (int)sizeof(C);
+  __shared__ __align__(16) C tiles[STAGE ? NW : 1][STAGE ? 32 * TRS : 4];
   if (blockDim.x != 32 * NW) return;  // the panel needs exactly NW warps (uniform over the block)
   Scal<C, NK> k;
 #pragma unroll
@@ -1642,13 +1737,19 @@ __device__ __forceinline__ void scanp_kernel(const Params& p) {
     rp[s] = (const S*)p.src[s] + ((gen_slot(s) || ((TRMASK >> s) & 1)) ? ii * p.rs[s] : ii);
   S* op = (S*)p.out + ((COOT_GM & GM_OUT) ? ii * p.out_rs : ii);
   const long long npan = (nc + PW - 1) / PW;
+  C* tile = tiles[STAGE ? w : 0];
+  // the band's first row, and whether all its rows are inside the tree (then
+  // a warp whose UC columns are inside reads and writes transposed runs
+  // together: uniform over the warp)
+  const long long i0 = (long long)blockIdx.x * RB;
+  const bool band_full = STAGE && (i0 + RB <= nr);
   Vals<C, NS, V> x[UC];
   {
     const long long c0 = (long long)w * UC;
     if (fullv && c0 + UC <= nc)
-      scanp_load<true, TRMASK, S, NS, V, UC>(p, rp, i, c0, nr, nc, x);
+      scanp_load<true, TRMASK, S, NS, V, UC>(p, rp, i, c0, nr, nc, x, band_full, i0);
     else if (i < nr)
-      scanp_load<false, TRMASK, S, NS, V, UC>(p, rp, i, c0, nr, nc, x);
+      scanp_load<false, TRMASK, S, NS, V, UC>(p, rp, i, c0, nr, nc, x, false, i0);
   }
   // every thread runs every panel and reaches the one barrier below once per
   // panel, whatever form of the halves it takes
@@ -1660,17 +1761,20 @@ __device__ __forceinline__ void scanp_kernel(const Params& p) {
     const bool more_full = fullv && (c0 + PW + UC <= nc);
     C y[UC][V];
     A agg[V];
+    const bool coop = band_full && full, more_coop = band_full && more_full;
     if (full)
       scanp_eval<true, TRMASK, T, S, NS, V, UC, NW>(p, k, err, x, y, agg, aggs[b], more, more_full, rp, i, c0, nr,
-                                                    nc);
+                                                    nc, coop, more_coop, i0, tile);
     else
       scanp_eval<false, TRMASK, T, S, NS, V, UC, NW>(p, k, err, x, y, agg, aggs[b], more, more_full, rp, i, c0, nr,
-                                                     nc);
+                                                     nc, false, false, i0, tile);
     __syncthreads();
     if (full)
-      scanp_write<true, S, V, UC, NW>(p, y, agg, aggs[b], carry_s[b], carry_s[b ^ 1], op, i, c0, nr, nc);
+      scanp_write<true, S, V, UC, NW>(p, y, agg, aggs[b], carry_s[b], carry_s[b ^ 1], op, i, c0, nr, nc, coop, i0,
+                                      tile);
     else
-      scanp_write<false, S, V, UC, NW>(p, y, agg, aggs[b], carry_s[b], carry_s[b ^ 1], op, i, c0, nr, nc);
+      scanp_write<false, S, V, UC, NW>(p, y, agg, aggs[b], carry_s[b], carry_s[b ^ 1], op, i, c0, nr, nc, false, i0,
+                                       tile);
   }
   if (err) atomicOr(p.err_flag, err);
 }
