@@ -221,6 +221,60 @@ template <class S, int V, class C> __device__ __forceinline__ void store_rows(co
 }
 
 // ---------------------------------------------------------------------------
+// 16-byte groups of the compute type in shared memory
+// ---------------------------------------------------------------------------
+// V values of the compute type from 16-byte aligned shared memory, one
+// 16-byte access per 16 bytes
+struct __align__(16) W4 {
+  u32 w[4];
+};
+template <class C> struct FromWords;
+template <> struct FromWords<float> {
+  static constexpr int per = 4;
+  __device__ static float get(const u32* w, int l) { return __uint_as_float(w[l]); }
+};
+template <> struct FromWords<int> {
+  static constexpr int per = 4;
+  __device__ static int get(const u32* w, int l) { return (int)w[l]; }
+};
+template <> struct FromWords<double> {
+  static constexpr int per = 2;
+  __device__ static double get(const u32* w, int l) { return __hiloint2double((int)w[2 * l + 1], (int)w[2 * l]); }
+};
+template <class C> struct ToWords;
+template <> struct ToWords<float> {
+  __device__ static void put(u32* w, int l, float x) { w[l] = __float_as_uint(x); }
+};
+template <> struct ToWords<int> {
+  __device__ static void put(u32* w, int l, int x) { w[l] = (u32)x; }
+};
+template <> struct ToWords<double> {
+  __device__ static void put(u32* w, int l, double x) {
+    w[2 * l] = (u32)__double2loint(x);
+    w[2 * l + 1] = (u32)__double2hiint(x);
+  }
+};
+// one 16-byte group of the compute type to 16-byte aligned shared memory
+template <class C, int G> __device__ __forceinline__ void sts_group(C* p, const C (&v)[G]) {
+  static_assert(G * sizeof(C) == 16, "one 16-byte group");
+  W4 t;
+#pragma unroll
+  for (int l = 0; l < G; ++l) ToWords<C>::put(t.w, l, v[l]);
+  *reinterpret_cast<W4*>(p) = t;
+}
+template <class C, int V> __device__ __forceinline__ void lds_vec(const C* p, C (&v)[V]) {
+  constexpr int PER = FromWords<C>::per;
+  static_assert(V % PER == 0, "whole 16-byte groups");
+  const W4* q = reinterpret_cast<const W4*>(p);
+#pragma unroll
+  for (int n = 0; n < V / PER; ++n) {
+    W4 t = q[n];
+#pragma unroll
+    for (int l = 0; l < PER; ++l) v[n * PER + l] = FromWords<C>::get(t.w, l);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // per-element contribution of the root to the reduction
 // ---------------------------------------------------------------------------
 // pos: the element's position in its reduction (column-major linear index for
@@ -624,6 +678,12 @@ __device__ __forceinline__ void row_kernel(const Params& p) {
   typedef typename ctype<S>::type C;
   typedef typename AccSel<C, RED>::type A;
   __shared__ int am_last;
+  // transposed runs read by a whole warp (blocks of up to 8 warps): a tile of
+  // 32 rows of U values per warp, rows padded by 16 bytes
+  constexpr int PER = 16 / (int)sizeof(S), CPR = U / PER > 0 ? U / PER : 1, GC = 16 / (int)sizeof(C);
+  constexpr bool COOP = TRMASK != 0 && U % PER == 0 && 32 % CPR == 0;
+  constexpr int TRS = U + GC;
+  __shared__ __align__(16) C rtiles[COOP ? 8 : 1][COOP ? 32 * TRS : 4];
   Scal<C, NK> k;
 #pragma unroll
   for (int q = 0; q < NK; ++q) k.k[q] = scalar_from_bits<C>(p.k[q]);
@@ -656,6 +716,12 @@ __device__ __forceinline__ void row_kernel(const Params& p) {
         rp[s] = (const S*)p.src[s] + ((gen_slot(s) || ((TRMASK >> s) & 1)) ? i * p.rs[s] : i);
       S* op = nullptr;
       if constexpr (OUT) op = (S*)p.out + ((COOT_GM & GM_OUT) ? i * p.out_rs : i);
+      // a warp whose 32 rows are all inside the tree reads transposed runs
+      // together (uniform over the warp)
+      const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+      const long long iw = i - lane;
+      const bool coop = COOP && blockDim.x <= 256 && iw + 32 <= nr && j0 % PER == 0;
+      C* tile = rtiles[COOP ? (wp & 7) : 0];
       for (; jb + U <= j1; jb += U) {
         Vals<C, NS, V> x[U];
 #pragma unroll
@@ -665,8 +731,24 @@ __device__ __forceinline__ void row_kernel(const Params& p) {
             // memory (16-byte vectors where the host found the rows aligned
             // and the segment starts on a whole vector)
             const S* q = rp[s] + jb;
-            constexpr int PER = 16 / (int)sizeof(S);
-            if (U % PER == 0 && j0 % PER == 0 && (p.flags & (PF_TRUN0 << s)) && slot_ok<S>(p, s, q, U)) {
+            if (COOP && coop && (p.flags & (PF_TRUN0 << s))) {
+              // lanes CPR apart read consecutive 16-byte pieces of one row's
+              // run; the pieces go to their rows below
+#pragma unroll
+              for (int g = 0; g < CPR; ++g) {
+                const S* qq = (const S*)p.src[s] + (iw + g * (32 / CPR) + lane / CPR) * p.rs[s] + jb +
+                              (lane % CPR) * PER;
+                C t[PER];
+                if (slot_ok<S>(p, s, qq, PER)) {
+                  IO<S>::template load<PER>(qq, t);
+                } else {
+#pragma unroll
+                  for (int e = 0; e < PER; ++e) t[e] = C(0);
+                }
+#pragma unroll
+                for (int e = 0; e < PER; ++e) x[g * PER + e].v[s][0] = t[e];
+              }
+            } else if (U % PER == 0 && j0 % PER == 0 && (p.flags & (PF_TRUN0 << s)) && slot_ok<S>(p, s, q, U)) {
 #pragma unroll
               for (int g0 = 0; g0 < U / PER; ++g0) {
                 C t[PER];
@@ -684,6 +766,33 @@ __device__ __forceinline__ void row_kernel(const Params& p) {
           const S* q = rp[s] + jb * ld;
 #pragma unroll
           for (int g = 0; g < U; ++g, q += ld) rows_from<S, V>(p, s, q, x[g].v[s]);
+        }
+        if constexpr (COOP) {
+          if (coop) {
+            // every cooperatively read slot: the pieces through the warp's
+            // tile, each lane taking back its own row's U values
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+              if (!((TRMASK >> s) & 1) || !(p.flags & (PF_TRUN0 << s))) continue;
+              __syncwarp();
+#pragma unroll
+              for (int g = 0; g < CPR; ++g) {
+                C* d = tile + (g * (32 / CPR) + lane / CPR) * TRS + (lane % CPR) * PER;
+#pragma unroll
+                for (int e0 = 0; e0 < PER; e0 += GC) {
+                  C v[GC];
+#pragma unroll
+                  for (int e = 0; e < GC; ++e) v[e] = x[g * PER + e0 + e].v[s][0];
+                  sts_group<C, GC>(d + e0, v);
+                }
+              }
+              __syncwarp();
+              C r[U];
+              lds_vec<C, U>(tile + lane * TRS, r);
+#pragma unroll
+              for (int u = 0; u < U; ++u) x[u].v[s][0] = r[u];
+            }
+          }
         }
 #pragma unroll
         for (int g = 0; g < U; ++g) {
@@ -978,57 +1087,6 @@ __device__ __forceinline__ void tile_kernel(const Params& p) {
 //   Reductions along a dim use the strip segments of the tile kernel, with
 //   strips of 32 columns (DIM 0) or TM rows (DIM 1).
 // ---------------------------------------------------------------------------
-// V values of the compute type from 16-byte aligned shared memory, one
-// 16-byte access per 16 bytes
-struct __align__(16) W4 {
-  u32 w[4];
-};
-template <class C> struct FromWords;
-template <> struct FromWords<float> {
-  static constexpr int per = 4;
-  __device__ static float get(const u32* w, int l) { return __uint_as_float(w[l]); }
-};
-template <> struct FromWords<int> {
-  static constexpr int per = 4;
-  __device__ static int get(const u32* w, int l) { return (int)w[l]; }
-};
-template <> struct FromWords<double> {
-  static constexpr int per = 2;
-  __device__ static double get(const u32* w, int l) { return __hiloint2double((int)w[2 * l + 1], (int)w[2 * l]); }
-};
-template <class C> struct ToWords;
-template <> struct ToWords<float> {
-  __device__ static void put(u32* w, int l, float x) { w[l] = __float_as_uint(x); }
-};
-template <> struct ToWords<int> {
-  __device__ static void put(u32* w, int l, int x) { w[l] = (u32)x; }
-};
-template <> struct ToWords<double> {
-  __device__ static void put(u32* w, int l, double x) {
-    w[2 * l] = (u32)__double2loint(x);
-    w[2 * l + 1] = (u32)__double2hiint(x);
-  }
-};
-// one 16-byte group of the compute type to 16-byte aligned shared memory
-template <class C, int G> __device__ __forceinline__ void sts_group(C* p, const C (&v)[G]) {
-  static_assert(G * sizeof(C) == 16, "one 16-byte group");
-  W4 t;
-#pragma unroll
-  for (int l = 0; l < G; ++l) ToWords<C>::put(t.w, l, v[l]);
-  *reinterpret_cast<W4*>(p) = t;
-}
-template <class C, int V> __device__ __forceinline__ void lds_vec(const C* p, C (&v)[V]) {
-  constexpr int PER = FromWords<C>::per;
-  static_assert(V % PER == 0, "whole 16-byte groups");
-  const W4* q = reinterpret_cast<const W4*>(p);
-#pragma unroll
-  for (int n = 0; n < V / PER; ++n) {
-    W4 t = q[n];
-#pragma unroll
-    for (int l = 0; l < PER; ++l) v[n * PER + l] = FromWords<C>::get(t.w, l);
-  }
-}
-
 template <class T, class S, int NS, int NK, int RED, int DIM, int TRMASK, bool OUT, int V>
 __device__ __forceinline__ void tilev_kernel(const Params& p) {
   typedef typename ctype<S>::type C;

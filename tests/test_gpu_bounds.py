@@ -128,3 +128,19 @@ def test_bounds_build_one_pass_scans(bounds_ctx, dtype, monkeypatch):
         parity.check(prog, [At, B], dtype)
         assert coot.last_launch()["kernel"] == "coot_scanp_v1u16w8"
         assert L.coot_check_device_flag(bounds_ctx, s) == 0, "%s (%s): device flag raised" % (prog, dtype)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64", "bf16"])
+def test_bounds_build_row_walk_with_transposed_runs(bounds_ctx, dtype):
+    # reductions along dim 1 of trees with a transposed read whose runs are
+    # 16-byte aligned (read by whole warps through shared memory) and a
+    # ragged last warp (read lane by lane)
+    s = torch.cuda.current_stream().cuda_stream
+    g = workloads.generator(8, "cuda")
+    mk = lambda r, c: workloads.uniform(r, c, 0.5, 2.0, dtype, g, "cuda")  # noqa: E731
+    m, n = 1003, 304
+    At, B = mk(n, m), mk(m, n)
+    for prog in ("A trans B % sum:1", "A trans B - max:1", "A trans B + vardim:1:1"):
+        parity.check(prog, [At, B], dtype)
+        assert coot.last_launch()["kernel"].startswith("coot_row"), coot.last_launch()
+        assert L.coot_check_device_flag(bounds_ctx, s) == 0, "%s (%s): device flag raised" % (prog, dtype)
