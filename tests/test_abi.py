@@ -209,6 +209,8 @@ def _tree_from_rpn(L, prog, shape, dtype):
     ("A B % C +", "R_CUMSUM0", "f32"),
     ("A B %", "R_CUMSUM1", "i32"),
     ("A exp", "R_CUMSUM1", "f16"),
+    ("A trans B %", "R_INDEX_MAX1", "bf16"),
+    ("A trans B +", "R_SUM1", "f64"),
 ])
 def test_generated_kernels_compile_for_sm103a(L, prog, red, dtype):
     shape = (256, 256)
@@ -217,7 +219,8 @@ def test_generated_kernels_compile_for_sm103a(L, prog, red, dtype):
     r = {"R_ACCU": L.reduce(L.R_ACCU), "R_NONE": L.reduce(), "R_SUM0": L.reduce(L.R_SUM, 0),
          "R_VAR": L.reduce(L.R_VAR), "R_INDEX_MAX1": L.reduce(L.R_INDEX_MAX, 1), "R_MIN0": L.reduce(L.R_MIN, 0),
          "R_PROD": L.reduce(L.R_PROD), "R_STDDEV1": L.reduce(L.R_STDDEV, 1),
-         "R_CUMSUM0": L.reduce(L.R_CUMSUM, 0), "R_CUMSUM1": L.reduce(L.R_CUMSUM, 1)}[red]
+         "R_CUMSUM0": L.reduce(L.R_CUMSUM, 0), "R_CUMSUM1": L.reduce(L.R_CUMSUM, 1),
+         "R_SUM1": L.reduce(L.R_SUM, 1)}[red]
     if red == "R_NONE" or red.startswith("R_CUMSUM"):
         out = L.mat(BASE + (1 << 34), L.DTYPE_CODE[dtype], *shape)
     src = L.coot_codegen(t, lv, out, r)
@@ -242,3 +245,21 @@ def test_context_creation_without_gpu_fails_cleanly(L):
         pytest.skip("a GPU is present")
     with pytest.raises(L.CootError, match="COOT_ERR_CUDA|COOT_ERR_INVALID"):
         L.coot_ctx_create(0, 0)
+
+
+def test_row_programs_carry_the_kernels_the_launcher_names(L):
+    # the launcher picks these kernels by name: the one-pass row scan for
+    # cumsum along dim 1, and the row walk with transposed reads for a
+    # reduction along dim 1 whose transposed reads are no more than its
+    # direct streams (more transposed reads stay on the tiles)
+    shape = (256, 256)
+    t, lv = _tree_from_rpn(L, "A B %", shape, "f32")
+    out = L.mat(BASE + (1 << 34), L.DTYPE_CODE["f32"], *shape)
+    buf = L.coot_codegen(t, lv, out, L.reduce(L.R_CUMSUM, 1))
+    assert "coot_scanp_v1u16w8" in buf and "scanp_kernel<" in buf
+    t, lv = _tree_from_rpn(L, "A trans B %", shape, "f32")
+    buf = L.coot_codegen(t, lv, None, L.reduce(L.R_SUM, 1))
+    assert "row_kernel<" in buf and "coot_row_v1u16" in buf and "tilev_kernel<" not in buf
+    t, lv = _tree_from_rpn(L, "A trans B trans +", shape, "f32")
+    buf = L.coot_codegen(t, lv, None, L.reduce(L.R_SUM, 1))
+    assert "row_kernel<" not in buf and "tile" in buf
