@@ -1521,6 +1521,10 @@ __device__ __forceinline__ void scan_row_kernel(const Params& p) {
 // next panel's carry.  Every row is read and written once and no block waits
 // on another; the order of additions is fixed by (V, UC, NW), so results are
 // deterministic.  The next panel's loads are issued before the barrier.
+// Transposed slots (TRMASK, V = 1) and a transposed output (a general output
+// of column stride 1) have each row's UC columns consecutive in memory; in a
+// band whose 32 rows are all inside the tree a warp moves those runs together
+// through its tile in shared memory (scanp_load / scanp_unstage / scanp_write).
 // ---------------------------------------------------------------------------
 // the UC columns from c0 of every slot at this thread's rows.  FULL: all V
 // rows and all UC columns are inside the tree (no checks); else rows at or
